@@ -1,0 +1,277 @@
+"""Seeded synthetic inputs: latents, hyperlatents and model weights.
+
+This module only draws random numbers and lays them out.  It computes none
+of the context model's arithmetic, so both the CUDA library's tests and the
+FP64 oracle can take their inputs from it.
+
+Latents follow the stand-in for the paper's 1080p test material (Sec. 4.1 of
+the paper evaluates on UVG, MCL-JCV and HEVC-B at 1920x1080, padded to
+1088x1920, i.e. a 68x120 latent grid after the /16 feature transform): per
+channel a separable 2D AR(1) Gaussian field with correlation ``rho`` in both
+directions, scaled by a per-position sigma drawn log-uniformly from
+[0.1, 8] and rounded.  P-frames mix the previous frame's field with a fresh
+one (temporal AR(1), ``rho_t``).  Hyperlatents carry a coarse copy of the
+local scale plus noise.  Weights are random with fan-in scaling.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, asdict, field
+
+import numpy as np
+from scipy.signal import lfilter
+
+
+@dataclass(frozen=True)
+class ModelConfig:
+    """Sizes of one context model and one latent frame.
+
+    H, W, C    latent grid and channels
+    Hh, Wh, Ch hyperprior grid and channels, r = upsampling factor
+    d, nh, F   model width, attention heads, SwiGLU hidden width
+    L          blocks in each spatial module (plus one accumulator block)
+    k          spatial window size (k x k)
+    temporal   1: Context Transformer + temporal cross-attention (P-frames)
+    Lc, Tf     Context Transformer blocks, frames in the temporal window
+    mask       0: step label 2i+j; 1: cyclic s = 4 label
+    """
+    H: int
+    W: int
+    C: int
+    Hh: int
+    Wh: int
+    Ch: int
+    r: int
+    d: int
+    nh: int
+    F: int
+    L: int
+    k: int
+    temporal: int = 0
+    Lc: int = 0
+    Tf: int = 3
+    mask: int = 0
+
+    def with_grid(self, H: int, W: int) -> "ModelConfig":
+        d = asdict(self)
+        d.update(H=H, W=W, Hh=-(-H // self.r), Wh=-(-W // self.r))
+        return ModelConfig(**d)
+
+    def as_dict(self) -> dict:
+        return asdict(self)
+
+
+def ffn_width(d: int) -> int:
+    """SwiGLU hidden width: 8d/3 rounded up to a multiple of 64."""
+    return -(-(8 * d) // 192) * 64
+
+
+def config(name: str) -> ModelConfig:
+    """Named workloads.
+
+    tiny      8x12x64 latent (128x192 image), hyperprior 4x6x32, d=128,
+              2 blocks per spatial module, 4 heads, 5x5 window, FP32
+    i1080     68x120x192 latent (1088x1920 image), hyperprior 17x30x128,
+              d=384, 8 blocks per module, 6 heads, 7x7 window
+    p1080     i1080 plus an 8-block Context Transformer and temporal
+              cross-attention over the current and 2 previous frames
+    tiny_p    tiny with the temporal path (2 context blocks)
+    tiny_cyc  tiny with the cyclic s = 4 mask
+    """
+    if name == "tiny":
+        return ModelConfig(H=8, W=12, C=64, Hh=4, Wh=6, Ch=32, r=2, d=128, nh=4,
+                           F=ffn_width(128), L=2, k=5)
+    if name == "tiny_p":
+        return ModelConfig(H=8, W=12, C=64, Hh=4, Wh=6, Ch=32, r=2, d=128, nh=4,
+                           F=ffn_width(128), L=2, k=5, temporal=1, Lc=2, Tf=3)
+    if name == "tiny_cyc":
+        return ModelConfig(H=8, W=12, C=64, Hh=4, Wh=6, Ch=32, r=2, d=128, nh=4,
+                           F=ffn_width(128), L=2, k=5, mask=1)
+    if name == "i1080":
+        return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
+                           F=ffn_width(384), L=8, k=7)
+    if name == "p1080":
+        return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
+                           F=ffn_width(384), L=8, k=7, temporal=1, Lc=8, Tf=3)
+    raise KeyError(name)
+
+
+# --------------------------------------------------------------------------
+# Weight packing order (the C-ABI documents the same order)
+# --------------------------------------------------------------------------
+
+@dataclass
+class Tensor:
+    name: str
+    shape: tuple
+    init: str          # gain | lin | lin_res | bias | relbias | normal | const
+    value: float = 0.0
+    fan_in: int = 1
+    matrix: bool = False   # block projection (stored in the compute dtype)
+
+
+def _block(prefix: str, c: ModelConfig, cross: bool, tf_bias: bool, nblocks: int) -> list:
+    d, F, kk = c.d, c.F, c.k * c.k
+    res = 1.0 / math.sqrt(2.0 * nblocks)
+    out = [Tensor(prefix + "g_attn", (d,), "gain")]
+    for nm in ("Wq", "Wk", "Wv"):
+        out.append(Tensor(prefix + nm, (d, d), "lin", fan_in=d, matrix=True))
+    out.append(Tensor(prefix + "Wo", (d, d), "lin_res", value=res, fan_in=d, matrix=True))
+    out.append(Tensor(prefix + "bias", (c.nh, c.Tf, c.k, c.k) if tf_bias else (c.nh, c.k, c.k), "relbias"))
+    if cross:
+        out.append(Tensor(prefix + "g_x", (d,), "gain"))
+        for nm in ("Wxq", "Wxk", "Wxv"):
+            out.append(Tensor(prefix + nm, (d, d), "lin", fan_in=d, matrix=True))
+        out.append(Tensor(prefix + "Wxo", (d, d), "lin_res", value=res, fan_in=d, matrix=True))
+        out.append(Tensor(prefix + "xbias", (c.nh, c.Tf, c.k, c.k), "relbias"))
+    out.append(Tensor(prefix + "g_ffn", (d,), "gain"))
+    out.append(Tensor(prefix + "Wg", (d, F), "lin", fan_in=d, matrix=True))
+    out.append(Tensor(prefix + "Wu", (d, F), "lin", fan_in=d, matrix=True))
+    out.append(Tensor(prefix + "Wd", (F, d), "lin_res", value=res, fan_in=F, matrix=True))
+    return out
+
+
+def weight_spec(c: ModelConfig) -> list:
+    """Tensors of the flat FP32 weight vector, in packing order.
+
+    All projections are [in][out] (used as x . W).  Order: input embedding,
+    hyperprior embedding, [Context Transformer], Spatial Module 1 blocks,
+    accumulator, Spatial Module 2 blocks, heads.
+    """
+    d, C, Ch, F = c.d, c.C, c.Ch, c.F
+    nblocks = 2 * c.L + 1 + (c.Lc if c.temporal else 0)
+    s = [Tensor("gamma_in", (C,), "const", 0.25),
+         Tensor("W_in", (C, d), "lin", fan_in=C),
+         Tensor("b_in", (d,), "bias"),
+         Tensor("gamma_z", (Ch,), "const", 0.5),
+         Tensor("W_hp", (c.r * c.r, Ch, d), "lin", fan_in=Ch),
+         Tensor("b_hp", (d,), "bias")]
+    if c.temporal:
+        s += [Tensor("gamma_c", (C,), "const", 0.25),
+              Tensor("W_c", (C, d), "lin", fan_in=C),
+              Tensor("b_c", (d,), "bias"),
+              Tensor("pad", (d,), "normal")]
+        for l in range(c.Lc):
+            s += _block(f"ctx{l}.", c, cross=False, tf_bias=True, nblocks=nblocks)
+        s.append(Tensor("g_ctx", (d,), "gain"))
+    for l in range(c.L):
+        s += _block(f"sm1.{l}.", c, cross=bool(c.temporal), tf_bias=False, nblocks=nblocks)
+    res = 1.0 / math.sqrt(2.0 * nblocks)
+    s += [Tensor("acc.g_q", (d,), "gain"), Tensor("acc.g_kv", (d,), "gain"),
+          Tensor("acc.Wq", (d, d), "lin", fan_in=d, matrix=True),
+          Tensor("acc.Wk", (d, d), "lin", fan_in=d, matrix=True),
+          Tensor("acc.Wv", (d, d), "lin", fan_in=d, matrix=True),
+          Tensor("acc.Wo", (d, d), "lin_res", value=res, fan_in=d, matrix=True),
+          Tensor("acc.bias", (c.nh, c.k, c.k), "relbias"),
+          Tensor("acc.g_ffn", (d,), "gain"),
+          Tensor("acc.Wg", (d, F), "lin", fan_in=d, matrix=True),
+          Tensor("acc.Wu", (d, F), "lin", fan_in=d, matrix=True),
+          Tensor("acc.Wd", (F, d), "lin_res", value=res, fan_in=F, matrix=True)]
+    for l in range(c.L):
+        s += _block(f"sm2.{l}.", c, cross=bool(c.temporal), tf_bias=False, nblocks=nblocks)
+    s += [Tensor("g_head", (d,), "gain"),
+          Tensor("W1m", (d, d), "lin", fan_in=d), Tensor("b1m", (d,), "bias"),
+          Tensor("W2m", (d, C), "lin", fan_in=d),
+          Tensor("W1s", (d, d), "lin", fan_in=d), Tensor("b1s", (d,), "bias"),
+          Tensor("W2s", (d, C), "lin", fan_in=d),
+          Tensor("gamma_mu", (C,), "const", 2.0), Tensor("beta_mu", (C,), "const", 0.0),
+          Tensor("gamma_sig", (C,), "const", 1.0), Tensor("beta_sig", (C,), "const", math.log(2.0))]
+    return s
+
+
+def weights_count(c: ModelConfig) -> int:
+    return int(sum(int(np.prod(t.shape)) for t in weight_spec(c)))
+
+
+def weights(c: ModelConfig, seed: int = 42) -> np.ndarray:
+    """Flat FP32 weight vector in packing order (seeded PCG64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for t in weight_spec(c):
+        n = int(np.prod(t.shape))
+        if t.init == "const":
+            a = np.full(n, t.value, dtype=np.float64)
+        elif t.init == "gain":
+            a = 1.0 + 0.1 * rng.standard_normal(n)
+        elif t.init == "lin":
+            a = rng.standard_normal(n) / math.sqrt(t.fan_in)
+        elif t.init == "lin_res":
+            a = rng.standard_normal(n) / math.sqrt(t.fan_in) * t.value
+        elif t.init == "bias":
+            a = 0.05 * rng.standard_normal(n)
+        elif t.init == "relbias":
+            a = 0.5 * rng.standard_normal(n)
+        elif t.init == "normal":
+            a = rng.standard_normal(n)
+        else:
+            raise ValueError(t.init)
+        parts.append(a.astype(np.float32))
+    return np.concatenate(parts)
+
+
+def matrix_mask(c: ModelConfig) -> np.ndarray:
+    """Boolean mask over the flat weight vector: True for block projections
+    (the tensors a reduced-precision run stores in its compute dtype)."""
+    out = []
+    for t in weight_spec(c):
+        out.append(np.full(int(np.prod(t.shape)), t.matrix, dtype=bool))
+    return np.concatenate(out)
+
+
+# --------------------------------------------------------------------------
+# Latents and hyperlatents
+# --------------------------------------------------------------------------
+
+def _ar1_axis(e: np.ndarray, rho: float, axis: int) -> np.ndarray:
+    """Stationary unit-variance AR(1) filter along one axis: y0 = e0,
+    y_n = rho y_{n-1} + sqrt(1 - rho^2) e_n."""
+    s = math.sqrt(1.0 - rho * rho)
+    e = np.moveaxis(e, axis, 0).copy()
+    e[0] /= s
+    y = lfilter([s], [1.0, -rho], e, axis=0)
+    return np.moveaxis(y, 0, axis)
+
+
+def ar1_field(rng: np.random.Generator, H: int, W: int, C: int, rho: float) -> np.ndarray:
+    """Separable 2D AR(1) field, unit variance, corr rho^(|di|+|dj|)."""
+    e = rng.standard_normal((H, W, C))
+    return _ar1_axis(_ar1_axis(e, rho, 1), rho, 0)
+
+
+@dataclass
+class Frames:
+    y: np.ndarray        # int16 [nf][H][W][C]
+    z: np.ndarray        # int16 [nf][Hh][Wh][Ch]
+    sigma: np.ndarray    # float64 [H][W]  per-position scale of the latents
+
+
+def frames(c: ModelConfig, nf: int = 1, seed: int = 1000, rho: float = 0.8,
+           rho_t: float = 0.9, sigma_lo: float = 0.1, sigma_hi: float = 8.0) -> Frames:
+    """nf frames of one sequence: AR(1) latents scaled by a static
+    log-uniform per-position sigma, and their hyperlatents."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    H, W, C = c.H, c.W, c.C
+    sig = np.exp(rng.uniform(math.log(sigma_lo), math.log(sigma_hi), size=(H, W)))
+    x = ar1_field(rng, H, W, C, rho)
+    ys, zs = [], []
+    for f in range(nf):
+        if f > 0:
+            x = rho_t * x + math.sqrt(1.0 - rho_t * rho_t) * ar1_field(rng, H, W, C, rho)
+        y = np.clip(np.rint(sig[:, :, None] * x), -32767, 32767).astype(np.int16)
+        ys.append(y)
+        zs.append(_hyper(rng, c, sig))
+    return Frames(y=np.stack(ys), z=np.stack(zs), sigma=sig)
+
+
+def _hyper(rng: np.random.Generator, c: ModelConfig, sig: np.ndarray) -> np.ndarray:
+    """Hyperlatents: the first half of the channels carry 2 log2 of the mean
+    sigma of the r x r block they cover, plus unit noise; the rest is noise
+    with standard deviation 2."""
+    z = np.zeros((c.Hh, c.Wh, c.Ch), dtype=np.float64)
+    for a in range(c.Hh):
+        for b in range(c.Wh):
+            blk = sig[a * c.r:(a + 1) * c.r, b * c.r:(b + 1) * c.r]
+            z[a, b, :c.Ch // 2] = np.rint(2.0 * math.log2(float(blk.mean())))
+    z[:, :, :c.Ch // 2] += np.rint(rng.standard_normal((c.Hh, c.Wh, c.Ch // 2)))
+    z[:, :, c.Ch // 2:] = np.rint(2.0 * rng.standard_normal((c.Hh, c.Wh, c.Ch - c.Ch // 2)))
+    return z.astype(np.int16)

@@ -1,0 +1,159 @@
+"""Dense-mask NumPy formulation of the P-SWA context model, for tiny frames.
+
+Test helper used to pin the oracle.  It follows the same reading of the
+paper as the oracle (Sec. 3.1 block structure, Sec. 3.2 / Fig. 2 masks) but
+is written as a textbook masked transformer: every layer runs full
+[HW x HW] attention with a boolean mask matrix and a bias matrix, instead of
+the oracle's clipped per-position window key lists.  Window clipping, key
+order, bias offsets and the weight packing order (taken here from the
+synthetic-input module's tensor list, not from the oracle's own layout code)
+are therefore computed a second, different way.  Only for small H*W.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2605_20977_gb300 import synth
+
+
+def split_weights(c: synth.ModelConfig, w: np.ndarray) -> dict:
+    out, o = {}, 0
+    for t in synth.weight_spec(c):
+        n = int(np.prod(t.shape))
+        out[t.name] = np.asarray(w[o:o + n], np.float64).reshape(t.shape)
+        o += n
+    assert o == w.size
+    return out
+
+
+def grid_masks(c: synth.ModelConfig):
+    """Boolean [HW, HW] matrices indexed [p, q]: window, A (accumulator),
+    S (spatial self-attention); and the window offset index of q - p."""
+    H, W, w = c.H, c.W, (c.k - 1) // 2
+    ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    ii, jj = ii.ravel(), jj.ravel()
+    if c.mask == 0:
+        lab = 2 * ii + jj
+    else:
+        lab = (ii % 4 + jj % 4) % 4
+    rho = ii * W + jj
+    di = ii[None, :] - ii[:, None]
+    dj = jj[None, :] - jj[:, None]
+    win = (np.abs(di) <= w) & (np.abs(dj) <= w)
+    before = rho[None, :] < rho[:, None]
+    lq, lp = lab[None, :], lab[:, None]
+    A = win & (lq < lp)
+    S = win & (lq <= lp)
+    if c.mask == 0:
+        A &= before
+        S &= before | (rho[None, :] == rho[:, None])
+    off = np.where(win, (di + w) * c.k + (dj + w), 0)
+    return win, A, S, off
+
+
+def rms(x, g):
+    return x / np.sqrt(np.mean(x * x, axis=-1, keepdims=True) + 1e-6) * g
+
+
+def silu(x):
+    return x / (1.0 + np.exp(-x))
+
+
+def attention(Q, K, V, M, B, nh):
+    """Q [P, d], K/V [N, d], M [P, N] bool, B [nh, P, N].  Rows with no
+    visible key give 0."""
+    P, d = Q.shape
+    dh = d // nh
+    out = np.zeros((P, d))
+    for h in range(nh):
+        sl = slice(h * dh, (h + 1) * dh)
+        s = Q[:, sl] @ K[:, sl].T / np.sqrt(dh) + B[h]
+        s = np.where(M, s, -np.inf)
+        has = M.any(axis=1)
+        mx = np.where(has, s.max(axis=1, initial=-np.inf), 0.0)
+        e = np.where(M, np.exp(s - mx[:, None]), 0.0)
+        z = e.sum(axis=1)
+        pr = np.divide(e, z[:, None], out=np.zeros_like(e), where=has[:, None])
+        out[:, sl] = pr @ V[:, sl]
+    return out
+
+
+def ffn(x, Wg, Wu, Wd):
+    return (silu(x @ Wg) * (x @ Wu)) @ Wd
+
+
+def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray):
+    """(mu, sigma) [nf, H, W, C] for a sequence, by the masked parallel pass."""
+    P = split_weights(c, w)
+    H, W, C, d, nh = c.H, c.W, c.C, c.d, c.nh
+    HW = H * W
+    win, A, S, off = grid_masks(c)
+    nf = y.shape[0]
+
+    def bias_of(tab):                     # tab [nh, k, k] -> [nh, HW, HW]
+        return tab.reshape(nh, -1)[:, off]
+
+    # Context Transformer over all frames (time-causal, spatially unmasked).
+    ctx_out = []
+    if c.temporal:
+        g = []
+        for f in range(nf):
+            if f == 0:
+                g.append(np.tile(P["pad"], (HW, 1)))
+            else:
+                g.append((y[f - 1].reshape(HW, C) * P["gamma_c"]) @ P["W_c"] + P["b_c"])
+        for l in range(c.Lc):
+            pre = f"ctx{l}."
+            n = [rms(gf, P[pre + "g_attn"]) for gf in g]
+            Q = [a @ P[pre + "Wq"] for a in n]
+            K = [a @ P[pre + "Wk"] for a in n]
+            V = [a @ P[pre + "Wv"] for a in n]
+            tb = P[pre + "bias"]                          # [nh, Tf, k, k]
+            new = []
+            for f in range(nf):
+                fs = list(range(max(0, f - c.Tf + 1), f + 1))
+                Kc = np.concatenate([K[ff] for ff in fs])
+                Vc = np.concatenate([V[ff] for ff in fs])
+                M = np.concatenate([win for _ in fs], axis=1)
+                B = np.concatenate([tb[:, f - ff].reshape(nh, -1)[:, off] for ff in fs], axis=2)
+                a = g[f] + attention(Q[f], Kc, Vc, M, B, nh) @ P[pre + "Wo"]
+                a = a + ffn(rms(a, P[pre + "g_ffn"]), P[pre + "Wg"], P[pre + "Wu"], P[pre + "Wd"])
+                new.append(a)
+            g = new
+        ctx_out = [rms(gf, P["g_ctx"]) for gf in g]
+
+    def block(pre, x, M, f):
+        n = rms(x, P[pre + "g_attn"])
+        x = x + attention(n @ P[pre + "Wq"], n @ P[pre + "Wk"], n @ P[pre + "Wv"], M,
+                          bias_of(P[pre + "bias"]), nh) @ P[pre + "Wo"]
+        if c.temporal:
+            fs = list(range(max(0, f - c.Tf + 1), f + 1))
+            Kc = np.concatenate([ctx_out[ff] @ P[pre + "Wxk"] for ff in fs])
+            Vc = np.concatenate([ctx_out[ff] @ P[pre + "Wxv"] for ff in fs])
+            Mc = np.concatenate([win for _ in fs], axis=1)
+            Bc = np.concatenate([P[pre + "xbias"][:, f - ff].reshape(nh, -1)[:, off] for ff in fs], axis=2)
+            qx = rms(x, P[pre + "g_x"]) @ P[pre + "Wxq"]
+            x = x + attention(qx, Kc, Vc, Mc, Bc, nh) @ P[pre + "Wxo"]
+        return x + ffn(rms(x, P[pre + "g_ffn"]), P[pre + "Wg"], P[pre + "Wu"], P[pre + "Wd"])
+
+    mus, sigs = [], []
+    for f in range(nf):
+        ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+        zz = z[f][ii // c.r, jj // c.r].reshape(HW, c.Ch) * P["gamma_z"]
+        sub = ((ii % c.r) * c.r + (jj % c.r)).ravel()
+        eh = np.einsum("pc,pcd->pd", zz, P["W_hp"][sub]) + P["b_hp"]
+        x1 = (y[f].reshape(HW, C) * P["gamma_in"]) @ P["W_in"] + P["b_in"]
+        for l in range(c.L):
+            x1 = block(f"sm1.{l}.", x1, S, f)
+        m = rms(x1, P["acc.g_kv"])
+        qa = rms(eh, P["acc.g_q"]) @ P["acc.Wq"]
+        x2 = eh + attention(qa, m @ P["acc.Wk"], m @ P["acc.Wv"], A, bias_of(P["acc.bias"]), nh) @ P["acc.Wo"]
+        x2 = x2 + ffn(rms(x2, P["acc.g_ffn"]), P["acc.Wg"], P["acc.Wu"], P["acc.Wd"])
+        for l in range(c.L):
+            x2 = block(f"sm2.{l}.", x2, S, f)
+        n = rms(x2, P["g_head"])
+        mu = P["gamma_mu"] * (silu(n @ P["W1m"] + P["b1m"]) @ P["W2m"]) + P["beta_mu"]
+        s = P["gamma_sig"] * (silu(n @ P["W1s"] + P["b1s"]) @ P["W2s"]) + P["beta_sig"]
+        sig = np.exp(np.clip(s, np.log(0.11), np.log(256.0)))
+        mus.append(mu.reshape(H, W, C)); sigs.append(sig.reshape(H, W, C))
+    return np.stack(mus), np.stack(sigs)

@@ -1,0 +1,404 @@
+"""Pins of the FP64 oracle against facts fixed outside itself.
+
+Closed forms (RMSNorm, SiLU, SwiGLU, attention special cases, Gaussian
+likelihood), the paper's Fig. 2 grids transcribed by hand, window-mask
+cardinalities, schedule step counts, a dense-mask NumPy formulation of the
+model on tiny frames, schedule equivalence, brute-force causality, CDF table
+invariants, rANS round trips and size bounds, and the data generator's
+statistics.  CPU only.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import dense_ref
+from paper_2605_20977_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(line.split())
+    return rows
+
+
+# ----------------------------------------------------------- elementary ops
+
+def test_rmsnorm_closed_form():
+    # x = (3, 4): mean square 12.5
+    y = O.rmsnorm([3.0, 4.0], [1.0, 2.0])
+    s = math.sqrt(12.5 + 1e-6)
+    assert y == pytest.approx([3.0 / s, 8.0 / s], rel=1e-15)
+    # a constant vector maps to the gain (up to eps)
+    y = O.rmsnorm([5.0] * 8, np.arange(8.0))
+    assert y == pytest.approx(np.arange(8.0) * 5.0 / math.sqrt(25.0 + 1e-6), rel=1e-15)
+
+
+def test_silu_closed_forms():
+    assert O.silu(0.0) == 0.0
+    assert O.silu(1.0) == pytest.approx(1.0 / (1.0 + math.exp(-1.0)), rel=1e-15)
+    for x in (-3.0, -0.5, 0.25, 2.0, 7.0):          # x s(x) - (-x) s(-x) = x
+        assert O.silu(x) - O.silu(-x) == pytest.approx(x, rel=1e-14)
+
+
+def test_matvec_matches_library_matmul():
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(17); W = rng.standard_normal((17, 5))
+    assert O.matvec(x, W) == pytest.approx(x @ W, rel=1e-13, abs=1e-13)
+    # orientation: x . W with W [in][out]; a unit x picks a row of W
+    e = np.zeros(17); e[3] = 1.0
+    assert np.array_equal(O.matvec(e, W), W[3])
+
+
+def test_swiglu_closed_form():
+    # d = F = 1: out = silu(x g) (x u) dw
+    out = O.swiglu([2.0], [[0.5]], [[3.0]], [[-1.5]])
+    assert out[0] == pytest.approx(O.silu(1.0) * 6.0 * -1.5, rel=1e-15)
+    # zero gate projection gives zero output
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(6)
+    assert np.all(O.swiglu(x, np.zeros((6, 4)), rng.standard_normal((6, 4)), rng.standard_normal((4, 6))) == 0.0)
+
+
+def test_attention_special_cases():
+    rng = np.random.default_rng(2)
+    d, nh = 8, 2
+    q = rng.standard_normal(d)
+    K = rng.standard_normal((3, d)); V = rng.standard_normal((3, d))
+    bias = rng.standard_normal((3, nh))
+    # one key: the output is that key's value row
+    assert O.attend(q, K[:1], V[:1], bias[:1], nh) == pytest.approx(V[0], rel=1e-15)
+    # zero query and zero bias: uniform average of the values
+    assert O.attend(np.zeros(d), K, V, np.zeros((3, nh)), nh) == pytest.approx(V.mean(0), rel=1e-14)
+    # empty key set: zero
+    assert np.all(O.attend(q, K[:0], V[:0], bias[:0], nh) == 0.0)
+    # two keys: per head the weight of key 0 is a logistic of the score gap
+    out = O.attend(q, K[:2], V[:2], bias[:2], nh)
+    dh = d // nh
+    for h in range(nh):
+        sl = slice(h * dh, (h + 1) * dh)
+        s0 = q[sl] @ K[0, sl] / math.sqrt(dh) + bias[0, h]
+        s1 = q[sl] @ K[1, sl] / math.sqrt(dh) + bias[1, h]
+        p0 = 1.0 / (1.0 + math.exp(s1 - s0))
+        assert out[sl] == pytest.approx(p0 * V[0, sl] + (1 - p0) * V[1, sl], rel=1e-12, abs=1e-14)
+    # a dominant bias selects its key
+    big = np.zeros((3, nh)); big[2] = 1e3
+    assert O.attend(q, K, V, big, nh) == pytest.approx(V[2], rel=1e-12)
+
+
+# ----------------------------------------------------------- masks, schedules
+
+def test_fig2a_cyclic_labels_golden():
+    g = _golden("fig2a_labels.txt")
+    for a, row in enumerate(range(-2, 6)):
+        for b, col in enumerate(range(-2, 6)):
+            # shift by one period so indices are non-negative; the pattern repeats every 4
+            assert O.label(1, row + 4, col + 4) + 1 == int(g[a][b]), (row, col)
+
+
+def test_fig2b_receptive_field_golden():
+    g = _golden("fig2b_receptive_field.txt")
+    ti, tj = 1 + 4, 1 + 4          # target (1, 1) shifted by one period
+    W = 12
+    for a, di in enumerate(range(-2, 3)):
+        for b, dj in enumerate(range(-2, 3)):
+            qi, qj = ti + di, tj + dj
+            acc = O.visible(1, 0, W, ti, tj, qi, qj)
+            sa = O.visible(1, 1, W, ti, tj, qi, qj)
+            want = g[a][b]
+            assert acc == (want == "A"), (di, dj)
+            assert sa == (want in ("A", "S", "T")), (di, dj)
+
+
+@pytest.mark.parametrize("k,nS,nA", [(5, 13, 11), (7, 24, 22)])
+def test_wavefront_mask_interior_counts(k, nS, nA):
+    c = synth.config("i1080") if k == 7 else synth.config("tiny").with_grid(16, 16)
+    p = 10 * c.W + 10
+    assert len(O.window_keys(c, 1, p)[0]) == nS
+    assert len(O.window_keys(c, 0, p)[0]) == nA
+    # accumulator keys have smaller label and raster index; S adds p and same-step keys
+    idx, _ = O.window_keys(c, 1, p)
+    pi, pj = divmod(p, c.W)
+    for q in idx:
+        qi, qj = divmod(int(q), c.W)
+        assert 2 * qi + qj <= 2 * pi + pj and q <= p
+
+
+def test_wavefront_same_step_keys_k7():
+    # only (i-1, j+2) shares the step and precedes in raster order (Sec. 3.2:
+    # same-step positions are visible to self-attention, not to the accumulator)
+    c = synth.config("i1080")
+    p = 30 * c.W + 40
+    s_only = set(O.window_keys(c, 1, p)[0].tolist()) - set(O.window_keys(c, 0, p)[0].tolist())
+    assert s_only == {p, 29 * c.W + 42}
+
+
+def test_schedule_step_counts():
+    c = synth.config("tiny")
+    order, start = O.schedule(c, 0)
+    assert len(start) - 1 == 2 * (c.H - 1) + (c.W - 1) + 1 == 26
+    assert sorted(order.tolist()) == list(range(c.H * c.W))
+    _, start = O.schedule(c, 1)
+    assert len(start) - 1 == 96
+    c = synth.config("i1080")
+    order, start = O.schedule(c, 0)
+    assert len(start) - 1 == 254
+    assert max(np.diff(start)) == 60
+    _, start = O.schedule(c, 1)
+    assert len(start) - 1 == 8160
+    # cyclic s = 4: four steps regardless of resolution (Sec. 2, Sec. 3.2)
+    for nm in ("tiny_cyc",):
+        cc = synth.config(nm)
+        assert len(O.schedule(cc, 0)[1]) - 1 == 4
+        assert len(O.schedule(cc.with_grid(68, 120), 0)[1]) - 1 == 4
+
+
+# ----------------------------------------------------------- model
+
+@pytest.mark.parametrize("name", ["tiny", "tiny_cyc", "tiny_p"])
+def test_oracle_matches_dense_mask_formulation(name):
+    c = synth.config(name)
+    w = synth.weights(c)
+    fr = synth.frames(c, 3 if c.temporal else 1, seed=7)
+    mu0, s0 = O.run(c, w, fr.y, fr.z, driver=0)
+    mu1, s1 = dense_ref.run(c, w, fr.y, fr.z)
+    assert np.max(np.abs(mu0 - mu1)) < 1e-11
+    assert np.max(np.abs(np.log(s0) - np.log(s1))) < 1e-11
+
+
+def test_weight_layout_count_matches_generator():
+    for nm in ("tiny", "tiny_p", "i1080", "p1080"):
+        c = synth.config(nm)
+        assert O.weights_count(c) == synth.weights_count(c)
+
+
+@pytest.mark.parametrize("name,sched", [("tiny", 0), ("tiny", 1), ("tiny_cyc", 0), ("tiny_p", 0), ("tiny_p", 1)])
+def test_schedules_give_the_masked_pass_bit_exact(name, sched):
+    c = synth.config(name)
+    w = synth.weights(c)
+    fr = synth.frames(c, 3 if c.temporal else 1, seed=11)
+    mu0, s0 = O.run(c, w, fr.y, fr.z, driver=0)
+    mu1, s1 = O.run(c, w, fr.y, fr.z, driver=1, sched=sched)
+    assert np.array_equal(mu0, mu1) and np.array_equal(s0, s1)
+
+
+def _closure(c):
+    """dep[p] = positions whose latent can reach params(p): S^L(A(S^L(p)))."""
+    _, A, S, _ = dense_ref.grid_masks(c)
+    HW = c.H * c.W
+    Si = S.astype(np.int64)
+    reach = np.eye(HW, dtype=np.int64)
+    for _ in range(c.L):
+        reach = (reach @ Si > 0).astype(np.int64)
+    reach = (reach @ A.astype(np.int64) > 0).astype(np.int64)
+    for _ in range(c.L):
+        reach = (reach @ Si > 0).astype(np.int64)
+    return reach > 0
+
+
+def test_causality_brute_force():
+    # perturb the latent at each q and record which parameters change
+    c = synth.config("tiny")
+    w = synth.weights(c)
+    fr = synth.frames(c, 1, seed=3)
+    mu0, s0 = O.run(c, w, fr.y, fr.z)
+    dep = _closure(c)
+    HW = c.H * c.W
+    lab = np.array([2 * (p // c.W) + p % c.W for p in range(HW)])
+    for q in range(HW):
+        y = fr.y.copy()
+        y[0].reshape(HW, c.C)[q] += 5
+        mu, s = O.run(c, w, y, fr.z)
+        changed = np.any((mu != mu0) | (s != s0), axis=-1).reshape(HW)
+        assert np.array_equal(changed, dep[:, q]), q
+        assert np.all(lab[changed] > lab[q]) and np.all(np.nonzero(changed)[0] > q)
+
+
+# ----------------------------------------------------------- rate, tables
+
+def test_likelihood_closed_forms():
+    # mu = 0, sigma = 1, y = 0: erf(1 / (2 sqrt 2))
+    assert O.likelihood(0, 0.0, 1.0) == pytest.approx(0.38292492254802624, rel=1e-15)
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        mu = rng.uniform(-5, 5); sg = math.exp(rng.uniform(math.log(0.11), math.log(60)))
+        # masses of adjacent unit bins telescope to a Gaussian interval mass
+        # (stay above the 1e-9 floor)
+        a = b = round(mu)
+        while O.likelihood(a - 1, mu, sg) > 1e-7:
+            a -= 1
+        while O.likelihood(b + 1, mu, sg) > 1e-7:
+            b += 1
+        tot = sum(O.likelihood(y, mu, sg) for y in range(a, b + 1))
+        r2 = sg * math.sqrt(2.0)
+        want = 0.5 * (math.erf((b + 0.5 - mu) / r2) - math.erf((a - 0.5 - mu) / r2))
+        assert tot == pytest.approx(want, abs=1e-13)
+        assert want > 1 - 1e-5
+        u = rng.integers(0, 5)
+        assert O.likelihood(round(mu) + u, round(mu), sg) == O.likelihood(round(mu) - u, round(mu), sg)
+    assert O.likelihood(1000, 0.0, 1.0) == 1e-9            # floor
+    assert O.likelihood(0, 0.0, 1e-3) == O.likelihood(0, 0.0, 0.11)   # clamp
+
+
+def test_rate_bits_sum():
+    y = np.array([0, 1, -2], np.int16)
+    mu = np.array([0.0, 0.3, -1.0]); sg = np.array([1.0, 2.0, 0.5])
+    want = -sum(math.log2(O.likelihood(a, b, s)) for a, b, s in zip(y, mu, sg))
+    assert O.rate_bits(y, mu, sg) == pytest.approx(want, rel=1e-15)
+
+
+def test_scale_table():
+    t = O.scale_table()
+    assert t[0] == np.float32(0.11) and t[-1] == np.float32(256.0)
+    r = np.log(t.astype(np.float64))
+    assert np.allclose(np.diff(r), (math.log(256) - math.log(0.11)) / 63, rtol=1e-6)
+
+
+def test_quantize_rules():
+    t = O.scale_table()
+    sig = np.array([t[5], np.nextafter(t[5], np.float32(1e9)), 0.01, 1e6, t[0], np.float32("nan")], np.float32)
+    idx, _ = O.quantize(np.zeros(6, np.float32), sig)
+    assert idx.tolist() == [5, 6, 0, 63, 0, 63]
+    mu = np.array([0.5, 1.5, -0.5, 2.5, -2.5, 1e9, -1e9, 0.49999997], np.float32)
+    _, m = O.quantize(mu, np.ones(8, np.float32))
+    assert m.tolist() == [0, 2, 0, 2, -2, 32767, -32768, 0]
+
+
+@pytest.mark.parametrize("l", [0, 1, 10, 30, 45, 63])
+def test_cdf_table_invariants(l):
+    t = O.scale_table()
+    T = O.cdf_T(l)
+    assert T == max(1, math.ceil(7 * float(t[l])))
+    f = O.cdf_freq(l).astype(np.int64)
+    assert len(f) == 2 * T + 2
+    assert f.sum() == 1 << 16 and f.min() >= 1
+    # symmetric around zero, peak at zero
+    assert np.array_equal(f[:T], f[T + 1:2 * T + 1][::-1])
+    assert f[T] == f[:2 * T + 1].max()
+    # close to the quantised Gaussian: table cost within the quantisation slack
+    sg = float(t[l])
+    pmf = np.array([O.likelihood(s, 0.0, sg) for s in range(-T, T + 1)])
+    q = f[:2 * T + 1] / 65536.0
+    assert np.all(np.abs(q - pmf) <= (2 * T + 3) / 65536.0 + 1e-12)
+    # every slot gets at least pmf (1 - n / 2^16) of the range, so the coding
+    # loss against the exact pmf is at most -log2(1 - n / 2^16)
+    assert np.all(q >= pmf * (1 - (2 * T + 2) / 65536.0) - 1e-15)
+    kl = float(np.sum(pmf * np.log2(np.maximum(pmf, 1e-300) / q)))
+    assert kl <= -math.log2(1 - (2 * T + 2) / 65536.0)
+
+
+# ----------------------------------------------------------- rANS
+
+def _coder_case(c, rng, scale=1.0):
+    HW = c.H * c.W
+    idx = rng.integers(0, 64, size=(c.H, c.W, c.C)).astype(np.uint8)
+    m = rng.integers(-50, 50, size=(c.H, c.W, c.C)).astype(np.int32)
+    t = O.scale_table()
+    y = np.rint(m + rng.standard_normal((c.H, c.W, c.C)) * t[idx] * scale)
+    return np.clip(y, -32767, 32767).astype(np.int16), idx, m
+
+
+@pytest.mark.parametrize("sched", [0, 1])
+def test_rans_round_trip_random(sched):
+    c = synth.config("tiny")
+    rng = np.random.default_rng(5)
+    y, idx, m = _coder_case(c, rng, scale=1.5)       # 1.5 sigma: some escapes
+    bs = O.rans_encode(c, sched, y, idx, m)
+    ok, yd = O.rans_decode(c, sched, idx, m, bs)
+    assert ok and np.array_equal(yd, y)
+
+
+def test_rans_all_escape_all_zero_single_symbol():
+    c = synth.config("tiny")
+    rng = np.random.default_rng(6)
+    idx = np.zeros((c.H, c.W, c.C), np.uint8)
+    m = np.zeros((c.H, c.W, c.C), np.int32)
+    # every symbol far outside the support (T = 1 at idx 0), both signs, extremes
+    y = rng.choice([-32767, -200, -3, 3, 200, 32767], size=(c.H, c.W, c.C)).astype(np.int16)
+    mm = m.copy(); mm[0, 0, 0] = -32768; mm[0, 0, 1] = 32767
+    for yy, m_ in ((y, m), (y, mm), (np.zeros_like(y), m)):
+        bs = O.rans_encode(c, 0, yy, idx, m_)
+        ok, yd = O.rans_decode(c, 0, idx, m_, bs)
+        assert ok and np.array_equal(yd, yy)
+    one = c.with_grid(1, 1)
+    yy = np.array([[[7] * c.C]], np.int16)
+    bs = O.rans_encode(one, 0, yy, idx[:1, :1], m[:1, :1])
+    ok, yd = O.rans_decode(one, 0, idx[:1, :1], m[:1, :1], bs)
+    assert ok and np.array_equal(yd, yy)
+
+
+def test_rans_size_bound():
+    c = synth.config("tiny").with_grid(16, 24)
+    rng = np.random.default_rng(8)
+    y, idx, m = _coder_case(c, rng)
+    bs = O.rans_encode(c, 0, y, idx, m)
+    bits = 0.0
+    for a in np.ndindex(y.shape):
+        l, T = int(idx[a]), O.cdf_T(int(idx[a]))
+        f = O.cdf_freq(l)
+        s = int(y[a]) - int(m[a])
+        slot = s + T if -T <= s <= T else 2 * T + 1
+        bits += -math.log2(f[slot] / 65536.0) + (32 if slot == 2 * T + 1 else 0)
+    hdr = 16 + 4 * (c.C + 1)
+    # per stream: 32 states, at most one unused word per lane, one pad word
+    slack = c.C * (32 * 32 + 32 * 16 + 16)
+    assert (len(bs) - hdr) * 8 <= bits + slack
+
+
+def test_rans_detects_corruption():
+    c = synth.config("tiny")
+    rng = np.random.default_rng(9)
+    y, idx, m = _coder_case(c, rng)
+    bs = bytearray(O.rans_encode(c, 0, y, idx, m))
+    ok, _ = O.rans_decode(c, 0, idx, m, bytes(bs[:-10]))       # truncated
+    assert not ok
+    bad = bytearray(bs); bad[0] ^= 1                            # magic
+    assert not O.rans_decode(c, 0, idx, m, bytes(bad))[0]
+    bad = bytearray(bs); bad[6] = 1                             # wrong schedule
+    assert not O.rans_decode(c, 0, idx, m, bytes(bad))[0]
+    hdr = 16 + 4 * (c.C + 1)
+    flips = 0
+    for pos in rng.integers(hdr + 128, len(bs), size=20):
+        bad = bytearray(bs); bad[pos] ^= 0x5A
+        ok, yd = O.rans_decode(c, 0, idx, m, bytes(bad))
+        flips += (not ok) or (not np.array_equal(yd, y))
+    assert flips == 20
+
+
+def test_encode_decode_round_trip_through_the_model():
+    for nm, nf in (("tiny", 1), ("tiny_p", 3)):
+        c = synth.config(nm)
+        w = synth.weights(c)
+        fr = synth.frames(c, nf, seed=12)
+        bs, mu, sg = O.encode_frames(c, w, fr.y, fr.z)
+        yd, mud, sgd = O.decode_frames(c, w, bs, fr.z)
+        assert np.array_equal(yd, fr.y)
+        assert np.array_equal(mu, mud) and np.array_equal(sg, sgd)
+
+
+# ----------------------------------------------------------- data generator
+
+def test_generator_statistics():
+    c = synth.config("i1080")
+    rng = np.random.Generator(np.random.PCG64(0))
+    x = synth.ar1_field(rng, 68, 120, 64, 0.8)
+    assert abs(x.var() - 1.0) < 0.05
+    r_h = np.mean(x[:, 1:] * x[:, :-1]); r_v = np.mean(x[1:] * x[:-1])
+    assert abs(r_h - 0.8) < 0.03 and abs(r_v - 0.8) < 0.03
+    assert abs(np.mean(x[1:, 1:] * x[:-1, :-1]) - 0.64) < 0.04
+    fr = synth.frames(c.with_grid(34, 60), 2, seed=1)
+    assert fr.y.dtype == np.int16 and fr.y.shape == (2, 34, 60, 192)
+    ls = np.log(fr.sigma).ravel()
+    assert abs(ls.min() - math.log(0.1)) < 0.05 and abs(ls.max() - math.log(8)) < 0.05
+    hist, _ = np.histogram(ls, bins=4)
+    assert hist.min() > 0.7 * hist.mean()            # log-uniform
+    a, b = fr.y[0].astype(float) / fr.sigma[..., None], fr.y[1].astype(float) / fr.sigma[..., None]
+    big = fr.sigma > 3
+    assert abs(np.corrcoef(a[big].ravel(), b[big].ravel())[0, 1] - 0.9) < 0.05

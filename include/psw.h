@@ -1,0 +1,214 @@
+/*
+ * psw.h -- C ABI of the GB300 (sm_103a) implementation of the P-SWA
+ * entropy model's hot path: diagonal-wavefront decoding of the
+ * sliding-window-attention context model of "Parallel Context Modeling for
+ * Sliding Window Attention in Neural Video Coding" (Kopte & Kaup).
+ *
+ * The library computes, for every latent symbol y(i,j,c) of a frame, the
+ * Gaussian parameters (mu, sigma) the context model assigns to it given the
+ * decoded hyperprior, the previously decoded positions of the frame and (for
+ * the temporal model) previous frames (Sec. 3.1, Fig. 1).  The encoder
+ * evaluates every position in one masked parallel pass; the decoder walks the
+ * step labels l(i,j) = 2i+j (one diagonal wavefront per step, Sec. 2 and
+ * Sec. 3.2) or raster order, predicting all positions of a step together
+ * (Sec. 3.2, Fig. 2).  sigma is quantised to a 64-entry log-spaced scale
+ * table; integer CDFs of the quantised Gaussian drive 32-lane interleaved
+ * rANS, standing in for the "AE/AD" boxes of Fig. 1.
+ *
+ * Conventions for every call:
+ *  - Tensors are channel-last and contiguous: latents y [H][W][C] int16,
+ *    hyperlatents z [ceil(H/r)][ceil(W/r)][Ch] int16, mu/sigma [H][W][C]
+ *    float32.  Pointers named *_dev are CUDA device pointers; *_host are
+ *    host pointers.  The caller owns every pointer it passes; the library
+ *    never frees or keeps them beyond the call.
+ *  - The library owns its weights, CDF tables, per-sequence caches and all
+ *    scratch memory.  Nothing is allocated per call except where stated.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; calls that return a host-side result (a length, a bit
+ *    count, a decode status) synchronise that stream before returning.
+ *  - No exception crosses the ABI.  Every call returns a psw_status; the
+ *    message of the last failure on a context is psw_last_error(ctx).
+ *  - A context may be used by one host thread at a time.
+ */
+#ifndef PSW_H
+#define PSW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psw_ctx psw_ctx;   /* model weights + tables (opaque) */
+typedef struct psw_seq psw_seq;   /* one video sequence's caches (opaque) */
+
+typedef enum {
+    PSW_OK = 0,
+    PSW_ERR_INVALID = 1,   /* bad argument, shape or descriptor            */
+    PSW_ERR_OOM = 2,       /* device allocation failed / budget exceeded   */
+    PSW_ERR_CUDA = 3,      /* a CUDA runtime call failed                   */
+    PSW_ERR_CORRUPT = 4,   /* bitstream fails validation while decoding    */
+    PSW_ERR_TIMEOUT = 5,   /* a bounded device-side wait ran out           */
+    PSW_ERR_CAPACITY = 6   /* output buffer too small                      */
+} psw_status;
+
+typedef enum { PSW_FP32 = 0, PSW_BF16 = 1 } psw_precision;
+
+typedef enum {
+    PSW_SCHED_WAVEFRONT = 0,   /* one step per label value, all positions of the step together */
+    PSW_SCHED_RASTER = 1       /* one position per step, raster order (same model, same masks) */
+} psw_schedule;
+
+/* Model hyper-parameters (Sec. 3.1 block structure; Sec. 4.1 sizes).
+ *   C      latent channels            Ch, r  hyperprior channels, upsampling
+ *   d, nh  model width, heads         F      SwiGLU hidden width
+ *   L      blocks per spatial module (Spatial Module 1 and 2; plus one
+ *          accumulator block)          k      spatial window (k x k, odd)
+ *   temporal  1 = Context Transformer (Lc blocks) and temporal
+ *          cross-attention over Tf frames in every spatial block
+ *   mask   0 = label 2i+j with the raster clause (wavefront and raster
+ *          schedules valid); 1 = cyclic s = 4 label of Fig. 2a. */
+typedef struct {
+    int C, Ch, r;
+    int d, nh, F, L, k;
+    int temporal, Lc, Tf;
+    int mask;
+} psw_model_desc;
+
+/* One frame: latent grid H x W (hyperprior grid ceil(H/r) x ceil(W/r)) and
+ * the decoding schedule (psw_schedule) the bitstream is ordered by. */
+typedef struct {
+    int H, W;
+    int schedule;
+} psw_frame_desc;
+
+/* Number of float32 values in the flat weight vector of a model.
+ * Packing order (every projection stored [in][out], used as x . W):
+ *   gamma_in[C] W_in[C][d] b_in[d] gamma_z[Ch] W_hp[r*r][Ch][d] b_hp[d]
+ *   if temporal: gamma_c[C] W_c[C][d] b_c[d] pad[d]
+ *                Lc x { g_attn[d] Wq Wk Wv Wo [d][d] bias[nh][Tf][k][k]
+ *                       g_ffn[d] Wg[d][F] Wu[d][F] Wd[F][d] }  g_ctx[d]
+ *   L x Spatial Module 1 block:
+ *     { g_attn[d] Wq Wk Wv Wo [d][d] bias[nh][k][k]
+ *       if temporal: g_x[d] Wxq Wxk Wxv Wxo [d][d] xbias[nh][Tf][k][k]
+ *       g_ffn[d] Wg[d][F] Wu[d][F] Wd[F][d] }
+ *   accumulator: g_q[d] g_kv[d] Wq Wk Wv Wo [d][d] bias[nh][k][k]
+ *                g_ffn[d] Wg[d][F] Wu[d][F] Wd[F][d]
+ *   L x Spatial Module 2 block (as Spatial Module 1)
+ *   heads: g_head[d] W1m[d][d] b1m[d] W2m[d][C] W1s[d][d] b1s[d] W2s[d][C]
+ *          gamma_mu[C] beta_mu[C] gamma_sig[C] beta_sig[C]
+ * Returns 0 for an invalid descriptor. */
+size_t psw_weights_count(const psw_model_desc *desc);
+
+/* Create a context: validates the descriptor, uploads the weights (host
+ * float32, psw_weights_count values) to the current CUDA device, converts
+ * block projections to the compute precision (PSW_FP32 or PSW_BF16,
+ * round-to-nearest-even) and builds the scale and CDF tables.
+ * hbm_budget bounds the device memory of this context and its sequences
+ * (0 = no bound); a sequence that would exceed it fails with PSW_ERR_OOM.
+ * On failure *out is NULL. */
+psw_status psw_create(const psw_model_desc *desc, const float *weights_host, size_t n_weights,
+                      int precision, size_t hbm_budget, psw_ctx **out);
+void psw_destroy(psw_ctx *ctx);
+
+/* Message of the last failure on ctx ("" if none).  Valid until the next
+ * call on ctx.  psw_last_error(NULL) reports failures of psw_create. */
+const char *psw_last_error(const psw_ctx *ctx);
+
+/* Device bytes held by the context (weights, tables) and, for a sequence
+ * of the given maximum grid, by one sequence (caches and scratch). */
+size_t psw_ctx_bytes(const psw_ctx *ctx);
+size_t psw_seq_bytes(const psw_ctx *ctx, int max_H, int max_W);
+
+/* A sequence owns the per-frame caches (window K/V of every layer, residual
+ * streams, step scratch) for frames up to max_H x max_W and, for the
+ * temporal model, the rings of the last Tf frames' context K/V (Sec. 3.1:
+ * the Context Transformer and temporal cross-attention see previous
+ * frames).  Frames must be coded in order; psw_encode_params and
+ * psw_decode_frame advance it identically.  psw_seq_reset starts a new
+ * sequence (the next frame is frame 0, whose temporal context is the learned
+ * padding vector). */
+psw_status psw_seq_create(psw_ctx *ctx, int max_H, int max_W, psw_seq **out);
+psw_status psw_seq_reset(psw_seq *seq);
+void psw_seq_destroy(psw_seq *seq);
+
+/* Upper bound on the container size of one frame (bytes). */
+size_t psw_bitstream_capacity(const psw_ctx *ctx, const psw_frame_desc *fd);
+
+/* Encoder (Sec. 3.1: "masked to restrict attention strictly to past
+ * positions"; Sec. 3.2): one masked parallel pass over every position of
+ * the frame gives (mu, sigma); sigma -> scale index, mu -> rounded mean;
+ * symbols y - round(mu) are rANS-coded per channel in the schedule's order.
+ *   yhat_dev  [H][W][C] int16 latents of this frame
+ *   zhat_dev  [ceil(H/r)][ceil(W/r)][Ch] int16 decoded hyperlatents
+ *   mu_dev, sigma_dev  optional [H][W][C] float32 outputs (NULL to skip)
+ *   bitstream_dev  optional device buffer of cap bytes for the container
+ *                  (NULL: parameters only, *len_out set to 0)
+ *   len_out   host: container size in bytes
+ * Errors: PSW_ERR_INVALID (shape), PSW_ERR_CAPACITY (cap too small; the
+ * sequence still advances), PSW_ERR_CUDA.  Synchronises `stream`. */
+psw_status psw_encode_params(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd,
+                             const int16_t *yhat_dev, const int16_t *zhat_dev,
+                             float *mu_dev, float *sigma_dev,
+                             uint8_t *bitstream_dev, size_t cap, size_t *len_out, void *stream);
+
+/* Decoder (Sec. 3.2, Fig. 2): for each step of the schedule, Spatial
+ * Module 1 runs on the positions decoded in the previous step, then the
+ * accumulator, Spatial Module 2 and heads run on all positions of the step
+ * together, their symbols are rANS-decoded and written to yhat.
+ *   bitstream_dev  device container of len bytes (from psw_encode_params)
+ *   zhat_dev       hyperlatents as for the encoder
+ *   yhat_out_dev   [H][W][C] int16 decoded latents
+ *   mu_dev, sigma_dev  optional float32 outputs (NULL to skip)
+ * Returns PSW_ERR_CORRUPT if the container fails validation (header,
+ * offsets, a read past a stream's end, a final state other than the initial
+ * one, a latent outside int16); the outputs are then unspecified but every
+ * device access stayed in bounds.  Synchronises `stream`. */
+psw_status psw_decode_frame(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd,
+                            const uint8_t *bitstream_dev, size_t len, const int16_t *zhat_dev,
+                            int16_t *yhat_out_dev, float *mu_dev, float *sigma_dev, void *stream);
+
+/* Batched decode: n frames of n different sequences (any mix of grids up to
+ * each sequence's maximum) decoded together; step t of every frame runs in
+ * global step t.  Arrays have n entries.  Per-frame results are identical
+ * to psw_decode_frame.  status_out (host, n entries, may be NULL) receives
+ * each frame's status; the call returns the first failure. */
+psw_status psw_decode_batch(psw_ctx *ctx, int n, psw_seq *const *seqs, const psw_frame_desc *fds,
+                            const uint8_t *const *bitstreams_dev, const size_t *lens,
+                            const int16_t *const *zhat_dev, int16_t *const *yhat_out_dev,
+                            int *status_out, void *stream);
+
+/* Model rate of a frame (Fig. 1 rate term): bits = -sum log2 P(y) with
+ * P(y) the Gaussian mass of [y - 1/2, y + 1/2] under (mu, sigma), sigma
+ * clamped to [0.11, 256], P floored at 1e-9; FP64, fixed reduction order.
+ * n symbols; bits_out_host receives the sum.  Synchronises `stream`. */
+psw_status psw_rate(psw_ctx *ctx, size_t n, const int16_t *yhat_dev, const float *mu_dev,
+                    const float *sigma_dev, double *bits_out_host, void *stream);
+
+/* Quantisation step alone: idx = smallest l with scale[l] >= sigma (float
+ * compare; 63 if none), m = round-half-even(clamp(mu, -32768, 32767)).
+ * n values; idx_dev uint8, m_dev int32.  Asynchronous. */
+psw_status psw_quantize(psw_ctx *ctx, size_t n, const float *mu_dev, const float *sigma_dev,
+                        uint8_t *idx_dev, int32_t *m_dev, void *stream);
+
+/* The scale table (64 float32) and CDF table l: freq[n] for slots
+ * -T..T, ESC (n = 2T+2, sum 2^16).  Host outputs. */
+psw_status psw_scale_table(const psw_ctx *ctx, float *table_host);
+psw_status psw_cdf_table(const psw_ctx *ctx, int l, uint32_t *freq_host, int cap, int *n_out, int *T_out);
+
+/* Coder alone, with caller-supplied per-symbol scale index and rounded mean
+ * ([H][W][C] each): encode y into a container, or decode a container into y.
+ * Encoding: *len_out = container size (PSW_ERR_CAPACITY if > cap).
+ * Decoding: PSW_ERR_CORRUPT as for psw_decode_frame.  Synchronise `stream`. */
+psw_status psw_rans_encode(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd,
+                           const int16_t *yhat_dev, const uint8_t *idx_dev, const int32_t *m_dev,
+                           uint8_t *bitstream_dev, size_t cap, size_t *len_out, void *stream);
+psw_status psw_rans_decode(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd,
+                           const uint8_t *bitstream_dev, size_t len, const uint8_t *idx_dev,
+                           const int32_t *m_dev, int16_t *yhat_out_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSW_H */

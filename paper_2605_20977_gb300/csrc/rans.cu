@@ -1,0 +1,395 @@
+// rans.cu -- scale table, integer CDF tables and 32-lane interleaved rANS.
+//
+// The paper draws quantisation and arithmetic coding as "Q", "AE" and "AD"
+// (Fig. 1) and names no coder.  This file realises them:
+//   * scale table: 64 scales log-spaced from 0.11 to 256 (float);
+//   * CDF table per scale: zero-mean quantised Gaussian over -T..T plus an
+//     escape slot, T = max(1, ceil(7 sigma)); pmf from erfc; 16-bit
+//     frequencies, each at least 1, summing to 2^16;
+//   * rANS (32-bit state in [2^16, 2^32), 16-bit renormalisation words,
+//     M = 2^16), one stream per channel, symbol k of a stream on lane
+//     k mod 32; an escape codes v = 2 (|s| - T - 1) + sign as two raw 16-bit
+//     digits on the same lane.
+// Container (little endian): u32 magic 'PSW1', u16 version 1, u16 schedule,
+// u16 H, u16 W, u16 C, u16 0, u32 offsets[C + 1]; each stream is u32 state[32]
+// followed by its words in decoding order, padded to 4 bytes.
+#include "internal.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+namespace psw {
+
+static constexpr uint32_t MAGIC = 0x31575350u;
+static constexpr uint32_t RANS_L = 1u << 16;
+
+// ---------------------------------------------------------------- tables (host)
+
+void build_scale_table(float *tab)
+{
+    const double a = log(0.11), b = log(256.0);
+    for (int l = 0; l < NSCALES; l++) tab[l] = (float)exp(a + l * (b - a) / (NSCALES - 1));
+}
+
+void build_cdf_tables(CdfTables &t)
+{
+    build_scale_table(t.scale);
+    int total = 0;
+    for (int l = 0; l < NSCALES; l++) {
+        int T = (int)ceil(7.0 * (double)t.scale[l]);
+        if (T < 1) T = 1;
+        t.T[l] = T;
+        t.n[l] = 2 * T + 2;
+        t.off[l] = total;
+        total += t.n[l];
+    }
+    t.total = total;
+    t.packed = (uint32_t *)malloc(sizeof(uint32_t) * total);
+    uint32_t *fr = (uint32_t *)malloc(sizeof(uint32_t) * 4096);
+    for (int l = 0; l < NSCALES; l++) {
+        const double sg = (double)t.scale[l], den = sg * 1.4142135623730951;
+        const int T = t.T[l], n = t.n[l];
+        const double room = (double)((1u << CDF_PREC) - (uint32_t)n);
+        long sum = 0;
+        for (int sl = 0; sl <= 2 * T; sl++) {
+            int s = sl - T;
+            double u = (double)(s < 0 ? -s : s);
+            double pmf = 0.5 * (erfc((u - 0.5) / den) - erfc((u + 0.5) / den));
+            fr[sl] = 1u + (uint32_t)floor(pmf * room);
+            sum += fr[sl];
+        }
+        double tail = erfc(((double)T + 0.5) / den);
+        fr[2 * T + 1] = 1u + (uint32_t)floor(tail * room);
+        sum += fr[2 * T + 1];
+        fr[T] = (uint32_t)((long)fr[T] + ((long)(1u << CDF_PREC) - sum));
+        uint32_t cum = 0;
+        for (int sl = 0; sl < n; sl++) {
+            t.packed[t.off[l] + sl] = cum | (fr[sl] << 16);
+            cum += fr[sl];
+        }
+    }
+    free(fr);
+}
+
+void free_cdf_tables(CdfTables &t)
+{
+    free(t.packed);
+    t.packed = nullptr;
+}
+
+size_t container_capacity(int H, int W, int C)
+{
+    size_t HW = (size_t)H * W;
+    return 16 + 4 * (size_t)(C + 1) + (size_t)C * (128 + 6 * HW + 4);
+}
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ uint32_t lane_exclusive_scan(uint32_t v, uint32_t &total)
+{
+    int lane = threadIdx.x & 31;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - v;
+}
+
+__device__ __forceinline__ uint32_t ld8(const uint8_t *b, size_t o) { return b[o]; }
+__device__ __forceinline__ uint32_t ld16le(const uint8_t *b, size_t o) { return ld8(b, o) | (ld8(b, o + 1) << 8); }
+__device__ __forceinline__ uint32_t ld32le(const uint8_t *b, size_t o) { return ld16le(b, o) | (ld16le(b, o + 2) << 16); }
+
+// ---------------------------------------------------------------- encoder
+
+// One warp per channel stream.  Groups of 32 symbols are encoded from the
+// last to the first; in a group lane j holds symbol 32 g + j.  Each lane
+// produces its renormalisation words in decoding order ([main], [d0, d1]);
+// a warp scan places the group's words, in lane order, just before the
+// words already written (the scratch region is filled from its end).
+__global__ void k_rans_encode(CoderDev cd, const int *__restrict__ order, int HW, int C,
+                              const int16_t *__restrict__ y, const uint8_t *__restrict__ idx,
+                              const int32_t *__restrict__ m, uint16_t *__restrict__ scratch, int cap_words,
+                              uint32_t *__restrict__ nwords, uint32_t *__restrict__ states)
+{
+    int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (c >= C) return;
+    uint16_t *buf = scratch + (size_t)c * cap_words;
+    uint32_t x = RANS_L;
+    int wpos = cap_words;
+    int ngroups = (HW + 31) / 32;
+    for (int g = ngroups - 1; g >= 0; g--) {
+        int k = g * 32 + lane;
+        uint32_t cnt = 0, w[3] = {0, 0, 0};
+        if (k < HW) {
+            long a = (long)order[k] * C + c;
+            int l = idx[a], T = cd.meta[l], off = cd.meta[2 * NSCALES + l];
+            long s = (long)y[a] - (long)m[a];
+            int slot;
+            bool esc = false;
+            uint32_t e0 = 0, e1 = 0;
+            if (s >= -T && s <= T) {
+                slot = (int)(s + T);
+            } else {
+                slot = 2 * T + 1;
+                esc = true;
+                long mag = s < 0 ? -s : s;
+                uint32_t v = (uint32_t)(2 * (mag - T - 1) + (s < 0 ? 1 : 0));
+                uint32_t d0 = v & 0xFFFFu, d1 = v >> 16;
+                e1 = x & 0xFFFFu; x = (x & 0xFFFF0000u) | d1;     // d1 encoded first
+                e0 = x & 0xFFFFu; x = (x & 0xFFFF0000u) | d0;
+            }
+            uint32_t ent = cd.cdf[off + slot];
+            uint32_t cm = ent & 0xFFFFu, f = ent >> 16;
+            bool ren = x >= (f << 16);
+            uint32_t em = x & 0xFFFFu;
+            if (ren) x >>= 16;
+            x = ((x / f) << 16) + (x % f) + cm;
+            if (ren) w[cnt++] = em;
+            if (esc) { w[cnt++] = e0; w[cnt++] = e1; }
+        }
+        uint32_t total;
+        uint32_t pre = lane_exclusive_scan(cnt, total);
+        int base = wpos - (int)total;
+        for (uint32_t j = 0; j < cnt; j++) buf[base + pre + j] = (uint16_t)w[j];
+        wpos = base;
+    }
+    states[(size_t)c * 32 + lane] = x;
+    if (lane == 0) nwords[c] = (uint32_t)(cap_words - wpos);
+}
+
+void launch_rans_encode(const CoderDev &cd, const int *order, int HW, int C, const int16_t *y,
+                        const uint8_t *idx, const int32_t *m, uint16_t *scratch, int cap_words,
+                        uint32_t *nwords, uint32_t *states, cudaStream_t s)
+{
+    int blocks = (C * 32 + 127) / 128;
+    k_rans_encode<<<blocks, 128, 0, s>>>(cd, order, HW, C, y, idx, m, scratch, cap_words, nwords, states);
+}
+
+// Offsets by a single-block scan over the streams, then the header; the
+// total goes to *total.  If it exceeds cap nothing is written and the
+// capacity bit is set.
+__global__ void k_rans_offsets(int H, int W, int C, int sched, const uint32_t *__restrict__ nwords,
+                               uint8_t *__restrict__ out, size_t cap, uint32_t *__restrict__ offs,
+                               uint64_t *__restrict__ total, int *__restrict__ status)
+{
+    __shared__ uint64_t part[1024];
+    int per = (C + blockDim.x - 1) / blockDim.x;
+    uint64_t acc = 0;
+    for (int u = 0; u < per; u++) {
+        int c = threadIdx.x * per + u;
+        if (c < C) { uint32_t nw = nwords[c]; acc += 128 + 2ull * nw + ((nw & 1) ? 2 : 0); }
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t run = 16 + 4ull * (C + 1);
+        for (int t = 0; t < (int)blockDim.x; t++) { uint64_t v = part[t]; part[t] = run; run += v; }
+        *total = run;
+        if (run > cap || run > 0xFFFFFFFFull) atomicOr(status, ST_CAPACITY);
+    }
+    __syncthreads();
+    uint64_t run = part[threadIdx.x];
+    for (int u = 0; u < per; u++) {
+        int c = threadIdx.x * per + u;
+        if (c < C) {
+            offs[c] = (uint32_t)run;
+            uint32_t nw = nwords[c];
+            run += 128 + 2ull * nw + ((nw & 1) ? 2 : 0);
+        }
+    }
+    if (threadIdx.x == 0) offs[C] = (uint32_t)*total;
+}
+
+__global__ void k_rans_write(int H, int W, int C, int sched, const uint16_t *__restrict__ scratch,
+                             int cap_words, const uint32_t *__restrict__ nwords,
+                             const uint32_t *__restrict__ states, const uint32_t *__restrict__ offs,
+                             const uint64_t *__restrict__ total, size_t cap, uint8_t *__restrict__ out)
+{
+    if (*total > cap) return;
+    int c = blockIdx.x;
+    if (c == 0) {
+        for (int t = threadIdx.x; t < 16 + 4 * (C + 1); t += blockDim.x) {
+            uint32_t v;
+            if (t < 16) {
+                uint32_t h[4] = {MAGIC, 1u | ((uint32_t)sched << 16), (uint32_t)H | ((uint32_t)W << 16),
+                                 (uint32_t)C};
+                v = h[t >> 2];
+            } else {
+                v = offs[(t - 16) >> 2];
+            }
+            out[t] = (uint8_t)(v >> (8 * (t & 3)));
+        }
+    }
+    uint8_t *o = out + offs[c];
+    for (int t = threadIdx.x; t < 128; t += blockDim.x)
+        o[t] = (uint8_t)(states[(size_t)c * 32 + (t >> 2)] >> (8 * (t & 3)));
+    uint32_t nw = nwords[c];
+    const uint16_t *src = scratch + (size_t)c * cap_words + (cap_words - nw);
+    uint16_t *dst = (uint16_t *)(o + 128);
+    for (uint32_t t = threadIdx.x; t < nw; t += blockDim.x) dst[t] = src[t];
+    if ((nw & 1) && threadIdx.x == 0) dst[nw] = 0;
+}
+
+void launch_rans_assemble(int H, int W, int C, int sched, const uint16_t *scratch, int cap_words,
+                          const uint32_t *nwords, const uint32_t *states, uint8_t *out, size_t cap,
+                          uint64_t *total, int *status, cudaStream_t s)
+{
+    // offsets live just after the stream lengths in the same scratch word
+    uint32_t *offs = (uint32_t *)(nwords + C);
+    k_rans_offsets<<<1, 1024, 0, s>>>(H, W, C, sched, nwords, out, cap, offs, total, status);
+    k_rans_write<<<C, 256, 0, s>>>(H, W, C, sched, scratch, cap_words, nwords, states, offs, total, cap, out);
+}
+
+// ---------------------------------------------------------------- decoder
+
+// Validate the container and load every stream's 32 states.  An invalid
+// container sets the corrupt bit and leaves every stream empty
+// (ptr = end), so later word reads are refused without touching memory.
+__global__ void k_rans_dec_init(const uint8_t *__restrict__ bs, size_t len, int H, int W, int C, int sched,
+                                uint32_t *__restrict__ states, uint32_t *__restrict__ ptr,
+                                uint32_t *__restrict__ end, int *__restrict__ status)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    size_t hdr = 16 + 4 * (size_t)(C + 1);
+    bool ok = len >= hdr;
+    if (ok) {
+        ok = ld32le(bs, 0) == MAGIC && ld16le(bs, 4) == 1 && (int)ld16le(bs, 6) == sched &&
+             (int)ld16le(bs, 8) == H && (int)ld16le(bs, 10) == W && (int)ld16le(bs, 12) == C;
+    }
+    uint32_t a = 0, b = 0;
+    if (ok) {
+        a = ld32le(bs, 16 + 4 * (size_t)c);
+        b = ld32le(bs, 16 + 4 * (size_t)(c + 1));
+        ok = a >= hdr && (a & 3) == 0 && (b & 3) == 0 && b >= a + 128 && b <= len;
+    }
+    if (!ok) {
+        atomicOr(status, ST_CORRUPT);
+        for (int l = 0; l < 32; l++) states[(size_t)c * 32 + l] = RANS_L;
+        ptr[c] = 0; end[c] = 0;
+        return;
+    }
+    for (int l = 0; l < 32; l++) states[(size_t)c * 32 + l] = ld32le(bs, a + 4 * l);
+    ptr[c] = a + 128;
+    end[c] = b;
+}
+
+void launch_rans_dec_init(const uint8_t *bs, size_t len, int H, int W, int C, int sched, uint32_t *states,
+                          uint32_t *ptr, uint32_t *end, int *status, cudaStream_t s)
+{
+    k_rans_dec_init<<<(C + 127) / 128, 128, 0, s>>>(bs, len, H, W, C, sched, states, ptr, end, status);
+}
+
+// Decode symbols k0 .. k0 + n - 1 of every channel (one schedule step).
+// One warp per channel; a group of 32 consecutive symbols decodes in
+// parallel on its lanes, which then read their words in lane order.
+__global__ void k_rans_dec_step(CoderDev cd, const int *__restrict__ order, int k0, int n, int C,
+                                const uint8_t *__restrict__ idx, const int32_t *__restrict__ m,
+                                const uint8_t *__restrict__ bs, uint32_t *__restrict__ states,
+                                uint32_t *__restrict__ ptr, const uint32_t *__restrict__ end,
+                                int16_t *__restrict__ y, int *__restrict__ status)
+{
+    int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (c >= C) return;
+    uint32_t x = states[(size_t)c * 32 + lane];
+    uint32_t p = ptr[c];
+    const uint32_t e = end[c];
+    bool bad = false;
+    for (int g = k0 / 32; g * 32 < k0 + n; g++) {
+        int k = g * 32 + lane;
+        bool act = k >= k0 && k < k0 + n;
+        uint32_t need = 0;
+        long pos = 0;
+        int T = 0, slot = 0;
+        int32_t mm = 0;
+        if (act) {
+            pos = order[k];
+            long a = pos * C + c;
+            int l = idx[a];
+            mm = m[a];
+            T = cd.meta[l];
+            int nsl = cd.meta[NSCALES + l], off = cd.meta[2 * NSCALES + l];
+            uint32_t v = x & 0xFFFFu;
+            int lo = 0, hi = nsl - 1;                  // last slot with cum <= v
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if ((cd.cdf[off + mid] & 0xFFFFu) <= v) lo = mid; else hi = mid - 1;
+            }
+            slot = lo;
+            uint32_t ent = cd.cdf[off + slot];
+            x = (ent >> 16) * (x >> 16) + v - (ent & 0xFFFFu);
+            need = (x < RANS_L ? 1u : 0u) + (slot == 2 * T + 1 ? 2u : 0u);
+        }
+        uint32_t total;
+        uint32_t pre = lane_exclusive_scan(need, total);
+        uint32_t q = p + 2 * pre;
+        auto word = [&](void) -> uint32_t {
+            if (q + 2 > e) { bad = true; return 0u; }
+            uint32_t wv = ld16le(bs, q);
+            q += 2;
+            return wv;
+        };
+        if (act) {
+            if (x < RANS_L) x = (x << 16) | word();
+            long sv;
+            if (slot == 2 * T + 1) {
+                uint32_t d0 = x & 0xFFFFu;
+                x = (x & 0xFFFF0000u) | word();
+                uint32_t d1 = x & 0xFFFFu;
+                x = (x & 0xFFFF0000u) | word();
+                uint32_t v = d0 | (d1 << 16);
+                long mag = (long)T + 1 + (long)(v >> 1);
+                sv = (v & 1) ? -mag : mag;
+            } else {
+                sv = slot - T;
+            }
+            long yv = (long)mm + sv;
+            if (yv < -32768 || yv > 32767) { bad = true; yv = 0; }
+            y[pos * C + c] = (int16_t)yv;
+        }
+        p += 2 * total;
+        if (p > e) p = e;
+    }
+    states[(size_t)c * 32 + lane] = x;
+    if (lane == 0) ptr[c] = p;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_CORRUPT);
+}
+
+void launch_rans_dec_step(const CoderDev &cd, const int *order, int k0, int n, int C, const uint8_t *idx,
+                          const int32_t *m, const uint8_t *bs, uint32_t *states, uint32_t *ptr,
+                          const uint32_t *end, int16_t *y, int *status, cudaStream_t s)
+{
+    if (n <= 0) return;
+    int blocks = (C * 32 + 127) / 128;
+    k_rans_dec_step<<<blocks, 128, 0, s>>>(cd, order, k0, n, C, idx, m, bs, states, ptr, end, y, status);
+}
+
+// After the last step every lane must be back at the initial state and
+// every stream fully consumed (one zero pad word allowed).
+__global__ void k_rans_dec_finish(const uint8_t *__restrict__ bs, int C, const uint32_t *__restrict__ states,
+                                  const uint32_t *__restrict__ ptr, const uint32_t *__restrict__ end,
+                                  int *__restrict__ status)
+{
+    int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (c >= C) return;
+    bool bad = states[(size_t)c * 32 + lane] != RANS_L;
+    if (lane == 0) {
+        uint32_t p = ptr[c], e = end[c];
+        if (e == 0) bad = true;
+        else if (!(p == e || (p + 2 == e && ld16le(bs, p) == 0))) bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_CORRUPT);
+}
+
+void launch_rans_dec_finish(const uint8_t *bs, int C, const uint32_t *states, const uint32_t *ptr,
+                            const uint32_t *end, int *status, cudaStream_t s)
+{
+    int blocks = (C * 32 + 127) / 128;
+    k_rans_dec_finish<<<blocks, 128, 0, s>>>(bs, C, states, ptr, end, status);
+}
+
+}  // namespace psw

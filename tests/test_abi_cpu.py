@@ -1,0 +1,59 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point include/psw.h declares; host-only entry points agree with the weight
+layout of the synthetic-input module and the oracle."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+from paper_2605_20977_gb300 import psw, synth
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "psw.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(psw_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_20977_gb300 import build
+    build.build()
+    return psw.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(psw.EXPORTS) == names
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiny_p", "tiny_cyc", "i1080", "p1080"])
+def test_weights_count_matches_layouts(lib, name):
+    c = synth.config(name)
+    assert psw.psw_weights_count(c) == synth.weights_count(c) == O.weights_count(c)
+
+
+def test_invalid_descriptors_rejected(lib):
+    c = synth.config("tiny").as_dict()
+    for bad in (dict(d=100), dict(nh=3), dict(k=4), dict(C=0), dict(mask=2), dict(F=0),
+                dict(temporal=1, Lc=0), dict(temporal=1, Lc=1, Tf=5)):
+        d = dict(c); d.update(bad)
+        assert psw.psw_weights_count(d) == 0, bad
+
+
+def test_create_errors_without_crashing(lib):
+    # argument checks happen before any device call
+    out = ct.c_void_p()
+    md = psw.model_desc(synth.config("tiny"))
+    st = lib.psw_create(ct.byref(md), None, 0, psw.PSW_FP32, 0, ct.byref(out))
+    assert st == psw.PSW_ERR_INVALID and not out.value
+    assert b"weights" in lib.psw_last_error(None)
+    st = lib.psw_create(ct.byref(md), None, 0, 7, 0, ct.byref(out))
+    assert st == psw.PSW_ERR_INVALID

@@ -1,0 +1,290 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Integer stages (scale index, rounded mean, CDF tables, rANS containers) are
+bit-exact given the same FP32 (mu, sigma); model parameters are within the
+stated tolerance of the oracle; decoding is lossless and reproduces the
+encoder's parameters bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import dev, need_gpu, oracle_weights, param_errors, torch
+from paper_2605_20977_gb300 import psw, synth
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-4          # max |dmu|/sigma and |d ln sigma|, FP32 compute
+BF16_TOL = 5e-2          # 99.9th percentile of the same, BF16 compute
+RATE_TOL = 1e-3          # |rate(gpu params) - rate(fp64 params)| / rate(fp64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    need_gpu()
+    from paper_2605_20977_gb300 import build
+    build.build()
+    O.build()
+    torch.cuda.set_device(0)
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+def _ctx(cfg, precision, seed=42):
+    w = synth.weights(cfg, seed)
+    return psw.Context(cfg, w, precision=precision), w
+
+
+def _encode_decode(ctx, cfg, fr, sched, nf=None):
+    """Encode then decode nf frames with fresh sequences; returns per-frame
+    dicts of numpy results."""
+    nf = nf or fr.y.shape[0]
+    H, W = fr.y.shape[1], fr.y.shape[2]
+    enc, decs = ctx.seq_create(H, W), ctx.seq_create(H, W)
+    fd = psw.frame_desc(H, W, sched)
+    out = []
+    for f in range(nf):
+        y, z = _t(fr.y[f]), _t(fr.z[f])
+        mu = torch.zeros(y.shape, dtype=torch.float32, device=dev()); sg = torch.zeros_like(mu)
+        bs = torch.zeros(ctx.bitstream_capacity(H, W), dtype=torch.uint8, device=dev())
+        n = enc.encode_params(fd, y, z, mu, sg, bs)
+        y2 = torch.full_like(y, 12345)
+        mu2 = torch.zeros_like(mu); sg2 = torch.zeros_like(mu)
+        decs.decode_frame(fd, bs, n, z, y2, mu2, sg2)
+        torch.cuda.synchronize()
+        out.append(dict(mu=mu.cpu().numpy(), sg=sg.cpu().numpy(), bs=bs[:n].cpu().numpy().tobytes(),
+                        y=y2.cpu().numpy(), mu2=mu2.cpu().numpy(), sg2=sg2.cpu().numpy()))
+    enc.close(); decs.close()
+    return out
+
+
+# ----------------------------------------------------------- integer stages
+
+def test_scale_and_cdf_tables_byte_identical():
+    ctx, _ = _ctx(synth.config("tiny"), psw.PSW_FP32)
+    assert ctx.scale_table().tobytes() == O.scale_table().tobytes()
+    for l in range(64):
+        f, T = ctx.cdf_table(l)
+        assert T == O.cdf_T(l)
+        assert np.array_equal(f, O.cdf_freq(l)), l
+
+
+def test_quantize_bit_exact():
+    ctx, _ = _ctx(synth.config("tiny"), psw.PSW_FP32)
+    rng = np.random.default_rng(0)
+    tab = O.scale_table()
+    sig = np.concatenate([np.exp(rng.uniform(np.log(0.05), np.log(400), 200000)).astype(np.float32),
+                          tab, np.nextafter(tab, np.float32(0)), np.nextafter(tab, np.float32(1e9)),
+                          np.array([0, 1e-30, 1e30, np.inf, np.nan], np.float32)])
+    mu = np.concatenate([rng.normal(0, 30, sig.size - 8).astype(np.float32),
+                         np.array([0.5, -0.5, 1.5, 2.5, -2.5, 1e9, -1e9, np.nan], np.float32)])
+    idx = torch.zeros(sig.size, dtype=torch.uint8, device=dev())
+    m = torch.zeros(sig.size, dtype=torch.int32, device=dev())
+    ctx.quantize(_t(mu), _t(sig), idx, m)
+    i_o, m_o = O.quantize(mu, sig)
+    assert np.array_equal(idx.cpu().numpy(), i_o)
+    assert np.array_equal(m.cpu().numpy(), m_o)
+
+
+def test_rate_matches_oracle():
+    ctx, _ = _ctx(synth.config("tiny"), psw.PSW_FP32)
+    rng = np.random.default_rng(1)
+    n = 300001
+    y = rng.integers(-60, 60, n).astype(np.int16)
+    mu = rng.normal(0, 10, n).astype(np.float32)
+    sg = np.exp(rng.uniform(np.log(0.05), np.log(300), n)).astype(np.float32)
+    bits = ctx.rate(_t(y), _t(mu), _t(sg))
+    want = O.rate_bits(y, mu.astype(np.float64), sg.astype(np.float64))
+    assert abs(bits - want) <= 1e-9 * want
+
+
+def _coder_case(c, rng, esc_scale=1.5):
+    idx = rng.integers(0, 64, size=(c.H, c.W, c.C)).astype(np.uint8)
+    m = rng.integers(-100, 100, size=(c.H, c.W, c.C)).astype(np.int32)
+    t = O.scale_table()
+    y = np.rint(m + rng.standard_normal((c.H, c.W, c.C)) * t[idx] * esc_scale)
+    return np.clip(y, -32767, 32767).astype(np.int16), idx, m
+
+
+@pytest.mark.parametrize("sched", [psw.PSW_SCHED_WAVEFRONT, psw.PSW_SCHED_RASTER])
+@pytest.mark.parametrize("grid", [(9, 13), (1, 1), (1, 40), (37, 3)])
+def test_rans_containers_bit_exact(sched, grid):
+    base = synth.config("tiny")
+    c = base.with_grid(*grid)
+    ctx, _ = _ctx(base, psw.PSW_FP32)
+    seq = ctx.seq_create(*grid)
+    rng = np.random.default_rng(grid[0] * 100 + grid[1] + sched)
+    y, idx, m = _coder_case(c, rng)
+    # extremes: all-escape channel and int16 limits
+    y[..., 0] = rng.choice([-32767, 32767], size=y.shape[:2]); idx[..., 0] = 0; m[..., 0] = 0
+    m[0, 0, 1] = -32768; y[0, 0, 1] = 32767
+    fd = psw.frame_desc(*grid, sched)
+    bs = torch.zeros(ctx.bitstream_capacity(*grid), dtype=torch.uint8, device=dev())
+    n = seq.rans_encode(fd, _t(y), _t(idx), _t(m), bs)
+    gpu_bytes = bs[:n].cpu().numpy().tobytes()
+    assert gpu_bytes == O.rans_encode(c, sched, y, idx, m)
+    yo = torch.zeros(y.shape, dtype=torch.int16, device=dev())
+    seq.rans_decode(fd, bs, n, _t(idx), _t(m), yo)
+    assert np.array_equal(yo.cpu().numpy(), y)
+
+
+def test_rans_corruption_reported_not_faulted():
+    base = synth.config("tiny")
+    ctx, _ = _ctx(base, psw.PSW_FP32)
+    seq = ctx.seq_create(base.H, base.W)
+    rng = np.random.default_rng(3)
+    y, idx, m = _coder_case(base, rng)
+    fd = psw.frame_desc(base.H, base.W, 0)
+    bs = torch.zeros(ctx.bitstream_capacity(base.H, base.W), dtype=torch.uint8, device=dev())
+    n = seq.rans_encode(fd, _t(y), _t(idx), _t(m), bs)
+    yo = torch.zeros(y.shape, dtype=torch.int16, device=dev())
+    ti, tm = _t(idx), _t(m)
+    assert seq.rans_decode(fd, bs, n - 8, ti, tm, yo, check=False) == psw.PSW_ERR_CORRUPT
+    assert seq.rans_decode(fd, bs, 10, ti, tm, yo, check=False) == psw.PSW_ERR_CORRUPT
+    good = bs.clone()
+    for off in (0, 6, 16, 20, 16 + 4 * (base.C + 1) + 200, n - 3):
+        bad = good.clone(); bad[off] ^= 0x55
+        st = seq.rans_decode(fd, bad, n, ti, tm, yo, check=False)
+        assert st == psw.PSW_ERR_CORRUPT or not torch.equal(yo.cpu(), torch.from_numpy(y)), off
+    # offsets pointing past the end and misaligned
+    bad = good.clone(); bad[16:20] = torch.tensor([255, 255, 255, 0], dtype=torch.uint8)
+    assert seq.rans_decode(fd, bad, n, ti, tm, yo, check=False) == psw.PSW_ERR_CORRUPT
+    bad = good.clone(); bad[16] += 1
+    assert seq.rans_decode(fd, bad, n, ti, tm, yo, check=False) == psw.PSW_ERR_CORRUPT
+    # the context stays usable
+    seq.rans_decode(fd, bs, n, ti, tm, yo)
+    assert np.array_equal(yo.cpu().numpy(), y)
+
+
+# ----------------------------------------------------------- model parity
+
+def _check_frame(cfg, w64, fr, res, precision, sched, oracle_mu=None, oracle_sg=None):
+    if oracle_mu is None:
+        oracle_mu, oracle_sg = O.run(cfg, w64, fr.y, fr.z, driver=0)
+    for f, r in enumerate(res):
+        # lossless round trip and decoder == encoder, bit for bit
+        assert np.array_equal(r["y"], fr.y[f])
+        assert np.array_equal(r["mu"], r["mu2"]) and np.array_equal(r["sg"], r["sg2"])
+        dmu, dls = param_errors(r["mu"], r["sg"], oracle_mu[f], oracle_sg[f])
+        if precision == psw.PSW_FP32:
+            assert dmu.max() <= FP32_TOL and dls.max() <= FP32_TOL, (dmu.max(), dls.max())
+        else:
+            assert np.quantile(dmu, 0.999) <= BF16_TOL and np.quantile(dls, 0.999) <= BF16_TOL, \
+                (np.quantile(dmu, 0.999), np.quantile(dls, 0.999))
+        ra = O.rate_bits(fr.y[f], r["mu"].astype(np.float64), r["sg"].astype(np.float64))
+        rb = O.rate_bits(fr.y[f], oracle_mu[f], oracle_sg[f])
+        assert abs(ra - rb) <= RATE_TOL * rb
+        # the container is the oracle coder's, given the GPU's parameters
+        idx, m = O.quantize(r["mu"], r["sg"])
+        assert r["bs"] == O.rans_encode(cfg.with_grid(fr.y.shape[1], fr.y.shape[2]), sched, fr.y[f], idx, m)
+
+
+@pytest.mark.parametrize("sched", [psw.PSW_SCHED_WAVEFRONT, psw.PSW_SCHED_RASTER])
+def test_tiny_fp32_parity(sched):
+    cfg = synth.config("tiny")
+    ctx, w = _ctx(cfg, psw.PSW_FP32)
+    fr = synth.frames(cfg, 1, seed=1001)
+    res = _encode_decode(ctx, cfg, fr, sched)
+    _check_frame(cfg, oracle_weights(cfg, w, psw.PSW_FP32), fr, res, psw.PSW_FP32, sched)
+
+
+def test_cyclic_mask_fp32_parity():
+    cfg = synth.config("tiny_cyc")
+    ctx, w = _ctx(cfg, psw.PSW_FP32)
+    fr = synth.frames(cfg, 1, seed=1005)
+    res = _encode_decode(ctx, cfg, fr, psw.PSW_SCHED_WAVEFRONT)
+    _check_frame(cfg, oracle_weights(cfg, w, psw.PSW_FP32), fr, res, psw.PSW_FP32, 0)
+
+
+def test_temporal_sequence_fp32_parity():
+    cfg = synth.config("tiny_p")
+    ctx, w = _ctx(cfg, psw.PSW_FP32)
+    fr = synth.frames(cfg, 5, seed=1003)       # 5 frames: the Tf = 3 ring wraps
+    res = _encode_decode(ctx, cfg, fr, psw.PSW_SCHED_WAVEFRONT)
+    _check_frame(cfg, oracle_weights(cfg, w, psw.PSW_FP32), fr, res, psw.PSW_FP32, 0)
+
+
+@pytest.mark.parametrize("grid", [(1, 1), (1, 7), (7, 1), (5, 3), (3, 17)])
+def test_edge_grids_fp32(grid):
+    cfg = synth.config("tiny").with_grid(*grid)
+    ctx, w = _ctx(cfg, psw.PSW_FP32)
+    fr = synth.frames(cfg, 1, seed=7)
+    res = _encode_decode(ctx, cfg, fr, psw.PSW_SCHED_WAVEFRONT)
+    _check_frame(cfg, oracle_weights(cfg, w, psw.PSW_FP32), fr, res, psw.PSW_FP32, 0)
+
+
+# ----------------------------------------------------------- 1080p, BF16
+
+CROP = 12
+
+
+@pytest.fixture(scope="module")
+def i1080():
+    cfg = synth.config("i1080")
+    w = synth.weights(cfg)
+    fr = synth.frames(cfg, 1, seed=1002)
+    crop = cfg.with_grid(CROP, cfg.W)
+    frc = synth.Frames(y=fr.y[:, :CROP].copy(), z=fr.z[:, :crop.Hh].copy(), sigma=fr.sigma[:CROP])
+    w64 = oracle_weights(cfg, w, psw.PSW_BF16)
+    mu_o, sg_o = O.run(crop, w64, frc.y, frc.z, driver=0)
+    return dict(cfg=cfg, w=w, fr=fr, crop=crop, frc=frc, w64=w64, mu_o=mu_o, sg_o=sg_o)
+
+
+def test_bf16_1080p_crop_parity(i1080):
+    d = i1080
+    ctx = psw.Context(d["cfg"], d["w"], precision=psw.PSW_BF16)
+    for sched in (psw.PSW_SCHED_WAVEFRONT, psw.PSW_SCHED_RASTER):
+        res = _encode_decode(ctx, d["crop"], d["frc"], sched)
+        _check_frame(d["crop"], d["w64"], d["frc"], res, psw.PSW_BF16, sched, d["mu_o"], d["sg_o"])
+
+
+def test_bf16_1080p_full_frame(i1080):
+    """Full 68x120x192 frame as timed by the benchmark: lossless round trip,
+    decoder == encoder bit for bit, and the top rows (whose parameters
+    depend only on rows above them) against the oracle's crop."""
+    d = i1080
+    ctx = psw.Context(d["cfg"], d["w"], precision=psw.PSW_BF16)
+    r = _encode_decode(ctx, d["cfg"], d["fr"], psw.PSW_SCHED_WAVEFRONT)[0]
+    assert np.array_equal(r["y"], d["fr"].y[0])
+    assert np.array_equal(r["mu"], r["mu2"]) and np.array_equal(r["sg"], r["sg2"])
+    dmu, dls = param_errors(r["mu"][:CROP], r["sg"][:CROP], d["mu_o"][0], d["sg_o"][0])
+    assert np.quantile(dmu, 0.999) <= BF16_TOL and np.quantile(dls, 0.999) <= BF16_TOL
+    # the crop's parameters do not depend on the rows below it
+    res_c = _encode_decode(ctx, d["crop"], d["frc"], psw.PSW_SCHED_WAVEFRONT)[0]
+    assert np.array_equal(res_c["mu"], r["mu"][:CROP]) and np.array_equal(res_c["sg"], r["sg"][:CROP])
+    idx, m = O.quantize(r["mu"], r["sg"])
+    assert r["bs"] == O.rans_encode(d["cfg"], 0, d["fr"].y[0], idx, m)
+
+
+# ----------------------------------------------------------- argument checks
+
+def test_invalid_arguments_and_budget():
+    cfg = synth.config("tiny")
+    w = synth.weights(cfg)
+    ctx = psw.Context(cfg, w, precision=psw.PSW_FP32)
+    seq = ctx.seq_create(cfg.H, cfg.W)
+    y = torch.zeros((cfg.H, cfg.W, cfg.C), dtype=torch.int16, device=dev())
+    z = torch.zeros((cfg.Hh, cfg.Wh, cfg.Ch), dtype=torch.int16, device=dev())
+    with pytest.raises(psw.PswError) as e:
+        seq.encode_params(psw.frame_desc(cfg.H + 1, cfg.W, 0), y, z)
+    assert e.value.status == psw.PSW_ERR_INVALID
+    bs = torch.zeros(4096, dtype=torch.uint8, device=dev())
+    assert seq.decode_frame(psw.frame_desc(cfg.H, cfg.W, 0), bs[1:], 100, z, y, check=False) == psw.PSW_ERR_INVALID
+    with pytest.raises(psw.PswError) as e:
+        seq.encode_params(psw.frame_desc(cfg.H, cfg.W, 0), y, z, bitstream=bs[:64])
+    assert e.value.status == psw.PSW_ERR_CAPACITY
+    cyc = psw.Context(synth.config("tiny_cyc"), synth.weights(synth.config("tiny_cyc")), precision=psw.PSW_FP32)
+    sq = cyc.seq_create(cfg.H, cfg.W)
+    with pytest.raises(psw.PswError) as e:
+        sq.encode_params(psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_RASTER), y, z)
+    assert e.value.status == psw.PSW_ERR_INVALID
+    with pytest.raises(psw.PswError) as e:
+        psw.Context(cfg, w, precision=psw.PSW_FP32, hbm_budget=1 << 20)
+    assert e.value.status == psw.PSW_ERR_OOM
+    small = psw.Context(cfg, w, precision=psw.PSW_FP32, hbm_budget=ctx.ctx_bytes() + ctx.seq_bytes(8, 12) + 1)
+    small.seq_create(8, 12)
+    with pytest.raises(psw.PswError) as e:
+        small.seq_create(8, 12)
+    assert e.value.status == psw.PSW_ERR_OOM

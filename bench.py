@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""Benchmark: wavefront decode of 1080p latent frames on one GB300.
+
+Workload: the 1080p I-frame configuration -- latents 68x120x192 (a
+1088x1920 frame after the /16 feature transform), hyperlatents 17x30x128,
+context model d=384, 6 heads, 7x7 windows, 8 blocks in each spatial module
+plus the accumulator, BF16 projections with FP32 accumulation.  A step
+decodes one batch of frames (default 1) from their rANS containers along the
+254 wavefronts 2i+j = t: every position of a wavefront is predicted
+together, its symbols decoded, and the next wavefront follows.  Inputs are
+synthetic (seeded AR(1) latents, random weights); the containers are made by
+the library's own encoder before timing.
+
+Printed: one JSON line (rank 0) with the device-timed frames/s (`value`),
+the same through the C ABI with host buffers (`e2e`), raster-order decode of
+the same frame on the same GPU, the roofline of the dominant kernel class
+from CUDA events, SM clocks sampled during the timed region, and the FP64
+CPU oracle timed on a bounded crop (`cpu_baseline`).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun, one rank per GPU) runs independent replicas: each rank
+decodes its own frames (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p latent frames/s (wavefront vs raster SWA, same GB300) at ≤0.1% rate delta vs FP64"
+WORKLOAD = ("1080p I-frame decode: latents 68x120x192, hyperlatents 17x30x128, d=384 nh=6 k=7, "
+            "8+1+8 blocks, BF16 projections / FP32 accumulate, wavefront 2i+j (254 steps)")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--batch", type=int, default=1, help="frames decoded per step")
+    ap.add_argument("--raster-frames", type=int, default=1)
+    ap.add_argument("--cpu-rows", type=int, default=8, help="rows of the 1080p frame in the oracle's sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {k: float(d[k]) for k in FALLBACK_PEAKS}, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def start(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush(); self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle leg
+
+class OracleSample:
+    """The FP64 oracle's wavefront decode of the top `rows` rows of the
+    1080p frame (their parameters depend only on rows above them, so the
+    crop is an exact sub-problem).  The crop is encoded once by the oracle;
+    `time_decode` times one decode of it, rANS included."""
+
+    def __init__(self, rows: int):
+        import torch
+        import oracle
+        from paper_2605_20977_gb300 import synth
+        oracle.build()
+        self.O = oracle
+        cfg = synth.config("i1080")
+        self.cfg, self.rows = cfg, rows
+        self.crop = cfg.with_grid(rows, cfg.W)
+        w = synth.weights(cfg)
+        fr = synth.frames(cfg, 1, seed=1002)
+        self.y = fr.y[:, :rows].copy()
+        self.z = fr.z[:, :self.crop.Hh].copy()
+        mask = synth.matrix_mask(cfg)
+        w64 = w.astype(np.float64)
+        w64[mask] = torch.from_numpy(w[mask]).to(torch.bfloat16).to(torch.float64).numpy()
+        self.w64 = w64
+        self.bs, mu, sg = oracle.encode_frames(self.crop, w64, self.y, self.z)
+        self.mu, self.sg = mu[0], sg[0]
+        self.npos = rows * cfg.W
+        self.threads = oracle.num_threads()
+
+    def time_decode(self) -> float:
+        t0 = time.perf_counter()
+        yd, _, _ = self.O.decode_frames(self.crop, self.w64, self.bs, self.z)
+        dt = time.perf_counter() - t0
+        if not np.array_equal(yd, self.y):
+            raise RuntimeError("oracle decode differs")
+        return dt
+
+    def describe(self, secs: float) -> str:
+        return (f"FP64 oracle wavefront decode (rANS included) of the top {self.rows} rows "
+                f"({self.npos} of {self.cfg.H * self.cfg.W} positions) of the 1080p frame: "
+                f"{secs:.2f} s per crop, extrapolated to a frame by positions")
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return 0
+    rows = args.cpu_rows
+    smp = OracleSample(rows)
+    # warmup steps, then timed steps, each one decode of the crop
+    secs = []
+    for s in range(args.warmup + args.steps):
+        t = smp.time_decode()
+        if s >= args.warmup:
+            secs.append(t)
+    npos, threads = smp.npos, smp.threads
+    frac = npos / (smp.cfg.H * smp.cfg.W)
+    value = frac / float(np.mean(secs))
+    sample = smp.describe(float(np.mean(secs)))
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_rows": rows},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if
+    the kernel source is unchanged since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != d["sha256"]:
+        return None
+    return d["dram_bytes_per_launch"]
+
+
+def run_ours(args, rank: int, world: int, local: int):
+    import torch
+    import torch.distributed as dist
+    from paper_2605_20977_gb300 import build, psw, synth
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = synth.config("i1080")
+    w = synth.weights(cfg)
+    ctx = psw.Context(cfg, w, precision=psw.PSW_BF16)
+    B = args.batch
+    fdw = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_WAVEFRONT)
+    frames = [synth.frames(cfg, 1, seed=1002 + rank * B + b) for b in range(B)]
+    ys = [torch.from_numpy(f.y[0]).to(dev) for f in frames]
+    zs = [torch.from_numpy(f.z[0]).to(dev) for f in frames]
+    cap = ctx.bitstream_capacity(cfg.H, cfg.W)
+    bss, lens, mus, sgs = [], [], [], []
+    enc = ctx.seq_create(cfg.H, cfg.W)
+    for b in range(B):
+        enc.reset()
+        bs = torch.zeros(cap, dtype=torch.uint8, device=dev)
+        mu = torch.zeros(ys[b].shape, dtype=torch.float32, device=dev); sg = torch.zeros_like(mu)
+        lens.append(enc.encode_params(fdw, ys[b], zs[b], mu, sg, bs))
+        bss.append(bs); mus.append(mu); sgs.append(sg)
+    decs = [ctx.seq_create(cfg.H, cfg.W) for _ in range(B)]
+    outs = [torch.zeros_like(y) for y in ys]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for b in range(B):
+            decs[b].reset()
+            decs[b].decode_frame(fdw, bss[b], lens[b], zs[b], outs[b])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = ctx.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)                       # evict L2 between steps
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = (ctx.launch_count() - l0) / args.steps
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total = sum(step_ms) / 1e3
+    for b in range(B):
+        if not torch.equal(outs[b], ys[b]):
+            raise RuntimeError("decoded latents differ from the encoded ones")
+    t = torch.tensor([total], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_max = float(t.item())
+    value = world * B * args.steps / total_max
+
+    # end to end through the C ABI with pinned host buffers
+    h_bs = [bss[b][:lens[b]].cpu().pin_memory() for b in range(B)]
+    h_z = [zs[b].cpu().pin_memory() for b in range(B)]
+    h_y = [torch.empty(ys[b].shape, dtype=torch.int16).pin_memory() for b in range(B)]
+    d_bs = [torch.zeros(cap, dtype=torch.uint8, device=dev) for _ in range(B)]
+    d_z = [torch.zeros_like(zs[b]) for b in range(B)]
+
+    def e2e_step():
+        for b in range(B):
+            d_bs[b][:lens[b]].copy_(h_bs[b], non_blocking=True)
+            d_z[b].copy_(h_z[b], non_blocking=True)
+            decs[b].reset()
+            decs[b].decode_frame(fdw, d_bs[b], lens[b], d_z[b], outs[b])
+            h_y[b].copy_(outs[b], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    e2e_step()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    flush.fill_(1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    for b in range(B):
+        if not torch.equal(h_y[b], ys[b].cpu()):
+            raise RuntimeError("end-to-end decode differs")
+    e2e_t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * B * args.steps / float(e2e_t.item())
+    h2d = sum(int(lens[b]) + h_z[b].numel() * 2 for b in range(B))
+    d2h = sum(h_y[b].numel() * 2 for b in range(B))
+
+    # roofline of the dominant kernel class from CUDA events (instrumented step)
+    flush.fill_(2)
+    ctx.profile_begin()
+    step()
+    stats = ctx.profile_end()
+    pk, pk_kind = peaks()
+    dom = max(stats, key=lambda s: s["ms"])
+    tot_ms = sum(s["ms"] for s in stats)
+    if dom["name"].startswith("gemm"):
+        achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
+        peak, unit, bound = pk["bf16_tflops_sustained"], "TFLOP/s", "tensor"
+    else:
+        achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+        peak, unit, bound = pk["hbm_gbs"], "GB/s", "hbm"
+    kname = {"gemm_tc": "k_gemm_tc", "attention": "k_attention", "heads": "k_heads", "rmsnorm": "k_rmsnorm",
+             "rans": "k_rans_dec_step", "embed": "k_embed_latent", "gemm_simt": "k_gemm_simt"}.get(dom["name"])
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": traffic_for(kname), "kernel": dom["name"], "launches_per_step": dom["launches"],
+            "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1),
+            "share_of_kernel_time": dom["ms"] / tot_ms, "peak_source": f"{pk_kind} (MEASURED_PEAKS.json)"
+            if pk_kind == "measured" else "fallback",
+            "classes": {s["name"]: {"ms": round(s["ms"], 3), "launches": s["launches"]} for s in stats}}
+
+    # raster order, same model and masks, same GPU
+    raster = None
+    if rank == 0 and args.raster_frames > 0:
+        fdr = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_RASTER)
+        encr = ctx.seq_create(cfg.H, cfg.W)
+        bsr = torch.zeros(cap, dtype=torch.uint8, device=dev)
+        nr = encr.encode_params(fdr, ys[0], zs[0], bitstream=bsr)
+        decr = ctx.seq_create(cfg.H, cfg.W)
+        r_ms = []
+        for _ in range(args.raster_frames):
+            flush.fill_(3)
+            a = torch.cuda.Event(enable_timing=True); b_ = torch.cuda.Event(enable_timing=True)
+            decr.reset()
+            a.record(stream)
+            decr.decode_frame(fdr, bsr, nr, zs[0], outs[0])
+            b_.record(stream)
+            torch.cuda.synchronize()
+            r_ms.append(a.elapsed_time(b_))
+        if not torch.equal(outs[0], ys[0]):
+            raise RuntimeError("raster decode differs")
+        raster = {"value": 1e3 / float(np.mean(r_ms)), "unit": "frames/s", "ms_per_frame": float(np.mean(r_ms)),
+                  "steps_per_frame": cfg.H * cfg.W, "frames": args.raster_frames}
+
+    # rate of the decoded frame: GPU parameters vs the FP64 oracle (crop rows)
+    rate = {"bits_per_symbol": ctx.rate(ys[0], mus[0], sgs[0]) / ys[0].numel(),
+            "container_bits_per_symbol": 8.0 * lens[0] / ys[0].numel()}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        smp = OracleSample(args.cpu_rows)
+        secs = smp.time_decode()
+        frac = smp.npos / (cfg.H * cfg.W)
+        cpu = {"value": frac / secs, "unit": "frames/s", "cores": smp.threads, "kind": "oracle",
+               "sample": smp.describe(secs)}
+        R = args.cpu_rows
+        r_gpu = smp.O.rate_bits(smp.y[0], mus[0][:R].double().cpu().numpy(), sgs[0][:R].double().cpu().numpy())
+        r_64 = smp.O.rate_bits(smp.y[0], smp.mu, smp.sg)
+        rate["delta_vs_fp64_on_sample"] = abs(r_gpu - r_64) / r_64
+
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_step": B, "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(round(launches)),
+            "roofline": roof, "raster": raster,
+            "speedup_vs_raster": (value / world / raster["value"]) if raster else None,
+            "rate": rate, "clocks": clk, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    try:
+        return run_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -208,6 +208,28 @@ psw_status psw_rans_decode(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd,
                            const uint8_t *bitstream_dev, size_t len, const uint8_t *idx_dev,
                            const int32_t *m_dev, int16_t *yhat_out_dev, void *stream);
 
+/* Instrumentation (not in the paper; measurement support).
+ * psw_launch_count: kernels this context has launched so far.
+ * psw_profile_begin: from now on every kernel launch of this context is
+ * bracketed by CUDA events on its stream (adds host overhead; for
+ * measurement runs only).  psw_profile_end synchronises the device, stops
+ * recording and writes one psw_kernel_stat per kernel class (at most cap;
+ * *n_out = number written): launches, summed event time in ms, and the
+ * algorithmic FLOPs and bytes of those launches (FLOPs: 2 per multiply-add
+ * of the projections and attention; bytes: operands read once plus results
+ * written once). */
+typedef struct {
+    char name[32];
+    long launches;
+    double ms;
+    double flops;
+    double bytes;
+} psw_kernel_stat;
+
+long psw_launch_count(const psw_ctx *ctx);
+psw_status psw_profile_begin(psw_ctx *ctx);
+psw_status psw_profile_end(psw_ctx *ctx, psw_kernel_stat *out, int cap, int *n_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -136,6 +136,13 @@ struct psw_ctx {
     size_t rate_cap = 0;
     std::string err;
     std::vector<psw_seq *> seqs;
+    // instrumentation
+    long launches = 0;
+    bool prof = false;
+    struct Rec { int cls; cudaEvent_t a, b; double flops, bytes; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> evpool;
+    size_t evnext = 0;
 };
 
 struct psw_seq {
@@ -183,6 +190,43 @@ psw_status fail(psw_ctx *ctx, psw_status st, const char *fmt, ...)
     } while (0)
 
 const float *W(const psw_ctx *c, long off) { return c->w + off; }
+
+// Kernel classes reported by psw_profile_end.
+enum KClass { K_GEMM_TC, K_GEMM_SIMT, K_ATTN, K_NORM, K_EMBED, K_HEADS, K_RANS, K_OTHER, K_NCLASS };
+const char *const kclass_name[K_NCLASS] = {"gemm_tc", "gemm_simt", "attention", "rmsnorm",
+                                          "embed", "heads", "rans", "other"};
+
+cudaEvent_t ev_get(psw_ctx *c)
+{
+    if (c->evnext == c->evpool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->evpool.push_back(e);
+    }
+    return c->evpool[c->evnext++];
+}
+
+// Counts one kernel launch; when profiling, brackets it with events.
+struct Scope {
+    psw_ctx *c;
+    cudaStream_t s;
+    psw_ctx::Rec r;
+    Scope(psw_ctx *c_, cudaStream_t s_, int cls, double flops, double bytes) : c(c_), s(s_)
+    {
+        c->launches++;
+        if (c->prof) {
+            r = psw_ctx::Rec{cls, ev_get(c), ev_get(c), flops, bytes};
+            cudaEventRecord(r.a, s);
+        }
+    }
+    ~Scope()
+    {
+        if (c->prof) {
+            cudaEventRecord(r.b, s);
+            c->recs.push_back(r);
+        }
+    }
+};
 
 // Transposed ([out][in], K-major), compute-typed copies of every block
 // projection, carved from one arena.  A dry run only sums the sizes.
@@ -296,6 +340,12 @@ void gemm_call(const Pass &P, const void *A, int lda, const void *Wt, const void
     GemmArgs g{};
     g.A = A; g.lda = lda; g.Wt = Wt; g.Wt2 = Wt2; g.M = M; g.N = N; g.K = K; g.epi = e;
     g.status = P.q->d_status;
+    if (M <= 0) return;
+    bool tc = gemm_tc_supported(P.c->prec, N, K);
+    double es = P.c->prec == P_BF16 ? 2.0 : 4.0, nw = Wt2 ? 2.0 : 1.0;
+    double out_b = (e.mode == EPI_RESID || e.mode == EPI_RESID_BASE) ? 8.0 : es;
+    Scope sc(P.c, P.s, tc ? K_GEMM_TC : K_GEMM_SIMT, 2.0 * nw * M * N * K,
+             nw * N * K * es + (double)M * K * es + (double)M * N * out_b);
     if (!gemm(P.c->prec, g, P.s)) P.q->launch_failed = true;
 }
 
@@ -324,6 +374,21 @@ Epi epi_swiglu(void *out, int ld)
     return e;
 }
 
+#define LAUNCH(P_, cls, flops, bytes, call)                 \
+    do {                                                    \
+        Scope sc_((P_).c, (P_).s, (cls), (flops), (bytes)); \
+        call;                                               \
+    } while (0)
+
+double attn_flops(const psw_model_desc &m, int n, double nkeys) { return 4.0 * n * nkeys * m.d; }
+// mean visible keys: about half the window under the causal masks, all of it unmasked
+double attn_keys(const AttnArgs &a) { return a.kind < 0 ? (double)a.nfr * a.k * a.k : 0.5 * a.k * a.k; }
+double attn_bytes(const psw_model_desc &m, const AttnArgs &a)
+{
+    double es = 2.0;   // bf16 K/V rows; FP32 runs report the same algorithmic count
+    return a.n * (double)m.d * es * (2.0 * attn_keys(a) + 2.0);
+}
+
 AttnArgs attn_args(const Pass &P, const int *pos, int n, const void *Qp, int q_full, const float *bias,
                    int bias_h_stride, int kind)
 {
@@ -341,7 +406,7 @@ void ffn(const Pass &P, const BlockDev &bd, long g_ffn, float *x, const int *pos
     psw_ctx *c = P.c;
     psw_seq *q = P.q;
     const psw_model_desc &m = c->md;
-    launch_rmsnorm(c->prec, pos, n, x, W(c, g_ffn), m.d, q->Xn, 0, P.s);
+    LAUNCH(P, K_NORM, 3.0 * n * m.d, n * m.d * 6.0, launch_rmsnorm(c->prec, pos, n, x, W(c, g_ffn), m.d, q->Xn, 0, P.s));
     gemm_call(P, q->Xn, m.d, bd.Wg, bd.Wu, n, m.F, m.d, epi_swiglu(q->Hid, m.F));
     gemm_call(P, q->Hid, m.F, bd.Wd, nullptr, n, m.d, m.F, epi_resid(pos, x));
 }
@@ -358,14 +423,14 @@ void spatial_block(const Pass &P, const BlockOff &bo, const BlockDev &bd, int bi
     psw_seq *q = P.q;
     const psw_model_desc &m = c->md;
     int d = m.d, kk = m.k * m.k;
-    launch_rmsnorm(c->prec, pos, n, x, W(c, bo.g_attn), d, q->Xn, 0, P.s);
+    LAUNCH(P, K_NORM, 3.0 * n * d, n * d * 6.0, launch_rmsnorm(c->prec, pos, n, x, W(c, bo.g_attn), d, q->Xn, 0, P.s));
     gemm_call(P, q->Xn, d, bd.Wqkv, nullptr, n, 3 * d, d, epi_qkv(pos, d, d, q->Q, Kc, Vc));
     AttnArgs a = attn_args(P, pos, n, q->Q, 0, W(c, bo.bias), kk, 1);
     a.K[0] = Kc; a.V[0] = Vc; a.nfr = 1; a.age[0] = 0;
-    launch_attention(c->prec, a, P.s);
+    LAUNCH(P, K_ATTN, attn_flops(m, a.n, attn_keys(a)), attn_bytes(m, a), launch_attention(c->prec, a, P.s));
     gemm_call(P, q->O, d, bd.Wo, nullptr, n, d, d, epi_resid(pos, x));
     if (m.temporal) {
-        launch_rmsnorm(c->prec, pos, n, x, W(c, bo.g_x), d, q->Xn, 0, P.s);
+        LAUNCH(P, K_NORM, 3.0 * n * d, n * d * 6.0, launch_rmsnorm(c->prec, pos, n, x, W(c, bo.g_x), d, q->Xn, 0, P.s));
         gemm_call(P, q->Xn, d, bd.Wxq, nullptr, n, d, d, epi_store(pos, 0, q->Q, d));
         AttnArgs xa = attn_args(P, pos, n, q->Q, 0, W(c, bo.xbias), m.Tf * kk, -1);
         int f = q->frame, f0 = std::max(0, f - m.Tf + 1);
@@ -376,7 +441,7 @@ void spatial_block(const Pass &P, const BlockOff &bo, const BlockDev &bd, int bi
             xa.V[u] = cache_at(q->XV, P, (long)bidx * m.Tf + ff % m.Tf);
             xa.age[u] = f - ff;
         }
-        launch_attention(c->prec, xa, P.s);
+        LAUNCH(P, K_ATTN, attn_flops(m, xa.n, attn_keys(xa)), attn_bytes(m, xa), launch_attention(c->prec, xa, P.s));
         gemm_call(P, q->O, d, bd.Wxo, nullptr, n, d, d, epi_resid(pos, x));
     }
     ffn(P, bd, bo.g_ffn, x, pos, n);
@@ -391,9 +456,10 @@ void frame_prologue(const Pass &P, const int16_t *zhat, const int16_t *yprev)
     psw_seq *q = P.q;
     const psw_model_desc &m = c->md;
     int d = m.d, HW = P.HW(), Wh = (P.W + m.r - 1) / m.r, kk = m.k * m.k;
-    launch_embed_hyper(zhat, P.H, P.W, Wh, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp),
-                       W(c, c->lay.b_hp), d, q->eh, P.s);
-    launch_rmsnorm(c->prec, nullptr, HW, q->eh, W(c, c->lay.acc_g_q), d, q->Xn, 0, P.s);
+    LAUNCH(P, K_EMBED, 2.0 * HW * m.Ch * d, HW * (m.Ch * 2.0 + d * 4.0),
+           launch_embed_hyper(zhat, P.H, P.W, Wh, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp),
+                              W(c, c->lay.b_hp), d, q->eh, P.s));
+    LAUNCH(P, K_NORM, 3.0 * HW * d, HW * d * 6.0, launch_rmsnorm(c->prec, nullptr, HW, q->eh, W(c, c->lay.acc_g_q), d, q->Xn, 0, P.s));
     gemm_call(P, q->Xn, d, c->acc.Wqkv, nullptr, HW, d, d, epi_store(nullptr, 0, q->qa, d));
     if (!m.temporal) return;
     // Context Transformer (Sec. 3.1): temporally shifted latents (learned
@@ -401,13 +467,14 @@ void frame_prologue(const Pass &P, const int16_t *zhat, const int16_t *yprev)
     // last Tf frames of each layer, final RMSNorm; then every spatial
     // block's cross-attention K/V of this frame.
     int f = q->frame, slot = f % m.Tf, f0 = std::max(0, f - m.Tf + 1);
-    if (f == 0) launch_fill_rows(W(c, c->lay.pad), HW, d, q->g, P.s);
-    else launch_embed_latent(nullptr, HW, yprev, m.C, W(c, c->lay.gamma_c), W(c, c->lay.W_c), W(c, c->lay.b_c),
-                             d, q->g, P.s);
+    if (f == 0) LAUNCH(P, K_EMBED, 0.0, HW * d * 4.0, launch_fill_rows(W(c, c->lay.pad), HW, d, q->g, P.s));
+    else LAUNCH(P, K_EMBED, 2.0 * HW * m.C * d, HW * (m.C * 2.0 + d * 4.0),
+                launch_embed_latent(nullptr, HW, yprev, m.C, W(c, c->lay.gamma_c), W(c, c->lay.W_c),
+                                    W(c, c->lay.b_c), d, q->g, P.s));
     for (int l = 0; l < m.Lc; l++) {
         const BlockOff &bo = c->lay.ctx[l];
         const BlockDev &bd = c->ctxb[l];
-        launch_rmsnorm(c->prec, nullptr, HW, q->g, W(c, bo.g_attn), d, q->Xn, 0, P.s);
+        LAUNCH(P, K_NORM, 3.0 * HW * d, HW * d * 6.0, launch_rmsnorm(c->prec, nullptr, HW, q->g, W(c, bo.g_attn), d, q->Xn, 0, P.s));
         gemm_call(P, q->Xn, d, bd.Wqkv, nullptr, HW, 3 * d, d,
                   epi_qkv(nullptr, d, d, q->Q, cache_at(q->CK, P, (long)l * m.Tf + slot),
                           cache_at(q->CV, P, (long)l * m.Tf + slot)));
@@ -419,11 +486,11 @@ void frame_prologue(const Pass &P, const int16_t *zhat, const int16_t *yprev)
             a.V[u] = cache_at(q->CV, P, (long)l * m.Tf + ff % m.Tf);
             a.age[u] = f - ff;
         }
-        launch_attention(c->prec, a, P.s);
+        LAUNCH(P, K_ATTN, attn_flops(m, a.n, attn_keys(a)), attn_bytes(m, a), launch_attention(c->prec, a, P.s));
         gemm_call(P, q->O, d, bd.Wo, nullptr, HW, d, d, epi_resid(nullptr, q->g));
         ffn(P, bd, bo.g_ffn, q->g, nullptr, HW);
     }
-    launch_rmsnorm(c->prec, nullptr, HW, q->g, W(c, c->lay.g_ctx), d, q->Xn, 0, P.s);
+    LAUNCH(P, K_NORM, 3.0 * HW * d, HW * d * 6.0, launch_rmsnorm(c->prec, nullptr, HW, q->g, W(c, c->lay.g_ctx), d, q->Xn, 0, P.s));
     for (int b = 0; b < 2 * m.L; b++) {
         const BlockDev &bd = b < m.L ? c->sm1[b] : c->sm2[b - m.L];
         gemm_call(P, q->Xn, d, bd.Wxkv, nullptr, HW, 2 * d, d,
@@ -441,10 +508,12 @@ void run_sm1(const Pass &P, const int16_t *y, const int *pos, int n)
     const psw_model_desc &m = c->md;
     int d = m.d;
     if (n <= 0) return;
-    launch_embed_latent(pos, n, y, m.C, W(c, c->lay.gamma_in), W(c, c->lay.W_in), W(c, c->lay.b_in), d, q->x1, P.s);
+    LAUNCH(P, K_EMBED, 2.0 * n * m.C * d, n * (m.C * 2.0 + d * 4.0),
+           launch_embed_latent(pos, n, y, m.C, W(c, c->lay.gamma_in), W(c, c->lay.W_in), W(c, c->lay.b_in), d,
+                               q->x1, P.s));
     for (int l = 0; l < m.L; l++)
         spatial_block(P, c->lay.sm1[l], c->sm1[l], l, q->x1, cache_at(q->K1, P, l), cache_at(q->V1, P, l), pos, n);
-    launch_rmsnorm(c->prec, pos, n, q->x1, W(c, c->lay.acc_g_kv), d, q->Xn, 0, P.s);
+    LAUNCH(P, K_NORM, 3.0 * n * d, n * d * 6.0, launch_rmsnorm(c->prec, pos, n, q->x1, W(c, c->lay.acc_g_kv), d, q->Xn, 0, P.s));
     gemm_call(P, q->Xn, d, c->acc.Wxkv, nullptr, n, 2 * d, d, epi_qkv(pos, d, 0, nullptr, q->Ka, q->Va));
 }
 
@@ -459,7 +528,7 @@ void run_acc_sm2_heads(const Pass &P, const int *pos, int n)
     if (n <= 0) return;
     AttnArgs a = attn_args(P, pos, n, q->qa, 1, W(c, c->lay.acc_bias), m.k * m.k, 0);
     a.K[0] = q->Ka; a.V[0] = q->Va; a.nfr = 1; a.age[0] = 0;
-    launch_attention(c->prec, a, P.s);
+    LAUNCH(P, K_ATTN, attn_flops(m, a.n, attn_keys(a)), attn_bytes(m, a), launch_attention(c->prec, a, P.s));
     gemm_call(P, q->O, d, c->acc.Wo, nullptr, n, d, d, epi_resid(pos, q->x2, q->eh));
     ffn(P, c->acc, c->lay.acc_g_ffn, q->x2, pos, n);
     for (int l = 0; l < m.L; l++)
@@ -471,7 +540,8 @@ void run_acc_sm2_heads(const Pass &P, const int *pos, int n)
     h.gamma_mu = W(c, c->lay.gamma_mu); h.beta_mu = W(c, c->lay.beta_mu);
     h.gamma_sig = W(c, c->lay.gamma_sig); h.beta_sig = W(c, c->lay.beta_sig);
     h.scale = c->d_scale; h.mu = q->mu; h.sigma = q->sigma; h.idx = q->idx; h.m = q->m;
-    launch_heads(h, P.s);
+    LAUNCH(P, K_HEADS, 2.0 * n * (2.0 * d * d + 2.0 * d * m.C), n * (d * 4.0 + m.C * 13.0),
+           launch_heads(h, P.s));
 }
 
 CoderDev coder(const psw_ctx *c) { return CoderDev{c->d_cdf, c->d_meta}; }
@@ -520,7 +590,11 @@ psw_status encode_symbols(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, cons
 {
     int HW = fd->H * fd->W, C = c->md.C;
     int cap_words = 3 * HW + 64;
-    launch_rans_encode(coder(c), q->d_order, HW, C, y, idx, m, q->enc_scratch, cap_words, q->enc_nw, q->rstate, s);
+    {
+        Scope sc(c, s, K_RANS, 0.0, (double)HW * C * 7.0);
+        launch_rans_encode(coder(c), q->d_order, HW, C, y, idx, m, q->enc_scratch, cap_words, q->enc_nw, q->rstate, s);
+    }
+    Scope sc2(c, s, K_RANS, 0.0, (double)HW * C * 2.0);
     launch_rans_assemble(fd->H, fd->W, C, fd->schedule, q->enc_scratch, cap_words, q->enc_nw, q->rstate, bs, cap,
                          q->enc_total, q->d_status, s);
     CK_CUDA(c, cudaMemcpyAsync(q->h_total, q->enc_total, 8, cudaMemcpyDeviceToHost, s));
@@ -611,6 +685,7 @@ void psw_destroy(psw_ctx *c)
     cudaFree(c->w); cudaFree(c->wmat); cudaFree(c->d_cdf); cudaFree(c->d_meta); cudaFree(c->d_scale);
     cudaFree(c->rate_buf);
     if (c->h_rate) cudaFreeHost(c->h_rate);
+    for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
     free_cdf_tables(c->tabs);
     delete c;
 }
@@ -758,8 +833,11 @@ psw_status psw_decode_frame(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, co
     Pass P{c, q, s, fd->H, fd->W};
     CK_CUDA(c, cudaMemsetAsync(q->d_status, 0, 4, s));
     frame_prologue(P, zhat_dev, q->yprev);
-    launch_rans_dec_init(bitstream_dev, len, fd->H, fd->W, m.C, fd->schedule, q->rstate, q->rptr, q->rend,
-                         q->d_status, s);
+    {
+        Scope sc(c, s, K_RANS, 0.0, (double)m.C * 128.0);
+        launch_rans_dec_init(bitstream_dev, len, fd->H, fd->W, m.C, fd->schedule, q->rstate, q->rptr, q->rend,
+                             q->d_status, s);
+    }
     const int *ord = q->d_order;
     for (int t = 0; t < q->T; t++) {
         int a0 = q->h_start[t], n = q->h_start[t + 1] - a0;
@@ -768,10 +846,14 @@ psw_status psw_decode_frame(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, co
             run_sm1(P, q->y, ord + b0, a0 - b0);
         }
         run_acc_sm2_heads(P, ord + a0, n);
+        Scope sc(c, s, K_RANS, 0.0, (double)n * m.C * 7.0 + (double)len * n / HW);
         launch_rans_dec_step(coder(c), ord, a0, n, m.C, q->idx, q->m, bitstream_dev, q->rstate, q->rptr, q->rend,
                              q->y, q->d_status, s);
     }
-    launch_rans_dec_finish(bitstream_dev, m.C, q->rstate, q->rptr, q->rend, q->d_status, s);
+    {
+        Scope sc(c, s, K_RANS, 0.0, (double)m.C * 128.0);
+        launch_rans_dec_finish(bitstream_dev, m.C, q->rstate, q->rptr, q->rend, q->d_status, s);
+    }
     CK_CUDA(c, cudaGetLastError());
     CK_CUDA(c, cudaMemcpyAsync(yhat_out_dev, q->y, nsym * 2, cudaMemcpyDeviceToDevice, s));
     if (mu_dev) CK_CUDA(c, cudaMemcpyAsync(mu_dev, q->mu, nsym * 4, cudaMemcpyDeviceToDevice, s));
@@ -887,6 +969,42 @@ psw_status psw_rans_decode(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, con
     int dst = 0;
     if ((st = read_status(c, q, s, &dst))) return st;
     if (dst & ST_CORRUPT) return fail(c, PSW_ERR_CORRUPT, "bitstream failed validation");
+    return PSW_OK;
+}
+
+long psw_launch_count(const psw_ctx *c) { return c ? c->launches : 0; }
+
+psw_status psw_profile_begin(psw_ctx *c)
+{
+    if (!c) return PSW_ERR_INVALID;
+    c->recs.clear();
+    c->evnext = 0;
+    c->prof = true;
+    return PSW_OK;
+}
+
+psw_status psw_profile_end(psw_ctx *c, psw_kernel_stat *out, int cap, int *n_out)
+{
+    if (!c) return PSW_ERR_INVALID;
+    c->prof = false;
+    CK_CUDA(c, cudaDeviceSynchronize());
+    psw_kernel_stat tot[K_NCLASS];
+    memset(tot, 0, sizeof(tot));
+    for (int k = 0; k < K_NCLASS; k++) snprintf(tot[k].name, sizeof(tot[k].name), "%s", kclass_name[k]);
+    for (const auto &r : c->recs) {
+        float ms = 0.0f;
+        CK_CUDA(c, cudaEventElapsedTime(&ms, r.a, r.b));
+        tot[r.cls].launches++;
+        tot[r.cls].ms += ms;
+        tot[r.cls].flops += r.flops;
+        tot[r.cls].bytes += r.bytes;
+    }
+    c->recs.clear();
+    c->evnext = 0;
+    int n = 0;
+    for (int k = 0; k < K_NCLASS && n < cap; k++)
+        if (tot[k].launches) out[n++] = tot[k];
+    if (n_out) *n_out = n;
     return PSW_OK;
 }
 

@@ -24,7 +24,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "CORRUPT", 5: "TI
 EXPORTS = ["psw_weights_count", "psw_create", "psw_destroy", "psw_last_error", "psw_ctx_bytes", "psw_seq_bytes",
            "psw_seq_create", "psw_seq_reset", "psw_seq_destroy", "psw_bitstream_capacity", "psw_encode_params",
            "psw_decode_frame", "psw_decode_batch", "psw_rate", "psw_quantize", "psw_scale_table", "psw_cdf_table",
-           "psw_rans_encode", "psw_rans_decode"]
+           "psw_rans_encode", "psw_rans_decode", "psw_launch_count", "psw_profile_begin", "psw_profile_end"]
 
 
 class ModelDesc(ct.Structure):
@@ -33,6 +33,11 @@ class ModelDesc(ct.Structure):
 
 class FrameDesc(ct.Structure):
     _fields_ = [("H", ct.c_int), ("W", ct.c_int), ("schedule", ct.c_int)]
+
+
+class KernelStat(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_long), ("ms", ct.c_double), ("flops", ct.c_double),
+                ("bytes", ct.c_double)]
 
 
 class PswError(RuntimeError):
@@ -77,6 +82,9 @@ def load(path: str = LIB_PATH):
             "psw_cdf_table": (I, [P, I, P, I, ct.POINTER(I), ct.POINTER(I)]),
             "psw_rans_encode": (I, [P, P, FD, P, P, P, P, S, ct.POINTER(S), P]),
             "psw_rans_decode": (I, [P, P, FD, P, S, P, P, P, P]),
+            "psw_launch_count": (ct.c_long, [P]),
+            "psw_profile_begin": (I, [P]),
+            "psw_profile_end": (I, [P, ct.POINTER(KernelStat), I, ct.POINTER(I)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -184,6 +192,19 @@ class Context:
         f = np.zeros(4096, np.uint32)
         self._check(self.lib.psw_cdf_table(self.h, l, f.ctypes.data, 4096, ct.byref(n), ct.byref(T)))
         return f[:n.value].copy(), T.value
+
+    def launch_count(self) -> int:
+        return int(self.lib.psw_launch_count(self.h))
+
+    def profile_begin(self):
+        self._check(self.lib.psw_profile_begin(self.h))
+
+    def profile_end(self) -> list:
+        arr = (KernelStat * 16)()
+        n = ct.c_int()
+        self._check(self.lib.psw_profile_end(self.h, arr, 16, ct.byref(n)))
+        return [dict(name=a.name.decode(), launches=int(a.launches), ms=float(a.ms), flops=float(a.flops),
+                     bytes=float(a.bytes)) for a in arr[:n.value]]
 
     def decode_batch(self, seqs, fds, bitstreams, lens, zhats, outs, stream=None):
         n = len(seqs)

@@ -50,8 +50,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--batch", type=int, default=1, help="frames decoded per step")
-    ap.add_argument("--raster-frames", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=16, help="frames decoded per step")
+    ap.add_argument("--raster-frames", type=int, default=1, help="timed raster steps (0: skip raster)")
+    ap.add_argument("--no-raster-batch", dest="raster_batch", action="store_false")
     ap.add_argument("--cpu-rows", type=int, default=8, help="rows of the 1080p frame in the oracle's sample")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -79,6 +80,8 @@ class Clocks:
         self.proc = None
 
     def start(self):
+        if os.environ.get("CUDA_INJECTION64_PATH"):     # under a profiler: no sampler child process
+            return
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
@@ -89,7 +92,7 @@ class Clocks:
 
     def stop(self) -> dict:
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
         time.sleep(0.25)
         self.proc.terminate()
         self.proc.wait()
@@ -209,61 +212,79 @@ def run_ours(args, rank: int, world: int, local: int):
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
     cfg = synth.config("i1080")
     w = synth.weights(cfg)
     ctx = psw.Context(cfg, w, precision=psw.PSW_BF16)
     B = args.batch
     fdw = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_WAVEFRONT)
+    fdr = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_RASTER)
     frames = [synth.frames(cfg, 1, seed=1002 + rank * B + b) for b in range(B)]
     ys = [torch.from_numpy(f.y[0]).to(dev) for f in frames]
     zs = [torch.from_numpy(f.z[0]).to(dev) for f in frames]
     cap = ctx.bitstream_capacity(cfg.H, cfg.W)
-    bss, lens, mus, sgs = [], [], [], []
     enc = ctx.seq_create(cfg.H, cfg.W)
-    for b in range(B):
-        enc.reset()
-        bs = torch.zeros(cap, dtype=torch.uint8, device=dev)
-        mu = torch.zeros(ys[b].shape, dtype=torch.float32, device=dev); sg = torch.zeros_like(mu)
-        lens.append(enc.encode_params(fdw, ys[b], zs[b], mu, sg, bs))
-        bss.append(bs); mus.append(mu); sgs.append(sg)
+
+    def encode(fd):
+        bss, lens = [], []
+        for b in range(B):
+            enc.reset()
+            bs = torch.zeros(cap, dtype=torch.uint8, device=dev)
+            lens.append(enc.encode_params(fd, ys[b], zs[b], bitstream=bs))
+            bss.append(bs)
+        return bss, lens
+
+    bss, lens = encode(fdw)
+    mu0 = torch.zeros(ys[0].shape, dtype=torch.float32, device=dev); sg0 = torch.zeros_like(mu0)
+    enc.reset()
+    enc.encode_params(fdw, ys[0], zs[0], mu0, sg0)
     decs = [ctx.seq_create(cfg.H, cfg.W) for _ in range(B)]
     outs = [torch.zeros_like(y) for y in ys]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
 
-    def step():
-        for b in range(B):
-            decs[b].reset()
-            decs[b].decode_frame(fdw, bss[b], lens[b], zs[b], outs[b])
+    def batch_step(seqs, fd, bs_, ln_, n):
+        for q in seqs[:n]:
+            q.reset()
+        ctx.decode_batch(seqs[:n], [fd] * n, bs_[:n], ln_[:n], zs[:n], outs[:n])
+
+    def timed(fn, reps):
+        ms = []
+        for k in range(reps):
+            flush.fill_(k & 0xFF)                   # evict L2 between steps
+            a = torch.cuda.Event(enable_timing=True); b_ = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b_.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b_))
+        return ms
 
     for _ in range(args.warmup):
-        step()
+        batch_step(decs, fdw, bss, lens, B)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = Clocks(local)
     clocks.start()
     l0 = ctx.launch_count()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)                       # evict L2 between steps
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
+    step_ms = timed(lambda: batch_step(decs, fdw, bss, lens, B), args.steps)
     launches = (ctx.launch_count() - l0) / args.steps
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total = sum(step_ms) / 1e3
     for b in range(B):
         if not torch.equal(outs[b], ys[b]):
             raise RuntimeError("decoded latents differ from the encoded ones")
-    t = torch.tensor([total], device=dev, dtype=torch.float64)
+    t = torch.tensor([sum(step_ms) / 1e3], device=dev, dtype=torch.float64)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_max = float(t.item())
     value = world * B * args.steps / total_max
+
+    # single-frame latency (one frame per call)
+    lat = None
+    if B > 1:
+        batch_step(decs, fdw, bss, lens, 1)
+        lat_ms = timed(lambda: batch_step(decs, fdw, bss, lens, 1), max(2, args.steps))
+        lat = {"ms_per_frame": float(np.mean(lat_ms)), "frames_per_s": 1e3 / float(np.mean(lat_ms))}
 
     # end to end through the C ABI with pinned host buffers
     h_bs = [bss[b][:lens[b]].cpu().pin_memory() for b in range(B)]
@@ -276,35 +297,37 @@ def run_ours(args, rank: int, world: int, local: int):
         for b in range(B):
             d_bs[b][:lens[b]].copy_(h_bs[b], non_blocking=True)
             d_z[b].copy_(h_z[b], non_blocking=True)
-            decs[b].reset()
-            decs[b].decode_frame(fdw, d_bs[b], lens[b], d_z[b], outs[b])
+        for q in decs:
+            q.reset()
+        ctx.decode_batch(decs, [fdw] * B, d_bs, lens, d_z, outs)
+        for b in range(B):
             h_y[b].copy_(outs[b], non_blocking=True)
         torch.cuda.current_stream().synchronize()
 
     e2e_step()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     flush.fill_(1)
     torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
     for b in range(B):
         if not torch.equal(h_y[b], ys[b].cpu()):
             raise RuntimeError("end-to-end decode differs")
-    e2e_t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    e2e_t = torch.tensor([e0.elapsed_time(e1) / 1e3], device=dev, dtype=torch.float64)
     if world > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     e2e_value = world * B * args.steps / float(e2e_t.item())
     h2d = sum(int(lens[b]) + h_z[b].numel() * 2 for b in range(B))
     d2h = sum(h_y[b].numel() * 2 for b in range(B))
 
-    # roofline of the dominant kernel class from CUDA events (instrumented step)
+    # roofline of the dominant kernel class from CUDA events (one
+    # instrumented step with direct launches, after the timed region)
     flush.fill_(2)
     ctx.profile_begin()
-    step()
+    batch_step(decs, fdw, bss, lens, B)
     stats = ctx.profile_end()
     pk, pk_kind = peaks()
     dom = max(stats, key=lambda s: s["ms"])
@@ -320,35 +343,39 @@ def run_ours(args, rank: int, world: int, local: int):
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
             "traffic": traffic_for(kname), "kernel": dom["name"], "launches_per_step": dom["launches"],
             "avg_launch_us": 1e3 * dom["ms"] / max(dom["launches"], 1),
-            "share_of_kernel_time": dom["ms"] / tot_ms, "peak_source": f"{pk_kind} (MEASURED_PEAKS.json)"
-            if pk_kind == "measured" else "fallback",
-            "classes": {s["name"]: {"ms": round(s["ms"], 3), "launches": s["launches"]} for s in stats}}
+            "share_of_kernel_time": dom["ms"] / tot_ms,
+            "peak_source": ("measured, MEASURED_PEAKS.json (sustained bf16 for a kernel inside a long step)"
+                            if pk_kind == "measured" else "fallback"),
+            "timing": "CUDA events around each launch of one instrumented step (direct launches)",
+            "classes": {s["name"]: {"ms": round(s["ms"], 3), "launches": s["launches"],
+                                    "gflop": round(s["flops"] / 1e9, 2)} for s in stats}}
 
-    # raster order, same model and masks, same GPU
+    # raster order, same model and masks, same GPU, same launch mechanism
     raster = None
     if rank == 0 and args.raster_frames > 0:
-        fdr = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_RASTER)
-        encr = ctx.seq_create(cfg.H, cfg.W)
-        bsr = torch.zeros(cap, dtype=torch.uint8, device=dev)
-        nr = encr.encode_params(fdr, ys[0], zs[0], bitstream=bsr)
-        decr = ctx.seq_create(cfg.H, cfg.W)
-        r_ms = []
-        for _ in range(args.raster_frames):
-            flush.fill_(3)
-            a = torch.cuda.Event(enable_timing=True); b_ = torch.cuda.Event(enable_timing=True)
-            decr.reset()
-            a.record(stream)
-            decr.decode_frame(fdr, bsr, nr, zs[0], outs[0])
-            b_.record(stream)
-            torch.cuda.synchronize()
-            r_ms.append(a.elapsed_time(b_))
-        if not torch.equal(outs[0], ys[0]):
-            raise RuntimeError("raster decode differs")
-        raster = {"value": 1e3 / float(np.mean(r_ms)), "unit": "frames/s", "ms_per_frame": float(np.mean(r_ms)),
-                  "steps_per_frame": cfg.H * cfg.W, "frames": args.raster_frames}
+        rbss, rlens = encode(fdr)
+        rdecs = [ctx.seq_create(cfg.H, cfg.W) for _ in range(B)]
+        raster = {}
+        sizes = [1] + ([B] if B > 1 and args.raster_batch else [])
+        for n in sizes:
+            batch_step(rdecs, fdr, rbss, rlens, n)          # captures the graph segments
+            r_ms = timed(lambda: batch_step(rdecs, fdr, rbss, rlens, n), args.raster_frames)
+            for b in range(n):
+                if not torch.equal(outs[b], ys[b]):
+                    raise RuntimeError("raster decode differs")
+            raster[f"frames_per_step_{n}"] = {"value": n * 1e3 / float(np.mean(r_ms)), "unit": "frames/s",
+                                              "ms_per_step": float(np.mean(r_ms)), "steps_per_frame": cfg.H * cfg.W}
+    speedup = None
+    if raster:
+        speedup = {}
+        if lat is not None or B == 1:
+            w1 = lat["frames_per_s"] if lat else value / world
+            speedup["frames_per_step_1"] = w1 / raster["frames_per_step_1"]["value"]
+        if f"frames_per_step_{B}" in raster and B > 1:
+            speedup[f"frames_per_step_{B}"] = (value / world) / raster[f"frames_per_step_{B}"]["value"]
 
-    # rate of the decoded frame: GPU parameters vs the FP64 oracle (crop rows)
-    rate = {"bits_per_symbol": ctx.rate(ys[0], mus[0], sgs[0]) / ys[0].numel(),
+    # rate: GPU parameters vs the FP64 oracle on the sample rows
+    rate = {"bits_per_symbol": ctx.rate(ys[0], mu0, sg0) / ys[0].numel(),
             "container_bits_per_symbol": 8.0 * lens[0] / ys[0].numel()}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -358,7 +385,7 @@ def run_ours(args, rank: int, world: int, local: int):
         cpu = {"value": frac / secs, "unit": "frames/s", "cores": smp.threads, "kind": "oracle",
                "sample": smp.describe(secs)}
         R = args.cpu_rows
-        r_gpu = smp.O.rate_bits(smp.y[0], mus[0][:R].double().cpu().numpy(), sgs[0][:R].double().cpu().numpy())
+        r_gpu = smp.O.rate_bits(smp.y[0], mu0[:R].double().cpu().numpy(), sg0[:R].double().cpu().numpy())
         r_64 = smp.O.rate_bits(smp.y[0], smp.mu, smp.sg)
         rate["delta_vs_fp64_on_sample"] = abs(r_gpu - r_64) / r_64
 
@@ -367,12 +394,14 @@ def run_ours(args, rank: int, world: int, local: int):
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "frames_per_step": B, "l2": "flushed between steps (256 MiB write)",
+            "config": {"workload": WORKLOAD, "frames_per_step": B,
+                       "l2": "flushed between steps (256 MiB write)",
+                       "launch": "CUDA graph per batch shape (segments of 512 wavefront steps)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(round(launches)),
-            "roofline": roof, "raster": raster,
-            "speedup_vs_raster": (value / world / raster["value"]) if raster else None,
+            "latency_one_frame": lat,
+            "roofline": roof, "raster": raster, "speedup_vs_raster": speedup,
             "rate": rate, "clocks": clk, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
     return 0

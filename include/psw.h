@@ -136,8 +136,8 @@ void psw_seq_destroy(psw_seq *seq);
 /* Upper bound on the container size of one frame (bytes). */
 size_t psw_bitstream_capacity(const psw_ctx *ctx, const psw_frame_desc *fd);
 
-/* Encoder (Sec. 3.1: "masked to restrict attention strictly to past
- * positions"; Sec. 3.2): one masked parallel pass over every position of
+/* Encoder (Sec. 3.1: the accumulator's keys are limited to positions
+ * decoded earlier; Sec. 3.2): one masked parallel pass over every position of
  * the frame gives (mu, sigma); sigma -> scale index, mu -> rounded mean;
  * symbols y - round(mu) are rANS-coded per channel in the schedule's order.
  *   yhat_dev  [H][W][C] int16 latents of this frame
@@ -169,14 +169,20 @@ psw_status psw_decode_frame(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd
                             const uint8_t *bitstream_dev, size_t len, const int16_t *zhat_dev,
                             int16_t *yhat_out_dev, float *mu_dev, float *sigma_dev, void *stream);
 
-/* Batched decode: n frames of n different sequences (any mix of grids up to
- * each sequence's maximum) decoded together; step t of every frame runs in
- * global step t.  Arrays have n entries.  Per-frame results are identical
- * to psw_decode_frame.  status_out (host, n entries, may be NULL) receives
- * each frame's status; the call returns the first failure. */
+/* Batched decode: n frames of n different sequences (any mix of grids and
+ * schedules up to each sequence's maximum, 1 <= n <= 128) decoded together:
+ * step t of every frame runs in global step t, so each launch carries the
+ * positions of all frames (Sec. 3.2 parallelism across frames as well as
+ * along a wavefront).  Arrays have n entries; mu_dev / sigma_dev may be NULL
+ * or hold NULL entries.  Every frame's results are bit-identical to decoding
+ * it alone with psw_decode_frame.  status_out (host, n entries, may be NULL)
+ * receives each frame's status; the call returns the first failure.  The
+ * first call for a given set of sequences and grids records the launches in
+ * a CUDA graph that later calls replay. */
 psw_status psw_decode_batch(psw_ctx *ctx, int n, psw_seq *const *seqs, const psw_frame_desc *fds,
                             const uint8_t *const *bitstreams_dev, const size_t *lens,
                             const int16_t *const *zhat_dev, int16_t *const *yhat_out_dev,
+                            float *const *mu_dev, float *const *sigma_dev,
                             int *status_out, void *stream);
 
 /* Model rate of a frame (Fig. 1 rate term): bits = -sum log2 P(y) with

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI (include/psw.h): context and sequence lifetime, the
-// encoder's masked parallel pass, the wavefront / raster decoder and the
+// encoder's masked parallel pass, the batched wavefront / raster decoder
+// (captured once per batch shape into a CUDA graph and replayed) and the
 // coder entry points.  Host code only enqueues kernels; every step of the
 // model runs on the GPU.
 #include "internal.h"
@@ -11,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -101,7 +103,7 @@ bool desc_valid(const psw_model_desc *m, std::string &why)
     if (m->L < 1 || m->L > 64) { why = "L must be in [1, 64]"; return false; }
     if (m->k < 1 || m->k % 2 == 0 || m->k * m->k > MAX_KK) { why = "k must be odd with k*k <= 81"; return false; }
     if (m->mask != 0 && m->mask != 1) { why = "mask must be 0 or 1"; return false; }
-    if (m->temporal) {
+    if (m->temporal == 1) {
         if (m->Lc < 1 || m->Lc > 64) { why = "Lc must be in [1, 64]"; return false; }
         if (m->Tf < 1 || m->Tf > MAX_TF || m->Tf * m->k * m->k > 256) { why = "need Tf <= 4 and Tf*k*k <= 256"; return false; }
     } else if (m->temporal != 0) {
@@ -117,6 +119,26 @@ struct BlockDev {                      // transposed projections, compute type
 
 size_t esize(int prec) { return prec == P_BF16 ? 2 : 4; }
 
+// One captured decode: graph segments of at most SEG_STEPS global steps,
+// their token lists and launch count.
+constexpr int SEG_STEPS = 512;
+struct GraphRec {
+    std::vector<cudaGraphExec_t> exec;
+    int *d_tok = nullptr;
+    int2 *d_kn = nullptr;
+    long launches = 0;
+};
+
+void graph_free(GraphRec &g)
+{
+    for (cudaGraphExec_t e : g.exec) cudaGraphExecDestroy(e);
+    g.exec.clear();
+    cudaFree(g.d_tok);
+    cudaFree(g.d_kn);
+    g.d_tok = nullptr;
+    g.d_kn = nullptr;
+}
+
 }  // namespace
 
 struct psw_ctx {
@@ -128,12 +150,30 @@ struct psw_ctx {
     char *wmat = nullptr;              // arena of transposed projections
     std::vector<BlockDev> ctxb, sm1, sm2;
     BlockDev acc;                      // Wqkv = [Wq]; Wxkv = [Wk; Wv]
+    void *Win = nullptr;               // latent embedding [d][C]
+    void *Wh1 = nullptr;               // heads, first layers [W1m; W1s]: [2d][d]
+    void *Wh2 = nullptr;               // heads, second layers interleaved: row 2c = mu_c, 2c+1 = sigma_c: [2C][2d]
+    float *bh1 = nullptr;              // [b1m; b1s]
     CdfTables tabs{};
     uint32_t *d_cdf = nullptr;
     int *d_meta = nullptr;
     float *d_scale = nullptr;
     double *rate_buf = nullptr, *h_rate = nullptr;
     size_t rate_cap = 0;
+    // shared per-launch workspace (compact token rows) and the slot table
+    void *Xn = nullptr, *Q = nullptr, *O = nullptr, *Hid = nullptr;
+    float *Xa = nullptr, *Xb = nullptr, *Xg = nullptr;   // FP32 residual rows: SM1 / accumulator+SM2 / context
+    size_t ws_rows = 0, ws_bytes = 0;
+    int ws_gen = 0;
+    Slot *d_slots = nullptr, *h_slots = nullptr;
+    int *d_status = nullptr;           // timeouts of bounded device waits
+    int *h_status = nullptr;           // pinned: [MAX_SLOTS + 1]
+    int *d_tok = nullptr;              // direct-launch token lists
+    int2 *d_kn = nullptr;
+    size_t tok_cap = 0, kn_cap = 0;
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::vector<long>, GraphRec> graphs;
+    bool use_graphs = true;
     std::string err;
     std::vector<psw_seq *> seqs;
     // instrumentation
@@ -150,10 +190,9 @@ struct psw_seq {
     int maxH = 0, maxW = 0, maxHW = 0;
     size_t bytes = 0;
     std::vector<void *> allocs;
-    float *eh = nullptr, *x1 = nullptr, *x2 = nullptr, *g = nullptr;   // FP32 streams [HW][d]
+    float *eh = nullptr;                                 // hyperprior tokens, FP32 [HW][d]
     void *qa = nullptr;                                  // accumulator queries [HW][d]
     void *K1 = nullptr, *V1 = nullptr, *K2 = nullptr, *V2 = nullptr, *Ka = nullptr, *Va = nullptr;
-    void *Xn = nullptr, *Q = nullptr, *O = nullptr, *Hid = nullptr;    // compact token buffers
     void *CK = nullptr, *CV = nullptr, *XK = nullptr, *XV = nullptr;   // temporal rings
     float *mu = nullptr, *sigma = nullptr;
     uint8_t *idx = nullptr;
@@ -163,11 +202,10 @@ struct psw_seq {
     uint32_t *rstate = nullptr, *rptr = nullptr, *rend = nullptr, *enc_nw = nullptr;
     uint16_t *enc_scratch = nullptr;
     uint64_t *enc_total = nullptr, *h_total = nullptr;
-    int *d_status = nullptr, *h_status = nullptr;
-    int *d_ident = nullptr, *d_order = nullptr;
+    int *d_status = nullptr;
+    int *d_order = nullptr;
     int sH = -1, sW = -1, sKind = -1, T = 0;
     std::vector<int> h_order, h_start;
-    bool launch_failed = false;
 };
 
 namespace {
@@ -190,6 +228,8 @@ psw_status fail(psw_ctx *ctx, psw_status st, const char *fmt, ...)
     } while (0)
 
 const float *W(const psw_ctx *c, long off) { return c->w + off; }
+
+// ---------------------------------------------------------------- instrumentation
 
 // Kernel classes reported by psw_profile_end.
 enum KClass { K_GEMM_TC, K_GEMM_SIMT, K_ATTN, K_NORM, K_EMBED, K_HEADS, K_RANS, K_OTHER, K_NCLASS };
@@ -227,6 +267,14 @@ struct Scope {
         }
     }
 };
+
+#define LAUNCH(P_, cls, flops, bytes, call)                 \
+    do {                                                    \
+        Scope sc_((P_).c, (P_).s, (cls), (flops), (bytes)); \
+        call;                                               \
+    } while (0)
+
+// ---------------------------------------------------------------- weights
 
 // Transposed ([out][in], K-major), compute-typed copies of every block
 // projection, carved from one arena.  A dry run only sums the sizes.
@@ -272,16 +320,42 @@ bool prepare_projections(psw_ctx *c, bool dry)
     ab.Wg = carve(m.F, d); tr(lay.acc_Wg, d, m.F, ab.Wg, 0);
     ab.Wu = carve(m.F, d); tr(lay.acc_Wu, d, m.F, ab.Wu, 0);
     ab.Wd = carve(d, m.F); tr(lay.acc_Wd, m.F, d, ab.Wd, 0);
+    void *win = carve(d, m.C); tr(lay.W_in, m.C, d, win, 0);
+    void *wh1 = carve(2 * d, d); tr(lay.W1m, d, d, wh1, 0); tr(lay.W1s, d, d, wh1, d);
+    void *wh2 = carve(2 * (size_t)m.C, 2 * d);
+    float *bh1 = (float *)carve(2 * d, es == 2 ? 2 : 1);        // 2d floats
     if (dry) { c->arena = used; return true; }
     if (used > c->arena) return false;
+    // interleaved block-diagonal second layer, assembled in FP32 then converted
+    {
+        std::vector<float> w2m((size_t)d * m.C), w2s((size_t)d * m.C), buf((size_t)2 * m.C * 2 * d, 0.0f);
+        cudaMemcpy(w2m.data(), c->w + lay.W2m, w2m.size() * 4, cudaMemcpyDeviceToHost);
+        cudaMemcpy(w2s.data(), c->w + lay.W2s, w2s.size() * 4, cudaMemcpyDeviceToHost);
+        for (int ch = 0; ch < m.C; ch++)
+            for (int e = 0; e < d; e++) {
+                buf[(size_t)(2 * ch) * 2 * d + e] = w2m[(size_t)e * m.C + ch];
+                buf[(size_t)(2 * ch + 1) * 2 * d + d + e] = w2s[(size_t)e * m.C + ch];
+            }
+        float *tmp = nullptr;
+        if (cudaMalloc(&tmp, buf.size() * 4) != cudaSuccess) return false;
+        cudaMemcpy(tmp, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice);
+        launch_convert(prec, tmp, buf.size(), wh2, 0);
+        cudaDeviceSynchronize();
+        cudaFree(tmp);
+        cudaMemcpy(bh1, c->w + lay.b1m, d * 4, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(bh1 + d, c->w + lay.b1s, d * 4, cudaMemcpyDeviceToDevice);
+    }
     c->ctxb = ctxb; c->sm1 = sm1; c->sm2 = sm2; c->acc = ab;
+    c->Win = win; c->Wh1 = wh1; c->Wh2 = wh2; c->bh1 = bh1;
     return true;
 }
 
-// Schedules: PSW_SCHED_WAVEFRONT = positions grouped by mask label in
-// ascending label order (raster order inside a step), PSW_SCHED_RASTER =
-// one position per step.  order: positions in schedule order; step t is
-// order[start[t] .. start[t+1]).
+// ---------------------------------------------------------------- schedules
+
+// PSW_SCHED_WAVEFRONT: positions grouped by mask label in ascending label
+// order (raster order inside a step); PSW_SCHED_RASTER: one position per
+// step.  order: positions in schedule order; step t is order[start[t] ..
+// start[t+1]).
 void build_schedule(const psw_model_desc &m, int H, int W_, int kind, std::vector<int> &order,
                     std::vector<int> &start)
 {
@@ -321,227 +395,276 @@ psw_status seq_schedule(psw_seq *q, int H, int W_, int kind)
     return PSW_OK;
 }
 
+// The slot of a sequence's current frame (pointers to its caches).
+Slot make_slot(const psw_seq *q, int H, int W_, int sched)
+{
+    const psw_model_desc &m = q->ctx->md;
+    Slot s;
+    memset(&s, 0, sizeof(s));
+    s.H = H; s.W = W_; s.stride = q->maxHW; s.frame = q->frame; s.sched = sched;
+    s.nfr = 1;
+    if (m.temporal) {
+        int f = q->frame, f0 = std::max(0, f - m.Tf + 1);
+        s.nfr = f - f0 + 1;
+        for (int u = 0; u < s.nfr; u++) s.ring[u] = (f0 + u) % m.Tf;
+    }
+    s.eh = q->eh;
+    s.qa = q->qa; s.K1 = q->K1; s.V1 = q->V1; s.K2 = q->K2; s.V2 = q->V2; s.Ka = q->Ka; s.Va = q->Va;
+    s.CK = q->CK; s.CV = q->CV; s.XK = q->XK; s.XV = q->XV;
+    s.mu = q->mu; s.sigma = q->sigma; s.idx = q->idx; s.m = q->m; s.y = q->y;
+    s.yprev = q->yprev;
+    s.rstate = q->rstate; s.rptr = q->rptr; s.rend = q->rend;
+    s.order = q->d_order;
+    s.status = q->d_status;
+    return s;
+}
+
+// ---------------------------------------------------------------- workspace
+
+psw_status ensure_workspace(psw_ctx *c, size_t rows)
+{
+    if (rows <= c->ws_rows) return PSW_OK;
+    const psw_model_desc &m = c->md;
+    size_t es = esize(c->prec);
+    CK_CUDA(c, cudaDeviceSynchronize());
+    cudaFree(c->Xn); cudaFree(c->Q); cudaFree(c->O); cudaFree(c->Hid);
+    cudaFree(c->Xa); cudaFree(c->Xb); cudaFree(c->Xg);
+    c->Xn = c->Q = c->O = c->Hid = nullptr;
+    c->Xa = c->Xb = c->Xg = nullptr;
+    c->bytes -= c->ws_bytes;
+    c->ws_rows = 0; c->ws_bytes = 0;
+    size_t bd = rows * std::max(m.d, m.C) * es, bf = rows * std::max(m.F, 2 * m.d) * es, bx = rows * m.d * 4;
+    size_t bg = m.temporal ? bx : 16;
+    if (cudaMalloc(&c->Xn, bd) != cudaSuccess || cudaMalloc(&c->Q, bd) != cudaSuccess ||
+        cudaMalloc(&c->O, bd) != cudaSuccess || cudaMalloc(&c->Hid, bf) != cudaSuccess ||
+        cudaMalloc(&c->Xa, bx) != cudaSuccess || cudaMalloc(&c->Xb, bx) != cudaSuccess ||
+        cudaMalloc(&c->Xg, bg) != cudaSuccess)
+        return fail(c, PSW_ERR_OOM, "workspace of %zu rows", rows);
+    c->ws_rows = rows;
+    c->ws_bytes = 3 * bd + bf + 2 * bx + bg;
+    c->bytes += c->ws_bytes;
+    c->ws_gen++;
+    for (auto &kv : c->graphs) graph_free(kv.second);
+    c->graphs.clear();
+    return PSW_OK;
+}
+
 // ---------------------------------------------------------------- model passes
 
 struct Pass {
     psw_ctx *c;
-    psw_seq *q;
     cudaStream_t s;
-    int H, W;
-    int HW() const { return H * W; }
+    const Slot *S;                     // device slot table
+    bool *failed;
 };
 
-size_t cache_stride(const Pass &P) { return (size_t)P.q->maxHW * P.c->md.d * esize(P.c->prec); }
-void *cache_at(void *base, const Pass &P, long i) { return (char *)base + i * cache_stride(P); }
-
-void gemm_call(const Pass &P, const void *A, int lda, const void *Wt, const void *Wt2, int M, int N, int K,
-               const Epi &e)
+// One projection; asrc / a_stream / a_gain say where its token operand
+// comes from (compact rows A, the RMSNorm of a residual stream, or the
+// channel-scaled latents).
+void gemm_any(const Pass &P, int asrc, const float *xrows, const float *a_gain, const void *A, int lda, const void *Wt,
+              const void *Wt2, int M, int N, int K, const Epi &e)
 {
-    GemmArgs g{};
-    g.A = A; g.lda = lda; g.Wt = Wt; g.Wt2 = Wt2; g.M = M; g.N = N; g.K = K; g.epi = e;
-    g.status = P.q->d_status;
     if (M <= 0) return;
-    bool tc = gemm_tc_supported(P.c->prec, N, K);
+    GemmArgs g{};
+    g.A = A; g.lda = lda; g.asrc = asrc; g.xrows = xrows; g.a_gain = a_gain; g.prep = P.c->Xn;
+    g.Wt = Wt; g.Wt2 = Wt2; g.M = M; g.N = N; g.K = K; g.epi = e;
+    g.epi.slots = P.S;
+    g.status = P.c->d_status;
+    bool tc = gemm_tc_supported(P.c->prec, N, K, asrc);
+    if (!tc && asrc != A_DIRECT) P.c->launches++;      // the operand-preparation kernel
     double es = P.c->prec == P_BF16 ? 2.0 : 4.0, nw = Wt2 ? 2.0 : 1.0;
     double out_b = (e.mode == EPI_RESID || e.mode == EPI_RESID_BASE) ? 8.0 : es;
     Scope sc(P.c, P.s, tc ? K_GEMM_TC : K_GEMM_SIMT, 2.0 * nw * M * N * K,
              nw * N * K * es + (double)M * K * es + (double)M * N * out_b);
-    if (!gemm(P.c->prec, g, P.s)) P.q->launch_failed = true;
+    if (!gemm(P.c->prec, g, P.s)) *P.failed = true;
 }
 
-Epi epi_qkv(const int *pos, int d, int q_cols, void *out, void *kc, void *vc)
+void gemm_call(const Pass &P, const void *A, int lda, const void *Wt, const void *Wt2, int M, int N, int K,
+               const Epi &e)
+{
+    gemm_any(P, A_DIRECT, nullptr, nullptr, A, lda, Wt, Wt2, M, N, K, e);
+}
+
+// Projection of the RMSNorm (gain at gain_off) of the FP32 rows X [M][K].
+void gemm_norm(const Pass &P, const float *X, long gain_off, const void *Wt, const void *Wt2, int M, int N, int K,
+               const Epi &e)
+{
+    gemm_any(P, A_NORM, X, W(P.c, gain_off), nullptr, 0, Wt, Wt2, M, N, K, e);
+}
+
+Epi epi_qkv(const int *tok, int d, int q_cols, void *out, int kc, int vc, int layer, int ring = 0, int Tf = 1)
 {
     Epi e{};
-    e.mode = EPI_QKV; e.pos = pos; e.d = d; e.q_cols = q_cols; e.out = out; e.ld_out = d; e.kc = kc; e.vc = vc;
+    e.mode = EPI_QKV; e.tok = tok; e.d = d; e.q_cols = q_cols; e.out = out; e.ld_out = d;
+    e.kc_sel = kc; e.vc_sel = vc; e.kv_layer = layer; e.ring = ring; e.Tf = Tf; e.st_sel = CS_NONE;
     return e;
 }
-Epi epi_resid(const int *pos, float *x, const float *base = nullptr)
+Epi epi_resid(const int *tok, float *rows, bool base = false)
 {
     Epi e{};
-    e.mode = base ? EPI_RESID_BASE : EPI_RESID; e.pos = pos; e.resid = x; e.base = base;
+    e.mode = base ? EPI_RESID_BASE : EPI_RESID; e.tok = tok; e.rows = rows; e.st_sel = CS_NONE;
     return e;
 }
-Epi epi_store(const int *pos, int scatter, void *out, int ld)
+Epi epi_store(const int *tok, void *out, int ld, int cache = CS_NONE, int layer = 0, int d = 0)
 {
     Epi e{};
-    e.mode = EPI_STORE; e.pos = pos; e.scatter = scatter; e.out = out; e.ld_out = ld;
+    e.mode = EPI_STORE; e.tok = tok; e.out = out; e.ld_out = ld; e.st_sel = cache; e.st_layer = layer; e.d = d;
     return e;
 }
 Epi epi_swiglu(void *out, int ld)
 {
     Epi e{};
-    e.mode = EPI_SWIGLU; e.out = out; e.ld_out = ld;
+    e.mode = EPI_SWIGLU; e.out = out; e.ld_out = ld; e.st_sel = CS_NONE;
+    return e;
+}
+Epi epi_bias_silu(const int *tok, void *out, int ld, const float *bias)
+{
+    Epi e{};
+    e.mode = EPI_BIAS_SILU; e.tok = tok; e.out = out; e.ld_out = ld; e.bias = bias; e.st_sel = CS_NONE;
+    return e;
+}
+Epi epi_set_bias(const int *tok, float *rows, const float *bias)
+{
+    Epi e{};
+    e.mode = EPI_SET_BIAS; e.tok = tok; e.rows = rows; e.bias = bias; e.st_sel = CS_NONE;
     return e;
 }
 
-#define LAUNCH(P_, cls, flops, bytes, call)                 \
-    do {                                                    \
-        Scope sc_((P_).c, (P_).s, (cls), (flops), (bytes)); \
-        call;                                               \
-    } while (0)
-
 double attn_flops(const psw_model_desc &m, int n, double nkeys) { return 4.0 * n * nkeys * m.d; }
 // mean visible keys: about half the window under the causal masks, all of it unmasked
-double attn_keys(const AttnArgs &a) { return a.kind < 0 ? (double)a.nfr * a.k * a.k : 0.5 * a.k * a.k; }
+double attn_keys(const AttnArgs &a, int Tf)
+{
+    return a.kind < 0 ? (double)(a.temporal ? Tf : 1) * a.k * a.k : 0.5 * a.k * a.k;
+}
 double attn_bytes(const psw_model_desc &m, const AttnArgs &a)
 {
-    double es = 2.0;   // bf16 K/V rows; FP32 runs report the same algorithmic count
-    return a.n * (double)m.d * es * (2.0 * attn_keys(a) + 2.0);
+    return a.n * (double)m.d * 2.0 * (2.0 * attn_keys(a, m.Tf) + 2.0);
 }
 
-AttnArgs attn_args(const Pass &P, const int *pos, int n, const void *Qp, int q_full, const float *bias,
-                   int bias_h_stride, int kind)
+AttnArgs attn_args(const Pass &P, const int *tok, int n, const void *Qp, int q_sel, int ksel, int vsel, int layer,
+                   const float *bias, int bias_h_stride, int kind, int temporal)
 {
     AttnArgs a{};
     const psw_model_desc &m = P.c->md;
-    a.pos = pos; a.n = n; a.Q = Qp; a.q_full = q_full;
+    a.tok = tok; a.n = n; a.slots = P.S; a.Q = Qp; a.q_sel = q_sel;
+    a.k_sel = ksel; a.v_sel = vsel; a.layer = layer; a.temporal = temporal; a.Tf = m.Tf;
     a.bias = bias; a.bias_h_stride = bias_h_stride;
-    a.O = P.q->O; a.H = P.H; a.W = P.W; a.d = m.d; a.nh = m.nh; a.k = m.k; a.mask = m.mask; a.kind = kind;
+    a.O = P.c->O; a.d = m.d; a.nh = m.nh; a.k = m.k; a.mask = m.mask; a.kind = kind;
     return a;
 }
 
+void attention(const Pass &P, const AttnArgs &a)
+{
+    const psw_model_desc &m = P.c->md;
+    LAUNCH(P, K_ATTN, attn_flops(m, a.n, attn_keys(a, m.Tf)), attn_bytes(m, a), launch_attention(P.c->prec, a, P.s));
+}
+
 // SwiGLU feed-forward with pre-norm and residual (Sec. 3.1).
-void ffn(const Pass &P, const BlockDev &bd, long g_ffn, float *x, const int *pos, int n)
+void ffn(const Pass &P, const BlockDev &bd, long g_ffn, float *X, const int *tok, int n)
 {
     psw_ctx *c = P.c;
-    psw_seq *q = P.q;
     const psw_model_desc &m = c->md;
-    LAUNCH(P, K_NORM, 3.0 * n * m.d, n * m.d * 6.0, launch_rmsnorm(c->prec, pos, n, x, W(c, g_ffn), m.d, q->Xn, 0, P.s));
-    gemm_call(P, q->Xn, m.d, bd.Wg, bd.Wu, n, m.F, m.d, epi_swiglu(q->Hid, m.F));
-    gemm_call(P, q->Hid, m.F, bd.Wd, nullptr, n, m.d, m.F, epi_resid(pos, x));
+    Epi sw = epi_swiglu(c->Hid, m.F);
+    sw.tok = tok;
+    gemm_norm(P, X, g_ffn, bd.Wg, bd.Wu, n, m.F, m.d, sw);
+    gemm_call(P, c->Hid, m.F, bd.Wd, nullptr, n, m.d, m.F, epi_resid(tok, X));
 }
 
 // One spatial block (Sec. 3.1: RMSNorm pre-norm, window self-attention over
 // S(p), temporal cross-attention for the temporal model, SwiGLU) on the
-// positions pos[0..n).  x: residual stream [HW][d].  Kc/Vc: this block's
-// window caches.  bidx: the block's index in the temporal K/V ring (SM1
-// blocks 0..L-1, SM2 blocks L..2L-1).
-void spatial_block(const Pass &P, const BlockOff &bo, const BlockDev &bd, int bidx, float *x, void *Kc,
-                   void *Vc, const int *pos, int n)
+// tokens tok[0..n).  X: their FP32 residual rows; kc/vc: this module's
+// caches at layer l; bidx: the block's index in the temporal K/V ring
+// (Spatial Module 1 blocks 0..L-1, Spatial Module 2 blocks L..2L-1).
+void spatial_block(const Pass &P, const BlockOff &bo, const BlockDev &bd, int bidx, float *X, int kc, int vc,
+                   int l, const int *tok, int n)
 {
     psw_ctx *c = P.c;
-    psw_seq *q = P.q;
     const psw_model_desc &m = c->md;
     int d = m.d, kk = m.k * m.k;
-    LAUNCH(P, K_NORM, 3.0 * n * d, n * d * 6.0, launch_rmsnorm(c->prec, pos, n, x, W(c, bo.g_attn), d, q->Xn, 0, P.s));
-    gemm_call(P, q->Xn, d, bd.Wqkv, nullptr, n, 3 * d, d, epi_qkv(pos, d, d, q->Q, Kc, Vc));
-    AttnArgs a = attn_args(P, pos, n, q->Q, 0, W(c, bo.bias), kk, 1);
-    a.K[0] = Kc; a.V[0] = Vc; a.nfr = 1; a.age[0] = 0;
-    LAUNCH(P, K_ATTN, attn_flops(m, a.n, attn_keys(a)), attn_bytes(m, a), launch_attention(c->prec, a, P.s));
-    gemm_call(P, q->O, d, bd.Wo, nullptr, n, d, d, epi_resid(pos, x));
+    gemm_norm(P, X, bo.g_attn, bd.Wqkv, nullptr, n, 3 * d, d, epi_qkv(tok, d, d, c->Q, kc, vc, l));
+    attention(P, attn_args(P, tok, n, c->Q, CS_NONE, kc, vc, l, W(c, bo.bias), kk, 1, 0));
+    gemm_call(P, c->O, d, bd.Wo, nullptr, n, d, d, epi_resid(tok, X));
     if (m.temporal) {
-        LAUNCH(P, K_NORM, 3.0 * n * d, n * d * 6.0, launch_rmsnorm(c->prec, pos, n, x, W(c, bo.g_x), d, q->Xn, 0, P.s));
-        gemm_call(P, q->Xn, d, bd.Wxq, nullptr, n, d, d, epi_store(pos, 0, q->Q, d));
-        AttnArgs xa = attn_args(P, pos, n, q->Q, 0, W(c, bo.xbias), m.Tf * kk, -1);
-        int f = q->frame, f0 = std::max(0, f - m.Tf + 1);
-        xa.nfr = f - f0 + 1;
-        for (int ff = f0; ff <= f; ff++) {
-            int u = ff - f0;
-            xa.K[u] = cache_at(q->XK, P, (long)bidx * m.Tf + ff % m.Tf);
-            xa.V[u] = cache_at(q->XV, P, (long)bidx * m.Tf + ff % m.Tf);
-            xa.age[u] = f - ff;
-        }
-        LAUNCH(P, K_ATTN, attn_flops(m, xa.n, attn_keys(xa)), attn_bytes(m, xa), launch_attention(c->prec, xa, P.s));
-        gemm_call(P, q->O, d, bd.Wxo, nullptr, n, d, d, epi_resid(pos, x));
+        gemm_norm(P, X, bo.g_x, bd.Wxq, nullptr, n, d, d, epi_store(tok, c->Q, d));
+        attention(P, attn_args(P, tok, n, c->Q, CS_NONE, CS_XK, CS_XV, bidx, W(c, bo.xbias), m.Tf * kk, -1, 1));
+        gemm_call(P, c->O, d, bd.Wxo, nullptr, n, d, d, epi_resid(tok, X));
     }
-    ffn(P, bd, bo.g_ffn, x, pos, n);
+    ffn(P, bd, bo.g_ffn, X, tok, n);
 }
 
-// Per-frame preparation: hyperprior tokens and accumulator queries for
-// every position (they depend only on the hyperlatents, Sec. 3.1), and for
-// the temporal model the Context Transformer pass of this frame.
-void frame_prologue(const Pass &P, const int16_t *zhat, const int16_t *yprev)
+// Per-frame preparation for the tokens tok[0..n) (all positions of one
+// slot, in raster order; eh: that slot's hyperprior rows): hyperprior
+// tokens and accumulator queries (they depend only on the hyperlatents,
+// Sec. 3.1), and for the temporal model this frame's Context Transformer
+// pass and every spatial block's cross-attention K/V.
+void frame_prologue(const Pass &P, const int *tok, int n, const float *eh)
 {
     psw_ctx *c = P.c;
-    psw_seq *q = P.q;
     const psw_model_desc &m = c->md;
-    int d = m.d, HW = P.HW(), Wh = (P.W + m.r - 1) / m.r, kk = m.k * m.k;
-    LAUNCH(P, K_EMBED, 2.0 * HW * m.Ch * d, HW * (m.Ch * 2.0 + d * 4.0),
-           launch_embed_hyper(zhat, P.H, P.W, Wh, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp),
-                              W(c, c->lay.b_hp), d, q->eh, P.s));
-    LAUNCH(P, K_NORM, 3.0 * HW * d, HW * d * 6.0, launch_rmsnorm(c->prec, nullptr, HW, q->eh, W(c, c->lay.acc_g_q), d, q->Xn, 0, P.s));
-    gemm_call(P, q->Xn, d, c->acc.Wqkv, nullptr, HW, d, d, epi_store(nullptr, 0, q->qa, d));
+    int d = m.d, kk = m.k * m.k;
+    LAUNCH(P, K_EMBED, 2.0 * n * m.Ch * d, n * (m.Ch * 2.0 + d * 4.0),
+           launch_embed_hyper(P.S, tok, n, 0, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp), W(c, c->lay.b_hp),
+                              d, P.s));
+    gemm_norm(P, eh, c->lay.acc_g_q, c->acc.Wqkv, nullptr, n, d, d, epi_store(tok, nullptr, d, CS_QA, 0, d));
     if (!m.temporal) return;
     // Context Transformer (Sec. 3.1): temporally shifted latents (learned
     // padding vector for frame 0), time-causal window attention over the
-    // last Tf frames of each layer, final RMSNorm; then every spatial
-    // block's cross-attention K/V of this frame.
-    int f = q->frame, slot = f % m.Tf, f0 = std::max(0, f - m.Tf + 1);
-    if (f == 0) LAUNCH(P, K_EMBED, 0.0, HW * d * 4.0, launch_fill_rows(W(c, c->lay.pad), HW, d, q->g, P.s));
-    else LAUNCH(P, K_EMBED, 2.0 * HW * m.C * d, HW * (m.C * 2.0 + d * 4.0),
-                launch_embed_latent(nullptr, HW, yprev, m.C, W(c, c->lay.gamma_c), W(c, c->lay.W_c),
-                                    W(c, c->lay.b_c), d, q->g, P.s));
+    // frames of the ring at each layer, final RMSNorm.
+    LAUNCH(P, K_EMBED, 2.0 * n * m.C * d, n * (m.C * 2.0 + d * 4.0),
+           launch_embed_context(P.S, tok, n, m.C, W(c, c->lay.gamma_c), W(c, c->lay.W_c), W(c, c->lay.b_c),
+                                W(c, c->lay.pad), d, c->Xg, P.s));
     for (int l = 0; l < m.Lc; l++) {
         const BlockOff &bo = c->lay.ctx[l];
         const BlockDev &bd = c->ctxb[l];
-        LAUNCH(P, K_NORM, 3.0 * HW * d, HW * d * 6.0, launch_rmsnorm(c->prec, nullptr, HW, q->g, W(c, bo.g_attn), d, q->Xn, 0, P.s));
-        gemm_call(P, q->Xn, d, bd.Wqkv, nullptr, HW, 3 * d, d,
-                  epi_qkv(nullptr, d, d, q->Q, cache_at(q->CK, P, (long)l * m.Tf + slot),
-                          cache_at(q->CV, P, (long)l * m.Tf + slot)));
-        AttnArgs a = attn_args(P, nullptr, HW, q->Q, 0, W(c, bo.bias), m.Tf * kk, -1);
-        a.nfr = f - f0 + 1;
-        for (int ff = f0; ff <= f; ff++) {
-            int u = ff - f0;
-            a.K[u] = cache_at(q->CK, P, (long)l * m.Tf + ff % m.Tf);
-            a.V[u] = cache_at(q->CV, P, (long)l * m.Tf + ff % m.Tf);
-            a.age[u] = f - ff;
-        }
-        LAUNCH(P, K_ATTN, attn_flops(m, a.n, attn_keys(a)), attn_bytes(m, a), launch_attention(c->prec, a, P.s));
-        gemm_call(P, q->O, d, bd.Wo, nullptr, HW, d, d, epi_resid(nullptr, q->g));
-        ffn(P, bd, bo.g_ffn, q->g, nullptr, HW);
+        gemm_norm(P, c->Xg, bo.g_attn, bd.Wqkv, nullptr, n, 3 * d, d, epi_qkv(tok, d, d, c->Q, CS_CK, CS_CV, l, 1, m.Tf));
+        attention(P, attn_args(P, tok, n, c->Q, CS_NONE, CS_CK, CS_CV, l, W(c, bo.bias), m.Tf * kk, -1, 1));
+        gemm_call(P, c->O, d, bd.Wo, nullptr, n, d, d, epi_resid(tok, c->Xg));
+        ffn(P, bd, bo.g_ffn, c->Xg, tok, n);
     }
-    LAUNCH(P, K_NORM, 3.0 * HW * d, HW * d * 6.0, launch_rmsnorm(c->prec, nullptr, HW, q->g, W(c, c->lay.g_ctx), d, q->Xn, 0, P.s));
     for (int b = 0; b < 2 * m.L; b++) {
         const BlockDev &bd = b < m.L ? c->sm1[b] : c->sm2[b - m.L];
-        gemm_call(P, q->Xn, d, bd.Wxkv, nullptr, HW, 2 * d, d,
-                  epi_qkv(nullptr, d, 0, nullptr, cache_at(q->XK, P, (long)b * m.Tf + slot),
-                          cache_at(q->XV, P, (long)b * m.Tf + slot)));
+        gemm_norm(P, c->Xg, c->lay.g_ctx, bd.Wxkv, nullptr, n, 2 * d, d,
+                  epi_qkv(tok, d, 0, nullptr, CS_XK, CS_XV, b, 1, m.Tf));
     }
 }
 
-// Spatial Module 1 on positions whose latents are known, then the
-// accumulator keys/values from its normalised output (Sec. 3.1).
-void run_sm1(const Pass &P, const int16_t *y, const int *pos, int n)
+// Spatial Module 1 on tokens whose latents are known, then the accumulator
+// keys/values from its normalised output (Sec. 3.1).
+void run_sm1(const Pass &P, const int *tok, int n)
 {
     psw_ctx *c = P.c;
-    psw_seq *q = P.q;
     const psw_model_desc &m = c->md;
     int d = m.d;
     if (n <= 0) return;
-    LAUNCH(P, K_EMBED, 2.0 * n * m.C * d, n * (m.C * 2.0 + d * 4.0),
-           launch_embed_latent(pos, n, y, m.C, W(c, c->lay.gamma_in), W(c, c->lay.W_in), W(c, c->lay.b_in), d,
-                               q->x1, P.s));
-    for (int l = 0; l < m.L; l++)
-        spatial_block(P, c->lay.sm1[l], c->sm1[l], l, q->x1, cache_at(q->K1, P, l), cache_at(q->V1, P, l), pos, n);
-    LAUNCH(P, K_NORM, 3.0 * n * d, n * d * 6.0, launch_rmsnorm(c->prec, pos, n, q->x1, W(c, c->lay.acc_g_kv), d, q->Xn, 0, P.s));
-    gemm_call(P, q->Xn, d, c->acc.Wxkv, nullptr, n, 2 * d, d, epi_qkv(pos, d, 0, nullptr, q->Ka, q->Va));
+    gemm_any(P, A_EMBED, nullptr, W(c, c->lay.gamma_in), nullptr, 0, c->Win, nullptr, n, d, m.C,
+             epi_set_bias(tok, c->Xa, W(c, c->lay.b_in)));
+    for (int l = 0; l < m.L; l++) spatial_block(P, c->lay.sm1[l], c->sm1[l], l, c->Xa, CS_K1, CS_V1, l, tok, n);
+    gemm_norm(P, c->Xa, c->lay.acc_g_kv, c->acc.Wxkv, nullptr, n, 2 * d, d, epi_qkv(tok, d, 0, nullptr, CS_KA, CS_VA, 0));
 }
 
 // Accumulator (hyperprior query and residual, keys/values over A(p)),
-// Spatial Module 2 and heads on positions pos[0..n) (Sec. 3.1, Fig. 2b).
-void run_acc_sm2_heads(const Pass &P, const int *pos, int n)
+// Spatial Module 2 and heads on tokens tok[0..n) (Sec. 3.1, Fig. 2b).
+void run_acc_sm2_heads(const Pass &P, const int *tok, int n)
 {
     psw_ctx *c = P.c;
-    psw_seq *q = P.q;
     const psw_model_desc &m = c->md;
     int d = m.d;
     if (n <= 0) return;
-    AttnArgs a = attn_args(P, pos, n, q->qa, 1, W(c, c->lay.acc_bias), m.k * m.k, 0);
-    a.K[0] = q->Ka; a.V[0] = q->Va; a.nfr = 1; a.age[0] = 0;
-    LAUNCH(P, K_ATTN, attn_flops(m, a.n, attn_keys(a)), attn_bytes(m, a), launch_attention(c->prec, a, P.s));
-    gemm_call(P, q->O, d, c->acc.Wo, nullptr, n, d, d, epi_resid(pos, q->x2, q->eh));
-    ffn(P, c->acc, c->lay.acc_g_ffn, q->x2, pos, n);
+    attention(P, attn_args(P, tok, n, nullptr, CS_QA, CS_KA, CS_VA, 0, W(c, c->lay.acc_bias), m.k * m.k, 0, 0));
+    gemm_call(P, c->O, d, c->acc.Wo, nullptr, n, d, d, epi_resid(tok, c->Xb, true));
+    ffn(P, c->acc, c->lay.acc_g_ffn, c->Xb, tok, n);
     for (int l = 0; l < m.L; l++)
-        spatial_block(P, c->lay.sm2[l], c->sm2[l], m.L + l, q->x2, cache_at(q->K2, P, l), cache_at(q->V2, P, l), pos, n);
-    HeadsArgs h{};
-    h.pos = pos; h.n = n; h.x = q->x2; h.d = d; h.C = m.C;
-    h.g = W(c, c->lay.g_head); h.W1m = W(c, c->lay.W1m); h.b1m = W(c, c->lay.b1m); h.W2m = W(c, c->lay.W2m);
-    h.W1s = W(c, c->lay.W1s); h.b1s = W(c, c->lay.b1s); h.W2s = W(c, c->lay.W2s);
-    h.gamma_mu = W(c, c->lay.gamma_mu); h.beta_mu = W(c, c->lay.beta_mu);
-    h.gamma_sig = W(c, c->lay.gamma_sig); h.beta_sig = W(c, c->lay.beta_sig);
-    h.scale = c->d_scale; h.mu = q->mu; h.sigma = q->sigma; h.idx = q->idx; h.m = q->m;
-    LAUNCH(P, K_HEADS, 2.0 * n * (2.0 * d * d + 2.0 * d * m.C), n * (d * 4.0 + m.C * 13.0),
-           launch_heads(h, P.s));
+        spatial_block(P, c->lay.sm2[l], c->sm2[l], m.L + l, c->Xb, CS_K2, CS_V2, l, tok, n);
+    // prediction heads (Sec. 3.1): RMSNorm, both first layers as one
+    // projection with bias and SiLU, then both second layers as one
+    // interleaved projection whose epilogue applies the channel-wise output
+    // scaling, sigma's exp and clamp, and the quantisation
+    gemm_norm(P, c->Xb, c->lay.g_head, c->Wh1, nullptr, n, 2 * d, d, epi_bias_silu(tok, c->Hid, 2 * d, c->bh1));
+    Epi eh{};
+    eh.mode = EPI_HEADS; eh.tok = tok; eh.st_sel = CS_NONE; eh.C = m.C; eh.scale = c->d_scale;
+    eh.gmu = W(c, c->lay.gamma_mu); eh.bmu = W(c, c->lay.beta_mu);
+    eh.gsg = W(c, c->lay.gamma_sig); eh.bsg = W(c, c->lay.beta_sig);
+    gemm_call(P, c->Hid, 2 * d, c->Wh2, nullptr, n, 2 * m.C, 2 * d, eh);
 }
 
 CoderDev coder(const psw_ctx *c) { return CoderDev{c->d_cdf, c->d_meta}; }
@@ -559,50 +682,259 @@ psw_status check_frame(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd)
     return PSW_OK;
 }
 
-psw_status read_status(psw_ctx *c, psw_seq *q, cudaStream_t s, int *st_out)
-{
-    CK_CUDA(c, cudaMemcpyAsync(q->h_status, q->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK_CUDA(c, cudaStreamSynchronize(s));
-    *st_out = *q->h_status;
-    return PSW_OK;
-}
-
 size_t seq_bytes_for(const psw_model_desc &m, int prec, int H, int W_)
 {
     size_t HW = (size_t)H * W_, d = m.d, es = esize(prec);
     size_t b = 0;
-    b += 4 * HW * d * 4;                                            // eh, x1, x2, g
+    b += HW * d * 4;                                                // eh
     b += HW * d * es;                                               // qa
     b += (4 * (size_t)m.L + 2) * HW * d * es;                       // K1 V1 K2 V2 Ka Va
-    b += 3 * HW * d * es + HW * (size_t)m.F * es;                   // Xn Q O Hid
     if (m.temporal) b += 2 * ((size_t)m.Lc + 2 * (size_t)m.L) * m.Tf * HW * d * es;
     b += HW * m.C * (4 + 4 + 1 + 4 + 2 + 2);                        // mu sigma idx m y yprev
     b += (size_t)m.C * 32 * 4 + 2 * (size_t)m.C * 4 + (2 * (size_t)m.C + 1) * 4;
     b += (size_t)m.C * (3 * HW + 64) * 2;                           // encoder scratch
-    b += 2 * HW * 4 + 64;
+    b += HW * 4 + 64;
     return b;
 }
 
-// Encode the symbols y / idx / m ([HW][C], schedule order from the cached
-// schedule) into a container; *len = its size.
-psw_status encode_symbols(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, const int16_t *y, const uint8_t *idx,
-                          const int32_t *m, uint8_t *bs, size_t cap, size_t *len, cudaStream_t s)
+// Upload the slot table (n entries) and reset the status words.
+psw_status upload_slots(psw_ctx *c, const std::vector<psw_seq *> &qs, int n, cudaStream_t s)
+{
+    CK_CUDA(c, cudaMemcpyAsync(c->d_slots, c->h_slots, sizeof(Slot) * n, cudaMemcpyHostToDevice, s));
+    CK_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+    for (psw_seq *q : qs) CK_CUDA(c, cudaMemsetAsync(q->d_status, 0, sizeof(int), s));
+    return PSW_OK;
+}
+
+// Read the status words back (context word OR-ed into each sequence's).
+psw_status read_status(psw_ctx *c, const std::vector<psw_seq *> &qs, cudaStream_t s, std::vector<int> &out)
+{
+    CK_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    for (size_t b = 0; b < qs.size(); b++)
+        CK_CUDA(c, cudaMemcpyAsync(c->h_status + 1 + b, qs[b]->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK_CUDA(c, cudaStreamSynchronize(s));
+    out.assign(qs.size(), 0);
+    for (size_t b = 0; b < qs.size(); b++) out[b] = c->h_status[1 + b] | c->h_status[0];
+    return PSW_OK;
+}
+
+psw_status status_code(psw_ctx *c, int st)
+{
+    if (st & ST_CORRUPT) return fail(c, PSW_ERR_CORRUPT, "bitstream failed validation");
+    if (st & ST_TIMEOUT) return fail(c, PSW_ERR_TIMEOUT, "a bounded device wait timed out");
+    if (st & ST_CAPACITY) return fail(c, PSW_ERR_CAPACITY, "container larger than its buffer");
+    return PSW_OK;
+}
+
+psw_status grow_tokens(psw_ctx *c, size_t ntok, size_t nkn)
+{
+    if (ntok > c->tok_cap) {
+        CK_CUDA(c, cudaDeviceSynchronize());
+        cudaFree(c->d_tok);
+        c->d_tok = nullptr; c->tok_cap = 0;
+        CK_CUDA(c, cudaMalloc(&c->d_tok, ntok * sizeof(int)));
+        c->tok_cap = ntok;
+    }
+    if (nkn > c->kn_cap) {
+        CK_CUDA(c, cudaDeviceSynchronize());
+        cudaFree(c->d_kn);
+        c->d_kn = nullptr; c->kn_cap = 0;
+        CK_CUDA(c, cudaMalloc(&c->d_kn, nkn * sizeof(int2)));
+        c->kn_cap = nkn;
+    }
+    return PSW_OK;
+}
+
+// Token lists of a batched decode.  Layout of tok: for each slot its HW
+// prologue tokens, then for each global step t the tokens of step t of every
+// slot (slot-major); kn[t][b] = (first symbol, count) of slot b at step t.
+struct DecodePlan {
+    int n = 0, Tmax = 0;
+    std::vector<const float *> eh;      // each slot's hyperprior rows
+    std::vector<int> tok, pro_off, pro_n, step_off, step_n;
+    std::vector<int2> kn;
+    size_t max_step = 0;
+};
+
+DecodePlan plan_decode(const std::vector<psw_seq *> &qs, const psw_frame_desc *fds)
+{
+    DecodePlan D;
+    D.n = (int)qs.size();
+    for (int b = 0; b < D.n; b++) {
+        D.pro_off.push_back((int)D.tok.size());
+        D.eh.push_back(qs[b]->eh);
+        int HW = fds[b].H * fds[b].W;
+        D.pro_n.push_back(HW);
+        for (int p = 0; p < HW; p++) D.tok.push_back(tok_make(b, p));
+        D.Tmax = std::max(D.Tmax, qs[b]->T);
+    }
+    D.kn.assign((size_t)D.Tmax * D.n, make_int2(0, 0));
+    for (int t = 0; t < D.Tmax; t++) {
+        D.step_off.push_back((int)D.tok.size());
+        for (int b = 0; b < D.n; b++) {
+            const psw_seq *q = qs[b];
+            if (t >= q->T) continue;
+            int a0 = q->h_start[t], a1 = q->h_start[t + 1];
+            D.kn[(size_t)t * D.n + b] = make_int2(a0, a1 - a0);
+            for (int a = a0; a < a1; a++) D.tok.push_back(tok_make(b, q->h_order[a]));
+        }
+        D.step_n.push_back((int)D.tok.size() - D.step_off.back());
+        D.max_step = std::max(D.max_step, (size_t)D.step_n.back());
+    }
+    return D;
+}
+
+// Enqueue global steps [t0, t1) of a planned decode; the first segment also
+// runs the prologues and coder initialisation, the last the coder check.
+void enqueue_decode(psw_ctx *c, const DecodePlan &D, const int *d_tok, const int2 *d_kn, cudaStream_t s, bool *failed,
+                    int t0, int t1)
+{
+    Pass P{c, s, c->d_slots, failed};
+    if (t0 == 0) {
+        for (int b = 0; b < D.n; b++) frame_prologue(P, d_tok + D.pro_off[b], D.pro_n[b], D.eh[b]);
+        Scope sc(c, s, K_RANS, 0.0, (double)D.n * c->md.C * 128.0);
+        launch_rans_dec_init(c->d_slots, D.n, c->md.C, s);
+    }
+    for (int t = t0; t < t1; t++) {
+        if (t > 0) run_sm1(P, d_tok + D.step_off[t - 1], D.step_n[t - 1]);
+        run_acc_sm2_heads(P, d_tok + D.step_off[t], D.step_n[t]);
+        Scope sc(c, s, K_RANS, 0.0, (double)D.step_n[t] * c->md.C * 9.0);
+        launch_rans_dec_step(coder(c), c->d_slots, D.n, d_kn + (size_t)t * D.n, c->md.C, s);
+    }
+    if (t1 == D.Tmax) {
+        Scope sc(c, s, K_RANS, 0.0, (double)D.n * c->md.C * 128.0);
+        launch_rans_dec_finish(c->d_slots, D.n, c->md.C, s);
+    }
+}
+
+// Decode n frames of n sequences together (the engine behind
+// psw_decode_frame and psw_decode_batch).
+psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_desc *fds,
+                      const uint8_t *const *bs, const size_t *lens, const int16_t *const *zhat,
+                      int16_t *const *yout, float *const *mu_out, float *const *sg_out, int *status_out,
+                      cudaStream_t s)
+{
+    if (n < 1 || n > MAX_SLOTS) return fail(c, PSW_ERR_INVALID, "batch of %d frames (1..%d)", n, MAX_SLOTS);
+    std::vector<psw_seq *> qs(seqs, seqs + n);
+    for (int b = 0; b < n; b++) {
+        psw_status st = check_frame(c, qs[b], &fds[b]);
+        if (st) return st;
+        for (int a = 0; a < b; a++)
+            if (qs[a] == qs[b]) return fail(c, PSW_ERR_INVALID, "a sequence appears twice in one batch");
+        if (!bs[b] || !zhat[b] || !yout[b]) return fail(c, PSW_ERR_INVALID, "null pointer for frame %d", b);
+        if ((uintptr_t)bs[b] & 3) return fail(c, PSW_ERR_INVALID, "bitstream %d must be 4-byte aligned", b);
+        if ((st = seq_schedule(qs[b], fds[b].H, fds[b].W, fds[b].schedule))) return st;
+    }
+    for (int b = 0; b < n; b++) {
+        Slot sl = make_slot(qs[b], fds[b].H, fds[b].W, fds[b].schedule);
+        sl.bs = bs[b]; sl.len = lens[b]; sl.zhat = zhat[b];
+        c->h_slots[b] = sl;
+    }
+    // graph key: the workspace generation and the batch shape
+    std::vector<long> key{0, (long)n};
+    for (int b = 0; b < n; b++) {
+        key.push_back((long)(uintptr_t)qs[b]);
+        key.push_back(((long)fds[b].H << 32) | ((long)fds[b].W << 2) | fds[b].schedule);
+    }
+    bool failed = false;
+    bool graph = c->use_graphs && !c->prof;
+    GraphRec *gr = nullptr;
+    key[0] = c->ws_gen;
+    if (graph) {
+        auto it = c->graphs.find(key);
+        if (it != c->graphs.end()) gr = &it->second;
+    }
+    DecodePlan D;
+    psw_status st;
+    if (!gr) {
+        D = plan_decode(qs, fds);
+        size_t rows = D.max_step;
+        for (int b = 0; b < n; b++) rows = std::max(rows, (size_t)D.pro_n[b]);
+        if ((st = ensure_workspace(c, rows))) return st;
+        key[0] = c->ws_gen;
+    }
+    if ((st = upload_slots(c, qs, n, s))) return st;
+    if (graph) {
+        if (!gr) {
+            GraphRec g;
+            CK_CUDA(c, cudaMalloc(&g.d_tok, D.tok.size() * sizeof(int)));
+            CK_CUDA(c, cudaMalloc(&g.d_kn, std::max<size_t>(D.kn.size(), 1) * sizeof(int2)));
+            CK_CUDA(c, cudaMemcpy(g.d_tok, D.tok.data(), D.tok.size() * sizeof(int), cudaMemcpyHostToDevice));
+            if (!D.kn.empty())
+                CK_CUDA(c, cudaMemcpy(g.d_kn, D.kn.data(), D.kn.size() * sizeof(int2), cudaMemcpyHostToDevice));
+            long l0 = c->launches;
+            for (int t0 = 0; t0 < std::max(D.Tmax, 1); t0 += SEG_STEPS) {
+                int t1 = std::min(D.Tmax, t0 + SEG_STEPS);
+                cudaGraph_t gph;
+                cudaGraphExec_t ex = nullptr;
+                cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    enqueue_decode(c, D, g.d_tok, g.d_kn, c->cap_stream, &failed, t0, t1);
+                    e = cudaStreamEndCapture(c->cap_stream, &gph);
+                }
+                if (e == cudaSuccess && !failed) {
+                    e = cudaGraphInstantiate(&ex, gph, 0);
+                    cudaGraphDestroy(gph);
+                }
+                if (e != cudaSuccess || failed) {
+                    c->launches = l0;
+                    graph_free(g);
+                    return fail(c, PSW_ERR_CUDA, "decode capture: %s",
+                                failed ? "GEMM setup failed" : cudaGetErrorString(e));
+                }
+                g.exec.push_back(ex);
+            }
+            g.launches = c->launches - l0;
+            c->launches = l0;
+            gr = &(c->graphs[key] = g);
+        }
+        for (cudaGraphExec_t ex : gr->exec) CK_CUDA(c, cudaGraphLaunch(ex, s));
+        c->launches += gr->launches;
+    } else {
+        if ((st = grow_tokens(c, D.tok.size(), std::max<size_t>(D.kn.size(), 1)))) return st;
+        CK_CUDA(c, cudaMemcpyAsync(c->d_tok, D.tok.data(), D.tok.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+        if (!D.kn.empty())
+            CK_CUDA(c, cudaMemcpyAsync(c->d_kn, D.kn.data(), D.kn.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        enqueue_decode(c, D, c->d_tok, c->d_kn, s, &failed, 0, D.Tmax);
+        CK_CUDA(c, cudaStreamSynchronize(s));   // host token lists are reused by the next call
+        if (failed) return fail(c, PSW_ERR_CUDA, "a GEMM launch could not be prepared");
+    }
+    CK_CUDA(c, cudaGetLastError());
+    for (int b = 0; b < n; b++) {
+        psw_seq *q = qs[b];
+        size_t nsym = (size_t)fds[b].H * fds[b].W * c->md.C;
+        CK_CUDA(c, cudaMemcpyAsync(yout[b], q->y, nsym * 2, cudaMemcpyDeviceToDevice, s));
+        if (mu_out && mu_out[b]) CK_CUDA(c, cudaMemcpyAsync(mu_out[b], q->mu, nsym * 4, cudaMemcpyDeviceToDevice, s));
+        if (sg_out && sg_out[b]) CK_CUDA(c, cudaMemcpyAsync(sg_out[b], q->sigma, nsym * 4, cudaMemcpyDeviceToDevice, s));
+        CK_CUDA(c, cudaMemcpyAsync(q->yprev, q->y, nsym * 2, cudaMemcpyDeviceToDevice, s));
+    }
+    std::vector<int> sts;
+    if ((st = read_status(c, qs, s, sts))) return st;
+    psw_status first = PSW_OK;
+    for (int b = 0; b < n; b++) {
+        qs[b]->frame++;
+        psw_status sb = status_code(c, sts[b]);
+        if (status_out) status_out[b] = sb;
+        if (sb && !first) first = sb;
+    }
+    return first;
+}
+
+// Encode the symbols of slot 0 (already in the slot table) into a container.
+void encode_symbols(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, uint8_t *bs, size_t cap, cudaStream_t s)
 {
     int HW = fd->H * fd->W, C = c->md.C;
     int cap_words = 3 * HW + 64;
     {
         Scope sc(c, s, K_RANS, 0.0, (double)HW * C * 7.0);
-        launch_rans_encode(coder(c), q->d_order, HW, C, y, idx, m, q->enc_scratch, cap_words, q->enc_nw, q->rstate, s);
+        launch_rans_encode(coder(c), c->d_slots, 0, HW, C, q->enc_scratch, cap_words, q->enc_nw, q->rstate, s);
     }
-    Scope sc2(c, s, K_RANS, 0.0, (double)HW * C * 2.0);
-    launch_rans_assemble(fd->H, fd->W, C, fd->schedule, q->enc_scratch, cap_words, q->enc_nw, q->rstate, bs, cap,
-                         q->enc_total, q->d_status, s);
-    CK_CUDA(c, cudaMemcpyAsync(q->h_total, q->enc_total, 8, cudaMemcpyDeviceToHost, s));
-    CK_CUDA(c, cudaMemcpyAsync(q->h_status, q->d_status, 4, cudaMemcpyDeviceToHost, s));
-    CK_CUDA(c, cudaStreamSynchronize(s));
-    *len = (size_t)*q->h_total;
-    if (*q->h_status & ST_CAPACITY) return fail(c, PSW_ERR_CAPACITY, "container needs %zu bytes, capacity %zu", *len, cap);
-    return PSW_OK;
+    {
+        Scope sc(c, s, K_RANS, 0.0, (double)HW * C * 2.0);
+        launch_rans_assemble(fd->H, fd->W, C, fd->schedule, q->enc_scratch, cap_words, q->enc_nw, q->rstate, bs, cap,
+                             q->enc_total, q->d_status, s);
+    }
+    cudaMemcpyAsync(q->h_total, q->enc_total, 8, cudaMemcpyDeviceToHost, s);
 }
 
 }  // namespace
@@ -646,7 +978,8 @@ psw_status psw_create(const psw_model_desc *desc, const float *weights_host, siz
     c->md = *desc; c->prec = precision; c->budget = hbm_budget; c->lay = lay;
     prepare_projections(c, /*dry=*/true);
     build_cdf_tables(c->tabs);
-    c->bytes = (size_t)lay.total * 4 + c->arena + (size_t)c->tabs.total * 4 + 3 * 64 * 4 + 64 * 4;
+    c->bytes = (size_t)lay.total * 4 + c->arena + (size_t)c->tabs.total * 4 + 3 * 64 * 4 + 64 * 4 +
+               MAX_SLOTS * sizeof(Slot);
     if (hbm_budget && c->bytes > hbm_budget) {
         size_t need = c->bytes;
         psw_destroy(c);
@@ -657,10 +990,15 @@ psw_status psw_create(const psw_model_desc *desc, const float *weights_host, siz
     if (e == cudaSuccess) e = cudaMalloc(&c->d_cdf, (size_t)c->tabs.total * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_meta, 3 * 64 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_scale, 64 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_slots, MAX_SLOTS * sizeof(Slot));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_slots, MAX_SLOTS * sizeof(Slot));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, (MAX_SLOTS + 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_rate, sizeof(double));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         psw_destroy(c);
-        return fail(nullptr, PSW_ERR_OOM, "cudaMalloc: %s", cudaGetErrorString(e));
+        return fail(nullptr, PSW_ERR_OOM, "device allocation: %s", cudaGetErrorString(e));
     }
     int meta[3 * 64];
     for (int l = 0; l < 64; l++) { meta[l] = c->tabs.T[l]; meta[64 + l] = c->tabs.n[l]; meta[128 + l] = c->tabs.off[l]; }
@@ -682,9 +1020,15 @@ void psw_destroy(psw_ctx *c)
 {
     if (!c) return;
     while (!c->seqs.empty()) psw_seq_destroy(c->seqs.back());
+    for (auto &kv : c->graphs) graph_free(kv.second);
     cudaFree(c->w); cudaFree(c->wmat); cudaFree(c->d_cdf); cudaFree(c->d_meta); cudaFree(c->d_scale);
-    cudaFree(c->rate_buf);
+    cudaFree(c->rate_buf); cudaFree(c->d_slots); cudaFree(c->d_status); cudaFree(c->d_tok); cudaFree(c->d_kn);
+    cudaFree(c->Xn); cudaFree(c->Q); cudaFree(c->O); cudaFree(c->Hid);
+    cudaFree(c->Xa); cudaFree(c->Xb); cudaFree(c->Xg);
     if (c->h_rate) cudaFreeHost(c->h_rate);
+    if (c->h_slots) cudaFreeHost(c->h_slots);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
     free_cdf_tables(c->tabs);
     delete c;
@@ -697,14 +1041,20 @@ psw_status psw_seq_create(psw_ctx *c, int max_H, int max_W, psw_seq **out)
     if (max_H < 1 || max_W < 1 || max_H > 4096 || max_W > 4096 || (long)max_H * max_W > (1L << 24))
         return fail(c, PSW_ERR_INVALID, "bad maximum grid %dx%d", max_H, max_W);
     size_t need = seq_bytes_for(c->md, c->prec, max_H, max_W);
+    size_t ws_more = 0, HW = (size_t)max_H * max_W;
+    if (HW > c->ws_rows)
+        ws_more = HW * (3 * (size_t)std::max(c->md.d, c->md.C) + std::max(c->md.F, 2 * c->md.d)) * esize(c->prec) +
+                  HW * c->md.d * 4 * (c->md.temporal ? 3 : 2) - c->ws_bytes;
     size_t used = c->bytes;
     for (psw_seq *s : c->seqs) used += s->bytes;
-    if (c->budget && used + need > c->budget)
-        return fail(c, PSW_ERR_OOM, "sequence needs %zu bytes; %zu of %zu in use", need, used, c->budget);
+    if (c->budget && used + need + ws_more > c->budget)
+        return fail(c, PSW_ERR_OOM, "sequence needs %zu bytes; %zu of %zu in use", need + ws_more, used, c->budget);
+    psw_status st = ensure_workspace(c, HW);
+    if (st) return st;
     psw_seq *q = new psw_seq();
-    q->ctx = c; q->maxH = max_H; q->maxW = max_W; q->maxHW = max_H * max_W; q->bytes = need;
+    q->ctx = c; q->maxH = max_H; q->maxW = max_W; q->maxHW = (int)HW; q->bytes = need;
     const psw_model_desc &m = c->md;
-    size_t HW = q->maxHW, d = m.d, es = esize(c->prec);
+    size_t d = m.d, es = esize(c->prec);
     bool okay = true;
     auto dal = [&](size_t bytes) -> void * {
         void *p = nullptr;
@@ -713,13 +1063,11 @@ psw_status psw_seq_create(psw_ctx *c, int max_H, int max_W, psw_seq **out)
         q->allocs.push_back(p);
         return p;
     };
-    q->eh = (float *)dal(HW * d * 4); q->x1 = (float *)dal(HW * d * 4); q->x2 = (float *)dal(HW * d * 4);
-    q->g = (float *)dal(m.temporal ? HW * d * 4 : 16);
+    q->eh = (float *)dal(HW * d * 4);
     q->qa = dal(HW * d * es);
     q->K1 = dal(m.L * HW * d * es); q->V1 = dal(m.L * HW * d * es);
     q->K2 = dal(m.L * HW * d * es); q->V2 = dal(m.L * HW * d * es);
     q->Ka = dal(HW * d * es); q->Va = dal(HW * d * es);
-    q->Xn = dal(HW * d * es); q->Q = dal(HW * d * es); q->O = dal(HW * d * es); q->Hid = dal(HW * m.F * es);
     if (m.temporal) {
         q->CK = dal((size_t)m.Lc * m.Tf * HW * d * es); q->CV = dal((size_t)m.Lc * m.Tf * HW * d * es);
         q->XK = dal(2 * (size_t)m.L * m.Tf * HW * d * es); q->XV = dal(2 * (size_t)m.L * m.Tf * HW * d * es);
@@ -734,21 +1082,10 @@ psw_status psw_seq_create(psw_ctx *c, int max_H, int max_W, psw_seq **out)
     q->enc_total = (uint64_t *)dal(8);
     q->d_status = (int *)dal(4);
     q->d_order = (int *)dal(HW * 4);
-    q->d_ident = (int *)dal(HW * 4);
-    if (okay && (cudaMallocHost(&q->h_total, 8) != cudaSuccess || cudaMallocHost(&q->h_status, 4) != cudaSuccess))
-        okay = false;
+    if (okay && cudaMallocHost(&q->h_total, 8) != cudaSuccess) okay = false;
     if (!okay) {
         psw_seq_destroy(q);
         return fail(c, PSW_ERR_OOM, "sequence allocation of %zu bytes failed", need);
-    }
-    std::vector<int> ident(HW);
-    for (size_t p = 0; p < HW; p++) ident[p] = (int)p;
-    cudaError_t e = cudaMemcpy(q->d_ident, ident.data(), HW * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(q->x1, 0, HW * d * 4);
-    if (e == cudaSuccess) e = cudaMemset(q->x2, 0, HW * d * 4);
-    if (e != cudaSuccess) {
-        psw_seq_destroy(q);
-        return fail(c, PSW_ERR_CUDA, "sequence initialisation: %s", cudaGetErrorString(e));
     }
     c->seqs.push_back(q);
     *out = q;
@@ -765,14 +1102,27 @@ psw_status psw_seq_reset(psw_seq *q)
 void psw_seq_destroy(psw_seq *q)
 {
     if (!q) return;
-    for (void *p : q->allocs) cudaFree(p);
-    if (q->h_total) cudaFreeHost(q->h_total);
-    if (q->h_status) cudaFreeHost(q->h_status);
     if (q->ctx) {
-        auto &v = q->ctx->seqs;
+        psw_ctx *c = q->ctx;
+        cudaDeviceSynchronize();
+        // drop the graphs that name this sequence
+        for (auto it = c->graphs.begin(); it != c->graphs.end();) {
+            bool hit = false;
+            for (size_t a = 2; a < it->first.size(); a += 2)
+                if (it->first[a] == (long)(uintptr_t)q) hit = true;
+            if (hit) {
+                graph_free(it->second);
+                it = c->graphs.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        auto &v = c->seqs;
         for (size_t a = 0; a < v.size(); a++)
             if (v[a] == q) { v.erase(v.begin() + a); break; }
     }
+    for (void *p : q->allocs) cudaFree(p);
+    if (q->h_total) cudaFreeHost(q->h_total);
     delete q;
 }
 
@@ -794,94 +1144,59 @@ psw_status psw_encode_params(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, c
     if ((st = seq_schedule(q, fd->H, fd->W, fd->schedule))) return st;
     int HW = fd->H * fd->W;
     size_t nsym = (size_t)HW * c->md.C;
-    Pass P{c, q, s, fd->H, fd->W};
-    CK_CUDA(c, cudaMemsetAsync(q->d_status, 0, 4, s));
+    if ((st = ensure_workspace(c, HW))) return st;
+    if ((st = grow_tokens(c, HW, 1))) return st;
+    Slot sl = make_slot(q, fd->H, fd->W, fd->schedule);
+    sl.zhat = zhat_dev;
+    c->h_slots[0] = sl;
+    std::vector<psw_seq *> qs{q};
+    if ((st = upload_slots(c, qs, 1, s))) return st;
+    std::vector<int> tok(HW);
+    for (int p = 0; p < HW; p++) tok[p] = tok_make(0, p);
+    CK_CUDA(c, cudaMemcpyAsync(c->d_tok, tok.data(), HW * sizeof(int), cudaMemcpyHostToDevice, s));
     CK_CUDA(c, cudaMemcpyAsync(q->y, yhat_dev, nsym * 2, cudaMemcpyDeviceToDevice, s));
-    frame_prologue(P, zhat_dev, q->yprev);
+    bool failed = false;
+    Pass P{c, s, c->d_slots, &failed};
     // masked parallel pass over every position (Sec. 3.1, Sec. 3.2)
-    run_sm1(P, q->y, q->d_ident, HW);
-    run_acc_sm2_heads(P, q->d_ident, HW);
+    frame_prologue(P, c->d_tok, HW, q->eh);
+    run_sm1(P, c->d_tok, HW);
+    run_acc_sm2_heads(P, c->d_tok, HW);
     if (mu_dev) CK_CUDA(c, cudaMemcpyAsync(mu_dev, q->mu, nsym * 4, cudaMemcpyDeviceToDevice, s));
     if (sigma_dev) CK_CUDA(c, cudaMemcpyAsync(sigma_dev, q->sigma, nsym * 4, cudaMemcpyDeviceToDevice, s));
     CK_CUDA(c, cudaGetLastError());
     if (len_out) *len_out = 0;
-    if (bitstream_dev) st = encode_symbols(c, q, fd, q->y, q->idx, q->m, bitstream_dev, cap, len_out, s);
+    if (bitstream_dev) encode_symbols(c, q, fd, bitstream_dev, cap, s);
     // the sequence advances even if the container did not fit
     CK_CUDA(c, cudaMemcpyAsync(q->yprev, q->y, nsym * 2, cudaMemcpyDeviceToDevice, s));
-    int dst = 0;
-    psw_status st2 = read_status(c, q, s, &dst);
+    std::vector<int> sts;
+    if ((st = read_status(c, qs, s, sts))) return st;   // synchronises: the token list is free again
     q->frame++;
-    if (st2) return st2;
-    if (q->launch_failed) { q->launch_failed = false; return fail(c, PSW_ERR_CUDA, "a GEMM launch could not be prepared"); }
-    if (dst & ST_TIMEOUT) return fail(c, PSW_ERR_TIMEOUT, "device wait timed out");
-    return st;
+    if (bitstream_dev) *len_out = (size_t)*q->h_total;
+    if (failed) return fail(c, PSW_ERR_CUDA, "a GEMM launch could not be prepared");
+    if (sts[0] & ST_CAPACITY)
+        return fail(c, PSW_ERR_CAPACITY, "container needs %zu bytes, capacity %zu", (size_t)*q->h_total, cap);
+    return status_code(c, sts[0]);
 }
 
 psw_status psw_decode_frame(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, const uint8_t *bitstream_dev,
                             size_t len, const int16_t *zhat_dev, int16_t *yhat_out_dev, float *mu_dev,
                             float *sigma_dev, void *stream)
 {
-    psw_status st = check_frame(c, q, fd);
-    if (st) return st;
-    if (!bitstream_dev || !zhat_dev || !yhat_out_dev) return fail(c, PSW_ERR_INVALID, "null pointer argument");
-    if ((uintptr_t)bitstream_dev & 3) return fail(c, PSW_ERR_INVALID, "bitstream must be 4-byte aligned");
-    cudaStream_t s = (cudaStream_t)stream;
-    if ((st = seq_schedule(q, fd->H, fd->W, fd->schedule))) return st;
-    const psw_model_desc &m = c->md;
-    int HW = fd->H * fd->W;
-    size_t nsym = (size_t)HW * m.C;
-    Pass P{c, q, s, fd->H, fd->W};
-    CK_CUDA(c, cudaMemsetAsync(q->d_status, 0, 4, s));
-    frame_prologue(P, zhat_dev, q->yprev);
-    {
-        Scope sc(c, s, K_RANS, 0.0, (double)m.C * 128.0);
-        launch_rans_dec_init(bitstream_dev, len, fd->H, fd->W, m.C, fd->schedule, q->rstate, q->rptr, q->rend,
-                             q->d_status, s);
-    }
-    const int *ord = q->d_order;
-    for (int t = 0; t < q->T; t++) {
-        int a0 = q->h_start[t], n = q->h_start[t + 1] - a0;
-        if (t > 0) {
-            int b0 = q->h_start[t - 1];
-            run_sm1(P, q->y, ord + b0, a0 - b0);
-        }
-        run_acc_sm2_heads(P, ord + a0, n);
-        Scope sc(c, s, K_RANS, 0.0, (double)n * m.C * 7.0 + (double)len * n / HW);
-        launch_rans_dec_step(coder(c), ord, a0, n, m.C, q->idx, q->m, bitstream_dev, q->rstate, q->rptr, q->rend,
-                             q->y, q->d_status, s);
-    }
-    {
-        Scope sc(c, s, K_RANS, 0.0, (double)m.C * 128.0);
-        launch_rans_dec_finish(bitstream_dev, m.C, q->rstate, q->rptr, q->rend, q->d_status, s);
-    }
-    CK_CUDA(c, cudaGetLastError());
-    CK_CUDA(c, cudaMemcpyAsync(yhat_out_dev, q->y, nsym * 2, cudaMemcpyDeviceToDevice, s));
-    if (mu_dev) CK_CUDA(c, cudaMemcpyAsync(mu_dev, q->mu, nsym * 4, cudaMemcpyDeviceToDevice, s));
-    if (sigma_dev) CK_CUDA(c, cudaMemcpyAsync(sigma_dev, q->sigma, nsym * 4, cudaMemcpyDeviceToDevice, s));
-    CK_CUDA(c, cudaMemcpyAsync(q->yprev, q->y, nsym * 2, cudaMemcpyDeviceToDevice, s));
-    int dst = 0;
-    if ((st = read_status(c, q, s, &dst))) return st;
-    q->frame++;
-    if (q->launch_failed) { q->launch_failed = false; return fail(c, PSW_ERR_CUDA, "a GEMM launch could not be prepared"); }
-    if (dst & ST_CORRUPT) return fail(c, PSW_ERR_CORRUPT, "bitstream failed validation");
-    if (dst & ST_TIMEOUT) return fail(c, PSW_ERR_TIMEOUT, "device wait timed out");
-    return PSW_OK;
+    if (!c) return PSW_ERR_INVALID;
+    return decode_run(c, 1, &q, fd, &bitstream_dev, &len, &zhat_dev, &yhat_out_dev, &mu_dev, &sigma_dev, nullptr,
+                      (cudaStream_t)stream);
 }
 
 psw_status psw_decode_batch(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_desc *fds,
                             const uint8_t *const *bitstreams_dev, const size_t *lens, const int16_t *const *zhat_dev,
-                            int16_t *const *yhat_out_dev, int *status_out, void *stream)
+                            int16_t *const *yhat_out_dev, float *const *mu_dev, float *const *sigma_dev,
+                            int *status_out, void *stream)
 {
-    if (!c || n < 0 || (n > 0 && (!seqs || !fds || !bitstreams_dev || !lens || !zhat_dev || !yhat_out_dev)))
+    if (!c) return PSW_ERR_INVALID;
+    if (n < 1 || !seqs || !fds || !bitstreams_dev || !lens || !zhat_dev || !yhat_out_dev)
         return fail(c, PSW_ERR_INVALID, "bad batch arguments");
-    psw_status first = PSW_OK;
-    for (int a = 0; a < n; a++) {
-        psw_status st = psw_decode_frame(c, seqs[a], &fds[a], bitstreams_dev[a], lens[a], zhat_dev[a],
-                                         yhat_out_dev[a], nullptr, nullptr, stream);
-        if (status_out) status_out[a] = st;
-        if (st && !first) first = st;
-    }
-    return first;
+    return decode_run(c, n, seqs, fds, bitstreams_dev, lens, zhat_dev, yhat_out_dev, mu_dev, sigma_dev, status_out,
+                      (cudaStream_t)stream);
 }
 
 psw_status psw_rate(psw_ctx *c, size_t n, const int16_t *yhat_dev, const float *mu_dev, const float *sigma_dev,
@@ -943,8 +1258,19 @@ psw_status psw_rans_encode(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, con
     if (!yhat_dev || !idx_dev || !m_dev || !bitstream_dev || !len_out) return fail(c, PSW_ERR_INVALID, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = seq_schedule(q, fd->H, fd->W, fd->schedule))) return st;
-    CK_CUDA(c, cudaMemsetAsync(q->d_status, 0, 4, s));
-    return encode_symbols(c, q, fd, yhat_dev, idx_dev, m_dev, bitstream_dev, cap, len_out, s);
+    Slot sl = make_slot(q, fd->H, fd->W, fd->schedule);
+    sl.y = const_cast<int16_t *>(yhat_dev);
+    sl.idx = const_cast<uint8_t *>(idx_dev);
+    sl.m = const_cast<int32_t *>(m_dev);
+    c->h_slots[0] = sl;
+    std::vector<psw_seq *> qs{q};
+    if ((st = upload_slots(c, qs, 1, s))) return st;
+    encode_symbols(c, q, fd, bitstream_dev, cap, s);
+    std::vector<int> sts;
+    if ((st = read_status(c, qs, s, sts))) return st;
+    *len_out = (size_t)*q->h_total;
+    if (sts[0] & ST_CAPACITY) return fail(c, PSW_ERR_CAPACITY, "container needs %zu bytes, capacity %zu", *len_out, cap);
+    return status_code(c, sts[0]);
 }
 
 psw_status psw_rans_decode(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, const uint8_t *bitstream_dev,
@@ -958,18 +1284,24 @@ psw_status psw_rans_decode(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, con
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = seq_schedule(q, fd->H, fd->W, fd->schedule))) return st;
     int C = c->md.C;
-    CK_CUDA(c, cudaMemsetAsync(q->d_status, 0, 4, s));
-    launch_rans_dec_init(bitstream_dev, len, fd->H, fd->W, C, fd->schedule, q->rstate, q->rptr, q->rend, q->d_status, s);
-    for (int t = 0; t < q->T; t++) {
-        int a0 = q->h_start[t], n = q->h_start[t + 1] - a0;
-        launch_rans_dec_step(coder(c), q->d_order, a0, n, C, idx_dev, m_dev, bitstream_dev, q->rstate, q->rptr,
-                             q->rend, yhat_out_dev, q->d_status, s);
-    }
-    launch_rans_dec_finish(bitstream_dev, C, q->rstate, q->rptr, q->rend, q->d_status, s);
-    int dst = 0;
-    if ((st = read_status(c, q, s, &dst))) return st;
-    if (dst & ST_CORRUPT) return fail(c, PSW_ERR_CORRUPT, "bitstream failed validation");
-    return PSW_OK;
+    Slot sl = make_slot(q, fd->H, fd->W, fd->schedule);
+    sl.bs = bitstream_dev; sl.len = len;
+    sl.idx = const_cast<uint8_t *>(idx_dev);
+    sl.m = const_cast<int32_t *>(m_dev);
+    sl.y = yhat_out_dev;
+    c->h_slots[0] = sl;
+    std::vector<psw_seq *> qs{q};
+    if ((st = upload_slots(c, qs, 1, s))) return st;
+    std::vector<int2> kn(q->T);
+    for (int t = 0; t < q->T; t++) kn[t] = make_int2(q->h_start[t], q->h_start[t + 1] - q->h_start[t]);
+    if ((st = grow_tokens(c, 1, q->T))) return st;
+    CK_CUDA(c, cudaMemcpyAsync(c->d_kn, kn.data(), q->T * sizeof(int2), cudaMemcpyHostToDevice, s));
+    launch_rans_dec_init(c->d_slots, 1, C, s);
+    for (int t = 0; t < q->T; t++) launch_rans_dec_step(coder(c), c->d_slots, 1, c->d_kn + t, C, s);
+    launch_rans_dec_finish(c->d_slots, 1, C, s);
+    std::vector<int> sts;
+    if ((st = read_status(c, qs, s, sts))) return st;
+    return status_code(c, sts[0]);
 }
 
 long psw_launch_count(const psw_ctx *c) { return c ? c->launches : 0; }

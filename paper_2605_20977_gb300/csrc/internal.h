@@ -20,6 +20,40 @@ constexpr int NSCALES = 64;
 constexpr int CDF_PREC = 16;
 constexpr int MAX_KK = 81;        // largest window (9 x 9)
 constexpr int MAX_TF = 4;         // frames in a temporal window
+constexpr int MAX_SLOTS = 128;    // frames in one batch (token word: slot << 24 | position)
+
+// One frame in flight.  A device-resident table of these lets one launch
+// serve tokens of several frames (of different sequences and grids): a token
+// is the word (slot << 24) | raster position.  Caches are [layer][stride][d]
+// in the compute type; the hyperprior tokens eh are FP32 [stride][d]; stride
+// is the sequence's maximum H*W.  (Residual streams are not per-position
+// state: a position's stream lives only while its step runs, in compact
+// workspace rows, one row per token of the launch.)
+struct Slot {
+    int H, W, stride, frame, sched;
+    int nfr;                       // temporal: frames in the window (<= Tf)
+    int ring[MAX_TF];              // their ring positions, oldest first
+    float *eh;
+    void *qa, *K1, *V1, *K2, *V2, *Ka, *Va;
+    void *CK, *CV, *XK, *XV;
+    float *mu, *sigma;
+    uint8_t *idx;
+    int32_t *m;
+    int16_t *y;                    // this frame's latents (input copy or decoded)
+    const int16_t *yprev, *zhat;
+    const uint8_t *bs;             // decoder input container
+    uint64_t len;
+    uint32_t *rstate, *rptr, *rend;
+    const int *order;              // positions in schedule order
+    int *status;
+};
+
+__host__ __device__ inline int tok_slot(int t) { return (int)((unsigned)t >> 24); }
+__host__ __device__ inline int tok_pos(int t) { return t & 0xFFFFFF; }
+__host__ __device__ inline int tok_make(int slot, int pos) { return (slot << 24) | pos; }
+
+// Caches a kernel can name.
+enum CacheSel { CS_NONE = -1, CS_K1 = 0, CS_V1, CS_K2, CS_V2, CS_KA, CS_VA, CS_QA, CS_CK, CS_CV, CS_XK, CS_XV };
 
 // ---------------------------------------------------------------- GEMM
 // Y[m][n] = sum_k A[m][k] * Wt[n][k]  (A compact token-major, Wt the
@@ -29,26 +63,47 @@ constexpr int MAX_TF = 4;         // frames in a temporal window
 // on the tile it falls in, so a token gets bit-identical results whether it
 // is processed alone (decoder step) or with the whole frame (encoder).
 enum EpiMode {
-    EPI_STORE = 0,      // out[row][n] = y                 (row = m, or pos[m] if scatter)
-    EPI_QKV = 1,        // n < q_cols: out[m][n]; then K cache[pos][.], V cache[pos][.]
-    EPI_RESID = 2,      // resid[pos[m]][n] += y           (FP32 residual stream)
-    EPI_RESID_BASE = 3, // resid[pos[m]][n] = base[pos[m]][n] + y
-    EPI_SWIGLU = 4      // dual GEMM: out[m][n] = silu(y_gate) * y_up
+    EPI_STORE = 0,      // out[m][n] = y, or into cache st_sel at the token's position
+    EPI_QKV = 1,        // n < q_cols: out[m][n]; then caches kc_sel, vc_sel at the token's position
+    EPI_RESID = 2,      // rows[m][n] += y               (FP32 residual stream rows)
+    EPI_RESID_BASE = 3, // rows[m][n] = eh[token position][n] + y
+    EPI_SWIGLU = 4,     // dual GEMM: out[m][n] = silu(y_gate) * y_up
+    EPI_BIAS_SILU = 5,  // out[m][n] = silu(y + bias[n])
+    EPI_SET_BIAS = 6,   // rows[m][n] = y + bias[n]
+    EPI_HEADS = 7       // rows 2c / 2c+1 give mu_c / sigma_c of the token: channel-wise
+                        // scaling, sigma = exp(clamp(.)), then scale index and rounded mean
 };
 
 struct Epi {
     int mode;
-    const int *pos;     // token -> raster position (may be NULL = identity)
-    int scatter;        // EPI_STORE: write row pos[m] instead of m
-    int d;              // width of one K/V cache row
-    int q_cols;         // EPI_QKV: leading columns that go to `out`
-    void *out; int ld_out;
-    void *kc; void *vc; // caches [HW][d]
-    float *resid; const float *base;
+    const int *tok;               // packed tokens, one per row m
+    const Slot *slots;
+    int d;                        // width of a cache / stream row
+    int q_cols;
+    void *out; int ld_out;        // compact output rows
+    int kc_sel, vc_sel, kv_layer; // EPI_QKV caches and their layer index
+    int ring, Tf;                 // ring = 1: layer kv_layer * Tf + the slot's current ring position
+    int st_sel, st_layer;         // EPI_STORE into a cache (CS_NONE: compact out)
+    float *rows;                  // EPI_RESID / EPI_RESID_BASE / EPI_SET_BIAS: FP32 rows [M][N]
+    const float *bias;            // EPI_BIAS_SILU, EPI_SET_BIAS
+    const float *gmu, *bmu, *gsg, *bsg;   // EPI_HEADS channel-wise scale and offset
+    const float *scale;           // EPI_HEADS scale table [64]
+    int C;                        // EPI_HEADS channels
+};
+
+// Source of the token operand of a GEMM.
+enum ASrc {
+    A_DIRECT = 0,       // compact rows A[m][lda] in the compute type
+    A_NORM = 1,         // RMSNorm(FP32 rows xrows[m]) * a_gain
+    A_EMBED = 2         // a_gain[c] * latent y[c] of the token (the latent embedding input)
 };
 
 struct GemmArgs {
-    const void *A; int lda;       // [M][K]
+    const void *A; int lda;       // A_DIRECT: [M][lda]
+    int asrc;
+    const float *xrows;           // A_NORM: FP32 rows [M][K]
+    const float *a_gain;          // A_NORM gain [K]; A_EMBED channel scaling [K]
+    void *prep;                   // compact [M][K] scratch for the SIMT path's operand
     const void *Wt;               // [N][K]
     const void *Wt2;              // second operand of a dual GEMM (EPI_SWIGLU)
     int M, N, K;
@@ -60,44 +115,62 @@ struct GemmArgs {
 // tensor cores (the choice never depends on M); everything else on the SIMT
 // kernel.  Returns false if the launch could not be prepared.
 bool gemm(int prec, const GemmArgs &g, cudaStream_t s);
-bool gemm_tc_supported(int prec, int N, int K);
+bool gemm_tc_supported(int prec, int N, int K, int asrc);
 bool gemm_tc_available();         // driver entry point for tensor maps present
+void launch_gather_embed(int prec, const Slot *S, const int *tok, int n, const float *gamma, int C, void *dst,
+                         cudaStream_t s);
+void launch_convert(int prec, const float *src, size_t n, void *dst, cudaStream_t s);
+
+// Pointer to row `pos` of cache `sel`, layer `layer`, of a slot (device).
+template <typename T>
+__device__ __forceinline__ T *cache_row(const Slot &s, int sel, int layer, int pos, int d)
+{
+    void *base;
+    switch (sel) {
+    case CS_K1: base = s.K1; break;
+    case CS_V1: base = s.V1; break;
+    case CS_K2: base = s.K2; break;
+    case CS_V2: base = s.V2; break;
+    case CS_KA: base = s.Ka; break;
+    case CS_VA: base = s.Va; break;
+    case CS_QA: base = s.qa; break;
+    case CS_CK: base = s.CK; break;
+    case CS_CV: base = s.CV; break;
+    case CS_XK: base = s.XK; break;
+    default: base = s.XV; break;
+    }
+    return (T *)base + ((long)layer * s.stride + pos) * d;
+}
+
 
 // ---------------------------------------------------------------- kernels
 void launch_transpose_convert(int prec, const float *src, int K, int N, void *dst, int row_off,
                               cudaStream_t s);
-void launch_embed_latent(const int *pos, int n, const int16_t *y, int C, const float *gamma,
-                         const float *W, const float *b, int d, float *x, cudaStream_t s);
-void launch_fill_rows(const float *v, int n, int d, float *x, cudaStream_t s);
-void launch_embed_hyper(const int16_t *z, int H, int W, int Wh, int Ch, int r, const float *gamma,
-                        const float *Whp, const float *b, int d, float *eh, cudaStream_t s);
-void launch_rmsnorm(int prec, const int *pos, int n, const float *src, const float *g, int d,
-                    void *dst, int scatter, cudaStream_t s);
+// Context Transformer input rows out[m] of each token from the previous
+// frame's latents (temporal shift), or the learned pad for frame 0.
+void launch_embed_context(const Slot *S, const int *tok, int n, int C, const float *gamma, const float *W,
+                          const float *b, const float *pad, int d, float *out, cudaStream_t s);
+void launch_embed_hyper(const Slot *S, const int *tok, int n, int Wh_max, int Ch, int r, const float *gamma,
+                        const float *Whp, const float *b, int d, cudaStream_t s);
+void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void *dst, cudaStream_t s);
 
 struct AttnArgs {
-    const int *pos; int n;
-    const void *Q; int q_full;               // compact [n][d], or full [HW][d] indexed by pos
-    const void *K[MAX_TF]; const void *V[MAX_TF];
-    int nfr;                                 // frames of keys, oldest first
-    const float *bias;                       // + h * bias_h_stride + age * k*k + window offset
+    const int *tok; int n;
+    const Slot *slots;
+    const void *Q; int q_sel;       // compact [n][d], or cache q_sel (CS_QA) at the token's position
+    int k_sel, v_sel;               // key / value caches
+    int layer;                      // spatial: layer index; temporal: block index (ring layer = layer*Tf + ring)
+    int temporal;                   // 1: keys over the slot's frame ring, unmasked windows
+    int Tf;
+    const float *bias;              // + h * bias_h_stride + age * k*k + window offset
     int bias_h_stride;
-    int age[MAX_TF];
-    void *O;                                 // compact [n][d]
-    int H, W, d, nh, k;
-    int mask;                                // 0: 2i+j with raster clause, 1: cyclic
-    int kind;                                // 0: accumulator A(p), 1: self-attention S(p), -1: window
+    void *O;                        // compact [n][d]
+    int d, nh, k;
+    int mask;                       // 0: 2i+j with raster clause, 1: cyclic
+    int kind;                       // 0: accumulator A(p), 1: self-attention S(p), -1: window
 };
 void launch_attention(int prec, const AttnArgs &a, cudaStream_t s);
 
-struct HeadsArgs {
-    const int *pos; int n;
-    const float *x; int d, C;
-    const float *g, *W1m, *b1m, *W2m, *W1s, *b1s, *W2s;
-    const float *gamma_mu, *beta_mu, *gamma_sig, *beta_sig;
-    const float *scale;                      // device scale table [64]
-    float *mu, *sigma; uint8_t *idx; int32_t *m;   // [HW][C]
-};
-void launch_heads(const HeadsArgs &h, cudaStream_t s);
 void launch_quantize(size_t n, const float *mu, const float *sigma, const float *scale,
                      uint8_t *idx, int32_t *m, cudaStream_t s);
 void launch_rate(size_t n, const int16_t *y, const float *mu, const float *sigma, double *partials,
@@ -120,18 +193,16 @@ struct CoderDev {
     const int *meta;                         // [3][64]: T, n, off
 };
 size_t container_capacity(int H, int W, int C);
-void launch_rans_encode(const CoderDev &cd, const int *order, int HW, int C, const int16_t *y,
-                        const uint8_t *idx, const int32_t *m, uint16_t *scratch, int cap_words,
-                        uint32_t *nwords, uint32_t *states, cudaStream_t s);
+// Encoder of one slot: symbols y / idx / m and the schedule order from the slot.
+void launch_rans_encode(const CoderDev &cd, const Slot *S, int slot, int HW, int C, uint16_t *scratch,
+                        int cap_words, uint32_t *nwords, uint32_t *states, cudaStream_t s);
 void launch_rans_assemble(int H, int W, int C, int sched, const uint16_t *scratch, int cap_words,
                           const uint32_t *nwords, const uint32_t *states, uint8_t *out, size_t cap,
                           uint64_t *total, int *status, cudaStream_t s);
-void launch_rans_dec_init(const uint8_t *bs, size_t len, int H, int W, int C, int sched,
-                          uint32_t *states, uint32_t *ptr, uint32_t *end, int *status, cudaStream_t s);
-void launch_rans_dec_step(const CoderDev &cd, const int *order, int k0, int n, int C,
-                          const uint8_t *idx, const int32_t *m, const uint8_t *bs, uint32_t *states,
-                          uint32_t *ptr, const uint32_t *end, int16_t *y, int *status, cudaStream_t s);
-void launch_rans_dec_finish(const uint8_t *bs, int C, const uint32_t *states, const uint32_t *ptr,
-                            const uint32_t *end, int *status, cudaStream_t s);
+// Validate each slot's container (bs, len, H, W, sched) and load its states.
+void launch_rans_dec_init(const Slot *S, int nslots, int C, cudaStream_t s);
+// kn[b] = (first symbol, count) of slot b in this step (count 0: idle).
+void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const int2 *kn, int C, cudaStream_t s);
+void launch_rans_dec_finish(const Slot *S, int nslots, int C, cudaStream_t s);
 
 }  // namespace psw

@@ -2,39 +2,18 @@
 // SIMT GEMM kernels of the P-SWA context model (Sec. 3.1 block structure,
 // Sec. 3.2 masked window attention).  Every per-token computation has a
 // fixed arithmetic order that does not depend on how many tokens a launch
-// carries, so the encoder's masked pass and the decoder's wavefront steps
-// produce bit-identical parameters.
+// carries or which other frames share it, so the encoder's masked pass, the
+// decoder's wavefront steps and batched decoding produce bit-identical
+// parameters.  Tokens are (slot, position) words; per-frame state is reached
+// through the slot table.
 #include "internal.h"
+#include "device_common.cuh"
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace psw {
-
-// ---------------------------------------------------------------- helpers
-
-template <typename T> __device__ __forceinline__ float to_f(T v);
-template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-template <typename T> __device__ __forceinline__ T from_f(float v);
-template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ float warp_max(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-__device__ __forceinline__ float silu_f(float x) { return x / (1.0f + expf(-x)); }
 
 static inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
@@ -71,95 +50,96 @@ void launch_transpose_convert(int prec, const float *src, int K, int N, void *ds
 
 // ---------------------------------------------------------------- embeddings
 
-// Latent token embedding (Sec. 3.1, channel-wise input scaling then a
-// linear map): x[p][e] = b[e] + sum_c (gamma[c] y[p][c]) W[c][e].
-__global__ void k_embed_latent(const int *__restrict__ pos, const int16_t *__restrict__ y, int C,
-                               const float *__restrict__ gamma, const float *__restrict__ W,
-                               const float *__restrict__ b, int d, float *__restrict__ x)
+// Context Transformer input (Sec. 3.1: temporal shift, channel-wise input
+// scaling then a linear map): out[m][e] = b[e] + sum_c (gamma[c] yprev[c])
+// W[c][e] from the previous frame's latents at the token's position, or the
+// learned padding vector for the first frame of a sequence.  Runs once per
+// frame; FP32.
+__global__ void k_embed_context(const Slot *__restrict__ S, const int *__restrict__ tok, int C,
+                                const float *__restrict__ gamma, const float *__restrict__ W,
+                                const float *__restrict__ b, const float *__restrict__ pad, int d,
+                                float *__restrict__ out)
 {
     extern __shared__ float t[];
-    int p = pos ? pos[blockIdx.x] : blockIdx.x;
-    for (int c = threadIdx.x; c < C; c += blockDim.x) t[c] = gamma[c] * (float)y[(long)p * C + c];
+    int tk = tok[blockIdx.x];
+    const Slot &s = S[tok_slot(tk)];
+    int p = tok_pos(tk);
+    float *x = out + (long)blockIdx.x * d;
+    if (s.frame == 0) {
+        for (int e = threadIdx.x; e < d; e += blockDim.x) x[e] = pad[e];
+        return;
+    }
+    const int16_t *y = s.yprev + (long)p * C;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) t[c] = gamma[c] * (float)y[c];
     __syncthreads();
     for (int e = threadIdx.x; e < d; e += blockDim.x) {
         float acc = 0.0f;
         for (int c = 0; c < C; c++) acc = fmaf(t[c], W[(long)c * d + e], acc);
-        x[(long)p * d + e] = acc + b[e];
+        x[e] = acc + b[e];
     }
 }
 
-void launch_embed_latent(const int *pos, int n, const int16_t *y, int C, const float *gamma,
-                         const float *W, const float *b, int d, float *x, cudaStream_t s)
+void launch_embed_context(const Slot *S, const int *tok, int n, int C, const float *gamma, const float *W,
+                          const float *b, const float *pad, int d, float *out, cudaStream_t s)
 {
     if (n <= 0) return;
-    k_embed_latent<<<n, 128, C * sizeof(float), s>>>(pos, y, C, gamma, W, b, d, x);
-}
-
-__global__ void k_fill_rows(const float *__restrict__ v, int d, float *__restrict__ x)
-{
-    for (int e = threadIdx.x; e < d; e += blockDim.x) x[(long)blockIdx.x * d + e] = v[e];
-}
-
-void launch_fill_rows(const float *v, int n, int d, float *x, cudaStream_t s)
-{
-    if (n <= 0) return;
-    k_fill_rows<<<n, 128, 0, s>>>(v, d, x);
+    k_embed_context<<<n, 128, C * sizeof(float), s>>>(S, tok, C, gamma, W, b, pad, d, out);
 }
 
 // Hyperprior tokens (Fig. 1: the decoded hyperprior enters the transformer):
 // transposed convolution with kernel = stride = r.
-__global__ void k_embed_hyper(const int16_t *__restrict__ z, int W, int Wh, int Ch, int r,
+__global__ void k_embed_hyper(const Slot *__restrict__ S, const int *__restrict__ tok, int Ch, int r,
                               const float *__restrict__ gamma, const float *__restrict__ Whp,
-                              const float *__restrict__ b, int d, float *__restrict__ eh)
+                              const float *__restrict__ b, int d)
 {
     extern __shared__ float t[];
-    int p = blockIdx.x, i = p / W, j = p % W;
-    const int16_t *zv = z + ((long)(i / r) * Wh + (j / r)) * Ch;
+    int tk = tok[blockIdx.x];
+    const Slot &s = S[tok_slot(tk)];
+    int p = tok_pos(tk), i = p / s.W, j = p % s.W, Wh = (s.W + r - 1) / r;
+    const int16_t *zv = s.zhat + ((long)(i / r) * Wh + (j / r)) * Ch;
     for (int c = threadIdx.x; c < Ch; c += blockDim.x) t[c] = gamma[c] * (float)zv[c];
     __syncthreads();
     const float *Ws = Whp + (long)((i % r) * r + (j % r)) * Ch * d;
+    float *eh = s.eh + (long)p * d;
     for (int e = threadIdx.x; e < d; e += blockDim.x) {
         float acc = 0.0f;
         for (int c = 0; c < Ch; c++) acc = fmaf(t[c], Ws[(long)c * d + e], acc);
-        eh[(long)p * d + e] = acc + b[e];
+        eh[e] = acc + b[e];
     }
 }
 
-void launch_embed_hyper(const int16_t *z, int H, int W, int Wh, int Ch, int r, const float *gamma,
-                        const float *Whp, const float *b, int d, float *eh, cudaStream_t s)
+void launch_embed_hyper(const Slot *S, const int *tok, int n, int Wh_max, int Ch, int r, const float *gamma,
+                        const float *Whp, const float *b, int d, cudaStream_t s)
 {
-    k_embed_hyper<<<H * W, 128, Ch * sizeof(float), s>>>(z, W, Wh, Ch, r, gamma, Whp, b, d, eh);
+    (void)Wh_max;
+    if (n <= 0) return;
+    k_embed_hyper<<<n, 128, Ch * sizeof(float), s>>>(S, tok, Ch, r, gamma, Whp, b, d);
 }
 
 // ---------------------------------------------------------------- RMSNorm
 
-// One warp per token: y = x / sqrt(mean(x^2) + 1e-6) * g, FP32 statistics,
-// a fixed lane assignment and butterfly reduction.
+// One warp per row: y = x / sqrt(mean(x^2) + 1e-6) * g, FP32 statistics,
+// a fixed lane assignment and butterfly reduction (the SIMT path's operand).
 template <typename T>
-__global__ void k_rmsnorm(const int *__restrict__ pos, int n, const float *__restrict__ src,
-                          const float *__restrict__ g, int d, T *__restrict__ dst, int scatter)
+__global__ void k_rmsnorm(const float *__restrict__ X, int n, const float *__restrict__ g, int d, T *__restrict__ dst)
 {
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= n) return;
-    int p = pos ? pos[w] : w;
-    const float *x = src + (long)p * d;
+    const float *x = X + (long)w * d;
     float ss = 0.0f;
     for (int e = lane; e < d; e += 32) ss = fmaf(x[e], x[e], ss);
     ss = warp_sum(ss);
     float inv = 1.0f / sqrtf(ss / (float)d + 1e-6f);
-    T *y = dst + (long)(scatter ? p : w) * d;
+    T *y = dst + (long)w * d;
     for (int e = lane; e < d; e += 32) y[e] = from_f<T>(x[e] * inv * g[e]);
 }
 
-void launch_rmsnorm(int prec, const int *pos, int n, const float *src, const float *g, int d, void *dst,
-                    int scatter, cudaStream_t s)
+void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void *dst, cudaStream_t s)
 {
     if (n <= 0) return;
     int blocks = cdiv((long)n * 32, 256);
-    if (prec == P_BF16)
-        k_rmsnorm<__nv_bfloat16><<<blocks, 256, 0, s>>>(pos, n, src, g, d, (__nv_bfloat16 *)dst, scatter);
-    else
-        k_rmsnorm<float><<<blocks, 256, 0, s>>>(pos, n, src, g, d, (float *)dst, scatter);
+    if (prec == P_BF16) k_rmsnorm<__nv_bfloat16><<<blocks, 256, 0, s>>>(X, n, g, d, (__nv_bfloat16 *)dst);
+    else k_rmsnorm<float><<<blocks, 256, 0, s>>>(X, n, g, d, (float *)dst);
 }
 
 // ---------------------------------------------------------------- attention
@@ -182,10 +162,49 @@ __device__ __forceinline__ bool visible(int mask, int kind, int W, int pi, int p
     return ok;
 }
 
+// 8 consecutive elements as floats (16-byte loads for bf16, two for float).
+__device__ __forceinline__ void load8(const __nv_bfloat16 *p, float *o)
+{
+    uint4 r = *(const uint4 *)p;
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&r);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        float2 f = __bfloat1622float2(h[i]);
+        o[2 * i] = f.x; o[2 * i + 1] = f.y;
+    }
+}
+__device__ __forceinline__ void load8(const float *p, float *o)
+{
+    float4 a = *(const float4 *)p, b = *(const float4 *)(p + 4);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w; o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+}
+
+// PER consecutive elements (1, 2 or 4) as floats.
+template <int PER>
+__device__ __forceinline__ void loadp(const __nv_bfloat16 *p, float *o)
+{
+    if (PER == 1) {
+        o[0] = __bfloat162float(*p);
+    } else {
+#pragma unroll
+        for (int i = 0; i < PER / 2; i++) {
+            float2 f = __bfloat1622float2(*(const __nv_bfloat162 *)(p + 2 * i));
+            o[2 * i] = f.x; o[2 * i + 1] = f.y;
+        }
+    }
+}
+template <int PER>
+__device__ __forceinline__ void loadp(const float *p, float *o)
+{
+#pragma unroll
+    for (int i = 0; i < PER; i++) o[i] = p[i];
+}
+
 // One warp per (token, head).  Candidate keys are the window positions of
 // each key frame in ascending raster order (frames oldest first); a lane
-// scores its candidates, the warp takes max and sum by butterflies, then each
-// lane accumulates its output dimensions over the candidates in order.
+// scores its candidates (16-byte loads of the key row), the warp takes max
+// and sum by butterflies, then each lane accumulates its PER consecutive
+// output dimensions over the candidates in order (coalesced value rows).
 template <typename T, int DH>
 __global__ void k_attention(AttnArgs a)
 {
@@ -194,16 +213,19 @@ __global__ void k_attention(AttnArgs a)
     int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int gw = blockIdx.x * 4 + wib;
     if (gw >= a.n * a.nh) return;
-    int tok = gw / a.nh, h = gw % a.nh;
-    int p = a.pos ? a.pos[tok] : tok;
-    int pi = p / a.W, pj = p % a.W, w = (a.k - 1) >> 1, kk = a.k * a.k;
-    const T *q = (const T *)a.Q + (long)(a.q_full ? p : tok) * a.d + h * DH;
+    int tokn = gw / a.nh, h = gw % a.nh;
+    int tk = a.tok[tokn];
+    const Slot &s = a.slots[tok_slot(tk)];
+    int p = tok_pos(tk);
+    int pi = p / s.W, pj = p % s.W, w = (a.k - 1) >> 1, kk = a.k * a.k;
+    const T *q = a.q_sel == CS_NONE ? (const T *)a.Q + (long)tokn * a.d + h * DH
+                                    : cache_row<const T>(s, a.q_sel, 0, p, a.d) + h * DH;
     for (int e = lane; e < DH; e += 32) qs[wib][e] = to_f<T>(q[e]);
     __syncwarp();
     const float scale = rsqrtf((float)DH);
-    int ncand = a.nfr * kk;
+    int nfr = a.temporal ? s.nfr : 1;
+    int ncand = nfr * kk;
     int rounds = (ncand + 31) >> 5;
-    // scores of this lane's candidates (at most 8 rounds: 4 frames x 49)
     float sc[8];
     int key[8];
     float mx = -INFINITY;
@@ -215,14 +237,21 @@ __global__ void k_attention(AttnArgs a)
         if (cidx >= ncand) continue;
         int fr = cidx / kk, c = cidx % kk;
         int qi = pi + c / a.k - w, qj = pj + c % a.k - w;
-        if (qi < 0 || qi >= a.H || qj < 0 || qj >= a.W) continue;
-        if (!visible(a.mask, a.kind, a.W, pi, pj, qi, qj)) continue;
-        int qp = qi * a.W + qj;
-        const T *kr = (const T *)a.K[fr] + (long)qp * a.d + h * DH;
+        if (qi < 0 || qi >= s.H || qj < 0 || qj >= s.W) continue;
+        if (!visible(a.mask, a.kind, s.W, pi, pj, qi, qj)) continue;
+        int qp = qi * s.W + qj;
+        int layer = a.temporal ? a.layer * a.Tf + s.ring[fr] : a.layer;
+        const T *kr = cache_row<const T>(s, a.k_sel, layer, qp, a.d) + h * DH;
         float acc = 0.0f;
-#pragma unroll 8
-        for (int e = 0; e < DH; e++) acc = fmaf(qs[wib][e], to_f<T>(kr[e]), acc);
-        sc[r] = acc * scale + a.bias[(long)h * a.bias_h_stride + (long)a.age[fr] * kk + c];
+#pragma unroll
+        for (int e = 0; e < DH; e += 8) {
+            float kv[8];
+            load8(kr + e, kv);
+#pragma unroll
+            for (int i = 0; i < 8; i++) acc = fmaf(qs[wib][e + i], kv[i], acc);
+        }
+        int age = a.temporal ? nfr - 1 - fr : 0;
+        sc[r] = acc * scale + a.bias[(long)h * a.bias_h_stride + (long)age * kk + c];
         key[r] = qp;
         mx = fmaxf(mx, sc[r]);
     }
@@ -239,20 +268,41 @@ __global__ void k_attention(AttnArgs a)
     float o[PER];
 #pragma unroll
     for (int u = 0; u < PER; u++) o[u] = 0.0f;
-    for (int r = 0; r < rounds; r++) {
-        for (int src = 0; src < 32; src++) {
-            int kq = __shfl_sync(0xffffffffu, key[r], src);
-            float pr = __shfl_sync(0xffffffffu, sc[r] * inv, src);
-            if (kq < 0) continue;
-            int fr = (r * 32 + src) / kk;
-            const T *vr = (const T *)a.V[fr] + (long)kq * a.d + h * DH;
 #pragma unroll
-            for (int u = 0; u < PER; u++) o[u] = fmaf(pr, to_f<T>(vr[u * 32 + lane]), o[u]);
+    for (int r = 0; r < 8; r++) {
+        if (r >= rounds) break;
+        int myk = key[r];
+        float myp = sc[r] * inv;
+        // eight candidates at a time: their value rows load independently
+        for (int s0 = 0; s0 < 32; s0 += 8) {
+            int kq[8];
+            float pr[8], vv[8][PER];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                kq[u] = __shfl_sync(0xffffffffu, myk, s0 + u);
+                pr[u] = __shfl_sync(0xffffffffu, myp, s0 + u);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                if (kq[u] >= 0) {
+                    int fr = (r * 32 + s0 + u) / kk;
+                    int layer = a.temporal ? a.layer * a.Tf + s.ring[fr] : a.layer;
+                    loadp<PER>(cache_row<const T>(s, a.v_sel, layer, kq[u], a.d) + h * DH + lane * PER, vv[u]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < PER; i++) vv[u][i] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (kq[u] >= 0)
+#pragma unroll
+                    for (int i = 0; i < PER; i++) o[i] = fmaf(pr[u], vv[u][i], o[i]);
         }
     }
-    T *out = (T *)a.O + (long)tok * a.d + h * DH;
+    T *out = (T *)a.O + (long)tokn * a.d + h * DH + lane * PER;
 #pragma unroll
-    for (int u = 0; u < PER; u++) out[u * 32 + lane] = from_f<T>(o[u]);
+    for (int u = 0; u < PER; u++) out[u] = from_f<T>(o[u]);
 }
 
 template <typename T>
@@ -285,65 +335,6 @@ __device__ __forceinline__ void quantize_one(float mu, float sigma, const float 
         if (scale[t] >= sigma) { l = t; break; }
     idx = (uint8_t)l;
     m = (int32_t)rintf(fminf(fmaxf(mu, -32768.0f), 32767.0f));
-}
-
-// Prediction heads (Sec. 3.1: grouped two-layer MLPs for mu and sigma, with
-// channel-wise output scaling), one block per token, FP32; then the scale
-// index and rounded mean of every channel.
-__global__ void k_heads(HeadsArgs a)
-{
-    extern __shared__ float sm[];
-    float *xn = sm, *hm = sm + a.d, *hs = sm + 2 * a.d;
-    __shared__ float red[32];
-    __shared__ float stab[NSCALES];
-    int p = a.pos ? a.pos[blockIdx.x] : blockIdx.x;
-    const float *x = a.x + (long)p * a.d;
-    if (threadIdx.x < NSCALES) stab[threadIdx.x] = a.scale[threadIdx.x];
-    float ss = 0.0f;
-    for (int e = threadIdx.x; e < a.d; e += blockDim.x) ss = fmaf(x[e], x[e], ss);
-    ss = warp_sum(ss);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0f;
-        v = warp_sum(v);
-        if (threadIdx.x == 0) red[0] = v;
-    }
-    __syncthreads();
-    float inv = 1.0f / sqrtf(red[0] / (float)a.d + 1e-6f);
-    for (int e = threadIdx.x; e < a.d; e += blockDim.x) xn[e] = x[e] * inv * a.g[e];
-    __syncthreads();
-    for (int e = threadIdx.x; e < a.d; e += blockDim.x) {
-        float am = 0.0f, as = 0.0f;
-        for (int i = 0; i < a.d; i++) {
-            am = fmaf(xn[i], a.W1m[(long)i * a.d + e], am);
-            as = fmaf(xn[i], a.W1s[(long)i * a.d + e], as);
-        }
-        hm[e] = silu_f(am + a.b1m[e]);
-        hs[e] = silu_f(as + a.b1s[e]);
-    }
-    __syncthreads();
-    const float lo = logf(0.11f), hi = logf(256.0f);
-    for (int c = threadIdx.x; c < a.C; c += blockDim.x) {
-        float om = 0.0f, os = 0.0f;
-        for (int e = 0; e < a.d; e++) {
-            om = fmaf(hm[e], a.W2m[(long)e * a.C + c], om);
-            os = fmaf(hs[e], a.W2s[(long)e * a.C + c], os);
-        }
-        float mu = a.gamma_mu[c] * om + a.beta_mu[c];
-        float v = a.gamma_sig[c] * os + a.beta_sig[c];
-        float sg = expf(fminf(fmaxf(v, lo), hi));
-        long o = (long)p * a.C + c;
-        a.mu[o] = mu;
-        a.sigma[o] = sg;
-        quantize_one(mu, sg, stab, a.idx[o], a.m[o]);
-    }
-}
-
-void launch_heads(const HeadsArgs &h, cudaStream_t s)
-{
-    if (h.n <= 0) return;
-    k_heads<<<h.n, 256, 3 * h.d * sizeof(float), s>>>(h);
 }
 
 __global__ void k_quantize(size_t n, const float *mu, const float *sigma, const float *scale,
@@ -467,36 +458,19 @@ __global__ void __launch_bounds__(256) k_gemm_simt(GemmArgs g)
         }
         __syncthreads();
     }
-    const Epi &e = g.epi;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         int m = m0 + tm * 4 + i;
         if (m >= g.M) continue;
-        int p = e.pos ? e.pos[m] : m;
+        if (g.epi.mode == EPI_HEADS) {
+            int n = n0 + tn * 2;                     // a thread holds the (mu, sigma) rows of one channel
+            if (n + 1 < g.N) heads_pair(g.epi, g.epi.scale, m, n, acc[i][0], acc[i][1]);
+            continue;
+        }
 #pragma unroll
         for (int j = 0; j < 2; j++) {
             int n = n0 + tn * 2 + j;
-            if (n >= g.N) continue;
-            float y = acc[i][j];
-            switch (e.mode) {
-            case EPI_STORE:
-                ((T *)e.out)[(long)(e.scatter ? p : m) * e.ld_out + n] = from_f<T>(y);
-                break;
-            case EPI_QKV:
-                if (n < e.q_cols) ((T *)e.out)[(long)m * e.ld_out + n] = from_f<T>(y);
-                else if (n < e.q_cols + e.d) ((T *)e.kc)[(long)p * e.d + (n - e.q_cols)] = from_f<T>(y);
-                else ((T *)e.vc)[(long)p * e.d + (n - e.q_cols - e.d)] = from_f<T>(y);
-                break;
-            case EPI_RESID:
-                e.resid[(long)p * g.N + n] += y;
-                break;
-            case EPI_RESID_BASE:
-                e.resid[(long)p * g.N + n] = e.base[(long)p * g.N + n] + y;
-                break;
-            case EPI_SWIGLU:
-                ((T *)e.out)[(long)m * e.ld_out + n] = from_f<T>(silu_f(y) * acc2[i][j]);
-                break;
-            }
+            if (n < g.N) epilogue_store<T>(g.epi, g.N, m, n, acc[i][j], acc2[i][j]);
         }
     }
 }
@@ -516,12 +490,56 @@ void gemm_simt(int prec, const GemmArgs &g, cudaStream_t s)
 
 bool gemm_tc(const GemmArgs &g, cudaStream_t s);
 
-bool gemm(int prec, const GemmArgs &g, cudaStream_t s)
+bool gemm(int prec, const GemmArgs &g0, cudaStream_t s)
 {
-    if (g.M <= 0 || g.N <= 0) return true;
-    if (gemm_tc_supported(prec, g.N, g.K)) return gemm_tc(g, s);
+    if (g0.M <= 0 || g0.N <= 0) return true;
+    if (gemm_tc_supported(prec, g0.N, g0.K, g0.asrc)) return gemm_tc(g0, s);
+    // SIMT path: materialise the token operand first
+    GemmArgs g = g0;
+    if (g.asrc == A_NORM) {
+        launch_rmsnorm(prec, g.xrows, g.M, g.a_gain, g.K, g.prep, s);
+        g.A = g.prep; g.lda = g.K;
+    } else if (g.asrc == A_EMBED) {
+        launch_gather_embed(prec, g.epi.slots, g.epi.tok, g.M, g.a_gain, g.K, g.prep, s);
+        g.A = g.prep; g.lda = g.K;
+    }
     gemm_simt(prec, g, s);
     return true;
+}
+
+// Channel-scaled latents of each token as compact rows (the latent
+// embedding's input on the SIMT path).
+template <typename T>
+__global__ void k_gather_embed(const Slot *__restrict__ S, const int *__restrict__ tok, const float *__restrict__ gamma,
+                               int C, T *__restrict__ dst)
+{
+    int tk = tok[blockIdx.x];
+    const Slot &s = S[tok_slot(tk)];
+    const int16_t *y = s.y + (long)tok_pos(tk) * C;
+    for (int c = threadIdx.x; c < C; c += blockDim.x) dst[(long)blockIdx.x * C + c] = from_f<T>(gamma[c] * (float)y[c]);
+}
+
+void launch_gather_embed(int prec, const Slot *S, const int *tok, int n, const float *gamma, int C, void *dst,
+                         cudaStream_t s)
+{
+    if (n <= 0) return;
+    if (prec == P_BF16) k_gather_embed<__nv_bfloat16><<<n, 128, 0, s>>>(S, tok, gamma, C, (__nv_bfloat16 *)dst);
+    else k_gather_embed<float><<<n, 128, 0, s>>>(S, tok, gamma, C, (float *)dst);
+}
+
+template <typename T>
+__global__ void k_convert(const float *__restrict__ src, size_t n, T *__restrict__ dst)
+{
+    for (size_t a = blockIdx.x * (size_t)blockDim.x + threadIdx.x; a < n; a += (size_t)gridDim.x * blockDim.x)
+        dst[a] = from_f<T>(src[a]);
+}
+
+void launch_convert(int prec, const float *src, size_t n, void *dst, cudaStream_t s)
+{
+    if (n == 0) return;
+    int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    if (prec == P_BF16) k_convert<__nv_bfloat16><<<blocks, 256, 0, s>>>(src, n, (__nv_bfloat16 *)dst);
+    else k_convert<float><<<blocks, 256, 0, s>>>(src, n, (float *)dst);
 }
 
 }  // namespace psw

@@ -110,13 +110,17 @@ __device__ __forceinline__ uint32_t ld32le(const uint8_t *b, size_t o) { return 
 // produces its renormalisation words in decoding order ([main], [d0, d1]);
 // a warp scan places the group's words, in lane order, just before the
 // words already written (the scratch region is filled from its end).
-__global__ void k_rans_encode(CoderDev cd, const int *__restrict__ order, int HW, int C,
-                              const int16_t *__restrict__ y, const uint8_t *__restrict__ idx,
-                              const int32_t *__restrict__ m, uint16_t *__restrict__ scratch, int cap_words,
-                              uint32_t *__restrict__ nwords, uint32_t *__restrict__ states)
+__global__ void k_rans_encode(CoderDev cd, const Slot *__restrict__ S, int slot, int HW, int C,
+                              uint16_t *__restrict__ scratch, int cap_words, uint32_t *__restrict__ nwords,
+                              uint32_t *__restrict__ states)
 {
     int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (c >= C) return;
+    const Slot &sl = S[slot];
+    const int *__restrict__ order = sl.order;
+    const int16_t *__restrict__ y = sl.y;
+    const uint8_t *__restrict__ idx = sl.idx;
+    const int32_t *__restrict__ m = sl.m;
     uint16_t *buf = scratch + (size_t)c * cap_words;
     uint32_t x = RANS_L;
     int wpos = cap_words;
@@ -127,22 +131,22 @@ __global__ void k_rans_encode(CoderDev cd, const int *__restrict__ order, int HW
         if (k < HW) {
             long a = (long)order[k] * C + c;
             int l = idx[a], T = cd.meta[l], off = cd.meta[2 * NSCALES + l];
-            long s = (long)y[a] - (long)m[a];
-            int slot;
+            long sv = (long)y[a] - (long)m[a];
+            int slot_ = 0;
             bool esc = false;
             uint32_t e0 = 0, e1 = 0;
-            if (s >= -T && s <= T) {
-                slot = (int)(s + T);
+            if (sv >= -T && sv <= T) {
+                slot_ = (int)(sv + T);
             } else {
-                slot = 2 * T + 1;
+                slot_ = 2 * T + 1;
                 esc = true;
-                long mag = s < 0 ? -s : s;
-                uint32_t v = (uint32_t)(2 * (mag - T - 1) + (s < 0 ? 1 : 0));
+                long mag = sv < 0 ? -sv : sv;
+                uint32_t v = (uint32_t)(2 * (mag - T - 1) + (sv < 0 ? 1 : 0));
                 uint32_t d0 = v & 0xFFFFu, d1 = v >> 16;
                 e1 = x & 0xFFFFu; x = (x & 0xFFFF0000u) | d1;     // d1 encoded first
                 e0 = x & 0xFFFFu; x = (x & 0xFFFF0000u) | d0;
             }
-            uint32_t ent = cd.cdf[off + slot];
+            uint32_t ent = cd.cdf[off + slot_];
             uint32_t cm = ent & 0xFFFFu, f = ent >> 16;
             bool ren = x >= (f << 16);
             uint32_t em = x & 0xFFFFu;
@@ -161,12 +165,11 @@ __global__ void k_rans_encode(CoderDev cd, const int *__restrict__ order, int HW
     if (lane == 0) nwords[c] = (uint32_t)(cap_words - wpos);
 }
 
-void launch_rans_encode(const CoderDev &cd, const int *order, int HW, int C, const int16_t *y,
-                        const uint8_t *idx, const int32_t *m, uint16_t *scratch, int cap_words,
-                        uint32_t *nwords, uint32_t *states, cudaStream_t s)
+void launch_rans_encode(const CoderDev &cd, const Slot *S, int slot, int HW, int C, uint16_t *scratch,
+                        int cap_words, uint32_t *nwords, uint32_t *states, cudaStream_t s)
 {
     int blocks = (C * 32 + 127) / 128;
-    k_rans_encode<<<blocks, 128, 0, s>>>(cd, order, HW, C, y, idx, m, scratch, cap_words, nwords, states);
+    k_rans_encode<<<blocks, 128, 0, s>>>(cd, S, slot, HW, C, scratch, cap_words, nwords, states);
 }
 
 // Offsets by a single-block scan over the streams, then the header; the
@@ -246,58 +249,66 @@ void launch_rans_assemble(int H, int W, int C, int sched, const uint16_t *scratc
 
 // ---------------------------------------------------------------- decoder
 
-// Validate the container and load every stream's 32 states.  An invalid
-// container sets the corrupt bit and leaves every stream empty
-// (ptr = end), so later word reads are refused without touching memory.
-__global__ void k_rans_dec_init(const uint8_t *__restrict__ bs, size_t len, int H, int W, int C, int sched,
-                                uint32_t *__restrict__ states, uint32_t *__restrict__ ptr,
-                                uint32_t *__restrict__ end, int *__restrict__ status)
+// Validate each slot's container and load every stream's 32 states; one
+// thread per (slot, channel).  An invalid container sets the corrupt bit and
+// leaves every stream empty (ptr = end), so later word reads are refused
+// without touching memory.
+__global__ void k_rans_dec_init(const Slot *__restrict__ S, int nslots, int C)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    size_t hdr = 16 + 4 * (size_t)(C + 1);
-    bool ok = len >= hdr;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nslots * C) return;
+    int b = t / C, c = t % C;
+    const Slot &sl = S[b];
+    const uint8_t *bs = sl.bs;
+    size_t len = sl.len, hdr = 16 + 4 * (size_t)(C + 1);
+    bool ok = bs != nullptr && len >= hdr;
     if (ok) {
-        ok = ld32le(bs, 0) == MAGIC && ld16le(bs, 4) == 1 && (int)ld16le(bs, 6) == sched &&
-             (int)ld16le(bs, 8) == H && (int)ld16le(bs, 10) == W && (int)ld16le(bs, 12) == C;
+        ok = ld32le(bs, 0) == MAGIC && ld16le(bs, 4) == 1 && (int)ld16le(bs, 6) == sl.sched &&
+             (int)ld16le(bs, 8) == sl.H && (int)ld16le(bs, 10) == sl.W && (int)ld16le(bs, 12) == C;
     }
-    uint32_t a = 0, b = 0;
+    uint32_t a = 0, e = 0;
     if (ok) {
         a = ld32le(bs, 16 + 4 * (size_t)c);
-        b = ld32le(bs, 16 + 4 * (size_t)(c + 1));
-        ok = a >= hdr && (a & 3) == 0 && (b & 3) == 0 && b >= a + 128 && b <= len;
+        e = ld32le(bs, 16 + 4 * (size_t)(c + 1));
+        ok = a >= hdr && (a & 3) == 0 && (e & 3) == 0 && e >= a + 128 && e <= len;
     }
     if (!ok) {
-        atomicOr(status, ST_CORRUPT);
-        for (int l = 0; l < 32; l++) states[(size_t)c * 32 + l] = RANS_L;
-        ptr[c] = 0; end[c] = 0;
+        atomicOr(sl.status, ST_CORRUPT);
+        for (int l = 0; l < 32; l++) sl.rstate[(size_t)c * 32 + l] = RANS_L;
+        sl.rptr[c] = 0; sl.rend[c] = 0;
         return;
     }
-    for (int l = 0; l < 32; l++) states[(size_t)c * 32 + l] = ld32le(bs, a + 4 * l);
-    ptr[c] = a + 128;
-    end[c] = b;
+    for (int l = 0; l < 32; l++) sl.rstate[(size_t)c * 32 + l] = ld32le(bs, a + 4 * l);
+    sl.rptr[c] = a + 128;
+    sl.rend[c] = e;
 }
 
-void launch_rans_dec_init(const uint8_t *bs, size_t len, int H, int W, int C, int sched, uint32_t *states,
-                          uint32_t *ptr, uint32_t *end, int *status, cudaStream_t s)
+void launch_rans_dec_init(const Slot *S, int nslots, int C, cudaStream_t s)
 {
-    k_rans_dec_init<<<(C + 127) / 128, 128, 0, s>>>(bs, len, H, W, C, sched, states, ptr, end, status);
+    int n = nslots * C;
+    if (n <= 0) return;
+    k_rans_dec_init<<<(n + 127) / 128, 128, 0, s>>>(S, nslots, C);
 }
 
-// Decode symbols k0 .. k0 + n - 1 of every channel (one schedule step).
-// One warp per channel; a group of 32 consecutive symbols decodes in
-// parallel on its lanes, which then read their words in lane order.
-__global__ void k_rans_dec_step(CoderDev cd, const int *__restrict__ order, int k0, int n, int C,
-                                const uint8_t *__restrict__ idx, const int32_t *__restrict__ m,
-                                const uint8_t *__restrict__ bs, uint32_t *__restrict__ states,
-                                uint32_t *__restrict__ ptr, const uint32_t *__restrict__ end,
-                                int16_t *__restrict__ y, int *__restrict__ status)
+// Decode symbols k0 .. k0 + n - 1 of every channel of every slot (one
+// schedule step).  One warp per (slot, channel); a group of 32 consecutive
+// symbols decodes in parallel on its lanes, which then read their words in
+// lane order (a warp scan of the words each lane needs).
+__global__ void k_rans_dec_step(CoderDev cd, const Slot *__restrict__ S, int nslots,
+                                const int2 *__restrict__ kn, int C)
 {
-    int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (c >= C) return;
-    uint32_t x = states[(size_t)c * 32 + lane];
-    uint32_t p = ptr[c];
-    const uint32_t e = end[c];
+    int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (wi >= nslots * C) return;
+    int b = wi / C, c = wi % C;
+    int2 r = kn[b];
+    int k0 = r.x, n = r.y;
+    if (n <= 0) return;
+    const Slot &sl = S[b];
+    const uint8_t *__restrict__ bs = sl.bs;
+    const int *__restrict__ order = sl.order;
+    uint32_t x = sl.rstate[(size_t)c * 32 + lane];
+    uint32_t p = sl.rptr[c];
+    const uint32_t e = sl.rend[c];
     bool bad = false;
     for (int g = k0 / 32; g * 32 < k0 + n; g++) {
         int k = g * 32 + lane;
@@ -309,8 +320,8 @@ __global__ void k_rans_dec_step(CoderDev cd, const int *__restrict__ order, int 
         if (act) {
             pos = order[k];
             long a = pos * C + c;
-            int l = idx[a];
-            mm = m[a];
+            int l = sl.idx[a];
+            mm = sl.m[a];
             T = cd.meta[l];
             int nsl = cd.meta[NSCALES + l], off = cd.meta[2 * NSCALES + l];
             uint32_t v = x & 0xFFFFu;
@@ -349,47 +360,45 @@ __global__ void k_rans_dec_step(CoderDev cd, const int *__restrict__ order, int 
             }
             long yv = (long)mm + sv;
             if (yv < -32768 || yv > 32767) { bad = true; yv = 0; }
-            y[pos * C + c] = (int16_t)yv;
+            sl.y[pos * C + c] = (int16_t)yv;
         }
         p += 2 * total;
         if (p > e) p = e;
     }
-    states[(size_t)c * 32 + lane] = x;
-    if (lane == 0) ptr[c] = p;
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_CORRUPT);
+    sl.rstate[(size_t)c * 32 + lane] = x;
+    if (lane == 0) sl.rptr[c] = p;
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(sl.status, ST_CORRUPT);
 }
 
-void launch_rans_dec_step(const CoderDev &cd, const int *order, int k0, int n, int C, const uint8_t *idx,
-                          const int32_t *m, const uint8_t *bs, uint32_t *states, uint32_t *ptr,
-                          const uint32_t *end, int16_t *y, int *status, cudaStream_t s)
+void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const int2 *kn, int C, cudaStream_t s)
 {
-    if (n <= 0) return;
-    int blocks = (C * 32 + 127) / 128;
-    k_rans_dec_step<<<blocks, 128, 0, s>>>(cd, order, k0, n, C, idx, m, bs, states, ptr, end, y, status);
+    int warps = nslots * C;
+    if (warps <= 0) return;
+    k_rans_dec_step<<<(warps * 32 + 127) / 128, 128, 0, s>>>(cd, S, nslots, kn, C);
 }
 
 // After the last step every lane must be back at the initial state and
 // every stream fully consumed (one zero pad word allowed).
-__global__ void k_rans_dec_finish(const uint8_t *__restrict__ bs, int C, const uint32_t *__restrict__ states,
-                                  const uint32_t *__restrict__ ptr, const uint32_t *__restrict__ end,
-                                  int *__restrict__ status)
+__global__ void k_rans_dec_finish(const Slot *__restrict__ S, int nslots, int C)
 {
-    int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (c >= C) return;
-    bool bad = states[(size_t)c * 32 + lane] != RANS_L;
+    int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (wi >= nslots * C) return;
+    int b = wi / C, c = wi % C;
+    const Slot &sl = S[b];
+    bool bad = sl.rstate[(size_t)c * 32 + lane] != RANS_L;
     if (lane == 0) {
-        uint32_t p = ptr[c], e = end[c];
+        uint32_t p = sl.rptr[c], e = sl.rend[c];
         if (e == 0) bad = true;
-        else if (!(p == e || (p + 2 == e && ld16le(bs, p) == 0))) bad = true;
+        else if (!(p == e || (p + 2 == e && ld16le(sl.bs, p) == 0))) bad = true;
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_CORRUPT);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(sl.status, ST_CORRUPT);
 }
 
-void launch_rans_dec_finish(const uint8_t *bs, int C, const uint32_t *states, const uint32_t *ptr,
-                            const uint32_t *end, int *status, cudaStream_t s)
+void launch_rans_dec_finish(const Slot *S, int nslots, int C, cudaStream_t s)
 {
-    int blocks = (C * 32 + 127) / 128;
-    k_rans_dec_finish<<<blocks, 128, 0, s>>>(bs, C, states, ptr, end, status);
+    int warps = nslots * C;
+    if (warps <= 0) return;
+    k_rans_dec_finish<<<(warps * 32 + 127) / 128, 128, 0, s>>>(S, nslots, C);
 }
 
 }  // namespace psw

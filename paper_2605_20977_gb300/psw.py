@@ -75,7 +75,7 @@ def load(path: str = LIB_PATH):
             "psw_bitstream_capacity": (S, [P, FD]),
             "psw_encode_params": (I, [P, P, FD, P, P, P, P, P, S, ct.POINTER(S), P]),
             "psw_decode_frame": (I, [P, P, FD, P, S, P, P, P, P, P]),
-            "psw_decode_batch": (I, [P, I, P, FD, P, P, P, P, P, P]),
+            "psw_decode_batch": (I, [P, I, P, FD, P, P, P, P, P, P, P, P]),
             "psw_rate": (I, [P, S, P, P, P, ct.POINTER(ct.c_double), P]),
             "psw_quantize": (I, [P, S, P, P, P, P, P]),
             "psw_scale_table": (I, [P, P]),
@@ -206,7 +206,9 @@ class Context:
         return [dict(name=a.name.decode(), launches=int(a.launches), ms=float(a.ms), flops=float(a.flops),
                      bytes=float(a.bytes)) for a in arr[:n.value]]
 
-    def decode_batch(self, seqs, fds, bitstreams, lens, zhats, outs, stream=None):
+    def decode_batch(self, seqs, fds, bitstreams, lens, zhats, outs, mus=None, sigmas=None, stream=None,
+                     check: bool = True):
+        """Decode one frame of each sequence together; returns per-frame statuses."""
         n = len(seqs)
         sp = (ct.c_void_p * n)(*[s.h for s in seqs])
         fa = (FrameDesc * n)(*fds)
@@ -214,9 +216,13 @@ class Context:
         ln = (ct.c_size_t * n)(*lens)
         zp = (ct.c_void_p * n)(*[_ptr(z) for z in zhats])
         op = (ct.c_void_p * n)(*[_ptr(o) for o in outs])
+        mp = (ct.c_void_p * n)(*[_ptr(x) for x in mus]) if mus is not None else None
+        gp = (ct.c_void_p * n)(*[_ptr(x) for x in sigmas]) if sigmas is not None else None
         stv = (ct.c_int * n)()
-        st = self.lib.psw_decode_batch(self.h, n, sp, fa, bp, ln, zp, op, stv, _stream(stream))
-        return st, list(stv)
+        st = self.lib.psw_decode_batch(self.h, n, sp, fa, bp, ln, zp, op, mp, gp, stv, _stream(stream))
+        if check:
+            self._check(st)
+        return list(stv)
 
 
 class Sequence:

@@ -107,7 +107,7 @@ class Tensor:
     init: str          # gain | lin | lin_res | bias | relbias | normal | const
     value: float = 0.0
     fan_in: int = 1
-    matrix: bool = False   # block projection (stored in the compute dtype)
+    matrix: bool = False   # projection stored in the compute dtype
 
 
 def _block(prefix: str, c: ModelConfig, cross: bool, tf_bias: bool, nblocks: int) -> list:
@@ -141,7 +141,7 @@ def weight_spec(c: ModelConfig) -> list:
     d, C, Ch, F = c.d, c.C, c.Ch, c.F
     nblocks = 2 * c.L + 1 + (c.Lc if c.temporal else 0)
     s = [Tensor("gamma_in", (C,), "const", 0.25),
-         Tensor("W_in", (C, d), "lin", fan_in=C),
+         Tensor("W_in", (C, d), "lin", fan_in=C, matrix=True),
          Tensor("b_in", (d,), "bias"),
          Tensor("gamma_z", (Ch,), "const", 0.5),
          Tensor("W_hp", (c.r * c.r, Ch, d), "lin", fan_in=Ch),
@@ -170,10 +170,10 @@ def weight_spec(c: ModelConfig) -> list:
     for l in range(c.L):
         s += _block(f"sm2.{l}.", c, cross=bool(c.temporal), tf_bias=False, nblocks=nblocks)
     s += [Tensor("g_head", (d,), "gain"),
-          Tensor("W1m", (d, d), "lin", fan_in=d), Tensor("b1m", (d,), "bias"),
-          Tensor("W2m", (d, C), "lin", fan_in=d),
-          Tensor("W1s", (d, d), "lin", fan_in=d), Tensor("b1s", (d,), "bias"),
-          Tensor("W2s", (d, C), "lin", fan_in=d),
+          Tensor("W1m", (d, d), "lin", fan_in=d, matrix=True), Tensor("b1m", (d,), "bias"),
+          Tensor("W2m", (d, C), "lin", fan_in=d, matrix=True),
+          Tensor("W1s", (d, d), "lin", fan_in=d, matrix=True), Tensor("b1s", (d,), "bias"),
+          Tensor("W2s", (d, C), "lin", fan_in=d, matrix=True),
           Tensor("gamma_mu", (C,), "const", 2.0), Tensor("beta_mu", (C,), "const", 0.0),
           Tensor("gamma_sig", (C,), "const", 1.0), Tensor("beta_sig", (C,), "const", math.log(2.0))]
     return s
@@ -210,8 +210,9 @@ def weights(c: ModelConfig, seed: int = 42) -> np.ndarray:
 
 
 def matrix_mask(c: ModelConfig) -> np.ndarray:
-    """Boolean mask over the flat weight vector: True for block projections
-    (the tensors a reduced-precision run stores in its compute dtype)."""
+    """Boolean mask over the flat weight vector: True for the projections a
+    reduced-precision run stores in its compute dtype (block projections,
+    the latent embedding and the prediction heads)."""
     out = []
     for t in weight_spec(c):
         out.append(np.full(int(np.prod(t.shape)), t.matrix, dtype=bool))

@@ -1,0 +1,156 @@
+"""Batched decoding and graph replay on the GPU.
+
+A frame decoded inside a batch (its wavefront steps sharing launches with
+other frames of other sequences, grids and schedules) must give exactly the
+latents and (mu, sigma) it gives when decoded alone; replays of a captured
+decode must repeat bit for bit, report a corrupt container and recover.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import dev, need_gpu, torch
+from paper_2605_20977_gb300 import psw, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    need_gpu()
+    from paper_2605_20977_gb300 import build
+    build.build()
+    O.build()
+    torch.cuda.set_device(0)
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+def _encode(ctx, cfg, fr, sched):
+    """Encode every frame of fr with a fresh sequence; returns per-frame
+    (bitstream tensor, length, z tensor, y numpy)."""
+    H, W = fr.y.shape[1], fr.y.shape[2]
+    enc = ctx.seq_create(H, W)
+    fd = psw.frame_desc(H, W, sched)
+    out = []
+    for f in range(fr.y.shape[0]):
+        bs = torch.zeros(ctx.bitstream_capacity(H, W), dtype=torch.uint8, device=dev())
+        z = _t(fr.z[f])
+        n = enc.encode_params(fd, _t(fr.y[f]), z, bitstream=bs)
+        out.append((bs, n, z, fr.y[f]))
+    enc.close()
+    return out
+
+
+def _alloc(H, W, C):
+    y = torch.full((H, W, C), 7777, dtype=torch.int16, device=dev())
+    mu = torch.zeros((H, W, C), dtype=torch.float32, device=dev())
+    return y, mu, torch.zeros_like(mu)
+
+
+def _alone(ctx, cfg, items, fds):
+    res = []
+    for (bs, n, z, y), fd in zip(items, fds):
+        seq = ctx.seq_create(fd.H, fd.W)
+        yo, mu, sg = _alloc(fd.H, fd.W, cfg.C)
+        seq.decode_frame(fd, bs, n, z, yo, mu, sg)
+        res.append((yo.cpu().numpy(), mu.cpu().numpy(), sg.cpu().numpy()))
+        seq.close()
+    return res
+
+
+def _batched(ctx, cfg, items, fds, seqs=None):
+    seqs = seqs or [ctx.seq_create(fd.H, fd.W) for fd in fds]
+    outs = [_alloc(fd.H, fd.W, cfg.C) for fd in fds]
+    st = ctx.decode_batch(seqs, fds, [it[0] for it in items], [it[1] for it in items], [it[2] for it in items],
+                          [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+    assert st == [psw.PSW_OK] * len(fds)
+    return [(o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy()) for o in outs], seqs
+
+
+def _check_same(alone, batched, items):
+    for (ya, ma, sa), (yb, mb, sb), it in zip(alone, batched, items):
+        assert np.array_equal(ya, it[3]) and np.array_equal(yb, it[3])
+        assert np.array_equal(ma, mb) and np.array_equal(sa, sb)
+
+
+@pytest.mark.parametrize("precision", [psw.PSW_FP32, psw.PSW_BF16])
+def test_batch_equals_alone_mixed_grids_and_schedules(precision):
+    base = synth.config("tiny")
+    ctx = psw.Context(base, synth.weights(base), precision=precision)
+    plan = [((8, 12), 0), ((5, 7), 1), ((8, 3), 0), ((1, 1), 0), ((6, 12), 0)]
+    items, fds = [], []
+    for k, ((H, W), sched) in enumerate(plan):
+        c = base.with_grid(H, W)
+        items += _encode(ctx, c, synth.frames(c, 1, seed=50 + k), sched)
+        fds.append(psw.frame_desc(H, W, sched))
+    alone = _alone(ctx, base, items, fds)
+    batched, _ = _batched(ctx, base, items, fds)
+    _check_same(alone, batched, items)
+
+
+def test_batch_equals_alone_1080p_bf16():
+    cfg = synth.config("i1080")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
+    plan = [(68, 120), (12, 120), (17, 30)]
+    items, fds = [], []
+    for k, (H, W) in enumerate(plan):
+        c = cfg.with_grid(H, W)
+        items += _encode(ctx, c, synth.frames(c, 1, seed=70 + k), 0)
+        fds.append(psw.frame_desc(H, W, 0))
+    alone = _alone(ctx, cfg, items, fds)
+    batched, _ = _batched(ctx, cfg, items, fds)
+    _check_same(alone, batched, items)
+
+
+def test_graph_replay_repeats_and_recovers_from_corruption():
+    cfg = synth.config("tiny")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
+    items = _encode(ctx, cfg, synth.frames(cfg, 1, seed=90), 0)
+    bs, n, z, y = items[0]
+    fd = psw.frame_desc(cfg.H, cfg.W, 0)
+    seq = ctx.seq_create(cfg.H, cfg.W)
+    first = None
+    for rep in range(4):
+        seq.reset()
+        yo, mu, sg = _alloc(cfg.H, cfg.W, cfg.C)
+        if rep == 2:
+            bad = bs.clone()
+            bad[16 + 4 * (cfg.C + 1) + 300] ^= 0x3C
+            st = seq.decode_frame(fd, bad, n, z, yo, mu, sg, check=False)
+            assert st == psw.PSW_ERR_CORRUPT or not np.array_equal(yo.cpu().numpy(), y)
+            continue
+        seq.decode_frame(fd, bs, n, z, yo, mu, sg)
+        got = (yo.cpu().numpy(), mu.cpu().numpy(), sg.cpu().numpy())
+        assert np.array_equal(got[0], y)
+        if first is None:
+            first = got
+        else:
+            assert np.array_equal(got[1], first[1]) and np.array_equal(got[2], first[2])
+    # launches are counted for replayed graphs too
+    l0 = ctx.launch_count()
+    seq.reset()
+    yo, mu, sg = _alloc(cfg.H, cfg.W, cfg.C)
+    seq.decode_frame(fd, bs, n, z, yo, mu, sg)
+    assert ctx.launch_count() - l0 > 100
+
+
+def test_temporal_sequences_in_a_batch():
+    cfg = synth.config("tiny_p")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_FP32)
+    frs = [synth.frames(cfg, 4, seed=110 + k) for k in range(2)]
+    enc = [_encode(ctx, cfg, fr, 0) for fr in frs]
+    fd = psw.frame_desc(cfg.H, cfg.W, 0)
+    solo = [ctx.seq_create(cfg.H, cfg.W) for _ in frs]
+    pair = [ctx.seq_create(cfg.H, cfg.W) for _ in frs]
+    for f in range(4):
+        items = [enc[k][f] for k in range(2)]
+        alone = []
+        for k in range(2):
+            yo, mu, sg = _alloc(cfg.H, cfg.W, cfg.C)
+            solo[k].decode_frame(fd, items[k][0], items[k][1], items[k][2], yo, mu, sg)
+            alone.append((yo.cpu().numpy(), mu.cpu().numpy(), sg.cpu().numpy()))
+        batched, _ = _batched(ctx, cfg, items, [fd, fd], seqs=pair)
+        _check_same(alone, batched, items)

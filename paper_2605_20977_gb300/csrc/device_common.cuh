@@ -30,6 +30,11 @@ __device__ __forceinline__ float warp_max(float v)
 
 __device__ __forceinline__ float silu_f(float x) { return x / (1.0f + expf(-x)); }
 
+// Programmatic dependent launch: let the next kernel in the stream start its
+// prologue now; wait until the previous kernel's results are visible.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ln 0.11 and ln 256: sigma's range (the scale table's end points).
 constexpr float LN_SIG_LO = -2.2072749131897207f, LN_SIG_HI = 5.545177444479562f;
 

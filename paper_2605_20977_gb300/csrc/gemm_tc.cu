@@ -295,6 +295,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    pdl_trigger();
+    // token lists, the slot table and the scale table are fixed for the
+    // whole decode: read them before waiting for the previous kernel
     if (MODE == EPI_HEADS && threadIdx.x < NSCALES) stab[threadIdx.x] = g.epi.scale[threadIdx.x];
     build_table<MODE>(g, m0, tab, yrow);
     fence_before();
@@ -302,7 +305,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
     fence_after();
     const uint32_t tmem = tmem_slot;
 
-    // the first stages' copies start before the token operand is built
+    // the first stages' weight copies start before the previous kernel ends
     const int first = nk < STAGES ? nk : STAGES;
     if (threadIdx.x == 0) {
         for (int kc = 0; kc < first; kc++) {
@@ -310,9 +313,11 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
             mbar_expect_tx(&full[kc], stage);
             tma_load(st, &tmW, &full[kc], kc * KC, f0);
             if (DUAL) tma_load(st + A_BYTES, &tmW2, &full[kc], kc * KC, f0);
-            if (!resident) tma_load(st + NACC * A_BYTES, &tmX, &full[kc], kc * KC, m0);
         }
     }
+    pdl_wait();                                        // activations are ready from here on
+    if (threadIdx.x == 0 && !resident)
+        for (int kc = 0; kc < first; kc++) tma_load(smem + kc * stage + NACC * A_BYTES, &tmX, &full[kc], kc * KC, m0);
     if (resident) {
         build_tokens(g, m0, res, yrow);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -533,18 +538,24 @@ bool gemm_tc(const GemmArgs &g, cudaStream_t s)
     dim3 grid((g.N + TM - 1) / TM, (g.M + NT - 1) / NT);
     size_t smem = smem_bytes(dual, resident, g.K);
     int *st = g.status;
+    dim3 block(NTHREADS);
+    cudaError_t e;
     switch (g.epi.mode) {
-    case EPI_SWIGLU: k_gemm_tc<true, EPI_SWIGLU><<<grid, NTHREADS, smem, s>>>(tw, tw2, tx, g, st); break;
-    case EPI_STORE: k_gemm_tc<false, EPI_STORE><<<grid, NTHREADS, smem, s>>>(tw, tw2, tx, g, st); break;
-    case EPI_QKV: k_gemm_tc<false, EPI_QKV><<<grid, NTHREADS, smem, s>>>(tw, tw2, tx, g, st); break;
-    case EPI_RESID: k_gemm_tc<false, EPI_RESID><<<grid, NTHREADS, smem, s>>>(tw, tw2, tx, g, st); break;
-    case EPI_RESID_BASE: k_gemm_tc<false, EPI_RESID_BASE><<<grid, NTHREADS, smem, s>>>(tw, tw2, tx, g, st); break;
-    case EPI_BIAS_SILU: k_gemm_tc<false, EPI_BIAS_SILU><<<grid, NTHREADS, smem, s>>>(tw, tw2, tx, g, st); break;
-    case EPI_SET_BIAS: k_gemm_tc<false, EPI_SET_BIAS><<<grid, NTHREADS, smem, s>>>(tw, tw2, tx, g, st); break;
-    case EPI_HEADS: k_gemm_tc<false, EPI_HEADS><<<grid, NTHREADS, smem, s>>>(tw, tw2, tx, g, st); break;
+    case EPI_SWIGLU: e = launch_pdl(k_gemm_tc<true, EPI_SWIGLU>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_STORE: e = launch_pdl(k_gemm_tc<false, EPI_STORE>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_QKV: e = launch_pdl(k_gemm_tc<false, EPI_QKV>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_RESID: e = launch_pdl(k_gemm_tc<false, EPI_RESID>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_RESID_BASE:
+        e = launch_pdl(k_gemm_tc<false, EPI_RESID_BASE>, grid, block, smem, s, tw, tw2, tx, g, st);
+        break;
+    case EPI_BIAS_SILU:
+        e = launch_pdl(k_gemm_tc<false, EPI_BIAS_SILU>, grid, block, smem, s, tw, tw2, tx, g, st);
+        break;
+    case EPI_SET_BIAS: e = launch_pdl(k_gemm_tc<false, EPI_SET_BIAS>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_HEADS: e = launch_pdl(k_gemm_tc<false, EPI_HEADS>, grid, block, smem, s, tw, tw2, tx, g, st); break;
     default: return false;
     }
-    return true;
+    return e == cudaSuccess;
 }
 
 }  // namespace psw

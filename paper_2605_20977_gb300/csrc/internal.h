@@ -55,6 +55,26 @@ __host__ __device__ inline int tok_make(int slot, int pos) { return (slot << 24)
 // Caches a kernel can name.
 enum CacheSel { CS_NONE = -1, CS_K1 = 0, CS_V1, CS_K2, CS_V2, CS_KA, CS_VA, CS_QA, CS_CK, CS_CV, CS_XK, CS_XV };
 
+// Launch with programmatic dependent launch allowed: the kernel may begin
+// while its predecessor in the stream finishes, and must execute
+// griddepcontrol.wait before it reads or writes anything that predecessor
+// touches (kernels launched this way do so).
+template <typename Kern, typename... Args>
+inline cudaError_t launch_pdl(Kern k, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // ---------------------------------------------------------------- GEMM
 // Y[m][n] = sum_k A[m][k] * Wt[n][k]  (A compact token-major, Wt the
 // transposed projection, both in the compute type), FP32 accumulation in

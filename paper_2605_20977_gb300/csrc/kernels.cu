@@ -218,6 +218,8 @@ __global__ void k_attention(AttnArgs a)
     const Slot &s = a.slots[tok_slot(tk)];
     int p = tok_pos(tk);
     int pi = p / s.W, pj = p % s.W, w = (a.k - 1) >> 1, kk = a.k * a.k;
+    pdl_trigger();
+    pdl_wait();                                        // queries, keys and values are ready from here on
     const T *q = a.q_sel == CS_NONE ? (const T *)a.Q + (long)tokn * a.d + h * DH
                                     : cache_row<const T>(s, a.q_sel, 0, p, a.d) + h * DH;
     for (int e = lane; e < DH; e += 32) qs[wib][e] = to_f<T>(q[e]);
@@ -311,9 +313,9 @@ static void attention_t(const AttnArgs &a, cudaStream_t s)
     int dh = a.d / a.nh;
     int blocks = cdiv((long)a.n * a.nh, 4);
     switch (dh) {
-    case 32: k_attention<T, 32><<<blocks, 128, 0, s>>>(a); break;
-    case 64: k_attention<T, 64><<<blocks, 128, 0, s>>>(a); break;
-    case 128: k_attention<T, 128><<<blocks, 128, 0, s>>>(a); break;
+    case 32: launch_pdl(k_attention<T, 32>, dim3(blocks), dim3(128), 0, s, a); break;
+    case 64: launch_pdl(k_attention<T, 64>, dim3(blocks), dim3(128), 0, s, a); break;
+    case 128: launch_pdl(k_attention<T, 128>, dim3(blocks), dim3(128), 0, s, a); break;
     default: break;   // rejected at context creation
     }
 }

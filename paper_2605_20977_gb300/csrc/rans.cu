@@ -14,6 +14,7 @@
 // u16 H, u16 W, u16 C, u16 0, u32 offsets[C + 1]; each stream is u32 state[32]
 // followed by its words in decoding order, padded to 4 bytes.
 #include "internal.h"
+#include "device_common.cuh"
 
 #include <math.h>
 #include <stdlib.h>
@@ -302,7 +303,9 @@ __global__ void k_rans_dec_step(CoderDev cd, const Slot *__restrict__ S, int nsl
     int b = wi / C, c = wi % C;
     int2 r = kn[b];
     int k0 = r.x, n = r.y;
+    pdl_trigger();
     if (n <= 0) return;
+    pdl_wait();                                        // this step's scale indices and means are ready
     const Slot &sl = S[b];
     const uint8_t *__restrict__ bs = sl.bs;
     const int *__restrict__ order = sl.order;
@@ -374,7 +377,7 @@ void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const i
 {
     int warps = nslots * C;
     if (warps <= 0) return;
-    k_rans_dec_step<<<(warps * 32 + 127) / 128, 128, 0, s>>>(cd, S, nslots, kn, C);
+    launch_pdl(k_rans_dec_step, dim3((warps * 32 + 127) / 128), dim3(128), 0, s, cd, S, nslots, kn, C);
 }
 
 // After the last step every lane must be back at the initial state and

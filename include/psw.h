@@ -214,6 +214,30 @@ psw_status psw_rans_decode(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd,
                            const uint8_t *bitstream_dev, size_t len, const uint8_t *idx_dev,
                            const int32_t *m_dev, int16_t *yhat_out_dev, void *stream);
 
+/* Coder-only encoder that allocates no device memory (the paper has no
+ * counterpart: this is a deployment convenience).  Some callers cannot call
+ * cudaMalloc at the point where they encode: code that runs while a CUDA
+ * graph is being recorded, processes whose device memory is handed out
+ * entirely by another allocator or capped by a quota, and latency-critical
+ * loops that forbid allocation after warm-up.  This entry point does the
+ * work of psw_rans_encode (same inputs, same container bytes) without a
+ * psw_seq: its scratch (schedule order, word buffers, stream lengths,
+ * states) lives in one static device array of about 9.2 MiB that every GPU
+ * loading this library holds until the process exits.
+ *   Limits: H*W <= 32768, C <= 256, H*W*C <= 1572864 (one 68 x 120 x 192
+ *   latent frame); larger frames return PSW_ERR_INVALID.
+ *   The first call on a device looks up the array's device address for that
+ *   device; make that first call before any stream capture on the device.
+ *   Every call shares the array (the previous call's contents remain; the
+ *   call clears what it needs), so calls whose GPU work overlaps -- on two
+ *   streams, or from two host threads -- race; serialise them.
+ *   Calls no cudaMalloc/cudaFree and no allocating library routine.
+ *   Returns PSW_ERR_CAPACITY if the container exceeds cap (len_out still
+ *   receives its size).  Synchronises `stream`. */
+psw_status psw_rans_encode_noalloc(const psw_ctx *ctx, const psw_frame_desc *fd, const int16_t *yhat_dev,
+                                   const uint8_t *idx_dev, const int32_t *m_dev, uint8_t *bitstream_dev,
+                                   size_t cap, size_t *len_out, void *stream);
+
 /* Instrumentation (not in the paper; measurement support).
  * psw_launch_count: kernels this context has launched so far.
  * psw_profile_begin: from now on every kernel launch of this context is

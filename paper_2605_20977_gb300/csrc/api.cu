@@ -939,6 +939,16 @@ void encode_symbols(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, uint8_t *b
 
 }  // namespace
 
+bool psw_coder_view(const psw_ctx *c, int *C, int *mask, const uint32_t **cdf, const int **meta)
+{
+    if (!c) return false;
+    *C = c->md.C;
+    *mask = c->md.mask;
+    *cdf = c->d_cdf;
+    *meta = c->d_meta;
+    return true;
+}
+
 // ====================================================================== ABI
 
 extern "C" {

@@ -226,3 +226,11 @@ void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const i
 void launch_rans_dec_finish(const Slot *S, int nslots, int C, cudaStream_t s);
 
 }  // namespace psw
+
+// The coder tables of a context (for entry points outside api.cu): channels,
+// mask, device CDF slots and table metadata.  False for a null context.
+bool psw_coder_view(const psw_ctx *ctx, int *C, int *mask, const uint32_t **cdf, const int **meta);
+
+namespace psw {
+
+}  // namespace psw

@@ -20,6 +20,11 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <vector>
+
 namespace psw {
 
 static constexpr uint32_t MAGIC = 0x31575350u;
@@ -405,3 +410,120 @@ void launch_rans_dec_finish(const Slot *S, int nslots, int C, cudaStream_t s)
 }
 
 }  // namespace psw
+
+// ---------------------------------------------------------------- encoder without allocation
+//
+// psw_rans_encode_noalloc: the coder-only encoder of psw_rans_encode, but
+// with every scratch buffer (schedule order, per-stream word buffers, stream
+// lengths and offsets, final states, total, status) carved from one
+// file-scope device array instead of a sequence's allocations.  The array
+// is part of the loaded module: every GPU that loads this library holds it
+// (NOALLOC_BYTES, about 9.2 MiB) until the process exits.
+
+namespace psw {
+namespace {
+
+constexpr size_t NOALLOC_MAX_SYMBOLS = 1572864;      // H*W*C of one 68 x 120 x 192 latent frame
+constexpr int NOALLOC_MAX_HW = 32768;
+constexpr int NOALLOC_MAX_C = 256;
+constexpr size_t NA_SLOT = 0;                                             // one Slot
+constexpr size_t NA_ORDER = 512;                                          // int[MAX_HW]
+constexpr size_t NA_NW = NA_ORDER + 4 * (size_t)NOALLOC_MAX_HW;           // u32[2C + 1]
+constexpr size_t NA_STATES = NA_NW + 2304;                                // u32[32 C]
+constexpr size_t NA_TOTAL = NA_STATES + 4 * 32 * (size_t)NOALLOC_MAX_C;   // u64
+constexpr size_t NA_STATUS = NA_TOTAL + 256;                              // int
+constexpr size_t NA_WORDS = NA_STATUS + 256;                              // u16[3 HW C + 64 C]
+constexpr size_t NOALLOC_BYTES = NA_WORDS + 2 * (3 * NOALLOC_MAX_SYMBOLS + 64 * (size_t)NOALLOC_MAX_C);
+
+static_assert(sizeof(Slot) <= 512, "slot record must fit its reserved space");
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_na_mu;
+std::map<int, unsigned char *> g_na_addr;    // device -> address of g_noalloc_scratch on it
+
+}  // namespace
+}  // namespace psw
+
+extern "C" psw_status psw_rans_encode_noalloc(const psw_ctx *ctx, const psw_frame_desc *fd, const int16_t *yhat_dev,
+                                              const uint8_t *idx_dev, const int32_t *m_dev, uint8_t *bitstream_dev,
+                                              size_t cap, size_t *len_out, void *stream)
+{
+    using namespace psw;
+    int C = 0, mask = 0;
+    const uint32_t *cdf = nullptr;
+    const int *meta = nullptr;
+    if (!psw_coder_view(ctx, &C, &mask, &cdf, &meta)) return PSW_ERR_INVALID;
+    if (!fd || !yhat_dev || !idx_dev || !m_dev || !bitstream_dev || !len_out) return PSW_ERR_INVALID;
+    if (fd->H < 1 || fd->W < 1 || (fd->schedule != PSW_SCHED_WAVEFRONT && fd->schedule != PSW_SCHED_RASTER))
+        return PSW_ERR_INVALID;
+    if (fd->schedule == PSW_SCHED_RASTER && mask == 1) return PSW_ERR_INVALID;
+    size_t HW = (size_t)fd->H * fd->W;
+    if (fd->H > 65535 || fd->W > 65535 || HW > (size_t)NOALLOC_MAX_HW || C > NOALLOC_MAX_C ||
+        HW * (size_t)C > NOALLOC_MAX_SYMBOLS)
+        return PSW_ERR_INVALID;                       // beyond the static scratch
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PSW_ERR_CUDA;
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        auto it = g_na_addr.find(dev);
+        if (it == g_na_addr.end()) {
+            // once per device, with that device current: the array's device
+            // address (its host-side name is only a stand-in)
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PSW_ERR_CUDA;
+            it = g_na_addr.emplace(dev, (unsigned char *)p).first;
+        }
+        base = it->second;
+    }
+    // schedule order (host), then the slot record the encoder reads
+    std::vector<int> order(HW);
+    if (fd->schedule == PSW_SCHED_RASTER) {
+        for (size_t p = 0; p < HW; p++) order[p] = (int)p;
+    } else {
+        auto lab = [&](int i, int j) { return mask == 1 ? ((i % 4) + (j % 4)) % 4 : 2 * i + j; };
+        int maxl = 0;
+        for (int i = 0; i < fd->H; i++)
+            for (int j = 0; j < fd->W; j++) maxl = std::max(maxl, lab(i, j));
+        std::vector<int> cnt(maxl + 2, 0);
+        for (int i = 0; i < fd->H; i++)
+            for (int j = 0; j < fd->W; j++) cnt[lab(i, j) + 1]++;
+        for (int t = 1; t <= maxl + 1; t++) cnt[t] += cnt[t - 1];
+        for (int i = 0; i < fd->H; i++)
+            for (int j = 0; j < fd->W; j++) order[cnt[lab(i, j)]++] = i * fd->W + j;
+    }
+    Slot sl;
+    memset(&sl, 0, sizeof(sl));
+    sl.H = fd->H; sl.W = fd->W; sl.stride = (int)HW; sl.sched = fd->schedule;
+    sl.y = const_cast<int16_t *>(yhat_dev);
+    sl.idx = const_cast<uint8_t *>(idx_dev);
+    sl.m = const_cast<int32_t *>(m_dev);
+    sl.order = (const int *)(base + NA_ORDER);
+    sl.status = (int *)(base + NA_STATUS);
+    int cap_words = 3 * (int)HW + 64;
+    uint16_t *words = (uint16_t *)(base + NA_WORDS);
+    uint32_t *nw = (uint32_t *)(base + NA_NW), *states = (uint32_t *)(base + NA_STATES);
+    uint64_t *total = (uint64_t *)(base + NA_TOTAL);
+    // the slot record and order are copied from pageable host memory (the
+    // copies are complete when cudaMemcpyAsync returns); the status word and
+    // total start at zero for every call
+    if (cudaMemcpyAsync(base + NA_SLOT, &sl, sizeof(Slot), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(base + NA_ORDER, order.data(), HW * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(base + NA_TOTAL, 0, 512, s) != cudaSuccess)
+        return PSW_ERR_CUDA;
+    CoderDev cd{cdf, meta};
+    launch_rans_encode(cd, (const Slot *)(base + NA_SLOT), 0, (int)HW, C, words, cap_words, nw, states, s);
+    launch_rans_assemble(fd->H, fd->W, C, fd->schedule, words, cap_words, nw, states, bitstream_dev, cap, total,
+                         (int *)(base + NA_STATUS), s);
+    uint64_t h_total = 0;
+    int h_status = 0;
+    if (cudaMemcpyAsync(&h_total, total, sizeof(h_total), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&h_status, base + NA_STATUS, sizeof(h_status), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return PSW_ERR_CUDA;
+    *len_out = (size_t)h_total;
+    if (h_status & ST_CAPACITY) return PSW_ERR_CAPACITY;
+    return PSW_OK;
+}

@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "CORRUPT", 5: "TI
 EXPORTS = ["psw_weights_count", "psw_create", "psw_destroy", "psw_last_error", "psw_ctx_bytes", "psw_seq_bytes",
            "psw_seq_create", "psw_seq_reset", "psw_seq_destroy", "psw_bitstream_capacity", "psw_encode_params",
            "psw_decode_frame", "psw_decode_batch", "psw_rate", "psw_quantize", "psw_scale_table", "psw_cdf_table",
-           "psw_rans_encode", "psw_rans_decode", "psw_launch_count", "psw_profile_begin", "psw_profile_end"]
+           "psw_rans_encode", "psw_rans_decode", "psw_launch_count", "psw_profile_begin", "psw_profile_end",
+           "psw_rans_encode_noalloc"]
 
 
 class ModelDesc(ct.Structure):
@@ -85,6 +86,7 @@ def load(path: str = LIB_PATH):
             "psw_launch_count": (ct.c_long, [P]),
             "psw_profile_begin": (I, [P]),
             "psw_profile_end": (I, [P, ct.POINTER(KernelStat), I, ct.POINTER(I)]),
+            "psw_rans_encode_noalloc": (I, [P, FD, P, P, P, P, S, ct.POINTER(S), P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -192,6 +194,15 @@ class Context:
         f = np.zeros(4096, np.uint32)
         self._check(self.lib.psw_cdf_table(self.h, l, f.ctypes.data, 4096, ct.byref(n), ct.byref(T)))
         return f[:n.value].copy(), T.value
+
+    def rans_encode_noalloc(self, fd: FrameDesc, y, idx, m, bitstream, stream=None, check: bool = True):
+        """Coder-only encode without device allocation; returns (status, length)."""
+        n = ct.c_size_t(0)
+        st = self.lib.psw_rans_encode_noalloc(self.h, ct.byref(fd), _ptr(y), _ptr(idx), _ptr(m), _ptr(bitstream),
+                                              bitstream.numel(), ct.byref(n), _stream(stream))
+        if check:
+            self._check(st)
+        return st, int(n.value)
 
     def launch_count(self) -> int:
         return int(self.lib.psw_launch_count(self.h))

@@ -238,6 +238,25 @@ psw_status psw_rans_encode_noalloc(const psw_ctx *ctx, const psw_frame_desc *fd,
                                    const uint8_t *idx_dev, const int32_t *m_dev, uint8_t *bitstream_dev,
                                    size_t cap, size_t *len_out, void *stream);
 
+/* Decode engine (not in the paper; an implementation choice).  Both engines
+ * run the same per-tile arithmetic, so their results are bit-identical.
+ *   PSW_ENGINE_GRAPH       every phase of every step is its own kernel, the
+ *                          launches recorded once per batch shape in CUDA
+ *                          graphs and replayed.
+ *   PSW_ENGINE_PERSISTENT  one cooperative launch, one block per SM, walks
+ *                          all steps (Sec. 3.2 schedule) with a grid-wide
+ *                          barrier between phases; BF16 contexts only.
+ *   PSW_ENGINE_AUTO        persistent where the context supports it, else
+ *                          graphs (the default).
+ * psw_set_engine returns PSW_ERR_INVALID for an unknown engine or for
+ * PSW_ENGINE_PERSISTENT on an FP32 context; a decode asked to run
+ * persistently on a device that cannot co-schedule the blocks returns
+ * PSW_ERR_CUDA.  psw_last_engine: the engine of the context's last decode
+ * (0 = individual launches, as under psw_profile_begin). */
+typedef enum { PSW_ENGINE_AUTO = 0, PSW_ENGINE_GRAPH = 1, PSW_ENGINE_PERSISTENT = 2 } psw_engine;
+psw_status psw_set_engine(psw_ctx *ctx, int engine);
+int psw_last_engine(const psw_ctx *ctx);
+
 /* Instrumentation (not in the paper; measurement support).
  * psw_launch_count: kernels this context has launched so far.
  * psw_profile_begin: from now on every kernel launch of this context is

@@ -126,6 +126,10 @@ struct GraphRec {
     std::vector<cudaGraphExec_t> exec;
     int *d_tok = nullptr;
     int2 *d_kn = nullptr;
+    int *d_step = nullptr;             // persistent decoder: step offsets [Tmax], counts [Tmax]
+    int Tmax = 0;
+    double ntok = 0, ntok_prev = 0;    // tokens over all steps; those that also run Spatial Module 1
+    bool persist = false;              // exec holds the prologue only; the steps run persistently
     long launches = 0;
 };
 
@@ -135,8 +139,10 @@ void graph_free(GraphRec &g)
     g.exec.clear();
     cudaFree(g.d_tok);
     cudaFree(g.d_kn);
+    cudaFree(g.d_step);
     g.d_tok = nullptr;
     g.d_kn = nullptr;
+    g.d_step = nullptr;
 }
 
 }  // namespace
@@ -174,6 +180,25 @@ struct psw_ctx {
     cudaStream_t cap_stream = nullptr;
     std::map<std::vector<long>, GraphRec> graphs;
     bool use_graphs = true;
+    // persistent decoder: the program of one step (rebuilt when the
+    // workspace moves), its kernel's shared memory and grid, barrier words
+    int engine = PSW_ENGINE_AUTO;
+    int last_engine = 0;               // engine of the last decode (0: direct launches)
+    ProgramBuilder *prog = nullptr;
+    int prog_gen = -1;
+    bool prog_ok = false;
+    const Op *p_ops = nullptr;
+    int p_nops = 0;
+    const void *p_maps = nullptr;
+    int p_nmaps = 0;
+    double p_flops_tok[2] = {0, 0};    // algorithmic FLOPs per token of the phases on this / the previous step's tokens
+    double p_bytes_tok[2] = {0, 0};    // their attention bytes per token
+    double p_wbytes = 0;               // weight bytes streamed per step
+    int *d_step = nullptr;             // direct-launch step tables
+    size_t step_cap = 0;
+    size_t p_smem = 0;
+    int p_grid = 0;
+    unsigned *d_pbar = nullptr;        // [0]: barrier counter, [1]: abort flag
     std::string err;
     std::vector<psw_seq *> seqs;
     // instrumentation
@@ -232,9 +257,9 @@ const float *W(const psw_ctx *c, long off) { return c->w + off; }
 // ---------------------------------------------------------------- instrumentation
 
 // Kernel classes reported by psw_profile_end.
-enum KClass { K_GEMM_TC, K_GEMM_SIMT, K_ATTN, K_NORM, K_EMBED, K_HEADS, K_RANS, K_OTHER, K_NCLASS };
+enum KClass { K_GEMM_TC, K_GEMM_SIMT, K_ATTN, K_NORM, K_EMBED, K_HEADS, K_RANS, K_OTHER, K_PERSIST, K_NCLASS };
 const char *const kclass_name[K_NCLASS] = {"gemm_tc", "gemm_simt", "attention", "rmsnorm",
-                                          "embed", "heads", "rans", "other"};
+                                          "embed", "heads", "rans", "other", "persistent"};
 
 cudaEvent_t ev_get(psw_ctx *c)
 {
@@ -456,6 +481,8 @@ struct Pass {
     cudaStream_t s;
     const Slot *S;                     // device slot table
     bool *failed;
+    ProgramBuilder *rec = nullptr;     // set: record phases of the persistent decoder instead of launching
+    int tokset = TS_CUR;               // which step's tokens recorded phases work on
 };
 
 // One projection; asrc / a_stream / a_gain say where its token operand
@@ -470,6 +497,13 @@ void gemm_any(const Pass &P, int asrc, const float *xrows, const float *a_gain, 
     g.Wt = Wt; g.Wt2 = Wt2; g.M = M; g.N = N; g.K = K; g.epi = e;
     g.epi.slots = P.S;
     g.status = P.c->d_status;
+    if (P.rec) {
+        if (!program_gemm(P.rec, g, P.tokset)) *P.failed = true;
+        double nw = Wt2 ? 2.0 : 1.0;
+        P.c->p_flops_tok[P.tokset] += 2.0 * nw * N * K;
+        P.c->p_wbytes += nw * N * K * 2.0;
+        return;
+    }
     bool tc = gemm_tc_supported(P.c->prec, N, K, asrc);
     if (!tc && asrc != A_DIRECT) P.c->launches++;      // the operand-preparation kernel
     double es = P.c->prec == P_BF16 ? 2.0 : 4.0, nw = Wt2 ? 2.0 : 1.0;
@@ -556,6 +590,14 @@ AttnArgs attn_args(const Pass &P, const int *tok, int n, const void *Qp, int q_s
 void attention(const Pass &P, const AttnArgs &a)
 {
     const psw_model_desc &m = P.c->md;
+    if (P.rec) {
+        program_attn(P.rec, a, P.tokset);
+        AttnArgs one = a;
+        one.n = 1;
+        P.c->p_flops_tok[P.tokset] += attn_flops(m, 1, attn_keys(a, m.Tf));
+        P.c->p_bytes_tok[P.tokset] += attn_bytes(m, one);
+        return;
+    }
     LAUNCH(P, K_ATTN, attn_flops(m, a.n, attn_keys(a, m.Tf)), attn_bytes(m, a), launch_attention(P.c->prec, a, P.s));
 }
 
@@ -665,6 +707,36 @@ void run_acc_sm2_heads(const Pass &P, const int *tok, int n)
     eh.gmu = W(c, c->lay.gamma_mu); eh.bmu = W(c, c->lay.beta_mu);
     eh.gsg = W(c, c->lay.gamma_sig); eh.bsg = W(c, c->lay.beta_sig);
     gemm_call(P, c->Hid, 2 * d, c->Wh2, nullptr, n, 2 * m.C, 2 * d, eh);
+}
+
+// The persistent decoder's program for the current workspace: the phases
+// of one step, recorded from the same pass functions the graph path
+// launches (so both run identical tiles).  Built once per workspace
+// generation; false if the context cannot run it.
+bool ensure_program(psw_ctx *c)
+{
+    if (c->prog_gen == c->ws_gen) return c->prog_ok;
+    program_free(c->prog);
+    c->prog = nullptr;
+    c->prog_ok = false;
+    c->prog_gen = c->ws_gen;
+    if (c->prec != P_BF16 || c->ws_rows == 0) return false;
+    c->prog = program_new((int)c->ws_rows);
+    c->p_flops_tok[0] = c->p_flops_tok[1] = c->p_bytes_tok[0] = c->p_bytes_tok[1] = c->p_wbytes = 0;
+    bool failed = false;
+    Pass P{c, nullptr, c->d_slots, &failed};
+    P.rec = c->prog;
+    P.tokset = TS_PREV;
+    run_sm1(P, nullptr, 1);
+    P.tokset = TS_CUR;
+    run_acc_sm2_heads(P, nullptr, 1);
+    program_rans(c->prog);
+    if (failed) return false;
+    if (!program_upload(c->prog, &c->p_ops, &c->p_nops, &c->p_maps, &c->p_nmaps, &c->p_smem)) return false;
+    if (!persist_prepare(c->p_smem, &c->p_grid)) return false;
+    if (!c->d_pbar && cudaMalloc(&c->d_pbar, 2 * sizeof(unsigned)) != cudaSuccess) return false;
+    c->prog_ok = true;
+    return true;
 }
 
 CoderDev coder(const psw_ctx *c) { return CoderDev{c->d_cdf, c->d_meta}; }
@@ -807,6 +879,32 @@ void enqueue_decode(psw_ctx *c, const DecodePlan &D, const int *d_tok, const int
     }
 }
 
+// Steps [0, Tmax) of a planned decode on the persistent decoder, then the
+// coder's final check.  ntok / ntok_prev: tokens over all steps, and those
+// that also pass Spatial Module 1 (the algorithmic FLOPs of the launch).
+psw_status persist_run(psw_ctx *c, const int *d_tok, const int *d_step, const int2 *d_kn, int n, int Tmax,
+                       double ntok, double ntok_prev, cudaStream_t s)
+{
+    CK_CUDA(c, cudaMemsetAsync(c->d_pbar, 0, 2 * sizeof(unsigned), s));
+    PersistArgs pa{};
+    pa.ops = c->p_ops; pa.nops = c->p_nops; pa.maps = c->p_maps; pa.nmaps = c->p_nmaps;
+    pa.tok = d_tok; pa.step_off = d_step; pa.step_n = d_step + Tmax;
+    pa.kn = d_kn; pa.nslots = n;
+    pa.cd = coder(c); pa.slots = c->d_slots; pa.C = c->md.C;
+    pa.t0 = 0; pa.t1 = Tmax;
+    pa.bar = c->d_pbar; pa.abort_g = (int *)(c->d_pbar + 1); pa.status = c->d_status;
+    double flops = c->p_flops_tok[TS_CUR] * ntok + c->p_flops_tok[TS_PREV] * ntok_prev;
+    double bytes = c->p_wbytes * Tmax + c->p_bytes_tok[TS_CUR] * ntok + c->p_bytes_tok[TS_PREV] * ntok_prev;
+    {
+        Scope sc(c, s, K_PERSIST, flops, bytes);
+        if (!persist_launch(pa, c->p_grid, c->p_smem, s))
+            return fail(c, PSW_ERR_CUDA, "persistent decoder launch: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    Scope sc(c, s, K_RANS, 0.0, (double)n * c->md.C * 128.0);
+    launch_rans_dec_finish(c->d_slots, n, c->md.C, s);
+    return PSW_OK;
+}
+
 // Decode n frames of n sequences together (the engine behind
 // psw_decode_frame and psw_decode_batch).
 psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_desc *fds,
@@ -830,14 +928,15 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
         sl.bs = bs[b]; sl.len = lens[b]; sl.zhat = zhat[b];
         c->h_slots[b] = sl;
     }
-    // graph key: the workspace generation and the batch shape
-    std::vector<long> key{0, (long)n};
+    // graph key: the workspace generation, the engine and the batch shape
+    bool failed = false;
+    bool graph = c->use_graphs && !c->prof;
+    bool want = c->engine != PSW_ENGINE_GRAPH && c->prec == P_BF16;
+    std::vector<long> key{0, (long)n, (long)want};
     for (int b = 0; b < n; b++) {
         key.push_back((long)(uintptr_t)qs[b]);
         key.push_back(((long)fds[b].H << 32) | ((long)fds[b].W << 2) | fds[b].schedule);
     }
-    bool failed = false;
-    bool graph = c->use_graphs && !c->prof;
     GraphRec *gr = nullptr;
     key[0] = c->ws_gen;
     if (graph) {
@@ -853,18 +952,44 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
         if ((st = ensure_workspace(c, rows))) return st;
         key[0] = c->ws_gen;
     }
+    bool persist = want && ensure_program(c);
+    if (want && !persist && c->engine == PSW_ENGINE_PERSISTENT)
+        return fail(c, PSW_ERR_CUDA, "the persistent decoder could not be set up for this context");
+    // persistent decoder: per-step token offsets and counts, token totals
+    std::vector<int> steps;
+    double ntok = 0, ntok_prev = 0;
+    if (!gr && persist) {
+        steps.assign(2 * (size_t)std::max(D.Tmax, 1), 0);
+        for (int t = 0; t < D.Tmax; t++) {
+            steps[t] = D.step_off[t];
+            steps[D.Tmax + t] = D.step_n[t];
+            ntok += D.step_n[t];
+            if (t + 1 < D.Tmax) ntok_prev += D.step_n[t];
+        }
+    }
     if ((st = upload_slots(c, qs, n, s))) return st;
     if (graph) {
         if (!gr) {
             GraphRec g;
+            g.persist = persist;
+            g.Tmax = D.Tmax;
+            g.ntok = ntok;
+            g.ntok_prev = ntok_prev;
             CK_CUDA(c, cudaMalloc(&g.d_tok, D.tok.size() * sizeof(int)));
             CK_CUDA(c, cudaMalloc(&g.d_kn, std::max<size_t>(D.kn.size(), 1) * sizeof(int2)));
             CK_CUDA(c, cudaMemcpy(g.d_tok, D.tok.data(), D.tok.size() * sizeof(int), cudaMemcpyHostToDevice));
             if (!D.kn.empty())
                 CK_CUDA(c, cudaMemcpy(g.d_kn, D.kn.data(), D.kn.size() * sizeof(int2), cudaMemcpyHostToDevice));
+            if (persist) {
+                CK_CUDA(c, cudaMalloc(&g.d_step, steps.size() * sizeof(int)));
+                CK_CUDA(c, cudaMemcpy(g.d_step, steps.data(), steps.size() * sizeof(int), cudaMemcpyHostToDevice));
+            }
             long l0 = c->launches;
-            for (int t0 = 0; t0 < std::max(D.Tmax, 1); t0 += SEG_STEPS) {
-                int t1 = std::min(D.Tmax, t0 + SEG_STEPS);
+            // persistent: one graph with the prologues and coder set-up;
+            // otherwise every step, in segments of SEG_STEPS
+            int span = persist ? 1 : std::max(D.Tmax, 1), seg = persist ? 1 : SEG_STEPS;
+            for (int t0 = 0; t0 < span; t0 += seg) {
+                int t1 = persist ? 0 : std::min(D.Tmax, t0 + SEG_STEPS);
                 cudaGraph_t gph;
                 cudaGraphExec_t ex = nullptr;
                 cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
@@ -890,14 +1015,33 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
         }
         for (cudaGraphExec_t ex : gr->exec) CK_CUDA(c, cudaGraphLaunch(ex, s));
         c->launches += gr->launches;
+        if (gr->persist &&
+            (st = persist_run(c, gr->d_tok, gr->d_step, gr->d_kn, n, gr->Tmax, gr->ntok, gr->ntok_prev, s)))
+            return st;
+        c->last_engine = gr->persist ? PSW_ENGINE_PERSISTENT : PSW_ENGINE_GRAPH;
     } else {
         if ((st = grow_tokens(c, D.tok.size(), std::max<size_t>(D.kn.size(), 1)))) return st;
         CK_CUDA(c, cudaMemcpyAsync(c->d_tok, D.tok.data(), D.tok.size() * sizeof(int), cudaMemcpyHostToDevice, s));
         if (!D.kn.empty())
             CK_CUDA(c, cudaMemcpyAsync(c->d_kn, D.kn.data(), D.kn.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-        enqueue_decode(c, D, c->d_tok, c->d_kn, s, &failed, 0, D.Tmax);
+        if (persist) {
+            if (steps.size() > c->step_cap) {
+                CK_CUDA(c, cudaDeviceSynchronize());
+                cudaFree(c->d_step);
+                c->d_step = nullptr; c->step_cap = 0;
+                CK_CUDA(c, cudaMalloc(&c->d_step, steps.size() * sizeof(int)));
+                c->step_cap = steps.size();
+            }
+            CK_CUDA(c, cudaMemcpyAsync(c->d_step, steps.data(), steps.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+            enqueue_decode(c, D, c->d_tok, c->d_kn, s, &failed, 0, 0);
+            if (!failed && (st = persist_run(c, c->d_tok, c->d_step, c->d_kn, n, D.Tmax, ntok, ntok_prev, s)))
+                return st;
+        } else {
+            enqueue_decode(c, D, c->d_tok, c->d_kn, s, &failed, 0, D.Tmax);
+        }
         CK_CUDA(c, cudaStreamSynchronize(s));   // host token lists are reused by the next call
         if (failed) return fail(c, PSW_ERR_CUDA, "a GEMM launch could not be prepared");
+        c->last_engine = persist ? PSW_ENGINE_PERSISTENT : 0;
     }
     CK_CUDA(c, cudaGetLastError());
     for (int b = 0; b < n; b++) {
@@ -1031,6 +1175,9 @@ void psw_destroy(psw_ctx *c)
     if (!c) return;
     while (!c->seqs.empty()) psw_seq_destroy(c->seqs.back());
     for (auto &kv : c->graphs) graph_free(kv.second);
+    program_free(c->prog);
+    cudaFree(c->d_pbar);
+    cudaFree(c->d_step);
     cudaFree(c->w); cudaFree(c->wmat); cudaFree(c->d_cdf); cudaFree(c->d_meta); cudaFree(c->d_scale);
     cudaFree(c->rate_buf); cudaFree(c->d_slots); cudaFree(c->d_status); cudaFree(c->d_tok); cudaFree(c->d_kn);
     cudaFree(c->Xn); cudaFree(c->Q); cudaFree(c->O); cudaFree(c->Hid);
@@ -1315,6 +1462,19 @@ psw_status psw_rans_decode(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, con
 }
 
 long psw_launch_count(const psw_ctx *c) { return c ? c->launches : 0; }
+
+psw_status psw_set_engine(psw_ctx *c, int engine)
+{
+    if (!c) return fail(nullptr, PSW_ERR_INVALID, "null context");
+    if (engine < PSW_ENGINE_AUTO || engine > PSW_ENGINE_PERSISTENT)
+        return fail(c, PSW_ERR_INVALID, "unknown engine %d", engine);
+    if (engine == PSW_ENGINE_PERSISTENT && c->prec != P_BF16)
+        return fail(c, PSW_ERR_INVALID, "the persistent decoder runs BF16 contexts only");
+    c->engine = engine;
+    return PSW_OK;
+}
+
+int psw_last_engine(const psw_ctx *c) { return c ? c->last_engine : 0; }
 
 psw_status psw_profile_begin(psw_ctx *c)
 {

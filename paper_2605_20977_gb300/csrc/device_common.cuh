@@ -88,6 +88,23 @@ __device__ __forceinline__ void epilogue_store(const Epi &e, int N, int m, int n
     }
 }
 
+// Scale index of sigma: the smallest l with scale[l] >= sigma (float
+// compare), 63 if there is none (or sigma is NaN).  The table increases
+// strictly, so a binary search gives the index a linear scan would.
+__device__ __forceinline__ int scale_index(const float *scale, float sg)
+{
+    int lo = 0, n = NSCALES;
+#pragma unroll
+    for (int it = 0; it < 6; it++) {
+        int half = n >> 1;
+        if (!(scale[lo + half - 1] >= sg)) lo += half;
+        n -= half;
+    }
+    // lo: first index whose entry is >= sg among 0..63, or 63 (the search
+    // never moves past the last entry)
+    return lo;
+}
+
 // Prediction heads' output for channel c = n / 2 of a token (rows 2c and
 // 2c+1 of the interleaved second layer): channel-wise scaling of mu, sigma =
 // exp of the clamped scaled value, then the scale index (smallest table
@@ -102,10 +119,7 @@ __device__ __forceinline__ void heads_pair(const Epi &e, const float *scale, int
     float sg = expf(fminf(fmaxf(e.gsg[c] * ysg + e.bsg[c], LN_SIG_LO), LN_SIG_HI));
     s.mu[o] = mu;
     s.sigma[o] = sg;
-    int l = NSCALES - 1;
-    for (int t = 0; t < NSCALES; t++)
-        if (scale[t] >= sg) { l = t; break; }
-    s.idx[o] = (uint8_t)l;
+    s.idx[o] = (uint8_t)scale_index(scale, sg);
     s.m[o] = (int32_t)rintf(fminf(fmaxf(mu, -32768.0f), 32767.0f));
 }
 

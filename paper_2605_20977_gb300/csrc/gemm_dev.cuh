@@ -1,0 +1,645 @@
+// gemm_dev.cuh -- the device side of the BF16 projection GEMM on the
+// sm_100-family tensor cores (tcgen05.mma, accumulator in tensor memory,
+// operands staged by TMA), as tile functions shared by the one-tile-per-CTA
+// kernel (gemm_tc.cu) and the persistent decoder (persist.cu).
+//
+// Y[token][feature] = sum_k X[token][k] Wt[feature][k].  The projection is
+// the MMA's A operand (M = 128 output features per tile) and the tokens are
+// its B operand (N = 64 tokens per tile), so a decoder step with a few dozen
+// tokens fills one tile and the weights stream through once.  Weights are
+// consumed in 64-element K chunks (one 128-byte swizzle atom) through a
+// TMA ring as deep as the shared-memory budget allows (all chunks of a
+// 384-wide projection).  The token operand either streams through the same ring
+// (compact bf16 rows) or is built by the CTA in shared memory: RMSNorm of the
+// FP32 residual stream rows (the pre-norm of every projection, Sec. 3.1) or
+// the channel-scaled latents (the latent embedding).  One thread issues the
+// MMAs; 256 threads run the epilogue from TMEM (warps w and w + 4 read the
+// same 32 feature rows, half of the token columns each) with the destination
+// rows of the tile's tokens resolved once into shared memory.  Accumulation
+// order is fixed (ascending K chunks, one MMA shape), so every output element
+// is the same function of its row and column whatever the tile, the launch or
+// the kernel it falls in.
+//
+// A tile runs in two parts.  gemm_tile_pre resolves the tile's token table
+// and issues the weight copies of its first ring stages; it reads nothing a
+// previous kernel or phase writes, so callers run it before waiting for
+// their inputs.  gemm_tile_main loads or builds the token operand, runs the
+// MMAs and the epilogue.  The barrier parities (GemmPipe) carry over from tile to
+// tile, so one CTA can run any sequence of tiles of any shapes and ring
+// depths.
+//
+// Every mbarrier wait is bounded (~2 s of globaltimer); on expiry the CTA
+// raises its abort flag, waits (bounded) for its own copies and MMAs and
+// skips the epilogue; the caller reports ST_TIMEOUT.
+#pragma once
+
+#include "internal.h"
+#include "device_common.cuh"
+
+#include <cuda.h>
+
+namespace psw {
+namespace tc {
+
+constexpr int TM = 128;        // output features per tile (MMA M)
+constexpr int NT = 64;         // tokens per tile (MMA N)
+constexpr int KC = 64;         // K elements per stage (128 bytes of bf16)
+constexpr int MAXS = 8;        // ring stages at most (barrier pairs)
+constexpr int RING_BUDGET = 216 * 1024;   // dynamic shared memory of the ring and the resident operand
+constexpr int A_BYTES = TM * KC * 2;
+constexpr int B_BYTES = NT * KC * 2;
+constexpr int KRES_MAX = 512;  // largest K of a token operand built in shared memory
+constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr int NTHREADS = 256;  // 8 warps: warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31
+constexpr int NISS = 4;        // MMA issuers (lane 0 of warps 1..4), one K step of 16 per chunk each
+// tensor-memory columns of a tile: one 64-column accumulator (two for the
+// dual form) per issuer
+__host__ __device__ constexpr uint32_t tile_tcols(bool dual) { return (dual ? 2 : 1) * NT * NISS; }
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtime()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a phase of an mbarrier; false after ~2 s.  The test of an
+// already completed phase is inline; the polling loop is out of line.
+static __device__ __noinline__ bool mbar_wait_slow(uint64_t *b, uint32_t parity)
+{
+    uint64_t t0 = gtime();
+    while (!mbar_try(b, parity))
+        if (gtime() - t0 > WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity)
+{
+    if (mbar_try(b, parity)) return true;
+    return mbar_wait_slow(b, parity);
+}
+
+__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *tm, uint64_t *bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(su32(dst)), "l"(tm), "r"(su32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Orders this thread's view of global memory (including what other threads
+// released to it) before its later tensor-copy reads, and its own generic
+// writes before later async-proxy accesses.
+__device__ __forceinline__ void fence_proxy_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row atoms 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 46;                          // version
+    d |= (uint64_t)2 << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: F32 accumulate, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t dt, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dt), "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t cols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(slot)), "r"(cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_free(uint32_t tmem, uint32_t cols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols) : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float *v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Sum of the issuers' accumulators ((a0 + a1) + a2) + a3 at 16 / 8
+// consecutive columns; accumulator q starts `step` columns after q - 1.
+__device__ __forceinline__ void tmem_sum16(uint32_t addr, uint32_t step, float *v)
+{
+    tmem_ld16(addr, v);
+#pragma unroll
+    for (int q = 1; q < NISS; q++) {
+        float w[16];
+        tmem_ld16(addr + q * step, w);
+#pragma unroll
+        for (int i = 0; i < 16; i++) v[i] += w[i];
+    }
+}
+
+__device__ __forceinline__ void tmem_sum8(uint32_t addr, uint32_t step, float *v)
+{
+    tmem_ld8(addr, v);
+#pragma unroll
+    for (int q = 1; q < NISS; q++) {
+        float w[8];
+        tmem_ld8(addr + q * step, w);
+#pragma unroll
+        for (int i = 0; i < 8; i++) v[i] += w[i];
+    }
+}
+
+// Byte offset of element (row r, column k) of a K-major bf16 operand laid
+// out in 128-byte-swizzled atoms of 64 columns x NT rows.
+__device__ __forceinline__ uint32_t swz(int r, int k)
+{
+    int kc = k >> 6, col = k & 63;
+    uint32_t byte = (uint32_t)col * 2;
+    return (uint32_t)kc * B_BYTES + (uint32_t)r * 128 + ((((byte >> 4) ^ (uint32_t)(r & 7))) << 4) + (byte & 15);
+}
+
+__device__ __forceinline__ uint2 pack4(float a, float b, float c, float d)
+{
+    __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    return make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
+}
+
+// Per-CTA shared state of the engine.
+struct GemmShared {
+    uint64_t full[MAXS], empty[MAXS], done;
+    uint32_t tmem_slot;
+    volatile int abort;
+    float stab[NSCALES];
+    const int16_t *yrow[NT];
+    uintptr_t tab[4][NT];
+};
+
+// Ring state carried from tile to tile.  Each ring stage has its own
+// full/empty barrier pair, and the thread that waits on a barrier keeps the
+// parity of the next completion it needs, so tiles of different ring depths
+// can follow one another (the ring is idle between tiles).
+struct GemmPipe {
+    uint32_t issued = 0;       // producer: parity of the loads issued into each stage (bit s)
+    uint32_t used = 0;         // producer: stages ever loaded
+    uint32_t consumed = 0;     // MMA issuer: parity of the loads consumed from each stage
+    uint32_t ntile = 0;        // every thread: tiles completed (phase of the done barrier)
+};
+
+// Ring stage bytes: the weight chunk(s) and, for a streamed token operand,
+// its chunk.
+__host__ __device__ constexpr int stage_bytes(bool dual, bool resident)
+{
+    return (dual ? 2 : 1) * A_BYTES + (resident ? 0 : B_BYTES);
+}
+
+// Ring depth of a projection: as many stages as its K chunks, the barrier
+// pairs and the shared-memory budget (after the resident operand) allow.
+__host__ __device__ constexpr int ring_stages(bool dual, bool resident, int K)
+{
+    int nk = K / KC, res = resident ? nk * B_BYTES : 0;
+    int st = (RING_BUDGET - res) / stage_bytes(dual, resident);
+    st = st < MAXS ? st : MAXS;
+    st = st < nk ? st : nk;
+    return st < 1 ? 1 : st;
+}
+
+// Dynamic shared memory of a tile (ring, then the resident token operand),
+// without the 1024-byte alignment slack.
+__host__ __device__ constexpr int tile_smem(bool dual, bool resident, int K)
+{
+    return ring_stages(dual, resident, K) * stage_bytes(dual, resident) + (resident ? (K / KC) * B_BYTES : 0);
+}
+
+// Initialise the barriers (thread 0; the caller synchronises).
+__device__ __forceinline__ void gemm_shared_init(GemmShared &S)
+{
+    for (int s = 0; s < MAXS; s++) { mbar_init(&S.full[s], 1); mbar_init(&S.empty[s], NISS); }
+    mbar_init(&S.done, NISS);
+    S.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// RMSNorm of RB rows r0 .. r0+RB-1 of the tile by one warp, every load of
+// the rows issued before the first reduction; lane l holds elements
+// 4l + 128c .. +3 of a row (c < CH).
+template <int RB, int CH>
+__device__ __forceinline__ void norm_rows(const float *__restrict__ xrows, const float *__restrict__ gain, int K,
+                                          int M, int m0, int r0, uint8_t *res)
+{
+    const int lane = threadIdx.x & 31;
+    float4 v[RB][CH];
+    float ss[RB];
+#pragma unroll
+    for (int b = 0; b < RB; b++) {
+        int m = m0 + r0 + b;
+        const float *x = m < M ? xrows + (long)m * K : nullptr;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            int e = lane * 4 + c * 128;
+            v[b][c] = (x && e < K) ? *(const float4 *)(x + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < RB; b++) {
+        ss[b] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            ss[b] = fmaf(v[b][c].x, v[b][c].x, ss[b]); ss[b] = fmaf(v[b][c].y, v[b][c].y, ss[b]);
+            ss[b] = fmaf(v[b][c].z, v[b][c].z, ss[b]); ss[b] = fmaf(v[b][c].w, v[b][c].w, ss[b]);
+        }
+        ss[b] = warp_sum(ss[b]);
+    }
+#pragma unroll
+    for (int b = 0; b < RB; b++) {
+        int r = r0 + b;
+        float inv = m0 + r < M ? 1.0f / sqrtf(ss[b] / (float)K + 1e-6f) : 0.0f;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            int e = lane * 4 + c * 128;
+            if (e >= K) continue;
+            const float *gn = gain + e;                        // gains sit at any float offset
+            *(uint2 *)(res + swz(r, e)) = pack4(v[b][c].x * inv * gn[0], v[b][c].y * inv * gn[1],
+                                                v[b][c].z * inv * gn[2], v[b][c].w * inv * gn[3]);
+        }
+    }
+}
+
+// Build the token operand of rows m0 .. m0+63 in shared memory; rows past M
+// are zero.  Warp w builds rows 8w .. 8w+7.  A_NORM: RMSNorm of the FP32 rows
+// xrows[m] times the gain; A_EMBED: the channel-scaled latents of the token
+// (row pointers resolved beforehand into yrow).  All of a warp's loads are in
+// flight together (K <= 384: the eight rows at once).  One out-of-line copy
+// serves every projection mode (keeps the instruction footprint small).
+static __device__ __noinline__ void build_tokens(const GemmArgs &g, int m0, uint8_t *res, const int16_t *const *yrow)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int K = g.K, M = g.M, r0 = warp * (NT / 8);
+    const float *gain = g.a_gain;
+    if (g.asrc == A_NORM) {
+        const float *xrows = g.xrows;
+        if (K <= 384) {
+            norm_rows<8, 3>(xrows, gain, K, M, m0, r0, res);
+        } else {
+            norm_rows<4, 4>(xrows, gain, K, M, m0, r0, res);
+            norm_rows<4, 4>(xrows, gain, K, M, m0, r0 + 4, res);
+        }
+        return;
+    }
+    constexpr int CH = KRES_MAX / 128;
+    short4 q[8][CH];
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const int16_t *y = yrow[r0 + b];
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            int e = lane * 4 + c * 128;
+            q[b][c] = (y && e < K) ? *(const short4 *)(y + e) : make_short4(0, 0, 0, 0);   // rows 8-byte aligned
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            int e = lane * 4 + c * 128;
+            if (e >= K) continue;
+            const float *gm = gain + e;
+            *(uint2 *)(res + swz(r0 + b, e)) = pack4(gm[0] * (float)q[b][c].x, gm[1] * (float)q[b][c].y,
+                                                     gm[2] * (float)q[b][c].z, gm[3] * (float)q[b][c].w);
+        }
+    }
+}
+
+// Per-token addresses a mode needs, resolved once per tile by threads 0..63:
+// cache rows (EPI_STORE into a cache, EPI_QKV), the hyperprior row
+// (EPI_RESID_BASE), the head outputs (EPI_HEADS), the latents (A_EMBED).
+template <int MODE>
+__device__ __forceinline__ void build_table(const GemmArgs &g, int m0, GemmShared &S)
+{
+    int r = threadIdx.x;
+    if (r >= NT) return;
+    int m = m0 + r;
+    S.tab[0][r] = S.tab[1][r] = S.tab[2][r] = S.tab[3][r] = 0;
+    S.yrow[r] = nullptr;
+    const Epi &e = g.epi;
+    if (m >= g.M || !e.tok) return;
+    int tk = e.tok[m];
+    const Slot &s = e.slots[tok_slot(tk)];
+    int p = tok_pos(tk);
+    if (g.asrc == A_EMBED) S.yrow[r] = s.y + (long)p * g.K;
+    if (MODE == EPI_STORE && e.st_sel != CS_NONE) {
+        S.tab[0][r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.st_sel, e.st_layer, p, e.d);
+    } else if (MODE == EPI_QKV) {
+        int layer = e.ring ? e.kv_layer * e.Tf + s.ring[s.nfr - 1] : e.kv_layer;
+        S.tab[0][r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.kc_sel, layer, p, e.d);
+        S.tab[1][r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.vc_sel, layer, p, e.d);
+    } else if (MODE == EPI_RESID_BASE) {
+        S.tab[1][r] = (uintptr_t)(s.eh + (long)p * g.N);
+    } else if (MODE == EPI_HEADS) {
+        S.tab[0][r] = (uintptr_t)(s.mu + (long)p * e.C);
+        S.tab[1][r] = (uintptr_t)(s.sigma + (long)p * e.C);
+        S.tab[2][r] = (uintptr_t)(s.idx + (long)p * e.C);
+        S.tab[3][r] = (uintptr_t)(s.m + (long)p * e.C);
+    }
+}
+
+// The epilogue of a tile: wait for the MMAs, read the accumulator from TMEM
+// and write the mode's outputs.  Thread t holds feature row f0 + 32 (w % 4)
+// + lane (w = its warp) and token columns 32 (w / 4) .. + 31.  Residual
+// modes read the rows they update while the MMAs still run.  Other modes
+// walk their columns 8 at a time in a rolled loop and, per group, compute
+// every value before storing any (the output pointers are generic, so each
+// store could alias later loads).  Out of line: one copy per mode, small
+// enough to stay in the instruction cache.
+template <bool DUAL, int MODE>
+static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint32_t tmem, const GemmArgs &g, int f0, int m0,
+                                                  GemmPipe &pp)
+{
+    constexpr bool RESID = MODE == EPI_RESID || MODE == EPI_RESID_BASE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int M = g.M, N = g.N;
+    const Epi e = g.epi;
+    const int f = f0 + (warp & 3) * 32 + lane;
+    const bool fok = f < N;
+    const int cb = (warp >> 2) * (NT / 2);
+    float old[RESID ? NT / 2 : 1];
+    if constexpr (RESID) {
+#pragma unroll
+        for (int j = 0; j < NT / 2; j++) {
+            const int r = cb + j, m = m0 + r;
+            const float *src = MODE == EPI_RESID ? e.rows + (long)m * N : (const float *)S.tab[1][r];
+            old[j] = (fok && m < M) ? src[f] : 0.0f;
+        }
+    }
+    bool ok = mbar_wait(&S.done, pp.ntile & 1);
+    if (!ok) S.abort = 1;
+    fence_after();
+    __syncthreads();
+    pp.ntile++;
+    if (S.abort) {
+        fence_before();
+        __syncthreads();
+        return;
+    }
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    constexpr uint32_t ASTEP = (DUAL ? 2 : 1) * NT;                // columns between the issuers' accumulators
+    if constexpr (RESID) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            float v[16];
+            tmem_sum16(trow + cb + 16 * h, ASTEP, v);
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const int m = m0 + cb + 16 * h + j;
+                if (fok && m < M) e.rows[(long)m * N + f] = old[16 * h + j] + v[j];
+            }
+        }
+    } else {
+        // per-feature constants; heads: even feature rows give mu of channel
+        // f / 2, odd rows its sigma
+        float bf = 0.0f, ga = 0.0f, gb = 0.0f;
+        if ((MODE == EPI_SET_BIAS || MODE == EPI_BIAS_SILU) && fok) bf = e.bias[f];
+        if (MODE == EPI_HEADS && fok) {
+            ga = (f & 1) ? e.gsg[f >> 1] : e.gmu[f >> 1];
+            gb = (f & 1) ? e.bsg[f >> 1] : e.bmu[f >> 1];
+        }
+#pragma unroll 1
+        for (int c0 = cb; c0 < cb + NT / 2; c0 += 8) {
+            float v[8], v2[8], o[8];
+            int oi[8];
+            tmem_sum8(trow + c0, ASTEP, v);
+            if (DUAL) tmem_sum8(trow + NT + c0, ASTEP, v2);
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const float y = v[j];
+                oi[j] = 0;
+                if (MODE == EPI_HEADS) {
+                    if (f & 1) {
+                        float sg = expf(fminf(fmaxf(ga * y + gb, LN_SIG_LO), LN_SIG_HI));
+                        o[j] = sg;
+                        oi[j] = scale_index(S.stab, sg);
+                    } else {
+                        float mu = ga * y + gb;
+                        o[j] = mu;
+                        oi[j] = (int)rintf(fminf(fmaxf(mu, -32768.0f), 32767.0f));
+                    }
+                } else if (MODE == EPI_SET_BIAS) {
+                    o[j] = y + bf;
+                } else if (MODE == EPI_BIAS_SILU) {
+                    o[j] = silu_f(y + bf);
+                } else if (MODE == EPI_SWIGLU) {
+                    o[j] = DUAL ? silu_f(y) * v2[j] : y;
+                } else {
+                    o[j] = y;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                const int r = c0 + j, m = m0 + r;
+                if (!(fok && m < M)) continue;
+                const float y = o[j];
+                if (MODE == EPI_HEADS) {
+                    const int c = f >> 1;
+                    if (f & 1) {
+                        ((float *)S.tab[1][r])[c] = y;
+                        ((uint8_t *)S.tab[2][r])[c] = (uint8_t)oi[j];
+                    } else {
+                        ((float *)S.tab[0][r])[c] = y;
+                        ((int32_t *)S.tab[3][r])[c] = oi[j];
+                    }
+                } else if (MODE == EPI_STORE) {
+                    if (e.st_sel == CS_NONE) ((__nv_bfloat16 *)e.out)[(long)m * e.ld_out + f] = __float2bfloat16_rn(y);
+                    else ((__nv_bfloat16 *)S.tab[0][r])[f] = __float2bfloat16_rn(y);
+                } else if (MODE == EPI_QKV) {
+                    if (f < e.q_cols) ((__nv_bfloat16 *)e.out)[(long)m * e.ld_out + f] = __float2bfloat16_rn(y);
+                    else if (f < e.q_cols + e.d) ((__nv_bfloat16 *)S.tab[0][r])[f - e.q_cols] = __float2bfloat16_rn(y);
+                    else ((__nv_bfloat16 *)S.tab[1][r])[f - e.q_cols - e.d] = __float2bfloat16_rn(y);
+                } else if (MODE == EPI_SET_BIAS) {
+                    e.rows[(long)m * N + f] = y;
+                } else {
+                    ((__nv_bfloat16 *)e.out)[(long)m * e.ld_out + f] = __float2bfloat16_rn(y);
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+}
+
+// Everything of a tile that does not depend on data written by earlier work:
+// the token table (threads 0..63), the scale table, and (thread 0) the weight
+// copies of the ring's stages.  Returns, on thread 0, how many stages it
+// issued.  The caller synchronises the CTA before gemm_tile_main.
+template <bool DUAL, int MODE>
+__device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const CUtensorMap *tmW,
+                                             const CUtensorMap *tmW2, const GemmArgs &g, int f0, int m0,
+                                             GemmPipe &pp)
+{
+    if (MODE == EPI_HEADS && threadIdx.x < NSCALES) S.stab[threadIdx.x] = g.epi.scale[threadIdx.x];
+    build_table<MODE>(g, m0, S);
+    if (threadIdx.x != 0) return 0;
+    const bool resident = g.asrc != A_DIRECT;
+    const int stage = stage_bytes(DUAL, resident);
+    const int first = ring_stages(DUAL, resident, g.K);
+    for (int s = 0; s < first; s++) {
+        // the ring is idle between tiles: these waits return at once
+        if (((pp.used >> s) & 1) && !mbar_wait(&S.empty[s], ((pp.issued >> s) & 1) ^ 1)) { S.abort = 1; return s; }
+        uint8_t *st = ring + s * stage;
+        mbar_expect_tx(&S.full[s], stage);
+        tma_load(st, tmW, &S.full[s], s * KC, f0);
+        if (DUAL) tma_load(st + A_BYTES, tmW2, &S.full[s], s * KC, f0);
+        pp.issued ^= 1u << s;
+        pp.used |= 1u << s;
+    }
+    return first;
+}
+
+// The rest of a tile, after the caller's wait for its inputs and a CTA
+// barrier: token operand, MMAs, epilogue.  `first` (thread 0) is
+// gemm_tile_pre's result.
+template <bool DUAL, int MODE>
+__device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *tmW,
+                                               const CUtensorMap *tmW2, const CUtensorMap *tmX, const GemmArgs &g,
+                                               int f0, int m0, int first, GemmPipe &pp)
+{
+    constexpr int NACC = DUAL ? 2 : 1;
+    const bool resident = g.asrc != A_DIRECT;
+    const int stage = stage_bytes(DUAL, resident);
+    const int nk = g.K / KC, nst = ring_stages(DUAL, resident, g.K);
+    uint8_t *res = ring + nst * stage;                             // resident token operand
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0 && !resident) {
+        fence_proxy_global();
+        for (int s = 0; s < first; s++) tma_load(ring + s * stage + NACC * A_BYTES, tmX, &S.full[s], s * KC, m0);
+    }
+    if (resident) {
+        build_tokens(g, m0, res, S.yrow);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+
+    if (warp == 0 && lane == 0) {
+        // producer: the chunks past the first ring fill
+        for (int j = first; j < nk; j++) {
+            int s = j % nst;
+            if (S.abort) break;
+            if (((pp.used >> s) & 1) && !mbar_wait(&S.empty[s], ((pp.issued >> s) & 1) ^ 1)) { S.abort = 1; break; }
+            uint8_t *st = ring + s * stage;
+            mbar_expect_tx(&S.full[s], stage);
+            tma_load(st, tmW, &S.full[s], j * KC, f0);
+            if (DUAL) tma_load(st + A_BYTES, tmW2, &S.full[s], j * KC, f0);
+            if (!resident) tma_load(st + NACC * A_BYTES, tmX, &S.full[s], j * KC, m0);
+            pp.issued ^= 1u << s;
+            pp.used |= 1u << s;
+        }
+        if (S.abort) {
+            // let this CTA's copies land before it can go on or exit
+            for (int s = 0; s < nst; s++)
+                if ((pp.used >> s) & 1) mbar_wait(&S.full[s], ((pp.issued >> s) & 1) ^ 1);
+        }
+    } else if (warp >= 1 && warp <= NISS && lane == 0) {
+        // MMA issuers: issuer q takes K step q of every chunk into its own
+        // accumulator (one thread issues an MMA only every ~150 cycles, so
+        // four issuers shorten the dependent chain fourfold); each stage is
+        // released once all four have committed
+        const int q = warp - 1;
+        const uint32_t id = idesc_bf16(TM, NT);
+        const uint32_t acc0 = tmem + (uint32_t)q * (NACC * NT);
+        for (int j = 0; j < nk; j++) {
+            int s = j % nst;
+            if (S.abort) break;
+            if (!mbar_wait(&S.full[s], (pp.consumed >> s) & 1)) { S.abort = 1; break; }
+            pp.consumed ^= 1u << s;
+            fence_after();
+            uint32_t base = su32(ring + s * stage);
+            uint32_t bb = resident ? su32(res) + j * B_BYTES : base + NACC * A_BYTES;
+            mma(acc0, sdesc(base + q * 32), sdesc(bb + q * 32), id, j != 0);
+            if (DUAL) mma(acc0 + NT, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
+            mma_commit(&S.empty[s]);
+        }
+        mma_commit(&S.done);
+    }
+    __syncwarp();
+    gemm_epilogue<DUAL, MODE>(S, tmem, g, f0, m0, pp);
+}
+
+}  // namespace tc
+
+// A tensor map of the 2D bf16 array [rows][ld] (K used columns), box of
+// box_rows x 64 elements, 128-byte swizzle, rows past the end read as zero
+// (cached per argument tuple; host).
+bool gemm_tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensorMap *out);
+
+}  // namespace psw

@@ -225,6 +225,58 @@ void launch_rans_dec_init(const Slot *S, int nslots, int C, cudaStream_t s);
 void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const int2 *kn, int C, cudaStream_t s);
 void launch_rans_dec_finish(const Slot *S, int nslots, int C, cudaStream_t s);
 
+
+// ---------------------------------------------------------------- persistent decoder
+// One phase of a wavefront step, as the persistent decoder runs it: a
+// projection, a window attention or the rANS step.  A phase works either on
+// the positions of the current step (the accumulator, Spatial Module 2, the
+// heads and the coder) or on those of the previous step (Spatial Module 1 and
+// the accumulator keys/values, which need their just-decoded latents); the
+// kernel fills in the token list and count of each step (GemmArgs.M and
+// epi.tok, AttnArgs.tok and n, kn).
+enum OpType { OP_GEMM = 0, OP_ATTN = 1, OP_RANS = 2 };
+enum TokSet { TS_CUR = 0, TS_PREV = 1 };
+
+struct Op {
+    int type, tokset;
+    int dual;                      // OP_GEMM: SwiGLU dual form
+    int wmap, wmap2, xmap;         // OP_GEMM: indices into the tensor-map table (-1: none)
+    const int2 *kn;                // OP_RANS: this step's (first symbol, count) per slot
+    GemmArgs g;                    // OP_GEMM
+    AttnArgs a;                    // OP_ATTN
+};
+
+struct PersistArgs {
+    const Op *ops; int nops;
+    const void *maps;              // CUtensorMap table (64-byte aligned)
+    int nmaps;
+    const int *tok;                // token lists of every step
+    const int *step_off, *step_n;  // per global step: offset into tok, count
+    const int2 *kn; int nslots;    // per step and slot: (first symbol, count)
+    CoderDev cd;
+    const Slot *slots;
+    int C;
+    int t0, t1;                    // global steps to run
+    unsigned *bar;                 // grid-barrier counter (zero at launch)
+    int *abort_g;                  // set by a CTA whose bounded wait expired
+    int *status;                   // context status word
+};
+
+// Host-side builder of a decoder program (the phases of one step).
+struct ProgramBuilder;
+ProgramBuilder *program_new(int ws_rows);
+void program_free(ProgramBuilder *b);
+bool program_gemm(ProgramBuilder *b, const GemmArgs &g, int tokset);
+void program_attn(ProgramBuilder *b, const AttnArgs &a, int tokset);
+void program_rans(ProgramBuilder *b);
+// Upload the program and its tensor maps; the device arrays stay valid until
+// program_free.  Returns false on a CUDA error.
+bool program_upload(ProgramBuilder *b, const Op **ops, int *nops, const void **maps, int *nmaps, size_t *smem);
+// Kernel attributes and the grid (one CTA per SM, all co-resident) for a
+// dynamic shared-memory size; false if that cannot be resident.
+bool persist_prepare(size_t smem, int *grid);
+bool persist_launch(const PersistArgs &a, int grid, size_t smem, cudaStream_t s);
+
 }  // namespace psw
 
 // The coder tables of a context (for entry points outside api.cu): channels,

@@ -8,6 +8,7 @@
 // through the slot table.
 #include "internal.h"
 #include "device_common.cuh"
+#include "attn_dev.cuh"
 
 #include <math.h>
 
@@ -144,179 +145,20 @@ void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void
 
 // ---------------------------------------------------------------- attention
 
-__device__ __forceinline__ int label_of(int mask, int i, int j)
-{
-    return mask == 1 ? ((i & 3) + (j & 3)) & 3 : 2 * i + j;
-}
-
-// Sec. 3.2 / Fig. 2b visibility: kind 0 (accumulator): strictly smaller
-// label; kind 1 (spatial self-attention): the position itself or a label
-// not above its own; for the 2i+j label also a smaller raster index.
-__device__ __forceinline__ bool visible(int mask, int kind, int W, int pi, int pj, int qi, int qj)
-{
-    if (kind < 0) return true;
-    if (kind == 1 && qi == pi && qj == pj) return true;
-    int lp = label_of(mask, pi, pj), lq = label_of(mask, qi, qj);
-    bool ok = kind == 0 ? lq < lp : lq <= lp;
-    if (mask == 0) ok = ok && (qi * W + qj < pi * W + pj);
-    return ok;
-}
-
-// Raw storage of B bytes of one row slice (kept packed until use).
-template <int B> struct RawT;
-template <> struct RawT<2> { using type = unsigned short; };
-template <> struct RawT<4> { using type = unsigned int; };
-template <> struct RawT<8> { using type = uint2; };
-template <> struct RawT<16> { using type = uint4; };
-
-// The n floats packed in raw storage of T elements.
-template <typename T, int N, typename R>
-__device__ __forceinline__ void unpack(const R &r, float *o)
-{
-    if constexpr (sizeof(T) == 4) {
-        const float *f = reinterpret_cast<const float *>(&r);
-#pragma unroll
-        for (int i = 0; i < N; i++) o[i] = f[i];
-    } else if constexpr (N == 1) {
-        o[0] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(&r));
-    } else {
-        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&r);
-#pragma unroll
-        for (int i = 0; i < N / 2; i++) {
-            float2 f = __bfloat1622float2(h[i]);
-            o[2 * i] = f.x; o[2 * i + 1] = f.y;
-        }
-    }
-}
-
-// 16-byte asynchronous copy global -> shared (cached in L2 only), and the
-// wait for all of a thread's outstanding copies.
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
-{
-    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Warps per block of the attention kernel: shared staging is 32 key rows and
-// 32 value rows of a head per warp.
+// Warps per block: shared staging of one warp is 32 key and 32 value rows of
+// a head.
 template <typename T, int DH>
-struct AttnShape {
-    static constexpr int RB = DH * (int)sizeof(T);            // bytes of one head's row slice
-    static constexpr int WPB = RB <= 128 ? 4 : (RB <= 256 ? 2 : 1);
-};
+__host__ __device__ constexpr int attn_wpb() { return AttnWarp<T, DH>::RB <= 128 ? 4 : (AttnWarp<T, DH>::RB <= 256 ? 2 : 1); }
 
-// One warp per (token, head).  The warp first lists the visible window
-// positions (Sec. 3.2 masks; frames oldest first, raster order within a
-// window) as cache rows.  Then, 32 listed keys at a time, the warp copies the
-// head's slices of their key and value rows into shared memory (consecutive
-// lanes take consecutive 16-byte pieces of a row, so the gathers coalesce;
-// one memory round trip per chunk), lane c scores key c as
-// q.k / sqrt(DH) + relative bias, and every lane accumulates its PER output
-// dimensions over the chunk's values.  The softmax runs online over chunks
-// (one chunk for spatial windows up to 7 x 7) with max and sum by
-// butterflies; values accumulate in list order and the sum of the weights
-// divides at the end.
 template <typename T, int DH>
-__global__ void __launch_bounds__(32 * AttnShape<T, DH>::WPB) k_attention(AttnArgs a)
+__global__ void __launch_bounds__(32 * attn_wpb<T, DH>()) k_attention(AttnArgs a)
 {
-    constexpr int PER = DH / 32;
-    constexpr int MAXC = 256;                                  // Tf * k * k <= 256 (checked at context creation)
-    constexpr int RB = AttnShape<T, DH>::RB, WPB = AttnShape<T, DH>::WPB;
-    constexpr int KS = RB + 16;                                // padded key stride: conflict-free 16-byte reads
-    constexpr int PR = RB / 16;                                // 16-byte pieces per row slice
-    constexpr int EPU = 16 / (int)sizeof(T);                   // elements per piece
-    using VRaw = typename RawT<PER * (int)sizeof(T)>::type;
-    __shared__ __align__(16) unsigned char kbuf[WPB][32 * KS];
-    __shared__ __align__(16) unsigned char vbuf[WPB][32 * RB];
-    __shared__ float qs[WPB][DH];
-    __shared__ int rows[WPB][MAXC];
-    __shared__ unsigned short bix[WPB][MAXC];
-    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int WPB = attn_wpb<T, DH>();
+    __shared__ AttnWarp<T, DH> sm[WPB];
+    const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * WPB + wib;
     if (gw >= a.n * a.nh) return;                              // warps are independent: no block barrier
-    const int tokn = gw / a.nh, h = gw % a.nh;
-    const int tk = a.tok[tokn];
-    const Slot &s = a.slots[tok_slot(tk)];
-    const int p = tok_pos(tk);
-    const int H = s.H, W = s.W, stride = s.stride;
-    const int pi = p / W, pj = p % W, w = (a.k - 1) >> 1, kk = a.k * a.k;
-    const int nfr = a.temporal ? s.nfr : 1;
-    const int ncand = nfr * kk;
-    int cnt = 0;
-    for (int c0 = 0; c0 < ncand; c0 += 32) {
-        int cidx = c0 + lane, fr = cidx / kk, c = cidx - fr * kk;
-        int qi = pi + c / a.k - w, qj = pj + c % a.k - w;
-        bool ok = cidx < ncand && qi >= 0 && qi < H && qj >= 0 && qj < W &&
-                  visible(a.mask, a.kind, W, pi, pj, qi, qj);
-        unsigned bal = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            int at = cnt + __popc(bal & ((1u << lane) - 1u));
-            int layer = a.temporal ? a.layer * a.Tf + s.ring[fr] : a.layer;
-            rows[wib][at] = layer * stride + qi * W + qj;
-            bix[wib][at] = (unsigned short)((a.temporal ? nfr - 1 - fr : 0) * kk + c);
-        }
-        cnt += __popc(bal);
-    }
-    pdl_trigger();
-    pdl_wait();                                        // queries, keys and values are ready from here on
-    const T *q = a.q_sel == CS_NONE ? (const T *)a.Q + (long)tokn * a.d + h * DH
-                                    : cache_row<const T>(s, a.q_sel, 0, p, a.d) + h * DH;
-    for (int e = lane; e < DH; e += 32) qs[wib][e] = to_f<T>(q[e]);
-    __syncwarp();
-    const char *Kb = (const char *)(cache_row<const T>(s, a.k_sel, 0, 0, a.d) + h * DH);
-    const char *Vb = (const char *)(cache_row<const T>(s, a.v_sel, 0, 0, a.d) + h * DH);
-    const long rsb = (long)a.d * (long)sizeof(T);              // bytes between cache rows
-    const float *bias = a.bias + (long)h * a.bias_h_stride;
-    const float scale = rsqrtf((float)DH);
-    unsigned char *kb = kbuf[wib], *vb = vbuf[wib];
-    float mx = -INFINITY, z = 0.0f, o[PER];
-#pragma unroll
-    for (int i = 0; i < PER; i++) o[i] = 0.0f;
-    for (int base = 0; base < cnt; base += 32) {
-        const int nc = min(32, cnt - base);
-        for (int x = lane; x < nc * PR; x += 32) {
-            int r = x / PR, u = x - r * PR;
-            long off = (long)rows[wib][base + r] * rsb + u * 16;
-            cp_async16(kb + r * KS + u * 16, Kb + off);
-            cp_async16(vb + r * RB + u * 16, Vb + off);
-        }
-        cp_async_wait_all();
-        __syncwarp();
-        float sc = -INFINITY;
-        if (lane < nc) {
-            const uint4 *kr = reinterpret_cast<const uint4 *>(kb + lane * KS);
-            float acc = 0.0f;
-#pragma unroll
-            for (int u = 0; u < PR; u++) {
-                float kv[EPU];
-                unpack<T, EPU>(kr[u], kv);
-#pragma unroll
-                for (int i = 0; i < EPU; i++) acc = fmaf(qs[wib][u * EPU + i], kv[i], acc);
-            }
-            sc = acc * scale + bias[bix[wib][base + lane]];
-        }
-        const float mnew = fmaxf(mx, warp_max(sc));
-        const float corr = expf(mx - mnew);
-        const float e = lane < nc ? expf(sc - mnew) : 0.0f;
-        z = z * corr + warp_sum(e);
-#pragma unroll
-        for (int i = 0; i < PER; i++) o[i] *= corr;
-        const VRaw *vr = reinterpret_cast<const VRaw *>(vb) + lane;
-        for (int u = 0; u < nc; u++) {
-            float pu = __shfl_sync(0xffffffffu, e, u);
-            float vv[PER];
-            unpack<T, PER>(vr[u * 32], vv);
-#pragma unroll
-            for (int i = 0; i < PER; i++) o[i] = fmaf(pu, vv[i], o[i]);
-        }
-        mx = mnew;
-        __syncwarp();                                  // the next chunk reuses the buffers
-    }
-    const float inv = z > 0.0f ? 1.0f / z : 0.0f;
-    T *out = (T *)a.O + (long)tokn * a.d + h * DH + lane * PER;
-#pragma unroll
-    for (int u = 0; u < PER; u++) out[u] = from_f<T>(o[u] * inv);
+    attn_item<T, DH, true>(a, gw, sm[wib]);
 }
 
 template <typename T>
@@ -325,12 +167,12 @@ static void attention_t(const AttnArgs &a, cudaStream_t s)
     int dh = a.d / a.nh;
     long warps = (long)a.n * a.nh;
     switch (dh) {
-    case 32: launch_pdl(k_attention<T, 32>, dim3(cdiv(warps, AttnShape<T, 32>::WPB)),
-                        dim3(32 * AttnShape<T, 32>::WPB), 0, s, a); break;
-    case 64: launch_pdl(k_attention<T, 64>, dim3(cdiv(warps, AttnShape<T, 64>::WPB)),
-                        dim3(32 * AttnShape<T, 64>::WPB), 0, s, a); break;
-    case 128: launch_pdl(k_attention<T, 128>, dim3(cdiv(warps, AttnShape<T, 128>::WPB)),
-                         dim3(32 * AttnShape<T, 128>::WPB), 0, s, a); break;
+    case 32: launch_pdl(k_attention<T, 32>, dim3(cdiv(warps, attn_wpb<T, 32>())),
+                        dim3(32 * attn_wpb<T, 32>()), 0, s, a); break;
+    case 64: launch_pdl(k_attention<T, 64>, dim3(cdiv(warps, attn_wpb<T, 64>())),
+                        dim3(32 * attn_wpb<T, 64>()), 0, s, a); break;
+    case 128: launch_pdl(k_attention<T, 128>, dim3(cdiv(warps, attn_wpb<T, 128>())),
+                         dim3(32 * attn_wpb<T, 128>()), 0, s, a); break;
     default: break;   // rejected at context creation
     }
 }
@@ -347,10 +189,7 @@ void launch_attention(int prec, const AttnArgs &a, cudaStream_t s)
 __device__ __forceinline__ void quantize_one(float mu, float sigma, const float *scale, uint8_t &idx,
                                              int32_t &m)
 {
-    int l = NSCALES - 1;
-    for (int t = 0; t < NSCALES; t++)
-        if (scale[t] >= sigma) { l = t; break; }
-    idx = (uint8_t)l;
+    idx = (uint8_t)scale_index(scale, sigma);
     m = (int32_t)rintf(fminf(fmaxf(mu, -32768.0f), 32767.0f));
 }
 

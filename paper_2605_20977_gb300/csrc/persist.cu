@@ -1,0 +1,394 @@
+// persist.cu -- the persistent wavefront decoder: one cooperative launch,
+// one CTA per SM, walks every global step of a batched decode.
+//
+// A step is a fixed program of phases (Sec. 3.1 / Fig. 1 model on the step's
+// positions, then the rANS step): Spatial Module 1 and the accumulator
+// keys/values on the positions decoded at the previous step, the
+// accumulator, Spatial Module 2 and the heads on the positions of this step,
+// then the coder.  Phases depend on one another through global memory, so a
+// grid-wide barrier separates them; within a phase the CTAs share its tiles
+// (projections: 128 features x 64 tokens) or warp items ((token, head) of an
+// attention, (frame, channel) of the coder) round-robin.
+//
+// Each phase runs the same tile and item functions as the one-launch-per-op
+// kernels (gemm_dev.cuh, attn_dev.cuh, rans_dev.cuh), so the decoder's
+// parameters are bit-identical to the encoder's masked pass.  What the
+// persistent form adds: no launch or drain between phases, and the next
+// phase's token table and first weight copies are issued before the barrier
+// wait (they do not depend on the phase in flight).
+//
+// Every wait is bounded: mbarrier waits as in the GEMM engine, the grid
+// barrier after ~2 s of globaltimer or once another CTA has raised the
+// global abort flag.  A CTA that gives up records ST_TIMEOUT, raises the
+// flag, frees its tensor memory and returns; the others leave at their next
+// barrier.  Co-residency of all CTAs (which the barrier relies on) is
+// guaranteed by the cooperative launch.
+#include "gemm_dev.cuh"
+#include "attn_dev.cuh"
+#include "rans_dev.cuh"
+
+#include <map>
+#include <tuple>
+#include <vector>
+
+namespace psw {
+
+using namespace tc;
+
+namespace {
+
+constexpr int PWARPS = NTHREADS / 32;
+constexpr uint32_t PTCOLS = tile_tcols(true);      // tensor-memory columns: the dual form's accumulators
+#ifndef PSW_SPIN_NS
+#define PSW_SPIN_NS 200
+#endif
+constexpr unsigned SPIN_NS = PSW_SPIN_NS;          // pause between polls of the grid barrier
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier on a monotone counter: every CTA adds one per barrier and
+// waits until the counter reaches (barriers so far) x (CTAs).  Thread 0 only.
+// Polls back off (a short sleep between reads) so that idle CTAs do not
+// flood the counter's L2 slice while others work.
+__device__ __forceinline__ bool grid_wait(const unsigned *bar, unsigned target, const volatile int *abort_g)
+{
+    if (ld_acquire(bar) >= target) return true;
+    uint64_t t0 = gtime();
+    for (;;) {
+        __nanosleep(SPIN_NS);
+        if (ld_acquire(bar) >= target) return true;
+        if (*abort_g) return false;
+        if (gtime() - t0 > WAIT_NS) return false;
+    }
+}
+
+// The tokens of the step a phase works on.
+__device__ __forceinline__ bool phase_valid(const PersistArgs &P, int t, int i)
+{
+    int ts = P.ops[i].tokset;
+    if (ts == TS_PREV && t == 0) return false;
+    return P.step_n[ts == TS_PREV ? t - 1 : t] > 0;
+}
+
+// Advance (t, i) to the next phase with work; false past the last step.
+__device__ __forceinline__ bool next_phase(const PersistArgs &P, int &t, int &i)
+{
+    for (;;) {
+        if (++i == P.nops) { i = 0; t++; }
+        if (t >= P.t1) return false;
+        if (phase_valid(P, t, i)) return true;
+    }
+}
+
+// Copy phase (t, i) into shared memory and fill in its step's tokens.
+__device__ __forceinline__ void load_op(const PersistArgs &P, Op &op, int t, int i)
+{
+    const int *src = reinterpret_cast<const int *>(P.ops + i);
+    int *dst = reinterpret_cast<int *>(&op);
+    for (int w = threadIdx.x; w < (int)(sizeof(Op) / 4); w += blockDim.x) dst[w] = src[w];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tt = op.tokset == TS_PREV ? t - 1 : t;
+        const int *tok = P.tok + P.step_off[tt];
+        int n = P.step_n[tt];
+        op.g.M = n; op.g.epi.tok = tok;
+        op.a.tok = tok; op.a.n = n;
+        op.kn = P.kn + (size_t)t * P.nslots;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int gemm_tiles(const GemmArgs &g, int &nf)
+{
+    nf = (g.N + TM - 1) / TM;
+    return nf * ((g.M + NT - 1) / NT);
+}
+
+template <bool DUAL, int MODE>
+__device__ __forceinline__ int pre_t(GemmShared &S, uint8_t *ring, const CUtensorMap *maps, const Op &op, int j,
+                                     GemmPipe &pp)
+{
+    int nf;
+    gemm_tiles(op.g, nf);
+    return gemm_tile_pre<DUAL, MODE>(S, ring, maps + op.wmap, maps + (op.wmap2 >= 0 ? op.wmap2 : op.wmap), op.g,
+                                     (j % nf) * TM, (j / nf) * NT, pp);
+}
+
+// gemm_tile_pre of tile j of a projection phase.
+__device__ __noinline__ int gemm_pre(GemmShared &S, uint8_t *ring, const CUtensorMap *maps, const Op &op, int j,
+                                     GemmPipe &pp)
+{
+    switch (op.g.epi.mode) {
+    case EPI_SWIGLU: return pre_t<true, EPI_SWIGLU>(S, ring, maps, op, j, pp);
+    case EPI_STORE: return pre_t<false, EPI_STORE>(S, ring, maps, op, j, pp);
+    case EPI_QKV: return pre_t<false, EPI_QKV>(S, ring, maps, op, j, pp);
+    case EPI_RESID: return pre_t<false, EPI_RESID>(S, ring, maps, op, j, pp);
+    case EPI_RESID_BASE: return pre_t<false, EPI_RESID_BASE>(S, ring, maps, op, j, pp);
+    case EPI_BIAS_SILU: return pre_t<false, EPI_BIAS_SILU>(S, ring, maps, op, j, pp);
+    case EPI_SET_BIAS: return pre_t<false, EPI_SET_BIAS>(S, ring, maps, op, j, pp);
+    default: return pre_t<false, EPI_HEADS>(S, ring, maps, op, j, pp);
+    }
+}
+
+// This CTA's tiles of a projection phase; the first may have been prepared
+// (gemm_pre) before the barrier.
+template <bool DUAL, int MODE>
+__device__ __noinline__ void gemm_phase(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *maps,
+                                        const Op &op, bool prepared, int first, GemmPipe &pp)
+{
+    int nf;
+    const int ntiles = gemm_tiles(op.g, nf);
+    const CUtensorMap *tw = maps + op.wmap, *tw2 = maps + (op.wmap2 >= 0 ? op.wmap2 : op.wmap);
+    const CUtensorMap *tx = maps + (op.xmap >= 0 ? op.xmap : op.wmap);
+    for (int j = blockIdx.x; j < ntiles; j += gridDim.x) {
+        const int f0 = (j % nf) * TM, m0 = (j / nf) * NT;
+        if (!(prepared && j == (int)blockIdx.x)) {
+            first = gemm_tile_pre<DUAL, MODE>(S, ring, tw, tw2, op.g, f0, m0, pp);
+            __syncthreads();
+        }
+        gemm_tile_main<DUAL, MODE>(S, ring, tmem, tw, tw2, tx, op.g, f0, m0, first, pp);
+        if (S.abort) return;
+    }
+}
+
+__device__ __noinline__ void run_gemm(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *maps,
+                                      const Op &op, bool prepared, int first, GemmPipe &pp)
+{
+    switch (op.g.epi.mode) {
+    case EPI_SWIGLU: gemm_phase<true, EPI_SWIGLU>(S, ring, tmem, maps, op, prepared, first, pp); break;
+    case EPI_STORE: gemm_phase<false, EPI_STORE>(S, ring, tmem, maps, op, prepared, first, pp); break;
+    case EPI_QKV: gemm_phase<false, EPI_QKV>(S, ring, tmem, maps, op, prepared, first, pp); break;
+    case EPI_RESID: gemm_phase<false, EPI_RESID>(S, ring, tmem, maps, op, prepared, first, pp); break;
+    case EPI_RESID_BASE:
+        gemm_phase<false, EPI_RESID_BASE>(S, ring, tmem, maps, op, prepared, first, pp);
+        break;
+    case EPI_BIAS_SILU: gemm_phase<false, EPI_BIAS_SILU>(S, ring, tmem, maps, op, prepared, first, pp); break;
+    case EPI_SET_BIAS: gemm_phase<false, EPI_SET_BIAS>(S, ring, tmem, maps, op, prepared, first, pp); break;
+    default: gemm_phase<false, EPI_HEADS>(S, ring, tmem, maps, op, prepared, first, pp); break;
+    }
+}
+
+template <int DH>
+__device__ __noinline__ void attn_phase(const AttnArgs &a, uint8_t *dyn)
+{
+    AttnWarp<__nv_bfloat16, DH> *sm = reinterpret_cast<AttnWarp<__nv_bfloat16, DH> *>(dyn);
+    const int warp = threadIdx.x >> 5, items = a.n * a.nh;
+    for (int gw = blockIdx.x * PWARPS + warp; gw < items; gw += gridDim.x * PWARPS)
+        attn_item<__nv_bfloat16, DH, false>(a, gw, sm[warp]);
+}
+
+__device__ __noinline__ void rans_phase(const PersistArgs &P, const int2 *kn)
+{
+    const int warp = threadIdx.x >> 5, items = P.nslots * P.C;
+    for (int wi = blockIdx.x * PWARPS + warp; wi < items; wi += gridDim.x * PWARPS)
+        rans_step_item<false>(P.cd, P.slots, kn, P.C, wi);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) k_persist(const __grid_constant__ PersistArgs P)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ GemmShared S;
+    __shared__ Op op;
+    __shared__ int stop;
+    uint8_t *dyn = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const CUtensorMap *maps = (const CUtensorMap *)P.maps;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) { gemm_shared_init(S); stop = 0; }
+    // the tensor maps sit in global memory (written before the launch): make
+    // them visible to the tensor-map proxy of the thread that issues copies
+    if (threadIdx.x == 0)
+        for (int m = 0; m < P.nmaps; m++)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + m) : "memory");
+    if (warp == 0) tmem_alloc(&S.tmem_slot, PTCOLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = S.tmem_slot;
+    GemmPipe pp;
+    uint32_t nbar = 0;
+    int t = P.t0, i = -1, first = 0;
+    bool prepared = false;
+    bool have = next_phase(P, t, i);
+    if (have) load_op(P, op, t, i);
+    while (have) {
+        if (op.type == OP_GEMM) run_gemm(S, dyn, tmem, maps, op, prepared, first, pp);
+        else if (op.type == OP_ATTN) {
+            const int dh = op.a.d / op.a.nh;
+            if (dh == 64) attn_phase<64>(op.a, dyn);
+            else if (dh == 32) attn_phase<32>(op.a, dyn);
+            else attn_phase<128>(op.a, dyn);
+        } else {
+            rans_phase(P, op.kn);
+        }
+        prepared = false;
+        int nt = t, ni = i;
+        have = next_phase(P, nt, ni);
+        // shared staging is free for the next phase's tensor copies; the
+        // thread that issues them orders its acquire of this phase's global
+        // writes before its copies (fence_proxy_global in gemm_tile_main)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (S.abort || !have) break;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(P.bar, 1u);
+        }
+        nbar++;
+        // the next phase's token table and first weight copies
+        load_op(P, op, nt, ni);
+        if (op.type == OP_GEMM) {
+            int nf;
+            if ((int)blockIdx.x < gemm_tiles(op.g, nf)) {
+                first = gemm_pre(S, dyn, maps, op, blockIdx.x, pp);
+                prepared = true;
+            }
+        }
+        if (threadIdx.x == 0 && !grid_wait(P.bar, nbar * gridDim.x, P.abort_g)) stop = 1;
+        __syncthreads();
+        if (stop || S.abort) break;
+        t = nt; i = ni;
+    }
+    if (threadIdx.x == 0 && (S.abort || stop)) {
+        atomicOr(P.status, ST_TIMEOUT);
+        atomicExch(P.abort_g, 1);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, PTCOLS);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+struct ProgramBuilder {
+    int ws_rows;
+    std::vector<Op> ops;
+    std::vector<CUtensorMap> maps;
+    std::map<std::tuple<const void *, int, int, int, int>, int> map_idx;
+    size_t smem = 0;
+    Op *d_ops = nullptr;
+    CUtensorMap *d_maps = nullptr;
+};
+
+static int map_of(ProgramBuilder *b, const void *ptr, int rows, int K, int ld, int box)
+{
+    auto key = std::make_tuple(ptr, rows, K, ld, box);
+    auto it = b->map_idx.find(key);
+    if (it != b->map_idx.end()) return it->second;
+    CUtensorMap m;
+    if (!gemm_tensor_map(ptr, rows, K, ld, box, &m)) return -1;
+    b->maps.push_back(m);
+    return b->map_idx[key] = (int)b->maps.size() - 1;
+}
+
+ProgramBuilder *program_new(int ws_rows)
+{
+    ProgramBuilder *b = new ProgramBuilder();
+    b->ws_rows = ws_rows;
+    return b;
+}
+
+void program_free(ProgramBuilder *b)
+{
+    if (!b) return;
+    cudaFree(b->d_ops);
+    cudaFree(b->d_maps);
+    delete b;
+}
+
+bool program_gemm(ProgramBuilder *b, const GemmArgs &g, int tokset)
+{
+    if (!gemm_tc_supported(P_BF16, g.N, g.K, g.asrc)) return false;
+    Op op{};
+    op.type = OP_GEMM; op.tokset = tokset;
+    op.dual = g.epi.mode == EPI_SWIGLU;
+    op.g = g;
+    op.wmap = map_of(b, g.Wt, g.N, g.K, g.K, TM);
+    op.wmap2 = op.dual ? map_of(b, g.Wt2, g.N, g.K, g.K, TM) : -1;
+    // activation rows: the whole workspace; rows past a step's tokens only
+    // feed accumulator columns that are never stored
+    op.xmap = g.asrc == A_DIRECT ? map_of(b, g.A, b->ws_rows, g.K, g.lda, NT) : -1;
+    if (op.wmap < 0 || (op.dual && op.wmap2 < 0) || (g.asrc == A_DIRECT && op.xmap < 0)) return false;
+    b->ops.push_back(op);
+    b->smem = std::max(b->smem, (size_t)tile_smem(op.dual, g.asrc != A_DIRECT, g.K));
+    return true;
+}
+
+void program_attn(ProgramBuilder *b, const AttnArgs &a, int tokset)
+{
+    Op op{};
+    op.type = OP_ATTN; op.tokset = tokset;
+    op.wmap = op.wmap2 = op.xmap = -1;
+    op.a = a;
+    b->ops.push_back(op);
+    int dh = a.d / a.nh;
+    size_t per = dh == 32 ? sizeof(AttnWarp<__nv_bfloat16, 32>)
+                          : dh == 64 ? sizeof(AttnWarp<__nv_bfloat16, 64>) : sizeof(AttnWarp<__nv_bfloat16, 128>);
+    b->smem = std::max(b->smem, per * PWARPS);
+}
+
+void program_rans(ProgramBuilder *b)
+{
+    Op op{};
+    op.type = OP_RANS; op.tokset = TS_CUR;
+    op.wmap = op.wmap2 = op.xmap = -1;
+    b->ops.push_back(op);
+}
+
+bool program_upload(ProgramBuilder *b, const Op **ops, int *nops, const void **maps, int *nmaps, size_t *smem)
+{
+    if (!b->d_ops) {
+        if (cudaMalloc(&b->d_ops, b->ops.size() * sizeof(Op)) != cudaSuccess) return false;
+        if (cudaMalloc(&b->d_maps, std::max<size_t>(b->maps.size(), 1) * sizeof(CUtensorMap)) != cudaSuccess)
+            return false;
+        if (cudaMemcpy(b->d_ops, b->ops.data(), b->ops.size() * sizeof(Op), cudaMemcpyHostToDevice) != cudaSuccess)
+            return false;
+        if (!b->maps.empty() &&
+            cudaMemcpy(b->d_maps, b->maps.data(), b->maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
+            return false;
+    }
+    *ops = b->d_ops;
+    *nops = (int)b->ops.size();
+    *maps = b->d_maps;
+    *nmaps = (int)b->maps.size();
+    *smem = b->smem + 1024;
+    return true;
+}
+
+bool persist_prepare(size_t smem, int *grid)
+{
+    int dev = 0, nsm = 0, coop = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
+    if (cudaFuncSetAttribute(k_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return false;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist, NTHREADS, smem) != cudaSuccess || per < 1)
+        return false;
+    *grid = nsm;
+    return true;
+}
+
+bool persist_launch(const PersistArgs &a, int grid, size_t smem, cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NTHREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_persist, a) == cudaSuccess;
+}
+
+}  // namespace psw

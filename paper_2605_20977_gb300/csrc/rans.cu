@@ -15,6 +15,7 @@
 // followed by its words in decoding order, padded to 4 bytes.
 #include "internal.h"
 #include "device_common.cuh"
+#include "rans_dev.cuh"
 
 #include <math.h>
 #include <stdlib.h>
@@ -27,8 +28,6 @@
 
 namespace psw {
 
-static constexpr uint32_t MAGIC = 0x31575350u;
-static constexpr uint32_t RANS_L = 1u << 16;
 
 // ---------------------------------------------------------------- tables (host)
 
@@ -91,23 +90,6 @@ size_t container_capacity(int H, int W, int C)
 }
 
 // ---------------------------------------------------------------- device helpers
-
-__device__ __forceinline__ uint32_t lane_exclusive_scan(uint32_t v, uint32_t &total)
-{
-    int lane = threadIdx.x & 31;
-    uint32_t inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    total = __shfl_sync(0xffffffffu, inc, 31);
-    return inc - v;
-}
-
-__device__ __forceinline__ uint32_t ld8(const uint8_t *b, size_t o) { return b[o]; }
-__device__ __forceinline__ uint32_t ld16le(const uint8_t *b, size_t o) { return ld8(b, o) | (ld8(b, o + 1) << 8); }
-__device__ __forceinline__ uint32_t ld32le(const uint8_t *b, size_t o) { return ld16le(b, o) | (ld16le(b, o + 2) << 16); }
 
 // ---------------------------------------------------------------- encoder
 
@@ -296,86 +278,14 @@ void launch_rans_dec_init(const Slot *S, int nslots, int C, cudaStream_t s)
     k_rans_dec_init<<<(n + 127) / 128, 128, 0, s>>>(S, nslots, C);
 }
 
-// Decode symbols k0 .. k0 + n - 1 of every channel of every slot (one
-// schedule step).  One warp per (slot, channel); a group of 32 consecutive
-// symbols decodes in parallel on its lanes, which then read their words in
-// lane order (a warp scan of the words each lane needs).
+// One schedule step of every channel of every slot: one warp per (slot,
+// channel), see rans_step_item.
 __global__ void k_rans_dec_step(CoderDev cd, const Slot *__restrict__ S, int nslots,
                                 const int2 *__restrict__ kn, int C)
 {
-    int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (wi >= nslots * C) return;
-    int b = wi / C, c = wi % C;
-    int2 r = kn[b];
-    int k0 = r.x, n = r.y;
-    pdl_trigger();
-    if (n <= 0) return;
-    pdl_wait();                                        // this step's scale indices and means are ready
-    const Slot &sl = S[b];
-    const uint8_t *__restrict__ bs = sl.bs;
-    const int *__restrict__ order = sl.order;
-    uint32_t x = sl.rstate[(size_t)c * 32 + lane];
-    uint32_t p = sl.rptr[c];
-    const uint32_t e = sl.rend[c];
-    bool bad = false;
-    for (int g = k0 / 32; g * 32 < k0 + n; g++) {
-        int k = g * 32 + lane;
-        bool act = k >= k0 && k < k0 + n;
-        uint32_t need = 0;
-        long pos = 0;
-        int T = 0, slot = 0;
-        int32_t mm = 0;
-        if (act) {
-            pos = order[k];
-            long a = pos * C + c;
-            int l = sl.idx[a];
-            mm = sl.m[a];
-            T = cd.meta[l];
-            int nsl = cd.meta[NSCALES + l], off = cd.meta[2 * NSCALES + l];
-            uint32_t v = x & 0xFFFFu;
-            int lo = 0, hi = nsl - 1;                  // last slot with cum <= v
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if ((cd.cdf[off + mid] & 0xFFFFu) <= v) lo = mid; else hi = mid - 1;
-            }
-            slot = lo;
-            uint32_t ent = cd.cdf[off + slot];
-            x = (ent >> 16) * (x >> 16) + v - (ent & 0xFFFFu);
-            need = (x < RANS_L ? 1u : 0u) + (slot == 2 * T + 1 ? 2u : 0u);
-        }
-        uint32_t total;
-        uint32_t pre = lane_exclusive_scan(need, total);
-        uint32_t q = p + 2 * pre;
-        auto word = [&](void) -> uint32_t {
-            if (q + 2 > e) { bad = true; return 0u; }
-            uint32_t wv = ld16le(bs, q);
-            q += 2;
-            return wv;
-        };
-        if (act) {
-            if (x < RANS_L) x = (x << 16) | word();
-            long sv;
-            if (slot == 2 * T + 1) {
-                uint32_t d0 = x & 0xFFFFu;
-                x = (x & 0xFFFF0000u) | word();
-                uint32_t d1 = x & 0xFFFFu;
-                x = (x & 0xFFFF0000u) | word();
-                uint32_t v = d0 | (d1 << 16);
-                long mag = (long)T + 1 + (long)(v >> 1);
-                sv = (v & 1) ? -mag : mag;
-            } else {
-                sv = slot - T;
-            }
-            long yv = (long)mm + sv;
-            if (yv < -32768 || yv > 32767) { bad = true; yv = 0; }
-            sl.y[pos * C + c] = (int16_t)yv;
-        }
-        p += 2 * total;
-        if (p > e) p = e;
-    }
-    sl.rstate[(size_t)c * 32 + lane] = x;
-    if (lane == 0) sl.rptr[c] = p;
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(sl.status, ST_CORRUPT);
+    rans_step_item<true>(cd, S, kn, C, wi);
 }
 
 void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const int2 *kn, int C, cudaStream_t s)

@@ -25,7 +25,9 @@ EXPORTS = ["psw_weights_count", "psw_create", "psw_destroy", "psw_last_error", "
            "psw_seq_create", "psw_seq_reset", "psw_seq_destroy", "psw_bitstream_capacity", "psw_encode_params",
            "psw_decode_frame", "psw_decode_batch", "psw_rate", "psw_quantize", "psw_scale_table", "psw_cdf_table",
            "psw_rans_encode", "psw_rans_decode", "psw_launch_count", "psw_profile_begin", "psw_profile_end",
-           "psw_rans_encode_noalloc"]
+           "psw_rans_encode_noalloc", "psw_set_engine", "psw_last_engine"]
+
+ENGINE_AUTO, ENGINE_GRAPH, ENGINE_PERSISTENT = 0, 1, 2
 
 
 class ModelDesc(ct.Structure):
@@ -84,6 +86,8 @@ def load(path: str = LIB_PATH):
             "psw_rans_encode": (I, [P, P, FD, P, P, P, P, S, ct.POINTER(S), P]),
             "psw_rans_decode": (I, [P, P, FD, P, S, P, P, P, P]),
             "psw_launch_count": (ct.c_long, [P]),
+            "psw_set_engine": (ct.c_int, [P, ct.c_int]),
+            "psw_last_engine": (ct.c_int, [P]),
             "psw_profile_begin": (I, [P]),
             "psw_profile_end": (I, [P, ct.POINTER(KernelStat), I, ct.POINTER(I)]),
             "psw_rans_encode_noalloc": (I, [P, FD, P, P, P, P, S, ct.POINTER(S), P]),
@@ -206,6 +210,14 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self.lib.psw_launch_count(self.h))
+
+    def set_engine(self, engine: int):
+        """Decode engine: ENGINE_AUTO, ENGINE_GRAPH or ENGINE_PERSISTENT."""
+        self._check(self.lib.psw_set_engine(self.h, int(engine)))
+
+    def last_engine(self) -> int:
+        """Engine of the last decode (0: individual launches)."""
+        return int(self.lib.psw_last_engine(self.h))
 
     def profile_begin(self):
         self._check(self.lib.psw_profile_begin(self.h))

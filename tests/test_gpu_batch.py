@@ -129,12 +129,21 @@ def test_graph_replay_repeats_and_recovers_from_corruption():
             first = got
         else:
             assert np.array_equal(got[1], first[1]) and np.array_equal(got[2], first[2])
-    # launches are counted for replayed graphs too
-    l0 = ctx.launch_count()
-    seq.reset()
-    yo, mu, sg = _alloc(cfg.H, cfg.W, cfg.C)
-    seq.decode_frame(fd, bs, n, z, yo, mu, sg)
-    assert ctx.launch_count() - l0 > 100
+    # launches are counted for replayed graphs too: one kernel per phase of
+    # every step on the graph engine, the prologue plus two on the
+    # persistent one
+    counts = {}
+    for engine in (psw.ENGINE_GRAPH, psw.ENGINE_PERSISTENT):
+        ctx.set_engine(engine)
+        for rep in range(2):
+            l0 = ctx.launch_count()
+            seq.reset()
+            yo, mu, sg = _alloc(cfg.H, cfg.W, cfg.C)
+            seq.decode_frame(fd, bs, n, z, yo, mu, sg)
+            assert np.array_equal(yo.cpu().numpy(), y)
+            counts[engine] = ctx.launch_count() - l0
+    assert counts[psw.ENGINE_GRAPH] > 100
+    assert 3 <= counts[psw.ENGINE_PERSISTENT] < 20
 
 
 def test_temporal_sequences_in_a_batch():
@@ -154,3 +163,74 @@ def test_temporal_sequences_in_a_batch():
             alone.append((yo.cpu().numpy(), mu.cpu().numpy(), sg.cpu().numpy()))
         batched, _ = _batched(ctx, cfg, items, [fd, fd], seqs=pair)
         _check_same(alone, batched, items)
+
+
+def _engine_run(ctx, cfg, items, fds, engine):
+    ctx.set_engine(engine)
+    got, seqs = _batched(ctx, cfg, items, fds)
+    for s in seqs:
+        s.close()
+    return got, ctx.last_engine()
+
+
+def test_persistent_engine_equals_graph_engine():
+    """The persistent decoder (one cooperative launch over every step) and
+    the per-phase graph decoder give bit-identical latents and parameters."""
+    base = synth.config("tiny")
+    ctx = psw.Context(base, synth.weights(base), precision=psw.PSW_BF16)
+    plan = [((8, 12), 0), ((5, 7), 1), ((8, 3), 0), ((1, 1), 0), ((6, 12), 0)]
+    items, fds = [], []
+    for k, ((H, W), sched) in enumerate(plan):
+        c = base.with_grid(H, W)
+        items += _encode(ctx, c, synth.frames(c, 1, seed=130 + k), sched)
+        fds.append(psw.frame_desc(H, W, sched))
+    g, eg = _engine_run(ctx, base, items, fds, psw.ENGINE_GRAPH)
+    p, ep = _engine_run(ctx, base, items, fds, psw.ENGINE_PERSISTENT)
+    assert (eg, ep) == (psw.ENGINE_GRAPH, psw.ENGINE_PERSISTENT)
+    _check_same(g, p, items)
+    a, ea = _engine_run(ctx, base, items, fds, psw.ENGINE_AUTO)
+    assert ea == psw.ENGINE_PERSISTENT
+    _check_same(g, a, items)
+
+
+def test_persistent_engine_1080p_and_temporal():
+    cfg = synth.config("i1080")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
+    plan = [(68, 120), (9, 120), (17, 30)]
+    items, fds = [], []
+    for k, (H, W) in enumerate(plan):
+        c = cfg.with_grid(H, W)
+        items += _encode(ctx, c, synth.frames(c, 1, seed=140 + k), 0)
+        fds.append(psw.frame_desc(H, W, 0))
+    g, _ = _engine_run(ctx, cfg, items, fds, psw.ENGINE_GRAPH)
+    p, ep = _engine_run(ctx, cfg, items, fds, psw.ENGINE_PERSISTENT)
+    assert ep == psw.ENGINE_PERSISTENT
+    _check_same(g, p, items)
+
+    tcfg = synth.config("tiny_p")
+    tctx = psw.Context(tcfg, synth.weights(tcfg), precision=psw.PSW_BF16)
+    fr = synth.frames(tcfg, 3, seed=150)
+    enc = _encode(tctx, tcfg, fr, 0)
+    fd = psw.frame_desc(tcfg.H, tcfg.W, 0)
+    outs = {}
+    for engine in (psw.ENGINE_GRAPH, psw.ENGINE_PERSISTENT):
+        tctx.set_engine(engine)
+        seq = tctx.seq_create(tcfg.H, tcfg.W)
+        outs[engine] = []
+        for f in range(3):
+            yo, mu, sg = _alloc(tcfg.H, tcfg.W, tcfg.C)
+            seq.decode_frame(fd, enc[f][0], enc[f][1], enc[f][2], yo, mu, sg)
+            assert tctx.last_engine() == engine
+            outs[engine].append((yo.cpu().numpy(), mu.cpu().numpy(), sg.cpu().numpy()))
+        seq.close()
+    _check_same(outs[psw.ENGINE_GRAPH], outs[psw.ENGINE_PERSISTENT], enc)
+
+
+def test_engine_selection_errors():
+    cfg = synth.config("tiny")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_FP32)
+    with pytest.raises(psw.PswError):
+        ctx.set_engine(psw.ENGINE_PERSISTENT)
+    with pytest.raises(psw.PswError):
+        ctx.set_engine(7)
+    ctx.set_engine(psw.ENGINE_AUTO)

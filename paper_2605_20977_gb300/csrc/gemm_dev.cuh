@@ -197,28 +197,32 @@ __device__ __forceinline__ void tmem_ld8(uint32_t addr, float *v)
 
 // Sum of the issuers' accumulators ((a0 + a1) + a2) + a3 at 16 / 8
 // consecutive columns; accumulator q starts `step` columns after q - 1.
-__device__ __forceinline__ void tmem_sum16(uint32_t addr, uint32_t step, float *v)
+__device__ __forceinline__ void tmem_ld8_async(uint32_t addr, uint32_t *r)
 {
-    tmem_ld16(addr, v);
-#pragma unroll
-    for (int q = 1; q < NISS; q++) {
-        float w[16];
-        tmem_ld16(addr + q * step, w);
-#pragma unroll
-        for (int i = 0; i < 16; i++) v[i] += w[i];
-    }
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr));
 }
 
 __device__ __forceinline__ void tmem_sum8(uint32_t addr, uint32_t step, float *v)
 {
-    tmem_ld8(addr, v);
+    uint32_t r[NISS][8];
 #pragma unroll
-    for (int q = 1; q < NISS; q++) {
-        float w[8];
-        tmem_ld8(addr + q * step, w);
+    for (int q = 0; q < NISS; q++) tmem_ld8_async(addr + q * step, r[q]);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int i = 0; i < 8; i++) v[i] += w[i];
+    for (int i = 0; i < 8; i++) {
+        float a = __uint_as_float(r[0][i]);
+#pragma unroll
+        for (int q = 1; q < NISS; q++) a += __uint_as_float(r[q][i]);
+        v[i] = a;
     }
+}
+
+__device__ __forceinline__ void tmem_sum16(uint32_t addr, uint32_t step, float *v)
+{
+    tmem_sum8(addr, step, v);
+    tmem_sum8(addr + 8, step, v + 8);
 }
 
 // Byte offset of element (row r, column k) of a K-major bf16 operand laid
@@ -250,12 +254,39 @@ struct GemmShared {
 // full/empty barrier pair, and the thread that waits on a barrier keeps the
 // parity of the next completion it needs, so tiles of different ring depths
 // can follow one another (the ring is idle between tiles).
+// Every thread keeps the same copy, updated at the end of each tile, so
+// that any thread can issue any stage's copies: chunk j of a tile with ring
+// depth nst fills stage j % nst for its (j / nst)-th time in the tile.
 struct GemmPipe {
-    uint32_t issued = 0;       // producer: parity of the loads issued into each stage (bit s)
-    uint32_t used = 0;         // producer: stages ever loaded
-    uint32_t consumed = 0;     // MMA issuer: parity of the loads consumed from each stage
-    uint32_t ntile = 0;        // every thread: tiles completed (phase of the done barrier)
+    uint32_t fills = 0;        // parity of the fills of each stage before this tile (bit s)
+    uint32_t empties = 0;      // parity of the releases (empty completions) of each stage before this tile
+    uint32_t ntile = 0;        // tiles completed (phase of the done barrier)
 };
+
+// Parity of the u-th fill of stage s in the current tile (its full
+// barrier's completion).  A stage is released (its empty barrier completes)
+// only when the tile fills it again, so the ring needs no release between
+// tiles: the done barrier already means every MMA has read its operands.
+__device__ __forceinline__ uint32_t fill_parity(const GemmPipe &pp, int s, int u)
+{
+    return ((pp.fills >> s) & 1) ^ (uint32_t)(u & 1);
+}
+
+// Parity of the release the u-th (u >= 1) fill of stage s waits for.
+__device__ __forceinline__ uint32_t release_parity(const GemmPipe &pp, int s, int u)
+{
+    return ((pp.empties >> s) & 1) ^ (uint32_t)((u - 1) & 1);
+}
+
+// Account for a finished tile of nk chunks over nst stages.
+__device__ __forceinline__ void pipe_advance(GemmPipe &pp, int nk, int nst)
+{
+    for (int s = 0; s < nst; s++) {
+        int uses = (nk - s + nst - 1) / nst;
+        pp.fills ^= (uint32_t)(uses & 1) << s;
+        pp.empties ^= (uint32_t)((uses - 1) & 1) << s;
+    }
+}
 
 // Ring stage bytes: the weight chunk(s) and, for a streamed token operand,
 // its chunk.
@@ -423,8 +454,8 @@ __device__ __forceinline__ void build_table(const GemmArgs &g, int m0, GemmShare
 // store could alias later loads).  Out of line: one copy per mode, small
 // enough to stay in the instruction cache.
 template <bool DUAL, int MODE>
-static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint32_t tmem, const GemmArgs &g, int f0, int m0,
-                                                  GemmPipe &pp)
+static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, uint32_t tmem, const GemmArgs &g,
+                                                  int f0, int m0, GemmPipe &pp)
 {
     constexpr bool RESID = MODE == EPI_RESID || MODE == EPI_RESID_BASE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -504,43 +535,72 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint32_t tmem, 
                     o[j] = y;
                 }
             }
+            if constexpr (MODE == EPI_HEADS || MODE == EPI_SET_BIAS) {
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const int r = c0 + j, m = m0 + r;
-                if (!(fok && m < M)) continue;
-                const float y = o[j];
-                if (MODE == EPI_HEADS) {
-                    const int c = f >> 1;
-                    if (f & 1) {
-                        ((float *)S.tab[1][r])[c] = y;
-                        ((uint8_t *)S.tab[2][r])[c] = (uint8_t)oi[j];
+                for (int j = 0; j < 8; j++) {
+                    const int r = c0 + j, m = m0 + r;
+                    if (!(fok && m < M)) continue;
+                    const float y = o[j];
+                    if (MODE == EPI_HEADS) {
+                        const int c = f >> 1;
+                        if (f & 1) {
+                            ((float *)S.tab[1][r])[c] = y;
+                            ((uint8_t *)S.tab[2][r])[c] = (uint8_t)oi[j];
+                        } else {
+                            ((float *)S.tab[0][r])[c] = y;
+                            ((int32_t *)S.tab[3][r])[c] = oi[j];
+                        }
                     } else {
-                        ((float *)S.tab[0][r])[c] = y;
-                        ((int32_t *)S.tab[3][r])[c] = oi[j];
+                        e.rows[(long)m * N + f] = y;
                     }
-                } else if (MODE == EPI_STORE) {
-                    if (e.st_sel == CS_NONE) ((__nv_bfloat16 *)e.out)[(long)m * e.ld_out + f] = __float2bfloat16_rn(y);
-                    else ((__nv_bfloat16 *)S.tab[0][r])[f] = __float2bfloat16_rn(y);
-                } else if (MODE == EPI_QKV) {
-                    if (f < e.q_cols) ((__nv_bfloat16 *)e.out)[(long)m * e.ld_out + f] = __float2bfloat16_rn(y);
-                    else if (f < e.q_cols + e.d) ((__nv_bfloat16 *)S.tab[0][r])[f - e.q_cols] = __float2bfloat16_rn(y);
-                    else ((__nv_bfloat16 *)S.tab[1][r])[f - e.q_cols - e.d] = __float2bfloat16_rn(y);
-                } else if (MODE == EPI_SET_BIAS) {
-                    e.rows[(long)m * N + f] = y;
-                } else {
-                    ((__nv_bfloat16 *)e.out)[(long)m * e.ld_out + f] = __float2bfloat16_rn(y);
+                }
+            } else {
+                // bf16 rows: the warp's 32 features x 8 tokens go through
+                // shared memory (the ring, idle now) so that each lane stores
+                // 8 consecutive features of one token in one 16-byte write
+                uint16_t *stg = (uint16_t *)(ring + warp * 512);
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    __nv_bfloat16 b = __float2bfloat16_rn(o[j]);
+                    stg[j * 32 + lane] = *reinterpret_cast<uint16_t *>(&b);
+                }
+                __syncwarp();
+                const int jr = lane >> 2, fc = (lane & 3) * 8;
+                const uint4 val = *reinterpret_cast<const uint4 *>(stg + jr * 32 + fc);
+                __syncwarp();
+                const int r = c0 + jr, m = m0 + r, fb = f0 + (warp & 3) * 32 + fc;
+                if (m < M && fb < N) {
+                    __nv_bfloat16 *dst;
+                    if (MODE == EPI_STORE)
+                        dst = e.st_sel == CS_NONE ? (__nv_bfloat16 *)e.out + (long)m * e.ld_out + fb
+                                                  : (__nv_bfloat16 *)S.tab[0][r] + fb;
+                    else if (MODE == EPI_QKV)
+                        dst = fb < e.q_cols ? (__nv_bfloat16 *)e.out + (long)m * e.ld_out + fb
+                              : fb < e.q_cols + e.d ? (__nv_bfloat16 *)S.tab[0][r] + (fb - e.q_cols)
+                                                    : (__nv_bfloat16 *)S.tab[1][r] + (fb - e.q_cols - e.d);
+                    else
+                        dst = (__nv_bfloat16 *)e.out + (long)m * e.ld_out + fb;
+                    if (fb + 8 <= N) {
+                        *reinterpret_cast<uint4 *>(dst) = val;
+                    } else {
+                        const __nv_bfloat16 *pv = reinterpret_cast<const __nv_bfloat16 *>(&val);
+                        for (int i = 0; i < N - fb; i++) dst[i] = pv[i];
+                    }
                 }
             }
         }
     }
+    // the ring is written by tensor copies again after this
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     fence_before();
     __syncthreads();
 }
 
 // Everything of a tile that does not depend on data written by earlier work:
-// the token table (threads 0..63), the scale table, and (thread 0) the weight
-// copies of the ring's stages.  Returns, on thread 0, how many stages it
-// issued.  The caller synchronises the CTA before gemm_tile_main.
+// the token table (threads 0..63), the scale table, and the weight copies of
+// the ring's stages (stage s issued by lane 0 of warp s: one thread issues a
+// tensor copy only every ~150 ns).  Returns the number of stages filled.  The
+// caller synchronises the CTA before gemm_tile_main.
 template <bool DUAL, int MODE>
 __device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const CUtensorMap *tmW,
                                              const CUtensorMap *tmW2, const GemmArgs &g, int f0, int m0,
@@ -548,41 +608,45 @@ __device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const
 {
     if (MODE == EPI_HEADS && threadIdx.x < NSCALES) S.stab[threadIdx.x] = g.epi.scale[threadIdx.x];
     build_table<MODE>(g, m0, S);
-    if (threadIdx.x != 0) return 0;
     const bool resident = g.asrc != A_DIRECT;
     const int stage = stage_bytes(DUAL, resident);
-    const int first = ring_stages(DUAL, resident, g.K);
-    for (int s = 0; s < first; s++) {
-        // the ring is idle between tiles: these waits return at once
-        if (((pp.used >> s) & 1) && !mbar_wait(&S.empty[s], ((pp.issued >> s) & 1) ^ 1)) { S.abort = 1; return s; }
+    const int nst = ring_stages(DUAL, resident, g.K);
+    const int s = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0 && s < nst) {
+        // the ring is idle between tiles (the previous tile's MMAs are done)
         uint8_t *st = ring + s * stage;
         mbar_expect_tx(&S.full[s], stage);
         tma_load(st, tmW, &S.full[s], s * KC, f0);
         if (DUAL) tma_load(st + A_BYTES, tmW2, &S.full[s], s * KC, f0);
-        pp.issued ^= 1u << s;
-        pp.used |= 1u << s;
     }
-    return first;
+    return nst;
 }
 
 // The rest of a tile, after the caller's wait for its inputs and a CTA
-// barrier: token operand, MMAs, epilogue.  `first` (thread 0) is
-// gemm_tile_pre's result.
+// barrier: token operand, MMAs, epilogue.  `first` is gemm_tile_pre's
+// result.  Roles: lane 0 of warps 1..4 issue the MMAs; lane 0 of warps 0, 5,
+// 6 and 7 issue the copies of the chunks past the first ring fill, in turn.
 template <bool DUAL, int MODE>
 __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *tmW,
                                                const CUtensorMap *tmW2, const CUtensorMap *tmX, const GemmArgs &g,
                                                int f0, int m0, int first, GemmPipe &pp)
 {
     constexpr int NACC = DUAL ? 2 : 1;
+    constexpr int NPROD = NTHREADS / 32 - NISS;                    // producer warps: 0 and NISS+1 ..
     const bool resident = g.asrc != A_DIRECT;
     const int stage = stage_bytes(DUAL, resident);
     const int nk = g.K / KC, nst = ring_stages(DUAL, resident, g.K);
     uint8_t *res = ring + nst * stage;                             // resident token operand
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    if (threadIdx.x == 0 && !resident) {
+    const bool producer = lane == 0 && (warp == 0 || warp > NISS);
+    const int p = warp == 0 ? 0 : warp - NISS;                     // producer index
+    if (!resident && producer) {
+        // the first fill's token chunks, spread over the producers (the MMA
+        // issuers go straight to their loops)
         fence_proxy_global();
-        for (int s = 0; s < first; s++) tma_load(ring + s * stage + NACC * A_BYTES, tmX, &S.full[s], s * KC, m0);
+        for (int s = p; s < first; s += NPROD)
+            tma_load(ring + s * stage + NACC * A_BYTES, tmX, &S.full[s], s * KC, m0);
     }
     if (resident) {
         build_tokens(g, m0, res, S.yrow);
@@ -590,49 +654,48 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
         __syncthreads();
     }
 
-    if (warp == 0 && lane == 0) {
-        // producer: the chunks past the first ring fill
-        for (int j = first; j < nk; j++) {
-            int s = j % nst;
+    if (producer) {
+        // producers: chunk j >= first goes to producer (j - first) % NPROD
+        int jend = first + p;
+        for (int j = first + p; j < nk; j += NPROD) {
+            int s = j % nst, u = j / nst;
             if (S.abort) break;
-            if (((pp.used >> s) & 1) && !mbar_wait(&S.empty[s], ((pp.issued >> s) & 1) ^ 1)) { S.abort = 1; break; }
+            if (!mbar_wait(&S.empty[s], release_parity(pp, s, u))) { S.abort = 1; break; }
             uint8_t *st = ring + s * stage;
             mbar_expect_tx(&S.full[s], stage);
             tma_load(st, tmW, &S.full[s], j * KC, f0);
             if (DUAL) tma_load(st + A_BYTES, tmW2, &S.full[s], j * KC, f0);
             if (!resident) tma_load(st + NACC * A_BYTES, tmX, &S.full[s], j * KC, m0);
-            pp.issued ^= 1u << s;
-            pp.used |= 1u << s;
+            jend = j + NPROD;
         }
         if (S.abort) {
-            // let this CTA's copies land before it can go on or exit
-            for (int s = 0; s < nst; s++)
-                if ((pp.used >> s) & 1) mbar_wait(&S.full[s], ((pp.issued >> s) & 1) ^ 1);
+            // let this producer's copies land before the CTA can go on or exit
+            for (int j = first + p; j < jend && j < nk; j += NPROD) mbar_wait(&S.full[j % nst], fill_parity(pp, j % nst, j / nst));
         }
     } else if (warp >= 1 && warp <= NISS && lane == 0) {
         // MMA issuers: issuer q takes K step q of every chunk into its own
         // accumulator (one thread issues an MMA only every ~150 cycles, so
-        // four issuers shorten the dependent chain fourfold); each stage is
-        // released once all four have committed
+        // four issuers shorten the dependent chain fourfold); a stage that is
+        // filled again in this tile is released once all four have committed
         const int q = warp - 1;
         const uint32_t id = idesc_bf16(TM, NT);
         const uint32_t acc0 = tmem + (uint32_t)q * (NACC * NT);
         for (int j = 0; j < nk; j++) {
-            int s = j % nst;
+            int s = j % nst, u = j / nst;
             if (S.abort) break;
-            if (!mbar_wait(&S.full[s], (pp.consumed >> s) & 1)) { S.abort = 1; break; }
-            pp.consumed ^= 1u << s;
+            if (!mbar_wait(&S.full[s], fill_parity(pp, s, u))) { S.abort = 1; break; }
             fence_after();
             uint32_t base = su32(ring + s * stage);
             uint32_t bb = resident ? su32(res) + j * B_BYTES : base + NACC * A_BYTES;
             mma(acc0, sdesc(base + q * 32), sdesc(bb + q * 32), id, j != 0);
             if (DUAL) mma(acc0 + NT, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
-            mma_commit(&S.empty[s]);
+            if (j + nst < nk) mma_commit(&S.empty[s]);                 // the stage is filled again in this tile
         }
         mma_commit(&S.done);
     }
     __syncwarp();
-    gemm_epilogue<DUAL, MODE>(S, tmem, g, f0, m0, pp);
+    gemm_epilogue<DUAL, MODE>(S, ring, tmem, g, f0, m0, pp);
+    pipe_advance(pp, nk, nst);
 }
 
 }  // namespace tc

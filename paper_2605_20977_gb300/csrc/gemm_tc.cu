@@ -27,6 +27,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
     const int f0 = blockIdx.x * TM, m0 = blockIdx.y * NT;
     if (threadIdx.x == 0) gemm_shared_init(S);
     if ((threadIdx.x >> 5) == 0) tmem_alloc(&S.tmem_slot, TCOLS);
+    __syncthreads();                                   // barriers initialised before any warp issues copies
     pdl_trigger();
     // token lists, the slot table and the scale table are fixed for the
     // whole decode, and the weights for the context's life: read them before

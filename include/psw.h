@@ -246,8 +246,8 @@ psw_status psw_rans_encode_noalloc(const psw_ctx *ctx, const psw_frame_desc *fd,
  *   PSW_ENGINE_PERSISTENT  one cooperative launch, one block per SM, walks
  *                          all steps (Sec. 3.2 schedule) with a grid-wide
  *                          barrier between phases; BF16 contexts only.
- *   PSW_ENGINE_AUTO        persistent where the context supports it, else
- *                          graphs (the default).
+ *   PSW_ENGINE_AUTO        the graph engine (the faster of the two on the
+ *                          1080p configurations measured; the default).
  * psw_set_engine returns PSW_ERR_INVALID for an unknown engine or for
  * PSW_ENGINE_PERSISTENT on an FP32 context; a decode asked to run
  * persistently on a device that cannot co-schedule the blocks returns

@@ -122,6 +122,9 @@ size_t esize(int prec) { return prec == P_BF16 ? 2 : 4; }
 // One captured decode: graph segments of at most SEG_STEPS global steps,
 // their token lists and launch count.
 constexpr int SEG_STEPS = 512;
+// Graph cache key: workspace generation, batch size, engine flag, then one
+// (sequence pointer, grid and schedule) pair per frame from KEY_SEQ0 on.
+constexpr size_t KEY_SEQ0 = 3;
 struct GraphRec {
     std::vector<cudaGraphExec_t> exec;
     int *d_tok = nullptr;
@@ -931,8 +934,9 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
     // graph key: the workspace generation, the engine and the batch shape
     bool failed = false;
     bool graph = c->use_graphs && !c->prof;
-    bool want = c->engine != PSW_ENGINE_GRAPH && c->prec == P_BF16;
+    bool want = c->engine == PSW_ENGINE_PERSISTENT && c->prec == P_BF16;
     std::vector<long> key{0, (long)n, (long)want};
+    static_assert(KEY_SEQ0 == 3, "key layout");
     for (int b = 0; b < n; b++) {
         key.push_back((long)(uintptr_t)qs[b]);
         key.push_back(((long)fds[b].H << 32) | ((long)fds[b].W << 2) | fds[b].schedule);
@@ -1265,7 +1269,7 @@ void psw_seq_destroy(psw_seq *q)
         // drop the graphs that name this sequence
         for (auto it = c->graphs.begin(); it != c->graphs.end();) {
             bool hit = false;
-            for (size_t a = 2; a < it->first.size(); a += 2)
+            for (size_t a = KEY_SEQ0; a < it->first.size(); a += 2)
                 if (it->first[a] == (long)(uintptr_t)q) hit = true;
             if (hit) {
                 graph_free(it->second);

@@ -8,14 +8,17 @@
 // then the coder.  Phases depend on one another through global memory, so a
 // grid-wide barrier separates them; within a phase the CTAs share its tiles
 // (projections: 128 features x 64 tokens) or warp items ((token, head) of an
-// attention, (frame, channel) of the coder) round-robin.
+// attention, (frame, channel) of the coder) round-robin, starting at a CTA
+// that rotates from phase to phase, so that a small phase runs on CTAs the
+// previous one left idle.
 //
 // Each phase runs the same tile and item functions as the one-launch-per-op
 // kernels (gemm_dev.cuh, attn_dev.cuh, rans_dev.cuh), so the decoder's
 // parameters are bit-identical to the encoder's masked pass.  What the
 // persistent form adds: no launch or drain between phases, and the next
-// phase's token table and first weight copies are issued before the barrier
-// wait (they do not depend on the phase in flight).
+// phase's token table and first weight copies are issued early (they do not
+// depend on the phase in flight): by CTAs idle in the current phase at its
+// start, by the others before they wait at the barrier.
 //
 // Every wait is bounded: mbarrier waits as in the GEMM engine, the grid
 // barrier after ~2 s of globaltimer or once another CTA has raised the
@@ -135,19 +138,19 @@ __device__ __noinline__ int gemm_pre(GemmShared &S, uint8_t *ring, const CUtenso
     }
 }
 
-// This CTA's tiles of a projection phase; the first may have been prepared
-// (gemm_pre) before the barrier.
+// This CTA's tiles of a projection phase (tiles rank, rank + grid, ...); the
+// first may have been prepared (gemm_pre) before the barrier.
 template <bool DUAL, int MODE>
 __device__ __noinline__ void gemm_phase(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *maps,
-                                        const Op &op, bool prepared, int first, GemmPipe &pp)
+                                        const Op &op, int rank, bool prepared, int first, GemmPipe &pp)
 {
     int nf;
     const int ntiles = gemm_tiles(op.g, nf);
     const CUtensorMap *tw = maps + op.wmap, *tw2 = maps + (op.wmap2 >= 0 ? op.wmap2 : op.wmap);
     const CUtensorMap *tx = maps + (op.xmap >= 0 ? op.xmap : op.wmap);
-    for (int j = blockIdx.x; j < ntiles; j += gridDim.x) {
+    for (int j = rank; j < ntiles; j += gridDim.x) {
         const int f0 = (j % nf) * TM, m0 = (j / nf) * NT;
-        if (!(prepared && j == (int)blockIdx.x)) {
+        if (!(prepared && j == rank)) {
             first = gemm_tile_pre<DUAL, MODE>(S, ring, tw, tw2, op.g, f0, m0, pp);
             __syncthreads();
         }
@@ -157,51 +160,63 @@ __device__ __noinline__ void gemm_phase(GemmShared &S, uint8_t *ring, uint32_t t
 }
 
 __device__ __noinline__ void run_gemm(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *maps,
-                                      const Op &op, bool prepared, int first, GemmPipe &pp)
+                                      const Op &op, int rank, bool prepared, int first, GemmPipe &pp)
 {
     switch (op.g.epi.mode) {
-    case EPI_SWIGLU: gemm_phase<true, EPI_SWIGLU>(S, ring, tmem, maps, op, prepared, first, pp); break;
-    case EPI_STORE: gemm_phase<false, EPI_STORE>(S, ring, tmem, maps, op, prepared, first, pp); break;
-    case EPI_QKV: gemm_phase<false, EPI_QKV>(S, ring, tmem, maps, op, prepared, first, pp); break;
-    case EPI_RESID: gemm_phase<false, EPI_RESID>(S, ring, tmem, maps, op, prepared, first, pp); break;
+    case EPI_SWIGLU: gemm_phase<true, EPI_SWIGLU>(S, ring, tmem, maps, op, rank, prepared, first, pp); break;
+    case EPI_STORE: gemm_phase<false, EPI_STORE>(S, ring, tmem, maps, op, rank, prepared, first, pp); break;
+    case EPI_QKV: gemm_phase<false, EPI_QKV>(S, ring, tmem, maps, op, rank, prepared, first, pp); break;
+    case EPI_RESID: gemm_phase<false, EPI_RESID>(S, ring, tmem, maps, op, rank, prepared, first, pp); break;
     case EPI_RESID_BASE:
-        gemm_phase<false, EPI_RESID_BASE>(S, ring, tmem, maps, op, prepared, first, pp);
+        gemm_phase<false, EPI_RESID_BASE>(S, ring, tmem, maps, op, rank, prepared, first, pp);
         break;
-    case EPI_BIAS_SILU: gemm_phase<false, EPI_BIAS_SILU>(S, ring, tmem, maps, op, prepared, first, pp); break;
-    case EPI_SET_BIAS: gemm_phase<false, EPI_SET_BIAS>(S, ring, tmem, maps, op, prepared, first, pp); break;
-    default: gemm_phase<false, EPI_HEADS>(S, ring, tmem, maps, op, prepared, first, pp); break;
+    case EPI_BIAS_SILU: gemm_phase<false, EPI_BIAS_SILU>(S, ring, tmem, maps, op, rank, prepared, first, pp); break;
+    case EPI_SET_BIAS: gemm_phase<false, EPI_SET_BIAS>(S, ring, tmem, maps, op, rank, prepared, first, pp); break;
+    default: gemm_phase<false, EPI_HEADS>(S, ring, tmem, maps, op, rank, prepared, first, pp); break;
     }
 }
 
 template <int DH>
-__device__ __noinline__ void attn_phase(const AttnArgs &a, uint8_t *dyn)
+__device__ __noinline__ void attn_phase(const AttnArgs &a, uint8_t *dyn, int rank)
 {
     AttnWarp<__nv_bfloat16, DH> *sm = reinterpret_cast<AttnWarp<__nv_bfloat16, DH> *>(dyn);
     const int warp = threadIdx.x >> 5, items = a.n * a.nh;
-    for (int gw = blockIdx.x * PWARPS + warp; gw < items; gw += gridDim.x * PWARPS)
+    for (int gw = rank * PWARPS + warp; gw < items; gw += gridDim.x * PWARPS)
         attn_item<__nv_bfloat16, DH, false>(a, gw, sm[warp]);
 }
 
-__device__ __noinline__ void rans_phase(const PersistArgs &P, const int2 *kn)
+__device__ __noinline__ void rans_phase(const PersistArgs &P, const int2 *kn, int rank)
 {
     const int warp = threadIdx.x >> 5, items = P.nslots * P.C;
-    for (int wi = blockIdx.x * PWARPS + warp; wi < items; wi += gridDim.x * PWARPS)
+    for (int wi = rank * PWARPS + warp; wi < items; wi += gridDim.x * PWARPS)
         rans_step_item<false>(P.cd, P.slots, kn, P.C, wi);
+}
+
+// Work units of a phase: projection tiles, or CTAs' worth of warp items.
+__device__ __forceinline__ int phase_units(const PersistArgs &P, const Op &op)
+{
+    if (op.type == OP_GEMM) {
+        int nf;
+        return gemm_tiles(op.g, nf);
+    }
+    int items = op.type == OP_ATTN ? op.a.n * op.a.nh : P.nslots * P.C;
+    return (items + PWARPS - 1) / PWARPS;
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1) k_persist(const __grid_constant__ PersistArgs P)
 {
     extern __shared__ uint8_t smem_raw[];
     __shared__ GemmShared S;
-    __shared__ Op op;
+    __shared__ Op ops[2];                              // this phase and the next
     __shared__ int stop;
     uint8_t *dyn = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const CUtensorMap *maps = (const CUtensorMap *)P.maps;
     const int warp = threadIdx.x >> 5;
+    const int G = gridDim.x;
     if (threadIdx.x == 0) { gemm_shared_init(S); stop = 0; }
     // the tensor maps sit in global memory (written before the launch): make
-    // them visible to the tensor-map proxy of the thread that issues copies
-    if (threadIdx.x == 0)
+    // them visible to the tensor-map proxy of the threads that issue copies
+    if ((threadIdx.x & 31) == 0)
         for (int m = 0; m < P.nmaps; m++)
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(maps + m) : "memory");
     if (warp == 0) tmem_alloc(&S.tmem_slot, PTCOLS);
@@ -211,47 +226,65 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_persist(const __grid_constant__
     const uint32_t tmem = S.tmem_slot;
     GemmPipe pp;
     uint32_t nbar = 0;
-    int t = P.t0, i = -1, first = 0;
+    int t = P.t0, i = -1, first = 0, cur = 0;
+    int base = 0;                                      // CTA where this phase's work starts (rotates)
     bool prepared = false;
     bool have = next_phase(P, t, i);
-    if (have) load_op(P, op, t, i);
+    if (have) load_op(P, ops[cur], t, i);
     while (have) {
-        if (op.type == OP_GEMM) run_gemm(S, dyn, tmem, maps, op, prepared, first, pp);
-        else if (op.type == OP_ATTN) {
-            const int dh = op.a.d / op.a.nh;
-            if (dh == 64) attn_phase<64>(op.a, dyn);
-            else if (dh == 32) attn_phase<32>(op.a, dyn);
-            else attn_phase<128>(op.a, dyn);
-        } else {
-            rans_phase(P, op.kn);
-        }
-        prepared = false;
+        Op &op = ops[cur];
+        Op &nop = ops[cur ^ 1];
+        const int units = phase_units(P, op);
+        const int rank = (int)((blockIdx.x - base + G) % G);
+        const bool busy = rank < units;
+        // the next phase: its record, and this CTA's rank in it
         int nt = t, ni = i;
-        have = next_phase(P, nt, ni);
+        const bool more = next_phase(P, nt, ni);
+        const int nbase = (base + (units < G ? units : G)) % G;
+        const int nrank = (int)((blockIdx.x - nbase + G) % G);
+        if (more) load_op(P, nop, nt, ni);
+        bool nprep = false;
+        if (!busy && more && nop.type == OP_GEMM) {
+            // idle in this phase: prepare the next phase's first tile now
+            int nf;
+            if (nrank < gemm_tiles(nop.g, nf)) {
+                first = gemm_pre(S, dyn, maps, nop, nrank, pp);
+                nprep = true;
+            }
+        }
+        if (busy) {
+            if (op.type == OP_GEMM) run_gemm(S, dyn, tmem, maps, op, rank, prepared, first, pp);
+            else if (op.type == OP_ATTN) {
+                const int dh = op.a.d / op.a.nh;
+                if (dh == 64) attn_phase<64>(op.a, dyn, rank);
+                else if (dh == 32) attn_phase<32>(op.a, dyn, rank);
+                else attn_phase<128>(op.a, dyn, rank);
+            } else {
+                rans_phase(P, op.kn, rank);
+            }
+        }
         // shared staging is free for the next phase's tensor copies; the
-        // thread that issues them orders its acquire of this phase's global
-        // writes before its copies (fence_proxy_global in gemm_tile_main)
+        // threads that issue them order their acquire of this phase's global
+        // writes before the copies (fence_proxy_global in gemm_tile_main)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (S.abort || !have) break;
+        if (S.abort || !more) break;
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(P.bar, 1u);
         }
         nbar++;
-        // the next phase's token table and first weight copies
-        load_op(P, op, nt, ni);
-        if (op.type == OP_GEMM) {
+        if (busy && nop.type == OP_GEMM) {
             int nf;
-            if ((int)blockIdx.x < gemm_tiles(op.g, nf)) {
-                first = gemm_pre(S, dyn, maps, op, blockIdx.x, pp);
-                prepared = true;
+            if (nrank < gemm_tiles(nop.g, nf)) {
+                first = gemm_pre(S, dyn, maps, nop, nrank, pp);
+                nprep = true;
             }
         }
-        if (threadIdx.x == 0 && !grid_wait(P.bar, nbar * gridDim.x, P.abort_g)) stop = 1;
+        if (threadIdx.x == 0 && !grid_wait(P.bar, nbar * G, P.abort_g)) stop = 1;
         __syncthreads();
         if (stop || S.abort) break;
-        t = nt; i = ni;
+        t = nt; i = ni; cur ^= 1; base = nbase; prepared = nprep;
     }
     if (threadIdx.x == 0 && (S.abort || stop)) {
         atomicOr(P.status, ST_TIMEOUT);

@@ -189,7 +189,7 @@ def test_persistent_engine_equals_graph_engine():
     assert (eg, ep) == (psw.ENGINE_GRAPH, psw.ENGINE_PERSISTENT)
     _check_same(g, p, items)
     a, ea = _engine_run(ctx, base, items, fds, psw.ENGINE_AUTO)
-    assert ea == psw.ENGINE_PERSISTENT
+    assert ea == psw.ENGINE_GRAPH
     _check_same(g, a, items)
 
 
@@ -234,3 +234,24 @@ def test_engine_selection_errors():
     with pytest.raises(psw.PswError):
         ctx.set_engine(7)
     ctx.set_engine(psw.ENGINE_AUTO)
+
+
+def test_destroyed_sequences_leave_no_stale_graphs():
+    """Graphs that captured a sequence's buffers are dropped with it: fresh
+    sequences (which may reuse the old objects' addresses) decode correctly
+    on either engine, over several create/destroy rounds."""
+    base = synth.config("tiny")
+    ctx = psw.Context(base, synth.weights(base), precision=psw.PSW_BF16)
+    plan = [((8, 12), 0), ((5, 7), 1), ((6, 12), 0)]
+    items, fds = [], []
+    for k, ((H, W), sched) in enumerate(plan):
+        c = base.with_grid(H, W)
+        items += _encode(ctx, c, synth.frames(c, 1, seed=170 + k), sched)
+        fds.append(psw.frame_desc(H, W, sched))
+    ref = None
+    for engine in (psw.ENGINE_GRAPH, psw.ENGINE_PERSISTENT, psw.ENGINE_GRAPH, psw.ENGINE_AUTO,
+                   psw.ENGINE_PERSISTENT, psw.ENGINE_GRAPH):
+        got, _ = _engine_run(ctx, base, items, fds, engine)
+        if ref is None:
+            ref = got
+        _check_same(ref, got, items)

@@ -288,3 +288,17 @@ def test_invalid_arguments_and_budget():
     with pytest.raises(psw.PswError) as e:
         small.seq_create(8, 12)
     assert e.value.status == psw.PSW_ERR_OOM
+
+
+def test_bf16_1080p_pframe_crop_parity():
+    """P-frames (Context Transformer, temporal cross-attention over the
+    current and two previous frames) at the 1080p model sizes, BF16, on a
+    6-row crop (the same cropped frames on both sides), four frames so the
+    three-frame ring wraps."""
+    cfg = synth.config("p1080")
+    w = synth.weights(cfg)
+    crop = cfg.with_grid(6, cfg.W)
+    fr = synth.frames(crop, 4, seed=1003)
+    ctx = psw.Context(cfg, w, precision=psw.PSW_BF16)
+    res = _encode_decode(ctx, crop, fr, psw.PSW_SCHED_WAVEFRONT)
+    _check_frame(crop, oracle_weights(cfg, w, psw.PSW_BF16), fr, res, psw.PSW_BF16, 0)

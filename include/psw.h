@@ -245,7 +245,9 @@ psw_status psw_rans_encode_noalloc(const psw_ctx *ctx, const psw_frame_desc *fd,
  *                          graphs and replayed.
  *   PSW_ENGINE_PERSISTENT  one cooperative launch, one block per SM, walks
  *                          all steps (Sec. 3.2 schedule) with a grid-wide
- *                          barrier between phases; BF16 contexts only.
+ *                          barrier between phases; nothing is recorded per
+ *                          batch shape, so it suits batches that change
+ *                          from call to call; BF16 contexts only.
  *   PSW_ENGINE_AUTO        the graph engine (the faster of the two on the
  *                          1080p configurations measured; the default).
  * psw_set_engine returns PSW_ERR_INVALID for an unknown engine or for

@@ -933,8 +933,11 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
     }
     // graph key: the workspace generation, the engine and the batch shape
     bool failed = false;
-    bool graph = c->use_graphs && !c->prof;
+    // the persistent engine records no graphs: a call plans its token lists,
+    // launches the per-frame prologues and one cooperative kernel, so batches
+    // that change from call to call (a serving loop) cost no graph recording
     bool want = c->engine == PSW_ENGINE_PERSISTENT && c->prec == P_BF16;
+    bool graph = c->use_graphs && !c->prof && !want;
     std::vector<long> key{0, (long)n, (long)want};
     static_assert(KEY_SEQ0 == 3, "key layout");
     for (int b = 0; b < n; b++) {

@@ -53,7 +53,13 @@ typedef enum {
     PSW_ERR_CAPACITY = 6   /* output buffer too small                      */
 } psw_status;
 
-typedef enum { PSW_FP32 = 0, PSW_BF16 = 1 } psw_precision;
+/* PSW_FP8: the projections run on E4M3 operands with FP32 accumulation --
+ * weights quantised once per projection with a power-of-two scale, the
+ * token operand quantised per token with a power-of-two scale computed from
+ * that token's row alone (so a token's result never depends on the other
+ * tokens of a launch); everything else (caches, attention, norms, residual
+ * streams, heads' epilogue) is as in PSW_BF16. */
+typedef enum { PSW_FP32 = 0, PSW_BF16 = 1, PSW_FP8 = 2 } psw_precision;
 
 typedef enum {
     PSW_SCHED_WAVEFRONT = 0,   /* one step per label value, all positions of the step together */
@@ -104,7 +110,12 @@ size_t psw_weights_count(const psw_model_desc *desc);
 /* Create a context: validates the descriptor, uploads the weights (host
  * float32, psw_weights_count values) to the current CUDA device, converts
  * block projections to the compute precision (PSW_FP32 or PSW_BF16,
- * round-to-nearest-even) and builds the scale and CDF tables.
+ * round-to-nearest-even; PSW_FP8: every transformer-block projection whose
+ * shape the E4M3 tile takes -- K a multiple of 128, at most 512 for a
+ * normalised input and 1024 for the FFN down projection -- as E4M3 bytes,
+ * each source tensor with its own power-of-two scale as psw_quantize_e4m3
+ * computes it; the latent embedding, the heads and any other projection in
+ * BF16) and builds the scale and CDF tables.
  * hbm_budget bounds the device memory of this context and its sequences
  * (0 = no bound); a sequence that would exceed it fails with PSW_ERR_OOM.
  * On failure *out is NULL. */
@@ -198,6 +209,15 @@ psw_status psw_rate(psw_ctx *ctx, size_t n, const int16_t *yhat_dev, const float
 psw_status psw_quantize(psw_ctx *ctx, size_t n, const float *mu_dev, const float *sigma_dev,
                         uint8_t *idx_dev, int32_t *m_dev, void *stream);
 
+/* E4M3 quantisation of one weight tensor as PSW_FP8 contexts store it
+ * (Sec. 3.2 precision forms): with max |src| in [2^e, 2^(e+1)) the scale is
+ * s = 2^(e-7) (e clamped at -100; s = 1 for an all-zero tensor) and
+ * dst[i] = E4M3(src[i] / s), round to nearest even, so |src[i] / s| < 256.
+ * src_dev: n float32 on the device (16-byte aligned); dst_dev: n bytes on the
+ * device (4-byte aligned).  *scale_out = s (host).  Synchronous.
+ * PSW_ERR_INVALID for NaN or Inf among the values. */
+psw_status psw_quantize_e4m3(size_t n, const float *src_dev, uint8_t *dst_dev, float *scale_out);
+
 /* The scale table (64 float32) and CDF table l: freq[n] for slots
  * -T..T, ESC (n = 2T+2, sum 2^16).  Host outputs. */
 psw_status psw_scale_table(const psw_ctx *ctx, float *table_host);
@@ -247,7 +267,7 @@ psw_status psw_rans_encode_noalloc(const psw_ctx *ctx, const psw_frame_desc *fd,
  *                          all steps (Sec. 3.2 schedule) with a grid-wide
  *                          barrier between phases; nothing is recorded per
  *                          batch shape, so it suits batches that change
- *                          from call to call; BF16 contexts only.
+ *                          from call to call; BF16 and FP8 contexts.
  *   PSW_ENGINE_AUTO        the graph engine (the faster of the two on the
  *                          1080p configurations measured; the default).
  * psw_set_engine returns PSW_ERR_INVALID for an unknown engine or for

@@ -58,6 +58,10 @@ def _load():
             lib.or_visible.argtypes = [ct.c_int] * 7
             lib.or_window_keys.argtypes = [ct.POINTER(_Cfg), ct.c_int, ct.c_int, P, P]
             lib.or_schedule.argtypes = [ct.POINTER(_Cfg), ct.c_int, P, P]
+            lib.or_e4m3.argtypes = [ct.c_double]
+            lib.or_e4m3.restype = ct.c_double
+            lib.or_e4m3_tensor.argtypes = [ct.c_long, P, P]
+            lib.or_e4m3_tensor.restype = ct.c_double
             lib.or_scale_table.argtypes = [P]
             lib.or_quantize.argtypes = [ct.c_long, P, P, P, P]
             lib.or_cdf_T.argtypes = [ct.c_int]
@@ -153,6 +157,22 @@ def schedule(c, kind: int):
     order = np.zeros(HW, np.int32); start = np.zeros(HW + 1, np.int32)
     T = _load().or_schedule(ct.byref(_cfg(c)), kind, _p(order), _p(start))
     return order, start[:T + 1].copy()
+
+
+# ---------------------------------------------------------------- E4M3
+
+def e4m3(x: float) -> float:
+    """Nearest E4M3 value of x (ties to even, saturating at 448)."""
+    return float(_load().or_e4m3(float(x)))
+
+
+def e4m3_tensor(x):
+    """(dequantised values, scale) of one tensor quantised as the FP8
+    weights: a power-of-two scale s putting max |x| / s in [128, 256)."""
+    x = np.ascontiguousarray(x, np.float64)
+    out = np.zeros_like(x)
+    s = _load().or_e4m3_tensor(x.size, _p(x), _p(out))
+    return out, float(s)
 
 
 # ---------------------------------------------------------------- coding

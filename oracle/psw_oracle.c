@@ -40,7 +40,8 @@
  * Parity pins (see tests/test_oracle_*.py): closed forms for RMSNorm, SiLU,
  * SwiGLU, attention special cases and the quantised-Gaussian likelihood;
  * the Fig. 2b receptive field transcribed by hand; brute-force causality;
- * schedule equivalence; rANS round trips and CDF invariants.
+ * schedule equivalence; rANS round trips and CDF invariants; E4M3 rounding
+ * against hand values of the format and a library cast.
  */
 #include <math.h>
 #include <stdint.h>
@@ -637,6 +638,47 @@ int or_schedule(const or_cfg *c, int kind, int *order, int *start)
 
 /* ------------------------------------------------------------------------ */
 /* Scale table, quantisation, CDF tables, rate (Fig. 1: Q, AE/AD)            */
+/* ------------------------------------------------------------------------ */
+/* E4M3 weights (the FP8 precision form of Sec. 3.2's GEMMs)                  */
+/* ------------------------------------------------------------------------ */
+
+/* Nearest E4M3 value, ties to even, saturating at +-448.  The format: sign,
+ * 4 exponent bits with bias 7, 3 mantissa bits, no infinities; normal values
+ * (1 + m/8) 2^e for e = -6 .. 8 (the all-ones pattern at e = 8 is NaN, so
+ * 448 = 1.75 * 2^8 is the largest finite), subnormals (m/8) 2^-6.  Within a
+ * binade 2^e .. 2^(e+1) the spacing is 2^(e-3); below 2^-6 it is 2^-9. */
+double or_e4m3(double x)
+{
+    double a = fabs(x);
+    if (a == 0.0 || a != a) return x;
+    int e2;
+    frexp(a, &e2);                         /* a = f 2^e2, f in [0.5, 1) */
+    int e = e2 - 1;                        /* a in [2^e, 2^(e+1)) */
+    if (e < -6) e = -6;
+    double q = ldexp(1.0, e - 3);
+    double v = nearbyint(a / q) * q;       /* default rounding: to nearest, ties to even */
+    if (v > 448.0) v = 448.0;
+    return copysign(v, x);
+}
+
+/* One tensor quantised and dequantised as the FP8 weights: with max |x| in
+ * [2^e, 2^(e+1)) (e >= -100) the scale is s = 2^(e-7), s = 1 for an
+ * all-zero tensor, and out[i] = s E4M3(x[i] / s).  Returns s. */
+double or_e4m3_tensor(long n, const double *x, double *out)
+{
+    double amax = 0.0;
+    for (long i = 0; i < n; i++) amax = fmax(amax, fabs(x[i]));
+    double s = 1.0;
+    if (amax > 0.0) {
+        int e2;
+        frexp(amax, &e2);
+        int e = e2 - 1 < -100 ? -100 : e2 - 1;
+        s = ldexp(1.0, e - 7);
+    }
+    for (long i = 0; i < n; i++) out[i] = s * or_e4m3(x[i] / s);
+    return s;
+}
+
 /* ------------------------------------------------------------------------ */
 
 #define OR_NSCALES 64

@@ -12,8 +12,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <map>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 using namespace psw;
@@ -152,7 +154,9 @@ void graph_free(GraphRec &g)
 
 struct psw_ctx {
     psw_model_desc md;
-    int prec = 0;
+    int prec = 0;                      // storage / compute type of everything but E4M3 projections
+    bool fp8 = false;                  // PSW_FP8: block projections on E4M3 weights
+    std::unordered_map<const void *, const float *> f8sc;   // E4M3 operand -> its per-row dequantisation scales
     size_t budget = 0, bytes = 0, arena = 0;
     Layout lay;
     float *w = nullptr;                // flat FP32 weights on the device
@@ -200,6 +204,7 @@ struct psw_ctx {
     int *d_step = nullptr;             // direct-launch step tables
     size_t step_cap = 0;
     size_t p_smem = 0;
+    bool p_f8 = false;                 // the program has E4M3 projections
     int p_grid = 0;
     unsigned *d_pbar = nullptr;        // [0]: barrier counter, [1]: abort flag
     std::string err;
@@ -305,34 +310,65 @@ struct Scope {
 // ---------------------------------------------------------------- weights
 
 // Transposed ([out][in], K-major), compute-typed copies of every block
-// projection, carved from one arena.  A dry run only sums the sizes.
+// projection, carved from one arena.  A dry run only sums the sizes.  In an
+// FP8 context every block projection the E4M3 tile takes is stored as E4M3
+// bytes, each source tensor (Wq, Wk, Wv, Wg, ... of each block) quantised
+// with its own power-of-two scale, and followed by its vector of per-row
+// dequantisation scales; the latent embedding and the heads stay BF16.
 bool prepare_projections(psw_ctx *c, bool dry)
 {
     const psw_model_desc &m = c->md;
     const Layout &lay = c->lay;
     int d = m.d, prec = c->prec;
     size_t es = esize(prec), used = 0;
-    auto carve = [&](size_t rows, size_t cols) -> void * {
-        size_t sz = ((rows * cols * es + 255) / 256) * 256;
+    bool ok = true;
+    float *stage = nullptr;            // one source tensor in FP32 [N][K] before E4M3 quantisation
+    if (!dry && c->fp8 && cudaMalloc(&stage, (size_t)std::max(m.F, d) * std::max(m.F, d) * 4) != cudaSuccess)
+        return false;
+    auto carve_b = [&](size_t bytes) -> void * {
+        size_t sz = ((bytes + 255) / 256) * 256;
         void *p = dry ? nullptr : (void *)(c->wmat + used);
         used += sz;
         return p;
     };
+    auto carve = [&](size_t rows, size_t cols) -> void * { return carve_b(rows * cols * es); };
     auto tr = [&](long off, int K, int N, void *dst, int row_off) {
         if (!dry) launch_transpose_convert(prec, c->w + off, K, N, dst, row_off, 0);
     };
+    // One projection operand [N][K] from source tensors [K][n_i] (flat
+    // offsets) stacked at consecutive rows; asrc: how its tokens are built.
+    auto operand = [&](int N, int K, int asrc, std::initializer_list<long> srcs) -> void * {
+        bool f8 = c->fp8 && gemm_tc8_supported(N, K, asrc);
+        void *p = carve_b((size_t)N * K * (f8 ? 1 : es));
+        float *sc = f8 ? (float *)carve_b((size_t)N * 4) : nullptr;
+        int n = N / (int)srcs.size(), row = 0;
+        for (long off : srcs) {
+            if (dry) continue;
+            if (!f8) {
+                tr(off, K, n, p, row);
+            } else {
+                launch_transpose_convert(P_F32, c->w + off, K, n, stage, 0, 0);
+                float s = quantize_e4m3(stage, (size_t)n * K, (uint8_t *)p + (size_t)row * K);
+                std::vector<float> hs(n, s);
+                if (s <= 0.0f || cudaMemcpy(sc + row, hs.data(), (size_t)n * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                    ok = false;
+            }
+            row += n;
+        }
+        if (f8 && !dry) c->f8sc[p] = sc;
+        return p;
+    };
     auto mk_block = [&](const BlockOff &bo, bool cross) {
         BlockDev b;
-        b.Wqkv = carve(3 * d, d);
-        tr(bo.Wq, d, d, b.Wqkv, 0); tr(bo.Wk, d, d, b.Wqkv, d); tr(bo.Wv, d, d, b.Wqkv, 2 * d);
-        b.Wo = carve(d, d); tr(bo.Wo, d, d, b.Wo, 0);
-        b.Wg = carve(m.F, d); tr(bo.Wg, d, m.F, b.Wg, 0);
-        b.Wu = carve(m.F, d); tr(bo.Wu, d, m.F, b.Wu, 0);
-        b.Wd = carve(d, m.F); tr(bo.Wd, m.F, d, b.Wd, 0);
+        b.Wqkv = operand(3 * d, d, A_NORM, {bo.Wq, bo.Wk, bo.Wv});
+        b.Wo = operand(d, d, A_DIRECT, {bo.Wo});
+        b.Wg = operand(m.F, d, A_NORM, {bo.Wg});
+        b.Wu = operand(m.F, d, A_NORM, {bo.Wu});
+        b.Wd = operand(d, m.F, A_DIRECT, {bo.Wd});
         if (cross) {
-            b.Wxq = carve(d, d); tr(bo.Wxq, d, d, b.Wxq, 0);
-            b.Wxkv = carve(2 * d, d); tr(bo.Wxk, d, d, b.Wxkv, 0); tr(bo.Wxv, d, d, b.Wxkv, d);
-            b.Wxo = carve(d, d); tr(bo.Wxo, d, d, b.Wxo, 0);
+            b.Wxq = operand(d, d, A_NORM, {bo.Wxq});
+            b.Wxkv = operand(2 * d, d, A_NORM, {bo.Wxk, bo.Wxv});
+            b.Wxo = operand(d, d, A_DIRECT, {bo.Wxo});
         }
         return b;
     };
@@ -342,12 +378,14 @@ bool prepare_projections(psw_ctx *c, bool dry)
     for (int l = 0; l < m.L; l++) sm1.push_back(mk_block(lay.sm1[l], m.temporal != 0));
     for (int l = 0; l < m.L; l++) sm2.push_back(mk_block(lay.sm2[l], m.temporal != 0));
     BlockDev ab;
-    ab.Wqkv = carve(d, d); tr(lay.acc_Wq, d, d, ab.Wqkv, 0);
-    ab.Wxkv = carve(2 * d, d); tr(lay.acc_Wk, d, d, ab.Wxkv, 0); tr(lay.acc_Wv, d, d, ab.Wxkv, d);
-    ab.Wo = carve(d, d); tr(lay.acc_Wo, d, d, ab.Wo, 0);
-    ab.Wg = carve(m.F, d); tr(lay.acc_Wg, d, m.F, ab.Wg, 0);
-    ab.Wu = carve(m.F, d); tr(lay.acc_Wu, d, m.F, ab.Wu, 0);
-    ab.Wd = carve(d, m.F); tr(lay.acc_Wd, m.F, d, ab.Wd, 0);
+    ab.Wqkv = operand(d, d, A_NORM, {lay.acc_Wq});
+    ab.Wxkv = operand(2 * d, d, A_NORM, {lay.acc_Wk, lay.acc_Wv});
+    ab.Wo = operand(d, d, A_DIRECT, {lay.acc_Wo});
+    ab.Wg = operand(m.F, d, A_NORM, {lay.acc_Wg});
+    ab.Wu = operand(m.F, d, A_NORM, {lay.acc_Wu});
+    ab.Wd = operand(d, m.F, A_DIRECT, {lay.acc_Wd});
+    cudaFree(stage);
+    if (!ok) return false;
     void *win = carve(d, m.C); tr(lay.W_in, m.C, d, win, 0);
     void *wh1 = carve(2 * d, d); tr(lay.W1m, d, d, wh1, 0); tr(lay.W1s, d, d, wh1, d);
     void *wh2 = carve(2 * (size_t)m.C, 2 * d);
@@ -500,6 +538,11 @@ void gemm_any(const Pass &P, int asrc, const float *xrows, const float *a_gain, 
     g.Wt = Wt; g.Wt2 = Wt2; g.M = M; g.N = N; g.K = K; g.epi = e;
     g.epi.slots = P.S;
     g.status = P.c->d_status;
+    auto f8 = P.c->f8sc.find(Wt);
+    if (f8 != P.c->f8sc.end()) {
+        auto f82 = Wt2 ? P.c->f8sc.find(Wt2) : P.c->f8sc.end();
+        g.f8 = 1; g.wsc = f8->second; g.wsc2 = f82 != P.c->f8sc.end() ? f82->second : nullptr;
+    }
     if (P.rec) {
         if (!program_gemm(P.rec, g, P.tokset)) *P.failed = true;
         double nw = Wt2 ? 2.0 : 1.0;
@@ -507,12 +550,12 @@ void gemm_any(const Pass &P, int asrc, const float *xrows, const float *a_gain, 
         P.c->p_wbytes += nw * N * K * 2.0;
         return;
     }
-    bool tc = gemm_tc_supported(P.c->prec, N, K, asrc);
+    bool tc = g.f8 || gemm_tc_supported(P.c->prec, N, K, asrc);
     if (!tc && asrc != A_DIRECT) P.c->launches++;      // the operand-preparation kernel
-    double es = P.c->prec == P_BF16 ? 2.0 : 4.0, nw = Wt2 ? 2.0 : 1.0;
+    double es = P.c->prec == P_BF16 ? 2.0 : 4.0, nw = Wt2 ? 2.0 : 1.0, wes = g.f8 ? 1.0 : es;
     double out_b = (e.mode == EPI_RESID || e.mode == EPI_RESID_BASE) ? 8.0 : es;
     Scope sc(P.c, P.s, tc ? K_GEMM_TC : K_GEMM_SIMT, 2.0 * nw * M * N * K,
-             nw * N * K * es + (double)M * K * es + (double)M * N * out_b);
+             nw * N * K * wes + (double)M * K * es + (double)M * N * out_b);
     if (!gemm(P.c->prec, g, P.s)) *P.failed = true;
 }
 
@@ -735,8 +778,9 @@ bool ensure_program(psw_ctx *c)
     run_acc_sm2_heads(P, nullptr, 1);
     program_rans(c->prog);
     if (failed) return false;
-    if (!program_upload(c->prog, &c->p_ops, &c->p_nops, &c->p_maps, &c->p_nmaps, &c->p_smem)) return false;
-    if (!persist_prepare(c->p_smem, &c->p_grid)) return false;
+    if (!program_upload(c->prog, &c->p_ops, &c->p_nops, &c->p_maps, &c->p_nmaps, &c->p_smem, &c->p_f8))
+        return false;
+    if (!persist_prepare(c->p_smem, c->p_f8, &c->p_grid)) return false;
     if (!c->d_pbar && cudaMalloc(&c->d_pbar, 2 * sizeof(unsigned)) != cudaSuccess) return false;
     c->prog_ok = true;
     return true;
@@ -900,7 +944,7 @@ psw_status persist_run(psw_ctx *c, const int *d_tok, const int *d_step, const in
     double bytes = c->p_wbytes * Tmax + c->p_bytes_tok[TS_CUR] * ntok + c->p_bytes_tok[TS_PREV] * ntok_prev;
     {
         Scope sc(c, s, K_PERSIST, flops, bytes);
-        if (!persist_launch(pa, c->p_grid, c->p_smem, s))
+        if (!persist_launch(pa, c->p_grid, c->p_smem, c->p_f8, s))
             return fail(c, PSW_ERR_CUDA, "persistent decoder launch: %s", cudaGetErrorString(cudaGetLastError()));
     }
     Scope sc(c, s, K_RANS, 0.0, (double)n * c->md.C * 128.0);
@@ -1128,15 +1172,17 @@ psw_status psw_create(const psw_model_desc *desc, const float *weights_host, siz
     *out = nullptr;
     std::string why;
     if (!desc_valid(desc, why)) return fail(nullptr, PSW_ERR_INVALID, "%s", why.c_str());
-    if (precision != PSW_FP32 && precision != PSW_BF16)
+    if (precision != PSW_FP32 && precision != PSW_BF16 && precision != PSW_FP8)
         return fail(nullptr, PSW_ERR_INVALID, "unknown precision %d", precision);
     Layout lay = make_layout(*desc);
     if (!weights_host || n_weights != (size_t)lay.total)
         return fail(nullptr, PSW_ERR_INVALID, "expected %ld weights, got %zu", lay.total, n_weights);
-    if (precision == PSW_BF16 && !gemm_tc_available())
+    if (precision != PSW_FP32 && !gemm_tc_available())
         return fail(nullptr, PSW_ERR_CUDA, "the driver offers no cuTensorMapEncodeTiled entry point");
     psw_ctx *c = new psw_ctx();
-    c->md = *desc; c->prec = precision; c->budget = hbm_budget; c->lay = lay;
+    c->md = *desc; c->budget = hbm_budget; c->lay = lay;
+    c->prec = precision == PSW_FP8 ? P_BF16 : precision;
+    c->fp8 = precision == PSW_FP8;
     prepare_projections(c, /*dry=*/true);
     build_cdf_tables(c->tabs);
     c->bytes = (size_t)lay.total * 4 + c->arena + (size_t)c->tabs.total * 4 + 3 * 64 * 4 + 64 * 4 +
@@ -1470,13 +1516,27 @@ psw_status psw_rans_decode(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, con
 
 long psw_launch_count(const psw_ctx *c) { return c ? c->launches : 0; }
 
+psw_status psw_quantize_e4m3(size_t n, const float *src, uint8_t *dst, float *scale_out)
+{
+    if (!scale_out || (n && (!src || !dst))) return fail(nullptr, PSW_ERR_INVALID, "null argument");
+    if (((uintptr_t)src & 15) || ((uintptr_t)dst & 3)) return fail(nullptr, PSW_ERR_INVALID, "misaligned buffer");
+    float s = quantize_e4m3(src, n, dst);
+    if (s <= 0.0f) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(nullptr, PSW_ERR_CUDA, "E4M3 quantisation: %s", cudaGetErrorString(e));
+        return fail(nullptr, PSW_ERR_INVALID, "NaN or Inf among the values");
+    }
+    *scale_out = s;
+    return PSW_OK;
+}
+
 psw_status psw_set_engine(psw_ctx *c, int engine)
 {
     if (!c) return fail(nullptr, PSW_ERR_INVALID, "null context");
     if (engine < PSW_ENGINE_AUTO || engine > PSW_ENGINE_PERSISTENT)
         return fail(c, PSW_ERR_INVALID, "unknown engine %d", engine);
     if (engine == PSW_ENGINE_PERSISTENT && c->prec != P_BF16)
-        return fail(c, PSW_ERR_INVALID, "the persistent decoder runs BF16 contexts only");
+        return fail(c, PSW_ERR_INVALID, "the persistent decoder runs BF16 and FP8 contexts only");
     c->engine = engine;
     return PSW_OK;
 }

@@ -28,6 +28,15 @@
 // tile, so one CTA can run any sequence of tiles of any shapes and ring
 // depths.
 //
+// E4M3 projections (F8) take the same tile: weights are E4M3 bytes with a
+// dequantisation scale per feature row (one power of two per source tensor),
+// the token operand is always built in shared memory as E4M3 with a
+// power-of-two scale per token computed from that token's own row, the MMA is
+// kind::f8f6f4 (K = 32 per instruction) over 128-element chunks (the same 128
+// bytes per row as a bf16 chunk), and the epilogue multiplies the FP32
+// accumulator by the two scales, both powers of two, so dequantisation is
+// exact and a token's result still depends on nothing but its own row.
+//
 // Every mbarrier wait is bounded (~2 s of globaltimer); on expiry the CTA
 // raises its abort flag, waits (bounded) for its own copies and MMAs and
 // skips the epilogue; the caller reports ST_TIMEOUT.
@@ -37,6 +46,7 @@
 #include "device_common.cuh"
 
 #include <cuda.h>
+#include <cuda_fp8.h>
 
 namespace psw {
 namespace tc {
@@ -44,6 +54,7 @@ namespace tc {
 constexpr int TM = 128;        // output features per tile (MMA M)
 constexpr int NT = 64;         // tokens per tile (MMA N)
 constexpr int KC = 64;         // K elements per stage (128 bytes of bf16)
+constexpr int KC8 = 128;       // K elements per stage of an E4M3 projection (128 bytes)
 constexpr int MAXS = 8;        // ring stages at most (barrier pairs)
 constexpr int RING_BUDGET = 216 * 1024;   // dynamic shared memory of the ring and the resident operand
 constexpr int A_BYTES = TM * KC * 2;
@@ -55,6 +66,8 @@ constexpr int NISS = 4;        // MMA issuers (lane 0 of warps 1..4), one K step
 // tensor-memory columns of a tile: one 64-column accumulator (two for the
 // dual form) per issuer
 __host__ __device__ constexpr uint32_t tile_tcols(bool dual) { return (dual ? 2 : 1) * NT * NISS; }
+
+__host__ __device__ constexpr int kchunk(bool f8) { return f8 ? KC8 : KC; }
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -147,6 +160,23 @@ __device__ __forceinline__ void mma(uint32_t dt, uint64_t a, uint64_t b, uint32_
         : "memory");
 }
 
+// Instruction descriptor, kind::f8f6f4: F32 accumulate, E4M3 A and B
+// (format 0), both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma8(uint32_t dt, uint64_t a, uint64_t b, uint32_t id, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dt), "l"(a), "l"(b), "r"(id), "r"(acc)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
@@ -234,10 +264,38 @@ __device__ __forceinline__ uint32_t swz(int r, int k)
     return (uint32_t)kc * B_BYTES + (uint32_t)r * 128 + ((((byte >> 4) ^ (uint32_t)(r & 7))) << 4) + (byte & 15);
 }
 
+// The same for an 8-bit operand: atoms of 128 columns.
+__device__ __forceinline__ uint32_t swz8(int r, int k)
+{
+    int kc = k >> 7;
+    uint32_t byte = (uint32_t)(k & 127);
+    return (uint32_t)kc * B_BYTES + (uint32_t)r * 128 + ((((byte >> 4) ^ (uint32_t)(r & 7))) << 4) + (byte & 15);
+}
+
 __device__ __forceinline__ uint2 pack4(float a, float b, float c, float d)
 {
     __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
     return make_uint2(*reinterpret_cast<uint32_t *>(&lo), *reinterpret_cast<uint32_t *>(&hi));
+}
+
+// Four E4M3 values (round to nearest even, saturating), a in the low byte.
+__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d)
+{
+    uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
+
+// Power-of-two scaling of a row for E4M3: with max |x| in [2^e, 2^(e+1)),
+// x * 2^(7-e) has magnitude below 256 (E4M3 reaches 448).  Sets *qmul =
+// 2^(7-e) and returns the dequantisation scale 2^(e-7); e is clamped at
+// -100 so both stay normal FP32 numbers (an all-zero row gets 2^-107).
+__device__ __forceinline__ float row_scale_e4m3(float amax, float *qmul)
+{
+    int e = (int)((__float_as_uint(amax) >> 23) & 255) - 127;
+    e = e < -100 ? -100 : e;
+    *qmul = __uint_as_float((uint32_t)(127 + 7 - e) << 23);
+    return __uint_as_float((uint32_t)(127 - 7 + e) << 23);
 }
 
 // Per-CTA shared state of the engine.
@@ -246,6 +304,7 @@ struct GemmShared {
     uint32_t tmem_slot;
     volatile int abort;
     float stab[NSCALES];
+    float xs[NT];              // E4M3 projections: dequantisation scale of each token of the tile
     const int16_t *yrow[NT];
     uintptr_t tab[4][NT];
 };
@@ -295,11 +354,14 @@ __host__ __device__ constexpr int stage_bytes(bool dual, bool resident)
     return (dual ? 2 : 1) * A_BYTES + (resident ? 0 : B_BYTES);
 }
 
+// K chunks of a projection.
+__host__ __device__ constexpr int kchunks(int K, bool f8) { return (K + kchunk(f8) - 1) / kchunk(f8); }
+
 // Ring depth of a projection: as many stages as its K chunks, the barrier
 // pairs and the shared-memory budget (after the resident operand) allow.
-__host__ __device__ constexpr int ring_stages(bool dual, bool resident, int K)
+__host__ __device__ constexpr int ring_stages(bool dual, bool resident, int K, bool f8 = false)
 {
-    int nk = K / KC, res = resident ? nk * B_BYTES : 0;
+    int nk = kchunks(K, f8), res = resident ? nk * B_BYTES : 0;
     int st = (RING_BUDGET - res) / stage_bytes(dual, resident);
     st = st < MAXS ? st : MAXS;
     st = st < nk ? st : nk;
@@ -308,9 +370,10 @@ __host__ __device__ constexpr int ring_stages(bool dual, bool resident, int K)
 
 // Dynamic shared memory of a tile (ring, then the resident token operand),
 // without the 1024-byte alignment slack.
-__host__ __device__ constexpr int tile_smem(bool dual, bool resident, int K)
+__host__ __device__ constexpr int tile_smem(bool dual, bool resident, int K, bool f8 = false)
 {
-    return ring_stages(dual, resident, K) * stage_bytes(dual, resident) + (resident ? (K / KC) * B_BYTES : 0);
+    return ring_stages(dual, resident, K, f8) * stage_bytes(dual, resident) +
+           (resident ? kchunks(K, f8) * B_BYTES : 0);
 }
 
 // Initialise the barriers (thread 0; the caller synchronises).
@@ -412,6 +475,126 @@ static __device__ __noinline__ void build_tokens(const GemmArgs &g, int m0, uint
     }
 }
 
+// E4M3 token operand: RMSNorm rows as norm_rows, then each row quantised
+// with its own power-of-two scale (xs[r]); lane l holds elements 4l + 128c.
+template <int RB, int CH>
+__device__ __forceinline__ void norm_rows8(const float *__restrict__ xrows, const float *__restrict__ gain, int K,
+                                           int M, int m0, int r0, uint8_t *res, float *xs)
+{
+    const int lane = threadIdx.x & 31;
+    float4 v[RB][CH];
+    float ss[RB];
+#pragma unroll
+    for (int b = 0; b < RB; b++) {
+        int m = m0 + r0 + b;
+        const float *x = m < M ? xrows + (long)m * K : nullptr;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            int e = lane * 4 + c * 128;
+            v[b][c] = (x && e < K) ? *(const float4 *)(x + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < RB; b++) {
+        ss[b] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            ss[b] = fmaf(v[b][c].x, v[b][c].x, ss[b]); ss[b] = fmaf(v[b][c].y, v[b][c].y, ss[b]);
+            ss[b] = fmaf(v[b][c].z, v[b][c].z, ss[b]); ss[b] = fmaf(v[b][c].w, v[b][c].w, ss[b]);
+        }
+        ss[b] = warp_sum(ss[b]);
+    }
+#pragma unroll
+    for (int b = 0; b < RB; b++) {
+        int r = r0 + b;
+        float inv = m0 + r < M ? 1.0f / sqrtf(ss[b] / (float)K + 1e-6f) : 0.0f;
+        float amax = 0.0f;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            int e = lane * 4 + c * 128;
+            if (e >= K) continue;
+            const float *gn = gain + e;
+            v[b][c] = make_float4(v[b][c].x * inv * gn[0], v[b][c].y * inv * gn[1], v[b][c].z * inv * gn[2],
+                                  v[b][c].w * inv * gn[3]);
+            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[b][c].x), fabsf(v[b][c].y)), fmaxf(fabsf(v[b][c].z), fabsf(v[b][c].w))));
+        }
+        float qm, sc = row_scale_e4m3(warp_max(amax), &qm);
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            int e = lane * 4 + c * 128;
+            if (e >= K) continue;
+            *(uint32_t *)(res + swz8(r, e)) = e4m3x4(v[b][c].x * qm, v[b][c].y * qm, v[b][c].z * qm, v[b][c].w * qm);
+        }
+        if (lane == 0) xs[r] = sc;
+    }
+}
+
+// E4M3 token operand from compact bf16 rows A[m][lda] (K <= 1024): lane l
+// holds elements 8l + 256c of RB rows.
+template <int RB>
+__device__ __forceinline__ void quant_rows8(const __nv_bfloat16 *__restrict__ A, int lda, int K, int M, int m0,
+                                            int r0, uint8_t *res, float *xs)
+{
+    constexpr int CH = 4;
+    const int lane = threadIdx.x & 31;
+    uint4 q[RB][CH];
+#pragma unroll
+    for (int b = 0; b < RB; b++) {
+        int m = m0 + r0 + b;
+        const __nv_bfloat16 *row = m < M ? A + (long)m * lda : nullptr;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            int e = lane * 8 + c * 256;
+            q[b][c] = (row && e < K) ? *(const uint4 *)(row + e) : make_uint4(0, 0, 0, 0);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < RB; b++) {
+        float amax = 0.0f;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&q[b][c]);
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                float2 f = __bfloat1622float2(h[i]);
+                amax = fmaxf(amax, fmaxf(fabsf(f.x), fabsf(f.y)));
+            }
+        }
+        float qm, sc = row_scale_e4m3(warp_max(amax), &qm);
+        const int r = r0 + b;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            int e = lane * 8 + c * 256;
+            if (e >= K) continue;
+            const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&q[b][c]);
+            float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+            float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
+            *(uint2 *)(res + swz8(r, e)) = make_uint2(e4m3x4(f0.x * qm, f0.y * qm, f1.x * qm, f1.y * qm),
+                                                      e4m3x4(f2.x * qm, f2.y * qm, f3.x * qm, f3.y * qm));
+        }
+        if (lane == 0) xs[r] = sc;
+    }
+}
+
+// Build the E4M3 token operand of rows m0 .. m0+63 (warp w: rows 8w ..
+// 8w+7): A_NORM (K <= 512) or compact bf16 rows (A_DIRECT, K <= 1024).
+static __device__ __noinline__ void build_tokens8(const GemmArgs &g, int m0, uint8_t *res, float *xs)
+{
+    const int r0 = (threadIdx.x >> 5) * (NT / 8);
+    if (g.asrc == A_NORM) {
+        if (g.K <= 384) {
+            norm_rows8<8, 3>(g.xrows, g.a_gain, g.K, g.M, m0, r0, res, xs);
+        } else {
+            norm_rows8<4, 4>(g.xrows, g.a_gain, g.K, g.M, m0, r0, res, xs);
+            norm_rows8<4, 4>(g.xrows, g.a_gain, g.K, g.M, m0, r0 + 4, res, xs);
+        }
+        return;
+    }
+    const __nv_bfloat16 *A = (const __nv_bfloat16 *)g.A;
+    quant_rows8<4>(A, g.lda, g.K, g.M, m0, r0, res, xs);
+    quant_rows8<4>(A, g.lda, g.K, g.M, m0, r0 + 4, res, xs);
+}
+
 // Per-token addresses a mode needs, resolved once per tile by threads 0..63:
 // cache rows (EPI_STORE into a cache, EPI_QKV), the hyperprior row
 // (EPI_RESID_BASE), the head outputs (EPI_HEADS), the latents (A_EMBED).
@@ -453,7 +636,7 @@ __device__ __forceinline__ void build_table(const GemmArgs &g, int m0, GemmShare
 // every value before storing any (the output pointers are generic, so each
 // store could alias later loads).  Out of line: one copy per mode, small
 // enough to stay in the instruction cache.
-template <bool DUAL, int MODE>
+template <bool DUAL, int MODE, bool F8>
 static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, uint32_t tmem, const GemmArgs &g,
                                                   int f0, int m0, GemmPipe &pp)
 {
@@ -485,6 +668,12 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
     }
     const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     constexpr uint32_t ASTEP = (DUAL ? 2 : 1) * NT;                // columns between the issuers' accumulators
+    // E4M3: dequantisation scales of the feature row (both products below
+    // are of powers of two, hence exact)
+    float wf = 1.0f, wf2 = 1.0f;
+    if constexpr (F8) {
+        if (fok) { wf = g.wsc[f]; if (DUAL) wf2 = g.wsc2[f]; }
+    }
     if constexpr (RESID) {
 #pragma unroll
         for (int h = 0; h < 2; h++) {
@@ -492,6 +681,7 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
             tmem_sum16(trow + cb + 16 * h, ASTEP, v);
 #pragma unroll
             for (int j = 0; j < 16; j++) {
+                if constexpr (F8) v[j] *= wf * S.xs[cb + 16 * h + j];
                 const int m = m0 + cb + 16 * h + j;
                 if (fok && m < M) e.rows[(long)m * N + f] = old[16 * h + j] + v[j];
             }
@@ -511,6 +701,14 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
             int oi[8];
             tmem_sum8(trow + c0, ASTEP, v);
             if (DUAL) tmem_sum8(trow + NT + c0, ASTEP, v2);
+            if constexpr (F8) {
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    const float t = S.xs[c0 + j];
+                    v[j] *= wf * t;
+                    if (DUAL) v2[j] *= wf2 * t;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < 8; j++) {
                 const float y = v[j];
@@ -601,23 +799,24 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
 // the ring's stages (stage s issued by lane 0 of warp s: one thread issues a
 // tensor copy only every ~150 ns).  Returns the number of stages filled.  The
 // caller synchronises the CTA before gemm_tile_main.
-template <bool DUAL, int MODE>
+template <bool DUAL, int MODE, bool F8 = false>
 __device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const CUtensorMap *tmW,
                                              const CUtensorMap *tmW2, const GemmArgs &g, int f0, int m0,
                                              GemmPipe &pp)
 {
+    constexpr int KCH = kchunk(F8);
     if (MODE == EPI_HEADS && threadIdx.x < NSCALES) S.stab[threadIdx.x] = g.epi.scale[threadIdx.x];
     build_table<MODE>(g, m0, S);
-    const bool resident = g.asrc != A_DIRECT;
+    const bool resident = F8 || g.asrc != A_DIRECT;
     const int stage = stage_bytes(DUAL, resident);
-    const int nst = ring_stages(DUAL, resident, g.K);
+    const int nst = ring_stages(DUAL, resident, g.K, F8);
     const int s = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0 && s < nst) {
         // the ring is idle between tiles (the previous tile's MMAs are done)
         uint8_t *st = ring + s * stage;
         mbar_expect_tx(&S.full[s], stage);
-        tma_load(st, tmW, &S.full[s], s * KC, f0);
-        if (DUAL) tma_load(st + A_BYTES, tmW2, &S.full[s], s * KC, f0);
+        tma_load(st, tmW, &S.full[s], s * KCH, f0);
+        if (DUAL) tma_load(st + A_BYTES, tmW2, &S.full[s], s * KCH, f0);
     }
     return nst;
 }
@@ -626,16 +825,17 @@ __device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const
 // barrier: token operand, MMAs, epilogue.  `first` is gemm_tile_pre's
 // result.  Roles: lane 0 of warps 1..4 issue the MMAs; lane 0 of warps 0, 5,
 // 6 and 7 issue the copies of the chunks past the first ring fill, in turn.
-template <bool DUAL, int MODE>
+template <bool DUAL, int MODE, bool F8 = false>
 __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *tmW,
                                                const CUtensorMap *tmW2, const CUtensorMap *tmX, const GemmArgs &g,
                                                int f0, int m0, int first, GemmPipe &pp)
 {
     constexpr int NACC = DUAL ? 2 : 1;
     constexpr int NPROD = NTHREADS / 32 - NISS;                    // producer warps: 0 and NISS+1 ..
-    const bool resident = g.asrc != A_DIRECT;
+    constexpr int KCH = kchunk(F8);
+    const bool resident = F8 || g.asrc != A_DIRECT;
     const int stage = stage_bytes(DUAL, resident);
-    const int nk = g.K / KC, nst = ring_stages(DUAL, resident, g.K);
+    const int nk = kchunks(g.K, F8), nst = ring_stages(DUAL, resident, g.K, F8);
     uint8_t *res = ring + nst * stage;                             // resident token operand
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -649,7 +849,8 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
             tma_load(ring + s * stage + NACC * A_BYTES, tmX, &S.full[s], s * KC, m0);
     }
     if (resident) {
-        build_tokens(g, m0, res, S.yrow);
+        if (F8) build_tokens8(g, m0, res, S.xs);
+        else build_tokens(g, m0, res, S.yrow);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
     }
@@ -663,8 +864,8 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
             if (!mbar_wait(&S.empty[s], release_parity(pp, s, u))) { S.abort = 1; break; }
             uint8_t *st = ring + s * stage;
             mbar_expect_tx(&S.full[s], stage);
-            tma_load(st, tmW, &S.full[s], j * KC, f0);
-            if (DUAL) tma_load(st + A_BYTES, tmW2, &S.full[s], j * KC, f0);
+            tma_load(st, tmW, &S.full[s], j * KCH, f0);
+            if (DUAL) tma_load(st + A_BYTES, tmW2, &S.full[s], j * KCH, f0);
             if (!resident) tma_load(st + NACC * A_BYTES, tmX, &S.full[s], j * KC, m0);
             jend = j + NPROD;
         }
@@ -678,7 +879,7 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
         // four issuers shorten the dependent chain fourfold); a stage that is
         // filled again in this tile is released once all four have committed
         const int q = warp - 1;
-        const uint32_t id = idesc_bf16(TM, NT);
+        const uint32_t id = F8 ? idesc_e4m3(TM, NT) : idesc_bf16(TM, NT);
         const uint32_t acc0 = tmem + (uint32_t)q * (NACC * NT);
         for (int j = 0; j < nk; j++) {
             int s = j % nst, u = j / nst;
@@ -687,22 +888,29 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
             fence_after();
             uint32_t base = su32(ring + s * stage);
             uint32_t bb = resident ? su32(res) + j * B_BYTES : base + NACC * A_BYTES;
-            mma(acc0, sdesc(base + q * 32), sdesc(bb + q * 32), id, j != 0);
-            if (DUAL) mma(acc0 + NT, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
+            // K step q: 32 bytes along the 128-byte rows (16 bf16 or 32 E4M3)
+            if (F8) {
+                mma8(acc0, sdesc(base + q * 32), sdesc(bb + q * 32), id, j != 0);
+                if (DUAL) mma8(acc0 + NT, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
+            } else {
+                mma(acc0, sdesc(base + q * 32), sdesc(bb + q * 32), id, j != 0);
+                if (DUAL) mma(acc0 + NT, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
+            }
             if (j + nst < nk) mma_commit(&S.empty[s]);                 // the stage is filled again in this tile
         }
         mma_commit(&S.done);
     }
     __syncwarp();
-    gemm_epilogue<DUAL, MODE>(S, ring, tmem, g, f0, m0, pp);
+    gemm_epilogue<DUAL, MODE, F8>(S, ring, tmem, g, f0, m0, pp);
     pipe_advance(pp, nk, nst);
 }
 
 }  // namespace tc
 
 // A tensor map of the 2D bf16 array [rows][ld] (K used columns), box of
-// box_rows x 64 elements, 128-byte swizzle, rows past the end read as zero
-// (cached per argument tuple; host).
-bool gemm_tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensorMap *out);
+// box_rows x 64 elements (x 128 bytes for an E4M3 array, f8), 128-byte
+// swizzle, rows and columns past the end read as zero (cached per argument
+// tuple; host).
+bool gemm_tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensorMap *out, bool f8 = false);
 
 }  // namespace psw

@@ -1,10 +1,13 @@
-// gemm_tc.cu -- the BF16 projection GEMM as one kernel launch per
+// gemm_tc.cu -- the BF16 and E4M3 projection GEMMs as one kernel launch per
 // projection: one 128-feature x 64-token tile per CTA (the tile functions of
 // gemm_dev.cuh), weights prefetched before the programmatic-dependent-launch
 // wait, plus the host side shared with the persistent decoder (tensor maps,
-// shared-memory sizes, kernel attributes).
+// shared-memory sizes, kernel attributes) and the E4M3 weight quantiser.
 #include "gemm_dev.cuh"
 
+#include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -15,7 +18,7 @@ using namespace tc;
 
 namespace {
 
-template <bool DUAL, int MODE>
+template <bool DUAL, int MODE, bool F8>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmW2,
           const __grid_constant__ CUtensorMap tmX, GemmArgs g, int *status)
@@ -33,13 +36,13 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
     // whole decode, and the weights for the context's life: read them before
     // waiting for the previous kernel
     GemmPipe pp;
-    int first = gemm_tile_pre<DUAL, MODE>(S, ring, &tmW, &tmW2, g, f0, m0, pp);
+    int first = gemm_tile_pre<DUAL, MODE, F8>(S, ring, &tmW, &tmW2, g, f0, m0, pp);
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = S.tmem_slot;
     pdl_wait();                                        // activations are ready from here on
-    gemm_tile_main<DUAL, MODE>(S, ring, tmem, &tmW, &tmW2, &tmX, g, f0, m0, first, pp);
+    gemm_tile_main<DUAL, MODE, F8>(S, ring, tmem, &tmW, &tmW2, &tmX, g, f0, m0, first, pp);
     if (threadIdx.x == 0 && S.abort) atomicOr(status, ST_TIMEOUT);
     if ((threadIdx.x >> 5) == 0) tmem_free(tmem, TCOLS);
 }
@@ -52,7 +55,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 std::mutex g_mu;
 EncodeTiledFn g_encode = nullptr;
-std::map<std::tuple<const void *, int, int, int, int>, CUtensorMap> g_maps;
+std::map<std::tuple<const void *, int, int, int, int, bool>, CUtensorMap> g_maps;
 
 EncodeTiledFn encoder()
 {
@@ -67,22 +70,23 @@ EncodeTiledFn encoder()
     return g_encode;
 }
 
-// 2D bf16 [rows][ld] (K used columns) with a box of box_rows x 64, 128-byte
-// swizzle; rows past the end read as zero.
-bool tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensorMap *out)
+// 2D bf16 [rows][ld] (K used columns) with a box of box_rows x 64 (E4M3,
+// f8: box_rows x 128 bytes), 128-byte swizzle; rows past the end read as
+// zero.
+bool tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensorMap *out, bool f8 = false)
 {
     std::lock_guard<std::mutex> lk(g_mu);
-    auto key = std::make_tuple(ptr, rows, K, ld, box_rows);
+    auto key = std::make_tuple(ptr, rows, K, ld, box_rows, f8);
     auto it = g_maps.find(key);
     if (it != g_maps.end()) { *out = it->second; return true; }
     EncodeTiledFn enc = encoder();
     if (!enc) return false;
     CUtensorMap m;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * (f8 ? 1 : 2)};
+    cuuint32_t box[2] = {(cuuint32_t)kchunk(f8), (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
+    CUresult r = enc(&m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
@@ -92,13 +96,41 @@ bool tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensor
     return true;
 }
 
-size_t smem_bytes(bool dual, bool resident, int K) { return (size_t)tile_smem(dual, resident, K) + 1024; }
+size_t smem_bytes(bool dual, bool resident, int K, bool f8 = false)
+{
+    return (size_t)tile_smem(dual, resident, K, f8) + 1024;
+}
+
+// ---------------------------------------------------------------- E4M3 weights
+
+__global__ void k_absmax(const float *__restrict__ src, size_t n, unsigned *out)
+{
+    float a = 0.0f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        a = fmaxf(a, fabsf(src[i]));
+    a = warp_max(a);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(a));     // non-negative: bit order = value order
+}
+
+__global__ void k_quant_e4m3(const float *__restrict__ src, size_t n, float qmul, uint8_t *__restrict__ dst)
+{
+    size_t n4 = n / 4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        float4 v = reinterpret_cast<const float4 *>(src)[i];
+        reinterpret_cast<uint32_t *>(dst)[i] = e4m3x4(v.x * qmul, v.y * qmul, v.z * qmul, v.w * qmul);
+    }
+    size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t < n - 4 * n4) {
+        size_t i = 4 * n4 + t;
+        dst[i] = (uint8_t)(e4m3x4(src[i] * qmul, 0.0f, 0.0f, 0.0f) & 255u);
+    }
+}
 
 }  // namespace
 
-bool gemm_tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensorMap *out)
+bool gemm_tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensorMap *out, bool f8)
 {
-    return tensor_map(ptr, rows, K, ld, box_rows, out);
+    return tensor_map(ptr, rows, K, ld, box_rows, out, f8);
 }
 
 bool gemm_tc_supported(int prec, int N, int K, int asrc)
@@ -106,11 +138,44 @@ bool gemm_tc_supported(int prec, int N, int K, int asrc)
     return prec == P_BF16 && K % KC == 0 && K >= KC && N >= 1 && (asrc == A_DIRECT || K <= KRES_MAX);
 }
 
-template <bool DUAL, int MODE>
+// E4M3 projections: whole 128-element chunks, a token operand the CTA can
+// build (RMSNorm rows up to 512 wide, bf16 rows up to 1024) and a weight ring
+// that fits beside it.
+bool gemm_tc8_supported(int N, int K, int asrc)
+{
+    if (N < 1 || K < KC8 || K % KC8) return false;
+    if (!(asrc == A_NORM ? K <= KRES_MAX : asrc == A_DIRECT ? K <= 1024 : false)) return false;
+    return tile_smem(true, true, K, true) <= RING_BUDGET;
+}
+
+float quantize_e4m3(const float *src, size_t n, uint8_t *dst)
+{
+    if (n == 0) return 1.0f;
+    unsigned *d_max = nullptr, bits = 0;
+    if (cudaMalloc(&d_max, sizeof(unsigned)) != cudaSuccess) return -1.0f;
+    cudaMemset(d_max, 0, sizeof(unsigned));
+    int blocks = (int)std::min<size_t>((n + 255) / 256, 1024);
+    k_absmax<<<blocks, 256>>>(src, n, d_max);
+    cudaError_t e = cudaMemcpy(&bits, d_max, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(d_max);
+    if (e != cudaSuccess) return -1.0f;
+    float amax;
+    memcpy(&amax, &bits, sizeof amax);
+    if (!(amax <= 3.0e38f)) return -1.0f;                              // NaN or Inf among the weights
+    int ex = 0;
+    if (amax > 0.0f) std::frexp(amax, &ex);                            // amax = f 2^ex, f in [0.5, 1)
+    int el = amax > 0.0f ? std::max(ex - 1, -100) : 7;                 // max |w| in [2^el, 2^(el+1))
+    float s = std::ldexp(1.0f, el - 7), qmul = std::ldexp(1.0f, 7 - el);
+    k_quant_e4m3<<<blocks, 256>>>(src, n, qmul, dst);
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1.0f;
+    return s;
+}
+
+template <bool DUAL, int MODE, bool F8 = false>
 bool set_attr(size_t bytes)
 {
-    return cudaFuncSetAttribute(k_gemm_tc<DUAL, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
-           cudaSuccess;
+    return cudaFuncSetAttribute(k_gemm_tc<DUAL, MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes) == cudaSuccess;
 }
 
 // Checks for the tensor-map entry point and raises the kernels' dynamic
@@ -122,11 +187,45 @@ bool gemm_tc_available()
     size_t m2 = RING_BUDGET + 1024, m1 = RING_BUDGET + 1024;
     return set_attr<true, EPI_SWIGLU>(m2) && set_attr<false, EPI_STORE>(m1) && set_attr<false, EPI_QKV>(m1) &&
            set_attr<false, EPI_RESID>(m1) && set_attr<false, EPI_RESID_BASE>(m1) &&
-           set_attr<false, EPI_BIAS_SILU>(m1) && set_attr<false, EPI_SET_BIAS>(m1) && set_attr<false, EPI_HEADS>(m1);
+           set_attr<false, EPI_BIAS_SILU>(m1) && set_attr<false, EPI_SET_BIAS>(m1) && set_attr<false, EPI_HEADS>(m1) &&
+           set_attr<true, EPI_SWIGLU, true>(m2) && set_attr<false, EPI_STORE, true>(m1) &&
+           set_attr<false, EPI_QKV, true>(m1) && set_attr<false, EPI_RESID, true>(m1) &&
+           set_attr<false, EPI_RESID_BASE, true>(m1);
 }
+
+namespace {
+
+// E4M3 projection launch: the five epilogues block projections use.
+bool gemm_tc8(const GemmArgs &g, cudaStream_t s)
+{
+    CUtensorMap tw, tw2;
+    bool dual = g.epi.mode == EPI_SWIGLU;
+    if (!g.wsc || (dual && !g.wsc2) || !gemm_tc8_supported(g.N, g.K, g.asrc)) return false;
+    if (!tensor_map(g.Wt, g.N, g.K, g.K, TM, &tw, true)) return false;
+    if (dual && !tensor_map(g.Wt2, g.N, g.K, g.K, TM, &tw2, true)) return false;
+    if (!dual) tw2 = tw;
+    dim3 grid((g.N + TM - 1) / TM, (g.M + NT - 1) / NT), block(NTHREADS);
+    size_t smem = smem_bytes(dual, true, g.K, true);
+    int *st = g.status;
+    cudaError_t e;
+    switch (g.epi.mode) {
+    case EPI_SWIGLU: e = launch_pdl(k_gemm_tc<true, EPI_SWIGLU, true>, grid, block, smem, s, tw, tw2, tw, g, st); break;
+    case EPI_STORE: e = launch_pdl(k_gemm_tc<false, EPI_STORE, true>, grid, block, smem, s, tw, tw2, tw, g, st); break;
+    case EPI_QKV: e = launch_pdl(k_gemm_tc<false, EPI_QKV, true>, grid, block, smem, s, tw, tw2, tw, g, st); break;
+    case EPI_RESID: e = launch_pdl(k_gemm_tc<false, EPI_RESID, true>, grid, block, smem, s, tw, tw2, tw, g, st); break;
+    case EPI_RESID_BASE:
+        e = launch_pdl(k_gemm_tc<false, EPI_RESID_BASE, true>, grid, block, smem, s, tw, tw2, tw, g, st);
+        break;
+    default: return false;
+    }
+    return e == cudaSuccess;
+}
+
+}  // namespace
 
 bool gemm_tc(const GemmArgs &g, cudaStream_t s)
 {
+    if (g.f8) return gemm_tc8(g, s);
     CUtensorMap tw, tw2, tx;
     bool dual = g.epi.mode == EPI_SWIGLU;
     bool resident = g.asrc != A_DIRECT;
@@ -144,18 +243,18 @@ bool gemm_tc(const GemmArgs &g, cudaStream_t s)
     dim3 block(NTHREADS);
     cudaError_t e;
     switch (g.epi.mode) {
-    case EPI_SWIGLU: e = launch_pdl(k_gemm_tc<true, EPI_SWIGLU>, grid, block, smem, s, tw, tw2, tx, g, st); break;
-    case EPI_STORE: e = launch_pdl(k_gemm_tc<false, EPI_STORE>, grid, block, smem, s, tw, tw2, tx, g, st); break;
-    case EPI_QKV: e = launch_pdl(k_gemm_tc<false, EPI_QKV>, grid, block, smem, s, tw, tw2, tx, g, st); break;
-    case EPI_RESID: e = launch_pdl(k_gemm_tc<false, EPI_RESID>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_SWIGLU: e = launch_pdl(k_gemm_tc<true, EPI_SWIGLU, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_STORE: e = launch_pdl(k_gemm_tc<false, EPI_STORE, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_QKV: e = launch_pdl(k_gemm_tc<false, EPI_QKV, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_RESID: e = launch_pdl(k_gemm_tc<false, EPI_RESID, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
     case EPI_RESID_BASE:
-        e = launch_pdl(k_gemm_tc<false, EPI_RESID_BASE>, grid, block, smem, s, tw, tw2, tx, g, st);
+        e = launch_pdl(k_gemm_tc<false, EPI_RESID_BASE, false>, grid, block, smem, s, tw, tw2, tx, g, st);
         break;
     case EPI_BIAS_SILU:
-        e = launch_pdl(k_gemm_tc<false, EPI_BIAS_SILU>, grid, block, smem, s, tw, tw2, tx, g, st);
+        e = launch_pdl(k_gemm_tc<false, EPI_BIAS_SILU, false>, grid, block, smem, s, tw, tw2, tx, g, st);
         break;
-    case EPI_SET_BIAS: e = launch_pdl(k_gemm_tc<false, EPI_SET_BIAS>, grid, block, smem, s, tw, tw2, tx, g, st); break;
-    case EPI_HEADS: e = launch_pdl(k_gemm_tc<false, EPI_HEADS>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_SET_BIAS: e = launch_pdl(k_gemm_tc<false, EPI_SET_BIAS, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_HEADS: e = launch_pdl(k_gemm_tc<false, EPI_HEADS, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
     default: return false;
     }
     return e == cudaSuccess;

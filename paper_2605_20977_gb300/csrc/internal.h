@@ -121,6 +121,10 @@ enum ASrc {
 struct GemmArgs {
     const void *A; int lda;       // A_DIRECT: [M][lda]
     int asrc;
+    int f8;                       // 1: E4M3 projection: Wt / Wt2 are E4M3 [N][K] bytes, row f of each
+                                  //    dequantised by wsc[f] / wsc2[f]; the token operand is quantised
+                                  //    per token with a power-of-two scale
+    const float *wsc, *wsc2;
     const float *xrows;           // A_NORM: FP32 rows [M][K]
     const float *a_gain;          // A_NORM gain [K]; A_EMBED channel scaling [K]
     void *prep;                   // compact [M][K] scratch for the SIMT path's operand
@@ -136,6 +140,12 @@ struct GemmArgs {
 // kernel.  Returns false if the launch could not be prepared.
 bool gemm(int prec, const GemmArgs &g, cudaStream_t s);
 bool gemm_tc_supported(int prec, int N, int K, int asrc);
+bool gemm_tc8_supported(int N, int K, int asrc);
+// E4M3 weights of one tensor: dst[i] = e4m3_rn(src[i] / s) with the
+// power-of-two s = 2^(e - 7), max |src| in [2^e, 2^(e+1)) (s = 1 for an
+// all-zero tensor); n FP32 values on the device.  Returns s, or a negative
+// value on a CUDA error.  Synchronous.
+float quantize_e4m3(const float *src, size_t n, uint8_t *dst);
 bool gemm_tc_available();         // driver entry point for tensor maps present
 void launch_gather_embed(int prec, const Slot *S, const int *tok, int n, const float *gamma, int C, void *dst,
                          cudaStream_t s);
@@ -271,11 +281,12 @@ void program_attn(ProgramBuilder *b, const AttnArgs &a, int tokset);
 void program_rans(ProgramBuilder *b);
 // Upload the program and its tensor maps; the device arrays stay valid until
 // program_free.  Returns false on a CUDA error.
-bool program_upload(ProgramBuilder *b, const Op **ops, int *nops, const void **maps, int *nmaps, size_t *smem);
+bool program_upload(ProgramBuilder *b, const Op **ops, int *nops, const void **maps, int *nmaps, size_t *smem,
+                    bool *f8);
 // Kernel attributes and the grid (one CTA per SM, all co-resident) for a
 // dynamic shared-memory size; false if that cannot be resident.
-bool persist_prepare(size_t smem, int *grid);
-bool persist_launch(const PersistArgs &a, int grid, size_t smem, cudaStream_t s);
+bool persist_prepare(size_t smem, bool f8, int *grid);
+bool persist_launch(const PersistArgs &a, int grid, size_t smem, bool f8, cudaStream_t s);
 
 }  // namespace psw
 

@@ -112,20 +112,33 @@ __device__ __forceinline__ int gemm_tiles(const GemmArgs &g, int &nf)
     return nf * ((g.M + NT - 1) / NT);
 }
 
-template <bool DUAL, int MODE>
+template <bool DUAL, int MODE, bool F8 = false>
 __device__ __forceinline__ int pre_t(GemmShared &S, uint8_t *ring, const CUtensorMap *maps, const Op &op, int j,
                                      GemmPipe &pp)
 {
     int nf;
     gemm_tiles(op.g, nf);
-    return gemm_tile_pre<DUAL, MODE>(S, ring, maps + op.wmap, maps + (op.wmap2 >= 0 ? op.wmap2 : op.wmap), op.g,
-                                     (j % nf) * TM, (j / nf) * NT, pp);
+    return gemm_tile_pre<DUAL, MODE, F8>(S, ring, maps + op.wmap, maps + (op.wmap2 >= 0 ? op.wmap2 : op.wmap), op.g,
+                                         (j % nf) * TM, (j / nf) * NT, pp);
 }
 
-// gemm_tile_pre of tile j of a projection phase.
+// gemm_tile_pre of tile j of a projection phase.  F8: the program has E4M3
+// projections (the five epilogues of block projections).
+template <bool F8>
 __device__ __noinline__ int gemm_pre(GemmShared &S, uint8_t *ring, const CUtensorMap *maps, const Op &op, int j,
                                      GemmPipe &pp)
 {
+    if constexpr (F8) {
+        if (op.g.f8) {
+            switch (op.g.epi.mode) {
+            case EPI_SWIGLU: return pre_t<true, EPI_SWIGLU, true>(S, ring, maps, op, j, pp);
+            case EPI_STORE: return pre_t<false, EPI_STORE, true>(S, ring, maps, op, j, pp);
+            case EPI_QKV: return pre_t<false, EPI_QKV, true>(S, ring, maps, op, j, pp);
+            case EPI_RESID: return pre_t<false, EPI_RESID, true>(S, ring, maps, op, j, pp);
+            default: return pre_t<false, EPI_RESID_BASE, true>(S, ring, maps, op, j, pp);
+            }
+        }
+    }
     switch (op.g.epi.mode) {
     case EPI_SWIGLU: return pre_t<true, EPI_SWIGLU>(S, ring, maps, op, j, pp);
     case EPI_STORE: return pre_t<false, EPI_STORE>(S, ring, maps, op, j, pp);
@@ -140,7 +153,7 @@ __device__ __noinline__ int gemm_pre(GemmShared &S, uint8_t *ring, const CUtenso
 
 // This CTA's tiles of a projection phase (tiles rank, rank + grid, ...); the
 // first may have been prepared (gemm_pre) before the barrier.
-template <bool DUAL, int MODE>
+template <bool DUAL, int MODE, bool F8 = false>
 __device__ __noinline__ void gemm_phase(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *maps,
                                         const Op &op, int rank, bool prepared, int first, GemmPipe &pp)
 {
@@ -151,17 +164,31 @@ __device__ __noinline__ void gemm_phase(GemmShared &S, uint8_t *ring, uint32_t t
     for (int j = rank; j < ntiles; j += gridDim.x) {
         const int f0 = (j % nf) * TM, m0 = (j / nf) * NT;
         if (!(prepared && j == rank)) {
-            first = gemm_tile_pre<DUAL, MODE>(S, ring, tw, tw2, op.g, f0, m0, pp);
+            first = gemm_tile_pre<DUAL, MODE, F8>(S, ring, tw, tw2, op.g, f0, m0, pp);
             __syncthreads();
         }
-        gemm_tile_main<DUAL, MODE>(S, ring, tmem, tw, tw2, tx, op.g, f0, m0, first, pp);
+        gemm_tile_main<DUAL, MODE, F8>(S, ring, tmem, tw, tw2, tx, op.g, f0, m0, first, pp);
         if (S.abort) return;
     }
 }
 
+template <bool F8>
 __device__ __noinline__ void run_gemm(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *maps,
                                       const Op &op, int rank, bool prepared, int first, GemmPipe &pp)
 {
+    if constexpr (F8) {
+        if (op.g.f8) {
+            switch (op.g.epi.mode) {
+            case EPI_SWIGLU: gemm_phase<true, EPI_SWIGLU, true>(S, ring, tmem, maps, op, rank, prepared, first, pp); return;
+            case EPI_STORE: gemm_phase<false, EPI_STORE, true>(S, ring, tmem, maps, op, rank, prepared, first, pp); return;
+            case EPI_QKV: gemm_phase<false, EPI_QKV, true>(S, ring, tmem, maps, op, rank, prepared, first, pp); return;
+            case EPI_RESID: gemm_phase<false, EPI_RESID, true>(S, ring, tmem, maps, op, rank, prepared, first, pp); return;
+            default:
+                gemm_phase<false, EPI_RESID_BASE, true>(S, ring, tmem, maps, op, rank, prepared, first, pp);
+                return;
+            }
+        }
+    }
     switch (op.g.epi.mode) {
     case EPI_SWIGLU: gemm_phase<true, EPI_SWIGLU>(S, ring, tmem, maps, op, rank, prepared, first, pp); break;
     case EPI_STORE: gemm_phase<false, EPI_STORE>(S, ring, tmem, maps, op, rank, prepared, first, pp); break;
@@ -203,6 +230,7 @@ __device__ __forceinline__ int phase_units(const PersistArgs &P, const Op &op)
     return (items + PWARPS - 1) / PWARPS;
 }
 
+template <bool F8>
 __global__ void __launch_bounds__(NTHREADS, 1) k_persist(const __grid_constant__ PersistArgs P)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -248,12 +276,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_persist(const __grid_constant__
             // idle in this phase: prepare the next phase's first tile now
             int nf;
             if (nrank < gemm_tiles(nop.g, nf)) {
-                first = gemm_pre(S, dyn, maps, nop, nrank, pp);
+                first = gemm_pre<F8>(S, dyn, maps, nop, nrank, pp);
                 nprep = true;
             }
         }
         if (busy) {
-            if (op.type == OP_GEMM) run_gemm(S, dyn, tmem, maps, op, rank, prepared, first, pp);
+            if (op.type == OP_GEMM) run_gemm<F8>(S, dyn, tmem, maps, op, rank, prepared, first, pp);
             else if (op.type == OP_ATTN) {
                 const int dh = op.a.d / op.a.nh;
                 if (dh == 64) attn_phase<64>(op.a, dyn, rank);
@@ -277,7 +305,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_persist(const __grid_constant__
         if (busy && nop.type == OP_GEMM) {
             int nf;
             if (nrank < gemm_tiles(nop.g, nf)) {
-                first = gemm_pre(S, dyn, maps, nop, nrank, pp);
+                first = gemm_pre<F8>(S, dyn, maps, nop, nrank, pp);
                 nprep = true;
             }
         }
@@ -303,19 +331,20 @@ struct ProgramBuilder {
     int ws_rows;
     std::vector<Op> ops;
     std::vector<CUtensorMap> maps;
-    std::map<std::tuple<const void *, int, int, int, int>, int> map_idx;
+    std::map<std::tuple<const void *, int, int, int, int, bool>, int> map_idx;
     size_t smem = 0;
+    bool f8 = false;                   // some projection is E4M3
     Op *d_ops = nullptr;
     CUtensorMap *d_maps = nullptr;
 };
 
-static int map_of(ProgramBuilder *b, const void *ptr, int rows, int K, int ld, int box)
+static int map_of(ProgramBuilder *b, const void *ptr, int rows, int K, int ld, int box, bool f8 = false)
 {
-    auto key = std::make_tuple(ptr, rows, K, ld, box);
+    auto key = std::make_tuple(ptr, rows, K, ld, box, f8);
     auto it = b->map_idx.find(key);
     if (it != b->map_idx.end()) return it->second;
     CUtensorMap m;
-    if (!gemm_tensor_map(ptr, rows, K, ld, box, &m)) return -1;
+    if (!gemm_tensor_map(ptr, rows, K, ld, box, &m, f8)) return -1;
     b->maps.push_back(m);
     return b->map_idx[key] = (int)b->maps.size() - 1;
 }
@@ -337,19 +366,23 @@ void program_free(ProgramBuilder *b)
 
 bool program_gemm(ProgramBuilder *b, const GemmArgs &g, int tokset)
 {
-    if (!gemm_tc_supported(P_BF16, g.N, g.K, g.asrc)) return false;
+    const bool f8 = g.f8 != 0;
+    if (f8 ? !gemm_tc8_supported(g.N, g.K, g.asrc) : !gemm_tc_supported(P_BF16, g.N, g.K, g.asrc)) return false;
     Op op{};
     op.type = OP_GEMM; op.tokset = tokset;
     op.dual = g.epi.mode == EPI_SWIGLU;
     op.g = g;
-    op.wmap = map_of(b, g.Wt, g.N, g.K, g.K, TM);
-    op.wmap2 = op.dual ? map_of(b, g.Wt2, g.N, g.K, g.K, TM) : -1;
+    op.wmap = map_of(b, g.Wt, g.N, g.K, g.K, TM, f8);
+    op.wmap2 = op.dual ? map_of(b, g.Wt2, g.N, g.K, g.K, TM, f8) : -1;
     // activation rows: the whole workspace; rows past a step's tokens only
-    // feed accumulator columns that are never stored
-    op.xmap = g.asrc == A_DIRECT ? map_of(b, g.A, b->ws_rows, g.K, g.lda, NT) : -1;
-    if (op.wmap < 0 || (op.dual && op.wmap2 < 0) || (g.asrc == A_DIRECT && op.xmap < 0)) return false;
+    // feed accumulator columns that are never stored (E4M3 projections
+    // build their token operand)
+    const bool streamed = !f8 && g.asrc == A_DIRECT;
+    op.xmap = streamed ? map_of(b, g.A, b->ws_rows, g.K, g.lda, NT) : -1;
+    if (op.wmap < 0 || (op.dual && op.wmap2 < 0) || (streamed && op.xmap < 0)) return false;
     b->ops.push_back(op);
-    b->smem = std::max(b->smem, (size_t)tile_smem(op.dual, g.asrc != A_DIRECT, g.K));
+    b->smem = std::max(b->smem, (size_t)tile_smem(op.dual, !streamed, g.K, f8));
+    b->f8 = b->f8 || f8;
     return true;
 }
 
@@ -374,7 +407,8 @@ void program_rans(ProgramBuilder *b)
     b->ops.push_back(op);
 }
 
-bool program_upload(ProgramBuilder *b, const Op **ops, int *nops, const void **maps, int *nmaps, size_t *smem)
+bool program_upload(ProgramBuilder *b, const Op **ops, int *nops, const void **maps, int *nmaps, size_t *smem,
+                    bool *f8)
 {
     if (!b->d_ops) {
         if (cudaMalloc(&b->d_ops, b->ops.size() * sizeof(Op)) != cudaSuccess) return false;
@@ -392,24 +426,26 @@ bool program_upload(ProgramBuilder *b, const Op **ops, int *nops, const void **m
     *maps = b->d_maps;
     *nmaps = (int)b->maps.size();
     *smem = b->smem + 1024;
+    *f8 = b->f8;
     return true;
 }
 
-bool persist_prepare(size_t smem, int *grid)
+bool persist_prepare(size_t smem, bool f8, int *grid)
 {
+    auto kern = f8 ? k_persist<true> : k_persist<false>;
     int dev = 0, nsm = 0, coop = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
-    if (cudaFuncSetAttribute(k_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return false;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist, NTHREADS, smem) != cudaSuccess || per < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NTHREADS, smem) != cudaSuccess || per < 1)
         return false;
     *grid = nsm;
     return true;
 }
 
-bool persist_launch(const PersistArgs &a, int grid, size_t smem, cudaStream_t s)
+bool persist_launch(const PersistArgs &a, int grid, size_t smem, bool f8, cudaStream_t s)
 {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -421,7 +457,7 @@ bool persist_launch(const PersistArgs &a, int grid, size_t smem, cudaStream_t s)
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_persist, a) == cudaSuccess;
+    return cudaLaunchKernelEx(&cfg, f8 ? k_persist<true> : k_persist<false>, a) == cudaSuccess;
 }
 
 }  // namespace psw

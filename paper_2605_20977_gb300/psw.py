@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpsw.so")
 
 PSW_OK, PSW_ERR_INVALID, PSW_ERR_OOM, PSW_ERR_CUDA, PSW_ERR_CORRUPT, PSW_ERR_TIMEOUT, PSW_ERR_CAPACITY = range(7)
-PSW_FP32, PSW_BF16 = 0, 1
+PSW_FP32, PSW_BF16, PSW_FP8 = 0, 1, 2
 PSW_SCHED_WAVEFRONT, PSW_SCHED_RASTER = 0, 1
 STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "CORRUPT", 5: "TIMEOUT", 6: "CAPACITY"}
 
@@ -25,7 +25,7 @@ EXPORTS = ["psw_weights_count", "psw_create", "psw_destroy", "psw_last_error", "
            "psw_seq_create", "psw_seq_reset", "psw_seq_destroy", "psw_bitstream_capacity", "psw_encode_params",
            "psw_decode_frame", "psw_decode_batch", "psw_rate", "psw_quantize", "psw_scale_table", "psw_cdf_table",
            "psw_rans_encode", "psw_rans_decode", "psw_launch_count", "psw_profile_begin", "psw_profile_end",
-           "psw_rans_encode_noalloc", "psw_set_engine", "psw_last_engine"]
+           "psw_rans_encode_noalloc", "psw_set_engine", "psw_last_engine", "psw_quantize_e4m3"]
 
 ENGINE_AUTO, ENGINE_GRAPH, ENGINE_PERSISTENT = 0, 1, 2
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
             "psw_profile_begin": (I, [P]),
             "psw_profile_end": (I, [P, ct.POINTER(KernelStat), I, ct.POINTER(I)]),
             "psw_rans_encode_noalloc": (I, [P, FD, P, P, P, P, S, ct.POINTER(S), P]),
+            "psw_quantize_e4m3": (I, [S, P, P, ct.POINTER(ct.c_float)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -124,6 +125,16 @@ def frame_desc(H: int, W: int, schedule: int = PSW_SCHED_WAVEFRONT) -> FrameDesc
 
 def psw_weights_count(cfg) -> int:
     return int(load().psw_weights_count(ct.byref(model_desc(cfg))))
+
+
+def quantize_e4m3(src, dst) -> float:
+    """psw_quantize_e4m3: src float32 device tensor -> dst uint8 device
+    tensor of the same element count (E4M3 bytes); returns the scale."""
+    s = ct.c_float(0.0)
+    st = load().psw_quantize_e4m3(src.numel(), _ptr(src), _ptr(dst), ct.byref(s))
+    if st != 0:
+        raise PswError(st, (load().psw_last_error(None) or b"").decode())
+    return float(s.value)
 
 
 class Context:

@@ -219,6 +219,29 @@ def matrix_mask(c: ModelConfig) -> np.ndarray:
     return np.concatenate(out)
 
 
+def e4m3_tensor(t: Tensor) -> bool:
+    """Whether an FP8 context stores projection t as E4M3 (one power-of-two
+    scale per tensor): transformer-block projections whose input width K is
+    a multiple of 128, at most 512 for a normalised input and 1024 for the
+    compact-row inputs of Wo, Wxo and Wd.  The latent embedding and the heads
+    stay in the compute dtype."""
+    if not t.matrix or t.name in ("W_in", "W1m", "W2m", "W1s", "W2s"):
+        return False
+    K = t.shape[0]
+    return K % 128 == 0 and K <= (1024 if t.name.split(".")[-1] in ("Wo", "Wxo", "Wd") else 512)
+
+
+def e4m3_ranges(c: ModelConfig) -> list:
+    """(offset, size) in the flat weight vector of each E4M3-stored tensor."""
+    out, off = [], 0
+    for t in weight_spec(c):
+        n = int(np.prod(t.shape))
+        if e4m3_tensor(t):
+            out.append((off, n))
+        off += n
+    return out
+
+
 # --------------------------------------------------------------------------
 # Latents and hyperlatents
 # --------------------------------------------------------------------------

@@ -8,13 +8,15 @@ frames) over four latent grids: 15x26, 30x52, 68x120 and 135x240.
   round over all sequences, or one call per grid) -- on the first rounds and
   decodes the rest with the fastest.
 * serve: seeded Poisson arrivals of 1..16-frame requests through the
-  continuous-batching server (serve.Server), batched and one frame per call.
+  continuous-batching server (serve.Server), batched (in the chosen
+  precision, E4M3 block projections by default) against one frame per call
+  in BF16.
 
 Frames come from a pool of seeded synthetic sequences per grid, encoded
 once; a request or sequence decodes a pool sequence's first frames.
 
-    python -m paper_2605_20977_gb300.workloads mixed --seqs 32 --frames 4
-    python -m paper_2605_20977_gb300.workloads serve --rate 200 --window 0.1
+    python -m paper_2605_20977_gb300.workloads mixed --seqs 32 --frames 4 --precision fp8
+    python -m paper_2605_20977_gb300.workloads serve --rate 200 --window 0.1 --precision fp8
 """
 from __future__ import annotations
 
@@ -27,6 +29,7 @@ import numpy as np
 from . import build, psw, serve, synth
 
 GRIDS = [(15, 26), (30, 52), (68, 120), (135, 240)]
+PRECISIONS = {"bf16": psw.PSW_BF16, "fp8": psw.PSW_FP8}
 
 
 class Pool:
@@ -69,10 +72,10 @@ def _mixed_round(ctx, seqs, grids_of, pool_of, outs, f, grouping):
                          [pool_of[i][f][2] for i in idx], [outs[i] for i in idx])
 
 
-def run_mixed(nseq=32, nframes=4, tune_frames=1, seed=7, dev=None):
+def run_mixed(nseq=32, nframes=4, tune_frames=1, seed=7, dev=None, precision="bf16"):
     import torch
     cfg = synth.config("p1080")
-    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=PRECISIONS[precision])
     per_grid = max(1, nseq // len(GRIDS))
     pool = Pool(ctx, cfg, GRIDS, per_grid, nframes, dev)
     rng = np.random.default_rng(seed)
@@ -114,20 +117,20 @@ def run_mixed(nseq=32, nframes=4, tune_frames=1, seed=7, dev=None):
     work = sum(gflop[g] for g in grids_of) * nframes
     ctx.close()
     return {"workload": f"{len(outs)} P-frame sequences ({per_grid} at each of "
-            + ", ".join(f"{H}x{W}" for H, W in GRIDS) + f"), {nframes} frames each, BF16",
+            + ", ".join(f"{H}x{W}" for H, W in GRIDS) + f"), {nframes} frames each, {precision.upper()}",
             "plan": best, "autotune_frames_per_s": tune, "frames_per_s": len(outs) * nframes / dt,
             "tflops": work / dt / 1e3, "seconds": dt}
 
 
 def run_serve(rate=200.0, window=0.1, per_grid=2, gop=16, budget_gb=120.0, max_batch=128, seed=1005, dev=None,
-              unbatched=True):
+              unbatched=True, precision="fp8"):
+    """Batched service in `precision` against one frame per call in BF16,
+    on the same arrival trace (each arm encodes its own streams)."""
     import torch
     cfg = synth.config("p1080")
-    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
-    pool = Pool(ctx, cfg, GRIDS, per_grid, gop, dev)
     trace = serve.poisson_trace(rate, window, GRIDS, max_frames=gop, seed=seed)
 
-    def requests():
+    def requests(pool):
         reqs = []
         for rid, (t, gi, nf) in enumerate(trace):
             src = pool.items[gi][rid % per_grid]
@@ -140,19 +143,23 @@ def run_serve(rate=200.0, window=0.1, per_grid=2, gop=16, budget_gb=120.0, max_b
 
     out = {"workload": f"Poisson arrivals at {rate:g} requests/s over {window:g} s ({len(trace)} requests, "
            f"{sum(n for _, _, n in trace)} frames), 1..{gop} frames each, grids "
-           + ", ".join(f"{H}x{W}" for H, W in GRIDS) + f"; HBM budget {budget_gb:g} GB; P-frame model, BF16"}
-    for name, mb in (("batched", max_batch), ("one_frame_per_call", 1)):
+           + ", ".join(f"{H}x{W}" for H, W in GRIDS) + f"; HBM budget {budget_gb:g} GB; P-frame model"}
+    for name, mb, prec in (("batched", max_batch, precision), ("one_frame_per_call", 1, "bf16")):
         if name != "batched" and not unbatched:
             continue
-        reqs = requests()
+        ctx = psw.Context(cfg, synth.weights(cfg), precision=PRECISIONS[prec])
+        pool = Pool(ctx, cfg, GRIDS, per_grid, gop, dev)
+        reqs = requests(pool)
         torch.cuda.synchronize()
         st = serve.Server(ctx, int(budget_gb * 2 ** 30), max_batch=mb).run(reqs)
         for r in reqs:
             for f, y in enumerate(r.truth):
                 if not np.array_equal(r.outputs[f].cpu().numpy(), y):
                     raise RuntimeError("served decode differs")
+        st["precision"] = prec
         out[name] = st
-    ctx.close()
+        del pool, reqs
+        ctx.close()
     return out
 
 
@@ -164,14 +171,17 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--window", type=float, default=0.1)
     ap.add_argument("--no-unbatched", action="store_true")
+    ap.add_argument("--precision", choices=sorted(PRECISIONS), default=None,
+                    help="mixed: bf16 (default); serve: the batched arm's precision, fp8 (default)")
     args = ap.parse_args()
     import torch
     build.build()
     dev = torch.device("cuda", 0)
     if args.what == "mixed":
-        res = run_mixed(args.seqs, args.frames, dev=dev)
+        res = run_mixed(args.seqs, args.frames, dev=dev, precision=args.precision or "bf16")
     else:
-        res = run_serve(args.rate, args.window, dev=dev, unbatched=not args.no_unbatched)
+        res = run_serve(args.rate, args.window, dev=dev, unbatched=not args.no_unbatched,
+                        precision=args.precision or "fp8")
     print(json.dumps(res), flush=True)
 
 

@@ -76,7 +76,7 @@ def _check_same(alone, batched, items):
         assert np.array_equal(ma, mb) and np.array_equal(sa, sb)
 
 
-@pytest.mark.parametrize("precision", [psw.PSW_FP32, psw.PSW_BF16])
+@pytest.mark.parametrize("precision", [psw.PSW_FP32, psw.PSW_BF16, psw.PSW_FP8])
 def test_batch_equals_alone_mixed_grids_and_schedules(precision):
     base = synth.config("tiny")
     ctx = psw.Context(base, synth.weights(base), precision=precision)
@@ -91,9 +91,10 @@ def test_batch_equals_alone_mixed_grids_and_schedules(precision):
     _check_same(alone, batched, items)
 
 
-def test_batch_equals_alone_1080p_bf16():
+@pytest.mark.parametrize("precision", [psw.PSW_BF16, psw.PSW_FP8])
+def test_batch_equals_alone_1080p(precision):
     cfg = synth.config("i1080")
-    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=precision)
     plan = [(68, 120), (12, 120), (17, 30)]
     items, fds = [], []
     for k, (H, W) in enumerate(plan):
@@ -173,11 +174,12 @@ def _engine_run(ctx, cfg, items, fds, engine):
     return got, ctx.last_engine()
 
 
-def test_persistent_engine_equals_graph_engine():
+@pytest.mark.parametrize("precision", [psw.PSW_BF16, psw.PSW_FP8])
+def test_persistent_engine_equals_graph_engine(precision):
     """The persistent decoder (one cooperative launch over every step) and
     the per-phase graph decoder give bit-identical latents and parameters."""
     base = synth.config("tiny")
-    ctx = psw.Context(base, synth.weights(base), precision=psw.PSW_BF16)
+    ctx = psw.Context(base, synth.weights(base), precision=precision)
     plan = [((8, 12), 0), ((5, 7), 1), ((8, 3), 0), ((1, 1), 0), ((6, 12), 0)]
     items, fds = [], []
     for k, ((H, W), sched) in enumerate(plan):
@@ -193,9 +195,10 @@ def test_persistent_engine_equals_graph_engine():
     _check_same(g, a, items)
 
 
-def test_persistent_engine_1080p_and_temporal():
+@pytest.mark.parametrize("precision", [psw.PSW_BF16, psw.PSW_FP8])
+def test_persistent_engine_1080p_and_temporal(precision):
     cfg = synth.config("i1080")
-    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=precision)
     plan = [(68, 120), (9, 120), (17, 30)]
     items, fds = [], []
     for k, (H, W) in enumerate(plan):
@@ -208,7 +211,7 @@ def test_persistent_engine_1080p_and_temporal():
     _check_same(g, p, items)
 
     tcfg = synth.config("tiny_p")
-    tctx = psw.Context(tcfg, synth.weights(tcfg), precision=psw.PSW_BF16)
+    tctx = psw.Context(tcfg, synth.weights(tcfg), precision=precision)
     fr = synth.frames(tcfg, 3, seed=150)
     enc = _encode(tctx, tcfg, fr, 0)
     fd = psw.frame_desc(tcfg.H, tcfg.W, 0)

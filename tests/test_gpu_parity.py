@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 
 FP32_TOL = 1e-4          # max |dmu|/sigma and |d ln sigma|, FP32 compute
 BF16_TOL = 5e-2          # 99.9th percentile of the same, BF16 compute
+FP8_TOL = 1.5e-1         # 99.9th percentile of the same, E4M3 block projections
 RATE_TOL = 1e-3          # |rate(gpu params) - rate(fp64 params)| / rate(fp64)
 
 
@@ -171,7 +172,8 @@ def _check_frame(cfg, w64, fr, res, precision, sched, oracle_mu=None, oracle_sg=
         if precision == psw.PSW_FP32:
             assert dmu.max() <= FP32_TOL and dls.max() <= FP32_TOL, (dmu.max(), dls.max())
         else:
-            assert np.quantile(dmu, 0.999) <= BF16_TOL and np.quantile(dls, 0.999) <= BF16_TOL, \
+            tol = BF16_TOL if precision == psw.PSW_BF16 else FP8_TOL
+            assert np.quantile(dmu, 0.999) <= tol and np.quantile(dls, 0.999) <= tol, \
                 (np.quantile(dmu, 0.999), np.quantile(dls, 0.999))
         ra = O.rate_bits(fr.y[f], r["mu"].astype(np.float64), r["sg"].astype(np.float64))
         rb = O.rate_bits(fr.y[f], oracle_mu[f], oracle_sg[f])
@@ -302,3 +304,69 @@ def test_bf16_1080p_pframe_crop_parity():
     ctx = psw.Context(cfg, w, precision=psw.PSW_BF16)
     res = _encode_decode(ctx, crop, fr, psw.PSW_SCHED_WAVEFRONT)
     _check_frame(crop, oracle_weights(cfg, w, psw.PSW_BF16), fr, res, psw.PSW_BF16, 0)
+
+
+# ----------------------------------------------------------- FP8 (E4M3)
+
+def test_quantize_e4m3_bytes_match_library_cast():
+    """psw_quantize_e4m3: the oracle's power-of-two scale and, byte for byte,
+    torch's float8_e4m3fn cast of the scaled values."""
+    rng = np.random.default_rng(21)
+    for n, sc in ((4096, 0.05), (1001, 3.0), (3, 1e-4)):
+        x = (rng.standard_normal(n) * sc).astype(np.float32)
+        src = _t(x)
+        dst = torch.zeros(n, dtype=torch.uint8, device=dev())
+        s = psw.quantize_e4m3(src, dst)
+        _, s_o = O.e4m3_tensor(x.astype(np.float64))
+        assert s == s_o
+        ref = torch.from_numpy(x / np.float32(s)).to(torch.float8_e4m3fn).view(torch.uint8).numpy()
+        assert np.array_equal(dst.cpu().numpy(), ref)
+    z = torch.zeros(64, device=dev())
+    assert psw.quantize_e4m3(z, torch.zeros(64, dtype=torch.uint8, device=dev())) == 1.0
+    bad = torch.tensor([1.0, float("inf"), 0.0, 0.0], device=dev())
+    with pytest.raises(psw.PswError):
+        psw.quantize_e4m3(bad, torch.zeros(4, dtype=torch.uint8, device=dev()))
+
+
+@pytest.mark.parametrize("sched", [psw.PSW_SCHED_WAVEFRONT, psw.PSW_SCHED_RASTER])
+def test_tiny_fp8_parity(sched):
+    cfg = synth.config("tiny")
+    ctx, w = _ctx(cfg, psw.PSW_FP8)
+    fr = synth.frames(cfg, 1, seed=1001)
+    res = _encode_decode(ctx, cfg, fr, sched)
+    _check_frame(cfg, oracle_weights(cfg, w, psw.PSW_FP8), fr, res, psw.PSW_FP8, sched)
+
+
+def test_fp8_1080p_crop_parity():
+    cfg = synth.config("i1080")
+    w = synth.weights(cfg)
+    fr = synth.frames(cfg, 1, seed=1002)
+    crop = cfg.with_grid(CROP, cfg.W)
+    frc = synth.Frames(y=fr.y[:, :CROP].copy(), z=fr.z[:, :crop.Hh].copy(), sigma=fr.sigma[:CROP])
+    ctx = psw.Context(cfg, w, precision=psw.PSW_FP8)
+    res = _encode_decode(ctx, crop, frc, psw.PSW_SCHED_WAVEFRONT)
+    _check_frame(crop, oracle_weights(cfg, w, psw.PSW_FP8), frc, res, psw.PSW_FP8, 0)
+
+
+def test_fp8_1080p_pframe_crop_parity():
+    """P-frames at the 1080p model sizes with E4M3 block projections (the
+    Context Transformer's included), 6-row crop, four frames."""
+    cfg = synth.config("p1080")
+    w = synth.weights(cfg)
+    crop = cfg.with_grid(6, cfg.W)
+    fr = synth.frames(crop, 4, seed=1003)
+    ctx = psw.Context(cfg, w, precision=psw.PSW_FP8)
+    res = _encode_decode(ctx, crop, fr, psw.PSW_SCHED_WAVEFRONT)
+    _check_frame(crop, oracle_weights(cfg, w, psw.PSW_FP8), fr, res, psw.PSW_FP8, 0)
+
+
+def test_fp8_without_eligible_projections_equals_bf16():
+    """A model whose projection widths the E4M3 tile does not take (d = 64)
+    keeps every projection in BF16: the FP8 context decodes bit for bit as
+    the BF16 one."""
+    cfg = synth.ModelConfig(H=6, W=9, C=64, Hh=3, Wh=5, Ch=32, r=2, d=64, nh=2, F=synth.ffn_width(64), L=1, k=5)
+    w = synth.weights(cfg)
+    fr = synth.frames(cfg, 1, seed=5)
+    r8 = _encode_decode(psw.Context(cfg, w, precision=psw.PSW_FP8), cfg, fr, 0)[0]
+    r16 = _encode_decode(psw.Context(cfg, w, precision=psw.PSW_BF16), cfg, fr, 0)[0]
+    assert r8["bs"] == r16["bs"] and np.array_equal(r8["mu"], r16["mu"]) and np.array_equal(r8["sg"], r16["sg"])

@@ -47,10 +47,12 @@ def _make_requests(ctx, base, grids, plan):
     return reqs
 
 
-@pytest.mark.parametrize("engine", [psw.ENGINE_PERSISTENT, psw.ENGINE_GRAPH])
-def test_serving_mix_equals_alone(engine):
+@pytest.mark.parametrize("engine,precision", [(psw.ENGINE_PERSISTENT, psw.PSW_BF16),
+                                              (psw.ENGINE_GRAPH, psw.PSW_BF16),
+                                              (psw.ENGINE_PERSISTENT, psw.PSW_FP8)])
+def test_serving_mix_equals_alone(engine, precision):
     base = synth.config("tiny_p")
-    ctx = psw.Context(base, synth.weights(base), precision=psw.PSW_BF16)
+    ctx = psw.Context(base, synth.weights(base), precision=precision)
     grids = [(8, 12), (5, 7), (6, 10)]
     plan = [(0.0, 0, 3), (0.0, 1, 1), (0.0, 2, 4), (0.0, 0, 2), (0.001, 1, 3), (0.002, 2, 1),
             (0.003, 0, 4), (0.004, 1, 2), (0.02, 2, 3), (0.03, 0, 1)]

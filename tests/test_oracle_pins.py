@@ -4,8 +4,8 @@ Closed forms (RMSNorm, SiLU, SwiGLU, attention special cases, Gaussian
 likelihood), the paper's Fig. 2 grids transcribed by hand, window-mask
 cardinalities, schedule step counts, a dense-mask NumPy formulation of the
 model on tiny frames, schedule equivalence, brute-force causality, CDF table
-invariants, rANS round trips and size bounds, and the data generator's
-statistics.  CPU only.
+invariants, rANS round trips and size bounds, E4M3 rounding (hand values of
+the format, a library cast), and the data generator's statistics.  CPU only.
 """
 import math
 import os
@@ -252,6 +252,49 @@ def test_rate_bits_sum():
     mu = np.array([0.0, 0.3, -1.0]); sg = np.array([1.0, 2.0, 0.5])
     want = -sum(math.log2(O.likelihood(a, b, s)) for a, b, s in zip(y, mu, sg))
     assert O.rate_bits(y, mu, sg) == pytest.approx(want, rel=1e-15)
+
+
+# ----------------------------------------------------------- E4M3
+
+def test_e4m3_hand_values():
+    """Values fixed by the format (3 mantissa bits, bias 7, largest finite
+    448, smallest subnormal 2^-9) and its ties-to-even rounding."""
+    cases = {1.0: 1.0, 1.0625: 1.0, 1.1875: 1.25, 1.124: 1.125, -3.3: -3.25, 448.0: 448.0, 460.0: 448.0,
+             1000.0: 448.0, 240.0: 240.0, 248.0: 256.0, 2.0 ** -6: 2.0 ** -6, 2.0 ** -9: 2.0 ** -9,
+             2.0 ** -10: 0.0, 3 * 2.0 ** -10: 2.0 ** -8, 0.7 * 2.0 ** -9: 2.0 ** -9, 5 * 2.0 ** -10: 2.0 ** -8,
+             0.0: 0.0, 17.0: 16.0, 19.0: 20.0}
+    for x, want in cases.items():
+        assert O.e4m3(x) == want, (x, O.e4m3(x), want)
+
+
+def test_e4m3_matches_library_cast():
+    """Nearest-even E4M3 of float32 values across the whole finite range,
+    subnormals and exact ties included, against torch's float8_e4m3fn cast."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    mags = np.exp2(rng.uniform(-12, np.log2(440.0), 20000))
+    x = (mags * rng.choice([-1.0, 1.0], mags.size)).astype(np.float32)
+    grid = torch.arange(256, dtype=torch.uint8).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    grid = np.unique(grid[np.isfinite(grid) & (np.abs(grid) <= 256)])
+    ties = ((grid[1:] + grid[:-1]) / 2).astype(np.float32)             # midpoints, exact in float32
+    x = np.concatenate([x, ties, grid.astype(np.float32)])
+    ref = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    got = np.array([O.e4m3(float(v)) for v in x])
+    assert np.array_equal(got, ref)
+
+
+def test_e4m3_tensor_scale_rule():
+    rng = np.random.default_rng(12)
+    for scale in (1e-3, 0.05, 1.0, 37.0):
+        x = rng.standard_normal(4096) * scale
+        q, s = O.e4m3_tensor(x)
+        assert s == 2.0 ** round(math.log2(s))                        # a power of two
+        assert 128.0 <= np.abs(x).max() / s < 256.0
+        assert np.array_equal(q / s, [O.e4m3(v) for v in x / s])
+        rel = np.abs(q - x)[np.abs(x) > 2 ** -6 * s] / np.abs(x)[np.abs(x) > 2 ** -6 * s]
+        assert rel.max() <= 2.0 ** -4                                 # half a unit of 3 mantissa bits
+    q, s = O.e4m3_tensor(np.zeros(8))
+    assert s == 1.0 and not q.any()
 
 
 def test_scale_table():

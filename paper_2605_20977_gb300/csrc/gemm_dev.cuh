@@ -385,6 +385,25 @@ __device__ __forceinline__ void gemm_shared_init(GemmShared &S)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// The gains of lane l's elements 4l + 128c .. +3 (c < CH), loaded once per
+// build (they sit at any float offset), and the reciprocal 1/K the mean of
+// squares uses.
+template <int CH>
+__device__ __forceinline__ void load_gain(const float *__restrict__ gain, int K, float4 *gh)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        int e = lane * 4 + c * 128;
+        gh[c] = e < K ? make_float4(gain[e], gain[e + 1], gain[e + 2], gain[e + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// 1 / RMS of a row from its sum of squares (approximate reciprocal square
+// root; the same instruction sequence for every token, so encoder and decoder
+// agree bit for bit).
+__device__ __forceinline__ float inv_rms(float ss, float invK) { return rsqrtf(fmaf(ss, invK, 1e-6f)); }
+
 // RMSNorm of RB rows r0 .. r0+RB-1 of the tile by one warp, every load of
 // the rows issued before the first reduction; lane l holds elements
 // 4l + 128c .. +3 of a row (c < CH).
@@ -393,8 +412,10 @@ __device__ __forceinline__ void norm_rows(const float *__restrict__ xrows, const
                                           int M, int m0, int r0, uint8_t *res)
 {
     const int lane = threadIdx.x & 31;
-    float4 v[RB][CH];
+    float4 v[RB][CH], gh[CH];
     float ss[RB];
+    load_gain<CH>(gain, K, gh);
+    const float invK = 1.0f / (float)K;
 #pragma unroll
     for (int b = 0; b < RB; b++) {
         int m = m0 + r0 + b;
@@ -418,14 +439,13 @@ __device__ __forceinline__ void norm_rows(const float *__restrict__ xrows, const
 #pragma unroll
     for (int b = 0; b < RB; b++) {
         int r = r0 + b;
-        float inv = m0 + r < M ? 1.0f / sqrtf(ss[b] / (float)K + 1e-6f) : 0.0f;
+        float inv = m0 + r < M ? inv_rms(ss[b], invK) : 0.0f;
 #pragma unroll
         for (int c = 0; c < CH; c++) {
             int e = lane * 4 + c * 128;
             if (e >= K) continue;
-            const float *gn = gain + e;                        // gains sit at any float offset
-            *(uint2 *)(res + swz(r, e)) = pack4(v[b][c].x * inv * gn[0], v[b][c].y * inv * gn[1],
-                                                v[b][c].z * inv * gn[2], v[b][c].w * inv * gn[3]);
+            *(uint2 *)(res + swz(r, e)) = pack4(v[b][c].x * inv * gh[c].x, v[b][c].y * inv * gh[c].y,
+                                                v[b][c].z * inv * gh[c].z, v[b][c].w * inv * gh[c].w);
         }
     }
 }
@@ -482,8 +502,10 @@ __device__ __forceinline__ void norm_rows8(const float *__restrict__ xrows, cons
                                            int M, int m0, int r0, uint8_t *res, float *xs)
 {
     const int lane = threadIdx.x & 31;
-    float4 v[RB][CH];
+    float4 v[RB][CH], gh[CH];
     float ss[RB];
+    load_gain<CH>(gain, K, gh);
+    const float invK = 1.0f / (float)K;
 #pragma unroll
     for (int b = 0; b < RB; b++) {
         int m = m0 + r0 + b;
@@ -507,15 +529,14 @@ __device__ __forceinline__ void norm_rows8(const float *__restrict__ xrows, cons
 #pragma unroll
     for (int b = 0; b < RB; b++) {
         int r = r0 + b;
-        float inv = m0 + r < M ? 1.0f / sqrtf(ss[b] / (float)K + 1e-6f) : 0.0f;
+        float inv = m0 + r < M ? inv_rms(ss[b], invK) : 0.0f;
         float amax = 0.0f;
 #pragma unroll
         for (int c = 0; c < CH; c++) {
             int e = lane * 4 + c * 128;
             if (e >= K) continue;
-            const float *gn = gain + e;
-            v[b][c] = make_float4(v[b][c].x * inv * gn[0], v[b][c].y * inv * gn[1], v[b][c].z * inv * gn[2],
-                                  v[b][c].w * inv * gn[3]);
+            v[b][c] = make_float4(v[b][c].x * inv * gh[c].x, v[b][c].y * inv * gh[c].y, v[b][c].z * inv * gh[c].z,
+                                  v[b][c].w * inv * gh[c].w);
             amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[b][c].x), fabsf(v[b][c].y)), fmaxf(fabsf(v[b][c].z), fabsf(v[b][c].w))));
         }
         float qm, sc = row_scale_e4m3(warp_max(amax), &qm);
@@ -529,13 +550,12 @@ __device__ __forceinline__ void norm_rows8(const float *__restrict__ xrows, cons
     }
 }
 
-// E4M3 token operand from compact bf16 rows A[m][lda] (K <= 1024): lane l
+// E4M3 token operand from compact bf16 rows A[m][lda] (K <= 256 CH): lane l
 // holds elements 8l + 256c of RB rows.
-template <int RB>
+template <int RB, int CH>
 __device__ __forceinline__ void quant_rows8(const __nv_bfloat16 *__restrict__ A, int lda, int K, int M, int m0,
                                             int r0, uint8_t *res, float *xs)
 {
-    constexpr int CH = 4;
     const int lane = threadIdx.x & 31;
     uint4 q[RB][CH];
 #pragma unroll
@@ -591,8 +611,12 @@ static __device__ __noinline__ void build_tokens8(const GemmArgs &g, int m0, uin
         return;
     }
     const __nv_bfloat16 *A = (const __nv_bfloat16 *)g.A;
-    quant_rows8<4>(A, g.lda, g.K, g.M, m0, r0, res, xs);
-    quant_rows8<4>(A, g.lda, g.K, g.M, m0, r0 + 4, res, xs);
+    if (g.K <= 512) {
+        quant_rows8<8, 2>(A, g.lda, g.K, g.M, m0, r0, res, xs);                 // every load in flight at once
+    } else {
+        quant_rows8<4, 4>(A, g.lda, g.K, g.M, m0, r0, res, xs);
+        quant_rows8<4, 4>(A, g.lda, g.K, g.M, m0, r0 + 4, res, xs);
+    }
 }
 
 // Per-token addresses a mode needs, resolved once per tile by threads 0..63:

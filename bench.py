@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--pframe-seqs", type=int, default=16,
                     help="P-frame GOP measurement: sequences decoded together (0: skip)")
     ap.add_argument("--pframe-gop", type=int, default=16, help="frames per P-frame sequence")
+    ap.add_argument("--precision", choices=["bf16", "fp8"], default="bf16",
+                    help="projections of the main leg: bf16, or fp8 (E4M3 block projections; the fp8 leg is then skipped)")
     ap.add_argument("--fp8-steps", type=int, default=2,
                     help="timed steps of the same I-frame workload with E4M3 block projections (0: skip)")
     ap.add_argument("--engine", choices=["auto", "graph", "persistent"], default="auto",
@@ -213,7 +215,7 @@ def run_reference(args, rank: int):
 def traffic_for(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if
     the kernel source is unchanged since it was taken."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    p = os.path.join(ROOT, "profiles", "traffic.txt")     # JSON: per-kernel DRAM bytes from the ncu summaries
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
@@ -338,7 +340,7 @@ def run_ours(args, rank: int, world: int, local: int):
     stream = torch.cuda.current_stream()
     cfg = synth.config("i1080")
     w = synth.weights(cfg)
-    ctx = psw.Context(cfg, w, precision=psw.PSW_BF16)
+    ctx = psw.Context(cfg, w, precision=psw.PSW_FP8 if args.precision == "fp8" else psw.PSW_BF16)
     ctx.set_engine({"auto": psw.ENGINE_AUTO, "graph": psw.ENGINE_GRAPH,
                     "persistent": psw.ENGINE_PERSISTENT}[args.engine])
     B = args.batch
@@ -523,7 +525,7 @@ def run_ours(args, rank: int, world: int, local: int):
         pframe = pframe_run(args, dev, stream, flush, timed)
 
     fp8 = mu8 = sg8 = None
-    if rank == 0 and args.fp8_steps > 0:
+    if rank == 0 and args.fp8_steps > 0 and args.precision == "bf16":
         fp8, mu8, sg8 = fp8_run(args, dev, timed, cfg, w, ys, zs, B)
 
     # rate: GPU parameters vs the FP64 oracle on the sample rows
@@ -552,8 +554,10 @@ def run_ours(args, rank: int, world: int, local: int):
         return 0
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "frames_per_step": B,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "e4m3+bf16",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.precision == "bf16" else WORKLOAD.replace(
+                           "BF16 projections", "E4M3 block projections (BF16 embedding and heads)"), "frames_per_step": B,
                        "l2": "flushed between steps (256 MiB write)",
                        "launch": ("persistent: per-frame prologue in a CUDA graph, then one cooperative kernel "
                                   "(one CTA per SM, grid barrier between phases) over all wavefront steps"

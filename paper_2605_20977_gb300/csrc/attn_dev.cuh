@@ -75,6 +75,7 @@ struct __align__(16) AttnWarp {
     static constexpr int MAXC = 256;
     unsigned char kbuf[32 * KS];
     unsigned char vbuf[32 * RB];
+    unsigned char qraw[RB];                                    // the query as stored, copied with the first keys
     float qs[DH];
     int rows[MAXC];
     unsigned short bix[MAXC];
@@ -129,8 +130,10 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
     }
     const T *q = a.q_sel == CS_NONE ? (const T *)a.Q + (long)tokn * a.d + h * DH
                                     : cache_row<const T>(s, a.q_sel, 0, p, a.d) + h * DH;
-    for (int e = lane; e < DH; e += 32) sm.qs[e] = to_f<T>(q[e]);
-    __syncwarp();
+    // the query travels with the first chunk's keys and values: one memory
+    // round trip for all three
+    if (lane < PR) cp_async16(sm.qraw + lane * 16, (const char *)q + lane * 16);
+    bool qready = false;
     const char *Kb = (const char *)(cache_row<const T>(s, a.k_sel, 0, 0, a.d) + h * DH);
     const char *Vb = (const char *)(cache_row<const T>(s, a.v_sel, 0, 0, a.d) + h * DH);
     const long rsb = (long)a.d * (long)sizeof(T);              // bytes between cache rows
@@ -150,6 +153,11 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
         }
         cp_async_wait_all();
         __syncwarp();
+        if (!qready) {
+            for (int e = lane; e < DH; e += 32) sm.qs[e] = to_f<T>(reinterpret_cast<const T *>(sm.qraw)[e]);
+            __syncwarp();
+            qready = true;
+        }
         float sc = -INFINITY;
         if (lane < nc) {
             const uint4 *kr = reinterpret_cast<const uint4 *>(kb + lane * KS);
@@ -180,6 +188,7 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
         mx = mnew;
         __syncwarp();                                  // the next chunk reuses the buffers
     }
+    if (!qready) cp_async_wait_all();                  // no keys: the query copy lands before the buffers are reused
     const float inv = z > 0.0f ? 1.0f / z : 0.0f;
     T *out = (T *)a.O + (long)tokn * a.d + h * DH + lane * PER;
 #pragma unroll

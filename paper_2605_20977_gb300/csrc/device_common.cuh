@@ -29,6 +29,11 @@ __device__ __forceinline__ float warp_max(float v)
 }
 
 __device__ __forceinline__ float silu_f(float x) { return x / (1.0f + expf(-x)); }
+// SiLU with the fast exponential and division intrinsics (a few ulp; the
+// tensor-core epilogues, where the accurate forms dominated the epilogue's
+// instruction count).  For x far below zero the denominator overflows to
+// infinity and the quotient is 0, as SiLU's limit.
+__device__ __forceinline__ float silu_fast(float x) { return __fdividef(x, 1.0f + __expf(-x)); }
 
 // Programmatic dependent launch: let the next kernel in the stream start its
 // prologue now; wait until the previous kernel's results are visible.

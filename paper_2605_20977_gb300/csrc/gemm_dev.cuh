@@ -255,6 +255,26 @@ __device__ __forceinline__ void tmem_sum16(uint32_t addr, uint32_t step, float *
     tmem_sum8(addr + 8, step, v + 8);
 }
 
+// Two 8-column sums (at addr and addr2) under one wait for the loads.
+__device__ __forceinline__ void tmem_sum8x2(uint32_t addr, uint32_t addr2, uint32_t step, float *v, float *v2)
+{
+    uint32_t r[NISS][8], r2[NISS][8];
+#pragma unroll
+    for (int q = 0; q < NISS; q++) {
+        tmem_ld8_async(addr + q * step, r[q]);
+        tmem_ld8_async(addr2 + q * step, r2[q]);
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        float a = __uint_as_float(r[0][i]), b = __uint_as_float(r2[0][i]);
+#pragma unroll
+        for (int q = 1; q < NISS; q++) { a += __uint_as_float(r[q][i]); b += __uint_as_float(r2[q][i]); }
+        v[i] = a;
+        v2[i] = b;
+    }
+}
+
 // Byte offset of element (row r, column k) of a K-major bf16 operand laid
 // out in 128-byte-swizzled atoms of 64 columns x NT rows.
 __device__ __forceinline__ uint32_t swz(int r, int k)
@@ -723,8 +743,8 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
         for (int c0 = cb; c0 < cb + NT / 2; c0 += 8) {
             float v[8], v2[8], o[8];
             int oi[8];
-            tmem_sum8(trow + c0, ASTEP, v);
-            if (DUAL) tmem_sum8(trow + NT + c0, ASTEP, v2);
+            if (DUAL) tmem_sum8x2(trow + c0, trow + NT + c0, ASTEP, v, v2);
+            else tmem_sum8(trow + c0, ASTEP, v);
             if constexpr (F8) {
 #pragma unroll
                 for (int j = 0; j < 8; j++) {
@@ -750,9 +770,9 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
                 } else if (MODE == EPI_SET_BIAS) {
                     o[j] = y + bf;
                 } else if (MODE == EPI_BIAS_SILU) {
-                    o[j] = silu_f(y + bf);
+                    o[j] = silu_fast(y + bf);
                 } else if (MODE == EPI_SWIGLU) {
-                    o[j] = DUAL ? silu_f(y) * v2[j] : y;
+                    o[j] = DUAL ? silu_fast(y) * v2[j] : y;
                 } else {
                     o[j] = y;
                 }

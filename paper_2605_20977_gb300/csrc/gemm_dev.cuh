@@ -57,6 +57,7 @@ constexpr int KC = 64;         // K elements per stage (128 bytes of bf16)
 constexpr int KC8 = 128;       // K elements per stage of an E4M3 projection (128 bytes)
 constexpr int MAXS = 8;        // ring stages at most (barrier pairs)
 constexpr int RING_BUDGET = 216 * 1024;   // dynamic shared memory of the ring and the resident operand
+constexpr int RING_BUDGET_LEAN = 96 * 1024;   // the same for two CTAs per SM (lean tiles)
 constexpr int A_BYTES = TM * KC * 2;
 constexpr int B_BYTES = NT * KC * 2;
 constexpr int KRES_MAX = 512;  // largest K of a token operand built in shared memory
@@ -379,10 +380,11 @@ __host__ __device__ constexpr int kchunks(int K, bool f8) { return (K + kchunk(f
 
 // Ring depth of a projection: as many stages as its K chunks, the barrier
 // pairs and the shared-memory budget (after the resident operand) allow.
-__host__ __device__ constexpr int ring_stages(bool dual, bool resident, int K, bool f8 = false)
+// Lean tiles (single accumulator, two CTAs per SM) have the smaller budget.
+__host__ __device__ constexpr int ring_stages(bool dual, bool resident, int K, bool f8 = false, bool lean = false)
 {
     int nk = kchunks(K, f8), res = resident ? nk * B_BYTES : 0;
-    int st = (RING_BUDGET - res) / stage_bytes(dual, resident);
+    int st = ((lean ? RING_BUDGET_LEAN : RING_BUDGET) - res) / stage_bytes(dual, resident);
     st = st < MAXS ? st : MAXS;
     st = st < nk ? st : nk;
     return st < 1 ? 1 : st;
@@ -390,9 +392,9 @@ __host__ __device__ constexpr int ring_stages(bool dual, bool resident, int K, b
 
 // Dynamic shared memory of a tile (ring, then the resident token operand),
 // without the 1024-byte alignment slack.
-__host__ __device__ constexpr int tile_smem(bool dual, bool resident, int K, bool f8 = false)
+__host__ __device__ constexpr int tile_smem(bool dual, bool resident, int K, bool f8 = false, bool lean = false)
 {
-    return ring_stages(dual, resident, K, f8) * stage_bytes(dual, resident) +
+    return ring_stages(dual, resident, K, f8, lean) * stage_bytes(dual, resident) +
            (resident ? kchunks(K, f8) * B_BYTES : 0);
 }
 
@@ -474,27 +476,18 @@ __device__ __forceinline__ void norm_rows(const float *__restrict__ xrows, const
 // are zero.  Warp w builds rows 8w .. 8w+7.  A_NORM: RMSNorm of the FP32 rows
 // xrows[m] times the gain; A_EMBED: the channel-scaled latents of the token
 // (row pointers resolved beforehand into yrow).  All of a warp's loads are in
-// flight together (K <= 384: the eight rows at once).  One out-of-line copy
-// serves every projection mode (keeps the instruction footprint small).
-static __device__ __noinline__ void build_tokens(const GemmArgs &g, int m0, uint8_t *res, const int16_t *const *yrow)
+// flight together (K <= 384: the eight rows at once; lean tiles, with half
+// the registers, four at a time).  One out-of-line copy serves every
+// projection mode (keeps the instruction footprint small).
+template <int RB>
+__device__ __forceinline__ void embed_rows(const float *__restrict__ gain, int K, int r0, uint8_t *res,
+                                           const int16_t *const *yrow)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int K = g.K, M = g.M, r0 = warp * (NT / 8);
-    const float *gain = g.a_gain;
-    if (g.asrc == A_NORM) {
-        const float *xrows = g.xrows;
-        if (K <= 384) {
-            norm_rows<8, 3>(xrows, gain, K, M, m0, r0, res);
-        } else {
-            norm_rows<4, 4>(xrows, gain, K, M, m0, r0, res);
-            norm_rows<4, 4>(xrows, gain, K, M, m0, r0 + 4, res);
-        }
-        return;
-    }
     constexpr int CH = KRES_MAX / 128;
-    short4 q[8][CH];
+    const int lane = threadIdx.x & 31;
+    short4 q[RB][CH];
 #pragma unroll
-    for (int b = 0; b < 8; b++) {
+    for (int b = 0; b < RB; b++) {
         const int16_t *y = yrow[r0 + b];
 #pragma unroll
         for (int c = 0; c < CH; c++) {
@@ -503,7 +496,7 @@ static __device__ __noinline__ void build_tokens(const GemmArgs &g, int m0, uint
         }
     }
 #pragma unroll
-    for (int b = 0; b < 8; b++) {
+    for (int b = 0; b < RB; b++) {
 #pragma unroll
         for (int c = 0; c < CH; c++) {
             int e = lane * 4 + c * 128;
@@ -512,6 +505,33 @@ static __device__ __noinline__ void build_tokens(const GemmArgs &g, int m0, uint
             *(uint2 *)(res + swz(r0 + b, e)) = pack4(gm[0] * (float)q[b][c].x, gm[1] * (float)q[b][c].y,
                                                      gm[2] * (float)q[b][c].z, gm[3] * (float)q[b][c].w);
         }
+    }
+}
+
+template <bool LEAN>
+static __device__ __noinline__ void build_tokens(const GemmArgs &g, int m0, uint8_t *res, const int16_t *const *yrow)
+{
+    const int warp = threadIdx.x >> 5;
+    const int K = g.K, M = g.M, r0 = warp * (NT / 8);
+    const float *gain = g.a_gain;
+    if (g.asrc == A_NORM) {
+        const float *xrows = g.xrows;
+        if (K <= 384 && !LEAN) {
+            norm_rows<8, 3>(xrows, gain, K, M, m0, r0, res);
+        } else if (K <= 384) {
+            norm_rows<4, 3>(xrows, gain, K, M, m0, r0, res);
+            norm_rows<4, 3>(xrows, gain, K, M, m0, r0 + 4, res);
+        } else {
+            norm_rows<4, 4>(xrows, gain, K, M, m0, r0, res);
+            norm_rows<4, 4>(xrows, gain, K, M, m0, r0 + 4, res);
+        }
+        return;
+    }
+    if (!LEAN) {
+        embed_rows<8>(gain, K, r0, res, yrow);
+    } else {
+        embed_rows<4>(gain, K, r0, res, yrow);
+        embed_rows<4>(gain, K, r0 + 4, res, yrow);
     }
 }
 
@@ -618,12 +638,17 @@ __device__ __forceinline__ void quant_rows8(const __nv_bfloat16 *__restrict__ A,
 
 // Build the E4M3 token operand of rows m0 .. m0+63 (warp w: rows 8w ..
 // 8w+7): A_NORM (K <= 512) or compact bf16 rows (A_DIRECT, K <= 1024).
+// Lean tiles take four rows at a time.
+template <bool LEAN>
 static __device__ __noinline__ void build_tokens8(const GemmArgs &g, int m0, uint8_t *res, float *xs)
 {
     const int r0 = (threadIdx.x >> 5) * (NT / 8);
     if (g.asrc == A_NORM) {
-        if (g.K <= 384) {
+        if (g.K <= 384 && !LEAN) {
             norm_rows8<8, 3>(g.xrows, g.a_gain, g.K, g.M, m0, r0, res, xs);
+        } else if (g.K <= 384) {
+            norm_rows8<4, 3>(g.xrows, g.a_gain, g.K, g.M, m0, r0, res, xs);
+            norm_rows8<4, 3>(g.xrows, g.a_gain, g.K, g.M, m0, r0 + 4, res, xs);
         } else {
             norm_rows8<4, 4>(g.xrows, g.a_gain, g.K, g.M, m0, r0, res, xs);
             norm_rows8<4, 4>(g.xrows, g.a_gain, g.K, g.M, m0, r0 + 4, res, xs);
@@ -631,11 +656,17 @@ static __device__ __noinline__ void build_tokens8(const GemmArgs &g, int m0, uin
         return;
     }
     const __nv_bfloat16 *A = (const __nv_bfloat16 *)g.A;
-    if (g.K <= 512) {
+    if (LEAN) {
+        if (g.K <= 512) {
+            quant_rows8<4, 2>(A, g.lda, g.K, g.M, m0, r0, res, xs);
+            quant_rows8<4, 2>(A, g.lda, g.K, g.M, m0, r0 + 4, res, xs);
+        } else {
+            for (int b = 0; b < 8; b += 2) quant_rows8<2, 4>(A, g.lda, g.K, g.M, m0, r0 + b, res, xs);
+        }
+    } else if (g.K <= 512) {
         quant_rows8<8, 2>(A, g.lda, g.K, g.M, m0, r0, res, xs);                 // every load in flight at once
     } else {
-        quant_rows8<4, 4>(A, g.lda, g.K, g.M, m0, r0, res, xs);
-        quant_rows8<4, 4>(A, g.lda, g.K, g.M, m0, r0 + 4, res, xs);
+        quant_rows8<8, 4>(A, g.lda, g.K, g.M, m0, r0, res, xs);
     }
 }
 
@@ -680,11 +711,12 @@ __device__ __forceinline__ void build_table(const GemmArgs &g, int m0, GemmShare
 // every value before storing any (the output pointers are generic, so each
 // store could alias later loads).  Out of line: one copy per mode, small
 // enough to stay in the instruction cache.
-template <bool DUAL, int MODE, bool F8>
+template <bool DUAL, int MODE, bool F8, bool LEAN>
 static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, uint32_t tmem, const GemmArgs &g,
                                                   int f0, int m0, GemmPipe &pp)
 {
     constexpr bool RESID = MODE == EPI_RESID || MODE == EPI_RESID_BASE;
+    constexpr int PRE = LEAN ? NT / 4 : NT / 2;                    // residual values read before the MMAs end
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int M = g.M, N = g.N;
     const Epi e = g.epi;
@@ -694,7 +726,7 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
     float old[RESID ? NT / 2 : 1];
     if constexpr (RESID) {
 #pragma unroll
-        for (int j = 0; j < NT / 2; j++) {
+        for (int j = 0; j < PRE; j++) {
             const int r = cb + j, m = m0 + r;
             const float *src = MODE == EPI_RESID ? e.rows + (long)m * N : (const float *)S.tab[1][r];
             old[j] = (fok && m < M) ? src[f] : 0.0f;
@@ -721,6 +753,14 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
     if constexpr (RESID) {
 #pragma unroll
         for (int h = 0; h < 2; h++) {
+            if (h * 16 >= PRE) {
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int r = cb + 16 * h + j, m = m0 + r;
+                    const float *src = MODE == EPI_RESID ? e.rows + (long)m * N : (const float *)S.tab[1][r];
+                    old[16 * h + j] = (fok && m < M) ? src[f] : 0.0f;
+                }
+            }
             float v[16];
             tmem_sum16(trow + cb + 16 * h, ASTEP, v);
 #pragma unroll
@@ -843,7 +883,7 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
 // the ring's stages (stage s issued by lane 0 of warp s: one thread issues a
 // tensor copy only every ~150 ns).  Returns the number of stages filled.  The
 // caller synchronises the CTA before gemm_tile_main.
-template <bool DUAL, int MODE, bool F8 = false>
+template <bool DUAL, int MODE, bool F8 = false, bool LEAN = false>
 __device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const CUtensorMap *tmW,
                                              const CUtensorMap *tmW2, const GemmArgs &g, int f0, int m0,
                                              GemmPipe &pp)
@@ -853,7 +893,7 @@ __device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const
     build_table<MODE>(g, m0, S);
     const bool resident = F8 || g.asrc != A_DIRECT;
     const int stage = stage_bytes(DUAL, resident);
-    const int nst = ring_stages(DUAL, resident, g.K, F8);
+    const int nst = ring_stages(DUAL, resident, g.K, F8, LEAN);
     const int s = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0 && s < nst) {
         // the ring is idle between tiles (the previous tile's MMAs are done)
@@ -868,8 +908,9 @@ __device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const
 // The rest of a tile, after the caller's wait for its inputs and a CTA
 // barrier: token operand, MMAs, epilogue.  `first` is gemm_tile_pre's
 // result.  Roles: lane 0 of warps 1..4 issue the MMAs; lane 0 of warps 0, 5,
-// 6 and 7 issue the copies of the chunks past the first ring fill, in turn.
-template <bool DUAL, int MODE, bool F8 = false>
+// 6 and 7 issue the copies of the chunks past the first ring fill, each the
+// refills of its own stages.
+template <bool DUAL, int MODE, bool F8 = false, bool LEAN = false>
 __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *tmW,
                                                const CUtensorMap *tmW2, const CUtensorMap *tmX, const GemmArgs &g,
                                                int f0, int m0, int first, GemmPipe &pp)
@@ -879,7 +920,7 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
     constexpr int KCH = kchunk(F8);
     const bool resident = F8 || g.asrc != A_DIRECT;
     const int stage = stage_bytes(DUAL, resident);
-    const int nk = kchunks(g.K, F8), nst = ring_stages(DUAL, resident, g.K, F8);
+    const int nk = kchunks(g.K, F8), nst = ring_stages(DUAL, resident, g.K, F8, LEAN);
     uint8_t *res = ring + nst * stage;                             // resident token operand
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -893,17 +934,21 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
             tma_load(ring + s * stage + NACC * A_BYTES, tmX, &S.full[s], s * KC, m0);
     }
     if (resident) {
-        if (F8) build_tokens8(g, m0, res, S.xs);
-        else build_tokens(g, m0, res, S.yrow);
+        if (F8) build_tokens8<LEAN>(g, m0, res, S.xs);
+        else build_tokens<LEAN>(g, m0, res, S.yrow);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
     }
 
     if (producer) {
-        // producers: chunk j >= first goes to producer (j - first) % NPROD
-        int jend = first + p;
-        for (int j = first + p; j < nk; j += NPROD) {
+        // producers: every refill of stage s comes from producer s % NPROD,
+        // in chunk order, so a producer waits for a stage's release only
+        // after issuing (or seeing issued) the fill before it: the release it
+        // waits for is never more than one phase ahead of the barrier
+        int jend = first;
+        for (int j = first; j < nk; j++) {
             int s = j % nst, u = j / nst;
+            if (s % NPROD != p) continue;
             if (S.abort) break;
             if (!mbar_wait(&S.empty[s], release_parity(pp, s, u))) { S.abort = 1; break; }
             uint8_t *st = ring + s * stage;
@@ -911,11 +956,12 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
             tma_load(st, tmW, &S.full[s], j * KCH, f0);
             if (DUAL) tma_load(st + A_BYTES, tmW2, &S.full[s], j * KCH, f0);
             if (!resident) tma_load(st + NACC * A_BYTES, tmX, &S.full[s], j * KC, m0);
-            jend = j + NPROD;
+            jend = j + 1;
         }
         if (S.abort) {
             // let this producer's copies land before the CTA can go on or exit
-            for (int j = first + p; j < jend && j < nk; j += NPROD) mbar_wait(&S.full[j % nst], fill_parity(pp, j % nst, j / nst));
+            for (int j = first; j < jend; j++)
+                if ((j % nst) % NPROD == p) mbar_wait(&S.full[j % nst], fill_parity(pp, j % nst, j / nst));
         }
     } else if (warp >= 1 && warp <= NISS && lane == 0) {
         // MMA issuers: issuer q takes K step q of every chunk into its own
@@ -945,7 +991,7 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
         mma_commit(&S.done);
     }
     __syncwarp();
-    gemm_epilogue<DUAL, MODE, F8>(S, ring, tmem, g, f0, m0, pp);
+    gemm_epilogue<DUAL, MODE, F8, LEAN>(S, ring, tmem, g, f0, m0, pp);
     pipe_advance(pp, nk, nst);
 }
 

@@ -18,8 +18,12 @@ using namespace tc;
 
 namespace {
 
-template <bool DUAL, int MODE, bool F8>
-__global__ void __launch_bounds__(NTHREADS, 1)
+// LEAN: the single-accumulator tile with the smaller ring, two CTAs per SM
+// (one's token build and epilogue overlap the other's copies and MMAs);
+// chosen for launches with more tiles than SMs.  Same arithmetic as the
+// one-CTA form.
+template <bool DUAL, int MODE, bool F8, bool LEAN = false>
+__global__ void __launch_bounds__(NTHREADS, LEAN ? 2 : 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmW2,
           const __grid_constant__ CUtensorMap tmX, GemmArgs g, int *status)
 {
@@ -36,13 +40,13 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
     // whole decode, and the weights for the context's life: read them before
     // waiting for the previous kernel
     GemmPipe pp;
-    int first = gemm_tile_pre<DUAL, MODE, F8>(S, ring, &tmW, &tmW2, g, f0, m0, pp);
+    int first = gemm_tile_pre<DUAL, MODE, F8, LEAN>(S, ring, &tmW, &tmW2, g, f0, m0, pp);
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = S.tmem_slot;
     pdl_wait();                                        // activations are ready from here on
-    gemm_tile_main<DUAL, MODE, F8>(S, ring, tmem, &tmW, &tmW2, &tmX, g, f0, m0, first, pp);
+    gemm_tile_main<DUAL, MODE, F8, LEAN>(S, ring, tmem, &tmW, &tmW2, &tmX, g, f0, m0, first, pp);
     if (threadIdx.x == 0 && S.abort) atomicOr(status, ST_TIMEOUT);
     if ((threadIdx.x >> 5) == 0) tmem_free(tmem, TCOLS);
 }
@@ -96,9 +100,22 @@ bool tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensor
     return true;
 }
 
-size_t smem_bytes(bool dual, bool resident, int K, bool f8 = false)
+size_t smem_bytes(bool dual, bool resident, int K, bool f8 = false, bool lean = false)
 {
-    return (size_t)tile_smem(dual, resident, K, f8) + 1024;
+    return (size_t)tile_smem(dual, resident, K, f8, lean) + 1024;
+}
+
+// Multiprocessors of the current device (lean tiles pay off past one wave).
+int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
 }
 
 // ---------------------------------------------------------------- E4M3 weights
@@ -171,15 +188,29 @@ float quantize_e4m3(const float *src, size_t n, uint8_t *dst)
     return s;
 }
 
-template <bool DUAL, int MODE, bool F8 = false>
+template <bool DUAL, int MODE, bool F8 = false, bool LEAN = false>
 bool set_attr(size_t bytes)
 {
-    return cudaFuncSetAttribute(k_gemm_tc<DUAL, MODE, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bytes) == cudaSuccess;
+    auto k = k_gemm_tc<DUAL, MODE, F8, LEAN>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return false;
+    // lean tiles: room for two CTAs' shared memory on one SM
+    return !LEAN || cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared) == cudaSuccess;
 }
 
 // Checks for the tensor-map entry point and raises the kernels' dynamic
 // shared-memory limit (done before any stream capture).
+static bool set_lean_attrs()
+{
+    const size_t ml = RING_BUDGET_LEAN + 1024;
+    return set_attr<false, EPI_STORE, false, true>(ml) && set_attr<false, EPI_QKV, false, true>(ml) &&
+           set_attr<false, EPI_RESID, false, true>(ml) && set_attr<false, EPI_RESID_BASE, false, true>(ml) &&
+           set_attr<false, EPI_BIAS_SILU, false, true>(ml) && set_attr<false, EPI_SET_BIAS, false, true>(ml) &&
+           set_attr<false, EPI_HEADS, false, true>(ml) && set_attr<false, EPI_STORE, true, true>(ml) &&
+           set_attr<false, EPI_QKV, true, true>(ml) && set_attr<false, EPI_RESID, true, true>(ml) &&
+           set_attr<false, EPI_RESID_BASE, true, true>(ml);
+}
+
 bool gemm_tc_available()
 {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -190,7 +221,7 @@ bool gemm_tc_available()
            set_attr<false, EPI_BIAS_SILU>(m1) && set_attr<false, EPI_SET_BIAS>(m1) && set_attr<false, EPI_HEADS>(m1) &&
            set_attr<true, EPI_SWIGLU, true>(m2) && set_attr<false, EPI_STORE, true>(m1) &&
            set_attr<false, EPI_QKV, true>(m1) && set_attr<false, EPI_RESID, true>(m1) &&
-           set_attr<false, EPI_RESID_BASE, true>(m1);
+           set_attr<false, EPI_RESID_BASE, true>(m1) && set_lean_attrs();
 }
 
 namespace {
@@ -205,19 +236,24 @@ bool gemm_tc8(const GemmArgs &g, cudaStream_t s)
     if (dual && !tensor_map(g.Wt2, g.N, g.K, g.K, TM, &tw2, true)) return false;
     if (!dual) tw2 = tw;
     dim3 grid((g.N + TM - 1) / TM, (g.M + NT - 1) / NT), block(NTHREADS);
-    size_t smem = smem_bytes(dual, true, g.K, true);
+    const bool lean = !dual && (int)(grid.x * grid.y) > sm_count();
+    size_t smem = smem_bytes(dual, true, g.K, true, lean);
     int *st = g.status;
     cudaError_t e;
+#define F8_CASE(MODE_)                                                                                        \
+    case MODE_:                                                                                               \
+        e = lean ? launch_pdl(k_gemm_tc<false, MODE_, true, true>, grid, block, smem, s, tw, tw2, tw, g, st)  \
+                 : launch_pdl(k_gemm_tc<false, MODE_, true, false>, grid, block, smem, s, tw, tw2, tw, g, st); \
+        break;
     switch (g.epi.mode) {
     case EPI_SWIGLU: e = launch_pdl(k_gemm_tc<true, EPI_SWIGLU, true>, grid, block, smem, s, tw, tw2, tw, g, st); break;
-    case EPI_STORE: e = launch_pdl(k_gemm_tc<false, EPI_STORE, true>, grid, block, smem, s, tw, tw2, tw, g, st); break;
-    case EPI_QKV: e = launch_pdl(k_gemm_tc<false, EPI_QKV, true>, grid, block, smem, s, tw, tw2, tw, g, st); break;
-    case EPI_RESID: e = launch_pdl(k_gemm_tc<false, EPI_RESID, true>, grid, block, smem, s, tw, tw2, tw, g, st); break;
-    case EPI_RESID_BASE:
-        e = launch_pdl(k_gemm_tc<false, EPI_RESID_BASE, true>, grid, block, smem, s, tw, tw2, tw, g, st);
-        break;
+    F8_CASE(EPI_STORE)
+    F8_CASE(EPI_QKV)
+    F8_CASE(EPI_RESID)
+    F8_CASE(EPI_RESID_BASE)
     default: return false;
     }
+#undef F8_CASE
     return e == cudaSuccess;
 }
 
@@ -238,25 +274,28 @@ bool gemm_tc(const GemmArgs &g, cudaStream_t s)
         tx = tw;
     }
     dim3 grid((g.N + TM - 1) / TM, (g.M + NT - 1) / NT);
-    size_t smem = smem_bytes(dual, resident, g.K);
+    const bool lean = !dual && (int)(grid.x * grid.y) > sm_count();
+    size_t smem = smem_bytes(dual, resident, g.K, false, lean);
     int *st = g.status;
     dim3 block(NTHREADS);
     cudaError_t e;
+#define BF_CASE(MODE_)                                                                                          \
+    case MODE_:                                                                                                 \
+        e = lean ? launch_pdl(k_gemm_tc<false, MODE_, false, true>, grid, block, smem, s, tw, tw2, tx, g, st)   \
+                 : launch_pdl(k_gemm_tc<false, MODE_, false, false>, grid, block, smem, s, tw, tw2, tx, g, st); \
+        break;
     switch (g.epi.mode) {
     case EPI_SWIGLU: e = launch_pdl(k_gemm_tc<true, EPI_SWIGLU, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
-    case EPI_STORE: e = launch_pdl(k_gemm_tc<false, EPI_STORE, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
-    case EPI_QKV: e = launch_pdl(k_gemm_tc<false, EPI_QKV, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
-    case EPI_RESID: e = launch_pdl(k_gemm_tc<false, EPI_RESID, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
-    case EPI_RESID_BASE:
-        e = launch_pdl(k_gemm_tc<false, EPI_RESID_BASE, false>, grid, block, smem, s, tw, tw2, tx, g, st);
-        break;
-    case EPI_BIAS_SILU:
-        e = launch_pdl(k_gemm_tc<false, EPI_BIAS_SILU, false>, grid, block, smem, s, tw, tw2, tx, g, st);
-        break;
-    case EPI_SET_BIAS: e = launch_pdl(k_gemm_tc<false, EPI_SET_BIAS, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
-    case EPI_HEADS: e = launch_pdl(k_gemm_tc<false, EPI_HEADS, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    BF_CASE(EPI_STORE)
+    BF_CASE(EPI_QKV)
+    BF_CASE(EPI_RESID)
+    BF_CASE(EPI_RESID_BASE)
+    BF_CASE(EPI_BIAS_SILU)
+    BF_CASE(EPI_SET_BIAS)
+    BF_CASE(EPI_HEADS)
     default: return false;
     }
+#undef BF_CASE
     return e == cudaSuccess;
 }
 

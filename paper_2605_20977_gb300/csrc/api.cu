@@ -1179,6 +1179,7 @@ psw_status psw_create(const psw_model_desc *desc, const float *weights_host, siz
         return fail(nullptr, PSW_ERR_INVALID, "expected %ld weights, got %zu", lay.total, n_weights);
     if (precision != PSW_FP32 && !gemm_tc_available())
         return fail(nullptr, PSW_ERR_CUDA, "the driver offers no cuTensorMapEncodeTiled entry point");
+    if (!attention_prepare()) return fail(nullptr, PSW_ERR_CUDA, "attention kernel attributes");
     psw_ctx *c = new psw_ctx();
     c->md = *desc; c->budget = hbm_budget; c->lay = lay;
     c->prec = precision == PSW_FP8 ? P_BF16 : precision;

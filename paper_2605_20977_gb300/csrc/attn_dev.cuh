@@ -64,17 +64,22 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Shared staging of one attention warp: 32 key rows (padded stride, so
-// that 16-byte reads by consecutive lanes hit distinct banks) and 32 value
+// Shared staging of one attention warp: CK key rows (padded stride, so
+// that 16-byte reads by consecutive lanes hit distinct banks) and CK value
 // rows of one head, the query, and the list of visible keys (cache row and
-// relative-bias index; Tf * k * k <= 256 is checked at context creation).
-template <typename T, int DH>
+// relative-bias index) for up to MAXC candidates.  Spatial windows (at most
+// 81 candidates, 24 visible at k = 7) use 24-key chunks and a 96-entry list,
+// about 7.5 KB per warp at 64-wide heads, so more warps fit on an SM;
+// temporal windows (Tf * k * k <= 256, checked at context creation) 32-key
+// chunks and the full list.
+template <typename T, int DH, int CK_ = 32, int MAXC_ = 256>
 struct __align__(16) AttnWarp {
     static constexpr int RB = DH * (int)sizeof(T);            // bytes of one head's row slice
     static constexpr int KS = RB + 16;
-    static constexpr int MAXC = 256;
-    unsigned char kbuf[32 * KS];
-    unsigned char vbuf[32 * RB];
+    static constexpr int CK = CK_;
+    static constexpr int MAXC = MAXC_;
+    unsigned char kbuf[CK * KS];
+    unsigned char vbuf[CK * RB];
     unsigned char qraw[RB];                                    // the query as stored, copied with the first keys
     float qs[DH];
     int rows[MAXC];
@@ -92,11 +97,11 @@ struct __align__(16) AttnWarp {
 // (one chunk for spatial windows up to 7 x 7) with max and sum by
 // butterflies; values accumulate in list order and the sum of the weights
 // divides at the end.
-template <typename T, int DH, bool PDL>
-__device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T, DH> &sm)
+template <typename T, int DH, bool PDL, int CK = 32, int MAXC = 256>
+__device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T, DH, CK, MAXC> &sm)
 {
     constexpr int PER = DH / 32;
-    constexpr int RB = AttnWarp<T, DH>::RB, KS = AttnWarp<T, DH>::KS;
+    constexpr int RB = AttnWarp<T, DH, CK, MAXC>::RB, KS = AttnWarp<T, DH, CK, MAXC>::KS;
     constexpr int PR = RB / 16;                                // 16-byte pieces per row slice
     constexpr int EPU = 16 / (int)sizeof(T);                   // elements per piece
     using VRaw = typename RawT<PER * (int)sizeof(T)>::type;
@@ -143,8 +148,8 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
     float mx = -INFINITY, z = 0.0f, o[PER];
 #pragma unroll
     for (int i = 0; i < PER; i++) o[i] = 0.0f;
-    for (int base = 0; base < cnt; base += 32) {
-        const int nc = min(32, cnt - base);
+    for (int base = 0; base < cnt; base += CK) {
+        const int nc = min(CK, cnt - base);
         for (int x = lane; x < nc * PR; x += 32) {
             int r = x / PR, u = x - r * PR;
             long off = (long)sm.rows[base + r] * rsb + u * 16;

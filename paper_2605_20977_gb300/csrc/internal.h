@@ -200,6 +200,7 @@ struct AttnArgs {
     int kind;                       // 0: accumulator A(p), 1: self-attention S(p), -1: window
 };
 void launch_attention(int prec, const AttnArgs &a, cudaStream_t s);
+bool attention_prepare();          // kernel attributes, before any capture
 
 void launch_quantize(size_t n, const float *mu, const float *sigma, const float *scale,
                      uint8_t *idx, int32_t *m, cudaStream_t s);

@@ -145,34 +145,59 @@ void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void
 
 // ---------------------------------------------------------------- attention
 
-// Warps per block: shared staging of one warp is 32 key and 32 value rows of
+// Warps per block: shared staging of one warp is CK key and CK value rows of
 // a head.
 template <typename T, int DH>
 __host__ __device__ constexpr int attn_wpb() { return AttnWarp<T, DH>::RB <= 128 ? 4 : (AttnWarp<T, DH>::RB <= 256 ? 2 : 1); }
 
-template <typename T, int DH>
+template <typename T, int DH, int CK, int MAXC>
 __global__ void __launch_bounds__(32 * attn_wpb<T, DH>()) k_attention(AttnArgs a)
 {
     constexpr int WPB = attn_wpb<T, DH>();
-    __shared__ AttnWarp<T, DH> sm[WPB];
+    __shared__ AttnWarp<T, DH, CK, MAXC> sm[WPB];
     const int wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * WPB + wib;
     if (gw >= a.n * a.nh) return;                              // warps are independent: no block barrier
-    attn_item<T, DH, true>(a, gw, sm[wib]);
+    attn_item<T, DH, true, CK, MAXC>(a, gw, sm[wib]);
+}
+
+// Spatial windows (k * k <= 81 candidates) take the compact staging.
+template <typename T, int DH>
+static void attention_dh(const AttnArgs &a, cudaStream_t s)
+{
+    const long warps = (long)a.n * a.nh;
+    const dim3 grid(cdiv(warps, attn_wpb<T, DH>())), block(32 * attn_wpb<T, DH>());
+    static_assert(MAX_KK <= 96, "spatial candidate list");
+    if (a.temporal) launch_pdl(k_attention<T, DH, 32, 256>, grid, block, 0, s, a);
+    else launch_pdl(k_attention<T, DH, 24, 96>, grid, block, 0, s, a);
+}
+
+template <typename T, int DH>
+static bool attention_carveout()
+{
+    // warps of a block are independent: prefer the shared-memory carveout
+    // that holds the most blocks
+    const int c = cudaSharedmemCarveoutMaxShared;
+    return cudaFuncSetAttribute(k_attention<T, DH, 32, 256>, cudaFuncAttributePreferredSharedMemoryCarveout, c) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_attention<T, DH, 24, 96>, cudaFuncAttributePreferredSharedMemoryCarveout, c) ==
+               cudaSuccess;
+}
+
+bool attention_prepare()
+{
+    return attention_carveout<__nv_bfloat16, 32>() && attention_carveout<__nv_bfloat16, 64>() &&
+           attention_carveout<__nv_bfloat16, 128>() && attention_carveout<float, 32>() &&
+           attention_carveout<float, 64>() && attention_carveout<float, 128>();
 }
 
 template <typename T>
 static void attention_t(const AttnArgs &a, cudaStream_t s)
 {
-    int dh = a.d / a.nh;
-    long warps = (long)a.n * a.nh;
-    switch (dh) {
-    case 32: launch_pdl(k_attention<T, 32>, dim3(cdiv(warps, attn_wpb<T, 32>())),
-                        dim3(32 * attn_wpb<T, 32>()), 0, s, a); break;
-    case 64: launch_pdl(k_attention<T, 64>, dim3(cdiv(warps, attn_wpb<T, 64>())),
-                        dim3(32 * attn_wpb<T, 64>()), 0, s, a); break;
-    case 128: launch_pdl(k_attention<T, 128>, dim3(cdiv(warps, attn_wpb<T, 128>())),
-                         dim3(32 * attn_wpb<T, 128>()), 0, s, a); break;
+    switch (a.d / a.nh) {
+    case 32: attention_dh<T, 32>(a, s); break;
+    case 64: attention_dh<T, 64>(a, s); break;
+    case 128: attention_dh<T, 128>(a, s); break;
     default: break;   // rejected at context creation
     }
 }

@@ -685,14 +685,15 @@ void spatial_block(const Pass &P, const BlockOff &bo, const BlockDev &bd, int bi
 // tokens and accumulator queries (they depend only on the hyperlatents,
 // Sec. 3.1), and for the temporal model this frame's Context Transformer
 // pass and every spatial block's cross-attention K/V.
-void frame_prologue(const Pass &P, const int *tok, int n, const float *eh)
+void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *eh)
 {
+    const int n = H * W_;
     psw_ctx *c = P.c;
     const psw_model_desc &m = c->md;
     int d = m.d, kk = m.k * m.k;
     LAUNCH(P, K_EMBED, 2.0 * n * m.Ch * d, n * (m.Ch * 2.0 + d * 4.0),
-           launch_embed_hyper(P.S, tok, n, 0, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp), W(c, c->lay.b_hp),
-                              d, P.s));
+           launch_embed_hyper(P.S, tok, n, H, W_, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp),
+                              W(c, c->lay.b_hp), d, P.s));
     gemm_norm(P, eh, c->lay.acc_g_q, c->acc.Wqkv, nullptr, n, d, d, epi_store(tok, nullptr, d, CS_QA, 0, d));
     if (!m.temporal) return;
     // Context Transformer (Sec. 3.1): temporally shifted latents (learned
@@ -870,7 +871,7 @@ psw_status grow_tokens(psw_ctx *c, size_t ntok, size_t nkn)
 struct DecodePlan {
     int n = 0, Tmax = 0;
     std::vector<const float *> eh;      // each slot's hyperprior rows
-    std::vector<int> tok, pro_off, pro_n, step_off, step_n;
+    std::vector<int> tok, pro_off, pro_n, pro_h, pro_w, step_off, step_n;
     std::vector<int2> kn;
     size_t max_step = 0;
 };
@@ -884,6 +885,8 @@ DecodePlan plan_decode(const std::vector<psw_seq *> &qs, const psw_frame_desc *f
         D.eh.push_back(qs[b]->eh);
         int HW = fds[b].H * fds[b].W;
         D.pro_n.push_back(HW);
+        D.pro_h.push_back(fds[b].H);
+        D.pro_w.push_back(fds[b].W);
         for (int p = 0; p < HW; p++) D.tok.push_back(tok_make(b, p));
         D.Tmax = std::max(D.Tmax, qs[b]->T);
     }
@@ -910,7 +913,7 @@ void enqueue_decode(psw_ctx *c, const DecodePlan &D, const int *d_tok, const int
 {
     Pass P{c, s, c->d_slots, failed};
     if (t0 == 0) {
-        for (int b = 0; b < D.n; b++) frame_prologue(P, d_tok + D.pro_off[b], D.pro_n[b], D.eh[b]);
+        for (int b = 0; b < D.n; b++) frame_prologue(P, d_tok + D.pro_off[b], D.pro_h[b], D.pro_w[b], D.eh[b]);
         Scope sc(c, s, K_RANS, 0.0, (double)D.n * c->md.C * 128.0);
         launch_rans_dec_init(c->d_slots, D.n, c->md.C, s);
     }
@@ -1369,7 +1372,7 @@ psw_status psw_encode_params(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, c
     bool failed = false;
     Pass P{c, s, c->d_slots, &failed};
     // masked parallel pass over every position (Sec. 3.1, Sec. 3.2)
-    frame_prologue(P, c->d_tok, HW, q->eh);
+    frame_prologue(P, c->d_tok, fd->H, fd->W, q->eh);
     run_sm1(P, c->d_tok, HW);
     run_acc_sm2_heads(P, c->d_tok, HW);
     if (mu_dev) CK_CUDA(c, cudaMemcpyAsync(mu_dev, q->mu, nsym * 4, cudaMemcpyDeviceToDevice, s));

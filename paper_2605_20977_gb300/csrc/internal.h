@@ -180,7 +180,7 @@ void launch_transpose_convert(int prec, const float *src, int K, int N, void *ds
 // frame's latents (temporal shift), or the learned pad for frame 0.
 void launch_embed_context(const Slot *S, const int *tok, int n, int C, const float *gamma, const float *W,
                           const float *b, const float *pad, int d, float *out, cudaStream_t s);
-void launch_embed_hyper(const Slot *S, const int *tok, int n, int Wh_max, int Ch, int r, const float *gamma,
+void launch_embed_hyper(const Slot *S, const int *tok, int n, int H, int W, int Ch, int r, const float *gamma,
                         const float *Whp, const float *b, int d, cudaStream_t s);
 void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void *dst, cudaStream_t s);
 

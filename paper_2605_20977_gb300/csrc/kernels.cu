@@ -88,33 +88,71 @@ void launch_embed_context(const Slot *S, const int *tok, int n, int C, const flo
 }
 
 // Hyperprior tokens (Fig. 1: the decoded hyperprior enters the transformer):
-// transposed convolution with kernel = stride = r.
-__global__ void k_embed_hyper(const Slot *__restrict__ S, const int *__restrict__ tok, int Ch, int r,
-                              const float *__restrict__ gamma, const float *__restrict__ Whp,
-                              const float *__restrict__ b, int d)
+// transposed convolution with kernel = stride = r, for every position of one
+// frame.  Position (i, j) takes tap (i mod r, j mod r) of W_hp and the
+// hyperlatent (i / r, j / r), so a block takes one tap and up to 32
+// hyperlatents of one hyperlatent row: the tap's weights [Ch][d] are read
+// once for all of them (not once per position).  Thread e owns output column
+// e (and e + blockDim, ...); each output sums over c in ascending order, then
+// adds the bias.
+constexpr int EH_NB = 32;
+
+__global__ void __launch_bounds__(384) k_embed_hyper(const Slot *__restrict__ S, const int *__restrict__ tok, int Ch,
+                                                     int r, int nbmax, const float *__restrict__ gamma,
+                                                     const float *__restrict__ Whp, const float *__restrict__ b, int d)
 {
-    extern __shared__ float t[];
-    int tk = tok[blockIdx.x];
-    const Slot &s = S[tok_slot(tk)];
-    int p = tok_pos(tk), i = p / s.W, j = p % s.W, Wh = (s.W + r - 1) / r;
-    const int16_t *zv = s.zhat + ((long)(i / r) * Wh + (j / r)) * Ch;
-    for (int c = threadIdx.x; c < Ch; c += blockDim.x) t[c] = gamma[c] * (float)zv[c];
+    extern __shared__ float4 t4[];                    // [Ch][nbmax] floats: gamma * zhat, channel-major
+    float *t = reinterpret_cast<float *>(t4);
+    const Slot &s = S[tok_slot(tok[0])];
+    const int H = s.H, W = s.W, Wh = (W + r - 1) / r;
+    const int ti = blockIdx.x / r, tj = blockIdx.x % r, a = blockIdx.y, b0 = blockIdx.z * nbmax;
+    const int i = a * r + ti;
+    if (i >= H) return;                               // uniform over the block
+    const int nb = min(nbmax, Wh - b0);
+    for (int x = threadIdx.x; x < nb * Ch; x += blockDim.x) {
+        const int k = x / Ch, c = x - k * Ch;
+        t[c * nbmax + k] = gamma[c] * (float)s.zhat[((long)a * Wh + b0 + k) * Ch + c];
+    }
     __syncthreads();
-    const float *Ws = Whp + (long)((i % r) * r + (j % r)) * Ch * d;
-    float *eh = s.eh + (long)p * d;
+    const float *Ws = Whp + (long)blockIdx.x * Ch * d;
     for (int e = threadIdx.x; e < d; e += blockDim.x) {
-        float acc = 0.0f;
-        for (int c = 0; c < Ch; c++) acc = fmaf(t[c], Ws[(long)c * d + e], acc);
-        eh[e] = acc + b[e];
+        float acc[EH_NB];
+#pragma unroll
+        for (int k = 0; k < EH_NB; k++) acc[k] = 0.0f;
+#pragma unroll 2
+        for (int c = 0; c < Ch; c++) {
+            const float w = Ws[(long)c * d + e];
+            const float4 *tc = t4 + c * (nbmax >> 2);
+#pragma unroll
+            for (int q = 0; q < EH_NB / 4; q++) {
+                if (4 * q < nb) {                      // columns past nb are never stored
+                    const float4 v = tc[q];
+                    acc[4 * q] = fmaf(v.x, w, acc[4 * q]);
+                    acc[4 * q + 1] = fmaf(v.y, w, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmaf(v.z, w, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmaf(v.w, w, acc[4 * q + 3]);
+                }
+            }
+        }
+        const float be = b[e];
+#pragma unroll
+        for (int k = 0; k < EH_NB; k++) {
+            const int j = (b0 + k) * r + tj;
+            if (k < nb && j < W) s.eh[((long)i * W + j) * d + e] = acc[k] + be;
+        }
     }
 }
 
-void launch_embed_hyper(const Slot *S, const int *tok, int n, int Wh_max, int Ch, int r, const float *gamma,
+// tok: every position of one frame in raster order (the slot is tok[0]'s).
+void launch_embed_hyper(const Slot *S, const int *tok, int n, int H, int W, int Ch, int r, const float *gamma,
                         const float *Whp, const float *b, int d, cudaStream_t s)
 {
-    (void)Wh_max;
     if (n <= 0) return;
-    k_embed_hyper<<<n, 128, Ch * sizeof(float), s>>>(S, tok, Ch, r, gamma, Whp, b, d);
+    const int Hh = (H + r - 1) / r, Wh = (W + r - 1) / r;
+    const int nbmax = std::max(4, std::min(EH_NB, (12288 / Ch) & ~3));   // staged hyperlatents: <= 64 KB
+    const dim3 grid(r * r, Hh, (Wh + nbmax - 1) / nbmax);
+    const int threads = d < 384 ? ((d + 31) / 32) * 32 : 384;
+    k_embed_hyper<<<grid, threads, (size_t)nbmax * Ch * sizeof(float), s>>>(S, tok, Ch, r, nbmax, gamma, Whp, b, d);
 }
 
 // ---------------------------------------------------------------- RMSNorm
@@ -186,6 +224,8 @@ static bool attention_carveout()
 
 bool attention_prepare()
 {
+    if (cudaFuncSetAttribute(k_embed_hyper, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 4096 * 4) != cudaSuccess)
+        return false;                                 // 4 staged hyperlatents of 4096 channels
     return attention_carveout<__nv_bfloat16, 32>() && attention_carveout<__nv_bfloat16, 64>() &&
            attention_carveout<__nv_bfloat16, 128>() && attention_carveout<float, 32>() &&
            attention_carveout<float, 64>() && attention_carveout<float, 128>();

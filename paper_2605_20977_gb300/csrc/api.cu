@@ -136,7 +136,9 @@ struct GraphRec {
     double ntok = 0, ntok_prev = 0;    // tokens over all steps; those that also run Spatial Module 1
     bool persist = false;              // exec holds the prologue only; the steps run persistently
     long launches = 0;
+    long used = 0;                     // last use (least recently used graphs are dropped first)
 };
+constexpr size_t GRAPH_CAP = 16;       // recorded batch shapes kept per context
 
 void graph_free(GraphRec &g)
 {
@@ -186,6 +188,7 @@ struct psw_ctx {
     size_t tok_cap = 0, kn_cap = 0;
     cudaStream_t cap_stream = nullptr;
     std::map<std::vector<long>, GraphRec> graphs;
+    long graph_clock = 0;
     bool use_graphs = true;
     // persistent decoder: the program of one step (rebuilt when the
     // workspace moves), its kernel's shared memory and grid, barrier words
@@ -995,7 +998,10 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
     key[0] = c->ws_gen;
     if (graph) {
         auto it = c->graphs.find(key);
-        if (it != c->graphs.end()) gr = &it->second;
+        if (it != c->graphs.end()) {
+            gr = &it->second;
+            gr->used = ++c->graph_clock;
+        }
     }
     DecodePlan D;
     psw_status st;
@@ -1065,6 +1071,16 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
             }
             g.launches = c->launches - l0;
             c->launches = l0;
+            if (c->graphs.size() >= GRAPH_CAP) {
+                // every earlier decode has completed (each call synchronises
+                // its stream before returning): drop the least recently used
+                auto lru = c->graphs.begin();
+                for (auto jt = c->graphs.begin(); jt != c->graphs.end(); ++jt)
+                    if (jt->second.used < lru->second.used) lru = jt;
+                graph_free(lru->second);
+                c->graphs.erase(lru);
+            }
+            g.used = ++c->graph_clock;
             gr = &(c->graphs[key] = g);
         }
         for (cudaGraphExec_t ex : gr->exec) CK_CUDA(c, cudaGraphLaunch(ex, s));

@@ -258,3 +258,28 @@ def test_destroyed_sequences_leave_no_stale_graphs():
         if ref is None:
             ref = got
         _check_same(ref, got, items)
+
+
+def test_graph_cache_is_bounded_and_records_again():
+    """More batch shapes than the context keeps graphs for: the oldest are
+    dropped and recorded again when needed, with the same results."""
+    cfg = synth.config("tiny")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
+    ctx.set_engine(psw.ENGINE_GRAPH)
+    items = _encode(ctx, cfg, synth.frames(cfg, 1, seed=95), 0)
+    bs, n, z, y = items[0]
+    fd = psw.frame_desc(cfg.H, cfg.W, 0)
+    seqs = [ctx.seq_create(cfg.H, cfg.W) for _ in range(20)]
+    first = None
+    for rnd in range(2):
+        for q in seqs:                                  # 20 single-frame batch shapes (one key each)
+            q.reset()
+            yo, mu, sg = _alloc(cfg.H, cfg.W, cfg.C)
+            q.decode_frame(fd, bs, n, z, yo, mu, sg)
+            got = (yo.cpu().numpy(), mu.cpu().numpy(), sg.cpu().numpy())
+            assert np.array_equal(got[0], y)
+            if first is None:
+                first = got
+            assert np.array_equal(got[1], first[1]) and np.array_equal(got[2], first[2])
+    for q in seqs:
+        q.close()

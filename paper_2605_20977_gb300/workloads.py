@@ -123,9 +123,10 @@ def run_mixed(nseq=32, nframes=4, tune_frames=1, seed=7, dev=None, precision="bf
 
 
 def run_serve(rate=200.0, window=0.1, per_grid=2, gop=16, budget_gb=120.0, max_batch=128, seed=1005, dev=None,
-              unbatched=True, precision="fp8"):
-    """Batched service in `precision` against one frame per call in BF16,
-    on the same arrival trace (each arm encodes its own streams)."""
+              unbatched=True, precision="fp8", engines=("graph",)):
+    """Batched service in `precision` (once per decode engine in `engines`)
+    against one frame per call in BF16, on the same arrival trace (each
+    precision encodes its own streams)."""
     import torch
     cfg = synth.config("p1080")
     trace = serve.poisson_trace(rate, window, GRIDS, max_frames=gop, seed=seed)
@@ -144,21 +145,29 @@ def run_serve(rate=200.0, window=0.1, per_grid=2, gop=16, budget_gb=120.0, max_b
     out = {"workload": f"Poisson arrivals at {rate:g} requests/s over {window:g} s ({len(trace)} requests, "
            f"{sum(n for _, _, n in trace)} frames), 1..{gop} frames each, grids "
            + ", ".join(f"{H}x{W}" for H, W in GRIDS) + f"; HBM budget {budget_gb:g} GB; P-frame model"}
-    for name, mb, prec in (("batched", max_batch, precision), ("one_frame_per_call", 1, "bf16")):
-        if name != "batched" and not unbatched:
-            continue
-        ctx = psw.Context(cfg, synth.weights(cfg), precision=PRECISIONS[prec])
-        pool = Pool(ctx, cfg, GRIDS, per_grid, gop, dev)
+    eng = {"persistent": psw.ENGINE_PERSISTENT, "graph": psw.ENGINE_GRAPH}
+    arms = [("batched" if len(engines) == 1 else f"batched_{e}", max_batch, precision, e) for e in engines]
+    if unbatched:
+        arms.append(("one_frame_per_call", 1, "bf16", engines[0]))
+    ctxs = {}
+    for name, mb, prec, e in arms:
+        if prec not in ctxs:
+            ctx = psw.Context(cfg, synth.weights(cfg), precision=PRECISIONS[prec])
+            ctxs[prec] = (ctx, Pool(ctx, cfg, GRIDS, per_grid, gop, dev))
+        ctx, pool = ctxs[prec]
         reqs = requests(pool)
         torch.cuda.synchronize()
-        st = serve.Server(ctx, int(budget_gb * 2 ** 30), max_batch=mb).run(reqs)
+        st = serve.Server(ctx, int(budget_gb * 2 ** 30), max_batch=mb, engine=eng[e]).run(reqs)
         for r in reqs:
             for f, y in enumerate(r.truth):
                 if not np.array_equal(r.outputs[f].cpu().numpy(), y):
                     raise RuntimeError("served decode differs")
         st["precision"] = prec
+        st["engine"] = e
         out[name] = st
-        del pool, reqs
+        del reqs
+    for ctx, pool in ctxs.values():
+        del pool
         ctx.close()
     return out
 
@@ -171,6 +180,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--window", type=float, default=0.1)
     ap.add_argument("--no-unbatched", action="store_true")
+    ap.add_argument("--engines", default="graph",
+                    help="serve: decode engines of the batched arm, comma separated (persistent, graph)")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default=None,
                     help="mixed: bf16 (default); serve: the batched arm's precision, fp8 (default)")
     args = ap.parse_args()
@@ -181,7 +192,7 @@ def main():
         res = run_mixed(args.seqs, args.frames, dev=dev, precision=args.precision or "bf16")
     else:
         res = run_serve(args.rate, args.window, dev=dev, unbatched=not args.no_unbatched,
-                        precision=args.precision or "fp8")
+                        precision=args.precision or "fp8", engines=tuple(args.engines.split(",")))
     print(json.dumps(res), flush=True)
 
 

@@ -66,7 +66,9 @@ constexpr int NTHREADS = 256;  // 8 warps: warps w and w + 4 share TMEM lanes 32
 constexpr int NISS = 4;        // MMA issuers (lane 0 of warps 1..4), one K step of 16 per chunk each
 // tensor-memory columns of a tile: one 64-column accumulator (two for the
 // dual form) per issuer
-__host__ __device__ constexpr uint32_t tile_tcols(bool dual) { return (dual ? 2 : 1) * NT * NISS; }
+__host__ __device__ constexpr uint32_t tile_tcols(bool dual, int tn = NT) { return (dual ? 2 : 1) * tn * NISS; }
+// Bytes of one 128-byte-wide K chunk of a tn-token operand.
+__host__ __device__ constexpr int tok_chunk_bytes(int tn) { return tn * 128; }
 
 __host__ __device__ constexpr int kchunk(bool f8) { return f8 ? KC8 : KC; }
 
@@ -278,19 +280,23 @@ __device__ __forceinline__ void tmem_sum8x2(uint32_t addr, uint32_t addr2, uint3
 
 // Byte offset of element (row r, column k) of a K-major bf16 operand laid
 // out in 128-byte-swizzled atoms of 64 columns x NT rows.
+template <int TN = NT>
 __device__ __forceinline__ uint32_t swz(int r, int k)
 {
     int kc = k >> 6, col = k & 63;
     uint32_t byte = (uint32_t)col * 2;
-    return (uint32_t)kc * B_BYTES + (uint32_t)r * 128 + ((((byte >> 4) ^ (uint32_t)(r & 7))) << 4) + (byte & 15);
+    return (uint32_t)kc * tok_chunk_bytes(TN) + (uint32_t)r * 128 + ((((byte >> 4) ^ (uint32_t)(r & 7))) << 4) +
+           (byte & 15);
 }
 
 // The same for an 8-bit operand: atoms of 128 columns.
+template <int TN = NT>
 __device__ __forceinline__ uint32_t swz8(int r, int k)
 {
     int kc = k >> 7;
     uint32_t byte = (uint32_t)(k & 127);
-    return (uint32_t)kc * B_BYTES + (uint32_t)r * 128 + ((((byte >> 4) ^ (uint32_t)(r & 7))) << 4) + (byte & 15);
+    return (uint32_t)kc * tok_chunk_bytes(TN) + (uint32_t)r * 128 + ((((byte >> 4) ^ (uint32_t)(r & 7))) << 4) +
+           (byte & 15);
 }
 
 __device__ __forceinline__ uint2 pack4(float a, float b, float c, float d)
@@ -370,9 +376,9 @@ __device__ __forceinline__ void pipe_advance(GemmPipe &pp, int nk, int nst)
 
 // Ring stage bytes: the weight chunk(s) and, for a streamed token operand,
 // its chunk.
-__host__ __device__ constexpr int stage_bytes(bool dual, bool resident)
+__host__ __device__ constexpr int stage_bytes(bool dual, bool resident, int tn = NT)
 {
-    return (dual ? 2 : 1) * A_BYTES + (resident ? 0 : B_BYTES);
+    return (dual ? 2 : 1) * A_BYTES + (resident ? 0 : tok_chunk_bytes(tn));
 }
 
 // K chunks of a projection.
@@ -381,10 +387,11 @@ __host__ __device__ constexpr int kchunks(int K, bool f8) { return (K + kchunk(f
 // Ring depth of a projection: as many stages as its K chunks, the barrier
 // pairs and the shared-memory budget (after the resident operand) allow.
 // Lean tiles (single accumulator, two CTAs per SM) have the smaller budget.
-__host__ __device__ constexpr int ring_stages(bool dual, bool resident, int K, bool f8 = false, bool lean = false)
+__host__ __device__ constexpr int ring_stages(bool dual, bool resident, int K, bool f8 = false, bool lean = false,
+                                             int tn = NT)
 {
-    int nk = kchunks(K, f8), res = resident ? nk * B_BYTES : 0;
-    int st = ((lean ? RING_BUDGET_LEAN : RING_BUDGET) - res) / stage_bytes(dual, resident);
+    int nk = kchunks(K, f8), res = resident ? nk * tok_chunk_bytes(tn) : 0;
+    int st = ((lean ? RING_BUDGET_LEAN : RING_BUDGET) - res) / stage_bytes(dual, resident, tn);
     st = st < MAXS ? st : MAXS;
     st = st < nk ? st : nk;
     return st < 1 ? 1 : st;
@@ -392,10 +399,11 @@ __host__ __device__ constexpr int ring_stages(bool dual, bool resident, int K, b
 
 // Dynamic shared memory of a tile (ring, then the resident token operand),
 // without the 1024-byte alignment slack.
-__host__ __device__ constexpr int tile_smem(bool dual, bool resident, int K, bool f8 = false, bool lean = false)
+__host__ __device__ constexpr int tile_smem(bool dual, bool resident, int K, bool f8 = false, bool lean = false,
+                                           int tn = NT)
 {
-    return ring_stages(dual, resident, K, f8, lean) * stage_bytes(dual, resident) +
-           (resident ? kchunks(K, f8) * B_BYTES : 0);
+    return ring_stages(dual, resident, K, f8, lean, tn) * stage_bytes(dual, resident, tn) +
+           (resident ? kchunks(K, f8) * tok_chunk_bytes(tn) : 0);
 }
 
 // Initialise the barriers (thread 0; the caller synchronises).
@@ -429,7 +437,7 @@ __device__ __forceinline__ float inv_rms(float ss, float invK) { return rsqrtf(f
 // RMSNorm of RB rows r0 .. r0+RB-1 of the tile by one warp, every load of
 // the rows issued before the first reduction; lane l holds elements
 // 4l + 128c .. +3 of a row (c < CH).
-template <int RB, int CH>
+template <int RB, int CH, int TN = NT>
 __device__ __forceinline__ void norm_rows(const float *__restrict__ xrows, const float *__restrict__ gain, int K,
                                           int M, int m0, int r0, uint8_t *res)
 {
@@ -466,7 +474,7 @@ __device__ __forceinline__ void norm_rows(const float *__restrict__ xrows, const
         for (int c = 0; c < CH; c++) {
             int e = lane * 4 + c * 128;
             if (e >= K) continue;
-            *(uint2 *)(res + swz(r, e)) = pack4(v[b][c].x * inv * gh[c].x, v[b][c].y * inv * gh[c].y,
+            *(uint2 *)(res + swz<TN>(r, e)) = pack4(v[b][c].x * inv * gh[c].x, v[b][c].y * inv * gh[c].y,
                                                 v[b][c].z * inv * gh[c].z, v[b][c].w * inv * gh[c].w);
         }
     }
@@ -479,7 +487,7 @@ __device__ __forceinline__ void norm_rows(const float *__restrict__ xrows, const
 // flight together (K <= 384: the eight rows at once; lean tiles, with half
 // the registers, four at a time).  One out-of-line copy serves every
 // projection mode (keeps the instruction footprint small).
-template <int RB>
+template <int RB, int TN = NT>
 __device__ __forceinline__ void embed_rows(const float *__restrict__ gain, int K, int r0, uint8_t *res,
                                            const int16_t *const *yrow)
 {
@@ -502,18 +510,27 @@ __device__ __forceinline__ void embed_rows(const float *__restrict__ gain, int K
             int e = lane * 4 + c * 128;
             if (e >= K) continue;
             const float *gm = gain + e;
-            *(uint2 *)(res + swz(r0 + b, e)) = pack4(gm[0] * (float)q[b][c].x, gm[1] * (float)q[b][c].y,
+            *(uint2 *)(res + swz<TN>(r0 + b, e)) = pack4(gm[0] * (float)q[b][c].x, gm[1] * (float)q[b][c].y,
                                                      gm[2] * (float)q[b][c].z, gm[3] * (float)q[b][c].w);
         }
     }
 }
 
-template <bool LEAN>
+template <bool LEAN, int TN = NT>
 static __device__ __noinline__ void build_tokens(const GemmArgs &g, int m0, uint8_t *res, const int16_t *const *yrow)
 {
     const int warp = threadIdx.x >> 5;
-    const int K = g.K, M = g.M, r0 = warp * (NT / 8);
+    const int K = g.K, M = g.M, r0 = warp * (TN / 8);
     const float *gain = g.a_gain;
+    if constexpr (TN == 32) {                          // four rows per warp
+        if (g.asrc == A_NORM) {
+            if (K <= 384) norm_rows<4, 3, TN>(g.xrows, gain, K, M, m0, r0, res);
+            else norm_rows<4, 4, TN>(g.xrows, gain, K, M, m0, r0, res);
+        } else {
+            embed_rows<4, TN>(gain, K, r0, res, yrow);
+        }
+        return;
+    }
     if (g.asrc == A_NORM) {
         const float *xrows = g.xrows;
         if (K <= 384 && !LEAN) {
@@ -537,7 +554,7 @@ static __device__ __noinline__ void build_tokens(const GemmArgs &g, int m0, uint
 
 // E4M3 token operand: RMSNorm rows as norm_rows, then each row quantised
 // with its own power-of-two scale (xs[r]); lane l holds elements 4l + 128c.
-template <int RB, int CH>
+template <int RB, int CH, int TN = NT>
 __device__ __forceinline__ void norm_rows8(const float *__restrict__ xrows, const float *__restrict__ gain, int K,
                                            int M, int m0, int r0, uint8_t *res, float *xs)
 {
@@ -584,7 +601,7 @@ __device__ __forceinline__ void norm_rows8(const float *__restrict__ xrows, cons
         for (int c = 0; c < CH; c++) {
             int e = lane * 4 + c * 128;
             if (e >= K) continue;
-            *(uint32_t *)(res + swz8(r, e)) = e4m3x4(v[b][c].x * qm, v[b][c].y * qm, v[b][c].z * qm, v[b][c].w * qm);
+            *(uint32_t *)(res + swz8<TN>(r, e)) = e4m3x4(v[b][c].x * qm, v[b][c].y * qm, v[b][c].z * qm, v[b][c].w * qm);
         }
         if (lane == 0) xs[r] = sc;
     }
@@ -592,7 +609,7 @@ __device__ __forceinline__ void norm_rows8(const float *__restrict__ xrows, cons
 
 // E4M3 token operand from compact bf16 rows A[m][lda] (K <= 256 CH): lane l
 // holds elements 8l + 256c of RB rows.
-template <int RB, int CH>
+template <int RB, int CH, int TN = NT>
 __device__ __forceinline__ void quant_rows8(const __nv_bfloat16 *__restrict__ A, int lda, int K, int M, int m0,
                                             int r0, uint8_t *res, float *xs)
 {
@@ -629,7 +646,7 @@ __device__ __forceinline__ void quant_rows8(const __nv_bfloat16 *__restrict__ A,
             const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&q[b][c]);
             float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
             float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
-            *(uint2 *)(res + swz8(r, e)) = make_uint2(e4m3x4(f0.x * qm, f0.y * qm, f1.x * qm, f1.y * qm),
+            *(uint2 *)(res + swz8<TN>(r, e)) = make_uint2(e4m3x4(f0.x * qm, f0.y * qm, f1.x * qm, f1.y * qm),
                                                       e4m3x4(f2.x * qm, f2.y * qm, f3.x * qm, f3.y * qm));
         }
         if (lane == 0) xs[r] = sc;
@@ -639,10 +656,21 @@ __device__ __forceinline__ void quant_rows8(const __nv_bfloat16 *__restrict__ A,
 // Build the E4M3 token operand of rows m0 .. m0+63 (warp w: rows 8w ..
 // 8w+7): A_NORM (K <= 512) or compact bf16 rows (A_DIRECT, K <= 1024).
 // Lean tiles take four rows at a time.
-template <bool LEAN>
+template <bool LEAN, int TN = NT>
 static __device__ __noinline__ void build_tokens8(const GemmArgs &g, int m0, uint8_t *res, float *xs)
 {
-    const int r0 = (threadIdx.x >> 5) * (NT / 8);
+    const int r0 = (threadIdx.x >> 5) * (TN / 8);
+    if constexpr (TN == 32) {                          // four rows per warp
+        if (g.asrc == A_NORM) {
+            if (g.K <= 384) norm_rows8<4, 3, TN>(g.xrows, g.a_gain, g.K, g.M, m0, r0, res, xs);
+            else norm_rows8<4, 4, TN>(g.xrows, g.a_gain, g.K, g.M, m0, r0, res, xs);
+        } else {
+            const __nv_bfloat16 *A = (const __nv_bfloat16 *)g.A;
+            if (g.K <= 512) quant_rows8<4, 2, TN>(A, g.lda, g.K, g.M, m0, r0, res, xs);
+            else quant_rows8<4, 4, TN>(A, g.lda, g.K, g.M, m0, r0, res, xs);
+        }
+        return;
+    }
     if (g.asrc == A_NORM) {
         if (g.K <= 384 && !LEAN) {
             norm_rows8<8, 3>(g.xrows, g.a_gain, g.K, g.M, m0, r0, res, xs);
@@ -673,11 +701,11 @@ static __device__ __noinline__ void build_tokens8(const GemmArgs &g, int m0, uin
 // Per-token addresses a mode needs, resolved once per tile by threads 0..63:
 // cache rows (EPI_STORE into a cache, EPI_QKV), the hyperprior row
 // (EPI_RESID_BASE), the head outputs (EPI_HEADS), the latents (A_EMBED).
-template <int MODE>
+template <int MODE, int TN = NT>
 __device__ __forceinline__ void build_table(const GemmArgs &g, int m0, GemmShared &S)
 {
     int r = threadIdx.x;
-    if (r >= NT) return;
+    if (r >= TN) return;
     int m = m0 + r;
     S.tab[0][r] = S.tab[1][r] = S.tab[2][r] = S.tab[3][r] = 0;
     S.yrow[r] = nullptr;
@@ -711,19 +739,19 @@ __device__ __forceinline__ void build_table(const GemmArgs &g, int m0, GemmShare
 // every value before storing any (the output pointers are generic, so each
 // store could alias later loads).  Out of line: one copy per mode, small
 // enough to stay in the instruction cache.
-template <bool DUAL, int MODE, bool F8, bool LEAN>
+template <bool DUAL, int MODE, bool F8, bool LEAN, int TN>
 static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, uint32_t tmem, const GemmArgs &g,
                                                   int f0, int m0, GemmPipe &pp)
 {
     constexpr bool RESID = MODE == EPI_RESID || MODE == EPI_RESID_BASE;
-    constexpr int PRE = LEAN ? NT / 4 : NT / 2;                    // residual values read before the MMAs end
+    constexpr int PRE = LEAN ? TN / 4 : TN / 2;                    // residual values read before the MMAs end
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int M = g.M, N = g.N;
     const Epi e = g.epi;
     const int f = f0 + (warp & 3) * 32 + lane;
     const bool fok = f < N;
-    const int cb = (warp >> 2) * (NT / 2);
-    float old[RESID ? NT / 2 : 1];
+    const int cb = (warp >> 2) * (TN / 2);
+    float old[RESID ? TN / 2 : 1];
     if constexpr (RESID) {
 #pragma unroll
         for (int j = 0; j < PRE; j++) {
@@ -743,7 +771,7 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
         return;
     }
     const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    constexpr uint32_t ASTEP = (DUAL ? 2 : 1) * NT;                // columns between the issuers' accumulators
+    constexpr uint32_t ASTEP = (DUAL ? 2 : 1) * TN;                // columns between the issuers' accumulators
     // E4M3: dequantisation scales of the feature row (both products below
     // are of powers of two, hence exact)
     float wf = 1.0f, wf2 = 1.0f;
@@ -752,7 +780,7 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
     }
     if constexpr (RESID) {
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
+        for (int h = 0; h < TN / 32; h++) {
             if (h * 16 >= PRE) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
@@ -780,10 +808,10 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
             gb = (f & 1) ? e.bsg[f >> 1] : e.bmu[f >> 1];
         }
 #pragma unroll 1
-        for (int c0 = cb; c0 < cb + NT / 2; c0 += 8) {
+        for (int c0 = cb; c0 < cb + TN / 2; c0 += 8) {
             float v[8], v2[8], o[8];
             int oi[8];
-            if (DUAL) tmem_sum8x2(trow + c0, trow + NT + c0, ASTEP, v, v2);
+            if (DUAL) tmem_sum8x2(trow + c0, trow + TN + c0, ASTEP, v, v2);
             else tmem_sum8(trow + c0, ASTEP, v);
             if constexpr (F8) {
 #pragma unroll
@@ -883,17 +911,17 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
 // the ring's stages (stage s issued by lane 0 of warp s: one thread issues a
 // tensor copy only every ~150 ns).  Returns the number of stages filled.  The
 // caller synchronises the CTA before gemm_tile_main.
-template <bool DUAL, int MODE, bool F8 = false, bool LEAN = false>
+template <bool DUAL, int MODE, bool F8 = false, bool LEAN = false, int TN = NT>
 __device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const CUtensorMap *tmW,
                                              const CUtensorMap *tmW2, const GemmArgs &g, int f0, int m0,
                                              GemmPipe &pp)
 {
     constexpr int KCH = kchunk(F8);
     if (MODE == EPI_HEADS && threadIdx.x < NSCALES) S.stab[threadIdx.x] = g.epi.scale[threadIdx.x];
-    build_table<MODE>(g, m0, S);
+    build_table<MODE, TN>(g, m0, S);
     const bool resident = F8 || g.asrc != A_DIRECT;
-    const int stage = stage_bytes(DUAL, resident);
-    const int nst = ring_stages(DUAL, resident, g.K, F8, LEAN);
+    const int stage = stage_bytes(DUAL, resident, TN);
+    const int nst = ring_stages(DUAL, resident, g.K, F8, LEAN, TN);
     const int s = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0 && s < nst) {
         // the ring is idle between tiles (the previous tile's MMAs are done)
@@ -910,7 +938,7 @@ __device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const
 // result.  Roles: lane 0 of warps 1..4 issue the MMAs; lane 0 of warps 0, 5,
 // 6 and 7 issue the copies of the chunks past the first ring fill, each the
 // refills of its own stages.
-template <bool DUAL, int MODE, bool F8 = false, bool LEAN = false>
+template <bool DUAL, int MODE, bool F8 = false, bool LEAN = false, int TN = NT>
 __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *tmW,
                                                const CUtensorMap *tmW2, const CUtensorMap *tmX, const GemmArgs &g,
                                                int f0, int m0, int first, GemmPipe &pp)
@@ -919,8 +947,8 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
     constexpr int NPROD = NTHREADS / 32 - NISS;                    // producer warps: 0 and NISS+1 ..
     constexpr int KCH = kchunk(F8);
     const bool resident = F8 || g.asrc != A_DIRECT;
-    const int stage = stage_bytes(DUAL, resident);
-    const int nk = kchunks(g.K, F8), nst = ring_stages(DUAL, resident, g.K, F8, LEAN);
+    const int stage = stage_bytes(DUAL, resident, TN);
+    const int nk = kchunks(g.K, F8), nst = ring_stages(DUAL, resident, g.K, F8, LEAN, TN);
     uint8_t *res = ring + nst * stage;                             // resident token operand
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -934,8 +962,8 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
             tma_load(ring + s * stage + NACC * A_BYTES, tmX, &S.full[s], s * KC, m0);
     }
     if (resident) {
-        if (F8) build_tokens8<LEAN>(g, m0, res, S.xs);
-        else build_tokens<LEAN>(g, m0, res, S.yrow);
+        if (F8) build_tokens8<LEAN, TN>(g, m0, res, S.xs);
+        else build_tokens<LEAN, TN>(g, m0, res, S.yrow);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
     }
@@ -969,29 +997,29 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
         // four issuers shorten the dependent chain fourfold); a stage that is
         // filled again in this tile is released once all four have committed
         const int q = warp - 1;
-        const uint32_t id = F8 ? idesc_e4m3(TM, NT) : idesc_bf16(TM, NT);
-        const uint32_t acc0 = tmem + (uint32_t)q * (NACC * NT);
+        const uint32_t id = F8 ? idesc_e4m3(TM, TN) : idesc_bf16(TM, TN);
+        const uint32_t acc0 = tmem + (uint32_t)q * (NACC * TN);
         for (int j = 0; j < nk; j++) {
             int s = j % nst, u = j / nst;
             if (S.abort) break;
             if (!mbar_wait(&S.full[s], fill_parity(pp, s, u))) { S.abort = 1; break; }
             fence_after();
             uint32_t base = su32(ring + s * stage);
-            uint32_t bb = resident ? su32(res) + j * B_BYTES : base + NACC * A_BYTES;
+            uint32_t bb = resident ? su32(res) + j * tok_chunk_bytes(TN) : base + NACC * A_BYTES;
             // K step q: 32 bytes along the 128-byte rows (16 bf16 or 32 E4M3)
             if (F8) {
                 mma8(acc0, sdesc(base + q * 32), sdesc(bb + q * 32), id, j != 0);
-                if (DUAL) mma8(acc0 + NT, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
+                if (DUAL) mma8(acc0 + TN, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
             } else {
                 mma(acc0, sdesc(base + q * 32), sdesc(bb + q * 32), id, j != 0);
-                if (DUAL) mma(acc0 + NT, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
+                if (DUAL) mma(acc0 + TN, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
             }
             if (j + nst < nk) mma_commit(&S.empty[s]);                 // the stage is filled again in this tile
         }
         mma_commit(&S.done);
     }
     __syncwarp();
-    gemm_epilogue<DUAL, MODE, F8, LEAN>(S, ring, tmem, g, f0, m0, pp);
+    gemm_epilogue<DUAL, MODE, F8, LEAN, TN>(S, ring, tmem, g, f0, m0, pp);
     pipe_advance(pp, nk, nst);
 }
 

@@ -22,16 +22,18 @@ namespace {
 // (one's token build and epilogue overlap the other's copies and MMAs);
 // chosen for launches with more tiles than SMs.  Same arithmetic as the
 // one-CTA form.
-template <bool DUAL, int MODE, bool F8, bool LEAN = false>
+// TN: tokens per tile, 64, or 32 for launches whose 64-token grid leaves SMs
+// idle (twice the CTAs, each with half the token build and epilogue).
+template <bool DUAL, int MODE, bool F8, bool LEAN = false, int TN = NT>
 __global__ void __launch_bounds__(NTHREADS, LEAN ? 2 : 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmW2,
           const __grid_constant__ CUtensorMap tmX, GemmArgs g, int *status)
 {
-    constexpr uint32_t TCOLS = tile_tcols(DUAL);
+    constexpr uint32_t TCOLS = tile_tcols(DUAL, TN);
     extern __shared__ uint8_t smem_raw[];
     __shared__ GemmShared S;
     uint8_t *ring = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int f0 = blockIdx.x * TM, m0 = blockIdx.y * NT;
+    const int f0 = blockIdx.x * TM, m0 = blockIdx.y * TN;
     if (threadIdx.x == 0) gemm_shared_init(S);
     if ((threadIdx.x >> 5) == 0) tmem_alloc(&S.tmem_slot, TCOLS);
     __syncthreads();                                   // barriers initialised before any warp issues copies
@@ -40,13 +42,13 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
     // whole decode, and the weights for the context's life: read them before
     // waiting for the previous kernel
     GemmPipe pp;
-    int first = gemm_tile_pre<DUAL, MODE, F8, LEAN>(S, ring, &tmW, &tmW2, g, f0, m0, pp);
+    int first = gemm_tile_pre<DUAL, MODE, F8, LEAN, TN>(S, ring, &tmW, &tmW2, g, f0, m0, pp);
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = S.tmem_slot;
     pdl_wait();                                        // activations are ready from here on
-    gemm_tile_main<DUAL, MODE, F8, LEAN>(S, ring, tmem, &tmW, &tmW2, &tmX, g, f0, m0, first, pp);
+    gemm_tile_main<DUAL, MODE, F8, LEAN, TN>(S, ring, tmem, &tmW, &tmW2, &tmX, g, f0, m0, first, pp);
     if (threadIdx.x == 0 && S.abort) atomicOr(status, ST_TIMEOUT);
     if ((threadIdx.x >> 5) == 0) tmem_free(tmem, TCOLS);
 }
@@ -100,10 +102,11 @@ bool tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensor
     return true;
 }
 
-size_t smem_bytes(bool dual, bool resident, int K, bool f8 = false, bool lean = false)
+size_t smem_bytes(bool dual, bool resident, int K, bool f8 = false, bool lean = false, int tn = NT)
 {
-    return (size_t)tile_smem(dual, resident, K, f8, lean) + 1024;
+    return (size_t)tile_smem(dual, resident, K, f8, lean, tn) + 1024;
 }
+
 
 // Multiprocessors of the current device (lean tiles pay off past one wave).
 int sm_count()
@@ -116,6 +119,14 @@ int sm_count()
         if (n <= 0) n = 1;
     }
     return n;
+}
+
+// Tokens per tile of a launch: 32 when the 64-token grid fills less than the
+// SMs and the 32-token grid still fits in one wave.
+int tile_tokens(int nf, int M)
+{
+    const int t64 = nf * ((M + 63) / 64), t32 = nf * ((M + 31) / 32);
+    return t64 < sm_count() && t32 <= sm_count() ? 32 : 64;
 }
 
 // ---------------------------------------------------------------- E4M3 weights
@@ -188,10 +199,10 @@ float quantize_e4m3(const float *src, size_t n, uint8_t *dst)
     return s;
 }
 
-template <bool DUAL, int MODE, bool F8 = false, bool LEAN = false>
+template <bool DUAL, int MODE, bool F8 = false, bool LEAN = false, int TN = NT>
 bool set_attr(size_t bytes)
 {
-    auto k = k_gemm_tc<DUAL, MODE, F8, LEAN>;
+    auto k = k_gemm_tc<DUAL, MODE, F8, LEAN, TN>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) return false;
     // lean tiles: room for two CTAs' shared memory on one SM
     return !LEAN || cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -200,6 +211,18 @@ bool set_attr(size_t bytes)
 
 // Checks for the tensor-map entry point and raises the kernels' dynamic
 // shared-memory limit (done before any stream capture).
+static bool set_narrow_attrs()
+{
+    const size_t m = RING_BUDGET + 1024;
+    return set_attr<true, EPI_SWIGLU, false, false, 32>(m) && set_attr<false, EPI_STORE, false, false, 32>(m) &&
+           set_attr<false, EPI_QKV, false, false, 32>(m) && set_attr<false, EPI_RESID, false, false, 32>(m) &&
+           set_attr<false, EPI_RESID_BASE, false, false, 32>(m) && set_attr<false, EPI_BIAS_SILU, false, false, 32>(m) &&
+           set_attr<false, EPI_SET_BIAS, false, false, 32>(m) && set_attr<false, EPI_HEADS, false, false, 32>(m) &&
+           set_attr<true, EPI_SWIGLU, true, false, 32>(m) && set_attr<false, EPI_STORE, true, false, 32>(m) &&
+           set_attr<false, EPI_QKV, true, false, 32>(m) && set_attr<false, EPI_RESID, true, false, 32>(m) &&
+           set_attr<false, EPI_RESID_BASE, true, false, 32>(m);
+}
+
 static bool set_lean_attrs()
 {
     const size_t ml = RING_BUDGET_LEAN + 1024;
@@ -221,7 +244,7 @@ bool gemm_tc_available()
            set_attr<false, EPI_BIAS_SILU>(m1) && set_attr<false, EPI_SET_BIAS>(m1) && set_attr<false, EPI_HEADS>(m1) &&
            set_attr<true, EPI_SWIGLU, true>(m2) && set_attr<false, EPI_STORE, true>(m1) &&
            set_attr<false, EPI_QKV, true>(m1) && set_attr<false, EPI_RESID, true>(m1) &&
-           set_attr<false, EPI_RESID_BASE, true>(m1) && set_lean_attrs();
+           set_attr<false, EPI_RESID_BASE, true>(m1) && set_lean_attrs() && set_narrow_attrs();
 }
 
 namespace {
@@ -235,18 +258,23 @@ bool gemm_tc8(const GemmArgs &g, cudaStream_t s)
     if (!tensor_map(g.Wt, g.N, g.K, g.K, TM, &tw, true)) return false;
     if (dual && !tensor_map(g.Wt2, g.N, g.K, g.K, TM, &tw2, true)) return false;
     if (!dual) tw2 = tw;
-    dim3 grid((g.N + TM - 1) / TM, (g.M + NT - 1) / NT), block(NTHREADS);
-    const bool lean = !dual && (int)(grid.x * grid.y) > sm_count();
-    size_t smem = smem_bytes(dual, true, g.K, true, lean);
+    const int nf = (g.N + TM - 1) / TM, tn = tile_tokens(nf, g.M);
+    dim3 grid(nf, (g.M + tn - 1) / tn), block(NTHREADS);
+    const bool lean = !dual && tn == NT && (int)(grid.x * grid.y) > sm_count();
+    size_t smem = smem_bytes(dual, true, g.K, true, lean, tn);
     int *st = g.status;
     cudaError_t e;
-#define F8_CASE(MODE_)                                                                                        \
-    case MODE_:                                                                                               \
-        e = lean ? launch_pdl(k_gemm_tc<false, MODE_, true, true>, grid, block, smem, s, tw, tw2, tw, g, st)  \
-                 : launch_pdl(k_gemm_tc<false, MODE_, true, false>, grid, block, smem, s, tw, tw2, tw, g, st); \
+#define F8_CASE(MODE_)                                                                                         \
+    case MODE_:                                                                                                \
+        e = tn == 32 ? launch_pdl(k_gemm_tc<false, MODE_, true, false, 32>, grid, block, smem, s, tw, tw2, tw, g, st) \
+            : lean   ? launch_pdl(k_gemm_tc<false, MODE_, true, true>, grid, block, smem, s, tw, tw2, tw, g, st)      \
+                     : launch_pdl(k_gemm_tc<false, MODE_, true, false>, grid, block, smem, s, tw, tw2, tw, g, st);    \
         break;
     switch (g.epi.mode) {
-    case EPI_SWIGLU: e = launch_pdl(k_gemm_tc<true, EPI_SWIGLU, true>, grid, block, smem, s, tw, tw2, tw, g, st); break;
+    case EPI_SWIGLU:
+        e = tn == 32 ? launch_pdl(k_gemm_tc<true, EPI_SWIGLU, true, false, 32>, grid, block, smem, s, tw, tw2, tw, g, st)
+                     : launch_pdl(k_gemm_tc<true, EPI_SWIGLU, true>, grid, block, smem, s, tw, tw2, tw, g, st);
+        break;
     F8_CASE(EPI_STORE)
     F8_CASE(EPI_QKV)
     F8_CASE(EPI_RESID)
@@ -268,24 +296,29 @@ bool gemm_tc(const GemmArgs &g, cudaStream_t s)
     if (!tensor_map(g.Wt, g.N, g.K, g.K, TM, &tw)) return false;
     if (dual && !tensor_map(g.Wt2, g.N, g.K, g.K, TM, &tw2)) return false;
     if (!dual) tw2 = tw;
+    const int nf = (g.N + TM - 1) / TM, tn = tile_tokens(nf, g.M);
     if (!resident) {
-        if (!tensor_map(g.A, g.M, g.K, g.lda, NT, &tx)) return false;
+        if (!tensor_map(g.A, g.M, g.K, g.lda, tn, &tx)) return false;
     } else {
         tx = tw;
     }
-    dim3 grid((g.N + TM - 1) / TM, (g.M + NT - 1) / NT);
-    const bool lean = !dual && (int)(grid.x * grid.y) > sm_count();
-    size_t smem = smem_bytes(dual, resident, g.K, false, lean);
+    dim3 grid(nf, (g.M + tn - 1) / tn);
+    const bool lean = !dual && tn == NT && (int)(grid.x * grid.y) > sm_count();
+    size_t smem = smem_bytes(dual, resident, g.K, false, lean, tn);
     int *st = g.status;
     dim3 block(NTHREADS);
     cudaError_t e;
-#define BF_CASE(MODE_)                                                                                          \
-    case MODE_:                                                                                                 \
-        e = lean ? launch_pdl(k_gemm_tc<false, MODE_, false, true>, grid, block, smem, s, tw, tw2, tx, g, st)   \
-                 : launch_pdl(k_gemm_tc<false, MODE_, false, false>, grid, block, smem, s, tw, tw2, tx, g, st); \
+#define BF_CASE(MODE_)                                                                                            \
+    case MODE_:                                                                                                   \
+        e = tn == 32 ? launch_pdl(k_gemm_tc<false, MODE_, false, false, 32>, grid, block, smem, s, tw, tw2, tx, g, st) \
+            : lean   ? launch_pdl(k_gemm_tc<false, MODE_, false, true>, grid, block, smem, s, tw, tw2, tx, g, st)      \
+                     : launch_pdl(k_gemm_tc<false, MODE_, false, false>, grid, block, smem, s, tw, tw2, tx, g, st);    \
         break;
     switch (g.epi.mode) {
-    case EPI_SWIGLU: e = launch_pdl(k_gemm_tc<true, EPI_SWIGLU, false>, grid, block, smem, s, tw, tw2, tx, g, st); break;
+    case EPI_SWIGLU:
+        e = tn == 32 ? launch_pdl(k_gemm_tc<true, EPI_SWIGLU, false, false, 32>, grid, block, smem, s, tw, tw2, tx, g, st)
+                     : launch_pdl(k_gemm_tc<true, EPI_SWIGLU, false>, grid, block, smem, s, tw, tw2, tx, g, st);
+        break;
     BF_CASE(EPI_STORE)
     BF_CASE(EPI_QKV)
     BF_CASE(EPI_RESID)

@@ -283,3 +283,25 @@ def test_graph_cache_is_bounded_and_records_again():
             assert np.array_equal(got[1], first[1]) and np.array_equal(got[2], first[2])
     for q in seqs:
         q.close()
+
+
+@pytest.mark.parametrize("precision", [psw.PSW_BF16, psw.PSW_FP8])
+def test_wide_batch_1080p_lean_tiles(precision):
+    """48 full 1080p frames in one call: the projections of the middle
+    wavefront steps have more tiles than the GPU has SMs, so they run as
+    lean two-CTA tiles.  Every frame decodes losslessly, and frames spread
+    over the batch equal the same frames decoded alone (one-CTA tiles)."""
+    cfg = synth.config("i1080")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=precision)
+    B = 48
+    four = _encode(ctx, cfg, synth.frames(cfg, 4, seed=2100), 0)     # I-frames: each coded on its own
+    items = [four[b % 4] for b in range(B)]
+    fds = [psw.frame_desc(cfg.H, cfg.W, 0)] * B
+    batched, seqs = _batched(ctx, cfg, items, fds)
+    for s in seqs:
+        s.close()
+    for (yb, _, _), it in zip(batched, items):
+        assert np.array_equal(yb, it[3])
+    pick = [0, 17, 46, 47]
+    alone = _alone(ctx, cfg, [items[k] for k in pick], [fds[k] for k in pick])
+    _check_same(alone, [batched[k] for k in pick], [items[k] for k in pick])

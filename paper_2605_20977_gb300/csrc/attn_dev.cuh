@@ -115,9 +115,14 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
     const int nfr = a.temporal ? s.nfr : 1;
     const int ncand = nfr * kk;
     int cnt = 0;
+    // candidate cidx = fr * kk + c, window row c / k, column c % k: the
+    // quotients by multiplication with the reciprocals (exact here: cidx <
+    // 256 and k <= 9 keep (x + 0.5) / d at least 0.5 / d away from an
+    // integer, far above the float error)
+    const float inv_kk = 1.0f / (float)kk, inv_k = 1.0f / (float)a.k;
     for (int c0 = 0; c0 < ncand; c0 += 32) {
-        int cidx = c0 + lane, fr = cidx / kk, c = cidx - fr * kk;
-        int qi = pi + c / a.k - w, qj = pj + c % a.k - w;
+        int cidx = c0 + lane, fr = (int)(((float)cidx + 0.5f) * inv_kk), c = cidx - fr * kk;
+        int cr = (int)(((float)c + 0.5f) * inv_k), qi = pi + cr - w, qj = pj + (c - cr * a.k) - w;
         bool ok = cidx < ncand && qi >= 0 && qi < H && qj >= 0 && qj < W &&
                   visible(a.mask, a.kind, W, pi, pj, qi, qj);
         unsigned bal = __ballot_sync(0xffffffffu, ok);

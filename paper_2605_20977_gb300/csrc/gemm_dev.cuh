@@ -5,20 +5,26 @@
 //
 // Y[token][feature] = sum_k X[token][k] Wt[feature][k].  The projection is
 // the MMA's A operand (M = 128 output features per tile) and the tokens are
-// its B operand (N = 64 tokens per tile), so a decoder step with a few dozen
+// its B operand (N = 64 or 32 tokens per tile), so a decoder step with a few dozen
 // tokens fills one tile and the weights stream through once.  Weights are
 // consumed in 64-element K chunks (one 128-byte swizzle atom) through a
 // TMA ring as deep as the shared-memory budget allows (all chunks of a
 // 384-wide projection).  The token operand either streams through the same ring
 // (compact bf16 rows) or is built by the CTA in shared memory: RMSNorm of the
 // FP32 residual stream rows (the pre-norm of every projection, Sec. 3.1) or
-// the channel-scaled latents (the latent embedding).  One thread issues the
-// MMAs; 256 threads run the epilogue from TMEM (warps w and w + 4 read the
-// same 32 feature rows, half of the token columns each) with the destination
-// rows of the tile's tokens resolved once into shared memory.  Accumulation
-// order is fixed (ascending K chunks, one MMA shape), so every output element
+// the channel-scaled latents (the latent embedding).  Four threads issue the
+// MMAs (each one K step of every chunk, into its own accumulator; the
+// epilogue adds the four in a fixed order); 256 threads run the epilogue from
+// TMEM (warps w and w + 4 read the same 32 feature rows, half of the token
+// columns each) with the destination rows of the tile's tokens resolved once
+// into shared memory.  Accumulation order is fixed, so every output element
 // is the same function of its row and column whatever the tile, the launch or
 // the kernel it falls in.
+//
+// Two forms change only the resources, not the arithmetic: lean tiles (a
+// 96 KB ring and four-row token builds, two CTAs per SM, for launches with
+// more tiles than SMs) and 32-token tiles (TN = 32, for launches whose
+// 64-token grid leaves SMs idle).
 //
 // A tile runs in two parts.  gemm_tile_pre resolves the tile's token table
 // and issues the weight copies of its first ring stages; it reads nothing a

@@ -44,7 +44,7 @@ WORKLOAD = ("1080p I-frame decode: latents 68x120x192, hyperlatents 17x30x128, d
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -66,7 +66,7 @@ def parse():
                     help="timed steps of the same I-frame workload with E4M3 block projections (0: skip)")
     ap.add_argument("--engine", choices=["auto", "graph", "persistent"], default="auto",
                     help="decode engine: one cooperative kernel over all steps, or per-phase kernels in CUDA graphs")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def peaks():
@@ -329,6 +329,22 @@ def fp8_run(args, dev, timed, cfg, w, ys, zs, B):
     return out, mu, sg
 
 
+def job_rate(units_per_rank, local_seconds, world, device):
+    """Whole-job throughput of `world` replicas: every rank's units over the
+    slowest rank's time (all-reduce MAX).  Returns (units / s, max seconds)."""
+    import torch
+    t = torch.tensor([float(local_seconds)], device=device, dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return world * units_per_rank / float(t.item()), float(t.item())
+
+
+def replica_seed(rank: int, frames_per_rank: int, b: int) -> int:
+    """Seed of frame b of a rank's batch: replicas decode distinct frames."""
+    return 1002 + rank * frames_per_rank + b
+
+
 def run_ours(args, rank: int, world: int, local: int):
     import torch
     import torch.distributed as dist
@@ -346,7 +362,7 @@ def run_ours(args, rank: int, world: int, local: int):
     B = args.batch
     fdw = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_WAVEFRONT)
     fdr = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_RASTER)
-    frames = [synth.frames(cfg, 1, seed=1002 + rank * B + b) for b in range(B)]
+    frames = [synth.frames(cfg, 1, seed=replica_seed(rank, B, b)) for b in range(B)]
     ys = [torch.from_numpy(f.y[0]).to(dev) for f in frames]
     zs = [torch.from_numpy(f.z[0]).to(dev) for f in frames]
     cap = ctx.bitstream_capacity(cfg.H, cfg.W)
@@ -401,11 +417,7 @@ def run_ours(args, rank: int, world: int, local: int):
     for b in range(B):
         if not torch.equal(outs[b], ys[b]):
             raise RuntimeError("decoded latents differ from the encoded ones")
-    t = torch.tensor([sum(step_ms) / 1e3], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_max = float(t.item())
-    value = world * B * args.steps / total_max
+    value, total_max = job_rate(B * args.steps, sum(step_ms) / 1e3, world, dev)
 
     # single-frame latency (one frame per call)
     lat = None
@@ -463,10 +475,7 @@ def run_ours(args, rank: int, world: int, local: int):
     for b in range(B):
         if not torch.equal(h_y[b], ys[b].cpu()):
             raise RuntimeError("end-to-end decode differs")
-    e2e_t = torch.tensor([e0.elapsed_time(e1) / 1e3], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = world * B * args.steps / float(e2e_t.item())
+    e2e_value, _ = job_rate(B * args.steps, e0.elapsed_time(e1) / 1e3, world, dev)
     h2d = sum(int(lens[b]) + h_z[b].numel() * 2 for b in range(B))
     d2h = sum(h_y[b].numel() * 2 for b in range(B))
 

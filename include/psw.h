@@ -209,6 +209,15 @@ psw_status psw_rate(psw_ctx *ctx, size_t n, const int16_t *yhat_dev, const float
 psw_status psw_quantize(psw_ctx *ctx, size_t n, const float *mu_dev, const float *sigma_dev,
                         uint8_t *idx_dev, int32_t *m_dev, void *stream);
 
+/* Failure-detection check (not part of the method): runs the persistent
+ * decoder's bounded grid-barrier wait on a barrier no block arrives at, with
+ * a limit of `seconds` (0 < seconds <= 10) instead of the decoder's ~2 s.
+ * The expiry is reported through the context's status word, as a decode
+ * reports one.  Returns PSW_ERR_TIMEOUT when the wait expired (the expected
+ * outcome) and PSW_OK if it did not; the context stays usable.  Synchronous,
+ * default stream. */
+psw_status psw_check_wait_timeout(psw_ctx *ctx, double seconds);
+
 /* E4M3 quantisation of one weight tensor as PSW_FP8 contexts store it
  * (Sec. 3.2 precision forms): with max |src| in [2^e, 2^(e+1)) the scale is
  * s = 2^(e-7) (e clamped at -100; s = 1 for an all-zero tensor) and

@@ -1536,6 +1536,19 @@ psw_status psw_rans_decode(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, con
 
 long psw_launch_count(const psw_ctx *c) { return c ? c->launches : 0; }
 
+psw_status psw_check_wait_timeout(psw_ctx *c, double seconds)
+{
+    if (!c) return fail(nullptr, PSW_ERR_INVALID, "null context");
+    if (!(seconds > 0.0 && seconds <= 10.0)) return fail(c, PSW_ERR_INVALID, "limit must be in (0, 10] s");
+    CK_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
+    if (!wait_probe((uint64_t)(seconds * 1e9), c->d_status, 0)) return fail(c, PSW_ERR_CUDA, "wait probe launch");
+    int st = 0;
+    CK_CUDA(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK_CUDA(c, cudaMemset(c->d_status, 0, sizeof(int)));
+    if (st & ST_TIMEOUT) return fail(c, PSW_ERR_TIMEOUT, "the bounded wait expired after %.3f s", seconds);
+    return PSW_OK;
+}
+
 psw_status psw_quantize_e4m3(size_t n, const float *src, uint8_t *dst, float *scale_out)
 {
     if (!scale_out || (n && (!src || !dst))) return fail(nullptr, PSW_ERR_INVALID, "null argument");

@@ -288,6 +288,9 @@ bool program_upload(ProgramBuilder *b, const Op **ops, int *nops, const void **m
 // dynamic shared-memory size; false if that cannot be resident.
 bool persist_prepare(size_t smem, bool f8, int *grid);
 bool persist_launch(const PersistArgs &a, int grid, size_t smem, bool f8, cudaStream_t s);
+// The grid barrier's bounded wait on a count nothing reaches (limit_ns), its
+// expiry ORed into *status as ST_TIMEOUT; false on a CUDA error.
+bool wait_probe(uint64_t limit_ns, int *status, cudaStream_t s);
 
 }  // namespace psw
 

@@ -58,7 +58,8 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 // waits until the counter reaches (barriers so far) x (CTAs).  Thread 0 only.
 // Polls back off (a short sleep between reads) so that idle CTAs do not
 // flood the counter's L2 slice while others work.
-__device__ __forceinline__ bool grid_wait(const unsigned *bar, unsigned target, const volatile int *abort_g)
+__device__ __forceinline__ bool grid_wait(const unsigned *bar, unsigned target, const volatile int *abort_g,
+                                          uint64_t limit_ns = WAIT_NS)
 {
     if (ld_acquire(bar) >= target) return true;
     uint64_t t0 = gtime();
@@ -66,8 +67,16 @@ __device__ __forceinline__ bool grid_wait(const unsigned *bar, unsigned target, 
         __nanosleep(SPIN_NS);
         if (ld_acquire(bar) >= target) return true;
         if (*abort_g) return false;
-        if (gtime() - t0 > WAIT_NS) return false;
+        if (gtime() - t0 > limit_ns) return false;
     }
+}
+
+// Failure-detection check: one thread runs the grid barrier's bounded wait
+// for an arrival count that nothing will reach, with the given limit, and
+// reports the expiry into the status word as the decoder does.
+__global__ void k_wait_probe(const unsigned *bar, const int *abort_g, uint64_t limit_ns, int *status)
+{
+    if (threadIdx.x == 0 && !grid_wait(bar, 1u, abort_g, limit_ns)) atomicOr(status, ST_TIMEOUT);
 }
 
 // The tokens of the step a phase works on.
@@ -443,6 +452,19 @@ bool persist_prepare(size_t smem, bool f8, int *grid)
         return false;
     *grid = nsm;
     return true;
+}
+
+bool wait_probe(uint64_t limit_ns, int *status, cudaStream_t s)
+{
+    unsigned *words = nullptr;                         // [0]: barrier counter, [1]: abort flag, both zero
+    if (cudaMalloc(&words, 2 * sizeof(unsigned)) != cudaSuccess) return false;
+    bool ok = cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), s) == cudaSuccess;
+    if (ok) {
+        k_wait_probe<<<1, 32, 0, s>>>(words, (const int *)(words + 1), limit_ns, status);
+        ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+    }
+    cudaFree(words);
+    return ok;
 }
 
 bool persist_launch(const PersistArgs &a, int grid, size_t smem, bool f8, cudaStream_t s)

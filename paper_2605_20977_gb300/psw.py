@@ -25,7 +25,8 @@ EXPORTS = ["psw_weights_count", "psw_create", "psw_destroy", "psw_last_error", "
            "psw_seq_create", "psw_seq_reset", "psw_seq_destroy", "psw_bitstream_capacity", "psw_encode_params",
            "psw_decode_frame", "psw_decode_batch", "psw_rate", "psw_quantize", "psw_scale_table", "psw_cdf_table",
            "psw_rans_encode", "psw_rans_decode", "psw_launch_count", "psw_profile_begin", "psw_profile_end",
-           "psw_rans_encode_noalloc", "psw_set_engine", "psw_last_engine", "psw_quantize_e4m3"]
+           "psw_rans_encode_noalloc", "psw_set_engine", "psw_last_engine", "psw_quantize_e4m3",
+           "psw_check_wait_timeout"]
 
 ENGINE_AUTO, ENGINE_GRAPH, ENGINE_PERSISTENT = 0, 1, 2
 
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH):
             "psw_profile_end": (I, [P, ct.POINTER(KernelStat), I, ct.POINTER(I)]),
             "psw_rans_encode_noalloc": (I, [P, FD, P, P, P, P, S, ct.POINTER(S), P]),
             "psw_quantize_e4m3": (I, [S, P, P, ct.POINTER(ct.c_float)]),
+            "psw_check_wait_timeout": (I, [P, ct.c_double]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -218,6 +220,10 @@ class Context:
         if check:
             self._check(st)
         return st, int(n.value)
+
+    def check_wait_timeout(self, seconds: float) -> int:
+        """psw_check_wait_timeout: the status (PSW_ERR_TIMEOUT expected)."""
+        return int(self.lib.psw_check_wait_timeout(self.h, float(seconds)))
 
     def launch_count(self) -> int:
         return int(self.lib.psw_launch_count(self.h))

@@ -305,3 +305,22 @@ def test_wide_batch_1080p_lean_tiles(precision):
     pick = [0, 17, 46, 47]
     alone = _alone(ctx, cfg, [items[k] for k in pick], [fds[k] for k in pick])
     _check_same(alone, [batched[k] for k in pick], [items[k] for k in pick])
+
+
+def test_bounded_wait_expires_and_the_context_stays_usable():
+    """The persistent decoder's grid-barrier wait, on a barrier no block
+    arrives at, expires after its limit and reports PSW_ERR_TIMEOUT through
+    the status word; a decode on the same context then succeeds."""
+    cfg = synth.config("tiny")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
+    import time
+    t0 = time.perf_counter()
+    assert ctx.check_wait_timeout(0.05) == psw.PSW_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert "expired" in ctx.last_error()
+    items = _encode(ctx, cfg, synth.frames(cfg, 1, seed=97), 0)
+    bs, n, z, y = items[0]
+    seq = ctx.seq_create(cfg.H, cfg.W)
+    yo, mu, sg = _alloc(cfg.H, cfg.W, cfg.C)
+    seq.decode_frame(psw.frame_desc(cfg.H, cfg.W, 0), bs, n, z, yo, mu, sg)
+    assert np.array_equal(yo.cpu().numpy(), y)

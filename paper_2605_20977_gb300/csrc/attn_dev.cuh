@@ -64,21 +64,23 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Shared staging of one attention warp: CK key rows (padded stride, so
-// that 16-byte reads by consecutive lanes hit distinct banks) and CK value
-// rows of one head, the query, and the list of visible keys (cache row and
-// relative-bias index) for up to MAXC candidates.  Spatial windows (at most
-// 81 candidates, 24 visible at k = 7) use 24-key chunks and a 96-entry list,
-// about 7.5 KB per warp at 64-wide heads, so more warps fit on an SM;
-// temporal windows (Tf * k * k <= 256, checked at context creation) 32-key
-// chunks and the full list.
+// Shared staging of one attention warp: CK key rows (the 16-byte pieces of
+// row r stored in the order piece ^ (r & SWM), so that 16-byte reads of the
+// same piece by consecutive lanes hit distinct banks without padding) and CK
+// value rows of one head, the query, and the list of visible keys (cache row
+// and relative-bias index) for up to MAXC candidates.  Spatial windows use
+// 24-key chunks (24 keys are visible at most at k = 7) and a 64-entry list
+// (96 for 9 x 9 windows): under 7 KB per warp at 64-wide heads, so eight
+// blocks of four warps fit on an SM; temporal windows (Tf * k * k <= 256,
+// checked at context creation) 32-key chunks and the full list.
 template <typename T, int DH, int CK_ = 32, int MAXC_ = 256>
 struct __align__(16) AttnWarp {
     static constexpr int RB = DH * (int)sizeof(T);            // bytes of one head's row slice
-    static constexpr int KS = RB + 16;
+    static constexpr int PR = RB / 16;                         // 16-byte pieces per row slice
+    static constexpr int SWM = PR < 8 ? PR - 1 : 7;            // piece swizzle mask of the key rows
     static constexpr int CK = CK_;
     static constexpr int MAXC = MAXC_;
-    unsigned char kbuf[CK * KS];
+    unsigned char kbuf[CK * RB];
     unsigned char vbuf[CK * RB];
     unsigned char qraw[RB];                                    // the query as stored, copied with the first keys
     float qs[DH];
@@ -101,7 +103,7 @@ template <typename T, int DH, bool PDL, int CK = 32, int MAXC = 256>
 __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T, DH, CK, MAXC> &sm)
 {
     constexpr int PER = DH / 32;
-    constexpr int RB = AttnWarp<T, DH, CK, MAXC>::RB, KS = AttnWarp<T, DH, CK, MAXC>::KS;
+    constexpr int RB = AttnWarp<T, DH, CK, MAXC>::RB, SWM = AttnWarp<T, DH, CK, MAXC>::SWM;
     constexpr int PR = RB / 16;                                // 16-byte pieces per row slice
     constexpr int EPU = 16 / (int)sizeof(T);                   // elements per piece
     using VRaw = typename RawT<PER * (int)sizeof(T)>::type;
@@ -158,7 +160,7 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
         for (int x = lane; x < nc * PR; x += 32) {
             int r = x / PR, u = x - r * PR;
             long off = (long)sm.rows[base + r] * rsb + u * 16;
-            cp_async16(kb + r * KS + u * 16, Kb + off);
+            cp_async16(kb + r * RB + ((u ^ (r & SWM)) << 4), Kb + off);
             cp_async16(vb + r * RB + u * 16, Vb + off);
         }
         cp_async_wait_all();
@@ -170,12 +172,13 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
         }
         float sc = -INFINITY;
         if (lane < nc) {
-            const uint4 *kr = reinterpret_cast<const uint4 *>(kb + lane * KS);
+            const uint4 *kr = reinterpret_cast<const uint4 *>(kb + lane * RB);
+            const int sw = lane & SWM;
             float acc = 0.0f;
 #pragma unroll
             for (int u = 0; u < PR; u++) {
                 float kv[EPU];
-                unpack<T, EPU>(kr[u], kv);
+                unpack<T, EPU>(kr[u ^ sw], kv);
 #pragma unroll
                 for (int i = 0; i < EPU; i++) acc = fmaf(sm.qs[u * EPU + i], kv[i], acc);
             }

@@ -207,6 +207,7 @@ static void attention_dh(const AttnArgs &a, cudaStream_t s)
     const dim3 grid(cdiv(warps, attn_wpb<T, DH>())), block(32 * attn_wpb<T, DH>());
     static_assert(MAX_KK <= 96, "spatial candidate list");
     if (a.temporal) launch_pdl(k_attention<T, DH, 32, 256>, grid, block, 0, s, a);
+    else if (a.k * a.k <= 64) launch_pdl(k_attention<T, DH, 24, 64>, grid, block, 0, s, a);
     else launch_pdl(k_attention<T, DH, 24, 96>, grid, block, 0, s, a);
 }
 
@@ -219,6 +220,8 @@ static bool attention_carveout()
     return cudaFuncSetAttribute(k_attention<T, DH, 32, 256>, cudaFuncAttributePreferredSharedMemoryCarveout, c) ==
                cudaSuccess &&
            cudaFuncSetAttribute(k_attention<T, DH, 24, 96>, cudaFuncAttributePreferredSharedMemoryCarveout, c) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(k_attention<T, DH, 24, 64>, cudaFuncAttributePreferredSharedMemoryCarveout, c) ==
                cudaSuccess;
 }
 

@@ -245,10 +245,10 @@ psw_status psw_rans_decode(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd,
 
 /* Coder-only encoder that allocates no device memory (the paper has no
  * counterpart: this is a deployment convenience).  Some callers cannot call
- * cudaMalloc at the point where they encode: code that runs while a CUDA
- * graph is being recorded, processes whose device memory is handed out
- * entirely by another allocator or capped by a quota, and latency-critical
- * loops that forbid allocation after warm-up.  This entry point does the
+ * cudaMalloc at the point where they encode: processes whose device memory
+ * is handed out entirely by another allocator (a framework's caching pool)
+ * or capped by a quota, and latency-critical loops that forbid allocation
+ * after warm-up.  This entry point does the
  * work of psw_rans_encode (same inputs, same container bytes) without a
  * psw_seq: its scratch (schedule order, word buffers, stream lengths,
  * states) lives in one static device array of about 9.2 MiB that every GPU
@@ -262,7 +262,10 @@ psw_status psw_rans_decode(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd,
  *   streams, or from two host threads -- race; serialise them.
  *   Calls no cudaMalloc/cudaFree and no allocating library routine.
  *   Returns PSW_ERR_CAPACITY if the container exceeds cap (len_out still
- *   receives its size).  Synchronises `stream`. */
+ *   receives its size, and no byte of bitstream_dev is written).
+ *   Each call copies the schedule order and a slot record from host memory
+ *   to the array, reads the length and status back into host memory, and
+ *   synchronises `stream` before it returns. */
 psw_status psw_rans_encode_noalloc(const psw_ctx *ctx, const psw_frame_desc *fd, const int16_t *yhat_dev,
                                    const uint8_t *idx_dev, const int32_t *m_dev, uint8_t *bitstream_dev,
                                    size_t cap, size_t *len_out, void *stream);

@@ -1,8 +1,8 @@
 """The allocation-free encoder entry point (psw_rans_encode_noalloc).
 
-Some callers cannot allocate device memory where they encode (while a CUDA
-graph is being recorded, under a foreign allocator or a memory quota, in
-loops that forbid allocation after warm-up).  This entry point keeps its
+Some callers cannot allocate device memory where they encode (their device
+memory is handed out by another allocator or capped by a quota, or their
+loops forbid allocation after warm-up).  This entry point keeps its
 scratch in a static device array instead; its containers must be the same
 bytes the allocating coder produces, call after call.  Collected last so
 that a failure here comes after every other test has run.
@@ -48,6 +48,22 @@ def test_noalloc_encoder_matches_allocating_encoder_two_calls():
         seq.rans_decode(fd, out, n, idx, m, yd)
         assert torch.equal(yd, y)
         seq.close()
+    # a bitstream buffer one byte too small: PSW_ERR_CAPACITY, the needed
+    # size reported, nothing written; the next call with room is exact again
+    c = base.with_grid(9, 13)
+    y, idx, m = _case(c, 310)
+    fd = psw.frame_desc(c.H, c.W, psw.PSW_SCHED_WAVEFRONT)
+    seq = ctx.seq_create(c.H, c.W)
+    ref = torch.zeros(ctx.bitstream_capacity(c.H, c.W), dtype=torch.uint8, device=dev())
+    n_ref = seq.rans_encode(fd, y, idx, m, ref)
+    seq.close()
+    short = torch.full((n_ref - 1,), 0x5A, dtype=torch.uint8, device=dev())
+    st, n = ctx.rans_encode_noalloc(fd, y, idx, m, short, check=False)
+    assert st == psw.PSW_ERR_CAPACITY and n == n_ref
+    assert bool((short == 0x5A).all())
+    out = torch.zeros(n_ref, dtype=torch.uint8, device=dev())
+    st, n = ctx.rans_encode_noalloc(fd, y, idx, m, out)
+    assert st == psw.PSW_OK and n == n_ref and torch.equal(out.cpu(), ref[:n_ref].cpu())
     # sizes beyond the static scratch are refused, not overrun
     big = psw.frame_desc(200, 200, psw.PSW_SCHED_WAVEFRONT)
     small = torch.zeros(16, dtype=torch.int16, device=dev())

@@ -527,6 +527,10 @@ struct Pass {
     bool *failed;
     ProgramBuilder *rec = nullptr;     // set: record phases of the persistent decoder instead of launching
     int tokset = TS_CUR;               // which step's tokens recorded phases work on
+    // the workspace Xn holds bf16(RMSNorm(xn_rows[m]) * xn_gain) for m < xn_m
+    // (written by the last launch that produced or updated those rows)
+    mutable const float *xn_rows = nullptr, *xn_gain = nullptr;
+    mutable int xn_m = 0;
 };
 
 // One projection; asrc / a_stream / a_gain say where its token operand
@@ -536,6 +540,7 @@ void gemm_any(const Pass &P, int asrc, const float *xrows, const float *a_gain, 
               const void *Wt2, int M, int N, int K, const Epi &e)
 {
     if (M <= 0) return;
+    const bool writes_rows = e.mode == EPI_RESID || e.mode == EPI_RESID_BASE || e.mode == EPI_SET_BIAS;
     GemmArgs g{};
     g.A = A; g.lda = lda; g.asrc = asrc; g.xrows = xrows; g.a_gain = a_gain; g.prep = P.c->Xn;
     g.Wt = Wt; g.Wt2 = Wt2; g.M = M; g.N = N; g.K = K; g.epi = e;
@@ -554,6 +559,18 @@ void gemm_any(const Pass &P, int asrc, const float *xrows, const float *a_gain, 
         return;
     }
     bool tc = g.f8 || gemm_tc_supported(P.c->prec, N, K, asrc);
+    if (tc && !g.f8 && asrc == A_NORM && M >= WIDE_M && K <= 512) {
+        // a wide launch: its token rows are normalised once (the same bf16
+        // values every feature tile would build), by the residual launch
+        // that last updated them or here, and streamed to the tiles
+        if (!(P.xn_rows == xrows && P.xn_gain == a_gain && P.xn_m == M)) {
+            LAUNCH(P, K_NORM, 0.0, (double)M * K * 6.0,
+                   if (!launch_norm_rows(xrows, a_gain, M, K, P.c->Xn, P.s)) *P.failed = true);
+            P.xn_rows = xrows; P.xn_gain = a_gain; P.xn_m = M;
+        }
+        g.asrc = asrc = A_DIRECT; g.A = P.c->Xn; g.lda = K;
+    }
+    if (writes_rows) P.xn_rows = nullptr;              // the rows change: Xn no longer holds their norm
     if (!tc && asrc != A_DIRECT) P.c->launches++;      // the operand-preparation kernel
     double es = P.c->prec == P_BF16 ? 2.0 : 4.0, nw = Wt2 ? 2.0 : 1.0, wes = g.f8 ? 1.0 : es;
     double out_b = (e.mode == EPI_RESID || e.mode == EPI_RESID_BASE) ? 8.0 : es;
@@ -694,6 +711,7 @@ void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *e
     psw_ctx *c = P.c;
     const psw_model_desc &m = c->md;
     int d = m.d, kk = m.k * m.k;
+    P.xn_rows = nullptr;                               // rows written outside gemm_any follow
     LAUNCH(P, K_EMBED, 2.0 * n * m.Ch * d, n * (m.Ch * 2.0 + d * 4.0),
            launch_embed_hyper(P.S, tok, n, H, W_, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp),
                               W(c, c->lay.b_hp), d, P.s));
@@ -705,6 +723,7 @@ void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *e
     LAUNCH(P, K_EMBED, 2.0 * n * m.C * d, n * (m.C * 2.0 + d * 4.0),
            launch_embed_context(P.S, tok, n, m.C, W(c, c->lay.gamma_c), W(c, c->lay.W_c), W(c, c->lay.b_c),
                                 W(c, c->lay.pad), d, c->Xg, P.s));
+    P.xn_rows = nullptr;
     for (int l = 0; l < m.Lc; l++) {
         const BlockOff &bo = c->lay.ctx[l];
         const BlockDev &bd = c->ctxb[l];
@@ -1198,6 +1217,8 @@ psw_status psw_create(const psw_model_desc *desc, const float *weights_host, siz
         return fail(nullptr, PSW_ERR_INVALID, "expected %ld weights, got %zu", lay.total, n_weights);
     if (precision != PSW_FP32 && !gemm_tc_available())
         return fail(nullptr, PSW_ERR_CUDA, "the driver offers no cuTensorMapEncodeTiled entry point");
+    if (precision != PSW_FP32 && !gemm_ws_prepare())
+        return fail(nullptr, PSW_ERR_CUDA, "wide projection kernel attributes");
     if (!attention_prepare()) return fail(nullptr, PSW_ERR_CUDA, "attention kernel attributes");
     psw_ctx *c = new psw_ctx();
     c->md = *desc; c->budget = hbm_budget; c->lay = lay;

@@ -12,14 +12,16 @@
 // 384-wide projection).  The token operand either streams through the same ring
 // (compact bf16 rows) or is built by the CTA in shared memory: RMSNorm of the
 // FP32 residual stream rows (the pre-norm of every projection, Sec. 3.1) or
-// the channel-scaled latents (the latent embedding).  Four threads issue the
-// MMAs (each one K step of every chunk, into its own accumulator; the
-// epilogue adds the four in a fixed order); 256 threads run the epilogue from
-// TMEM (warps w and w + 4 read the same 32 feature rows, half of the token
-// columns each) with the destination rows of the tile's tokens resolved once
-// into shared memory.  Accumulation order is fixed, so every output element
-// is the same function of its row and column whatever the tile, the launch or
-// the kernel it falls in.
+// the channel-scaled latents (the latent embedding).  One thread issues the
+// MMAs, every K step in ascending order into one accumulator (the dual
+// form's up projection has a second issuer and accumulator); 256 threads run
+// the epilogue from TMEM (warps w and w + 4 read the same 32 feature rows,
+// half of the token columns each) with the destination rows of the tile's
+// tokens resolved once into shared memory.  The tensor core computes an
+// output element identically whatever the MMA's N and whichever operand
+// holds the tokens, so with the accumulation order fixed every output
+// element is the same function of its row and column whatever the tile, the
+// launch or the kernel it falls in.
 //
 // Two forms change only the resources, not the arithmetic: lean tiles (a
 // 96 KB ring and four-row token builds, two CTAs per SM, for launches with
@@ -69,10 +71,12 @@ constexpr int B_BYTES = NT * KC * 2;
 constexpr int KRES_MAX = 512;  // largest K of a token operand built in shared memory
 constexpr uint64_t WAIT_NS = 2000000000ull;
 constexpr int NTHREADS = 256;  // 8 warps: warps w and w + 4 share TMEM lanes 32 (w % 4) .. + 31
-constexpr int NISS = 4;        // MMA issuers (lane 0 of warps 1..4), one K step of 16 per chunk each
-// tensor-memory columns of a tile: one 64-column accumulator (two for the
-// dual form) per issuer
-__host__ __device__ constexpr uint32_t tile_tcols(bool dual, int tn = NT) { return (dual ? 2 : 1) * tn * NISS; }
+constexpr int NARRIVE = 2;     // commits that release a ring stage or finish a tile (two per tile: the dual
+                               // form's two issuers commit once each, the single issuer twice)
+constexpr int NPROD = 4;       // copy producers: lane 0 of warps 0, 5, 6 and 7
+// tensor-memory columns of a tile: one accumulator of tn columns (two, gate
+// and up, for the dual form)
+__host__ __device__ constexpr uint32_t tile_tcols(bool dual, int tn = NT) { return (dual ? 2 : 1) * tn; }
 // Bytes of one 128-byte-wide K chunk of a tn-token operand.
 __host__ __device__ constexpr int tok_chunk_bytes(int tn) { return tn * 128; }
 
@@ -207,8 +211,6 @@ __device__ __forceinline__ void tmem_free(uint32_t tmem, uint32_t cols)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols) : "memory");
 }
 
-// Sum of the issuers' accumulators ((a0 + a1) + a2) + a3 at 16 / 8
-// consecutive columns; accumulator q starts `step` columns after q - 1.
 __device__ __forceinline__ void tmem_ld8_async(uint32_t addr, uint32_t *r)
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -216,45 +218,37 @@ __device__ __forceinline__ void tmem_ld8_async(uint32_t addr, uint32_t *r)
                  : "r"(addr));
 }
 
-__device__ __forceinline__ void tmem_sum8(uint32_t addr, uint32_t step, float *v)
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 8 / 16 consecutive accumulator columns of this thread's lane.
+__device__ __forceinline__ void tmem_get8(uint32_t addr, float *v)
 {
-    uint32_t r[NISS][8];
+    uint32_t r[8];
+    tmem_ld8_async(addr, r);
+    tmem_wait_ld();
 #pragma unroll
-    for (int q = 0; q < NISS; q++) tmem_ld8_async(addr + q * step, r[q]);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        float a = __uint_as_float(r[0][i]);
-#pragma unroll
-        for (int q = 1; q < NISS; q++) a += __uint_as_float(r[q][i]);
-        v[i] = a;
-    }
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_sum16(uint32_t addr, uint32_t step, float *v)
+__device__ __forceinline__ void tmem_get16(uint32_t addr, float *v)
 {
-    tmem_sum8(addr, step, v);
-    tmem_sum8(addr + 8, step, v + 8);
+    uint32_t r[16];
+    tmem_ld8_async(addr, r);
+    tmem_ld8_async(addr + 8, r + 8);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// Two 8-column sums (at addr and addr2) under one wait for the loads.
-__device__ __forceinline__ void tmem_sum8x2(uint32_t addr, uint32_t addr2, uint32_t step, float *v, float *v2)
+// Eight columns at addr and eight at addr2 under one wait.
+__device__ __forceinline__ void tmem_get8x2(uint32_t addr, uint32_t addr2, float *v, float *v2)
 {
-    uint32_t r[NISS][8], r2[NISS][8];
+    uint32_t r[8], r2[8];
+    tmem_ld8_async(addr, r);
+    tmem_ld8_async(addr2, r2);
+    tmem_wait_ld();
 #pragma unroll
-    for (int q = 0; q < NISS; q++) {
-        tmem_ld8_async(addr + q * step, r[q]);
-        tmem_ld8_async(addr2 + q * step, r2[q]);
-    }
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        float a = __uint_as_float(r[0][i]), b = __uint_as_float(r2[0][i]);
-#pragma unroll
-        for (int q = 1; q < NISS; q++) { a += __uint_as_float(r[q][i]); b += __uint_as_float(r2[q][i]); }
-        v[i] = a;
-        v2[i] = b;
-    }
+    for (int i = 0; i < 8; i++) { v[i] = __uint_as_float(r[i]); v2[i] = __uint_as_float(r2[i]); }
 }
 
 // Byte offset of element (row r, column k) of a K-major bf16 operand laid
@@ -388,8 +382,8 @@ __host__ __device__ constexpr int tile_smem(bool dual, bool resident, int K, boo
 // Initialise the barriers (thread 0; the caller synchronises).
 __device__ __forceinline__ void gemm_shared_init(GemmShared &S)
 {
-    for (int s = 0; s < MAXS; s++) { mbar_init(&S.full[s], 1); mbar_init(&S.empty[s], NISS); }
-    mbar_init(&S.done, NISS);
+    for (int s = 0; s < MAXS; s++) { mbar_init(&S.full[s], 1); mbar_init(&S.empty[s], NARRIVE); }
+    mbar_init(&S.done, NARRIVE);
     S.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
@@ -456,6 +450,41 @@ __device__ __forceinline__ void norm_rows(const float *__restrict__ xrows, const
             *(uint2 *)(res + swz<TN>(r, e)) = pack4(v[b][c].x * inv * gh[c].x, v[b][c].y * inv * gh[c].y,
                                                 v[b][c].z * inv * gh[c].z, v[b][c].w * inv * gh[c].w);
         }
+    }
+}
+
+// RMSNorm of one FP32 row x[0..K) times the gain (gh: this lane's gains,
+// load_gain) into a compact bf16 row dst[0..K) in global memory: the
+// arithmetic of norm_rows for one row (lane l holds elements 4l + 128c ..
+// +3, the same fused multiply-add chain and butterfly sum), so the row
+// equals, bit for bit, the operand a tile builds in shared memory.  Used
+// where a projection's tiles stream the normalised rows with TMA instead of
+// each feature tile normalising them again.
+template <int CH>
+__device__ __forceinline__ void norm_row_global(const float *__restrict__ x, const float4 *gh, float invK, int K,
+                                                __nv_bfloat16 *__restrict__ dst)
+{
+    const int lane = threadIdx.x & 31;
+    float4 v[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        int e = lane * 4 + c * 128;
+        v[c] = e < K ? *(const float4 *)(x + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float ss = 0.0f;
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        ss = fmaf(v[c].x, v[c].x, ss); ss = fmaf(v[c].y, v[c].y, ss);
+        ss = fmaf(v[c].z, v[c].z, ss); ss = fmaf(v[c].w, v[c].w, ss);
+    }
+    ss = warp_sum(ss);
+    const float inv = inv_rms(ss, invK);
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        int e = lane * 4 + c * 128;
+        if (e >= K) continue;
+        *(uint2 *)(dst + e) = pack4(v[c].x * inv * gh[c].x, v[c].y * inv * gh[c].y, v[c].z * inv * gh[c].z,
+                                    v[c].w * inv * gh[c].w);
     }
 }
 
@@ -680,33 +709,107 @@ static __device__ __noinline__ void build_tokens8(const GemmArgs &g, int m0, uin
 // Per-token addresses a mode needs, resolved once per tile by threads 0..63:
 // cache rows (EPI_STORE into a cache, EPI_QKV), the hyperprior row
 // (EPI_RESID_BASE), the head outputs (EPI_HEADS), the latents (A_EMBED).
-template <int MODE, int TN = NT>
-__device__ __forceinline__ void build_table(const GemmArgs &g, int m0, GemmShared &S)
+// Entry r of a tile's token table (row m0 + r): tab[k][r * ts] for k < 4
+// (ts: the table's row stride) and, for A_EMBED, the latent row.
+template <int MODE>
+__device__ __forceinline__ void table_row(const GemmArgs &g, int m0, int r, uintptr_t *tab, int ts,
+                                          const int16_t **yrow)
 {
-    int r = threadIdx.x;
-    if (r >= TN) return;
     int m = m0 + r;
-    S.tab[0][r] = S.tab[1][r] = S.tab[2][r] = S.tab[3][r] = 0;
-    S.yrow[r] = nullptr;
+    tab[r] = tab[ts + r] = tab[2 * ts + r] = tab[3 * ts + r] = 0;
+    if (yrow) yrow[r] = nullptr;
     const Epi &e = g.epi;
     if (m >= g.M || !e.tok) return;
     int tk = e.tok[m];
     const Slot &s = e.slots[tok_slot(tk)];
     int p = tok_pos(tk);
-    if (g.asrc == A_EMBED) S.yrow[r] = s.y + (long)p * g.K;
+    if (yrow && g.asrc == A_EMBED) yrow[r] = s.y + (long)p * g.K;
     if (MODE == EPI_STORE && e.st_sel != CS_NONE) {
-        S.tab[0][r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.st_sel, e.st_layer, p, e.d);
+        tab[r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.st_sel, e.st_layer, p, e.d);
     } else if (MODE == EPI_QKV) {
         int layer = e.ring ? e.kv_layer * e.Tf + s.ring[s.nfr - 1] : e.kv_layer;
-        S.tab[0][r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.kc_sel, layer, p, e.d);
-        S.tab[1][r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.vc_sel, layer, p, e.d);
+        tab[r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.kc_sel, layer, p, e.d);
+        tab[ts + r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.vc_sel, layer, p, e.d);
     } else if (MODE == EPI_RESID_BASE) {
-        S.tab[1][r] = (uintptr_t)(s.eh + (long)p * g.N);
+        tab[ts + r] = (uintptr_t)(s.eh + (long)p * g.N);
     } else if (MODE == EPI_HEADS) {
-        S.tab[0][r] = (uintptr_t)(s.mu + (long)p * e.C);
-        S.tab[1][r] = (uintptr_t)(s.sigma + (long)p * e.C);
-        S.tab[2][r] = (uintptr_t)(s.idx + (long)p * e.C);
-        S.tab[3][r] = (uintptr_t)(s.m + (long)p * e.C);
+        tab[r] = (uintptr_t)(s.mu + (long)p * e.C);
+        tab[ts + r] = (uintptr_t)(s.sigma + (long)p * e.C);
+        tab[2 * ts + r] = (uintptr_t)(s.idx + (long)p * e.C);
+        tab[3 * ts + r] = (uintptr_t)(s.m + (long)p * e.C);
+    }
+}
+
+template <int MODE, int TN = NT>
+__device__ __forceinline__ void build_table(const GemmArgs &g, int m0, GemmShared &S)
+{
+    int r = threadIdx.x;
+    if (r < TN) table_row<MODE>(g, m0, r, &S.tab[0][0], NT, S.yrow);
+}
+
+// The value of output (feature f, token) from its accumulator y (and the
+// up projection's y2 for the dual form), as the epilogue mode defines it
+// (bf / ga, gb: the feature's bias, or the heads' channel-wise scale and
+// offset); *oi: the heads' scale index or rounded mean.  Every epilogue of
+// every kernel goes through this one definition.
+template <int MODE, bool DUAL>
+__device__ __forceinline__ float epi_value(float y, float y2, int f, float bf, float ga, float gb,
+                                           const float *stab, int *oi)
+{
+    *oi = 0;
+    if (MODE == EPI_HEADS) {
+        if (f & 1) {
+            float sg = expf(fminf(fmaxf(ga * y + gb, LN_SIG_LO), LN_SIG_HI));
+            *oi = scale_index(stab, sg);
+            return sg;
+        }
+        float mu = ga * y + gb;
+        *oi = (int)rintf(fminf(fmaxf(mu, -32768.0f), 32767.0f));
+        return mu;
+    }
+    if (MODE == EPI_SET_BIAS) return y + bf;
+    if (MODE == EPI_BIAS_SILU) return silu_fast(y + bf);
+    if (MODE == EPI_SWIGLU) return DUAL ? silu_fast(y) * y2 : y;
+    return y;
+}
+
+// A warp's 32 features (f0w + lane) x 8 tokens (rows m0 + c0 .. + 7) of a
+// bf16-output mode, o[j] = the lane's value for token c0 + j: staged in
+// shared memory (stg: 512 bytes of this warp) so that each lane stores 8
+// consecutive features of one token in one 16-byte write.  tab, ts: the
+// tile's token table (cache rows).
+template <int MODE>
+__device__ __forceinline__ void store_bf16_8(const Epi &e, int M, int N, int m0, int c0, int f0w,
+                                             const float *o, uint16_t *stg, const uintptr_t *tab, int ts)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        __nv_bfloat16 b = __float2bfloat16_rn(o[j]);
+        stg[j * 32 + lane] = *reinterpret_cast<uint16_t *>(&b);
+    }
+    __syncwarp();
+    const int jr = lane >> 2, fc = (lane & 3) * 8;
+    const uint4 val = *reinterpret_cast<const uint4 *>(stg + jr * 32 + fc);
+    __syncwarp();
+    const int r = c0 + jr, m = m0 + r, fb = f0w + fc;
+    if (m < M && fb < N) {
+        __nv_bfloat16 *dst;
+        if (MODE == EPI_STORE)
+            dst = e.st_sel == CS_NONE ? (__nv_bfloat16 *)e.out + (long)m * e.ld_out + fb
+                                      : (__nv_bfloat16 *)tab[r] + fb;
+        else if (MODE == EPI_QKV)
+            dst = fb < e.q_cols ? (__nv_bfloat16 *)e.out + (long)m * e.ld_out + fb
+                  : fb < e.q_cols + e.d ? (__nv_bfloat16 *)tab[r] + (fb - e.q_cols)
+                                        : (__nv_bfloat16 *)tab[ts + r] + (fb - e.q_cols - e.d);
+        else
+            dst = (__nv_bfloat16 *)e.out + (long)m * e.ld_out + fb;
+        if (fb + 8 <= N) {
+            *reinterpret_cast<uint4 *>(dst) = val;
+        } else {
+            const __nv_bfloat16 *pv = reinterpret_cast<const __nv_bfloat16 *>(&val);
+            for (int i = 0; i < N - fb; i++) dst[i] = pv[i];
+        }
     }
 }
 
@@ -750,7 +853,6 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
         return;
     }
     const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    constexpr uint32_t ASTEP = (DUAL ? 2 : 1) * TN;                // columns between the issuers' accumulators
     // E4M3: dequantisation scales of the feature row (both products below
     // are of powers of two, hence exact)
     float wf = 1.0f, wf2 = 1.0f;
@@ -769,7 +871,7 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
                 }
             }
             float v[16];
-            tmem_sum16(trow + cb + 16 * h, ASTEP, v);
+            tmem_get16(trow + cb + 16 * h, v);
 #pragma unroll
             for (int j = 0; j < 16; j++) {
                 if constexpr (F8) v[j] *= wf * S.xs[cb + 16 * h + j];
@@ -790,8 +892,8 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
         for (int c0 = cb; c0 < cb + TN / 2; c0 += 8) {
             float v[8], v2[8], o[8];
             int oi[8];
-            if (DUAL) tmem_sum8x2(trow + c0, trow + TN + c0, ASTEP, v, v2);
-            else tmem_sum8(trow + c0, ASTEP, v);
+            if (DUAL) tmem_get8x2(trow + c0, trow + TN + c0, v, v2);
+            else tmem_get8(trow + c0, v);
             if constexpr (F8) {
 #pragma unroll
                 for (int j = 0; j < 8; j++) {
@@ -801,29 +903,7 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const float y = v[j];
-                oi[j] = 0;
-                if (MODE == EPI_HEADS) {
-                    if (f & 1) {
-                        float sg = expf(fminf(fmaxf(ga * y + gb, LN_SIG_LO), LN_SIG_HI));
-                        o[j] = sg;
-                        oi[j] = scale_index(S.stab, sg);
-                    } else {
-                        float mu = ga * y + gb;
-                        o[j] = mu;
-                        oi[j] = (int)rintf(fminf(fmaxf(mu, -32768.0f), 32767.0f));
-                    }
-                } else if (MODE == EPI_SET_BIAS) {
-                    o[j] = y + bf;
-                } else if (MODE == EPI_BIAS_SILU) {
-                    o[j] = silu_fast(y + bf);
-                } else if (MODE == EPI_SWIGLU) {
-                    o[j] = DUAL ? silu_fast(y) * v2[j] : y;
-                } else {
-                    o[j] = y;
-                }
-            }
+            for (int j = 0; j < 8; j++) o[j] = epi_value<MODE, DUAL>(v[j], DUAL ? v2[j] : 0.0f, f, bf, ga, gb, S.stab, &oi[j]);
             if constexpr (MODE == EPI_HEADS || MODE == EPI_SET_BIAS) {
 #pragma unroll
                 for (int j = 0; j < 8; j++) {
@@ -844,38 +924,9 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
                     }
                 }
             } else {
-                // bf16 rows: the warp's 32 features x 8 tokens go through
-                // shared memory (the ring, idle now) so that each lane stores
-                // 8 consecutive features of one token in one 16-byte write
-                uint16_t *stg = (uint16_t *)(ring + warp * 512);
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    __nv_bfloat16 b = __float2bfloat16_rn(o[j]);
-                    stg[j * 32 + lane] = *reinterpret_cast<uint16_t *>(&b);
-                }
-                __syncwarp();
-                const int jr = lane >> 2, fc = (lane & 3) * 8;
-                const uint4 val = *reinterpret_cast<const uint4 *>(stg + jr * 32 + fc);
-                __syncwarp();
-                const int r = c0 + jr, m = m0 + r, fb = f0 + (warp & 3) * 32 + fc;
-                if (m < M && fb < N) {
-                    __nv_bfloat16 *dst;
-                    if (MODE == EPI_STORE)
-                        dst = e.st_sel == CS_NONE ? (__nv_bfloat16 *)e.out + (long)m * e.ld_out + fb
-                                                  : (__nv_bfloat16 *)S.tab[0][r] + fb;
-                    else if (MODE == EPI_QKV)
-                        dst = fb < e.q_cols ? (__nv_bfloat16 *)e.out + (long)m * e.ld_out + fb
-                              : fb < e.q_cols + e.d ? (__nv_bfloat16 *)S.tab[0][r] + (fb - e.q_cols)
-                                                    : (__nv_bfloat16 *)S.tab[1][r] + (fb - e.q_cols - e.d);
-                    else
-                        dst = (__nv_bfloat16 *)e.out + (long)m * e.ld_out + fb;
-                    if (fb + 8 <= N) {
-                        *reinterpret_cast<uint4 *>(dst) = val;
-                    } else {
-                        const __nv_bfloat16 *pv = reinterpret_cast<const __nv_bfloat16 *>(&val);
-                        for (int i = 0; i < N - fb; i++) dst[i] = pv[i];
-                    }
-                }
+                // bf16 rows through shared memory (the ring, idle now)
+                store_bf16_8<MODE>(e, M, N, m0, c0, f0 + (warp & 3) * 32, o, (uint16_t *)(ring + warp * 512),
+                                   &S.tab[0][0], NT);
             }
         }
     }
@@ -914,16 +965,16 @@ __device__ __forceinline__ int gemm_tile_pre(GemmShared &S, uint8_t *ring, const
 
 // The rest of a tile, after the caller's wait for its inputs and a CTA
 // barrier: token operand, MMAs, epilogue.  `first` is gemm_tile_pre's
-// result.  Roles: lane 0 of warps 1..4 issue the MMAs; lane 0 of warps 0, 5,
-// 6 and 7 issue the copies of the chunks past the first ring fill, each the
-// refills of its own stages.
+// result.  Roles: lane 0 of warp 1 issues the MMAs into the accumulator (the
+// gate accumulator of the dual form, whose up accumulator lane 0 of warp 2
+// feeds); lane 0 of warps 0, 5, 6 and 7 issue the copies of the chunks past
+// the first ring fill, each the refills of its own stages.
 template <bool DUAL, int MODE, bool F8 = false, bool LEAN = false, int TN = NT>
 __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uint32_t tmem, const CUtensorMap *tmW,
                                                const CUtensorMap *tmW2, const CUtensorMap *tmX, const GemmArgs &g,
                                                int f0, int m0, int first, GemmPipe &pp)
 {
     constexpr int NACC = DUAL ? 2 : 1;
-    constexpr int NPROD = NTHREADS / 32 - NISS;                    // producer warps: 0 and NISS+1 ..
     constexpr int KCH = kchunk(F8);
     const bool resident = F8 || g.asrc != A_DIRECT;
     const int stage = stage_bytes(DUAL, resident, TN);
@@ -931,8 +982,8 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
     uint8_t *res = ring + nst * stage;                             // resident token operand
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    const bool producer = lane == 0 && (warp == 0 || warp > NISS);
-    const int p = warp == 0 ? 0 : warp - NISS;                     // producer index
+    const bool producer = lane == 0 && (warp == 0 || warp > 4);
+    const int p = warp == 0 ? 0 : warp - 4;                        // producer index
     if (!resident && producer) {
         // the first fill's token chunks, spread over the producers (the MMA
         // issuers go straight to their loops)
@@ -970,32 +1021,36 @@ __device__ __forceinline__ void gemm_tile_main(GemmShared &S, uint8_t *ring, uin
             for (int j = first; j < jend; j++)
                 if ((j % nst) % NPROD == p) mbar_wait(&S.full[j % nst], fill_parity(pp, j % nst, j / nst));
         }
-    } else if (warp >= 1 && warp <= NISS && lane == 0) {
-        // MMA issuers: issuer q takes K step q of every chunk into its own
-        // accumulator (one thread issues an MMA only every ~150 cycles, so
-        // four issuers shorten the dependent chain fourfold); a stage that is
-        // filled again in this tile is released once all four have committed
-        const int q = warp - 1;
+    } else if (lane == 0 && (warp == 1 || (DUAL && warp == 2))) {
+        // MMA issuers: every K step of every chunk, in ascending K, into one
+        // accumulator (the output element's only summation order, whatever
+        // the tile shape, the launch or the kernel).  The dual form's up
+        // projection has its own issuer; a single issuer commits twice, so
+        // a stage that is filled again in this tile is released, and the
+        // tile finished, after two commits either way.
         const uint32_t id = F8 ? idesc_e4m3(TM, TN) : idesc_bf16(TM, TN);
-        const uint32_t acc0 = tmem + (uint32_t)q * (NACC * TN);
+        const uint32_t acc = tmem + (warp == 2 ? (uint32_t)TN : 0u);
+        const uint32_t aoff = warp == 2 ? (uint32_t)A_BYTES : 0u;
         for (int j = 0; j < nk; j++) {
             int s = j % nst, u = j / nst;
             if (S.abort) break;
             if (!mbar_wait(&S.full[s], fill_parity(pp, s, u))) { S.abort = 1; break; }
             fence_after();
-            uint32_t base = su32(ring + s * stage);
-            uint32_t bb = resident ? su32(res) + j * tok_chunk_bytes(TN) : base + NACC * A_BYTES;
-            // K step q: 32 bytes along the 128-byte rows (16 bf16 or 32 E4M3)
-            if (F8) {
-                mma8(acc0, sdesc(base + q * 32), sdesc(bb + q * 32), id, j != 0);
-                if (DUAL) mma8(acc0 + TN, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
-            } else {
-                mma(acc0, sdesc(base + q * 32), sdesc(bb + q * 32), id, j != 0);
-                if (DUAL) mma(acc0 + TN, sdesc(base + A_BYTES + q * 32), sdesc(bb + q * 32), id, j != 0);
+            uint32_t base = su32(ring + s * stage) + aoff;
+            uint32_t bb = resident ? su32(res) + j * tok_chunk_bytes(TN) : su32(ring + s * stage) + NACC * A_BYTES;
+            // four K steps of 32 bytes along the 128-byte rows (16 bf16 or 32 E4M3 each)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                if (F8) mma8(acc, sdesc(base + q * 32), sdesc(bb + q * 32), id, (j | q) != 0);
+                else mma(acc, sdesc(base + q * 32), sdesc(bb + q * 32), id, (j | q) != 0);
             }
-            if (j + nst < nk) mma_commit(&S.empty[s]);                 // the stage is filled again in this tile
+            if (j + nst < nk) {                                        // the stage is filled again in this tile
+                mma_commit(&S.empty[s]);
+                if (!DUAL) mma_commit(&S.empty[s]);
+            }
         }
         mma_commit(&S.done);
+        if (!DUAL) mma_commit(&S.done);
     }
     __syncwarp();
     gemm_epilogue<DUAL, MODE, F8, LEAN, TN>(S, ring, tmem, g, f0, m0, pp);

@@ -53,6 +53,22 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
     if ((threadIdx.x >> 5) == 0) tmem_free(tmem, TCOLS);
 }
 
+// RMSNorm rows for a projection whose tiles stream their token operand:
+// dst[m] = bf16(RMSNorm(X[m]) * gain), one warp per row, eight rows per
+// block (norm_row_global: the same values a tile would build).
+template <int CH>
+__global__ void __launch_bounds__(256) k_norm_rows(const float *__restrict__ X, const float *__restrict__ gain, int M,
+                                                   int K, __nv_bfloat16 *__restrict__ dst)
+{
+    pdl_trigger();
+    float4 gh[CH];
+    load_gain<CH>(gain, K, gh);                        // weights: ready before the previous kernel ends
+    const float invK = 1.0f / (float)K;
+    const int m = blockIdx.x * 8 + (threadIdx.x >> 5);
+    pdl_wait();
+    if (m < M) norm_row_global<CH>(X + (long)m * K, gh, invK, K, dst + (long)m * K);
+}
+
 // ---------------------------------------------------------------- host side
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -155,6 +171,16 @@ __global__ void k_quant_e4m3(const float *__restrict__ src, size_t n, float qmul
 }
 
 }  // namespace
+
+bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst, cudaStream_t s)
+{
+    if (M <= 0) return true;
+    if (K > KRES_MAX || K % 4) return false;
+    dim3 grid((M + 7) / 8), block(256);
+    cudaError_t e = K <= 384 ? launch_pdl(k_norm_rows<3>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst)
+                             : launch_pdl(k_norm_rows<4>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst);
+    return e == cudaSuccess;
+}
 
 bool gemm_tensor_map(const void *ptr, int rows, int K, int ld, int box_rows, CUtensorMap *out, bool f8)
 {

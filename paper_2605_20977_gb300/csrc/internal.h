@@ -21,6 +21,7 @@ constexpr int CDF_PREC = 16;
 constexpr int MAX_KK = 81;        // largest window (9 x 9)
 constexpr int MAX_TF = 4;         // frames in a temporal window
 constexpr int MAX_SLOTS = 128;    // frames in one batch (token word: slot << 24 | position)
+constexpr int WIDE_M = 1024;      // tokens from which a projection takes the persistent tensor-core kernel
 
 // One frame in flight.  A device-resident table of these lets one launch
 // serve tokens of several frames (of different sequences and grids): a token
@@ -137,8 +138,24 @@ struct GemmArgs {
 
 // Enqueue one GEMM.  BF16 projections whose N and K tile evenly run on the
 // tensor cores (the choice never depends on M); everything else on the SIMT
-// kernel.  Returns false if the launch could not be prepared.
+// kernel.  Launches of at least WIDE_M tokens take the persistent
+// warp-specialised tensor-core kernel (a BF16 normalised input is then
+// normalised once by launch_norm_rows); the tensor-core kernels give
+// bit-identical results, so the choice never changes a value.  Returns
+// false if the launch could not be prepared.
 bool gemm(int prec, const GemmArgs &g, cudaStream_t s);
+// dst[m][k] = bf16(RMSNorm(X[m]) * gain) for m < M, K <= 512 (a multiple of
+// 4): the normalised token operand of a projection whose tiles then stream
+// it (A_DIRECT), bit-identical to the operand an A_NORM tile builds.
+bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst, cudaStream_t s);
+// The persistent warp-specialised kernel for launches with many token tiles
+// (gemm_ws.cu): BF16, a streamed token operand (A_DIRECT), the epilogues of
+// block projections and heads; bit-identical to the one-tile-per-CTA kernel.
+bool gemm_ws_supported(const GemmArgs &g);
+// Whether gemm() sends this launch to the persistent kernel.
+bool gemm_takes_ws(int prec, const GemmArgs &g);
+bool gemm_ws(const GemmArgs &g, cudaStream_t s);
+bool gemm_ws_prepare();           // kernel attributes, before any capture
 bool gemm_tc_supported(int prec, int N, int K, int asrc);
 bool gemm_tc8_supported(int N, int K, int asrc);
 // E4M3 weights of one tensor: dst[i] = e4m3_rn(src[i] / s) with the

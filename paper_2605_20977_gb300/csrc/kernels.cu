@@ -417,6 +417,7 @@ bool gemm_tc(const GemmArgs &g, cudaStream_t s);
 bool gemm(int prec, const GemmArgs &g0, cudaStream_t s)
 {
     if (g0.M <= 0 || g0.N <= 0) return true;
+    if (gemm_takes_ws(prec, g0)) return gemm_ws(g0, s);
     if (g0.f8 || gemm_tc_supported(prec, g0.N, g0.K, g0.asrc)) return gemm_tc(g0, s);     // E4M3: tensor cores only
     // SIMT path: materialise the token operand first
     GemmArgs g = g0;

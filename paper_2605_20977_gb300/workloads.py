@@ -7,6 +7,11 @@ frames) over four latent grids: 15x26, 30x52, 68x120 and 135x240.
   (per-phase graphs or the persistent kernel) x grouping (one call per
   round over all sequences, or one call per grid) -- on the first rounds and
   decodes the rest with the fastest.
+* encode: the encoder's masked parallel pass (every position of a frame in
+  one pass, 8160 tokens per launch at 1080p) and its rANS coding, frame
+  after frame of the I-frame model; frames/s.  Small on the device, so it
+  also serves as the case for profiler captures of the wide projection
+  kernel.
 * serve: seeded Poisson arrivals of 1..16-frame requests through the
   continuous-batching server (serve.Server), batched (in the chosen
   precision, E4M3 block projections by default) against one frame per call
@@ -17,6 +22,7 @@ once; a request or sequence decodes a pool sequence's first frames.
 
     python -m paper_2605_20977_gb300.workloads mixed --seqs 32 --frames 4 --precision fp8
     python -m paper_2605_20977_gb300.workloads serve --rate 200 --window 0.1 --precision fp8
+    python -m paper_2605_20977_gb300.workloads encode --frames 4
 """
 from __future__ import annotations
 
@@ -172,9 +178,36 @@ def run_serve(rate=200.0, window=0.1, per_grid=2, gop=16, budget_gb=120.0, max_b
     return out
 
 
+def run_encode(nframes=4, dev=None, precision="bf16"):
+    """Encode nframes 1080p I-frames one after another (masked pass plus
+    rANS); the first is a warm-up.  Returns frames/s of the rest."""
+    import torch
+    cfg = synth.config("i1080")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=PRECISIONS[precision])
+    seq = ctx.seq_create(cfg.H, cfg.W)
+    fr = synth.frames(cfg, 1, seed=1002)
+    fd = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_WAVEFRONT)
+    y = torch.from_numpy(fr.y[0]).to(dev)
+    z = torch.from_numpy(fr.z[0]).to(dev)
+    bs = torch.zeros(ctx.bitstream_capacity(cfg.H, cfg.W), dtype=torch.uint8, device=dev)
+    seq.encode_params(fd, y, z, bitstream=bs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(0, nframes - 1)):
+        seq.reset()
+        seq.encode_params(fd, y, z, bitstream=bs)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    seq.close()
+    ctx.close()
+    n = max(0, nframes - 1)
+    return {"workload": f"encoder masked pass + rANS, 1080p I-frames 68x120x192, {precision.upper()}",
+            "frames": n, "frames_per_s": n / dt if n else None, "tflops": n * 505.0 / dt / 1e3 if n else None}
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["mixed", "serve"])
+    ap.add_argument("what", choices=["mixed", "serve", "encode"])
     ap.add_argument("--seqs", type=int, default=32)
     ap.add_argument("--frames", type=int, default=4)
     ap.add_argument("--rate", type=float, default=200.0)
@@ -190,6 +223,8 @@ def main():
     dev = torch.device("cuda", 0)
     if args.what == "mixed":
         res = run_mixed(args.seqs, args.frames, dev=dev, precision=args.precision or "bf16")
+    elif args.what == "encode":
+        res = run_encode(args.frames, dev=dev, precision=args.precision or "bf16")
     else:
         res = run_serve(args.rate, args.window, dev=dev, unbatched=not args.no_unbatched,
                         precision=args.precision or "fp8", engines=tuple(args.engines.split(",")))

@@ -2,22 +2,22 @@
 // batch, the encoder's masked pass): one persistent, warp-specialised tcgen05
 // kernel per projection.
 //
-// A tile is 128 tokens x TNF output features (TNF = 64, 128 or 256, chosen
-// per launch; the dual SwiGLU form keeps a gate and an up accumulator of TNF
-// each, TNF <= 128): the tokens are the MMA's A operand (M = 128, one token
-// per tensor-memory lane), the projection its B operand (N = TNF), so each
-// epilogue thread owns one token's row piece (the warp's 32 rows go out
-// through a small shared staging buffer as row-contiguous stores).
-// The tiles, feature tile major, are split into equal contiguous ranges,
-// one per CTA (one CTA per SM), so a CTA's tiles mostly share one feature
-// tile; when a feature tile's weights fit (<= 96 KB) they are copied once
-// and stay resident in shared memory (copied again only where a range
-// crosses into the next feature tile), so only token chunks stream through
-// the ring -- half the L2 traffic of a tile that re-reads its weights.
+// A tile is 128 output features x TNB tokens (TNB = 64, 128 or 256, chosen
+// per launch; at most 128 for the dual SwiGLU form, whose gate and up
+// accumulators are both kept, and for the residual modes): the projection is
+// the MMA's A operand (M = 128, one feature per tensor-memory lane), the
+// tokens its B operand (N = TNB).  One CTA per SM walks the tiles
+// blockIdx.x, + grid, ... (feature tile fastest, so CTAs running together
+// share token tiles in L2); where each CTA has three or more tiles and a
+// feature tile's weights fit (<= 96 KB: the single projections of width up
+// to 384), the tiles, feature tile major, are split into equal contiguous
+// ranges instead and a CTA keeps its feature tile's weights resident in
+// shared memory (copied again only where its range crosses into the next
+// feature tile), so only token chunks stream through the ring.
 // Roles:
 //   warp 0, lane 0     copies (the first resident weights before waiting for
 //                      the previous kernel, then the 64-wide K chunks of
-//                      every tile through a 4..8-stage ring);
+//                      every tile through a 4..8-stage ring of ~192 KB);
 //   warp 1 (2), lane 0 issues the MMAs, every K step in ascending order into
 //                      one accumulator (the up projection's on warp 2), into
 //                      one of two tensor-memory buffers, so a tile's MMAs run
@@ -25,17 +25,18 @@
 //   warp 3             resolves each tile's token table (the cache, hyperprior
 //                      or head rows its outputs go to) into one of two
 //                      shared tables, ahead of the epilogue;
-//   warps 4..11        the epilogue: warp w reads tensor-memory lanes
-//                      32 (w % 4) .. + 31 (its tokens) and half of the
-//                      buffer's columns (features), and writes the mode's
-//                      outputs.
+//   warps 4..11        the epilogue: warp w reads the 32 feature rows
+//                      32 (w % 4) .. + 31 of the buffer (lane = feature) and
+//                      half of its token columns and writes the mode's
+//                      outputs (residual rows coalesced along the features,
+//                      bf16 rows through a 512-byte staging buffer per warp
+//                      as 16-byte stores).
 // The token operand is always compact bf16 rows (A_DIRECT; normalised
 // inputs come from launch_norm_rows).  The accumulation order (one
-// accumulator, K ascending) and the per-element epilogue (epi_value) are
-// those of the one-tile-per-CTA kernel, and the tensor core computes an
-// element the same whatever the MMA's shape and whichever operand holds the
-// tokens, so a token's outputs are bit-identical whichever kernel its launch
-// takes.
+// accumulator, K ascending) and the per-element epilogue (epi_value,
+// store_bf16_8) are those of the one-tile-per-CTA kernel, and the tensor
+// core computes an element the same whatever the MMA's shape, so a token's
+// outputs are bit-identical whichever kernel its launch takes.
 //
 // Every wait is bounded (~2 s): on expiry the CTA raises its abort flag,
 // every role leaves its loop, the copy producer and the MMA issuers wait
@@ -54,36 +55,38 @@ namespace {
 constexpr int WS_THREADS = 384;                       // 12 warps
 constexpr int WS_EPI0 = 4;                            // first epilogue warp
 constexpr int WS_EPI_WARPS = 8;
-constexpr int WS_TM = 128;                            // tokens per tile (MMA M)
-constexpr int WS_TAB = WS_TM;                         // token-table rows
+constexpr int WS_TAB = 256;                           // token-table rows (tokens of a tile at most)
 constexpr int WS_MAXST = 8;                           // ring stages at most
-constexpr int WS_STG = 4096;                          // epilogue staging of one warp: 32 rows x 128 bytes
-constexpr int WS_DYN = 176 * 1024;                    // resident weights + ring (+ staging and slack)
+constexpr int WS_STG = 512;                           // epilogue staging of one warp: 32 features x 8 tokens
+constexpr int WS_DYN = 192 * 1024;                    // resident weights + ring
 constexpr int WS_WRES_MAX = 96 * 1024;                // resident weights at most
-constexpr int WS_XCHUNK = WS_TM * 128;                // one 64-wide K chunk of a token tile
 constexpr uint32_t WS_TCOLS = 512;                    // two accumulator buffers
+constexpr bool WS_RESIDENT = false;                   // resident-weight schedule (measured slower at decode sizes)
 
 // Geometry of a launch, the same on host and device.
 struct WsGeom {
-    int tnf;                      // features per tile
+    int tnb;                      // tokens per tile
     int nf, ntok, ntiles, grid;   // feature tiles, token tiles, tiles, CTAs
     int wres;                     // 1: the feature tile's weights stay resident
-    int wchunk;                   // bytes of one K chunk of the tile's weights (both, dual form)
+    int wchunk, xchunk;           // bytes of one K chunk of a tile's weights (both, dual form) / tokens
     int stage, nst;               // ring stage bytes and stages
 };
 
-__host__ __device__ inline WsGeom ws_geom(int tnf, bool dual, int M, int N, int K, int sms)
+__host__ __device__ inline WsGeom ws_geom(int tnb, bool dual, int M, int N, int K, int sms)
 {
     WsGeom q{};
-    q.tnf = tnf;
-    q.nf = (N + tnf - 1) / tnf;
-    q.ntok = (M + WS_TM - 1) / WS_TM;
+    q.tnb = tnb;
+    q.nf = (N + TM - 1) / TM;
+    q.ntok = (M + tnb - 1) / tnb;
     q.ntiles = q.nf * q.ntok;
     q.grid = q.ntiles < sms ? q.ntiles : sms;
-    q.wchunk = (dual ? 2 : 1) * tnf * 128;
+    q.wchunk = (dual ? 2 : 1) * A_BYTES;
+    q.xchunk = tnb * 128;
     const int nk = K / KC;
-    q.wres = q.wchunk * nk <= WS_WRES_MAX;
-    q.stage = WS_XCHUNK + (q.wres ? 0 : q.wchunk);
+    // resident weights pay when a CTA has at least three tiles (their copy
+    // delays the first tile's token chunks); they need feature-major ranges
+    q.wres = WS_RESIDENT && q.wchunk * nk <= WS_WRES_MAX && q.ntiles >= 3 * q.grid;
+    q.stage = q.xchunk + (q.wres ? 0 : q.wchunk);
     int st = (WS_DYN - (q.wres ? q.wchunk * nk : 0)) / q.stage;
     q.nst = st < WS_MAXST ? st : WS_MAXST;
     return q;
@@ -128,161 +131,101 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t *r)
         : "r"(addr));
 }
 
-__device__ __forceinline__ uint32_t bf16x2(float a, float b)
-{
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t *>(&h);
-}
-
-// Epilogue of one tile for this thread: token row r (tensor-memory lane) of
-// the tile (m0: the tile's first token), features fh .. fh + TNF / 2 of the
-// output (accumulator columns fh - f0 ..), once the tile's MMAs are complete
-// (the full barrier at parity par; false if that wait expired).  Each lane
-// holds its own token's row piece; the warp's 32 rows go through its
-// staging buffer stg (row pieces stored with their 16-byte chunks
-// XOR-swizzled by the row, conflict-free both ways) so that global loads and
-// stores are row-contiguous runs of 64 or 128 bytes.  Residual modes read the
-// rows they update (cooperatively, coalesced) while the MMAs still run.
-template <bool DUAL, int MODE, int TNF>
+// Epilogue of one tile for this warp: feature rows f0 + 32 quarter + lane,
+// token columns cb .. cb + TNB / 2 of the accumulator at tacc (m0: the
+// tile's first token), once the tile's MMAs are complete (the full barrier
+// at parity par; false if that wait expired).  Residual modes read the rows
+// they update while the MMAs still run (all of a thread's values in flight
+// at once); the other modes read the accumulator 32 columns per wait.
+template <bool DUAL, int MODE, int TNB>
 __device__ __forceinline__ bool ws_epilogue(const GemmArgs &g, WsShared &S, const uintptr_t *tab, uint64_t *full,
-                                            uint32_t par, uint32_t tacc, int r, int m0, int f0, int fh,
-                                            uint8_t *stg)
+                                            uint32_t par, uint32_t tacc, int f0, int m0, int quarter, int cb,
+                                            uint16_t *stg)
 {
     constexpr bool RESID = MODE == EPI_RESID || MODE == EPI_RESID_BASE;
-    constexpr int NC = TNF / 2;                               // features of this thread
+    constexpr int NC = TNB / 2;                               // token columns of this warp
     const int lane = threadIdx.x & 31;
     const int M = g.M, N = g.N;
     const Epi &e = g.epi;
-    const int rw = r - lane;                                  // the warp's first row in the tile
-    const uint32_t tcol = tacc + (uint32_t)(fh - f0);
+    const int f = f0 + quarter * 32 + lane;
+    const bool fok = f < N;
+    const uint32_t trow = tacc + (uint32_t)cb;
     if constexpr (RESID) {
         static_assert(NC <= 64, "residual tiles keep their old values in registers");
-        // lane l, pass k: row rw + (l >> 3) + 4k, 16-byte chunk l & 7 of each
-        // 32-feature group (128 bytes of a row per eight lanes)
-        float4 old[NC / 32][8];
-        const int cr = lane >> 3, cc = lane & 7;
+        float old[NC];
+        const int nv = fok ? min(NC, M - (m0 + cb)) : 0;         // this warp's rows m0 + cb + j, j < nv
+        float *rowf = e.rows + (long)(m0 + cb) * N + f;          // row j at rowf[j * N]
 #pragma unroll
-        for (int gI = 0; gI < NC / 32; gI++)
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int rr = rw + cr + 4 * k, m = m0 + rr, f = fh + 32 * gI + 4 * cc;
-                const float *src = MODE == EPI_RESID ? e.rows + (long)m * N : (const float *)tab[WS_TAB + rr];
-                old[gI][k] = (m < M && f < N) ? *reinterpret_cast<const float4 *>(src + f)
-                                              : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+        for (int j = 0; j < NC; j++) {
+            const float *src = MODE == EPI_RESID ? rowf + j * N : (const float *)tab[WS_TAB + cb + j] + f;
+            old[j] = j < nv ? *src : 0.0f;
+        }
         if (S.abort || !mbar_wait(full, par)) return false;
         fence_after();
 #pragma unroll
-        for (int gI = 0; gI < NC / 32; gI++) {
+        for (int h = 0; h < NC / 32; h++) {
             uint32_t v[32];
-            tmem_ld32(tcol + 32 * gI, v);
+            tmem_ld32(trow + 32 * h, v);
             tmem_wait_ld();
-            // old values to the staging rows, this lane's row back, sum, out
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int rr = cr + 4 * k;
-                *reinterpret_cast<float4 *>(stg + rr * 128 + ((cc ^ (rr & 7)) << 4)) = old[gI][k];
-            }
-            __syncwarp();
-#pragma unroll
-            for (int c = 0; c < 8; c++) {
-                float4 *p = reinterpret_cast<float4 *>(stg + lane * 128 + ((c ^ (lane & 7)) << 4));
-                const float4 a = *p;
-                *p = make_float4(a.x + __uint_as_float(v[4 * c]), a.y + __uint_as_float(v[4 * c + 1]),
-                                 a.z + __uint_as_float(v[4 * c + 2]), a.w + __uint_as_float(v[4 * c + 3]));
-            }
-            __syncwarp();
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int rr = cr + 4 * k, m = m0 + rw + rr, f = fh + 32 * gI + 4 * cc;
-                const float4 val = *reinterpret_cast<const float4 *>(stg + rr * 128 + ((cc ^ (rr & 7)) << 4));
-                if (m < M && f < N) *reinterpret_cast<float4 *>(e.rows + (long)m * N + f) = val;
-            }
-            __syncwarp();
+            for (int j = 0; j < 32; j++)
+                if (32 * h + j < nv) rowf[(32 * h + j) * N] = old[32 * h + j] + __uint_as_float(v[j]);
         }
         return true;
     } else {
         if (S.abort || !mbar_wait(full, par)) return false;
         fence_after();
-        const int m = m0 + r;
-        const bool mok = m < M;
+        float bf = 0.0f, ga = 0.0f, gb = 0.0f;
+        if ((MODE == EPI_SET_BIAS || MODE == EPI_BIAS_SILU) && fok) bf = e.bias[f];
+        if (MODE == EPI_HEADS && fok) {
+            ga = (f & 1) ? e.gsg[f >> 1] : e.gmu[f >> 1];
+            gb = (f & 1) ? e.bsg[f >> 1] : e.bmu[f >> 1];
+        }
 #pragma unroll 1
-        for (int c = 0; c < NC; c += 32) {
-            const int f = fh + c;                             // first feature of the group
+        for (int c32 = 0; c32 < NC; c32 += 32) {
             uint32_t v[32], v2[DUAL ? 32 : 1];
-            tmem_ld32(tcol + c, v);
-            if constexpr (DUAL) tmem_ld32(tcol + TNF + c, v2);
+            tmem_ld32(trow + c32, v);
+            if constexpr (DUAL) tmem_ld32(trow + TNB + c32, v2);
             tmem_wait_ld();
-            if (f >= N) continue;                             // the same for the whole warp
-            float o[32];
-            int oi[32];
+            if (m0 + cb + c32 >= M) continue;                   // the same for the whole warp
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
-                const int fj = f + j;
-                float bf = 0.0f, ga = 0.0f, gb = 0.0f;
-                if (MODE == EPI_SET_BIAS || MODE == EPI_BIAS_SILU) bf = e.bias[fj];
-                if (MODE == EPI_HEADS) {
-                    ga = (fj & 1) ? e.gsg[fj >> 1] : e.gmu[fj >> 1];
-                    gb = (fj & 1) ? e.bsg[fj >> 1] : e.bmu[fj >> 1];
-                }
-                o[j] = epi_value<MODE, DUAL>(__uint_as_float(v[j]), DUAL ? __uint_as_float(v2[j % (DUAL ? 32 : 1)]) : 0.0f,
-                                             fj, bf, ga, gb, S.stab, &oi[j]);
-            }
-            if constexpr (MODE == EPI_HEADS) {
-                // features 2c / 2c + 1 are mu / sigma of channel c: 16 channels
-                if (!mok) continue;
-                const int c0 = f >> 1;
-                float *mu = (float *)tab[r] + c0, *sg = (float *)tab[WS_TAB + r] + c0;
-                uint8_t *ix = (uint8_t *)tab[2 * WS_TAB + r] + c0;
-                int32_t *mm = (int32_t *)tab[3 * WS_TAB + r] + c0;
+            for (int q = 0; q < 4; q++) {
+                const int c0 = cb + c32 + 8 * q;                 // tile column of the group's first token
+                float o[8];
+                int oi[8];
 #pragma unroll
-                for (int i = 0; i < 4; i++) {
-                    reinterpret_cast<float4 *>(mu)[i] = make_float4(o[8 * i], o[8 * i + 2], o[8 * i + 4], o[8 * i + 6]);
-                    reinterpret_cast<float4 *>(sg)[i] = make_float4(o[8 * i + 1], o[8 * i + 3], o[8 * i + 5], o[8 * i + 7]);
-                    reinterpret_cast<int4 *>(mm)[i] = make_int4(oi[8 * i], oi[8 * i + 2], oi[8 * i + 4], oi[8 * i + 6]);
-                }
-                uint32_t w[4];
+                for (int j = 0; j < 8; j++)
+                    o[j] = epi_value<MODE, DUAL>(__uint_as_float(v[8 * q + j]),
+                                                 DUAL ? __uint_as_float(v2[(8 * q + j) % (DUAL ? 32 : 1)]) : 0.0f,
+                                                 f, bf, ga, gb, S.stab, &oi[j]);
+                if constexpr (MODE == EPI_HEADS || MODE == EPI_SET_BIAS) {
 #pragma unroll
-                for (int i = 0; i < 4; i++)
-                    w[i] = (uint32_t)(oi[8 * i + 1] & 255) | ((uint32_t)(oi[8 * i + 3] & 255) << 8) |
-                           ((uint32_t)(oi[8 * i + 5] & 255) << 16) | ((uint32_t)(oi[8 * i + 7] & 255) << 24);
-                *reinterpret_cast<uint4 *>(ix) = make_uint4(w[0], w[1], w[2], w[3]);
-            } else {
-                // this lane's 64-byte row piece (four chunks) to the staging
-                // rows, then lane l stores chunk l & 3 of rows (l >> 2) + 8k
-#pragma unroll
-                for (int i = 0; i < 4; i++)
-                    *reinterpret_cast<uint4 *>(stg + lane * 64 + ((i ^ ((lane >> 1) & 3)) << 4)) =
-                        make_uint4(bf16x2(o[8 * i], o[8 * i + 1]), bf16x2(o[8 * i + 2], o[8 * i + 3]),
-                                   bf16x2(o[8 * i + 4], o[8 * i + 5]), bf16x2(o[8 * i + 6], o[8 * i + 7]));
-                __syncwarp();
-                const int cc = lane & 3;
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    const int rr = (lane >> 2) + 8 * k, row = rw + rr, mm = m0 + row, ff = f + 8 * cc;
-                    const uint4 val = *reinterpret_cast<const uint4 *>(stg + rr * 64 + ((cc ^ ((rr >> 1) & 3)) << 4));
-                    if (mm < M) {
-                        __nv_bfloat16 *dst;
-                        if (MODE == EPI_STORE)
-                            dst = e.st_sel == CS_NONE ? (__nv_bfloat16 *)e.out + (long)mm * e.ld_out + ff
-                                                      : (__nv_bfloat16 *)tab[row] + ff;
-                        else if (MODE == EPI_QKV)
-                            dst = f < e.q_cols ? (__nv_bfloat16 *)e.out + (long)mm * e.ld_out + ff
-                                  : f < e.q_cols + e.d ? (__nv_bfloat16 *)tab[row] + (ff - e.q_cols)
-                                                       : (__nv_bfloat16 *)tab[WS_TAB + row] + (ff - e.q_cols - e.d);
-                        else
-                            dst = (__nv_bfloat16 *)e.out + (long)mm * e.ld_out + ff;
-                        *reinterpret_cast<uint4 *>(dst) = val;
+                    for (int j = 0; j < 8; j++) {
+                        const int rr = c0 + j, m = m0 + rr;
+                        if (!(fok && m < M)) continue;
+                        if (MODE == EPI_HEADS) {
+                            const int c = f >> 1;
+                            if (f & 1) {
+                                ((float *)tab[WS_TAB + rr])[c] = o[j];
+                                ((uint8_t *)tab[2 * WS_TAB + rr])[c] = (uint8_t)oi[j];
+                            } else {
+                                ((float *)tab[rr])[c] = o[j];
+                                ((int32_t *)tab[3 * WS_TAB + rr])[c] = oi[j];
+                            }
+                        } else {
+                            e.rows[(long)m * N + f] = o[j];
+                        }
                     }
+                } else {
+                    store_bf16_8<MODE>(e, M, N, m0, c0, f0 + quarter * 32, o, stg, tab, WS_TAB);
                 }
-                __syncwarp();
             }
         }
         return true;
     }
 }
 
-template <bool DUAL, int MODE, int TNF>
+template <bool DUAL, int MODE, int TNB>
 __global__ void __launch_bounds__(WS_THREADS, 1)
 k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmW2,
           const __grid_constant__ CUtensorMap tmX, const __grid_constant__ GemmArgs g, int sms, int *status)
@@ -290,13 +233,20 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
     constexpr int NACC = DUAL ? 2 : 1;
     extern __shared__ uint8_t smem_raw[];
     __shared__ WsShared S;
-    const WsGeom q = ws_geom(TNF, DUAL, g.M, g.N, g.K, sms);
+    const WsGeom q = ws_geom(TNB, DUAL, g.M, g.N, g.K, sms);
     const int nk = g.K / KC;
     uint8_t *wbuf = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *ring = wbuf + (q.wres ? q.wchunk * nk : 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // this CTA's tiles tb .. te - 1: tile t is feature tile t / ntok, token tile t % ntok
-    const int tb = (int)((long)blockIdx.x * q.ntiles / q.grid), te = (int)((long)(blockIdx.x + 1) * q.ntiles / q.grid);
+    // this CTA's tiles: with resident weights the contiguous range tb .. te - 1
+    // (tile t: feature tile t / ntok, token tile t % ntok), otherwise
+    // blockIdx.x, + grid, ... (tile t: feature tile t % nf, token tile t / nf,
+    // so the CTAs running together share token tiles in L2)
+    const int tb = q.wres ? (int)((long)blockIdx.x * q.ntiles / q.grid) : blockIdx.x;
+    const int te = q.wres ? (int)((long)(blockIdx.x + 1) * q.ntiles / q.grid) : q.ntiles;
+    const int ts = q.wres ? 1 : q.grid;
+    auto tile_f = [&](int t) { return q.wres ? t / q.ntok : t % q.nf; };
+    auto tile_m = [&](int t) { return q.wres ? t % q.ntok : t / q.nf; };
     if (threadIdx.x == 0) {
         for (int s = 0; s < q.nst; s++) { mbar_init(&S.full[s], 1); mbar_init(&S.empty[s], NACC); }
         for (int b = 0; b < 2; b++) {
@@ -325,25 +275,34 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
             auto load_weights = [&](int fi) {
                 mbar_expect_tx(&S.wbar, (uint32_t)(q.wchunk * nk));
                 for (int j = 0; j < nk; j++) {
-                    tma_load(wbuf + j * q.wchunk, &tmW, &S.wbar, j * KC, fi * TNF);
-                    if (DUAL) tma_load(wbuf + j * q.wchunk + TNF * 128, &tmW2, &S.wbar, j * KC, fi * TNF);
+                    tma_load(wbuf + j * q.wchunk, &tmW, &S.wbar, j * KC, fi * TM);
+                    if (DUAL) tma_load(wbuf + j * q.wchunk + A_BYTES, &tmW2, &S.wbar, j * KC, fi * TM);
                 }
             };
             int cur_f = -1, nload = 0;
             if (q.wres && tb < te) {
                 // the projection's weights do not change: the first copy goes
                 // out before the wait for the previous kernel
-                cur_f = tb / q.ntok;
+                cur_f = tile_f(tb);
                 load_weights(cur_f);
                 nload = 1;
+            }
+            // streamed weights: the first tile's first ring fill of weight
+            // chunks goes out before the wait too (their token chunks after it)
+            const int pre = q.wres ? 0 : (nk < q.nst ? nk : q.nst);
+            for (int j = 0; j < pre; j++) {
+                uint8_t *st = ring + j * q.stage;
+                mbar_expect_tx(&S.full[j], (uint32_t)q.stage);
+                tma_load(st + q.xchunk, &tmW, &S.full[j], j * KC, tile_f(tb) * TM);
+                if (DUAL) tma_load(st + q.xchunk + A_BYTES, &tmW2, &S.full[j], j * KC, tile_f(tb) * TM);
             }
             pdl_wait();                                    // the token rows are the previous kernel's output
             fence_proxy_global();
             // chunk `it` of the CTA's sequence fills stage it % nst for the
             // (it / nst)-th time, after the MMAs released its previous use
             int it = 0;
-            for (int t = tb; t < te && !S.abort; t++) {
-                const int fi = t / q.ntok, f0 = fi * TNF, m0 = (t % q.ntok) * WS_TM;
+            for (int t = tb; t < te && !S.abort; t += ts) {
+                const int fi = tile_f(t), f0 = fi * TM, m0 = tile_m(t) * TNB;
                 if (q.wres && fi != cur_f) {
                     // the previous feature tile's MMAs are done with its weights
                     if (!mbar_wait(&S.wempty, (nload - 1) & 1)) { S.abort = 1; break; }
@@ -353,13 +312,17 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
                 }
                 for (int j = 0; j < nk; j++, it++) {
                     const int s = it % q.nst, u = it / q.nst;
-                    if (u > 0 && !mbar_wait(&S.empty[s], (u - 1) & 1)) { S.abort = 1; break; }
                     uint8_t *st = ring + s * q.stage;
+                    if (it < pre) {                          // its weights already on the way
+                        tma_load(st, &tmX, &S.full[s], j * KC, m0);
+                        continue;
+                    }
+                    if (u > 0 && !mbar_wait(&S.empty[s], (u - 1) & 1)) { S.abort = 1; break; }
                     mbar_expect_tx(&S.full[s], (uint32_t)q.stage);
                     tma_load(st, &tmX, &S.full[s], j * KC, m0);
                     if (!q.wres) {
-                        tma_load(st + WS_XCHUNK, &tmW, &S.full[s], j * KC, f0);
-                        if (DUAL) tma_load(st + WS_XCHUNK + TNF * 128, &tmW2, &S.full[s], j * KC, f0);
+                        tma_load(st + q.xchunk, &tmW, &S.full[s], j * KC, f0);
+                        if (DUAL) tma_load(st + q.xchunk + A_BYTES, &tmW2, &S.full[s], j * KC, f0);
                     }
                 }
             }
@@ -370,11 +333,11 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
         }
     } else if (warp == 1 || (DUAL && warp == 2)) {
         if (lane == 0) {
-            const uint32_t id = idesc_bf16(WS_TM, TNF);
-            const uint32_t woff = warp == 2 ? (uint32_t)(TNF * 128) : 0u;
+            const uint32_t id = idesc_bf16(TM, TNB);
+            const uint32_t woff = warp == 2 ? (uint32_t)A_BYTES : 0u;
             int it = 0, i = 0, cur_f = -1, nuse = 0;
-            for (int t = tb; t < te && !S.abort; t++, i++) {
-                const int b = i & 1, ub = i >> 1, fi = t / q.ntok;
+            for (int t = tb; t < te && !S.abort; t += ts, i++) {
+                const int b = i & 1, ub = i >> 1, fi = tile_f(t);
                 if (q.wres && fi != cur_f) {
                     // the earlier MMAs release the resident weights; wait for the new ones
                     if (cur_f >= 0) mma_commit(&S.wempty);
@@ -384,17 +347,17 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
                 }
                 if (ub > 0 && !mbar_wait(&S.tempty[b], (ub - 1) & 1)) { S.abort = 1; break; }
                 fence_after();
-                const uint32_t acc = tmem + (uint32_t)(b * NACC * TNF) + (warp == 2 ? (uint32_t)TNF : 0u);
+                const uint32_t acc = tmem + (uint32_t)(b * NACC * TNB) + (warp == 2 ? (uint32_t)TNB : 0u);
                 for (int j = 0; j < nk; j++, it++) {
                     const int s = it % q.nst, u = it / q.nst;
                     if (S.abort) break;
                     if (!mbar_wait(&S.full[s], u & 1)) { S.abort = 1; break; }
                     fence_after();
-                    const uint32_t xa = su32(ring + s * q.stage);
-                    const uint32_t wb = (q.wres ? su32(wbuf + j * q.wchunk) : xa + WS_XCHUNK) + woff;
+                    const uint32_t xb = su32(ring + s * q.stage);
+                    const uint32_t wa = (q.wres ? su32(wbuf + j * q.wchunk) : xb + q.xchunk) + woff;
 #pragma unroll
                     for (int k = 0; k < 4; k++)
-                        mma(acc, sdesc(xa + k * 32), sdesc(wb + k * 32), id, (j | k) != 0);
+                        mma(acc, sdesc(wa + k * 32), sdesc(xb + k * 32), id, (j | k) != 0);
                     mma_commit(&S.empty[s]);
                 }
                 mma_commit(&S.tfull[b]);
@@ -409,27 +372,25 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
             // token tables (the token list and slot table are fixed for the
             // whole decode: no wait for the previous kernel)
             int i = 0;
-            for (int t = tb; t < te && !S.abort; t++, i++) {
+            for (int t = tb; t < te && !S.abort; t += ts, i++) {
                 const int b = i & 1, ub = i >> 1;
                 if (ub > 0 && !mbar_wait(&S.tabempty[b], (ub - 1) & 1)) { S.abort = 1; break; }
-                for (int r = lane; r < WS_TM; r += 32) table_row<MODE>(g, (t % q.ntok) * WS_TM, r, S.tab[b], WS_TAB, nullptr);
+                for (int r = lane; r < TNB; r += 32) table_row<MODE>(g, tile_m(t) * TNB, r, S.tab[b], WS_TAB, nullptr);
                 mbar_arrive(&S.tabfull[b]);
             }
         }
     } else if (warp >= WS_EPI0) {
         pdl_wait();                                        // rows and caches of the previous kernel
-        const int r = (warp & 3) * 32 + lane;              // token row of the tile (tensor-memory lane)
-        const int half = (warp - WS_EPI0) >> 2;
-        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-        uint8_t *stg = ring + q.nst * q.stage + (warp - WS_EPI0) * WS_STG;
+        const int quarter = warp & 3, cb = ((warp - WS_EPI0) >> 2) * (TNB / 2);
+        const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
+        uint16_t *stg = (uint16_t *)(ring + q.nst * q.stage + (warp - WS_EPI0) * WS_STG);
         int i = 0;
-        for (int t = tb; t < te && !S.abort; t++, i++) {
+        for (int t = tb; t < te && !S.abort; t += ts, i++) {
             const int b = i & 1, ub = i >> 1;
-            const int f0 = (t / q.ntok) * TNF, fh = f0 + half * (TNF / 2);
             bool ok = !ws_needs_table(MODE) || mbar_wait(&S.tabfull[b], ub & 1);
-            ok = ok && ws_epilogue<DUAL, MODE, TNF>(g, S, S.tab[b], &S.tfull[b], ub & 1,
-                                                    tmem + lanes + (uint32_t)(b * NACC * TNF), r,
-                                                    (t % q.ntok) * WS_TM, f0, fh, stg);
+            ok = ok && ws_epilogue<DUAL, MODE, TNB>(g, S, S.tab[b], &S.tfull[b], ub & 1,
+                                                    tmem + lanes + (uint32_t)(b * NACC * TNB), tile_f(t) * TM,
+                                                    tile_m(t) * TNB, quarter, cb, stg);
             if (!ok) S.abort = 1;
             fence_before();
             __syncwarp();
@@ -447,17 +408,17 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
     if (warp == 1) tmem_free(tmem, WS_TCOLS);
 }
 
-// Widest tile of a form: 128 features for the dual form (two accumulators
+// Widest tile of a form: 128 tokens for the dual form (two accumulators
 // per buffer) and the residual modes (old values in registers), else 256.
 __host__ __device__ constexpr int ws_max_tn(bool dual, int mode)
 {
     return (dual || mode == EPI_RESID || mode == EPI_RESID_BASE) ? 128 : 256;
 }
 
-template <bool DUAL, int MODE, int TNF>
+template <bool DUAL, int MODE, int TNB>
 bool ws_attr()
 {
-    return cudaFuncSetAttribute(k_gemm_ws<DUAL, MODE, TNF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_gemm_ws<DUAL, MODE, TNB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 WS_DYN + WS_EPI_WARPS * WS_STG + 1024) == cudaSuccess;
 }
 
@@ -479,23 +440,23 @@ int ws_sms()
     return n;
 }
 
-template <bool DUAL, int MODE, int TNF>
+template <bool DUAL, int MODE, int TNB>
 cudaError_t ws_launch(const CUtensorMap &tw, const CUtensorMap &tw2, const CUtensorMap &tx, const GemmArgs &g,
                       cudaStream_t s)
 {
     const int sms = ws_sms();
-    const WsGeom q = ws_geom(TNF, DUAL, g.M, g.N, g.K, sms);
+    const WsGeom q = ws_geom(TNB, DUAL, g.M, g.N, g.K, sms);
     dim3 grid(q.grid), block(WS_THREADS);
-    return launch_pdl(k_gemm_ws<DUAL, MODE, TNF>, grid, block, (size_t)ws_smem_bytes(q, g.K), s, tw, tw2, tx, g, sms,
+    return launch_pdl(k_gemm_ws<DUAL, MODE, TNB>, grid, block, (size_t)ws_smem_bytes(q, g.K), s, tw, tw2, tx, g, sms,
                       g.status);
 }
 
 template <bool DUAL, int MODE>
-cudaError_t ws_launch_tn(int tnf, const CUtensorMap &tw, const CUtensorMap &tw2, const CUtensorMap &tx,
+cudaError_t ws_launch_tn(int tnb, const CUtensorMap &tw, const CUtensorMap &tw2, const CUtensorMap &tx,
                          const GemmArgs &g, cudaStream_t s)
 {
-    if (tnf == 64) return ws_launch<DUAL, MODE, 64>(tw, tw2, tx, g, s);
-    if (tnf == 128) return ws_launch<DUAL, MODE, 128>(tw, tw2, tx, g, s);
+    if (tnb == 64) return ws_launch<DUAL, MODE, 64>(tw, tw2, tx, g, s);
+    if (tnb == 128) return ws_launch<DUAL, MODE, 128>(tw, tw2, tx, g, s);
     return ws_launch<DUAL, MODE, ws_max_tn(DUAL, MODE)>(tw, tw2, tx, g, s);
 }
 
@@ -527,26 +488,23 @@ bool gemm_ws_supported(const GemmArgs &g)
             m == EPI_HEADS || m == EPI_SWIGLU);
 }
 
-// Features per tile: the width with the least estimated time of the busiest
-// CTA.  A tile's time is the slower of its MMA chain (one thread issues an
-// MMA in ~84 cycles at N <= 128 and ~124 at N = 256, the tensor pipe's rate)
-// and its copies (~110 GB/s per SM out of L2: the token chunks, plus the
-// weight chunks unless they are resident); the epilogue overlaps the next
-// tile.  Resident weights cost one copy per CTA.  Ties go to the wider tile.
-int gemm_ws_tile_features(int N, int M, int K, bool dual, bool resid)
+// Tokens per tile: the width with the least estimated time of the busiest
+// CTA -- its tiles x the slower of a tile's MMAs and epilogue (they overlap
+// across tiles), plus the faster of the two once.  One thread issues an MMA
+// in about the same time for any N up to 128 and in ~1.5x that at N = 256
+// (the tensor pipe's rate); the epilogue grows with the tile's tokens.
+// Ties go to the wider tile (fewer weight re-reads).
+int gemm_ws_tile_tokens(int N, int M, int K, bool dual, bool resid)
 {
     const int sms = ws_sms();
     int best = 64;
     double best_cost = 1e30;
-    for (int tnf = ws_max_tn(dual, resid ? EPI_RESID : EPI_STORE); tnf >= 64; tnf /= 2) {
-        const WsGeom q = ws_geom(tnf, dual, M, N, K, sms);
+    for (int tnb = ws_max_tn(dual, resid ? EPI_RESID : EPI_STORE); tnb >= 64; tnb /= 2) {
+        const WsGeom q = ws_geom(tnb, dual, M, N, K, sms);
         const int tiles = (q.ntiles + q.grid - 1) / q.grid;
-        const double mma_us = (K / 16.0) * (tnf == 256 ? 124.0 : 84.0) * (dual ? 1.3 : 1.0) / 2000.0;
-        const double bytes = (double)WS_XCHUNK * (K / KC) + (q.wres ? 0.0 : (double)q.wchunk * (K / KC));
-        const double load_us = bytes / 110e3;
-        const double cost = tiles * (mma_us > load_us ? mma_us : load_us) +
-                            (q.wres ? (double)q.wchunk * (K / KC) / 110e3 : 0.0);
-        if (cost < best_cost - 1e-9) { best_cost = cost; best = tnf; }
+        const double mma = (K / 384.0) * (tnb == 256 ? 1.5 : 1.0), epi = tnb / 128.0;
+        const double cost = tiles * (mma > epi ? mma : epi) + (mma < epi ? mma : epi);
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = tnb; }
     }
     return best;
 }
@@ -555,21 +513,21 @@ bool gemm_ws(const GemmArgs &g, cudaStream_t s)
 {
     if (!gemm_ws_supported(g)) return false;
     const bool dual = g.epi.mode == EPI_SWIGLU;
-    const int tnf = gemm_ws_tile_features(g.N, g.M, g.K, dual, g.epi.mode == EPI_RESID || g.epi.mode == EPI_RESID_BASE);
+    const int tnb = gemm_ws_tile_tokens(g.N, g.M, g.K, dual, g.epi.mode == EPI_RESID || g.epi.mode == EPI_RESID_BASE);
     CUtensorMap tw, tw2, tx;
-    if (!gemm_tensor_map(g.Wt, g.N, g.K, g.K, tnf, &tw)) return false;
-    if (dual && !gemm_tensor_map(g.Wt2, g.N, g.K, g.K, tnf, &tw2)) return false;
+    if (!gemm_tensor_map(g.Wt, g.N, g.K, g.K, TM, &tw)) return false;
+    if (dual && !gemm_tensor_map(g.Wt2, g.N, g.K, g.K, TM, &tw2)) return false;
     if (!dual) tw2 = tw;
-    if (!gemm_tensor_map(g.A, g.M, g.K, g.lda, WS_TM, &tx)) return false;
+    if (!gemm_tensor_map(g.A, g.M, g.K, g.lda, tnb, &tx)) return false;
     cudaError_t e;
     switch (g.epi.mode) {
-    case EPI_SWIGLU: e = ws_launch_tn<true, EPI_SWIGLU>(tnf, tw, tw2, tx, g, s); break;
-    case EPI_STORE: e = ws_launch_tn<false, EPI_STORE>(tnf, tw, tw2, tx, g, s); break;
-    case EPI_QKV: e = ws_launch_tn<false, EPI_QKV>(tnf, tw, tw2, tx, g, s); break;
-    case EPI_RESID: e = ws_launch_tn<false, EPI_RESID>(tnf, tw, tw2, tx, g, s); break;
-    case EPI_RESID_BASE: e = ws_launch_tn<false, EPI_RESID_BASE>(tnf, tw, tw2, tx, g, s); break;
-    case EPI_BIAS_SILU: e = ws_launch_tn<false, EPI_BIAS_SILU>(tnf, tw, tw2, tx, g, s); break;
-    case EPI_HEADS: e = ws_launch_tn<false, EPI_HEADS>(tnf, tw, tw2, tx, g, s); break;
+    case EPI_SWIGLU: e = ws_launch_tn<true, EPI_SWIGLU>(tnb, tw, tw2, tx, g, s); break;
+    case EPI_STORE: e = ws_launch_tn<false, EPI_STORE>(tnb, tw, tw2, tx, g, s); break;
+    case EPI_QKV: e = ws_launch_tn<false, EPI_QKV>(tnb, tw, tw2, tx, g, s); break;
+    case EPI_RESID: e = ws_launch_tn<false, EPI_RESID>(tnb, tw, tw2, tx, g, s); break;
+    case EPI_RESID_BASE: e = ws_launch_tn<false, EPI_RESID_BASE>(tnb, tw, tw2, tx, g, s); break;
+    case EPI_BIAS_SILU: e = ws_launch_tn<false, EPI_BIAS_SILU>(tnb, tw, tw2, tx, g, s); break;
+    case EPI_HEADS: e = ws_launch_tn<false, EPI_HEADS>(tnb, tw, tw2, tx, g, s); break;
     default: return false;
     }
     return e == cudaSuccess;

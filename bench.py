@@ -64,6 +64,8 @@ def parse(argv=None):
                     help="projections of the main leg: bf16, or fp8 (E4M3 block projections; the fp8 leg is then skipped)")
     ap.add_argument("--fp8-steps", type=int, default=2,
                     help="timed steps of the same I-frame workload with E4M3 block projections (0: skip)")
+    ap.add_argument("--cyclic-steps", type=int, default=2,
+                    help="timed steps of the cyclic s = 4 schedule leg (0: skip)")
     ap.add_argument("--engine", choices=["auto", "graph", "persistent"], default="auto",
                     help="decode engine: one cooperative kernel over all steps, or per-phase kernels in CUDA graphs")
     return ap.parse_args(argv)
@@ -329,6 +331,67 @@ def fp8_run(args, dev, timed, cfg, w, ys, zs, B):
     return out, mu, sg
 
 
+def cyclic_run(args, dev, timed, w, ys, zs, B):
+    """The paper's own schedule (cyclic s = 4 mask, Fig. 2a): the same model
+    sizes and frames, 4 steps per frame of 2040 positions each.  Frames/s at
+    B frames per call, single-frame latency, and the projections' tensor
+    rate from one instrumented step (about 261 k tokens per launch at 128
+    frames)."""
+    import torch
+    from paper_2605_20977_gb300 import psw, synth
+    cfg = synth.config("i1080_cyc")
+    ctx = psw.Context(cfg, w, precision=psw.PSW_BF16)
+    fd = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_WAVEFRONT)
+    cap = ctx.bitstream_capacity(cfg.H, cfg.W)
+    enc = ctx.seq_create(cfg.H, cfg.W)
+    bss, lens = [], []
+    for b in range(B):
+        enc.reset()
+        bs = torch.zeros(cap, dtype=torch.uint8, device=dev)
+        lens.append(enc.encode_params(fd, ys[b], zs[b], bitstream=bs))
+        bss.append(bs)
+    enc.close()
+    decs = [ctx.seq_create(cfg.H, cfg.W) for _ in range(B)]
+    outs = [torch.zeros_like(y) for y in ys]
+
+    def step(n):
+        for q in decs[:n]:
+            q.reset()
+        ctx.decode_batch(decs[:n], [fd] * n, bss[:n], lens[:n], zs[:n], outs[:n])
+
+    step(B)                                     # records the graphs
+    ms = timed(lambda: step(B), args.cyclic_steps)
+    for b in range(B):
+        if not torch.equal(outs[b], ys[b]):
+            raise RuntimeError("cyclic decode differs")
+    step(1)
+    lat = timed(lambda: step(1), max(2, args.cyclic_steps))
+    ctx.profile_begin()
+    step(B)
+    stats = ctx.profile_end()
+    pk, pk_kind = peaks()
+    g = next((s_ for s_ in stats if s_["name"] == "gemm_tc"), None)
+    nrm = next((s_ for s_ in stats if s_["name"] == "rmsnorm"), None)
+    out = {"value": B * 1e3 / float(np.mean(ms)), "unit": "frames/s", "frames_per_step": B,
+           "ms_per_step": float(np.mean(ms)), "steps_per_frame": 4,
+           "latency_one_frame": {"ms_per_frame": float(np.mean(lat)), "frames_per_s": 1e3 / float(np.mean(lat))},
+           "workload": "1080p I-frames 68x120x192 with the cyclic s = 4 mask (Fig. 2a), same model sizes and "
+                       "frames as the headline, BF16",
+           "classes": {s_["name"]: {"ms": round(s_["ms"], 3), "launches": s_["launches"],
+                                    "gflop": round(s_["flops"] / 1e9, 2)} for s_ in stats}}
+    if g:
+        t = g["ms"] + (nrm["ms"] if nrm else 0.0)
+        ach = g["flops"] / (t / 1e3) / 1e12
+        out["projections"] = {"achieved": ach, "unit": "TFLOP/s", "peak": pk["bf16_tflops_sustained"],
+                              "frac": ach / pk["bf16_tflops_sustained"],
+                              "timing": "CUDA events, projection launches plus the row normalisations feeding them",
+                              "tokens_per_launch": B * 2040}
+    for q in decs:
+        q.close()
+    ctx.close()
+    return out
+
+
 def job_rate(units_per_rank, local_seconds, world, device):
     """Whole-job throughput of `world` replicas: every rank's units over the
     slowest rank's time (all-reduce MAX).  Returns (units / s, max seconds)."""
@@ -488,8 +551,12 @@ def run_ours(args, rank: int, world: int, local: int):
     pk, pk_kind = peaks()
     dom = max(stats, key=lambda s: s["ms"])
     tot_ms = sum(s["ms"] for s in stats)
+    nrm = next((s for s in stats if s["name"] == "rmsnorm"), None)
     if dom["name"].startswith("gemm"):
-        achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
+        # the projections' time includes the row normalisations that feed
+        # their wide launches (the operand a tile would otherwise build)
+        dom_ms = dom["ms"] + (nrm["ms"] if nrm and dom["name"] == "gemm_tc" else 0.0)
+        achieved = dom["flops"] / (dom_ms / 1e3) / 1e12
         peak, unit, bound = pk["bf16_tflops_sustained"], "TFLOP/s", "tensor"
     else:
         achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
@@ -499,7 +566,7 @@ def run_ours(args, rank: int, world: int, local: int):
         # (projections and attention of every position) over its duration
         achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
         peak, unit, bound = pk["bf16_tflops_sustained"], "TFLOP/s", "tensor"
-    kname = {"gemm_tc": "k_gemm_tc", "attention": "k_attention", "heads": "k_heads", "rmsnorm": "k_rmsnorm",
+    kname = {"gemm_tc": "k_gemm_ws", "attention": "k_attention", "heads": "k_heads", "rmsnorm": "k_rmsnorm",
              "rans": "k_rans_dec_step", "embed": "k_embed_latent", "gemm_simt": "k_gemm_simt",
              "persistent": "k_persist"}.get(dom["name"])
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
@@ -508,7 +575,8 @@ def run_ours(args, rank: int, world: int, local: int):
             "share_of_kernel_time": dom["ms"] / tot_ms,
             "peak_source": ("measured, MEASURED_PEAKS.json (sustained bf16 for a kernel inside a long step)"
                             if pk_kind == "measured" else "fallback"),
-            "timing": "CUDA events around each launch of one instrumented step (direct launches, same engine)",
+            "timing": ("CUDA events around each launch of one instrumented step (direct launches, same engine); "
+                       "projection time includes the row normalisations feeding the wide launches"),
             "classes": {s["name"]: {"ms": round(s["ms"], 3), "launches": s["launches"],
                                     "gflop": round(s["flops"] / 1e9, 2)} for s in stats}}
 
@@ -556,6 +624,11 @@ def run_ours(args, rank: int, world: int, local: int):
     if rank == 0 and args.fp8_steps > 0 and args.precision == "bf16":
         fp8, mu8, sg8 = fp8_run(args, dev, timed, cfg, w, ys, zs, B)
 
+    # the paper's own cyclic s = 4 schedule on the same frames
+    cyclic = None
+    if rank == 0 and args.cyclic_steps > 0 and args.precision == "bf16":
+        cyclic = cyclic_run(args, dev, timed, w, ys, zs, B)
+
     # rate: GPU parameters vs the FP64 oracle on the sample rows
     rate = {"bits_per_symbol": ctx.rate(ys[0], mu0, sg0) / ys[0].numel(),
             "container_bits_per_symbol": 8.0 * lens[0] / ys[0].numel()}
@@ -595,7 +668,7 @@ def run_ours(args, rank: int, world: int, local: int):
             "gpu_launches": int(round(launches)),
             "latency_one_frame": lat,
             "roofline": roof, "raster": raster, "speedup_vs_raster": speedup,
-            "rate": rate, "clocks": clk, "cpu_baseline": cpu, "pframe": pframe, "fp8": fp8}
+            "rate": rate, "clocks": clk, "cpu_baseline": cpu, "pframe": pframe, "fp8": fp8, "cyclic": cyclic}
     print(json.dumps(line), flush=True)
     return 0
 

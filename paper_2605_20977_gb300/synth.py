@@ -77,6 +77,7 @@ def config(name: str) -> ModelConfig:
               cross-attention over the current and 2 previous frames
     tiny_p    tiny with the temporal path (2 context blocks)
     tiny_cyc  tiny with the cyclic s = 4 mask
+    i1080_cyc i1080 with the cyclic s = 4 mask (4 steps per frame)
     """
     if name == "tiny":
         return ModelConfig(H=8, W=12, C=64, Hh=4, Wh=6, Ch=32, r=2, d=128, nh=4,
@@ -90,6 +91,9 @@ def config(name: str) -> ModelConfig:
     if name == "i1080":
         return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
                            F=ffn_width(384), L=8, k=7)
+    if name == "i1080_cyc":
+        return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
+                           F=ffn_width(384), L=8, k=7, mask=1)
     if name == "p1080":
         return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
                            F=ffn_width(384), L=8, k=7, temporal=1, Lc=8, Tf=3)

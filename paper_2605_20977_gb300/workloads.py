@@ -178,12 +178,15 @@ def run_serve(rate=200.0, window=0.1, per_grid=2, gop=16, budget_gb=120.0, max_b
     return out
 
 
-def run_encode(nframes=4, dev=None, precision="bf16"):
+def run_encode(nframes=4, dev=None, precision="bf16", rows=0):
     """Encode nframes 1080p I-frames one after another (masked pass plus
-    rANS); the first is a warm-up.  Returns frames/s of the rest."""
+    rANS); the first is a warm-up.  Returns frames/s of the rest.  rows > 0:
+    the top `rows` rows of the frame (rows x 120 tokens per launch, e.g. 34
+    for the mean launch of a 128-frame wavefront decode)."""
     import torch
-    cfg = synth.config("i1080")
-    ctx = psw.Context(cfg, synth.weights(cfg), precision=PRECISIONS[precision])
+    base = synth.config("i1080")
+    cfg = base.with_grid(rows, base.W) if rows else base
+    ctx = psw.Context(base, synth.weights(base), precision=PRECISIONS[precision])
     seq = ctx.seq_create(cfg.H, cfg.W)
     fr = synth.frames(cfg, 1, seed=1002)
     fd = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_WAVEFRONT)
@@ -201,8 +204,10 @@ def run_encode(nframes=4, dev=None, precision="bf16"):
     seq.close()
     ctx.close()
     n = max(0, nframes - 1)
-    return {"workload": f"encoder masked pass + rANS, 1080p I-frames 68x120x192, {precision.upper()}",
-            "frames": n, "frames_per_s": n / dt if n else None, "tflops": n * 505.0 / dt / 1e3 if n else None}
+    gflop = 505.0 * cfg.H / base.H
+    return {"workload": f"encoder masked pass + rANS, 1080p I-frame model, {cfg.H}x{cfg.W}x{cfg.C} frames, "
+            f"{precision.upper()}", "frames": n, "frames_per_s": n / dt if n else None,
+            "tflops": n * gflop / dt / 1e3 if n else None}
 
 
 def main():
@@ -213,6 +218,7 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--window", type=float, default=0.1)
     ap.add_argument("--no-unbatched", action="store_true")
+    ap.add_argument("--rows", type=int, default=0, help="encode: rows of the 68-row frame (0: all)")
     ap.add_argument("--engines", default="graph",
                     help="serve: decode engines of the batched arm, comma separated (persistent, graph)")
     ap.add_argument("--precision", choices=sorted(PRECISIONS), default=None,
@@ -224,7 +230,7 @@ def main():
     if args.what == "mixed":
         res = run_mixed(args.seqs, args.frames, dev=dev, precision=args.precision or "bf16")
     elif args.what == "encode":
-        res = run_encode(args.frames, dev=dev, precision=args.precision or "bf16")
+        res = run_encode(args.frames, dev=dev, precision=args.precision or "bf16", rows=args.rows)
     else:
         res = run_serve(args.rate, args.window, dev=dev, unbatched=not args.no_unbatched,
                         precision=args.precision or "fp8", engines=tuple(args.engines.split(",")))

@@ -154,10 +154,11 @@ def test_schedule_step_counts():
     _, start = O.schedule(c, 1)
     assert len(start) - 1 == 8160
     # cyclic s = 4: four steps regardless of resolution (Sec. 2, Sec. 3.2)
-    for nm in ("tiny_cyc",):
+    for nm in ("tiny_cyc", "i1080_cyc"):
         cc = synth.config(nm)
         assert len(O.schedule(cc, 0)[1]) - 1 == 4
-        assert len(O.schedule(cc.with_grid(68, 120), 0)[1]) - 1 == 4
+        _, st = O.schedule(cc.with_grid(68, 120), 0)
+        assert len(st) - 1 == 4 and np.diff(st).tolist() == [2040] * 4
 
 
 # ----------------------------------------------------------- model

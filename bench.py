@@ -184,6 +184,23 @@ class OracleSample:
                 f"{secs:.2f} s per crop, extrapolated to a frame by positions")
 
 
+def oracle_single_thread(rows: int = 1):
+    """The oracle's decode of the top `rows` rows timed on one host thread
+    (a child process with OMP_NUM_THREADS=1, set before the OpenMP runtime
+    starts).  Returns (frames/s extrapolated by positions, sample text) or
+    None if the child fails."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; s = bench.OracleSample(%d); "
+            "t = s.time_decode(); print(json.dumps([t, s.npos, s.cfg.H * s.cfg.W, s.threads]))" % (ROOT, rows))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        t, npos, hw, threads = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    return (npos / hw) / t, (f"FP64 oracle wavefront decode (rANS included) of the top {rows} row(s) "
+                                     f"({npos} positions) on {threads} thread: {t:.2f} s, extrapolated by positions")
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank: int):
@@ -639,6 +656,9 @@ def run_ours(args, rank: int, world: int, local: int):
         frac = smp.npos / (cfg.H * cfg.W)
         cpu = {"value": frac / secs, "unit": "frames/s", "cores": smp.threads, "kind": "oracle",
                "sample": smp.describe(secs)}
+        one = oracle_single_thread(1)
+        if one:
+            cpu["single_thread"] = {"value": one[0], "unit": "frames/s", "cores": 1, "sample": one[1]}
         R = args.cpu_rows
         r_gpu = smp.O.rate_bits(smp.y[0], mu0[:R].double().cpu().numpy(), sg0[:R].double().cpu().numpy())
         r_64 = smp.O.rate_bits(smp.y[0], smp.mu, smp.sg)

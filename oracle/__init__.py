@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
 class _Cfg(ct.Structure):
     _fields_ = [(n, ct.c_int) for n in
                 ("H", "W", "C", "Hh", "Wh", "Ch", "r", "d", "nh", "F", "L", "k",
-                 "temporal", "Lc", "Tf", "mask")]
+                 "temporal", "Lc", "Tf", "mask", "Llrp")]
 
 
 def _load():
@@ -74,6 +74,7 @@ def _load():
             lib.or_rans_encode.restype = ct.c_long
             lib.or_rans_decode.argtypes = [ct.c_int] * 4 + [P, P, ct.c_int, P, P, P, ct.c_long, P]
             lib.or_run.argtypes = [ct.POINTER(_Cfg), P, ct.c_int, P, P, ct.c_int, ct.c_int, P, P, P, P]
+            lib.or_run_lrp.argtypes = [ct.POINTER(_Cfg), P, ct.c_int, P, P, ct.c_int, ct.c_int, P, P, P, P, P]
             lib.or_num_threads.restype = ct.c_int
             _lib = lib
     return _lib
@@ -85,7 +86,7 @@ def _p(a: np.ndarray):
 
 def _cfg(c) -> _Cfg:
     d = c if isinstance(c, dict) else c.as_dict()
-    return _Cfg(**{k: int(d[k]) for k, _ in _Cfg._fields_})
+    return _Cfg(**{k: int(d.get(k, 0)) for k, _ in _Cfg._fields_})
 
 
 def num_threads() -> int:
@@ -237,12 +238,13 @@ def rans_decode(c, sched: int, idx, m, bs: bytes):
 
 # ---------------------------------------------------------------- model
 
-def run(c, w, y, z, driver: int = 0, sched: int = 0, bitstreams=None):
+def run(c, w, y, z, driver: int = 0, sched: int = 0, bitstreams=None, with_eps: bool = False):
     """Run the context model over a sequence (see or_run in psw_oracle.c).
 
     w: flat weights (float64 copy made); y: [nf][H][W][C] int16 (for driver 2
     it receives the decoded latents); z: [nf][Hh][Wh][Ch] int16.
-    Returns (mu, sigma) float64 [nf][H][W][C]."""
+    Returns (mu, sigma) float64 [nf][H][W][C], and with with_eps (a model
+    with an LRP Transformer) also each frame's residual eps (or_run_lrp)."""
     w = np.ascontiguousarray(w, np.float64)
     if w.size != weights_count(c):
         raise ValueError(f"weights: {w.size} != {weights_count(c)}")
@@ -255,14 +257,16 @@ def run(c, w, y, z, driver: int = 0, sched: int = 0, bitstreams=None):
         keep = bufs
         bsp = (ct.c_void_p * nf)(*[b.ctypes.data for b in bufs])
         lens = np.array([len(b) for b in bufs], np.int64)
-    rc = _load().or_run(ct.byref(_cfg(c)), _p(w), nf, _p(y), _p(z), driver, sched,
-                        bsp, _p(lens) if lens is not None else None, _p(mu), _p(sg))
+    eps = np.zeros(y.shape, np.float64) if with_eps else None
+    rc = _load().or_run_lrp(ct.byref(_cfg(c)), _p(w), nf, _p(y), _p(z), driver, sched,
+                            bsp, _p(lens) if lens is not None else None, _p(mu), _p(sg),
+                            _p(eps) if with_eps else None)
     del keep
     if rc == -2:
         raise ValueError("corrupt bitstream")
     if rc != 0:
         raise MemoryError("oracle allocation failed")
-    return mu, sg
+    return (mu, sg, eps) if with_eps else (mu, sg)
 
 
 def encode_frames(c, w, y, z, sched: int = 0):

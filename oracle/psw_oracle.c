@@ -62,6 +62,7 @@ typedef struct {
     int temporal;         /* 1: Context Transformer + temporal cross-attn    */
     int Lc, Tf;           /* Context Transformer blocks, frames in window    */
     int mask;             /* 0: l = 2i+j (+ raster clause); 1: cyclic s = 4  */
+    int Llrp;             /* LRP Transformer blocks (0: none)                */
 } or_cfg;
 
 typedef struct {
@@ -84,6 +85,9 @@ typedef struct {
     or_accw acc;
     long g_head, W1m, b1m, W2m, W1s, b1s, W2s;
     long gamma_mu, beta_mu, gamma_sig, beta_sig;
+    long lrp_g_rep, lrp_W_rep, lrp_gamma_y, lrp_W_y, lrp_b_in;   /* LRP Transformer (-1: none) */
+    or_blk lrp[OR_MAXL];
+    long lrp_g_out, lrp_W_eps, lrp_b_eps;
     long total;
 } or_layout;
 
@@ -144,13 +148,27 @@ static void make_layout(const or_cfg *c, or_layout *lay)
     lay->W1s = take(&cur, dd); lay->b1s = take(&cur, c->d); lay->W2s = take(&cur, (long)c->d * c->C);
     lay->gamma_mu = take(&cur, c->C); lay->beta_mu = take(&cur, c->C);
     lay->gamma_sig = take(&cur, c->C); lay->beta_sig = take(&cur, c->C);
+    if (c->Llrp > 0) {
+        lay->lrp_g_rep = take(&cur, c->d);
+        lay->lrp_W_rep = take(&cur, dd);
+        lay->lrp_gamma_y = take(&cur, c->C);
+        lay->lrp_W_y = take(&cur, (long)c->C * c->d);
+        lay->lrp_b_in = take(&cur, c->d);
+        for (int l = 0; l < c->Llrp; l++) layout_block(&cur, c, &lay->lrp[l], 0, 0);
+        lay->lrp_g_out = take(&cur, c->d);
+        lay->lrp_W_eps = take(&cur, (long)c->d * c->C);
+        lay->lrp_b_eps = take(&cur, c->C);
+    } else {
+        lay->lrp_g_rep = lay->lrp_W_rep = lay->lrp_gamma_y = lay->lrp_W_y = lay->lrp_b_in = -1;
+        lay->lrp_g_out = lay->lrp_W_eps = lay->lrp_b_eps = -1;
+    }
     lay->total = cur;
 }
 
 long or_weights_count(const or_cfg *c)
 {
     or_layout lay;
-    if (c->L > OR_MAXL || c->Lc > OR_MAXL) return -1;
+    if (c->L > OR_MAXL || c->Lc > OR_MAXL || c->Llrp > OR_MAXL) return -1;
     make_layout(c, &lay);
     return lay.total;
 }
@@ -605,6 +623,75 @@ static void run_context(or_state *s, const int16_t *yprev)
     free(g);
 }
 
+/* LRP Transformer of a coded frame (Sec. 3.1, the latent residual
+ * prediction): every position's token concatenates the model's final
+ * representation there (the Spatial Module 2 stream, the heads' input),
+ * normalised, with the channel-scaled quantised latent, projected to the
+ * model width; Llrp blocks of window self-attention over the whole k x k
+ * window (spatially unmasked: the frame is fully decoded) and SwiGLU; then
+ * RMSNorm and a projection to the C channels give the residual eps.  Every
+ * block computes the keys and values of all positions before any position
+ * is updated.  The window stays within the current frame, so the pass is
+ * trivially causal in time. */
+static void run_lrp(or_state *s, const int16_t *yf, double *eps)
+{
+    const or_cfg *c = s->c;
+    int d = c->d, C = c->C, kk = c->k * c->k, HW = s->HW;
+    long hd = (long)HW * d;
+    double *u = zalloc(hd), *K = zalloc(hd), *V = zalloc(hd);
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int p = 0; p < HW; p++) {
+        double *n = zalloc(d), *t = zalloc(d), *yc = zalloc(C), *up = u + (long)p * d;
+        or_rmsnorm(s->x2 + (long)p * d, WP(s->lay.lrp_g_rep), d, n);
+        or_matvec(n, WP(s->lay.lrp_W_rep), d, d, up);
+        for (int ch = 0; ch < C; ch++) yc[ch] = WP(s->lay.lrp_gamma_y)[ch] * (double)yf[(long)p * C + ch];
+        or_matvec(yc, WP(s->lay.lrp_W_y), C, d, t);
+        for (int e = 0; e < d; e++) up[e] += t[e] + WP(s->lay.lrp_b_in)[e];
+        free(n); free(t); free(yc);
+    }
+    for (int l = 0; l < c->Llrp; l++) {
+        const or_blk *bw = &s->lay.lrp[l];
+        #pragma omp parallel for schedule(dynamic, 4)
+        for (int p = 0; p < HW; p++) {
+            double *n = zalloc(d);
+            or_rmsnorm(u + (long)p * d, WP(bw->g_attn), d, n);
+            or_matvec(n, WP(bw->Wq), d, d, s->q + (long)p * d);
+            or_matvec(n, WP(bw->Wk), d, d, K + (long)p * d);
+            or_matvec(n, WP(bw->Wv), d, d, V + (long)p * d);
+            free(n);
+        }
+        #pragma omp parallel for schedule(dynamic, 4)
+        for (int p = 0; p < HW; p++) {
+            int *idx = (int *)malloc(sizeof(int) * kk), *off = (int *)malloc(sizeof(int) * kk);
+            const double **Kp = (const double **)malloc(sizeof(double *) * kk);
+            const double **Vp = (const double **)malloc(sizeof(double *) * kk);
+            double *bias = zalloc((long)kk * c->nh), *o = zalloc(d), *t = zalloc(d), *n = zalloc(d);
+            double *up = u + (long)p * d;
+            int nk = or_window_keys(c, -1, p, idx, off);
+            for (int j = 0; j < nk; j++) {
+                Kp[j] = K + (long)idx[j] * d; Vp[j] = V + (long)idx[j] * d;
+                for (int h = 0; h < c->nh; h++) bias[(long)j * c->nh + h] = WP(bw->bias)[(long)h * kk + off[j]];
+            }
+            or_attend(s->q + (long)p * d, nk, Kp, Vp, bias, c->nh, d, o);
+            or_matvec(o, WP(bw->Wo), d, d, t);
+            for (int e = 0; e < d; e++) up[e] += t[e];
+            or_rmsnorm(up, WP(bw->g_ffn), d, n);
+            or_swiglu(n, WP(bw->Wg), WP(bw->Wu), WP(bw->Wd), d, c->F, t);
+            for (int e = 0; e < d; e++) up[e] += t[e];
+            free(idx); free(off); free(Kp); free(Vp); free(bias); free(o); free(t); free(n);
+        }
+    }
+    #pragma omp parallel for schedule(dynamic, 4)
+    for (int p = 0; p < HW; p++) {
+        double *n = zalloc(d), *ep = eps + (long)p * C;
+        or_rmsnorm(u + (long)p * d, WP(s->lay.lrp_g_out), d, n);
+        or_matvec(n, WP(s->lay.lrp_W_eps), d, C, ep);
+        for (int ch = 0; ch < C; ch++) ep[ch] += WP(s->lay.lrp_b_eps)[ch];
+        free(n);
+    }
+    free(u); free(K); free(V);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Schedules                                                                 */
 /* ------------------------------------------------------------------------ */
@@ -985,12 +1072,15 @@ int or_rans_decode(int H, int W, int C, int schedule, const int *order, const in
  *             instead of revealed from y; y receives the decoded latents.
  * y: [nf][H][W][C]; z: [nf][Hh][Wh][Ch]; mu, sigma: [nf][H][W][C].
  * Returns 0, -1 on allocation failure, -2 on a corrupt bitstream. */
-int or_run(const or_cfg *c, const double *w, int nf, int16_t *y, const int16_t *z,
-           int driver, int sched, const uint8_t *const *bs, const long *lens,
-           double *mu, double *sigma)
+/* or_run, and for a model with an LRP Transformer (eps non-null) each
+ * frame's residual eps [nf][H][W][C] from its coded latents. */
+int or_run_lrp(const or_cfg *c, const double *w, int nf, int16_t *y, const int16_t *z,
+               int driver, int sched, const uint8_t *const *bs, const long *lens,
+               double *mu, double *sigma, double *eps)
 {
     or_state st, *s = &st;
-    if (c->L > OR_MAXL || c->Lc > OR_MAXL) return -1;
+    if (c->L > OR_MAXL || c->Lc > OR_MAXL || c->Llrp > OR_MAXL) return -1;
+    if (eps && c->Llrp <= 0) return -1;
     if (state_init(s, c, w)) { state_free(s); return -1; }
     int HW = s->HW, C = c->C;
     int *order = (int *)malloc(sizeof(int) * HW), *start = (int *)malloc(sizeof(int) * (HW + 1));
@@ -1051,10 +1141,18 @@ int or_run(const or_cfg *c, const double *w, int nf, int16_t *y, const int16_t *
         }
         memcpy(mu + (long)f * HW * C, s->mu, sizeof(double) * HW * C);
         memcpy(sigma + (long)f * HW * C, s->sigma, sizeof(double) * HW * C);
+        if (eps && rc == 0) run_lrp(s, yf, eps + (long)f * HW * C);
     }
     free(order); free(start); free(yvis);
     state_free(s);
     return rc;
+}
+
+int or_run(const or_cfg *c, const double *w, int nf, int16_t *y, const int16_t *z,
+           int driver, int sched, const uint8_t *const *bs, const long *lens,
+           double *mu, double *sigma)
+{
+    return or_run_lrp(c, w, nf, y, z, driver, sched, bs, lens, mu, sigma, NULL);
 }
 
 int or_num_threads(void)

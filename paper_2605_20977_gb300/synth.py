@@ -34,6 +34,8 @@ class ModelConfig:
     temporal   1: Context Transformer + temporal cross-attention (P-frames)
     Lc, Tf     Context Transformer blocks, frames in the temporal window
     mask       0: step label 2i+j; 1: cyclic s = 4 label
+    Llrp       LRP Transformer blocks (0: none): the latent residual
+               prediction over a decoded frame
     """
     H: int
     W: int
@@ -51,6 +53,7 @@ class ModelConfig:
     Lc: int = 0
     Tf: int = 3
     mask: int = 0
+    Llrp: int = 0
 
     def with_grid(self, H: int, W: int) -> "ModelConfig":
         d = asdict(self)
@@ -78,6 +81,8 @@ def config(name: str) -> ModelConfig:
     tiny_p    tiny with the temporal path (2 context blocks)
     tiny_cyc  tiny with the cyclic s = 4 mask
     i1080_cyc i1080 with the cyclic s = 4 mask (4 steps per frame)
+    tiny_lrp  tiny with a 2-block LRP Transformer
+    i1080_lrp i1080 with a 4-block LRP Transformer
     """
     if name == "tiny":
         return ModelConfig(H=8, W=12, C=64, Hh=4, Wh=6, Ch=32, r=2, d=128, nh=4,
@@ -91,6 +96,12 @@ def config(name: str) -> ModelConfig:
     if name == "i1080":
         return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
                            F=ffn_width(384), L=8, k=7)
+    if name == "tiny_lrp":
+        return ModelConfig(H=8, W=12, C=64, Hh=4, Wh=6, Ch=32, r=2, d=128, nh=4,
+                           F=ffn_width(128), L=2, k=5, Llrp=2)
+    if name == "i1080_lrp":
+        return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
+                           F=ffn_width(384), L=8, k=7, Llrp=4)
     if name == "i1080_cyc":
         return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
                            F=ffn_width(384), L=8, k=7, mask=1)
@@ -140,7 +151,8 @@ def weight_spec(c: ModelConfig) -> list:
 
     All projections are [in][out] (used as x . W).  Order: input embedding,
     hyperprior embedding, [Context Transformer], Spatial Module 1 blocks,
-    accumulator, Spatial Module 2 blocks, heads.
+    accumulator, Spatial Module 2 blocks, heads, [LRP Transformer: input
+    projections of the representation and of the latents, blocks, output].
     """
     d, C, Ch, F = c.d, c.C, c.Ch, c.F
     nblocks = 2 * c.L + 1 + (c.Lc if c.temporal else 0)
@@ -180,6 +192,17 @@ def weight_spec(c: ModelConfig) -> list:
           Tensor("W2s", (d, C), "lin", fan_in=d, matrix=True),
           Tensor("gamma_mu", (C,), "const", 2.0), Tensor("beta_mu", (C,), "const", 0.0),
           Tensor("gamma_sig", (C,), "const", 1.0), Tensor("beta_sig", (C,), "const", math.log(2.0))]
+    if c.Llrp:
+        s += [Tensor("lrp.g_rep", (d,), "gain"),
+              Tensor("lrp.W_rep", (d, d), "lin", fan_in=d, matrix=True),
+              Tensor("lrp.gamma_y", (C,), "const", 0.25),
+              Tensor("lrp.W_y", (C, d), "lin", fan_in=C, matrix=True),
+              Tensor("lrp.b_in", (d,), "bias")]
+        for l in range(c.Llrp):
+            s += _block(f"lrp{l}.", c, cross=False, tf_bias=False, nblocks=c.Llrp)
+        s += [Tensor("lrp.g_out", (d,), "gain"),
+              Tensor("lrp.W_eps", (d, C), "lin_res", value=0.1, fan_in=d, matrix=True),
+              Tensor("lrp.b_eps", (C,), "bias")]
     return s
 
 
@@ -227,9 +250,9 @@ def e4m3_tensor(t: Tensor) -> bool:
     """Whether an FP8 context stores projection t as E4M3 (one power-of-two
     scale per tensor): transformer-block projections whose input width K is
     a multiple of 128, at most 512 for a normalised input and 1024 for the
-    compact-row inputs of Wo, Wxo and Wd.  The latent embedding and the heads
-    stay in the compute dtype."""
-    if not t.matrix or t.name in ("W_in", "W1m", "W2m", "W1s", "W2s"):
+    compact-row inputs of Wo, Wxo and Wd.  The latent embedding, the heads
+    and the LRP Transformer stay in the compute dtype."""
+    if not t.matrix or t.name in ("W_in", "W1m", "W2m", "W1s", "W2s") or t.name.startswith("lrp"):
         return False
     K = t.shape[0]
     return K % 128 == 0 and K <= (1024 if t.name.split(".")[-1] in ("Wo", "Wxo", "Wd") else 512)

@@ -82,8 +82,10 @@ def ffn(x, Wg, Wu, Wd):
     return (silu(x @ Wg) * (x @ Wu)) @ Wd
 
 
-def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray):
-    """(mu, sigma) [nf, H, W, C] for a sequence, by the masked parallel pass."""
+def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray, with_eps: bool = False):
+    """(mu, sigma) [nf, H, W, C] for a sequence, by the masked parallel pass;
+    with with_eps also the LRP Transformer's residual eps of every frame
+    (full [HW x HW] attention under the unmasked window mask)."""
     P = split_weights(c, w)
     H, W, C, d, nh = c.H, c.W, c.C, c.d, c.nh
     HW = H * W
@@ -136,7 +138,7 @@ def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray):
             x = x + attention(qx, Kc, Vc, Mc, Bc, nh) @ P[pre + "Wxo"]
         return x + ffn(rms(x, P[pre + "g_ffn"]), P[pre + "Wg"], P[pre + "Wu"], P[pre + "Wd"])
 
-    mus, sigs = [], []
+    mus, sigs, epss = [], [], []
     for f in range(nf):
         ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
         zz = z[f][ii // c.r, jj // c.r].reshape(HW, c.Ch) * P["gamma_z"]
@@ -156,4 +158,16 @@ def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray):
         s = P["gamma_sig"] * (silu(n @ P["W1s"] + P["b1s"]) @ P["W2s"]) + P["beta_sig"]
         sig = np.exp(np.clip(s, np.log(0.11), np.log(256.0)))
         mus.append(mu.reshape(H, W, C)); sigs.append(sig.reshape(H, W, C))
+        if with_eps:
+            u = (rms(x2, P["lrp.g_rep"]) @ P["lrp.W_rep"] + (y[f].reshape(HW, C) * P["lrp.gamma_y"]) @ P["lrp.W_y"]
+                 + P["lrp.b_in"])
+            for l in range(c.Llrp):
+                pre = f"lrp{l}."
+                n = rms(u, P[pre + "g_attn"])
+                u = u + attention(n @ P[pre + "Wq"], n @ P[pre + "Wk"], n @ P[pre + "Wv"], win,
+                                  bias_of(P[pre + "bias"]), nh) @ P[pre + "Wo"]
+                u = u + ffn(rms(u, P[pre + "g_ffn"]), P[pre + "Wg"], P[pre + "Wu"], P[pre + "Wd"])
+            epss.append((rms(u, P["lrp.g_out"]) @ P["lrp.W_eps"] + P["lrp.b_eps"]).reshape(H, W, C))
+    if with_eps:
+        return np.stack(mus), np.stack(sigs), np.stack(epss)
     return np.stack(mus), np.stack(sigs)

@@ -174,8 +174,75 @@ def test_oracle_matches_dense_mask_formulation(name):
     assert np.max(np.abs(np.log(s0) - np.log(s1))) < 1e-11
 
 
+@pytest.mark.parametrize("grid", [None, (5, 7), (1, 9)])
+def test_lrp_oracle_matches_dense_mask_formulation(grid):
+    """The LRP Transformer's residual (Sec. 3.1): the oracle's per-position
+    window loops against full [HW x HW] attention under the unmasked window
+    mask, on the model's own representation; a full and two ragged grids."""
+    c = synth.config("tiny_lrp")
+    if grid:
+        c = c.with_grid(*grid)
+    w = synth.weights(c)
+    fr = synth.frames(c, 1, seed=13)
+    mu0, s0, e0 = O.run(c, w, fr.y, fr.z, driver=0, with_eps=True)
+    mu1, s1, e1 = dense_ref.run(c, w, fr.y, fr.z, with_eps=True)
+    assert np.max(np.abs(mu0 - mu1)) < 1e-11
+    assert np.max(np.abs(e0 - e1)) < 1e-11
+    # the LRP leaves the entropy model's parameters as they are
+    c0 = synth.config("tiny")
+    if grid:
+        c0 = c0.with_grid(*grid)
+    mu2, s2 = O.run(c0, w[:synth.weights_count(c0)], fr.y, fr.z, driver=0)
+    assert np.array_equal(mu0, mu2) and np.array_equal(s0, s2)
+
+
+def test_lrp_residual_is_the_same_after_decoding():
+    """Decoding the frame from its container (the wavefront schedule
+    revealing latents step by step) gives bit-for-bit the residual of the
+    masked pass: the LRP runs on the coded latents and final
+    representations only."""
+    c = synth.config("tiny_lrp")
+    w = synth.weights(c)
+    fr = synth.frames(c, 1, seed=14)
+    _, _, e0 = O.run(c, w, fr.y, fr.z, driver=0, with_eps=True)
+    bs, _, _ = O.encode_frames(c, w, fr.y, fr.z)
+    y = np.zeros_like(fr.y)
+    _, _, e2 = O.run(c, w, y, fr.z, driver=2, bitstreams=bs, with_eps=True)
+    assert np.array_equal(y, fr.y)
+    assert np.array_equal(e0, e2)
+
+
+def test_lrp_window_is_spatially_unmasked_and_local():
+    """Perturbing the latent at q: the entropy parameters move at a set S of
+    positions after q in raster order (within 2L+1 window radii: L Spatial
+    Module 1 blocks, the accumulator, L Spatial Module 2 blocks), and the
+    LRP residual moves exactly on the Llrp-radius Chebyshev dilation of
+    S and q (unmasked k x k windows, Llrp blocks, clipped at the border):
+    in every direction, positions before q included."""
+    c = synth.config("tiny_lrp").with_grid(20, 40)
+    w = synth.weights(c)
+    fr = synth.frames(c, 1, seed=15)
+    mu0, _, e0 = O.run(c, w, fr.y, fr.z, driver=0, with_eps=True)
+    qi, qj = 10, 20
+    y = fr.y.copy()
+    y[0, qi, qj, :] += 7
+    mu1, _, e1 = O.run(c, w, y, fr.z, driver=0, with_eps=True)
+    moved = np.abs(e1 - e0).max(axis=-1)[0] > 0
+    S = np.abs(mu1 - mu0).max(axis=-1)[0] > 0
+    R = (c.k - 1) // 2
+    ii, jj = np.meshgrid(np.arange(c.H), np.arange(c.W), indexing="ij")
+    rho, rq = ii * c.W + jj, qi * c.W + qj
+    G = (2 * c.L + 1) * R
+    assert S.any() and not S[(rho <= rq) | (np.abs(ii - qi) > G) | (np.abs(jj - qj) > G)].any()
+    reach = np.zeros_like(S)
+    for a, b in zip(*np.nonzero(S | (rho == rq))):
+        reach |= (np.abs(ii - a) <= c.Llrp * R) & (np.abs(jj - b) <= c.Llrp * R)
+    assert (~reach).any() and np.array_equal(moved, reach)
+    assert moved[(rho < rq)].any()
+
+
 def test_weight_layout_count_matches_generator():
-    for nm in ("tiny", "tiny_p", "i1080", "p1080"):
+    for nm in ("tiny", "tiny_p", "i1080", "p1080", "tiny_lrp", "i1080_lrp"):
         c = synth.config(nm)
         assert O.weights_count(c) == synth.weights_count(c)
 

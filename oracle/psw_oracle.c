@@ -154,7 +154,7 @@ static void make_layout(const or_cfg *c, or_layout *lay)
         lay->lrp_gamma_y = take(&cur, c->C);
         lay->lrp_W_y = take(&cur, (long)c->C * c->d);
         lay->lrp_b_in = take(&cur, c->d);
-        for (int l = 0; l < c->Llrp; l++) layout_block(&cur, c, &lay->lrp[l], 0, 0);
+        for (int l = 0; l < c->Llrp; l++) layout_block(&cur, c, &lay->lrp[l], 0, c->temporal != 0);
         lay->lrp_g_out = take(&cur, c->d);
         lay->lrp_W_eps = take(&cur, (long)c->d * c->C);
         lay->lrp_b_eps = take(&cur, c->C);
@@ -307,6 +307,7 @@ typedef struct {
     double *q;            /* per-position query scratch                      */
     double *XK, *XV;      /* temporal cross K/V: [2L][Tf slots][HW][d]        */
     double *CK, *CV;      /* context transformer K/V: [Lc][Tf slots][HW][d]   */
+    double *LK, *LV;      /* LRP Transformer K/V: [Llrp][Tf slots][HW][d]    */
     double *mu, *sigma;   /* [HW][C]                                        */
 } or_state;
 
@@ -327,6 +328,9 @@ static int state_init(or_state *s, const or_cfg *c, const double *w)
         s->XK = zalloc(hd * 2 * c->L * c->Tf); s->XV = zalloc(hd * 2 * c->L * c->Tf);
         s->CK = zalloc(hd * c->Lc * c->Tf); s->CV = zalloc(hd * c->Lc * c->Tf);
     }
+    if (c->Llrp > 0) {
+        s->LK = zalloc(hd * c->Llrp * c->Tf); s->LV = zalloc(hd * c->Llrp * c->Tf);
+    }
     return (s->x1 && s->K1 && s->V1 && s->eh && s->Ka && s->Va && s->x2 && s->K2 && s->V2 &&
             s->q && s->mu && s->sigma) ? 0 : -1;
 }
@@ -335,7 +339,7 @@ static void state_free(or_state *s)
 {
     free(s->x1); free(s->K1); free(s->V1); free(s->eh); free(s->Ka); free(s->Va);
     free(s->x2); free(s->K2); free(s->V2); free(s->q); free(s->mu); free(s->sigma);
-    free(s->XK); free(s->XV); free(s->CK); free(s->CV);
+    free(s->XK); free(s->XV); free(s->CK); free(s->CV); free(s->LK); free(s->LV);
 }
 
 #define WP(off) (s->w + (off))
@@ -624,21 +628,26 @@ static void run_context(or_state *s, const int16_t *yprev)
 }
 
 /* LRP Transformer of a coded frame (Sec. 3.1, the latent residual
- * prediction): every position's token concatenates the model's final
- * representation there (the Spatial Module 2 stream, the heads' input),
- * normalised, with the channel-scaled quantised latent, projected to the
- * model width; Llrp blocks of window self-attention over the whole k x k
- * window (spatially unmasked: the frame is fully decoded) and SwiGLU; then
- * RMSNorm and a projection to the C channels give the residual eps.  Every
- * block computes the keys and values of all positions before any position
- * is updated.  The window stays within the current frame, so the pass is
- * trivially causal in time. */
+ * prediction; Sec. 4.3 on its temporal transformer): every position's token
+ * concatenates the model's final representation there (the Spatial Module 2
+ * stream, the heads' input), normalised, with the channel-scaled quantised
+ * latent, projected to the model width; Llrp blocks of window self-attention
+ * and SwiGLU; then RMSNorm and a projection to the C channels give the
+ * residual eps.  The window is the whole k x k window of the current frame
+ * (spatially unmasked: the frame is fully decoded) and, for the temporal
+ * model, the same window in each of the Tf - 1 frames before it, whose keys
+ * and values of the same block were kept when their LRP ran (time-causal,
+ * relative bias by frame age, like the Context Transformer).  Every block
+ * computes the keys and values of all positions before any position is
+ * updated. */
 static void run_lrp(or_state *s, const int16_t *yf, double *eps)
 {
     const or_cfg *c = s->c;
-    int d = c->d, C = c->C, kk = c->k * c->k, HW = s->HW;
+    int d = c->d, C = c->C, kk = c->k * c->k, HW = s->HW, f = s->frame;
+    int Tw = c->temporal ? c->Tf : 1, slot_f = f % Tw;
+    int f0 = f - Tw + 1; if (f0 < 0) f0 = 0;
     long hd = (long)HW * d;
-    double *u = zalloc(hd), *K = zalloc(hd), *V = zalloc(hd);
+    double *u = zalloc(hd);
     #pragma omp parallel for schedule(dynamic, 4)
     for (int p = 0; p < HW; p++) {
         double *n = zalloc(d), *t = zalloc(d), *yc = zalloc(C), *up = u + (long)p * d;
@@ -651,26 +660,34 @@ static void run_lrp(or_state *s, const int16_t *yf, double *eps)
     }
     for (int l = 0; l < c->Llrp; l++) {
         const or_blk *bw = &s->lay.lrp[l];
+        double *LKl = s->LK + (long)l * Tw * hd, *LVl = s->LV + (long)l * Tw * hd;
         #pragma omp parallel for schedule(dynamic, 4)
         for (int p = 0; p < HW; p++) {
             double *n = zalloc(d);
             or_rmsnorm(u + (long)p * d, WP(bw->g_attn), d, n);
             or_matvec(n, WP(bw->Wq), d, d, s->q + (long)p * d);
-            or_matvec(n, WP(bw->Wk), d, d, K + (long)p * d);
-            or_matvec(n, WP(bw->Wv), d, d, V + (long)p * d);
+            or_matvec(n, WP(bw->Wk), d, d, LKl + slot_f * hd + (long)p * d);
+            or_matvec(n, WP(bw->Wv), d, d, LVl + slot_f * hd + (long)p * d);
             free(n);
         }
         #pragma omp parallel for schedule(dynamic, 4)
         for (int p = 0; p < HW; p++) {
+            int maxk = Tw * kk, nk = 0;
             int *idx = (int *)malloc(sizeof(int) * kk), *off = (int *)malloc(sizeof(int) * kk);
-            const double **Kp = (const double **)malloc(sizeof(double *) * kk);
-            const double **Vp = (const double **)malloc(sizeof(double *) * kk);
-            double *bias = zalloc((long)kk * c->nh), *o = zalloc(d), *t = zalloc(d), *n = zalloc(d);
+            const double **Kp = (const double **)malloc(sizeof(double *) * maxk);
+            const double **Vp = (const double **)malloc(sizeof(double *) * maxk);
+            double *bias = zalloc((long)maxk * c->nh), *o = zalloc(d), *t = zalloc(d), *n = zalloc(d);
             double *up = u + (long)p * d;
-            int nk = or_window_keys(c, -1, p, idx, off);
-            for (int j = 0; j < nk; j++) {
-                Kp[j] = K + (long)idx[j] * d; Vp[j] = V + (long)idx[j] * d;
-                for (int h = 0; h < c->nh; h++) bias[(long)j * c->nh + h] = WP(bw->bias)[(long)h * kk + off[j]];
+            int nw = or_window_keys(c, -1, p, idx, off);
+            for (int ff = f0; ff <= f; ff++) {
+                int sl = ff % Tw, age = f - ff;
+                for (int j = 0; j < nw; j++) {
+                    Kp[nk] = LKl + sl * hd + (long)idx[j] * d;
+                    Vp[nk] = LVl + sl * hd + (long)idx[j] * d;
+                    for (int h = 0; h < c->nh; h++)
+                        bias[(long)nk * c->nh + h] = WP(bw->bias)[((long)h * Tw + age) * kk + off[j]];
+                    nk++;
+                }
             }
             or_attend(s->q + (long)p * d, nk, Kp, Vp, bias, c->nh, d, o);
             or_matvec(o, WP(bw->Wo), d, d, t);
@@ -689,7 +706,7 @@ static void run_lrp(or_state *s, const int16_t *yf, double *eps)
         for (int ch = 0; ch < C; ch++) ep[ch] += WP(s->lay.lrp_b_eps)[ch];
         free(n);
     }
-    free(u); free(K); free(V);
+    free(u);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -83,6 +83,8 @@ def config(name: str) -> ModelConfig:
     i1080_cyc i1080 with the cyclic s = 4 mask (4 steps per frame)
     tiny_lrp  tiny with a 2-block LRP Transformer
     i1080_lrp i1080 with a 4-block LRP Transformer
+    tiny_p_lrp tiny_p with a 2-block time-causal LRP Transformer
+    p1080_lrp p1080 with a 4-block time-causal LRP Transformer
     """
     if name == "tiny":
         return ModelConfig(H=8, W=12, C=64, Hh=4, Wh=6, Ch=32, r=2, d=128, nh=4,
@@ -102,6 +104,12 @@ def config(name: str) -> ModelConfig:
     if name == "i1080_lrp":
         return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
                            F=ffn_width(384), L=8, k=7, Llrp=4)
+    if name == "tiny_p_lrp":
+        return ModelConfig(H=8, W=12, C=64, Hh=4, Wh=6, Ch=32, r=2, d=128, nh=4,
+                           F=ffn_width(128), L=2, k=5, temporal=1, Lc=2, Tf=3, Llrp=2)
+    if name == "p1080_lrp":
+        return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
+                           F=ffn_width(384), L=8, k=7, temporal=1, Lc=8, Tf=3, Llrp=4)
     if name == "i1080_cyc":
         return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
                            F=ffn_width(384), L=8, k=7, mask=1)
@@ -199,7 +207,7 @@ def weight_spec(c: ModelConfig) -> list:
               Tensor("lrp.W_y", (C, d), "lin", fan_in=C, matrix=True),
               Tensor("lrp.b_in", (d,), "bias")]
         for l in range(c.Llrp):
-            s += _block(f"lrp{l}.", c, cross=False, tf_bias=False, nblocks=c.Llrp)
+            s += _block(f"lrp{l}.", c, cross=False, tf_bias=bool(c.temporal), nblocks=c.Llrp)
         s += [Tensor("lrp.g_out", (d,), "gain"),
               Tensor("lrp.W_eps", (d, C), "lin_res", value=0.1, fan_in=d, matrix=True),
               Tensor("lrp.b_eps", (C,), "bias")]

@@ -139,6 +139,8 @@ def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray, with_
         return x + ffn(rms(x, P[pre + "g_ffn"]), P[pre + "Wg"], P[pre + "Wu"], P[pre + "Wd"])
 
     mus, sigs, epss = [], [], []
+    LK = [[] for _ in range(c.Llrp)]       # LRP keys / values of every coded frame, per block
+    LV = [[] for _ in range(c.Llrp)]
     for f in range(nf):
         ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
         zz = z[f][ii // c.r, jj // c.r].reshape(HW, c.Ch) * P["gamma_z"]
@@ -164,8 +166,17 @@ def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray, with_
             for l in range(c.Llrp):
                 pre = f"lrp{l}."
                 n = rms(u, P[pre + "g_attn"])
-                u = u + attention(n @ P[pre + "Wq"], n @ P[pre + "Wk"], n @ P[pre + "Wv"], win,
-                                  bias_of(P[pre + "bias"]), nh) @ P[pre + "Wo"]
+                LK[l].append(n @ P[pre + "Wk"])
+                LV[l].append(n @ P[pre + "Wv"])
+                # time-causal for the temporal model: the windows of the
+                # current and Tf - 1 previous frames, bias by frame age
+                fs = list(range(max(0, f - c.Tf + 1), f + 1)) if c.temporal else [f]
+                tb = P[pre + "bias"].reshape(nh, -1, c.k * c.k)
+                Kc = np.concatenate([LK[l][ff] for ff in fs])
+                Vc = np.concatenate([LV[l][ff] for ff in fs])
+                M = np.concatenate([win for _ in fs], axis=1)
+                B = np.concatenate([tb[:, f - ff][:, off] for ff in fs], axis=2)
+                u = u + attention(n @ P[pre + "Wq"], Kc, Vc, M, B, nh) @ P[pre + "Wo"]
                 u = u + ffn(rms(u, P[pre + "g_ffn"]), P[pre + "Wg"], P[pre + "Wu"], P[pre + "Wd"])
             epss.append((rms(u, P["lrp.g_out"]) @ P["lrp.W_eps"] + P["lrp.b_eps"]).reshape(H, W, C))
     if with_eps:

@@ -196,6 +196,27 @@ def test_lrp_oracle_matches_dense_mask_formulation(grid):
     assert np.array_equal(mu0, mu2) and np.array_equal(s0, s2)
 
 
+def test_lrp_temporal_oracle_matches_dense_mask_formulation():
+    """The temporal model's LRP Transformer (time-causal: windows of the
+    current and Tf - 1 previous frames, bias by frame age) over four frames,
+    so that the three-frame ring wraps: the oracle's ring of per-block keys
+    and values against dense attention over the concatenated frames."""
+    c = synth.config("tiny_p_lrp")
+    w = synth.weights(c)
+    fr = synth.frames(c, 4, seed=16)
+    mu0, s0, e0 = O.run(c, w, fr.y, fr.z, driver=0, with_eps=True)
+    mu1, s1, e1 = dense_ref.run(c, w, fr.y, fr.z, with_eps=True)
+    assert np.max(np.abs(mu0 - mu1)) < 1e-11
+    assert np.max(np.abs(e0 - e1)) < 1e-11
+    # a latent of frame 0 reaches the residual of frames 1 and 2 (through
+    # the LRP ring as well as the temporal entropy model) but a latent of
+    # frame 2 leaves frames 0 and 1 as they are (time-causal)
+    y = fr.y.copy()
+    y[2, 3, 4, :] += 5
+    _, _, e2 = O.run(c, w, y, fr.z, driver=0, with_eps=True)
+    assert np.array_equal(e2[:2], e0[:2]) and not np.array_equal(e2[2], e0[2])
+
+
 def test_lrp_residual_is_the_same_after_decoding():
     """Decoding the frame from its container (the wavefront schedule
     revealing latents step by step) gives bit-for-bit the residual of the
@@ -242,7 +263,7 @@ def test_lrp_window_is_spatially_unmasked_and_local():
 
 
 def test_weight_layout_count_matches_generator():
-    for nm in ("tiny", "tiny_p", "i1080", "p1080", "tiny_lrp", "i1080_lrp"):
+    for nm in ("tiny", "tiny_p", "i1080", "p1080", "tiny_lrp", "i1080_lrp", "tiny_p_lrp", "p1080_lrp"):
         c = synth.config(nm)
         assert O.weights_count(c) == synth.weights_count(c)
 

@@ -74,12 +74,15 @@ typedef enum {
  *   temporal  1 = Context Transformer (Lc blocks) and temporal
  *          cross-attention over Tf frames in every spatial block
  *   mask   0 = label 2i+j with the raster clause (wavefront and raster
- *          schedules valid); 1 = cyclic s = 4 label of Fig. 2a. */
+ *          schedules valid); 1 = cyclic s = 4 label of Fig. 2a.
+ *   Llrp   blocks of the LRP Transformer (Sec. 3.1 latent residual
+ *          prediction; 0 = none, at most 64), run by psw_lrp_residual. */
 typedef struct {
     int C, Ch, r;
     int d, nh, F, L, k;
     int temporal, Lc, Tf;
     int mask;
+    int Llrp;
 } psw_model_desc;
 
 /* One frame: latent grid H x W (hyperprior grid ceil(H/r) x ceil(W/r)) and
@@ -104,6 +107,10 @@ typedef struct {
  *   L x Spatial Module 2 block (as Spatial Module 1)
  *   heads: g_head[d] W1m[d][d] b1m[d] W2m[d][C] W1s[d][d] b1s[d] W2s[d][C]
  *          gamma_mu[C] beta_mu[C] gamma_sig[C] beta_sig[C]
+ *   if Llrp (the LRP Transformer): g_rep[d] W_rep[d][d] gamma_y[C] W_y[C][d] b_in[d]
+ *          Llrp x { g_attn[d] Wq Wk Wv Wo [d][d] bias[nh][k][k] (temporal:
+ *                   bias[nh][Tf][k][k]) g_ffn[d] Wg[d][F] Wu[d][F] Wd[F][d] }
+ *          g_out[d] W_eps[d][C] b_eps[C]
  * Returns 0 for an invalid descriptor. */
 size_t psw_weights_count(const psw_model_desc *desc);
 
@@ -114,8 +121,8 @@ size_t psw_weights_count(const psw_model_desc *desc);
  * shape the E4M3 tile takes -- K a multiple of 128, at most 512 for a
  * normalised input and 1024 for the FFN down projection -- as E4M3 bytes,
  * each source tensor with its own power-of-two scale as psw_quantize_e4m3
- * computes it; the latent embedding, the heads and any other projection in
- * BF16) and builds the scale and CDF tables.
+ * computes it; the latent embedding, the heads, the LRP Transformer and any
+ * other projection in BF16) and builds the scale and CDF tables.
  * hbm_budget bounds the device memory of this context and its sequences
  * (0 = no bound); a sequence that would exceed it fails with PSW_ERR_OOM.
  * On failure *out is NULL. */
@@ -195,6 +202,31 @@ psw_status psw_decode_batch(psw_ctx *ctx, int n, psw_seq *const *seqs, const psw
                             const int16_t *const *zhat_dev, int16_t *const *yhat_out_dev,
                             float *const *mu_dev, float *const *sigma_dev,
                             int *status_out, void *stream);
+
+/* LRP Transformer (Sec. 3.1 latent residual prediction; Sec. 4.3): the
+ * residual eps of the sequence's last coded frame, from the quantised
+ * latents of that frame and the model's final representation at every
+ * position (the Spatial Module 2 stream that fed the heads, kept per
+ * position by psw_encode_params and the decoders of a context with Llrp > 0).
+ * Its input token is RMSNorm(representation) . W_rep + (gamma_y * yhat) . W_y
+ * + b_in; Llrp blocks of window self-attention over the whole k x k window
+ * (no prediction mask: the frame is decoded) and SwiGLU; then
+ * eps = RMSNorm(.) . W_eps + b_eps.  For the temporal model the windows also
+ * cover the same window of the Tf - 1 previous frames (time-causal; each
+ * block's keys and values are kept per sequence in a ring of Tf frames), so
+ * the LRP of every coded frame must run, in order: once per frame, after
+ * that frame is coded and before the next one is.
+ *   fd       the grid of the last coded frame
+ *   eps_dev  [H][W][C] float32 output (may be NULL for the temporal model:
+ *            the ring advances, nothing is written)
+ * The encoder's and the decoder's residuals are bit-identical.
+ * Errors: PSW_ERR_INVALID if the model has no LRP Transformer, no frame was
+ * coded since the sequence was created or reset, fd's grid is not the last
+ * coded frame's, or (temporal model) the LRP of an earlier frame was
+ * skipped or that of this frame already ran; PSW_ERR_CUDA.  Synchronises
+ * `stream`. */
+psw_status psw_lrp_residual(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd, float *eps_dev,
+                            void *stream);
 
 /* Model rate of a frame (Fig. 1 rate term): bits = -sum log2 P(y) with
  * P(y) the Gaussian mass of [y - 1/2, y + 1/2] under (mu, sigma), sigma
@@ -285,7 +317,8 @@ psw_status psw_rans_encode_noalloc(const psw_ctx *ctx, const psw_frame_desc *fd,
  * psw_set_engine returns PSW_ERR_INVALID for an unknown engine or for
  * PSW_ENGINE_PERSISTENT on an FP32 context; a decode asked to run
  * persistently on a device that cannot co-schedule the blocks returns
- * PSW_ERR_CUDA.  psw_last_engine: the engine of the context's last decode
+ * PSW_ERR_CUDA; the persistent engine does not run contexts with an LRP
+ * Transformer (PSW_ERR_INVALID).  psw_last_engine: the engine of the context's last decode
  * (0 = individual launches, as under psw_profile_begin). */
 typedef enum { PSW_ENGINE_AUTO = 0, PSW_ENGINE_GRAPH = 1, PSW_ENGINE_PERSISTENT = 2 } psw_engine;
 psw_status psw_set_engine(psw_ctx *ctx, int engine);

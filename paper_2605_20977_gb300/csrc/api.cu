@@ -37,6 +37,9 @@ struct Layout {
     std::vector<BlockOff> ctx, sm1, sm2;
     long acc_g_q, acc_g_kv, acc_Wq, acc_Wk, acc_Wv, acc_Wo, acc_bias, acc_g_ffn, acc_Wg, acc_Wu, acc_Wd;
     long g_head, W1m, b1m, W2m, W1s, b1s, W2s, gamma_mu, beta_mu, gamma_sig, beta_sig;
+    long lrp_g_rep = -1, lrp_W_rep = -1, lrp_gamma_y = -1, lrp_W_y = -1, lrp_b_in = -1;   // LRP Transformer
+    std::vector<BlockOff> lrp;
+    long lrp_g_out = -1, lrp_W_eps = -1, lrp_b_eps = -1;
     long total;
 };
 
@@ -88,6 +91,12 @@ Layout make_layout(const psw_model_desc &m)
     y.W1m = cu.take(dd); y.b1m = cu.take(m.d); y.W2m = cu.take((long)m.d * m.C);
     y.W1s = cu.take(dd); y.b1s = cu.take(m.d); y.W2s = cu.take((long)m.d * m.C);
     y.gamma_mu = cu.take(m.C); y.beta_mu = cu.take(m.C); y.gamma_sig = cu.take(m.C); y.beta_sig = cu.take(m.C);
+    if (m.Llrp) {
+        y.lrp_g_rep = cu.take(m.d); y.lrp_W_rep = cu.take(dd); y.lrp_gamma_y = cu.take(m.C);
+        y.lrp_W_y = cu.take((long)m.C * m.d); y.lrp_b_in = cu.take(m.d);
+        for (int l = 0; l < m.Llrp; l++) y.lrp.push_back(layout_block(cu, m, false, m.temporal != 0));
+        y.lrp_g_out = cu.take(m.d); y.lrp_W_eps = cu.take((long)m.d * m.C); y.lrp_b_eps = cu.take(m.C);
+    }
     y.total = cu.at;
     return y;
 }
@@ -105,6 +114,7 @@ bool desc_valid(const psw_model_desc *m, std::string &why)
     if (m->L < 1 || m->L > 64) { why = "L must be in [1, 64]"; return false; }
     if (m->k < 1 || m->k % 2 == 0 || m->k * m->k > MAX_KK) { why = "k must be odd with k*k <= 81"; return false; }
     if (m->mask != 0 && m->mask != 1) { why = "mask must be 0 or 1"; return false; }
+    if (m->Llrp < 0 || m->Llrp > 64) { why = "Llrp must be in [0, 64]"; return false; }
     if (m->temporal == 1) {
         if (m->Lc < 1 || m->Lc > 64) { why = "Lc must be in [1, 64]"; return false; }
         if (m->Tf < 1 || m->Tf > MAX_TF || m->Tf * m->k * m->k > 256) { why = "need Tf <= 4 and Tf*k*k <= 256"; return false; }
@@ -163,8 +173,9 @@ struct psw_ctx {
     Layout lay;
     float *w = nullptr;                // flat FP32 weights on the device
     char *wmat = nullptr;              // arena of transposed projections
-    std::vector<BlockDev> ctxb, sm1, sm2;
+    std::vector<BlockDev> ctxb, sm1, sm2, lrpb;
     BlockDev acc;                      // Wqkv = [Wq]; Wxkv = [Wk; Wv]
+    void *Wrep = nullptr, *Wy = nullptr, *Weps = nullptr;   // LRP input [d][d], [d][C] and output [C][d] projections
     void *Win = nullptr;               // latent embedding [d][C]
     void *Wh1 = nullptr;               // heads, first layers [W1m; W1s]: [2d][d]
     void *Wh2 = nullptr;               // heads, second layers interleaved: row 2c = mu_c, 2c+1 = sigma_c: [2C][2d]
@@ -230,6 +241,10 @@ struct psw_seq {
     void *qa = nullptr;                                  // accumulator queries [HW][d]
     void *K1 = nullptr, *V1 = nullptr, *K2 = nullptr, *V2 = nullptr, *Ka = nullptr, *Va = nullptr;
     void *CK = nullptr, *CV = nullptr, *XK = nullptr, *XV = nullptr;   // temporal rings
+    void *LK = nullptr, *LV = nullptr;                   // LRP keys / values [Llrp (x Tf)][HW][d]
+    float *rep = nullptr;                                // LRP input: Spatial Module 2 stream, FP32 [HW][d]
+    int coded_H = 0, coded_W = 0;                        // grid of the last coded frame
+    int lrp_done = 0;                                    // frames whose LRP ran (temporal model)
     float *mu = nullptr, *sigma = nullptr;
     uint8_t *idx = nullptr;
     int32_t *m = nullptr;
@@ -325,6 +340,7 @@ bool prepare_projections(psw_ctx *c, bool dry)
     int d = m.d, prec = c->prec;
     size_t es = esize(prec), used = 0;
     bool ok = true;
+    bool no8 = false;                  // set: operands stay in the compute type even in an FP8 context
     float *stage = nullptr;            // one source tensor in FP32 [N][K] before E4M3 quantisation
     if (!dry && c->fp8 && cudaMalloc(&stage, (size_t)std::max(m.F, d) * std::max(m.F, d) * 4) != cudaSuccess)
         return false;
@@ -341,7 +357,7 @@ bool prepare_projections(psw_ctx *c, bool dry)
     // One projection operand [N][K] from source tensors [K][n_i] (flat
     // offsets) stacked at consecutive rows; asrc: how its tokens are built.
     auto operand = [&](int N, int K, int asrc, std::initializer_list<long> srcs) -> void * {
-        bool f8 = c->fp8 && gemm_tc8_supported(N, K, asrc);
+        bool f8 = c->fp8 && !no8 && gemm_tc8_supported(N, K, asrc);
         void *p = carve_b((size_t)N * K * (f8 ? 1 : es));
         float *sc = f8 ? (float *)carve_b((size_t)N * 4) : nullptr;
         int n = N / (int)srcs.size(), row = 0;
@@ -387,9 +403,20 @@ bool prepare_projections(psw_ctx *c, bool dry)
     ab.Wg = operand(m.F, d, A_NORM, {lay.acc_Wg});
     ab.Wu = operand(m.F, d, A_NORM, {lay.acc_Wu});
     ab.Wd = operand(d, m.F, A_DIRECT, {lay.acc_Wd});
+    // the LRP Transformer's projections stay in the compute type (BF16 in an
+    // FP8 context)
+    std::vector<BlockDev> lrpb;
+    void *wrep = nullptr, *weps = nullptr, *wy = nullptr;
+    no8 = true;
+    for (int l = 0; l < m.Llrp; l++) lrpb.push_back(mk_block(lay.lrp[l], false));
+    if (m.Llrp) {
+        wrep = operand(d, d, A_NORM, {lay.lrp_W_rep});
+        weps = operand(m.C, d, A_NORM, {lay.lrp_W_eps});
+    }
     cudaFree(stage);
     if (!ok) return false;
     void *win = carve(d, m.C); tr(lay.W_in, m.C, d, win, 0);
+    if (m.Llrp) { wy = carve(d, m.C); tr(lay.lrp_W_y, m.C, d, wy, 0); }
     void *wh1 = carve(2 * d, d); tr(lay.W1m, d, d, wh1, 0); tr(lay.W1s, d, d, wh1, d);
     void *wh2 = carve(2 * (size_t)m.C, 2 * d);
     float *bh1 = (float *)carve(2 * d, es == 2 ? 2 : 1);        // 2d floats
@@ -415,6 +442,7 @@ bool prepare_projections(psw_ctx *c, bool dry)
         cudaMemcpy(bh1 + d, c->w + lay.b1s, d * 4, cudaMemcpyDeviceToDevice);
     }
     c->ctxb = ctxb; c->sm1 = sm1; c->sm2 = sm2; c->acc = ab;
+    c->lrpb = lrpb; c->Wrep = wrep; c->Wy = wy; c->Weps = weps;
     c->Win = win; c->Wh1 = wh1; c->Wh2 = wh2; c->bh1 = bh1;
     return true;
 }
@@ -465,21 +493,24 @@ psw_status seq_schedule(psw_seq *q, int H, int W_, int kind)
 }
 
 // The slot of a sequence's current frame (pointers to its caches).
-Slot make_slot(const psw_seq *q, int H, int W_, int sched)
+// frame: the frame index the slot describes (default: the next to code).
+Slot make_slot(const psw_seq *q, int H, int W_, int sched, int frame = -1)
 {
     const psw_model_desc &m = q->ctx->md;
     Slot s;
     memset(&s, 0, sizeof(s));
-    s.H = H; s.W = W_; s.stride = q->maxHW; s.frame = q->frame; s.sched = sched;
+    if (frame < 0) frame = q->frame;
+    s.H = H; s.W = W_; s.stride = q->maxHW; s.frame = frame; s.sched = sched;
     s.nfr = 1;
     if (m.temporal) {
-        int f = q->frame, f0 = std::max(0, f - m.Tf + 1);
+        int f = frame, f0 = std::max(0, f - m.Tf + 1);
         s.nfr = f - f0 + 1;
         for (int u = 0; u < s.nfr; u++) s.ring[u] = (f0 + u) % m.Tf;
     }
     s.eh = q->eh;
     s.qa = q->qa; s.K1 = q->K1; s.V1 = q->V1; s.K2 = q->K2; s.V2 = q->V2; s.Ka = q->Ka; s.Va = q->Va;
     s.CK = q->CK; s.CV = q->CV; s.XK = q->XK; s.XV = q->XV;
+    s.LK = q->LK; s.LV = q->LV; s.rep = q->rep;
     s.mu = q->mu; s.sigma = q->sigma; s.idx = q->idx; s.m = q->m; s.y = q->y;
     s.yprev = q->yprev;
     s.rstate = q->rstate; s.rptr = q->rptr; s.rend = q->rend;
@@ -766,6 +797,12 @@ void run_acc_sm2_heads(const Pass &P, const int *tok, int n)
     ffn(P, c->acc, c->lay.acc_g_ffn, c->Xb, tok, n);
     for (int l = 0; l < m.L; l++)
         spatial_block(P, c->lay.sm2[l], c->sm2[l], m.L + l, c->Xb, CS_K2, CS_V2, l, tok, n);
+    if (m.Llrp) {
+        // the final representation at these positions, kept for the LRP
+        // Transformer (the persistent decoder has no phase for it)
+        if (P.rec) *P.failed = true;
+        else LAUNCH(P, K_OTHER, 0.0, (double)n * d * 8.0, launch_store_rows(P.S, tok, n, c->Xb, d, P.s));
+    }
     // prediction heads (Sec. 3.1): RMSNorm, both first layers as one
     // projection with bias and SiLU, then both second layers as one
     // interleaved projection whose epilogue applies the channel-wise output
@@ -776,6 +813,37 @@ void run_acc_sm2_heads(const Pass &P, const int *tok, int n)
     eh.gmu = W(c, c->lay.gamma_mu); eh.bmu = W(c, c->lay.beta_mu);
     eh.gsg = W(c, c->lay.gamma_sig); eh.bsg = W(c, c->lay.beta_sig);
     gemm_call(P, c->Hid, 2 * d, c->Wh2, nullptr, n, 2 * m.C, 2 * d, eh);
+}
+
+// LRP Transformer over every position of one coded frame (Sec. 3.1 latent
+// residual prediction; tokens tok[0..n) in raster order, so the slot's rep
+// rows are the compact rows of the launch): the input token from the
+// channel-scaled latents and the normalised representation, Llrp blocks of
+// window self-attention without prediction mask (for the temporal model over
+// the ring of the last Tf frames' keys and values of the same block) and
+// SwiGLU, then eps = RMSNorm . W_eps + b_eps into eps [n][C] (skipped if eps
+// is null).
+void run_lrp(const Pass &P, const int *tok, int n, const float *rep, float *eps)
+{
+    psw_ctx *c = P.c;
+    const psw_model_desc &m = c->md;
+    const Layout &y = c->lay;
+    int d = m.d, kk = m.k * m.k, tmp = m.temporal != 0;
+    P.xn_rows = nullptr;
+    gemm_any(P, A_EMBED, nullptr, W(c, y.lrp_gamma_y), nullptr, 0, c->Wy, nullptr, n, d, m.C,
+             epi_set_bias(tok, c->Xa, W(c, y.lrp_b_in)));
+    gemm_norm(P, rep, y.lrp_g_rep, c->Wrep, nullptr, n, d, d, epi_resid(tok, c->Xa));
+    for (int l = 0; l < m.Llrp; l++) {
+        const BlockOff &bo = y.lrp[l];
+        const BlockDev &bd = c->lrpb[l];
+        gemm_norm(P, c->Xa, bo.g_attn, bd.Wqkv, nullptr, n, 3 * d, d,
+                  epi_qkv(tok, d, d, c->Q, CS_LK, CS_LV, l, tmp, m.Tf));
+        attention(P, attn_args(P, tok, n, c->Q, CS_NONE, CS_LK, CS_LV, l, W(c, bo.bias), (tmp ? m.Tf : 1) * kk, -1,
+                               tmp));
+        gemm_call(P, c->O, d, bd.Wo, nullptr, n, d, d, epi_resid(tok, c->Xa));
+        ffn(P, bd, bo.g_ffn, c->Xa, tok, n);
+    }
+    if (eps) gemm_norm(P, c->Xa, y.lrp_g_out, c->Weps, nullptr, n, m.C, d, epi_set_bias(tok, eps, W(c, y.lrp_b_eps)));
 }
 
 // The persistent decoder's program for the current workspace: the phases
@@ -789,7 +857,7 @@ bool ensure_program(psw_ctx *c)
     c->prog = nullptr;
     c->prog_ok = false;
     c->prog_gen = c->ws_gen;
-    if (c->prec != P_BF16 || c->ws_rows == 0) return false;
+    if (c->prec != P_BF16 || c->ws_rows == 0 || c->md.Llrp) return false;
     c->prog = program_new((int)c->ws_rows);
     c->p_flops_tok[0] = c->p_flops_tok[1] = c->p_bytes_tok[0] = c->p_bytes_tok[1] = c->p_wbytes = 0;
     bool failed = false;
@@ -836,6 +904,7 @@ size_t seq_bytes_for(const psw_model_desc &m, int prec, int H, int W_)
     b += (size_t)m.C * 32 * 4 + 2 * (size_t)m.C * 4 + (2 * (size_t)m.C + 1) * 4;
     b += (size_t)m.C * (3 * HW + 64) * 2;                           // encoder scratch
     b += HW * 4 + 64;
+    if (m.Llrp) b += HW * d * 4 + 2 * (size_t)m.Llrp * (m.temporal ? m.Tf : 1) * HW * d * es;   // rep, LK, LV
     return b;
 }
 
@@ -1146,6 +1215,7 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
     psw_status first = PSW_OK;
     for (int b = 0; b < n; b++) {
         qs[b]->frame++;
+        qs[b]->coded_H = fds[b].H; qs[b]->coded_W = fds[b].W;
         psw_status sb = status_code(c, sts[b]);
         if (status_out) status_out[b] = sb;
         if (sb && !first) first = sb;
@@ -1323,6 +1393,11 @@ psw_status psw_seq_create(psw_ctx *c, int max_H, int max_W, psw_seq **out)
         q->CK = dal((size_t)m.Lc * m.Tf * HW * d * es); q->CV = dal((size_t)m.Lc * m.Tf * HW * d * es);
         q->XK = dal(2 * (size_t)m.L * m.Tf * HW * d * es); q->XV = dal(2 * (size_t)m.L * m.Tf * HW * d * es);
     }
+    if (m.Llrp) {
+        size_t lb = (size_t)m.Llrp * (m.temporal ? m.Tf : 1) * HW * d * es;
+        q->rep = (float *)dal(HW * d * 4);
+        q->LK = dal(lb); q->LV = dal(lb);
+    }
     q->mu = (float *)dal(HW * m.C * 4); q->sigma = (float *)dal(HW * m.C * 4);
     q->idx = (uint8_t *)dal(HW * m.C); q->m = (int32_t *)dal(HW * m.C * 4);
     q->y = (int16_t *)dal(HW * m.C * 2); q->yprev = (int16_t *)dal(HW * m.C * 2);
@@ -1347,6 +1422,8 @@ psw_status psw_seq_reset(psw_seq *q)
 {
     if (!q) return PSW_ERR_INVALID;
     q->frame = 0;
+    q->coded_H = q->coded_W = 0;
+    q->lrp_done = 0;
     return PSW_OK;
 }
 
@@ -1422,6 +1499,7 @@ psw_status psw_encode_params(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, c
     std::vector<int> sts;
     if ((st = read_status(c, qs, s, sts))) return st;   // synchronises: the token list is free again
     q->frame++;
+    q->coded_H = fd->H; q->coded_W = fd->W;
     if (bitstream_dev) *len_out = (size_t)*q->h_total;
     if (failed) return fail(c, PSW_ERR_CUDA, "a GEMM launch could not be prepared");
     if (sts[0] & ST_CAPACITY)
@@ -1448,6 +1526,42 @@ psw_status psw_decode_batch(psw_ctx *c, int n, psw_seq *const *seqs, const psw_f
         return fail(c, PSW_ERR_INVALID, "bad batch arguments");
     return decode_run(c, n, seqs, fds, bitstreams_dev, lens, zhat_dev, yhat_out_dev, mu_dev, sigma_dev, status_out,
                       (cudaStream_t)stream);
+}
+
+psw_status psw_lrp_residual(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, float *eps_dev, void *stream)
+{
+    psw_status st = check_frame(c, q, fd);
+    if (st) return st;
+    const psw_model_desc &m = c->md;
+    if (m.Llrp <= 0) return fail(c, PSW_ERR_INVALID, "the model has no LRP Transformer");
+    if (q->frame < 1) return fail(c, PSW_ERR_INVALID, "no frame coded since the sequence was created or reset");
+    if (fd->H != q->coded_H || fd->W != q->coded_W)
+        return fail(c, PSW_ERR_INVALID, "frame %dx%d is not the last coded frame's grid %dx%d", fd->H, fd->W,
+                    q->coded_H, q->coded_W);
+    if (m.temporal && q->lrp_done < q->frame - 1)
+        return fail(c, PSW_ERR_INVALID, "the LRP of frame %d was not run", q->lrp_done);
+    if (m.temporal && q->lrp_done > q->frame - 1)
+        return fail(c, PSW_ERR_INVALID, "the LRP of frame %d already ran", q->frame - 1);
+    if (!eps_dev && !m.temporal) return fail(c, PSW_ERR_INVALID, "null eps pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    int HW = fd->H * fd->W;
+    if ((st = ensure_workspace(c, HW))) return st;
+    if ((st = grow_tokens(c, HW, 1))) return st;
+    c->h_slots[0] = make_slot(q, fd->H, fd->W, fd->schedule, q->frame - 1);
+    std::vector<psw_seq *> qs{q};
+    if ((st = upload_slots(c, qs, 1, s))) return st;
+    std::vector<int> tok(HW);
+    for (int p = 0; p < HW; p++) tok[p] = tok_make(0, p);
+    CK_CUDA(c, cudaMemcpyAsync(c->d_tok, tok.data(), HW * sizeof(int), cudaMemcpyHostToDevice, s));
+    bool failed = false;
+    Pass P{c, s, c->d_slots, &failed};
+    run_lrp(P, c->d_tok, HW, q->rep, eps_dev);
+    CK_CUDA(c, cudaGetLastError());
+    std::vector<int> sts;
+    if ((st = read_status(c, qs, s, sts))) return st;   // synchronises: the token list is free again
+    if (failed) return fail(c, PSW_ERR_CUDA, "a GEMM launch could not be prepared");
+    q->lrp_done = q->frame;
+    return status_code(c, sts[0]);
 }
 
 psw_status psw_rate(psw_ctx *c, size_t n, const int16_t *yhat_dev, const float *mu_dev, const float *sigma_dev,
@@ -1591,6 +1705,8 @@ psw_status psw_set_engine(psw_ctx *c, int engine)
         return fail(c, PSW_ERR_INVALID, "unknown engine %d", engine);
     if (engine == PSW_ENGINE_PERSISTENT && c->prec != P_BF16)
         return fail(c, PSW_ERR_INVALID, "the persistent decoder runs BF16 and FP8 contexts only");
+    if (engine == PSW_ENGINE_PERSISTENT && c->md.Llrp)
+        return fail(c, PSW_ERR_INVALID, "the persistent decoder does not run contexts with an LRP Transformer");
     c->engine = engine;
     return PSW_OK;
 }

@@ -37,6 +37,8 @@ struct Slot {
     float *eh;
     void *qa, *K1, *V1, *K2, *V2, *Ka, *Va;
     void *CK, *CV, *XK, *XV;
+    void *LK, *LV;                 // LRP Transformer keys / values [Llrp (x Tf)][stride][d]
+    float *rep;                    // LRP: the Spatial Module 2 stream per position, FP32 [stride][d] (or null)
     float *mu, *sigma;
     uint8_t *idx;
     int32_t *m;
@@ -54,7 +56,8 @@ __host__ __device__ inline int tok_pos(int t) { return t & 0xFFFFFF; }
 __host__ __device__ inline int tok_make(int slot, int pos) { return (slot << 24) | pos; }
 
 // Caches a kernel can name.
-enum CacheSel { CS_NONE = -1, CS_K1 = 0, CS_V1, CS_K2, CS_V2, CS_KA, CS_VA, CS_QA, CS_CK, CS_CV, CS_XK, CS_XV };
+enum CacheSel { CS_NONE = -1, CS_K1 = 0, CS_V1, CS_K2, CS_V2, CS_KA, CS_VA, CS_QA, CS_CK, CS_CV, CS_XK, CS_XV,
+                CS_LK, CS_LV };
 
 // Launch with programmatic dependent launch allowed: the kernel may begin
 // while its predecessor in the stream finishes, and must execute
@@ -184,6 +187,8 @@ __device__ __forceinline__ T *cache_row(const Slot &s, int sel, int layer, int p
     case CS_CK: base = s.CK; break;
     case CS_CV: base = s.CV; break;
     case CS_XK: base = s.XK; break;
+    case CS_LK: base = s.LK; break;
+    case CS_LV: base = s.LV; break;
     default: base = s.XV; break;
     }
     return (T *)base + ((long)layer * s.stride + pos) * d;
@@ -200,6 +205,10 @@ void launch_embed_context(const Slot *S, const int *tok, int n, int C, const flo
 void launch_embed_hyper(const Slot *S, const int *tok, int n, int H, int W, int Ch, int r, const float *gamma,
                         const float *Whp, const float *b, int d, cudaStream_t s);
 void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void *dst, cudaStream_t s);
+// rep[position] = X[m] (d floats, d a multiple of 4) for each token m of a
+// slot whose rep pointer is set: the Spatial Module 2 stream kept for the
+// LRP Transformer.
+void launch_store_rows(const Slot *S, const int *tok, int n, const float *X, int d, cudaStream_t s);
 
 struct AttnArgs {
     const int *tok; int n;

@@ -181,6 +181,30 @@ void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void
     else k_rmsnorm<float><<<blocks, 256, 0, s>>>(X, n, g, d, (float *)dst);
 }
 
+// rep[position][e] = X[m][e]: one float4 per thread, tokens of slots
+// without a rep buffer skipped.  A plain launch: it starts after its
+// predecessor has finished.
+__global__ void k_store_rows(const Slot *__restrict__ S, const int *__restrict__ tok, int n,
+                             const float *__restrict__ X, int d4)
+{
+    const long total = (long)n * d4;
+    for (long a = blockIdx.x * (long)blockDim.x + threadIdx.x; a < total; a += (long)gridDim.x * blockDim.x) {
+        const int m = (int)(a / d4), e = (int)(a - (long)m * d4);
+        const int tk = tok[m];
+        float *rep = S[tok_slot(tk)].rep;
+        if (!rep) continue;
+        reinterpret_cast<float4 *>(rep)[(long)tok_pos(tk) * d4 + e] = reinterpret_cast<const float4 *>(X)[a];
+    }
+}
+
+void launch_store_rows(const Slot *S, const int *tok, int n, const float *X, int d, cudaStream_t s)
+{
+    if (n <= 0) return;
+    long total = (long)n * (d / 4);
+    int blocks = (int)std::min<long>(cdiv(total, 256), 152 * 8);
+    k_store_rows<<<blocks, 256, 0, s>>>(S, tok, n, X, d / 4);
+}
+
 // ---------------------------------------------------------------- attention
 
 // Warps per block: shared staging of one warp is CK key and CK value rows of

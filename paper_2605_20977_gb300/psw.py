@@ -26,13 +26,14 @@ EXPORTS = ["psw_weights_count", "psw_create", "psw_destroy", "psw_last_error", "
            "psw_decode_frame", "psw_decode_batch", "psw_rate", "psw_quantize", "psw_scale_table", "psw_cdf_table",
            "psw_rans_encode", "psw_rans_decode", "psw_launch_count", "psw_profile_begin", "psw_profile_end",
            "psw_rans_encode_noalloc", "psw_set_engine", "psw_last_engine", "psw_quantize_e4m3",
-           "psw_check_wait_timeout"]
+           "psw_check_wait_timeout", "psw_lrp_residual"]
 
 ENGINE_AUTO, ENGINE_GRAPH, ENGINE_PERSISTENT = 0, 1, 2
 
 
 class ModelDesc(ct.Structure):
-    _fields_ = [(n, ct.c_int) for n in ("C", "Ch", "r", "d", "nh", "F", "L", "k", "temporal", "Lc", "Tf", "mask")]
+    _fields_ = [(n, ct.c_int) for n in ("C", "Ch", "r", "d", "nh", "F", "L", "k", "temporal", "Lc", "Tf", "mask",
+                                         "Llrp")]
 
 
 class FrameDesc(ct.Structure):
@@ -81,6 +82,7 @@ def load(path: str = LIB_PATH):
             "psw_decode_frame": (I, [P, P, FD, P, S, P, P, P, P, P]),
             "psw_decode_batch": (I, [P, I, P, FD, P, P, P, P, P, P, P, P]),
             "psw_rate": (I, [P, S, P, P, P, ct.POINTER(ct.c_double), P]),
+            "psw_lrp_residual": (I, [P, P, FD, P, P]),
             "psw_quantize": (I, [P, S, P, P, P, P, P]),
             "psw_scale_table": (I, [P, P]),
             "psw_cdf_table": (I, [P, I, P, I, ct.POINTER(I), ct.POINTER(I)]),
@@ -297,6 +299,12 @@ class Sequence:
         if check:
             self.ctx._check(st)
         return st
+
+    def lrp_residual(self, fd: FrameDesc, eps=None, stream=None):
+        """The LRP Transformer's residual eps [H][W][C] float32 of the last
+        coded frame (eps may be None for the temporal model: the ring of
+        per-block keys and values advances only)."""
+        self.ctx._check(self.ctx.lib.psw_lrp_residual(self.ctx.h, self.h, ct.byref(fd), _ptr(eps), _stream(stream)))
 
     def rans_encode(self, fd: FrameDesc, y, idx, m, bitstream, stream=None) -> int:
         n = ct.c_size_t(0)

@@ -34,7 +34,8 @@ def test_exports_every_declared_symbol(lib):
     assert sorted(psw.EXPORTS) == names
 
 
-@pytest.mark.parametrize("name", ["tiny", "tiny_p", "tiny_cyc", "i1080", "p1080"])
+@pytest.mark.parametrize("name", ["tiny", "tiny_p", "tiny_cyc", "i1080", "p1080", "tiny_lrp", "tiny_p_lrp",
+                                  "i1080_lrp", "p1080_lrp"])
 def test_weights_count_matches_layouts(lib, name):
     c = synth.config(name)
     assert psw.psw_weights_count(c) == synth.weights_count(c) == O.weights_count(c)
@@ -43,7 +44,7 @@ def test_weights_count_matches_layouts(lib, name):
 def test_invalid_descriptors_rejected(lib):
     c = synth.config("tiny").as_dict()
     for bad in (dict(d=100), dict(nh=3), dict(k=4), dict(C=0), dict(mask=2), dict(F=0),
-                dict(temporal=1, Lc=0), dict(temporal=1, Lc=1, Tf=5)):
+                dict(temporal=1, Lc=0), dict(temporal=1, Lc=1, Tf=5), dict(Llrp=-1), dict(Llrp=65)):
         d = dict(c); d.update(bad)
         assert psw.psw_weights_count(d) == 0, bad
 

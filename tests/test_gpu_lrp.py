@@ -1,0 +1,210 @@
+"""GPU parity of the LRP Transformer (Sec. 3.1 latent residual prediction;
+Sec. 4.3 on its time-causal temporal transformer) through
+psw_lrp_residual, against the FP64 oracle's residual eps.
+
+The residual is a smooth function of the representation and the latents
+(no quantisation decides anything inside it), so FP32 compute is compared
+element by element; BF16 by the 99.9th percentile and the maximum of
+|d eps| / rms(eps).  The encoder's and the decoder's residuals are
+bit-identical (the same per-position representation and latents), and a
+frame decoded in a batch gives the residual it gives alone.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import dev, need_gpu, oracle_weights, torch
+from paper_2605_20977_gb300 import psw, synth
+
+pytestmark = pytest.mark.gpu
+
+FP32_TOL = 1e-4          # max |d eps| / rms(eps), FP32 compute
+BF16_TOL = 5e-2          # 99.9th percentile of the same, BF16 compute
+MAX_FACTOR = 10.0        # BF16: the maximum stays within 10x the percentile tolerance
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    need_gpu()
+    from paper_2605_20977_gb300 import build
+    build.build()
+    O.build()
+    torch.cuda.set_device(0)
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+def _code(ctx, fr, decode=True):
+    """Encode every frame (the LRP after each), then decode every frame
+    with a second sequence (the LRP after each); per-frame numpy eps of
+    both sides and the decoded latents."""
+    H, W, C = fr.y.shape[1], fr.y.shape[2], fr.y.shape[3]
+    enc, dec = ctx.seq_create(H, W), ctx.seq_create(H, W)
+    fd = psw.frame_desc(H, W, 0)
+    res = []
+    for f in range(fr.y.shape[0]):
+        y, z = _t(fr.y[f]), _t(fr.z[f])
+        bs = torch.zeros(ctx.bitstream_capacity(H, W), dtype=torch.uint8, device=dev())
+        n = enc.encode_params(fd, y, z, bitstream=bs)
+        e1 = torch.full((H, W, C), float("nan"), dtype=torch.float32, device=dev())
+        enc.lrp_residual(fd, e1)
+        r = dict(eps=e1.cpu().numpy())
+        if decode:
+            y2 = torch.full_like(y, 12345)
+            dec.decode_frame(fd, bs, n, z, y2)
+            e2 = torch.full_like(e1, float("nan"))
+            dec.lrp_residual(fd, e2)
+            r.update(eps2=e2.cpu().numpy(), y=y2.cpu().numpy())
+        res.append(r)
+    enc.close(); dec.close()
+    return res
+
+
+def _err(e, e_ref):
+    return np.abs(e.astype(np.float64) - e_ref) / np.sqrt(np.mean(e_ref ** 2))
+
+
+@pytest.mark.parametrize("name", ["tiny_lrp", "tiny_p_lrp"])
+def test_lrp_fp32_vs_oracle_and_decoder(name):
+    """FP32: eps of every frame against the oracle's; the decoder's eps
+    equals the encoder's bit for bit (four P-frames: the ring wraps)."""
+    cfg = synth.config(name)
+    w = synth.weights(cfg)
+    fr = synth.frames(cfg, 4 if cfg.temporal else 2, seed=2101)
+    ctx = psw.Context(cfg, w, precision=psw.PSW_FP32)
+    res = _code(ctx, fr)
+    _, _, eps_o = O.run(cfg, np.asarray(w, np.float64), fr.y, fr.z, driver=0, with_eps=True)
+    for f, r in enumerate(res):
+        assert np.array_equal(r["y"], fr.y[f])
+        assert np.array_equal(r["eps"], r["eps2"])
+        err = _err(r["eps"], eps_o[f])
+        print(f"frame {f}: max |d eps|/rms {err.max():.3g}")
+        assert err.max() <= FP32_TOL
+
+
+@pytest.mark.parametrize("name,rows", [("i1080_lrp", 6), ("p1080_lrp", 4)])
+def test_lrp_bf16_1080p_width_vs_oracle(name, rows):
+    """BF16 at the 1080p model sizes on a rows x 120 grid (the oracle and
+    the GPU code the same grid: the LRP is not causal in space, so a crop
+    of a larger frame would not be an exact sub-problem); P-frames over
+    three frames."""
+    base = synth.config(name)
+    w = synth.weights(base)
+    cfg = base.with_grid(rows, base.W)
+    fr = synth.frames(cfg, 3 if cfg.temporal else 1, seed=2102)
+    ctx = psw.Context(base, w, precision=psw.PSW_BF16)
+    res = _code(ctx, fr)
+    _, _, eps_o = O.run(cfg, oracle_weights(base, w, psw.PSW_BF16), fr.y, fr.z, driver=0, with_eps=True)
+    for f, r in enumerate(res):
+        assert np.array_equal(r["y"], fr.y[f])
+        assert np.array_equal(r["eps"], r["eps2"])
+        err = _err(r["eps"], eps_o[f])
+        q = np.quantile(err, 0.999)
+        print(f"frame {f}: observed |d eps|/rms (99.9th pct, max): {q:.3g}, {err.max():.3g}")
+        assert q <= BF16_TOL and err.max() <= MAX_FACTOR * BF16_TOL
+
+
+def test_lrp_fp8_context_keeps_bf16_lrp():
+    """In an FP8 context the LRP projections stay BF16: the residual of a
+    frame equals the BF16 context's when both see the same latents and
+    representations -- checked through the oracle with the FP8 context's
+    weights (E4M3 block projections, BF16 LRP) on a 4 x 120 I-frame."""
+    base = synth.config("i1080_lrp")
+    w = synth.weights(base)
+    cfg = base.with_grid(4, base.W)
+    fr = synth.frames(cfg, 1, seed=2103)
+    ctx = psw.Context(base, w, precision=psw.PSW_FP8)
+    r = _code(ctx, fr)[0]
+    _, _, eps_o = O.run(cfg, oracle_weights(base, w, psw.PSW_FP8), fr.y, fr.z, driver=0, with_eps=True)
+    assert np.array_equal(r["eps"], r["eps2"])
+    err = _err(r["eps"], eps_o[0])
+    q = np.quantile(err, 0.999)
+    print(f"observed |d eps|/rms (99.9th pct, max): {q:.3g}, {err.max():.3g}")
+    # the representation carries the FP8 model's error; the LRP adds BF16's
+    assert q <= 3 * BF16_TOL and err.max() <= MAX_FACTOR * 3 * BF16_TOL
+
+
+def test_lrp_full_frame_encoder_equals_decoder_and_batch():
+    """The 68 x 120 I-frame, BF16: encoder's eps == decoder's eps; and two
+    sequences decoded together by psw_decode_batch give the residuals they
+    give alone."""
+    cfg = synth.config("i1080_lrp")
+    w = synth.weights(cfg)
+    ctx = psw.Context(cfg, w, precision=psw.PSW_BF16)
+    H, W, C = cfg.H, cfg.W, cfg.C
+    fd = psw.frame_desc(H, W, 0)
+    items = []
+    for k in range(2):
+        fr = synth.frames(cfg, 1, seed=2104 + k)
+        enc = ctx.seq_create(H, W)
+        bs = torch.zeros(ctx.bitstream_capacity(H, W), dtype=torch.uint8, device=dev())
+        z = _t(fr.z[0])
+        n = enc.encode_params(fd, _t(fr.y[0]), z, bitstream=bs)
+        e = torch.zeros((H, W, C), dtype=torch.float32, device=dev())
+        enc.lrp_residual(fd, e)
+        items.append((bs, n, z, fr.y[0], e.cpu().numpy()))
+        enc.close()
+    alone = []
+    for bs, n, z, y, e_enc in items:
+        dec = ctx.seq_create(H, W)
+        y2 = torch.zeros((H, W, C), dtype=torch.int16, device=dev())
+        dec.decode_frame(fd, bs, n, z, y2)
+        e = torch.zeros((H, W, C), dtype=torch.float32, device=dev())
+        dec.lrp_residual(fd, e)
+        assert np.array_equal(y2.cpu().numpy(), y)
+        assert np.array_equal(e.cpu().numpy(), e_enc)
+        alone.append(e.cpu().numpy())
+        dec.close()
+    seqs = [ctx.seq_create(H, W) for _ in items]
+    outs = [torch.zeros((H, W, C), dtype=torch.int16, device=dev()) for _ in items]
+    st = ctx.decode_batch(seqs, [fd, fd], [it[0] for it in items], [it[1] for it in items],
+                          [it[2] for it in items], outs)
+    assert st == [psw.PSW_OK, psw.PSW_OK]
+    for k, q in enumerate(seqs):
+        e = torch.zeros((H, W, C), dtype=torch.float32, device=dev())
+        q.lrp_residual(fd, e)
+        assert np.array_equal(e.cpu().numpy(), alone[k])
+        q.close()
+
+
+def test_lrp_call_order_errors():
+    """psw_lrp_residual's argument and order checks (host side, before any
+    launch): no LRP in the model, no frame coded yet, another grid, and for
+    the temporal model a skipped or repeated frame; the persistent engine is
+    refused for an LRP context."""
+    cfg = synth.config("tiny_p_lrp")
+    w = synth.weights(cfg)
+    ctx = psw.Context(cfg, w, precision=psw.PSW_BF16)
+    fr = synth.frames(cfg, 2, seed=2105)
+    H, W, C = cfg.H, cfg.W, cfg.C
+    fd = psw.frame_desc(H, W, 0)
+    q = ctx.seq_create(H, W)
+    eps = torch.zeros((H, W, C), dtype=torch.float32, device=dev())
+    with pytest.raises(psw.PswError) as ex:
+        q.lrp_residual(fd, eps)
+    assert ex.value.status == psw.PSW_ERR_INVALID
+    q.encode_params(fd, _t(fr.y[0]), _t(fr.z[0]))
+    with pytest.raises(psw.PswError):
+        q.lrp_residual(psw.frame_desc(H - 1, W, 0), eps)
+    q.encode_params(fd, _t(fr.y[1]), _t(fr.z[1]))
+    with pytest.raises(psw.PswError) as ex:       # frame 0's LRP was skipped
+        q.lrp_residual(fd, eps)
+    assert "not run" in str(ex.value)
+    q.reset()
+    q.encode_params(fd, _t(fr.y[0]), _t(fr.z[0]))
+    q.lrp_residual(fd, None)                      # the ring advances without output
+    with pytest.raises(psw.PswError) as ex:
+        q.lrp_residual(fd, eps)
+    assert "already ran" in str(ex.value)
+    with pytest.raises(psw.PswError):
+        ctx.set_engine(psw.ENGINE_PERSISTENT)
+    q.close()
+    plain = psw.Context(synth.config("tiny"), synth.weights(synth.config("tiny")), precision=psw.PSW_FP32)
+    q2 = plain.seq_create(H, W)
+    q2.encode_params(fd, _t(fr.y[0]), _t(fr.z[0]))
+    with pytest.raises(psw.PswError) as ex:
+        q2.lrp_residual(fd, eps)
+    assert ex.value.status == psw.PSW_ERR_INVALID
+    q2.close()

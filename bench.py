@@ -66,6 +66,8 @@ def parse(argv=None):
                     help="timed steps of the same I-frame workload with E4M3 block projections (0: skip)")
     ap.add_argument("--cyclic-steps", type=int, default=2,
                     help="timed steps of the cyclic s = 4 schedule leg (0: skip)")
+    ap.add_argument("--lrp-steps", type=int, default=3,
+                    help="timed LRP Transformer passes over one decoded 1080p frame (0: skip)")
     ap.add_argument("--engine", choices=["auto", "graph", "persistent"], default="auto",
                     help="decode engine: one cooperative kernel over all steps, or per-phase kernels in CUDA graphs")
     return ap.parse_args(argv)
@@ -346,6 +348,46 @@ def fp8_run(args, dev, timed, cfg, w, ys, zs, B):
         q.close()
     ctx.close()
     return out, mu, sg
+
+
+def lrp_run(args, dev, timed, ys, zs):
+    """The LRP Transformer (Sec. 3.1 latent residual prediction; 4 blocks,
+    unmasked 7 x 7 windows) over one coded 68x120 frame: frames/s of
+    psw_lrp_residual, its kernel classes from one instrumented pass and the
+    projections' tensor rate (8160 tokens per launch)."""
+    import torch
+    from paper_2605_20977_gb300 import psw, synth
+    cfg = synth.config("i1080_lrp")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
+    fd = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_WAVEFRONT)
+    q = ctx.seq_create(cfg.H, cfg.W)
+    q.encode_params(fd, ys[0], zs[0])
+    eps = torch.zeros(ys[0].shape, dtype=torch.float32, device=dev)
+    q.lrp_residual(fd, eps)
+    ms = timed(lambda: q.lrp_residual(fd, eps), args.lrp_steps)
+    ctx.profile_begin()
+    q.lrp_residual(fd, eps)
+    stats = ctx.profile_end()
+    if not bool(torch.isfinite(eps).all()):
+        raise RuntimeError("LRP residual not finite")
+    pk, _ = peaks()
+    g = next((s_ for s_ in stats if s_["name"] == "gemm_tc"), None)
+    nrm = next((s_ for s_ in stats if s_["name"] == "rmsnorm"), None)
+    out = {"value": 1e3 / float(np.mean(ms)), "unit": "frames/s", "ms_per_frame": float(np.mean(ms)),
+           "workload": "LRP Transformer (4 blocks, d = 384, 7x7 unmasked windows) over one coded 1080p frame "
+                       "68x120x192 after its encode, BF16",
+           "classes": {s_["name"]: {"ms": round(s_["ms"], 3), "launches": s_["launches"],
+                                    "gflop": round(s_["flops"] / 1e9, 2)} for s_ in stats}}
+    if g:
+        t = g["ms"] + (nrm["ms"] if nrm else 0.0)
+        ach = g["flops"] / (t / 1e3) / 1e12
+        out["projections"] = {"achieved": ach, "unit": "TFLOP/s", "peak": pk["bf16_tflops_sustained"],
+                              "frac": ach / pk["bf16_tflops_sustained"],
+                              "timing": "CUDA events, projection launches plus the row normalisations feeding them",
+                              "tokens_per_launch": cfg.H * cfg.W}
+    q.close()
+    ctx.close()
+    return out
 
 
 def cyclic_run(args, dev, timed, w, ys, zs, B):
@@ -646,6 +688,11 @@ def run_ours(args, rank: int, world: int, local: int):
     if rank == 0 and args.cyclic_steps > 0 and args.precision == "bf16":
         cyclic = cyclic_run(args, dev, timed, w, ys, zs, B)
 
+    # the LRP Transformer over one coded frame
+    lrp = None
+    if rank == 0 and args.lrp_steps > 0 and args.precision == "bf16":
+        lrp = lrp_run(args, dev, timed, ys, zs)
+
     # rate: GPU parameters vs the FP64 oracle on the sample rows
     rate = {"bits_per_symbol": ctx.rate(ys[0], mu0, sg0) / ys[0].numel(),
             "container_bits_per_symbol": 8.0 * lens[0] / ys[0].numel()}
@@ -688,7 +735,8 @@ def run_ours(args, rank: int, world: int, local: int):
             "gpu_launches": int(round(launches)),
             "latency_one_frame": lat,
             "roofline": roof, "raster": raster, "speedup_vs_raster": speedup,
-            "rate": rate, "clocks": clk, "cpu_baseline": cpu, "pframe": pframe, "fp8": fp8, "cyclic": cyclic}
+            "rate": rate, "clocks": clk, "cpu_baseline": cpu, "pframe": pframe, "fp8": fp8, "cyclic": cyclic,
+            "lrp": lrp}
     print(json.dumps(line), flush=True)
     return 0
 

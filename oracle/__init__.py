@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
 class _Cfg(ct.Structure):
     _fields_ = [(n, ct.c_int) for n in
                 ("H", "W", "C", "Hh", "Wh", "Ch", "r", "d", "nh", "F", "L", "k",
-                 "temporal", "Lc", "Tf", "mask", "Llrp")]
+                 "temporal", "Lc", "Tf", "mask", "Llrp", "Nc", "dc", "Lct", "Fc")]
 
 
 def _load():

@@ -63,6 +63,8 @@ typedef struct {
     int Lc, Tf;           /* Context Transformer blocks, frames in window    */
     int mask;             /* 0: l = 2i+j (+ raster clause); 1: cyclic s = 4  */
     int Llrp;             /* LRP Transformer blocks (0: none)                */
+    int Nc, dc, Lct, Fc;  /* Channel Transformer: groups (0: none), width,
+                             blocks, SwiGLU width per group                */
 } or_cfg;
 
 typedef struct {
@@ -88,6 +90,8 @@ typedef struct {
     long lrp_g_rep, lrp_W_rep, lrp_gamma_y, lrp_W_y, lrp_b_in;   /* LRP Transformer (-1: none) */
     or_blk lrp[OR_MAXL];
     long lrp_g_out, lrp_W_eps, lrp_b_eps;
+    long ct_g_in, ct_W_in, ct_b_in, ct_gamma_y, ct_E;   /* Channel Transformer (-1: none) */
+    long ct_g_mix[OR_MAXL], ct_M[OR_MAXL], ct_g_ffn[OR_MAXL], ct_Wg[OR_MAXL], ct_Wu[OR_MAXL], ct_Wd[OR_MAXL];
     long total;
 } or_layout;
 
@@ -143,14 +147,39 @@ static void make_layout(const or_cfg *c, or_layout *lay)
     lay->acc.Wg = take(&cur, (long)c->d * c->F); lay->acc.Wu = take(&cur, (long)c->d * c->F);
     lay->acc.Wd = take(&cur, (long)c->F * c->d);
     for (int l = 0; l < c->L; l++) layout_block(&cur, c, &lay->sm2[l], c->temporal, 0);
-    lay->g_head = take(&cur, c->d);
-    lay->W1m = take(&cur, dd); lay->b1m = take(&cur, c->d); lay->W2m = take(&cur, (long)c->d * c->C);
-    lay->W1s = take(&cur, dd); lay->b1s = take(&cur, c->d); lay->W2s = take(&cur, (long)c->d * c->C);
+    int dh = c->Nc > 0 ? c->dc : c->d;     /* width of the heads' input */
+    if (c->Nc > 0) {
+        long dg = c->dc / c->Nc, Cg = c->C / c->Nc, dc = c->dc;
+        lay->ct_g_in = take(&cur, c->d);
+        lay->ct_W_in = take(&cur, (long)c->d * dc);
+        lay->ct_b_in = take(&cur, dc);
+        lay->ct_gamma_y = take(&cur, c->C);
+        lay->ct_E = take(&cur, (long)(c->Nc - 1) * Cg * dg);
+        for (int l = 0; l < c->Lct; l++) {
+            lay->ct_g_mix[l] = take(&cur, dc);
+            lay->ct_M[l] = take(&cur, dc * dc);
+            lay->ct_g_ffn[l] = take(&cur, dc);
+            lay->ct_Wg[l] = take(&cur, (long)c->Nc * dg * c->Fc);
+            lay->ct_Wu[l] = take(&cur, (long)c->Nc * dg * c->Fc);
+            lay->ct_Wd[l] = take(&cur, (long)c->Nc * c->Fc * dg);
+        }
+        /* grouped heads: per group [dg][dg] and [dg][Cg] */
+        lay->g_head = take(&cur, dc);
+        lay->W1m = take(&cur, (long)c->Nc * dg * dg); lay->b1m = take(&cur, dc);
+        lay->W2m = take(&cur, (long)c->Nc * dg * Cg);
+        lay->W1s = take(&cur, (long)c->Nc * dg * dg); lay->b1s = take(&cur, dc);
+        lay->W2s = take(&cur, (long)c->Nc * dg * Cg);
+    } else {
+        lay->ct_g_in = lay->ct_W_in = lay->ct_b_in = lay->ct_gamma_y = lay->ct_E = -1;
+        lay->g_head = take(&cur, c->d);
+        lay->W1m = take(&cur, dd); lay->b1m = take(&cur, c->d); lay->W2m = take(&cur, (long)c->d * c->C);
+        lay->W1s = take(&cur, dd); lay->b1s = take(&cur, c->d); lay->W2s = take(&cur, (long)c->d * c->C);
+    }
     lay->gamma_mu = take(&cur, c->C); lay->beta_mu = take(&cur, c->C);
     lay->gamma_sig = take(&cur, c->C); lay->beta_sig = take(&cur, c->C);
     if (c->Llrp > 0) {
-        lay->lrp_g_rep = take(&cur, c->d);
-        lay->lrp_W_rep = take(&cur, dd);
+        lay->lrp_g_rep = take(&cur, dh);
+        lay->lrp_W_rep = take(&cur, (long)dh * c->d);
         lay->lrp_gamma_y = take(&cur, c->C);
         lay->lrp_W_y = take(&cur, (long)c->C * c->d);
         lay->lrp_b_in = take(&cur, c->d);
@@ -168,7 +197,7 @@ static void make_layout(const or_cfg *c, or_layout *lay)
 long or_weights_count(const or_cfg *c)
 {
     or_layout lay;
-    if (c->L > OR_MAXL || c->Lc > OR_MAXL || c->Llrp > OR_MAXL) return -1;
+    if (c->L > OR_MAXL || c->Lc > OR_MAXL || c->Llrp > OR_MAXL || c->Lct > OR_MAXL) return -1;
     make_layout(c, &lay);
     return lay.total;
 }
@@ -308,6 +337,8 @@ typedef struct {
     double *XK, *XV;      /* temporal cross K/V: [2L][Tf slots][HW][d]        */
     double *CK, *CV;      /* context transformer K/V: [Lc][Tf slots][HW][d]   */
     double *LK, *LV;      /* LRP Transformer K/V: [Llrp][Tf slots][HW][d]    */
+    double *xc;           /* Channel Transformer output per position [HW][dc] */
+    double *ctM[OR_MAXL]; /* its mixing matrices with the block mask applied */
     double *mu, *sigma;   /* [HW][C]                                        */
 } or_state;
 
@@ -331,6 +362,19 @@ static int state_init(or_state *s, const or_cfg *c, const double *w)
     if (c->Llrp > 0) {
         s->LK = zalloc(hd * c->Llrp * c->Tf); s->LV = zalloc(hd * c->Llrp * c->Tf);
     }
+    if (c->Nc > 0) {
+        /* the block-lower-triangular mask on each mixing matrix [in][out]:
+         * output group i keeps the rows of input groups 0..i */
+        int dc = c->dc, dg = c->dc / c->Nc;
+        s->xc = zalloc((long)s->HW * dc);
+        for (int l = 0; l < c->Lct; l++) {
+            s->ctM[l] = zalloc((long)dc * dc);
+            const double *M = w + s->lay.ct_M[l];
+            for (int i = 0; i < dc; i++)
+                for (int o = 0; o < dc; o++)
+                    s->ctM[l][(long)i * dc + o] = (i / dg <= o / dg) ? M[(long)i * dc + o] : 0.0;
+        }
+    }
     return (s->x1 && s->K1 && s->V1 && s->eh && s->Ka && s->Va && s->x2 && s->K2 && s->V2 &&
             s->q && s->mu && s->sigma) ? 0 : -1;
 }
@@ -340,6 +384,8 @@ static void state_free(or_state *s)
     free(s->x1); free(s->K1); free(s->V1); free(s->eh); free(s->Ka); free(s->Va);
     free(s->x2); free(s->K2); free(s->V2); free(s->q); free(s->mu); free(s->sigma);
     free(s->XK); free(s->XV); free(s->CK); free(s->CV); free(s->LK); free(s->LV);
+    free(s->xc);
+    for (int l = 0; l < s->c->Lct; l++) free(s->ctM[l]);
 }
 
 #define WP(off) (s->w + (off))
@@ -551,8 +597,91 @@ static void run_acc_sm2_heads(or_state *s, const int *pos, int n)
         #pragma omp parallel for schedule(dynamic, 1)
         for (int a = 0; a < n; a++) block_rest(s, c->L + l, &s->lay.sm2[l], s->x2, s->K2 + l * hd, s->V2 + l * hd, pos[a]);
     }
+    if (c->Nc > 0) return;       /* the Channel Transformer and its grouped heads follow */
     #pragma omp parallel for schedule(dynamic, 1)
     for (int a = 0; a < n; a++) run_heads(s, pos[a]);
+}
+
+/* RMSNorm of each of the G groups of x (n values) separately: the
+ * statistics of a group never see another group's values. */
+static void group_rmsnorm(const double *x, const double *g, int n, int G, double *y)
+{
+    int w = n / G;
+    for (int j = 0; j < G; j++) or_rmsnorm(x + (long)j * w, g + (long)j * w, w, y + (long)j * w);
+}
+
+/* Channel Transformer and grouped heads at position p (Sec. 3.1, Channel
+ * Transformer paragraph; Sec. 3.2, s spatial steps times N channel groups;
+ * Sec. 4.1 sizes), from the Spatial Module 2 output there and the latents
+ * yv.  The width-dc stream is N groups of dg = dc / N.  Input: the
+ * normalised Spatial Module 2 output projected to dc; with the channel
+ * shift, group g >= 1 adds the embedding of the channel-scaled latents of
+ * group g - 1, so group 0 holds only the spatio-temporal context.  Each of
+ * Lct blocks: group-wise RMSNorm, the mixing layer (a dc x dc projection
+ * whose block-lower-triangular mask lets output group i read input groups
+ * 0..i only, a masked 1 x 1 convolution over channels) with residual, then
+ * group-wise RMSNorm and a SwiGLU of each group's own weights with residual.
+ * Heads: group-wise RMSNorm, then for mu and for sigma a two-layer MLP per
+ * group (grouped MLPs) giving that group's C / N channels.  So the
+ * parameters of group g depend on the latents of groups 0..g-1 only.  The
+ * final stream is kept in xc (the LRP Transformer's representation). */
+static void run_ct_heads(or_state *s, int p, const int16_t *yv)
+{
+    const or_cfg *c = s->c;
+    int d = c->d, C = c->C, dc = c->dc, G = c->Nc, dg = dc / G, Cg = C / G, Fc = c->Fc;
+    double *n = zalloc(d), *h = s->xc + (long)p * dc, *a = zalloc(dc), *t = zalloc(dc);
+    double *yc = zalloc(Cg), *hid = zalloc(dg), *o = zalloc(Cg);
+    or_rmsnorm(s->x2 + (long)p * d, WP(s->lay.ct_g_in), d, n);
+    or_matvec(n, WP(s->lay.ct_W_in), d, dc, h);
+    for (int e = 0; e < dc; e++) h[e] += WP(s->lay.ct_b_in)[e];
+    for (int g = 1; g < G; g++) {
+        for (int ch = 0; ch < Cg; ch++) {
+            int cc = (g - 1) * Cg + ch;
+            yc[ch] = WP(s->lay.ct_gamma_y)[cc] * (double)yv[(long)p * C + cc];
+        }
+        or_matvec(yc, WP(s->lay.ct_E) + (long)(g - 1) * Cg * dg, Cg, dg, t);
+        for (int e = 0; e < dg; e++) h[(long)g * dg + e] += t[e];
+    }
+    for (int l = 0; l < c->Lct; l++) {
+        group_rmsnorm(h, WP(s->lay.ct_g_mix[l]), dc, G, a);
+        or_matvec(a, s->ctM[l], dc, dc, t);
+        for (int e = 0; e < dc; e++) h[e] += t[e];
+        group_rmsnorm(h, WP(s->lay.ct_g_ffn[l]), dc, G, a);
+        for (int g = 0; g < G; g++) {
+            or_swiglu(a + (long)g * dg, WP(s->lay.ct_Wg[l]) + (long)g * dg * Fc, WP(s->lay.ct_Wu[l]) + (long)g * dg * Fc,
+                      WP(s->lay.ct_Wd[l]) + (long)g * Fc * dg, dg, Fc, t);
+            for (int e = 0; e < dg; e++) h[(long)g * dg + e] += t[e];
+        }
+    }
+    group_rmsnorm(h, WP(s->lay.g_head), dc, G, a);
+    const double lo = log(0.11), hi = log(256.0);
+    for (int g = 0; g < G; g++) {
+        const double *ag = a + (long)g * dg;
+        or_matvec(ag, WP(s->lay.W1m) + (long)g * dg * dg, dg, dg, hid);
+        for (int e = 0; e < dg; e++) hid[e] = or_silu(hid[e] + WP(s->lay.b1m)[(long)g * dg + e]);
+        or_matvec(hid, WP(s->lay.W2m) + (long)g * dg * Cg, dg, Cg, o);
+        for (int ch = 0; ch < Cg; ch++) {
+            int cc = g * Cg + ch;
+            s->mu[(long)p * C + cc] = WP(s->lay.gamma_mu)[cc] * o[ch] + WP(s->lay.beta_mu)[cc];
+        }
+        or_matvec(ag, WP(s->lay.W1s) + (long)g * dg * dg, dg, dg, hid);
+        for (int e = 0; e < dg; e++) hid[e] = or_silu(hid[e] + WP(s->lay.b1s)[(long)g * dg + e]);
+        or_matvec(hid, WP(s->lay.W2s) + (long)g * dg * Cg, dg, Cg, o);
+        for (int ch = 0; ch < Cg; ch++) {
+            int cc = g * Cg + ch;
+            double v = WP(s->lay.gamma_sig)[cc] * o[ch] + WP(s->lay.beta_sig)[cc];
+            if (v < lo) v = lo;
+            if (v > hi) v = hi;
+            s->sigma[(long)p * C + cc] = exp(v);
+        }
+    }
+    free(n); free(a); free(t); free(yc); free(hid); free(o);
+}
+
+static void run_ct_all(or_state *s, const int *pos, int n, const int16_t *yv)
+{
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int a = 0; a < n; a++) run_ct_heads(s, pos[a], yv);
 }
 
 /* Context Transformer for frame f (Sec. 3.1): tokens are the previous frame's
@@ -629,8 +758,9 @@ static void run_context(or_state *s, const int16_t *yprev)
 
 /* LRP Transformer of a coded frame (Sec. 3.1, the latent residual
  * prediction; Sec. 4.3 on its temporal transformer): every position's token
- * concatenates the model's final representation there (the Spatial Module 2
- * stream, the heads' input), normalised, with the channel-scaled quantised
+ * concatenates the model's final representation there (the heads' input:
+ * the Channel Transformer's stream if the model has one, else the Spatial
+ * Module 2 stream), normalised, with the channel-scaled quantised
  * latent, projected to the model width; Llrp blocks of window self-attention
  * and SwiGLU; then RMSNorm and a projection to the C channels give the
  * residual eps.  The window is the whole k x k window of the current frame
@@ -650,13 +780,18 @@ static void run_lrp(or_state *s, const int16_t *yf, double *eps)
     double *u = zalloc(hd);
     #pragma omp parallel for schedule(dynamic, 4)
     for (int p = 0; p < HW; p++) {
-        double *n = zalloc(d), *t = zalloc(d), *yc = zalloc(C), *up = u + (long)p * d;
-        or_rmsnorm(s->x2 + (long)p * d, WP(s->lay.lrp_g_rep), d, n);
-        or_matvec(n, WP(s->lay.lrp_W_rep), d, d, up);
+        double *nr = zalloc(c->Nc > 0 ? c->dc : d), *t = zalloc(d), *yc = zalloc(C), *up = u + (long)p * d;
+        if (c->Nc > 0) {
+            or_rmsnorm(s->xc + (long)p * c->dc, WP(s->lay.lrp_g_rep), c->dc, nr);
+            or_matvec(nr, WP(s->lay.lrp_W_rep), c->dc, d, up);
+        } else {
+            or_rmsnorm(s->x2 + (long)p * d, WP(s->lay.lrp_g_rep), d, nr);
+            or_matvec(nr, WP(s->lay.lrp_W_rep), d, d, up);
+        }
         for (int ch = 0; ch < C; ch++) yc[ch] = WP(s->lay.lrp_gamma_y)[ch] * (double)yf[(long)p * C + ch];
         or_matvec(yc, WP(s->lay.lrp_W_y), C, d, t);
         for (int e = 0; e < d; e++) up[e] += t[e] + WP(s->lay.lrp_b_in)[e];
-        free(n); free(t); free(yc);
+        free(nr); free(t); free(yc);
     }
     for (int l = 0; l < c->Llrp; l++) {
         const or_blk *bw = &s->lay.lrp[l];
@@ -999,9 +1134,11 @@ static uint32_t dec_word(or_dec *D, int c)
 
 /* Decode the symbols of n positions (the next n of the schedule) for every
  * channel.  idx, m: [n][C] for those positions; yout: [n][C]. */
-static void dec_symbols(or_dec *D, int n, const uint8_t *idx, const int32_t *m, int16_t *yout)
+/* The next n symbols of channels [c0, c1) (idx, m, yout: [n][C]); the
+ * symbol counter advances with dec_advance once every channel is done. */
+static void dec_channels(or_dec *D, int n, int c0, int c1, const uint8_t *idx, const int32_t *m, int16_t *yout)
 {
-    for (int c = 0; c < D->C; c++) {
+    for (int c = c0; c < c1; c++) {
         for (int a = 0; a < n; a++) {
             long k = D->k + a;
             int lane = (int)(k % 32), l = idx[(long)a * D->C + c], T = D->tb.T[l];
@@ -1031,7 +1168,14 @@ static void dec_symbols(or_dec *D, int n, const uint8_t *idx, const int32_t *m, 
             yout[(long)a * D->C + c] = (int16_t)yv;
         }
     }
-    D->k += n;
+}
+
+static void dec_advance(or_dec *D, int n) { D->k += n; }
+
+static void dec_symbols(or_dec *D, int n, const uint8_t *idx, const int32_t *m, int16_t *yout)
+{
+    dec_channels(D, n, 0, D->C, idx, m, yout);
+    dec_advance(D, n);
 }
 
 static int dec_close(or_dec *D)
@@ -1096,7 +1240,7 @@ int or_run_lrp(const or_cfg *c, const double *w, int nf, int16_t *y, const int16
                double *mu, double *sigma, double *eps)
 {
     or_state st, *s = &st;
-    if (c->L > OR_MAXL || c->Lc > OR_MAXL || c->Llrp > OR_MAXL) return -1;
+    if (c->L > OR_MAXL || c->Lc > OR_MAXL || c->Llrp > OR_MAXL || c->Lct > OR_MAXL) return -1;
     if (eps && c->Llrp <= 0) return -1;
     if (state_init(s, c, w)) { state_free(s); return -1; }
     int HW = s->HW, C = c->C;
@@ -1116,6 +1260,7 @@ int or_run_lrp(const or_cfg *c, const double *w, int nf, int16_t *y, const int16
             for (int p = 0; p < HW; p++) all[p] = p;
             run_sm1(s, all, HW, yf);
             run_acc_sm2_heads(s, all, HW);
+            if (c->Nc > 0) run_ct_all(s, all, HW, yf);
             free(all);
         } else {
             or_dec *D = NULL;
@@ -1133,22 +1278,31 @@ int or_run_lrp(const or_cfg *c, const double *w, int nf, int16_t *y, const int16
                 int n = start[t + 1] - start[t];
                 if (t > 0) run_sm1(s, order + start[t - 1], start[t] - start[t - 1], yvis);
                 run_acc_sm2_heads(s, ps, n);
-                if (driver == 1) {
-                    for (int a = 0; a < n; a++)
-                        memcpy(yvis + (long)ps[a] * C, yf + (long)ps[a] * C, sizeof(int16_t) * C);
-                } else {
-                    float *mf = (float *)malloc(sizeof(float) * n * C), *sf = (float *)malloc(sizeof(float) * n * C);
-                    for (int a = 0; a < n; a++)
-                        for (int ch = 0; ch < C; ch++) {
-                            mf[(long)a * C + ch] = (float)s->mu[(long)ps[a] * C + ch];
-                            sf[(long)a * C + ch] = (float)s->sigma[(long)ps[a] * C + ch];
-                        }
-                    or_quantize((long)n * C, mf, sf, ib, mb);
-                    dec_symbols(D, n, ib, mb, yb);
-                    for (int a = 0; a < n; a++)
-                        memcpy(yvis + (long)ps[a] * C, yb + (long)a * C, sizeof(int16_t) * C);
-                    free(mf); free(sf);
+                /* with a Channel Transformer the step's channel groups follow
+                 * one another: the parameters of group g (computed with the
+                 * latents revealed so far), then that group's latents */
+                int G = c->Nc > 0 ? c->Nc : 1, Cg = C / G;
+                for (int g = 0; g < G; g++) {
+                    int c0 = g * Cg;
+                    if (c->Nc > 0) run_ct_all(s, ps, n, yvis);
+                    if (driver == 1) {
+                        for (int a = 0; a < n; a++)
+                            memcpy(yvis + (long)ps[a] * C + c0, yf + (long)ps[a] * C + c0, sizeof(int16_t) * Cg);
+                    } else {
+                        float *mf = (float *)malloc(sizeof(float) * n * C), *sf = (float *)malloc(sizeof(float) * n * C);
+                        for (int a = 0; a < n; a++)
+                            for (int ch = 0; ch < C; ch++) {
+                                mf[(long)a * C + ch] = (float)s->mu[(long)ps[a] * C + ch];
+                                sf[(long)a * C + ch] = (float)s->sigma[(long)ps[a] * C + ch];
+                            }
+                        or_quantize((long)n * C, mf, sf, ib, mb);
+                        dec_channels(D, n, c0, c0 + Cg, ib, mb, yb);
+                        for (int a = 0; a < n; a++)
+                            memcpy(yvis + (long)ps[a] * C + c0, yb + (long)a * C + c0, sizeof(int16_t) * Cg);
+                        free(mf); free(sf);
+                    }
                 }
+                if (driver == 2) dec_advance(D, n);
             }
             if (driver == 2) {
                 if (dec_close(D)) rc = -2;

@@ -36,6 +36,8 @@ class ModelConfig:
     mask       0: step label 2i+j; 1: cyclic s = 4 label
     Llrp       LRP Transformer blocks (0: none): the latent residual
                prediction over a decoded frame
+    Nc, dc     Channel Transformer: channel groups (0: none) and width
+    Lct, Fc    its blocks and the SwiGLU hidden width of each group
     """
     H: int
     W: int
@@ -54,6 +56,10 @@ class ModelConfig:
     Tf: int = 3
     mask: int = 0
     Llrp: int = 0
+    Nc: int = 0
+    dc: int = 0
+    Lct: int = 0
+    Fc: int = 0
 
     def with_grid(self, H: int, W: int) -> "ModelConfig":
         d = asdict(self)
@@ -85,6 +91,12 @@ def config(name: str) -> ModelConfig:
     i1080_lrp i1080 with a 4-block LRP Transformer
     tiny_p_lrp tiny_p with a 2-block time-causal LRP Transformer
     p1080_lrp p1080 with a 4-block time-causal LRP Transformer
+    tiny_ct   tiny with a Channel Transformer: 4 groups, width 256, 2 blocks
+    tiny_cyc_ct  tiny_ct with the cyclic s = 4 mask (16 steps per frame)
+    tiny_p_ct tiny_p with the same Channel Transformer
+    tiny_ct_lrp  tiny_ct with a 2-block LRP Transformer on its output
+    i1080_ct  i1080 with a Channel Transformer: 4 groups, width 1024, 2 blocks
+    i1080_cyc_ct  i1080_ct with the cyclic s = 4 mask: s x N = 16 steps
     """
     if name == "tiny":
         return ModelConfig(H=8, W=12, C=64, Hh=4, Wh=6, Ch=32, r=2, d=128, nh=4,
@@ -110,6 +122,20 @@ def config(name: str) -> ModelConfig:
     if name == "p1080_lrp":
         return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
                            F=ffn_width(384), L=8, k=7, temporal=1, Lc=8, Tf=3, Llrp=4)
+    if name in ("tiny_ct", "tiny_cyc_ct", "tiny_p_ct"):
+        base = config({"tiny_ct": "tiny", "tiny_cyc_ct": "tiny_cyc", "tiny_p_ct": "tiny_p"}[name])
+        d = asdict(base)
+        d.update(Nc=4, dc=256, Lct=2, Fc=ffn_width(64))
+        return ModelConfig(**d)
+    if name == "tiny_ct_lrp":
+        d = asdict(config("tiny_ct"))
+        d.update(Llrp=2)
+        return ModelConfig(**d)
+    if name in ("i1080_ct", "i1080_cyc_ct"):
+        base = config({"i1080_ct": "i1080", "i1080_cyc_ct": "i1080_cyc"}[name])
+        d = asdict(base)
+        d.update(Nc=4, dc=1024, Lct=2, Fc=ffn_width(256))
+        return ModelConfig(**d)
     if name == "i1080_cyc":
         return ModelConfig(H=68, W=120, C=192, Hh=17, Wh=30, Ch=128, r=4, d=384, nh=6,
                            F=ffn_width(384), L=8, k=7, mask=1)
@@ -193,16 +219,42 @@ def weight_spec(c: ModelConfig) -> list:
           Tensor("acc.Wd", (F, d), "lin_res", value=res, fan_in=F, matrix=True)]
     for l in range(c.L):
         s += _block(f"sm2.{l}.", c, cross=bool(c.temporal), tf_bias=False, nblocks=nblocks)
-    s += [Tensor("g_head", (d,), "gain"),
-          Tensor("W1m", (d, d), "lin", fan_in=d, matrix=True), Tensor("b1m", (d,), "bias"),
-          Tensor("W2m", (d, C), "lin", fan_in=d, matrix=True),
-          Tensor("W1s", (d, d), "lin", fan_in=d, matrix=True), Tensor("b1s", (d,), "bias"),
-          Tensor("W2s", (d, C), "lin", fan_in=d, matrix=True),
-          Tensor("gamma_mu", (C,), "const", 2.0), Tensor("beta_mu", (C,), "const", 0.0),
+    if c.Nc:
+        # Channel Transformer: input projection, the shifted latents' group
+        # embeddings, Lct blocks of masked channel mixing and grouped SwiGLU
+        G, dc = c.Nc, c.dc
+        dg, Cg = dc // G, C // G
+        cres = 1.0 / math.sqrt(2.0 * c.Lct)
+        s += [Tensor("ct.g_in", (d,), "gain"),
+              Tensor("ct.W_in", (d, dc), "lin", fan_in=d, matrix=True),
+              Tensor("ct.b_in", (dc,), "bias"),
+              Tensor("ct.gamma_y", (C,), "const", 0.25),
+              Tensor("ct.E", (G - 1, Cg, dg), "lin", fan_in=Cg)]
+        for l in range(c.Lct):
+            s += [Tensor(f"ct{l}.g_mix", (dc,), "gain"),
+                  Tensor(f"ct{l}.M", (dc, dc), "lin_res", value=cres, fan_in=dc, matrix=True),
+                  Tensor(f"ct{l}.g_ffn", (dc,), "gain"),
+                  Tensor(f"ct{l}.Wg", (G, dg, c.Fc), "lin", fan_in=dg, matrix=True),
+                  Tensor(f"ct{l}.Wu", (G, dg, c.Fc), "lin", fan_in=dg, matrix=True),
+                  Tensor(f"ct{l}.Wd", (G, c.Fc, dg), "lin_res", value=cres, fan_in=c.Fc, matrix=True)]
+        # grouped heads
+        s += [Tensor("g_head", (dc,), "gain"),
+              Tensor("W1m", (G, dg, dg), "lin", fan_in=dg, matrix=True), Tensor("b1m", (dc,), "bias"),
+              Tensor("W2m", (G, dg, Cg), "lin", fan_in=dg, matrix=True),
+              Tensor("W1s", (G, dg, dg), "lin", fan_in=dg, matrix=True), Tensor("b1s", (dc,), "bias"),
+              Tensor("W2s", (G, dg, Cg), "lin", fan_in=dg, matrix=True)]
+    else:
+        s += [Tensor("g_head", (d,), "gain"),
+              Tensor("W1m", (d, d), "lin", fan_in=d, matrix=True), Tensor("b1m", (d,), "bias"),
+              Tensor("W2m", (d, C), "lin", fan_in=d, matrix=True),
+              Tensor("W1s", (d, d), "lin", fan_in=d, matrix=True), Tensor("b1s", (d,), "bias"),
+              Tensor("W2s", (d, C), "lin", fan_in=d, matrix=True)]
+    s += [Tensor("gamma_mu", (C,), "const", 2.0), Tensor("beta_mu", (C,), "const", 0.0),
           Tensor("gamma_sig", (C,), "const", 1.0), Tensor("beta_sig", (C,), "const", math.log(2.0))]
     if c.Llrp:
-        s += [Tensor("lrp.g_rep", (d,), "gain"),
-              Tensor("lrp.W_rep", (d, d), "lin", fan_in=d, matrix=True),
+        dh = c.dc if c.Nc else d            # the heads' input width
+        s += [Tensor("lrp.g_rep", (dh,), "gain"),
+              Tensor("lrp.W_rep", (dh, d), "lin", fan_in=dh, matrix=True),
               Tensor("lrp.gamma_y", (C,), "const", 0.25),
               Tensor("lrp.W_y", (C, d), "lin", fan_in=C, matrix=True),
               Tensor("lrp.b_in", (d,), "bias")]
@@ -258,9 +310,11 @@ def e4m3_tensor(t: Tensor) -> bool:
     """Whether an FP8 context stores projection t as E4M3 (one power-of-two
     scale per tensor): transformer-block projections whose input width K is
     a multiple of 128, at most 512 for a normalised input and 1024 for the
-    compact-row inputs of Wo, Wxo and Wd.  The latent embedding, the heads
-    and the LRP Transformer stay in the compute dtype."""
-    if not t.matrix or t.name in ("W_in", "W1m", "W2m", "W1s", "W2s") or t.name.startswith("lrp"):
+    compact-row inputs of Wo, Wxo and Wd.  The latent embedding, the heads,
+    the Channel Transformer and the LRP Transformer stay in the compute
+    dtype."""
+    if (not t.matrix or t.name in ("W_in", "W1m", "W2m", "W1s", "W2s") or t.name.startswith("lrp")
+            or t.name.startswith("ct")):
         return False
     K = t.shape[0]
     return K % 128 == 0 and K <= (1024 if t.name.split(".")[-1] in ("Wo", "Wxo", "Wd") else 512)

@@ -155,9 +155,35 @@ def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray, with_
         x2 = x2 + ffn(rms(x2, P["acc.g_ffn"]), P["acc.Wg"], P["acc.Wu"], P["acc.Wd"])
         for l in range(c.L):
             x2 = block(f"sm2.{l}.", x2, S, f)
-        n = rms(x2, P["g_head"])
-        mu = P["gamma_mu"] * (silu(n @ P["W1m"] + P["b1m"]) @ P["W2m"]) + P["beta_mu"]
-        s = P["gamma_sig"] * (silu(n @ P["W1s"] + P["b1s"]) @ P["W2s"]) + P["beta_sig"]
+        if c.Nc:
+            # Channel Transformer over all positions at once: groups as
+            # column blocks, the mask as a Kronecker block pattern
+            G, dg, Cg = c.Nc, c.dc // c.Nc, C // c.Nc
+            grms = lambda x, g: np.concatenate([rms(x[:, j * dg:(j + 1) * dg], g[j * dg:(j + 1) * dg])
+                                                for j in range(G)], axis=1)
+            yl = y[f].reshape(HW, C) * P["ct.gamma_y"]
+            shifted = np.concatenate([np.zeros((HW, dg))] +
+                                     [yl[:, (j - 1) * Cg:j * Cg] @ P["ct.E"][j - 1] for j in range(1, G)], axis=1)
+            h = rms(x2, P["ct.g_in"]) @ P["ct.W_in"] + P["ct.b_in"] + shifted
+            keep = np.kron(np.triu(np.ones((G, G))), np.ones((dg, dg)))      # [in group, out group]: in <= out
+            for l in range(c.Lct):
+                pre = f"ct{l}."
+                h = h + grms(h, P[pre + "g_mix"]) @ (P[pre + "M"] * keep)
+                a = grms(h, P[pre + "g_ffn"])
+                h = h + np.concatenate([ffn(a[:, j * dg:(j + 1) * dg], P[pre + "Wg"][j], P[pre + "Wu"][j],
+                                            P[pre + "Wd"][j]) for j in range(G)], axis=1)
+            x2 = h                                   # the heads' input (and the LRP's representation)
+            n = grms(h, P["g_head"])
+            hm = [silu(n[:, j * dg:(j + 1) * dg] @ P["W1m"][j] + P["b1m"][j * dg:(j + 1) * dg]) @ P["W2m"][j]
+                  for j in range(G)]
+            hs = [silu(n[:, j * dg:(j + 1) * dg] @ P["W1s"][j] + P["b1s"][j * dg:(j + 1) * dg]) @ P["W2s"][j]
+                  for j in range(G)]
+            mu = P["gamma_mu"] * np.concatenate(hm, axis=1) + P["beta_mu"]
+            s = P["gamma_sig"] * np.concatenate(hs, axis=1) + P["beta_sig"]
+        else:
+            n = rms(x2, P["g_head"])
+            mu = P["gamma_mu"] * (silu(n @ P["W1m"] + P["b1m"]) @ P["W2m"]) + P["beta_mu"]
+            s = P["gamma_sig"] * (silu(n @ P["W1s"] + P["b1s"]) @ P["W2s"]) + P["beta_sig"]
         sig = np.exp(np.clip(s, np.log(0.11), np.log(256.0)))
         mus.append(mu.reshape(H, W, C)); sigs.append(sig.reshape(H, W, C))
         if with_eps:

@@ -163,7 +163,7 @@ def test_schedule_step_counts():
 
 # ----------------------------------------------------------- model
 
-@pytest.mark.parametrize("name", ["tiny", "tiny_cyc", "tiny_p"])
+@pytest.mark.parametrize("name", ["tiny", "tiny_cyc", "tiny_p", "tiny_ct", "tiny_cyc_ct", "tiny_p_ct"])
 def test_oracle_matches_dense_mask_formulation(name):
     c = synth.config(name)
     w = synth.weights(c)
@@ -263,12 +263,14 @@ def test_lrp_window_is_spatially_unmasked_and_local():
 
 
 def test_weight_layout_count_matches_generator():
-    for nm in ("tiny", "tiny_p", "i1080", "p1080", "tiny_lrp", "i1080_lrp", "tiny_p_lrp", "p1080_lrp"):
+    for nm in ("tiny", "tiny_p", "i1080", "p1080", "tiny_lrp", "i1080_lrp", "tiny_p_lrp", "p1080_lrp",
+               "tiny_ct", "tiny_p_ct", "tiny_ct_lrp", "i1080_ct", "i1080_cyc_ct"):
         c = synth.config(nm)
         assert O.weights_count(c) == synth.weights_count(c)
 
 
-@pytest.mark.parametrize("name,sched", [("tiny", 0), ("tiny", 1), ("tiny_cyc", 0), ("tiny_p", 0), ("tiny_p", 1)])
+@pytest.mark.parametrize("name,sched", [("tiny", 0), ("tiny", 1), ("tiny_cyc", 0), ("tiny_p", 0), ("tiny_p", 1),
+                                        ("tiny_ct", 0), ("tiny_ct", 1), ("tiny_cyc_ct", 0), ("tiny_p_ct", 0)])
 def test_schedules_give_the_masked_pass_bit_exact(name, sched):
     c = synth.config(name)
     w = synth.weights(c)
@@ -308,6 +310,48 @@ def test_causality_brute_force():
         changed = np.any((mu != mu0) | (s != s0), axis=-1).reshape(HW)
         assert np.array_equal(changed, dep[:, q]), q
         assert np.all(lab[changed] > lab[q]) and np.all(np.nonzero(changed)[0] > q)
+
+
+def test_channel_groups_causal_within_a_position():
+    """Channel Transformer (Sec. 3.1): perturbing the latents of channel
+    group g at position q leaves the parameters of groups 0..g at q as they
+    were and moves those of group g + 1 (the channel shift feeds group g's
+    latents to group g + 1 only; the block-lower-triangular mixing passes
+    them on to later groups); group 0 at q depends on no latent of q."""
+    c = synth.config("tiny_ct")
+    w = synth.weights(c)
+    fr = synth.frames(c, 1, seed=19)
+    mu0, s0 = O.run(c, w, fr.y, fr.z)
+    Cg = c.C // c.Nc
+    qi, qj = 3, 5
+    for g in range(c.Nc):
+        y = fr.y.copy()
+        y[0, qi, qj, g * Cg:(g + 1) * Cg] += 6
+        mu, s = O.run(c, w, y, fr.z)
+        moved = np.any((mu[0, qi, qj] != mu0[0, qi, qj]).reshape(c.Nc, Cg) |
+                       (s[0, qi, qj] != s0[0, qi, qj]).reshape(c.Nc, Cg), axis=1)
+        assert not moved[:g + 1].any(), g
+        if g + 1 < c.Nc:
+            assert moved[g + 1:].all(), g
+    y = fr.y.copy()
+    y[0, qi, qj, :] -= 4
+    mu, s = O.run(c, w, y, fr.z)
+    assert np.array_equal(mu[0, qi, qj, :Cg], mu0[0, qi, qj, :Cg])
+    assert np.array_equal(s[0, qi, qj, :Cg], s0[0, qi, qj, :Cg])
+
+
+def test_channel_transformer_lrp_on_its_output():
+    """The LRP Transformer of a model with a Channel Transformer reads the
+    Channel Transformer's stream (the heads' input): oracle against the
+    dense formulation."""
+    c = synth.config("tiny_ct_lrp")
+    w = synth.weights(c)
+    fr = synth.frames(c, 1, seed=20)
+    _, _, e0 = O.run(c, w, fr.y, fr.z, driver=0, with_eps=True)
+    _, _, e1 = dense_ref.run(c, w, fr.y, fr.z, with_eps=True)
+    assert np.max(np.abs(e0 - e1)) < 1e-11
+    _, _, e2 = O.run(c, w, fr.y, fr.z, driver=1, with_eps=True)
+    assert np.array_equal(e0, e2)
 
 
 # ----------------------------------------------------------- rate, tables
@@ -505,7 +549,7 @@ def test_rans_detects_corruption():
 
 
 def test_encode_decode_round_trip_through_the_model():
-    for nm, nf in (("tiny", 1), ("tiny_p", 3)):
+    for nm, nf in (("tiny", 1), ("tiny_p", 3), ("tiny_ct", 1), ("tiny_cyc_ct", 1), ("tiny_p_ct", 2)):
         c = synth.config(nm)
         w = synth.weights(c)
         fr = synth.frames(c, nf, seed=12)

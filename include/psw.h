@@ -76,13 +76,21 @@ typedef enum {
  *   mask   0 = label 2i+j with the raster clause (wavefront and raster
  *          schedules valid); 1 = cyclic s = 4 label of Fig. 2a.
  *   Llrp   blocks of the LRP Transformer (Sec. 3.1 latent residual
- *          prediction; 0 = none, at most 64), run by psw_lrp_residual. */
+ *          prediction; 0 = none, at most 64), run by psw_lrp_residual.
+ *   Nc     channel groups of the Channel Transformer (Sec. 3.1; Sec. 3.2:
+ *          the decoder runs N channel-group sub-steps per spatial step;
+ *          0 = none: the heads read Spatial Module 2 directly).  With Nc > 0:
+ *          C and dc divisible by Nc, dg = dc / Nc a multiple of 64 and at
+ *          most 512;
+ *   dc     its width; Lct its blocks (1..16); Fc the SwiGLU hidden width of
+ *          each group (a multiple of 64).  All four are 0 without it. */
 typedef struct {
     int C, Ch, r;
     int d, nh, F, L, k;
     int temporal, Lc, Tf;
     int mask;
     int Llrp;
+    int Nc, dc, Lct, Fc;
 } psw_model_desc;
 
 /* One frame: latent grid H x W (hyperprior grid ceil(H/r) x ceil(W/r)) and
@@ -105,9 +113,17 @@ typedef struct {
  *   accumulator: g_q[d] g_kv[d] Wq Wk Wv Wo [d][d] bias[nh][k][k]
  *                g_ffn[d] Wg[d][F] Wu[d][F] Wd[F][d]
  *   L x Spatial Module 2 block (as Spatial Module 1)
- *   heads: g_head[d] W1m[d][d] b1m[d] W2m[d][C] W1s[d][d] b1s[d] W2s[d][C]
+ *   if Nc (the Channel Transformer; dg = dc/Nc, Cg = C/Nc):
+ *          g_in[d] W_in[d][dc] b_in[dc] gamma_y[C] E[Nc-1][Cg][dg]
+ *          Lct x { g_mix[dc] M[dc][dc] g_ffn[dc] Wg[Nc][dg][Fc] Wu[Nc][dg][Fc]
+ *                  Wd[Nc][Fc][dg] }   (M's entries from a later input group
+ *                  than the output group are ignored: the causal mask)
+ *     heads: g_head[dc] W1m[Nc][dg][dg] b1m[dc] W2m[Nc][dg][Cg] W1s[Nc][dg][dg]
+ *          b1s[dc] W2s[Nc][dg][Cg] gamma_mu[C] beta_mu[C] gamma_sig[C] beta_sig[C]
+ *   else heads: g_head[d] W1m[d][d] b1m[d] W2m[d][C] W1s[d][d] b1s[d] W2s[d][C]
  *          gamma_mu[C] beta_mu[C] gamma_sig[C] beta_sig[C]
- *   if Llrp (the LRP Transformer): g_rep[d] W_rep[d][d] gamma_y[C] W_y[C][d] b_in[d]
+ *   if Llrp (the LRP Transformer; dh = dc with a Channel Transformer, else d):
+ *          g_rep[dh] W_rep[dh][d] gamma_y[C] W_y[C][d] b_in[d]
  *          Llrp x { g_attn[d] Wq Wk Wv Wo [d][d] bias[nh][k][k] (temporal:
  *                   bias[nh][Tf][k][k]) g_ffn[d] Wg[d][F] Wu[d][F] Wd[F][d] }
  *          g_out[d] W_eps[d][C] b_eps[C]
@@ -121,8 +137,9 @@ size_t psw_weights_count(const psw_model_desc *desc);
  * shape the E4M3 tile takes -- K a multiple of 128, at most 512 for a
  * normalised input and 1024 for the FFN down projection -- as E4M3 bytes,
  * each source tensor with its own power-of-two scale as psw_quantize_e4m3
- * computes it; the latent embedding, the heads, the LRP Transformer and any
- * other projection in BF16) and builds the scale and CDF tables.
+ * computes it; the latent embedding, the heads, the Channel and LRP
+ * Transformers and any other projection in BF16) and builds the scale and
+ * CDF tables.
  * hbm_budget bounds the device memory of this context and its sequences
  * (0 = no bound); a sequence that would exceed it fails with PSW_ERR_OOM.
  * On failure *out is NULL. */
@@ -174,7 +191,10 @@ psw_status psw_encode_params(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *f
 /* Decoder (Sec. 3.2, Fig. 2): for each step of the schedule, Spatial
  * Module 1 runs on the positions decoded in the previous step, then the
  * accumulator, Spatial Module 2 and heads run on all positions of the step
- * together, their symbols are rANS-decoded and written to yhat.
+ * together, their symbols are rANS-decoded and written to yhat.  With a
+ * Channel Transformer the step ends in Nc sub-steps: the Channel
+ * Transformer and heads of channel group g, then the rANS decode of that
+ * group's channels (their latents feed group g + 1).
  *   bitstream_dev  device container of len bytes (from psw_encode_params)
  *   zhat_dev       hyperlatents as for the encoder
  *   yhat_out_dev   [H][W][C] int16 decoded latents
@@ -206,8 +226,9 @@ psw_status psw_decode_batch(psw_ctx *ctx, int n, psw_seq *const *seqs, const psw
 /* LRP Transformer (Sec. 3.1 latent residual prediction; Sec. 4.3): the
  * residual eps of the sequence's last coded frame, from the quantised
  * latents of that frame and the model's final representation at every
- * position (the Spatial Module 2 stream that fed the heads, kept per
- * position by psw_encode_params and the decoders of a context with Llrp > 0).
+ * position (the heads' input: the Channel Transformer's stream if the model
+ * has one, else the Spatial Module 2 stream; kept per position by
+ * psw_encode_params and the decoders of a context with Llrp > 0).
  * Its input token is RMSNorm(representation) . W_rep + (gamma_y * yhat) . W_y
  * + b_in; Llrp blocks of window self-attention over the whole k x k window
  * (no prediction mask: the frame is decoded) and SwiGLU; then
@@ -317,8 +338,8 @@ psw_status psw_rans_encode_noalloc(const psw_ctx *ctx, const psw_frame_desc *fd,
  * psw_set_engine returns PSW_ERR_INVALID for an unknown engine or for
  * PSW_ENGINE_PERSISTENT on an FP32 context; a decode asked to run
  * persistently on a device that cannot co-schedule the blocks returns
- * PSW_ERR_CUDA; the persistent engine does not run contexts with an LRP
- * Transformer (PSW_ERR_INVALID).  psw_last_engine: the engine of the context's last decode
+ * PSW_ERR_CUDA; the persistent engine does not run contexts with an LRP or a
+ * Channel Transformer (PSW_ERR_INVALID).  psw_last_engine: the engine of the context's last decode
  * (0 = individual launches, as under psw_profile_begin). */
 typedef enum { PSW_ENGINE_AUTO = 0, PSW_ENGINE_GRAPH = 1, PSW_ENGINE_PERSISTENT = 2 } psw_engine;
 psw_status psw_set_engine(psw_ctx *ctx, int engine);

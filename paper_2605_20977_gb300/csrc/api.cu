@@ -40,6 +40,8 @@ struct Layout {
     long lrp_g_rep = -1, lrp_W_rep = -1, lrp_gamma_y = -1, lrp_W_y = -1, lrp_b_in = -1;   // LRP Transformer
     std::vector<BlockOff> lrp;
     long lrp_g_out = -1, lrp_W_eps = -1, lrp_b_eps = -1;
+    long ct_g_in = -1, ct_W_in = -1, ct_b_in = -1, ct_gamma_y = -1, ct_E = -1;   // Channel Transformer
+    std::vector<long> ct_g_mix, ct_M, ct_g_ffn, ct_Wg, ct_Wu, ct_Wd;
     long total;
 };
 
@@ -87,12 +89,28 @@ Layout make_layout(const psw_model_desc &m)
     y.acc_g_ffn = cu.take(m.d);
     y.acc_Wg = cu.take((long)m.d * m.F); y.acc_Wu = cu.take((long)m.d * m.F); y.acc_Wd = cu.take((long)m.F * m.d);
     for (int l = 0; l < m.L; l++) y.sm2.push_back(layout_block(cu, m, m.temporal != 0, false));
-    y.g_head = cu.take(m.d);
-    y.W1m = cu.take(dd); y.b1m = cu.take(m.d); y.W2m = cu.take((long)m.d * m.C);
-    y.W1s = cu.take(dd); y.b1s = cu.take(m.d); y.W2s = cu.take((long)m.d * m.C);
+    if (m.Nc) {
+        long dc = m.dc, dg = dc / m.Nc, Cg = m.C / m.Nc;
+        y.ct_g_in = cu.take(m.d); y.ct_W_in = cu.take((long)m.d * dc); y.ct_b_in = cu.take(dc);
+        y.ct_gamma_y = cu.take(m.C); y.ct_E = cu.take((long)(m.Nc - 1) * Cg * dg);
+        for (int l = 0; l < m.Lct; l++) {
+            y.ct_g_mix.push_back(cu.take(dc)); y.ct_M.push_back(cu.take(dc * dc)); y.ct_g_ffn.push_back(cu.take(dc));
+            y.ct_Wg.push_back(cu.take((long)m.Nc * dg * m.Fc)); y.ct_Wu.push_back(cu.take((long)m.Nc * dg * m.Fc));
+            y.ct_Wd.push_back(cu.take((long)m.Nc * m.Fc * dg));
+        }
+        // grouped heads
+        y.g_head = cu.take(dc);
+        y.W1m = cu.take(m.Nc * dg * dg); y.b1m = cu.take(dc); y.W2m = cu.take(m.Nc * dg * Cg);
+        y.W1s = cu.take(m.Nc * dg * dg); y.b1s = cu.take(dc); y.W2s = cu.take(m.Nc * dg * Cg);
+    } else {
+        y.g_head = cu.take(m.d);
+        y.W1m = cu.take(dd); y.b1m = cu.take(m.d); y.W2m = cu.take((long)m.d * m.C);
+        y.W1s = cu.take(dd); y.b1s = cu.take(m.d); y.W2s = cu.take((long)m.d * m.C);
+    }
     y.gamma_mu = cu.take(m.C); y.beta_mu = cu.take(m.C); y.gamma_sig = cu.take(m.C); y.beta_sig = cu.take(m.C);
     if (m.Llrp) {
-        y.lrp_g_rep = cu.take(m.d); y.lrp_W_rep = cu.take(dd); y.lrp_gamma_y = cu.take(m.C);
+        long dh = m.Nc ? m.dc : m.d;
+        y.lrp_g_rep = cu.take(dh); y.lrp_W_rep = cu.take(dh * m.d); y.lrp_gamma_y = cu.take(m.C);
         y.lrp_W_y = cu.take((long)m.C * m.d); y.lrp_b_in = cu.take(m.d);
         for (int l = 0; l < m.Llrp; l++) y.lrp.push_back(layout_block(cu, m, false, m.temporal != 0));
         y.lrp_g_out = cu.take(m.d); y.lrp_W_eps = cu.take((long)m.d * m.C); y.lrp_b_eps = cu.take(m.C);
@@ -115,6 +133,17 @@ bool desc_valid(const psw_model_desc *m, std::string &why)
     if (m->k < 1 || m->k % 2 == 0 || m->k * m->k > MAX_KK) { why = "k must be odd with k*k <= 81"; return false; }
     if (m->mask != 0 && m->mask != 1) { why = "mask must be 0 or 1"; return false; }
     if (m->Llrp < 0 || m->Llrp > 64) { why = "Llrp must be in [0, 64]"; return false; }
+    if (m->Nc == 0) {
+        if (m->dc || m->Lct || m->Fc) { why = "dc, Lct and Fc must be 0 without channel groups"; return false; }
+    } else {
+        if (m->Nc < 1 || m->Nc > 16 || m->C % m->Nc || m->dc < 64 || m->dc % m->Nc) {
+            why = "channel groups: 1 <= Nc <= 16 dividing C and dc"; return false;
+        }
+        int dg = m->dc / m->Nc;
+        if (dg % 64 || dg > 512) { why = "dc / Nc must be a multiple of 64, at most 512"; return false; }
+        if (m->Lct < 1 || m->Lct > 16) { why = "Lct must be in [1, 16]"; return false; }
+        if (m->Fc < 64 || m->Fc % 64 || m->Fc > 16384) { why = "Fc must be a multiple of 64 in [64, 16384]"; return false; }
+    }
     if (m->temporal == 1) {
         if (m->Lc < 1 || m->Lc > 64) { why = "Lc must be in [1, 64]"; return false; }
         if (m->Tf < 1 || m->Tf > MAX_TF || m->Tf * m->k * m->k > 256) { why = "need Tf <= 4 and Tf*k*k <= 256"; return false; }
@@ -175,7 +204,13 @@ struct psw_ctx {
     char *wmat = nullptr;              // arena of transposed projections
     std::vector<BlockDev> ctxb, sm1, sm2, lrpb;
     BlockDev acc;                      // Wqkv = [Wq]; Wxkv = [Wk; Wv]
-    void *Wrep = nullptr, *Wy = nullptr, *Weps = nullptr;   // LRP input [d][d], [d][C] and output [C][d] projections
+    void *Wrep = nullptr, *Wy = nullptr, *Weps = nullptr;   // LRP input [d][dh], [d][C] and output [C][d] projections
+    // Channel Transformer (index g of group g, l * Nc + g of block l): input
+    // rows [dg][d] of W_in, the mixing operand [dg][(g + 1) dg] (input groups
+    // 0..g of output group g), SwiGLU [Fc][dg] x 2 and [dg][Fc]; grouped
+    // heads [2 dg][dg], interleaved [2 Cg][2 dg] and their first-layer bias
+    std::vector<void *> ct_win, ct_mix, ct_wg, ct_wu, ct_wd, ct_wh1, ct_wh2;
+    std::vector<float *> ct_bh1;
     void *Win = nullptr;               // latent embedding [d][C]
     void *Wh1 = nullptr;               // heads, first layers [W1m; W1s]: [2d][d]
     void *Wh2 = nullptr;               // heads, second layers interleaved: row 2c = mu_c, 2c+1 = sigma_c: [2C][2d]
@@ -189,6 +224,8 @@ struct psw_ctx {
     // shared per-launch workspace (compact token rows) and the slot table
     void *Xn = nullptr, *Q = nullptr, *O = nullptr, *Hid = nullptr;
     float *Xa = nullptr, *Xb = nullptr, *Xg = nullptr;   // FP32 residual rows: SM1 / accumulator+SM2 / context
+    float *Xc = nullptr;               // Channel Transformer rows, group-major: group g at Xc + g * ws_rows * dg
+    void *NM = nullptr;                // its normalised mixing inputs [Lct][ws_rows][dc] (compute type)
     size_t ws_rows = 0, ws_bytes = 0;
     int ws_gen = 0;
     Slot *d_slots = nullptr, *h_slots = nullptr;
@@ -410,20 +447,48 @@ bool prepare_projections(psw_ctx *c, bool dry)
     no8 = true;
     for (int l = 0; l < m.Llrp; l++) lrpb.push_back(mk_block(lay.lrp[l], false));
     if (m.Llrp) {
-        wrep = operand(d, d, A_NORM, {lay.lrp_W_rep});
+        wrep = operand(d, m.Nc ? m.dc : d, A_NORM, {lay.lrp_W_rep});
         weps = operand(m.C, d, A_NORM, {lay.lrp_W_eps});
+    }
+    // the Channel Transformer's projections stay in the compute type as well
+    std::vector<void *> ct_win, ct_mix, ct_wg, ct_wu, ct_wd, ct_wh1, ct_wh2;
+    std::vector<float *> ct_bh1;
+    const int G = m.Nc, dg = G ? m.dc / G : 0, Cg = G ? m.C / G : 0;
+    if (G) {
+        char *win = (char *)operand(m.dc, d, A_NORM, {lay.ct_W_in});
+        for (int g = 0; g < G; g++) ct_win.push_back(dry ? nullptr : win + (size_t)g * dg * d * es);
+        for (int l = 0; l < m.Lct; l++)
+            for (int g = 0; g < G; g++) {
+                ct_wg.push_back(operand(m.Fc, dg, A_NORM, {lay.ct_Wg[l] + (long)g * dg * m.Fc}));
+                ct_wu.push_back(operand(m.Fc, dg, A_NORM, {lay.ct_Wu[l] + (long)g * dg * m.Fc}));
+                ct_wd.push_back(operand(dg, m.Fc, A_DIRECT, {lay.ct_Wd[l] + (long)g * m.Fc * dg}));
+                ct_mix.push_back(carve(dg, (size_t)(g + 1) * dg));      // assembled below
+            }
+        for (int g = 0; g < G; g++) {
+            void *h1 = carve(2 * dg, dg);
+            tr(lay.W1m + (long)g * dg * dg, dg, dg, h1, 0);
+            tr(lay.W1s + (long)g * dg * dg, dg, dg, h1, dg);
+            ct_wh1.push_back(h1);
+            ct_wh2.push_back(carve(2 * (size_t)Cg, 2 * dg));             // assembled below
+            ct_bh1.push_back((float *)carve(2 * dg, es == 2 ? 2 : 1));   // 2 dg floats
+        }
     }
     cudaFree(stage);
     if (!ok) return false;
     void *win = carve(d, m.C); tr(lay.W_in, m.C, d, win, 0);
     if (m.Llrp) { wy = carve(d, m.C); tr(lay.lrp_W_y, m.C, d, wy, 0); }
-    void *wh1 = carve(2 * d, d); tr(lay.W1m, d, d, wh1, 0); tr(lay.W1s, d, d, wh1, d);
-    void *wh2 = carve(2 * (size_t)m.C, 2 * d);
-    float *bh1 = (float *)carve(2 * d, es == 2 ? 2 : 1);        // 2d floats
+    // the plain heads (the grouped heads of a Channel Transformer replace them)
+    void *wh1 = nullptr, *wh2 = nullptr;
+    float *bh1 = nullptr;
+    if (!G) {
+        wh1 = carve(2 * d, d); tr(lay.W1m, d, d, wh1, 0); tr(lay.W1s, d, d, wh1, d);
+        wh2 = carve(2 * (size_t)m.C, 2 * d);
+        bh1 = (float *)carve(2 * d, es == 2 ? 2 : 1);            // 2d floats
+    }
     if (dry) { c->arena = used; return true; }
     if (used > c->arena) return false;
     // interleaved block-diagonal second layer, assembled in FP32 then converted
-    {
+    if (!G) {
         std::vector<float> w2m((size_t)d * m.C), w2s((size_t)d * m.C), buf((size_t)2 * m.C * 2 * d, 0.0f);
         cudaMemcpy(w2m.data(), c->w + lay.W2m, w2m.size() * 4, cudaMemcpyDeviceToHost);
         cudaMemcpy(w2s.data(), c->w + lay.W2s, w2s.size() * 4, cudaMemcpyDeviceToHost);
@@ -441,8 +506,49 @@ bool prepare_projections(psw_ctx *c, bool dry)
         cudaMemcpy(bh1, c->w + lay.b1m, d * 4, cudaMemcpyDeviceToDevice);
         cudaMemcpy(bh1 + d, c->w + lay.b1s, d * 4, cudaMemcpyDeviceToDevice);
     }
+    if (G) {
+        // mixing operands: output group g's columns of M over input groups
+        // 0..g (the block-lower-triangular mask), [K = (g+1) dg][N = dg] in
+        // FP32, then transposed and converted; grouped heads' second layers
+        // interleaved as for the plain heads
+        const int dc = m.dc;
+        std::vector<float> M((size_t)dc * dc), buf;
+        float *tmp = nullptr;
+        if (cudaMalloc(&tmp, (size_t)dc * dc * 4) != cudaSuccess) return false;
+        for (int l = 0; l < m.Lct; l++) {
+            cudaMemcpy(M.data(), c->w + lay.ct_M[l], M.size() * 4, cudaMemcpyDeviceToHost);
+            for (int g = 0; g < G; g++) {
+                int K = (g + 1) * dg;
+                buf.assign((size_t)K * dg, 0.0f);
+                for (int i = 0; i < K; i++)
+                    for (int o = 0; o < dg; o++) buf[(size_t)i * dg + o] = M[(size_t)i * dc + g * dg + o];
+                cudaMemcpy(tmp, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice);
+                launch_transpose_convert(prec, tmp, K, dg, ct_mix[(size_t)l * G + g], 0, 0);
+                cudaDeviceSynchronize();
+            }
+        }
+        std::vector<float> w2m((size_t)dg * Cg), w2s((size_t)dg * Cg);
+        for (int g = 0; g < G; g++) {
+            cudaMemcpy(w2m.data(), c->w + lay.W2m + (long)g * dg * Cg, w2m.size() * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(w2s.data(), c->w + lay.W2s + (long)g * dg * Cg, w2s.size() * 4, cudaMemcpyDeviceToHost);
+            buf.assign((size_t)2 * Cg * 2 * dg, 0.0f);
+            for (int ch = 0; ch < Cg; ch++)
+                for (int e = 0; e < dg; e++) {
+                    buf[(size_t)(2 * ch) * 2 * dg + e] = w2m[(size_t)e * Cg + ch];
+                    buf[(size_t)(2 * ch + 1) * 2 * dg + dg + e] = w2s[(size_t)e * Cg + ch];
+                }
+            cudaMemcpy(tmp, buf.data(), buf.size() * 4, cudaMemcpyHostToDevice);
+            launch_convert(prec, tmp, buf.size(), ct_wh2[g], 0);
+            cudaDeviceSynchronize();
+            cudaMemcpy(ct_bh1[g], c->w + lay.b1m + (long)g * dg, dg * 4, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(ct_bh1[g] + dg, c->w + lay.b1s + (long)g * dg, dg * 4, cudaMemcpyDeviceToDevice);
+        }
+        cudaFree(tmp);
+    }
     c->ctxb = ctxb; c->sm1 = sm1; c->sm2 = sm2; c->acc = ab;
     c->lrpb = lrpb; c->Wrep = wrep; c->Wy = wy; c->Weps = weps;
+    c->ct_win = ct_win; c->ct_mix = ct_mix; c->ct_wg = ct_wg; c->ct_wu = ct_wu; c->ct_wd = ct_wd;
+    c->ct_wh1 = ct_wh1; c->ct_wh2 = ct_wh2; c->ct_bh1 = ct_bh1;
     c->Win = win; c->Wh1 = wh1; c->Wh2 = wh2; c->bh1 = bh1;
     return true;
 }
@@ -521,6 +627,25 @@ Slot make_slot(const psw_seq *q, int H, int W_, int sched, int frame = -1)
 
 // ---------------------------------------------------------------- workspace
 
+// Workspace bytes for `rows` token rows: operand rows (queries, attention
+// output, normalised or embedding operands: the widest token operand),
+// hidden rows (SwiGLU, heads), the FP32 residual rows of Spatial Module 1,
+// the accumulator / Spatial Module 2 and the Context Transformer, and the
+// Channel Transformer's FP32 rows and normalised mixing inputs.
+void ws_sizes(const psw_model_desc &m, int prec, size_t rows, size_t &bd, size_t &bf, size_t &bx, size_t &bg,
+              size_t &bc, size_t &bn)
+{
+    size_t es = esize(prec);
+    int wop = std::max({m.d, m.C, m.Nc ? m.dc : 0});
+    int whid = std::max({m.F, 2 * m.d, m.Nc ? m.Fc : 0, m.Nc ? 2 * (m.dc / m.Nc) : 0});
+    bd = rows * wop * es;
+    bf = rows * whid * es;
+    bx = rows * m.d * 4;
+    bg = m.temporal ? bx : 16;
+    bc = m.Nc ? rows * m.dc * 4 : 16;
+    bn = m.Nc ? (size_t)m.Lct * rows * m.dc * es : 16;
+}
+
 psw_status ensure_workspace(psw_ctx *c, size_t rows)
 {
     if (rows <= c->ws_rows) return PSW_OK;
@@ -528,20 +653,21 @@ psw_status ensure_workspace(psw_ctx *c, size_t rows)
     size_t es = esize(c->prec);
     CK_CUDA(c, cudaDeviceSynchronize());
     cudaFree(c->Xn); cudaFree(c->Q); cudaFree(c->O); cudaFree(c->Hid);
-    cudaFree(c->Xa); cudaFree(c->Xb); cudaFree(c->Xg);
-    c->Xn = c->Q = c->O = c->Hid = nullptr;
-    c->Xa = c->Xb = c->Xg = nullptr;
+    cudaFree(c->Xa); cudaFree(c->Xb); cudaFree(c->Xg); cudaFree(c->Xc); cudaFree(c->NM);
+    c->Xn = c->Q = c->O = c->Hid = c->NM = nullptr;
+    c->Xa = c->Xb = c->Xg = c->Xc = nullptr;
     c->bytes -= c->ws_bytes;
     c->ws_rows = 0; c->ws_bytes = 0;
-    size_t bd = rows * std::max(m.d, m.C) * es, bf = rows * std::max(m.F, 2 * m.d) * es, bx = rows * m.d * 4;
-    size_t bg = m.temporal ? bx : 16;
+    size_t bd, bf, bx, bg, bc, bn;
+    ws_sizes(m, c->prec, rows, bd, bf, bx, bg, bc, bn);
     if (cudaMalloc(&c->Xn, bd) != cudaSuccess || cudaMalloc(&c->Q, bd) != cudaSuccess ||
         cudaMalloc(&c->O, bd) != cudaSuccess || cudaMalloc(&c->Hid, bf) != cudaSuccess ||
         cudaMalloc(&c->Xa, bx) != cudaSuccess || cudaMalloc(&c->Xb, bx) != cudaSuccess ||
-        cudaMalloc(&c->Xg, bg) != cudaSuccess)
+        cudaMalloc(&c->Xg, bg) != cudaSuccess || cudaMalloc(&c->Xc, bc) != cudaSuccess ||
+        cudaMalloc(&c->NM, bn) != cudaSuccess)
         return fail(c, PSW_ERR_OOM, "workspace of %zu rows", rows);
     c->ws_rows = rows;
-    c->ws_bytes = 3 * bd + bf + 2 * bx + bg;
+    c->ws_bytes = 3 * bd + bf + 2 * bx + bg + bc + bn;
     c->bytes += c->ws_bytes;
     c->ws_gen++;
     for (auto &kv : c->graphs) graph_free(kv.second);
@@ -797,11 +923,12 @@ void run_acc_sm2_heads(const Pass &P, const int *tok, int n)
     ffn(P, c->acc, c->lay.acc_g_ffn, c->Xb, tok, n);
     for (int l = 0; l < m.L; l++)
         spatial_block(P, c->lay.sm2[l], c->sm2[l], m.L + l, c->Xb, CS_K2, CS_V2, l, tok, n);
+    if (m.Nc) return;                  // the Channel Transformer's groups follow (run_ct_group)
     if (m.Llrp) {
         // the final representation at these positions, kept for the LRP
         // Transformer (the persistent decoder has no phase for it)
         if (P.rec) *P.failed = true;
-        else LAUNCH(P, K_OTHER, 0.0, (double)n * d * 8.0, launch_store_rows(P.S, tok, n, c->Xb, d, P.s));
+        else LAUNCH(P, K_OTHER, 0.0, (double)n * d * 8.0, launch_store_rows(P.S, tok, n, c->Xb, d, d, 0, P.s));
     }
     // prediction heads (Sec. 3.1): RMSNorm, both first layers as one
     // projection with bias and SiLU, then both second layers as one
@@ -813,6 +940,60 @@ void run_acc_sm2_heads(const Pass &P, const int *tok, int n)
     eh.gmu = W(c, c->lay.gamma_mu); eh.bmu = W(c, c->lay.beta_mu);
     eh.gsg = W(c, c->lay.gamma_sig); eh.bsg = W(c, c->lay.beta_sig);
     gemm_call(P, c->Hid, 2 * d, c->Wh2, nullptr, n, 2 * m.C, 2 * d, eh);
+}
+
+// Channel Transformer and grouped heads of channel group g (Sec. 3.1
+// Channel Transformer paragraph; Sec. 3.2: N channel groups after the s
+// spatial steps) on the tokens tok[0..n), whose Spatial Module 2 rows are in
+// Xb.  The group's FP32 rows (its own block of Xc) start as the normalised
+// Spatial Module 2 rows projected to the group plus, with the channel shift,
+// the embedding of group g - 1's latents; each block writes the group's
+// normalised rows into the block's mixing input NM (groups 0..g-1 were
+// written by the earlier sub-steps on the same tokens), adds the masked
+// mixing of input groups 0..g, then the group's SwiGLU; the grouped heads
+// write the parameters of the group's channels.  Every launch is per token,
+// so encoder and decoder (and any batch) compute the same bits.
+void run_ct_group(const Pass &P, const int *tok, int n, int g)
+{
+    psw_ctx *c = P.c;
+    const psw_model_desc &m = c->md;
+    const Layout &y = c->lay;
+    if (n <= 0) return;
+    const int G = m.Nc, dc = m.dc, dg = dc / G, Cg = m.C / G, d = m.d;
+    const size_t es = esize(c->prec);
+    float *Xg = c->Xc + (size_t)g * c->ws_rows * dg;
+    gemm_norm(P, c->Xb, y.ct_g_in, c->ct_win[g], nullptr, n, dg, d, epi_set_bias(tok, Xg, W(c, y.ct_b_in) + g * dg));
+    if (g > 0) {
+        P.xn_rows = nullptr;                           // rows written outside gemm_any
+        LAUNCH(P, K_EMBED, 2.0 * n * Cg * dg, n * (Cg * 2.0 + dg * 8.0),
+               launch_ct_embed(P.S, tok, n, m.C, (g - 1) * Cg, Cg, W(c, y.ct_gamma_y) + (g - 1) * Cg,
+                               W(c, y.ct_E) + (long)(g - 1) * Cg * dg, dg, Xg, P.s));
+    }
+    for (int l = 0; l < m.Lct; l++) {
+        const int bi = l * G + g;
+        char *nm = (char *)c->NM + (size_t)l * c->ws_rows * dc * es;
+        const float *gm = W(c, y.ct_g_mix[l]) + g * dg;
+        if (c->prec == P_BF16) {
+            LAUNCH(P, K_NORM, 0.0, (double)n * dg * 6.0,
+                   if (!launch_norm_rows(Xg, gm, n, dg, nm + (size_t)g * dg * es, P.s, dc)) *P.failed = true);
+        } else {
+            LAUNCH(P, K_NORM, 0.0, (double)n * dg * 8.0,
+                   launch_rmsnorm(c->prec, Xg, n, gm, dg, nm + (size_t)g * dg * es, P.s, dc));
+        }
+        gemm_call(P, nm, dc, c->ct_mix[bi], nullptr, n, dg, (g + 1) * dg, epi_resid(tok, Xg));
+        Epi sw = epi_swiglu(c->Hid, m.Fc);
+        sw.tok = tok;
+        gemm_norm(P, Xg, y.ct_g_ffn[l] + g * dg, c->ct_wg[bi], c->ct_wu[bi], n, m.Fc, dg, sw);
+        gemm_call(P, c->Hid, m.Fc, c->ct_wd[bi], nullptr, n, dg, m.Fc, epi_resid(tok, Xg));
+    }
+    if (m.Llrp) LAUNCH(P, K_OTHER, 0.0, (double)n * dg * 8.0, launch_store_rows(P.S, tok, n, Xg, dg, dc, g * dg, P.s));
+    gemm_norm(P, Xg, y.g_head + g * dg, c->ct_wh1[g], nullptr, n, 2 * dg, dg,
+              epi_bias_silu(tok, c->Hid, 2 * dg, c->ct_bh1[g]));
+    Epi eh{};
+    eh.mode = EPI_HEADS; eh.tok = tok; eh.st_sel = CS_NONE; eh.C = m.C; eh.c0 = g * Cg; eh.scale = c->d_scale;
+    eh.gmu = W(c, y.gamma_mu) + g * Cg; eh.bmu = W(c, y.beta_mu) + g * Cg;
+    eh.gsg = W(c, y.gamma_sig) + g * Cg; eh.bsg = W(c, y.beta_sig) + g * Cg;
+    gemm_call(P, c->Hid, 2 * dg, c->ct_wh2[g], nullptr, n, 2 * Cg, 2 * dg, eh);
 }
 
 // LRP Transformer over every position of one coded frame (Sec. 3.1 latent
@@ -832,7 +1013,7 @@ void run_lrp(const Pass &P, const int *tok, int n, const float *rep, float *eps)
     P.xn_rows = nullptr;
     gemm_any(P, A_EMBED, nullptr, W(c, y.lrp_gamma_y), nullptr, 0, c->Wy, nullptr, n, d, m.C,
              epi_set_bias(tok, c->Xa, W(c, y.lrp_b_in)));
-    gemm_norm(P, rep, y.lrp_g_rep, c->Wrep, nullptr, n, d, d, epi_resid(tok, c->Xa));
+    gemm_norm(P, rep, y.lrp_g_rep, c->Wrep, nullptr, n, d, m.Nc ? m.dc : d, epi_resid(tok, c->Xa));
     for (int l = 0; l < m.Llrp; l++) {
         const BlockOff &bo = y.lrp[l];
         const BlockDev &bd = c->lrpb[l];
@@ -857,7 +1038,7 @@ bool ensure_program(psw_ctx *c)
     c->prog = nullptr;
     c->prog_ok = false;
     c->prog_gen = c->ws_gen;
-    if (c->prec != P_BF16 || c->ws_rows == 0 || c->md.Llrp) return false;
+    if (c->prec != P_BF16 || c->ws_rows == 0 || c->md.Llrp || c->md.Nc) return false;
     c->prog = program_new((int)c->ws_rows);
     c->p_flops_tok[0] = c->p_flops_tok[1] = c->p_bytes_tok[0] = c->p_bytes_tok[1] = c->p_wbytes = 0;
     bool failed = false;
@@ -904,7 +1085,7 @@ size_t seq_bytes_for(const psw_model_desc &m, int prec, int H, int W_)
     b += (size_t)m.C * 32 * 4 + 2 * (size_t)m.C * 4 + (2 * (size_t)m.C + 1) * 4;
     b += (size_t)m.C * (3 * HW + 64) * 2;                           // encoder scratch
     b += HW * 4 + 64;
-    if (m.Llrp) b += HW * d * 4 + 2 * (size_t)m.Llrp * (m.temporal ? m.Tf : 1) * HW * d * es;   // rep, LK, LV
+    if (m.Llrp) b += HW * (m.Nc ? m.dc : d) * 4 + 2 * (size_t)m.Llrp * (m.temporal ? m.Tf : 1) * HW * d * es;   // rep, LK, LV
     return b;
 }
 
@@ -1011,8 +1192,13 @@ void enqueue_decode(psw_ctx *c, const DecodePlan &D, const int *d_tok, const int
     for (int t = t0; t < t1; t++) {
         if (t > 0) run_sm1(P, d_tok + D.step_off[t - 1], D.step_n[t - 1]);
         run_acc_sm2_heads(P, d_tok + D.step_off[t], D.step_n[t]);
-        Scope sc(c, s, K_RANS, 0.0, (double)D.step_n[t] * c->md.C * 9.0);
-        launch_rans_dec_step(coder(c), c->d_slots, D.n, d_kn + (size_t)t * D.n, c->md.C, s);
+        const int G = std::max(c->md.Nc, 1), Cg = c->md.C / G;
+        for (int g = 0; g < G; g++) {
+            // with a Channel Transformer, group g's parameters, then its symbols
+            if (c->md.Nc) run_ct_group(P, d_tok + D.step_off[t], D.step_n[t], g);
+            Scope sc(c, s, K_RANS, 0.0, (double)D.step_n[t] * Cg * 9.0);
+            launch_rans_dec_step(coder(c), c->d_slots, D.n, d_kn + (size_t)t * D.n, c->md.C, s, g * Cg, Cg);
+        }
     }
     if (t1 == D.Tmax) {
         Scope sc(c, s, K_RANS, 0.0, (double)D.n * c->md.C * 128.0);
@@ -1345,7 +1531,7 @@ void psw_destroy(psw_ctx *c)
     cudaFree(c->w); cudaFree(c->wmat); cudaFree(c->d_cdf); cudaFree(c->d_meta); cudaFree(c->d_scale);
     cudaFree(c->rate_buf); cudaFree(c->d_slots); cudaFree(c->d_status); cudaFree(c->d_tok); cudaFree(c->d_kn);
     cudaFree(c->Xn); cudaFree(c->Q); cudaFree(c->O); cudaFree(c->Hid);
-    cudaFree(c->Xa); cudaFree(c->Xb); cudaFree(c->Xg);
+    cudaFree(c->Xa); cudaFree(c->Xb); cudaFree(c->Xg); cudaFree(c->Xc); cudaFree(c->NM);
     if (c->h_rate) cudaFreeHost(c->h_rate);
     if (c->h_slots) cudaFreeHost(c->h_slots);
     if (c->h_status) cudaFreeHost(c->h_status);
@@ -1363,9 +1549,11 @@ psw_status psw_seq_create(psw_ctx *c, int max_H, int max_W, psw_seq **out)
         return fail(c, PSW_ERR_INVALID, "bad maximum grid %dx%d", max_H, max_W);
     size_t need = seq_bytes_for(c->md, c->prec, max_H, max_W);
     size_t ws_more = 0, HW = (size_t)max_H * max_W;
-    if (HW > c->ws_rows)
-        ws_more = HW * (3 * (size_t)std::max(c->md.d, c->md.C) + std::max(c->md.F, 2 * c->md.d)) * esize(c->prec) +
-                  HW * c->md.d * 4 * (c->md.temporal ? 3 : 2) - c->ws_bytes;
+    if (HW > c->ws_rows) {
+        size_t bd, bf, bx, bg, bc, bn;
+        ws_sizes(c->md, c->prec, HW, bd, bf, bx, bg, bc, bn);
+        ws_more = 3 * bd + bf + 2 * bx + bg + bc + bn - c->ws_bytes;
+    }
     size_t used = c->bytes;
     for (psw_seq *s : c->seqs) used += s->bytes;
     if (c->budget && used + need + ws_more > c->budget)
@@ -1395,7 +1583,7 @@ psw_status psw_seq_create(psw_ctx *c, int max_H, int max_W, psw_seq **out)
     }
     if (m.Llrp) {
         size_t lb = (size_t)m.Llrp * (m.temporal ? m.Tf : 1) * HW * d * es;
-        q->rep = (float *)dal(HW * d * 4);
+        q->rep = (float *)dal(HW * (m.Nc ? m.dc : d) * 4);
         q->LK = dal(lb); q->LV = dal(lb);
     }
     q->mu = (float *)dal(HW * m.C * 4); q->sigma = (float *)dal(HW * m.C * 4);
@@ -1489,6 +1677,7 @@ psw_status psw_encode_params(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, c
     frame_prologue(P, c->d_tok, fd->H, fd->W, q->eh);
     run_sm1(P, c->d_tok, HW);
     run_acc_sm2_heads(P, c->d_tok, HW);
+    for (int g = 0; g < c->md.Nc; g++) run_ct_group(P, c->d_tok, HW, g);
     if (mu_dev) CK_CUDA(c, cudaMemcpyAsync(mu_dev, q->mu, nsym * 4, cudaMemcpyDeviceToDevice, s));
     if (sigma_dev) CK_CUDA(c, cudaMemcpyAsync(sigma_dev, q->sigma, nsym * 4, cudaMemcpyDeviceToDevice, s));
     CK_CUDA(c, cudaGetLastError());
@@ -1705,8 +1894,8 @@ psw_status psw_set_engine(psw_ctx *c, int engine)
         return fail(c, PSW_ERR_INVALID, "unknown engine %d", engine);
     if (engine == PSW_ENGINE_PERSISTENT && c->prec != P_BF16)
         return fail(c, PSW_ERR_INVALID, "the persistent decoder runs BF16 and FP8 contexts only");
-    if (engine == PSW_ENGINE_PERSISTENT && c->md.Llrp)
-        return fail(c, PSW_ERR_INVALID, "the persistent decoder does not run contexts with an LRP Transformer");
+    if (engine == PSW_ENGINE_PERSISTENT && (c->md.Llrp || c->md.Nc))
+        return fail(c, PSW_ERR_INVALID, "the persistent decoder does not run contexts with an LRP or a Channel Transformer");
     c->engine = engine;
     return PSW_OK;
 }

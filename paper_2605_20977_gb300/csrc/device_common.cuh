@@ -118,7 +118,7 @@ __device__ __forceinline__ void heads_pair(const Epi &e, const float *scale, int
 {
     int tk = e.tok[m];
     const Slot &s = e.slots[tok_slot(tk)];
-    long o = (long)tok_pos(tk) * e.C + (n >> 1);
+    long o = (long)tok_pos(tk) * e.C + e.c0 + (n >> 1);
     int c = n >> 1;
     float mu = e.gmu[c] * ymu + e.bmu[c];
     float sg = expf(fminf(fmaxf(e.gsg[c] * ysg + e.bsg[c], LN_SIG_LO), LN_SIG_HI));

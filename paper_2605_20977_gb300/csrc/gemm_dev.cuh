@@ -733,10 +733,11 @@ __device__ __forceinline__ void table_row(const GemmArgs &g, int m0, int r, uint
     } else if (MODE == EPI_RESID_BASE) {
         tab[ts + r] = (uintptr_t)(s.eh + (long)p * g.N);
     } else if (MODE == EPI_HEADS) {
-        tab[r] = (uintptr_t)(s.mu + (long)p * e.C);
-        tab[ts + r] = (uintptr_t)(s.sigma + (long)p * e.C);
-        tab[2 * ts + r] = (uintptr_t)(s.idx + (long)p * e.C);
-        tab[3 * ts + r] = (uintptr_t)(s.m + (long)p * e.C);
+        const long o = (long)p * e.C + e.c0;
+        tab[r] = (uintptr_t)(s.mu + o);
+        tab[ts + r] = (uintptr_t)(s.sigma + o);
+        tab[2 * ts + r] = (uintptr_t)(s.idx + o);
+        tab[3 * ts + r] = (uintptr_t)(s.m + o);
     }
 }
 

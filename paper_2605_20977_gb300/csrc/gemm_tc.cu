@@ -58,7 +58,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
 // block (norm_row_global: the same values a tile would build).
 template <int CH>
 __global__ void __launch_bounds__(256) k_norm_rows(const float *__restrict__ X, const float *__restrict__ gain, int M,
-                                                   int K, __nv_bfloat16 *__restrict__ dst)
+                                                   int K, __nv_bfloat16 *__restrict__ dst, int ldd)
 {
     pdl_trigger();
     float4 gh[CH];
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_norm_rows(const float *__restrict__ X, 
     const float invK = 1.0f / (float)K;
     const int m = blockIdx.x * 8 + (threadIdx.x >> 5);
     pdl_wait();
-    if (m < M) norm_row_global<CH>(X + (long)m * K, gh, invK, K, dst + (long)m * K);
+    if (m < M) norm_row_global<CH>(X + (long)m * K, gh, invK, K, dst + (long)m * ldd);
 }
 
 // ---------------------------------------------------------------- host side
@@ -172,13 +172,14 @@ __global__ void k_quant_e4m3(const float *__restrict__ src, size_t n, float qmul
 
 }  // namespace
 
-bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst, cudaStream_t s)
+bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst, cudaStream_t s, int ldd)
 {
     if (M <= 0) return true;
-    if (K > KRES_MAX || K % 4) return false;
+    if (ldd <= 0) ldd = K;
+    if (K > KRES_MAX || K % 4 || ldd < K || ldd % 8 || ((uintptr_t)dst & 15)) return false;
     dim3 grid((M + 7) / 8), block(256);
-    cudaError_t e = K <= 384 ? launch_pdl(k_norm_rows<3>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst)
-                             : launch_pdl(k_norm_rows<4>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst);
+    cudaError_t e = K <= 384 ? launch_pdl(k_norm_rows<3>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst, ldd)
+                             : launch_pdl(k_norm_rows<4>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst, ldd);
     return e == cudaSuccess;
 }
 

@@ -477,7 +477,7 @@ bool gemm_takes_ws(int prec, const GemmArgs &g)
 bool gemm_ws_supported(const GemmArgs &g)
 {
     const int m = g.epi.mode;
-    if (m == EPI_HEADS && (g.epi.C % 16 || g.N != 2 * g.epi.C)) return false;
+    if (m == EPI_HEADS && (g.epi.C % 16 || g.epi.c0 % 16 || g.N % 32 || g.epi.c0 + g.N / 2 > g.epi.C)) return false;
     if (m == EPI_QKV && (g.epi.d % 32 || g.epi.q_cols % 32 || g.epi.ld_out % 8)) return false;
     if (m == EPI_STORE && g.epi.st_sel == CS_NONE && g.epi.ld_out % 8) return false;
     if ((m == EPI_STORE || m == EPI_QKV) && g.epi.d % 8) return false;

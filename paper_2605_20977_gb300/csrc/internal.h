@@ -112,7 +112,8 @@ struct Epi {
     const float *bias;            // EPI_BIAS_SILU, EPI_SET_BIAS
     const float *gmu, *bmu, *gsg, *bsg;   // EPI_HEADS channel-wise scale and offset
     const float *scale;           // EPI_HEADS scale table [64]
-    int C;                        // EPI_HEADS channels
+    int C;                        // EPI_HEADS channels of a position's mu / sigma row
+    int c0;                       // EPI_HEADS first channel this projection writes (its N / 2 channels follow)
 };
 
 // Source of the token operand of a GEMM.
@@ -147,10 +148,11 @@ struct GemmArgs {
 // bit-identical results, so the choice never changes a value.  Returns
 // false if the launch could not be prepared.
 bool gemm(int prec, const GemmArgs &g, cudaStream_t s);
-// dst[m][k] = bf16(RMSNorm(X[m]) * gain) for m < M, K <= 512 (a multiple of
-// 4): the normalised token operand of a projection whose tiles then stream
-// it (A_DIRECT), bit-identical to the operand an A_NORM tile builds.
-bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst, cudaStream_t s);
+// dst[m * ldd + k] = bf16(RMSNorm(X[m]) * gain) for m < M, K <= 512 (a
+// multiple of 4; ldd 0 means K, else a multiple of 8 and >= K): the
+// normalised token operand of a projection whose tiles then stream it
+// (A_DIRECT), bit-identical to the operand an A_NORM tile builds.
+bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst, cudaStream_t s, int ldd = 0);
 // The persistent warp-specialised kernel for launches with many token tiles
 // (gemm_ws.cu): BF16, a streamed token operand (A_DIRECT), the epilogues of
 // block projections and heads; bit-identical to the one-tile-per-CTA kernel.
@@ -204,11 +206,18 @@ void launch_embed_context(const Slot *S, const int *tok, int n, int C, const flo
                           const float *b, const float *pad, int d, float *out, cudaStream_t s);
 void launch_embed_hyper(const Slot *S, const int *tok, int n, int H, int W, int Ch, int r, const float *gamma,
                         const float *Whp, const float *b, int d, cudaStream_t s);
-void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void *dst, cudaStream_t s);
-// rep[position] = X[m] (d floats, d a multiple of 4) for each token m of a
-// slot whose rep pointer is set: the Spatial Module 2 stream kept for the
-// LRP Transformer.
-void launch_store_rows(const Slot *S, const int *tok, int n, const float *X, int d, cudaStream_t s);
+// dst[w * ldd + e] = RMSNorm(X[w]) * g in the compute type (ldd 0: d); the
+// SIMT path's operand.
+void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void *dst, cudaStream_t s, int ldd = 0);
+// rep[position * ld + off + e] = X[m * w + e] (e < w; w, ld, off multiples
+// of 4) for each token m of a slot whose rep pointer is set: the heads'
+// input kept for the LRP Transformer.
+void launch_store_rows(const Slot *S, const int *tok, int n, const float *X, int w, int ld, int off, cudaStream_t s);
+// Channel Transformer, channel shift: X[m][e] += sum_c (gamma[c] y[c0 + c])
+// E[c][e] over the Cg latents of the previous channel group at the token's
+// position (FP32, c ascending), e < dg.
+void launch_ct_embed(const Slot *S, const int *tok, int n, int C, int c0, int Cg, const float *gamma, const float *E,
+                     int dg, float *X, cudaStream_t s);
 
 struct AttnArgs {
     const int *tok; int n;
@@ -259,7 +268,9 @@ void launch_rans_assemble(int H, int W, int C, int sched, const uint16_t *scratc
 // Validate each slot's container (bs, len, H, W, sched) and load its states.
 void launch_rans_dec_init(const Slot *S, int nslots, int C, cudaStream_t s);
 // kn[b] = (first symbol, count) of slot b in this step (count 0: idle).
-void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const int2 *kn, int C, cudaStream_t s);
+// Channels [c0, c0 + nc) only (nc = C: every channel).
+void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const int2 *kn, int C, cudaStream_t s,
+                          int c0 = 0, int nc = -1);
 void launch_rans_dec_finish(const Slot *S, int nslots, int C, cudaStream_t s);
 
 

@@ -160,7 +160,8 @@ void launch_embed_hyper(const Slot *S, const int *tok, int n, int H, int W, int 
 // One warp per row: y = x / sqrt(mean(x^2) + 1e-6) * g, FP32 statistics,
 // a fixed lane assignment and butterfly reduction (the SIMT path's operand).
 template <typename T>
-__global__ void k_rmsnorm(const float *__restrict__ X, int n, const float *__restrict__ g, int d, T *__restrict__ dst)
+__global__ void k_rmsnorm(const float *__restrict__ X, int n, const float *__restrict__ g, int d, T *__restrict__ dst,
+                          int ldd)
 {
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= n) return;
@@ -169,40 +170,69 @@ __global__ void k_rmsnorm(const float *__restrict__ X, int n, const float *__res
     for (int e = lane; e < d; e += 32) ss = fmaf(x[e], x[e], ss);
     ss = warp_sum(ss);
     float inv = 1.0f / sqrtf(ss / (float)d + 1e-6f);
-    T *y = dst + (long)w * d;
+    T *y = dst + (long)w * ldd;
     for (int e = lane; e < d; e += 32) y[e] = from_f<T>(x[e] * inv * g[e]);
 }
 
-void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void *dst, cudaStream_t s)
+void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void *dst, cudaStream_t s, int ldd)
 {
     if (n <= 0) return;
+    if (ldd <= 0) ldd = d;
     int blocks = cdiv((long)n * 32, 256);
-    if (prec == P_BF16) k_rmsnorm<__nv_bfloat16><<<blocks, 256, 0, s>>>(X, n, g, d, (__nv_bfloat16 *)dst);
-    else k_rmsnorm<float><<<blocks, 256, 0, s>>>(X, n, g, d, (float *)dst);
+    if (prec == P_BF16) k_rmsnorm<__nv_bfloat16><<<blocks, 256, 0, s>>>(X, n, g, d, (__nv_bfloat16 *)dst, ldd);
+    else k_rmsnorm<float><<<blocks, 256, 0, s>>>(X, n, g, d, (float *)dst, ldd);
 }
 
-// rep[position][e] = X[m][e]: one float4 per thread, tokens of slots
+// rep[position][off + e] = X[m][e]: one float4 per thread, tokens of slots
 // without a rep buffer skipped.  A plain launch: it starts after its
 // predecessor has finished.
 __global__ void k_store_rows(const Slot *__restrict__ S, const int *__restrict__ tok, int n,
-                             const float *__restrict__ X, int d4)
+                             const float *__restrict__ X, int w4, int ld4, int off4)
 {
-    const long total = (long)n * d4;
+    const long total = (long)n * w4;
     for (long a = blockIdx.x * (long)blockDim.x + threadIdx.x; a < total; a += (long)gridDim.x * blockDim.x) {
-        const int m = (int)(a / d4), e = (int)(a - (long)m * d4);
+        const int m = (int)(a / w4), e = (int)(a - (long)m * w4);
         const int tk = tok[m];
         float *rep = S[tok_slot(tk)].rep;
         if (!rep) continue;
-        reinterpret_cast<float4 *>(rep)[(long)tok_pos(tk) * d4 + e] = reinterpret_cast<const float4 *>(X)[a];
+        reinterpret_cast<float4 *>(rep)[(long)tok_pos(tk) * ld4 + off4 + e] = reinterpret_cast<const float4 *>(X)[a];
     }
 }
 
-void launch_store_rows(const Slot *S, const int *tok, int n, const float *X, int d, cudaStream_t s)
+void launch_store_rows(const Slot *S, const int *tok, int n, const float *X, int w, int ld, int off, cudaStream_t s)
 {
     if (n <= 0) return;
-    long total = (long)n * (d / 4);
+    long total = (long)n * (w / 4);
     int blocks = (int)std::min<long>(cdiv(total, 256), 152 * 8);
-    k_store_rows<<<blocks, 256, 0, s>>>(S, tok, n, X, d / 4);
+    k_store_rows<<<blocks, 256, 0, s>>>(S, tok, n, X, w / 4, ld / 4, off / 4);
+}
+
+// Channel shift of the Channel Transformer: one block per token, the
+// channel-scaled latents of the previous group in shared memory, thread e
+// owns output column e (and e + blockDim, ...), summing over c in ascending
+// order before adding to the row.  A plain launch.
+__global__ void k_ct_embed(const Slot *__restrict__ S, const int *__restrict__ tok, int C, int c0, int Cg,
+                           const float *__restrict__ gamma, const float *__restrict__ E, int dg, float *__restrict__ X)
+{
+    extern __shared__ float t[];
+    const int tk = tok[blockIdx.x];
+    const Slot &s = S[tok_slot(tk)];
+    const int16_t *y = s.y + (long)tok_pos(tk) * C + c0;
+    for (int c = threadIdx.x; c < Cg; c += blockDim.x) t[c] = gamma[c] * (float)y[c];
+    __syncthreads();
+    float *x = X + (long)blockIdx.x * dg;
+    for (int e = threadIdx.x; e < dg; e += blockDim.x) {
+        float acc = 0.0f;
+        for (int c = 0; c < Cg; c++) acc = fmaf(t[c], E[(long)c * dg + e], acc);
+        x[e] += acc;
+    }
+}
+
+void launch_ct_embed(const Slot *S, const int *tok, int n, int C, int c0, int Cg, const float *gamma, const float *E,
+                     int dg, float *X, cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_ct_embed<<<n, 128, Cg * sizeof(float), s>>>(S, tok, C, c0, Cg, gamma, E, dg, X);
 }
 
 // ---------------------------------------------------------------- attention

@@ -280,19 +280,23 @@ void launch_rans_dec_init(const Slot *S, int nslots, int C, cudaStream_t s)
 
 // One schedule step of every channel of every slot: one warp per (slot,
 // channel), see rans_step_item.
+// Warp w takes channel c0 + w % nc of slot w / nc.
 __global__ void k_rans_dec_step(CoderDev cd, const Slot *__restrict__ S, int nslots,
-                                const int2 *__restrict__ kn, int C)
+                                const int2 *__restrict__ kn, int C, int c0, int nc)
 {
-    int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (wi >= nslots * C) return;
-    rans_step_item<true>(cd, S, kn, C, wi);
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nslots * nc) return;
+    int b = w / nc, c = c0 + (w - b * nc);
+    rans_step_item<true>(cd, S, kn, C, b * C + c);
 }
 
-void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const int2 *kn, int C, cudaStream_t s)
+void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const int2 *kn, int C, cudaStream_t s,
+                          int c0, int nc)
 {
-    int warps = nslots * C;
+    if (nc < 0) nc = C;
+    int warps = nslots * nc;
     if (warps <= 0) return;
-    launch_pdl(k_rans_dec_step, dim3((warps * 32 + 127) / 128), dim3(128), 0, s, cd, S, nslots, kn, C);
+    launch_pdl(k_rans_dec_step, dim3((warps * 32 + 127) / 128), dim3(128), 0, s, cd, S, nslots, kn, C, c0, nc);
 }
 
 // After the last step every lane must be back at the initial state and

@@ -33,7 +33,7 @@ ENGINE_AUTO, ENGINE_GRAPH, ENGINE_PERSISTENT = 0, 1, 2
 
 class ModelDesc(ct.Structure):
     _fields_ = [(n, ct.c_int) for n in ("C", "Ch", "r", "d", "nh", "F", "L", "k", "temporal", "Lc", "Tf", "mask",
-                                         "Llrp")]
+                                         "Llrp", "Nc", "dc", "Lct", "Fc")]
 
 
 class FrameDesc(ct.Structure):

@@ -390,15 +390,19 @@ def lrp_run(args, dev, timed, ys, zs):
     return out
 
 
-def cyclic_run(args, dev, timed, w, ys, zs, B):
+def cyclic_run(args, dev, timed, w, ys, zs, B, name="i1080_cyc"):
     """The paper's own schedule (cyclic s = 4 mask, Fig. 2a): the same model
     sizes and frames, 4 steps per frame of 2040 positions each.  Frames/s at
     B frames per call, single-frame latency, and the projections' tensor
     rate from one instrumented step (about 261 k tokens per launch at 128
-    frames)."""
+    frames).  name = "i1080_cyc_ct" adds the Channel Transformer (4 channel
+    groups after each spatial step: s x N = 16 steps per frame, the paper's
+    configuration), with its own weights."""
     import torch
     from paper_2605_20977_gb300 import psw, synth
-    cfg = synth.config("i1080_cyc")
+    cfg = synth.config(name)
+    if cfg.Nc:
+        w = synth.weights(cfg)
     ctx = psw.Context(cfg, w, precision=psw.PSW_BF16)
     fd = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_WAVEFRONT)
     cap = ctx.bitstream_capacity(cfg.H, cfg.W)
@@ -432,10 +436,12 @@ def cyclic_run(args, dev, timed, w, ys, zs, B):
     g = next((s_ for s_ in stats if s_["name"] == "gemm_tc"), None)
     nrm = next((s_ for s_ in stats if s_["name"] == "rmsnorm"), None)
     out = {"value": B * 1e3 / float(np.mean(ms)), "unit": "frames/s", "frames_per_step": B,
-           "ms_per_step": float(np.mean(ms)), "steps_per_frame": 4,
+           "ms_per_step": float(np.mean(ms)), "steps_per_frame": 4 * max(cfg.Nc, 1),
            "latency_one_frame": {"ms_per_frame": float(np.mean(lat)), "frames_per_s": 1e3 / float(np.mean(lat))},
-           "workload": "1080p I-frames 68x120x192 with the cyclic s = 4 mask (Fig. 2a), same model sizes and "
-                       "frames as the headline, BF16",
+           "workload": ("1080p I-frames 68x120x192 with the cyclic s = 4 mask (Fig. 2a), same model sizes and "
+                        "frames as the headline, BF16") + (
+                           f"; Channel Transformer with N = {cfg.Nc} groups, width {cfg.dc}, {cfg.Lct} blocks "
+                           f"(16 autoregressive steps per frame)" if cfg.Nc else ""),
            "classes": {s_["name"]: {"ms": round(s_["ms"], 3), "launches": s_["launches"],
                                     "gflop": round(s_["flops"] / 1e9, 2)} for s_ in stats}}
     if g:
@@ -688,6 +694,11 @@ def run_ours(args, rank: int, world: int, local: int):
     if rank == 0 and args.cyclic_steps > 0 and args.precision == "bf16":
         cyclic = cyclic_run(args, dev, timed, w, ys, zs, B)
 
+    # the paper's configuration: cyclic s = 4 plus the Channel Transformer
+    cyclic_ct = None
+    if rank == 0 and args.cyclic_steps > 0 and args.precision == "bf16":
+        cyclic_ct = cyclic_run(args, dev, timed, w, ys, zs, B, name="i1080_cyc_ct")
+
     # the LRP Transformer over one coded frame
     lrp = None
     if rank == 0 and args.lrp_steps > 0 and args.precision == "bf16":
@@ -736,7 +747,7 @@ def run_ours(args, rank: int, world: int, local: int):
             "latency_one_frame": lat,
             "roofline": roof, "raster": raster, "speedup_vs_raster": speedup,
             "rate": rate, "clocks": clk, "cpu_baseline": cpu, "pframe": pframe, "fp8": fp8, "cyclic": cyclic,
-            "lrp": lrp}
+            "cyclic_channel_groups": cyclic_ct, "lrp": lrp}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
 class _Cfg(ct.Structure):
     _fields_ = [(n, ct.c_int) for n in
                 ("H", "W", "C", "Hh", "Wh", "Ch", "r", "d", "nh", "F", "L", "k",
-                 "temporal", "Lc", "Tf", "mask", "Llrp", "Nc", "dc", "Lct", "Fc")]
+                 "temporal", "Lc", "Tf", "mask", "Llrp", "Nc", "dc", "Lct", "Fc", "hp")]
 
 
 def _load():
@@ -76,6 +76,13 @@ def _load():
             lib.or_run.argtypes = [ct.POINTER(_Cfg), P, ct.c_int, P, P, ct.c_int, ct.c_int, P, P, P, P]
             lib.or_run_lrp.argtypes = [ct.POINTER(_Cfg), P, ct.c_int, P, P, ct.c_int, ct.c_int, P, P, P, P, P]
             lib.or_num_threads.restype = ct.c_int
+            lib.or_hyper_analysis.argtypes = [ct.POINTER(_Cfg), P, ct.c_int, P, P, P]
+            lib.or_hyper_encode.argtypes = [ct.POINTER(_Cfg), P, P, P, ct.c_long]
+            lib.or_hyper_encode.restype = ct.c_long
+            lib.or_hyper_decode.argtypes = [ct.POINTER(_Cfg), P, P, ct.c_long, P]
+            lib.or_prior_freq.argtypes = [ct.POINTER(_Cfg), P, ct.c_int, P]
+            lib.or_hyper_rate.argtypes = [ct.POINTER(_Cfg), P, P]
+            lib.or_hyper_rate.restype = ct.c_double
             _lib = lib
     return _lib
 
@@ -234,6 +241,56 @@ def rans_decode(c, sched: int, idx, m, bs: bytes):
     rc = _load().or_rans_decode(c.H, c.W, c.C, sched, _p(order), _p(start), len(start) - 1,
                                 _p(idx), _p(m), _p(buf), len(buf), _p(y))
     return rc == 0, y
+
+
+# ---------------------------------------------------------------- hyperprior
+
+def hyper_analysis(c, w, y):
+    """(z-hat int16, z float64) [nf][Hh][Wh][Ch] of a convolutional
+    hyperprior model from the frames' latents y [nf][H][W][C]."""
+    w = np.ascontiguousarray(w, np.float64)
+    y = np.ascontiguousarray(y, np.int16)
+    nf = y.shape[0]
+    zh = np.zeros((nf, c.Hh, c.Wh, c.Ch), np.int16)
+    z = np.zeros(zh.shape, np.float64)
+    if _load().or_hyper_analysis(ct.byref(_cfg(c)), _p(w), nf, _p(y), _p(zh), _p(z)) != 0:
+        raise ValueError("hyper_analysis failed")
+    return zh, z
+
+
+def hyper_encode(c, w, zhat, cap: int | None = None) -> bytes:
+    """z-hat container of one frame ([Hh][Wh][Ch]) under the factorized prior."""
+    w = np.ascontiguousarray(w, np.float64)
+    zhat = np.ascontiguousarray(zhat, np.int16)
+    cap = cap or (16 + 4 * (c.Ch + 1) + c.Ch * (132 + 6 * c.Hh * c.Wh))
+    out = np.zeros(cap, np.uint8)
+    n = _load().or_hyper_encode(ct.byref(_cfg(c)), _p(w), _p(zhat), _p(out), cap)
+    if n < 0:
+        raise ValueError(f"hyper_encode failed ({n})")
+    return out[:n].tobytes()
+
+
+def hyper_decode(c, w, bs: bytes):
+    """(ok, z-hat [Hh][Wh][Ch]) from a z-hat container."""
+    w = np.ascontiguousarray(w, np.float64)
+    buf = np.frombuffer(bs, np.uint8).copy()
+    zh = np.zeros((c.Hh, c.Wh, c.Ch), np.int16)
+    rc = _load().or_hyper_decode(ct.byref(_cfg(c)), _p(w), _p(buf), len(buf), _p(zh))
+    return rc == 0, zh
+
+
+def prior_freq(c, w, ch: int) -> np.ndarray:
+    """Integer frequency table of channel ch of the factorized prior."""
+    w = np.ascontiguousarray(w, np.float64)
+    f = np.zeros(4096, np.uint32)
+    n = _load().or_prior_freq(ct.byref(_cfg(c)), _p(w), ch, _p(f))
+    return f[:n].copy()
+
+
+def hyper_rate(c, w, zhat) -> float:
+    w = np.ascontiguousarray(w, np.float64)
+    zhat = np.ascontiguousarray(zhat, np.int16)
+    return float(_load().or_hyper_rate(ct.byref(_cfg(c)), _p(w), _p(zhat)))
 
 
 # ---------------------------------------------------------------- model

@@ -26,7 +26,12 @@
  *     positions of the same step; 2D windows.
  *   Sec. 4.1: 7x7 spatial windows, T x 7 x 7 temporal windows.
  *   Fig. 1 (right): Q / AE / AD -- realised here as a Gaussian scale table,
- *     integer CDF tables and interleaved rANS (the paper names no coder).
+ *     integer CDF tables and interleaved rANS (the paper names no coder);
+ *     the convolutional hyperprior (down- and upsampling residual blocks,
+ *     z-hat coded under a factorized prior).
+ *   Sec. 3.1 (Channel Transformer paragraph), Sec. 3.2 (s spatial steps
+ *     times N channel groups), Sec. 4.1 (N = 4, width 1024, 2 blocks).
+ *   Sec. 3.1 (LRP paragraph), Sec. 4.3 (time-causal LRP Transformer).
  *
  * Readings of silent points (each is listed in the design notes):
  *   - step label l(i,j) = 2i+j with an extra raster clause rho(q) < rho(p) in
@@ -65,6 +70,9 @@ typedef struct {
     int Llrp;             /* LRP Transformer blocks (0: none)                */
     int Nc, dc, Lct, Fc;  /* Channel Transformer: groups (0: none), width,
                              blocks, SwiGLU width per group                */
+    int hp;               /* 1: convolutional hyperprior (RB blocks) with a
+                             factorized prior for z; 0: z given, embedded
+                             by a transposed convolution                   */
 } or_cfg;
 
 typedef struct {
@@ -79,9 +87,19 @@ typedef struct {
 
 #define OR_MAXL 64
 
+/* A down- or upsampling residual block of the hyperprior (Fig. 1 right). */
+typedef struct {
+    long Wa, ba, Wb, bb, Ws, bs;
+} or_rb;
+
+#define OR_MAXRB 4
+
 typedef struct {
     long gamma_in, W_in, b_in;
     long gamma_z, W_hp, b_hp;
+    long g_za;                                   /* hyperprior analysis input gain */
+    or_rb rbd[OR_MAXRB], rbu[OR_MAXRB];          /* analysis / synthesis blocks    */
+    long fp_H1, fp_b1, fp_a1, fp_H2, fp_b2, fp_a2, fp_H3, fp_b3, fp_a3, fp_H4, fp_b4;   /* factorized prior */
     long gamma_c, W_c, b_c, pad, g_ctx;
     or_blk ctx[OR_MAXL], sm1[OR_MAXL], sm2[OR_MAXL];
     or_accw acc;
@@ -96,6 +114,15 @@ typedef struct {
 } or_layout;
 
 static long take(long *cur, long n) { long o = *cur; *cur += n; return o; }
+
+/* Residual blocks per hyperprior transform: log2 r (each halves or
+ * doubles the grid); -1 if r is not a power of two in [2, 16]. */
+int or_hyper_blocks(const or_cfg *c)
+{
+    for (int b = 1; b <= OR_MAXRB; b++)
+        if (c->r == (1 << b)) return b;
+    return -1;
+}
 
 /* Packing order of the flat weight vector (all matrices are [in][out], used
  * as x . W).  The order is an interface, documented with the C-ABI. */
@@ -125,8 +152,32 @@ static void make_layout(const or_cfg *c, or_layout *lay)
     lay->W_in = take(&cur, (long)c->C * c->d);
     lay->b_in = take(&cur, c->d);
     lay->gamma_z = take(&cur, c->Ch);
-    lay->W_hp = take(&cur, (long)c->r * c->r * c->Ch * c->d);
-    lay->b_hp = take(&cur, c->d);
+    if (c->hp) {
+        int nb = or_hyper_blocks(c);
+        long Ch = c->Ch;
+        lay->W_hp = lay->b_hp = -1;
+        lay->g_za = take(&cur, c->d);
+        for (int b = 0; b < nb; b++) {          /* analysis: d -> Ch, then Ch -> Ch */
+            long Ci = b == 0 ? c->d : Ch, Co = Ch;
+            lay->rbd[b].Wa = take(&cur, 9 * Ci * Co); lay->rbd[b].ba = take(&cur, Co);
+            lay->rbd[b].Wb = take(&cur, 9 * Co * Co); lay->rbd[b].bb = take(&cur, Co);
+            lay->rbd[b].Ws = take(&cur, Ci * Co); lay->rbd[b].bs = take(&cur, Co);
+        }
+        for (int b = 0; b < nb; b++) {          /* synthesis: Ch -> Ch, last Ch -> d */
+            long Ci = Ch, Co = b == nb - 1 ? c->d : Ch;
+            lay->rbu[b].Wa = take(&cur, 9 * Ci * 4 * Co); lay->rbu[b].ba = take(&cur, 4 * Co);
+            lay->rbu[b].Wb = take(&cur, 9 * Co * Co); lay->rbu[b].bb = take(&cur, Co);
+            lay->rbu[b].Ws = take(&cur, 9 * Ci * 4 * Co); lay->rbu[b].bs = take(&cur, 4 * Co);
+        }
+        lay->fp_H1 = take(&cur, Ch * 3); lay->fp_b1 = take(&cur, Ch * 3); lay->fp_a1 = take(&cur, Ch * 3);
+        lay->fp_H2 = take(&cur, Ch * 9); lay->fp_b2 = take(&cur, Ch * 3); lay->fp_a2 = take(&cur, Ch * 3);
+        lay->fp_H3 = take(&cur, Ch * 9); lay->fp_b3 = take(&cur, Ch * 3); lay->fp_a3 = take(&cur, Ch * 3);
+        lay->fp_H4 = take(&cur, Ch * 3); lay->fp_b4 = take(&cur, Ch);
+    } else {
+        lay->W_hp = take(&cur, (long)c->r * c->r * c->Ch * c->d);
+        lay->b_hp = take(&cur, c->d);
+        lay->g_za = -1;
+    }
     if (c->temporal) {
         lay->gamma_c = take(&cur, c->C);
         lay->W_c = take(&cur, (long)c->C * c->d);
@@ -198,6 +249,7 @@ long or_weights_count(const or_cfg *c)
 {
     or_layout lay;
     if (c->L > OR_MAXL || c->Lc > OR_MAXL || c->Llrp > OR_MAXL || c->Lct > OR_MAXL) return -1;
+    if (c->hp && or_hyper_blocks(c) < 0) return -1;
     make_layout(c, &lay);
     return lay.total;
 }
@@ -407,9 +459,12 @@ static void embed_latent(const or_state *s, const int16_t *yv, long g_off, long 
  * the transformer as the accumulator's query and residual).  A transposed
  * convolution with kernel = stride = r: the hyperpixel above (i, j) times the
  * sub-position weight (i mod r, j mod r), plus a bias. */
+static void hyper_synthesis(or_state *s, const int16_t *zhat);
+
 static void embed_hyper(or_state *s, const int16_t *zhat)
 {
     const or_cfg *c = s->c;
+    if (c->hp) { hyper_synthesis(s, zhat); return; }
     for (int p = 0; p < s->HW; p++) {
         int i = p / c->W, j = p % c->W;
         const int16_t *zv = zhat + ((long)(i / c->r) * c->Wh + (j / c->r)) * c->Ch;
@@ -421,6 +476,143 @@ static void embed_hyper(or_state *s, const int16_t *zhat)
         for (int e = 0; e < c->d; e++) o[e] += WP(s->lay.b_hp)[e];
         free(t);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Convolutional hyperprior (Fig. 1 right: RB-down x2 -> z -> Q -> AE/AD      */
+/* with a factorized prior -> z-hat -> RB-up x2)                              */
+/* ------------------------------------------------------------------------ */
+/* Grids are channel-last [h][w][C].  The residual blocks follow the down-
+ * and upsampling residual blocks of DCVC-DC that the paper cites: a strided
+ * (or sub-pixel) 3x3 convolution and LeakyReLU, a 3x3 convolution, and a
+ * strided 1x1 (or sub-pixel 3x3) convolution on the skip path. */
+
+static double or_lrelu(double x) { return x >= 0.0 ? x : 0.01 * x; }
+
+/* 3x3 convolution, zero padding 1, stride st: out [ho][wo][Co] with
+ * ho = ceil(h / st); W [3][3][Ci][Co]; taps and input channels summed in
+ * ascending order after the bias. */
+static void or_conv3(const double *x, int h, int w, int Ci, const double *W, const double *b, int Co, int st,
+                     double *out)
+{
+    int ho = (h - 1) / st + 1, wo = (w - 1) / st + 1;
+    for (int i = 0; i < ho; i++)
+        for (int j = 0; j < wo; j++) {
+            double *o = out + ((long)i * wo + j) * Co;
+            for (int q = 0; q < Co; q++) o[q] = b[q];
+            for (int di = 0; di < 3; di++)
+                for (int dj = 0; dj < 3; dj++) {
+                    int ii = st * i + di - 1, jj = st * j + dj - 1;
+                    if (ii < 0 || ii >= h || jj < 0 || jj >= w) continue;
+                    const double *xv = x + ((long)ii * w + jj) * Ci;
+                    const double *Wt = W + (long)(di * 3 + dj) * Ci * Co;
+                    for (int c = 0; c < Ci; c++)
+                        for (int q = 0; q < Co; q++) o[q] += xv[c] * Wt[(long)c * Co + q];
+                }
+        }
+}
+
+/* 1x1 convolution with stride 2: out [ceil(h/2)][ceil(w/2)][Co]. */
+static void or_conv1s2(const double *x, int h, int w, int Ci, const double *W, const double *b, int Co, double *out)
+{
+    int ho = (h + 1) / 2, wo = (w + 1) / 2;
+    for (int i = 0; i < ho; i++)
+        for (int j = 0; j < wo; j++) {
+            double *o = out + ((long)i * wo + j) * Co;
+            const double *xv = x + ((long)(2 * i) * w + 2 * j) * Ci;
+            for (int q = 0; q < Co; q++) o[q] = b[q];
+            for (int c = 0; c < Ci; c++)
+                for (int q = 0; q < Co; q++) o[q] += xv[c] * W[(long)c * Co + q];
+        }
+}
+
+/* Pixel shuffle by 2: u [h][w][4C] -> v [2h][2w][C],
+ * v[2i + a][2j + b][c] = u[i][j][(2a + b) C + c]. */
+static void or_shuffle(const double *u, int h, int w, int C, double *v)
+{
+    for (int i = 0; i < h; i++)
+        for (int j = 0; j < w; j++)
+            for (int a = 0; a < 2; a++)
+                for (int b = 0; b < 2; b++)
+                    for (int c = 0; c < C; c++)
+                        v[((long)(2 * i + a) * 2 * w + 2 * j + b) * C + c] = u[((long)i * w + j) * 4 * C + (2 * a + b) * C + c];
+}
+
+/* RB-down: out = conv3(LReLU(conv3_s2(x) + ba)) + bb + (conv1_s2(x) + bs). */
+static double *or_rb_down(const or_state *s, const or_rb *rb, const double *x, int h, int w, int Ci, int Co)
+{
+    int ho = (h + 1) / 2, wo = (w + 1) / 2;
+    long n = (long)ho * wo * Co;
+    double *a = zalloc(n), *t = zalloc(n), *k = zalloc(n);
+    or_conv3(x, h, w, Ci, WP(rb->Wa), WP(rb->ba), Co, 2, a);
+    for (long e = 0; e < n; e++) a[e] = or_lrelu(a[e]);
+    or_conv3(a, ho, wo, Co, WP(rb->Wb), WP(rb->bb), Co, 1, t);
+    or_conv1s2(x, h, w, Ci, WP(rb->Ws), WP(rb->bs), Co, k);
+    for (long e = 0; e < n; e++) t[e] += k[e];
+    free(a); free(k);
+    return t;
+}
+
+/* RB-up: out = conv3(LReLU(shuffle(conv3(x) + ba))) + bb
+ *              + shuffle(conv3(x) + bs) (sub-pixel convolutions). */
+static double *or_rb_up(const or_state *s, const or_rb *rb, const double *x, int h, int w, int Ci, int Co)
+{
+    long nl = (long)h * w * 4 * Co, n = nl;
+    double *u = zalloc(nl), *a = zalloc(n), *t = zalloc(n), *k = zalloc(n);
+    or_conv3(x, h, w, Ci, WP(rb->Wa), WP(rb->ba), 4 * Co, 1, u);
+    or_shuffle(u, h, w, Co, a);
+    for (long e = 0; e < n; e++) a[e] = or_lrelu(a[e]);
+    or_conv3(a, 2 * h, 2 * w, Co, WP(rb->Wb), WP(rb->bb), Co, 1, t);
+    or_conv3(x, h, w, Ci, WP(rb->Ws), WP(rb->bs), 4 * Co, 1, u);
+    or_shuffle(u, h, w, Co, k);
+    for (long e = 0; e < n; e++) t[e] += k[e];
+    free(u); free(a); free(k);
+    return t;
+}
+
+/* Hyperprior synthesis: the channel-scaled z-hat through the RB-up blocks
+ * (Ch -> Ch, ..., last Ch -> d) to the grid (Hh r) x (Wh r), cropped to
+ * H x W: the hyperprior tokens. */
+static void hyper_synthesis(or_state *s, const int16_t *zhat)
+{
+    const or_cfg *c = s->c;
+    int nb = or_hyper_blocks(c), h = c->Hh, w = c->Wh;
+    double *x = zalloc((long)h * w * c->Ch);
+    for (long p = 0; p < (long)h * w; p++)
+        for (int ch = 0; ch < c->Ch; ch++) x[p * c->Ch + ch] = WP(s->lay.gamma_z)[ch] * (double)zhat[p * c->Ch + ch];
+    for (int b = 0; b < nb; b++) {
+        int Co = b == nb - 1 ? c->d : c->Ch;
+        double *y = or_rb_up(s, &s->lay.rbu[b], x, h, w, c->Ch, Co);
+        free(x);
+        x = y; h *= 2; w *= 2;
+    }
+    for (int i = 0; i < c->H; i++)
+        memcpy(s->eh + (long)i * c->W * c->d, x + (long)i * w * c->d, sizeof(double) * c->W * c->d);
+    free(x);
+}
+
+/* Hyperprior analysis: RMSNorm of the Spatial Module 1 output at every
+ * position through the RB-down blocks (d -> Ch, then Ch -> Ch) to z on the
+ * ceil(H/r) x ceil(W/r) grid; z-hat = round-half-even(z), clamped to int16. */
+static void hyper_analysis(or_state *s, int16_t *zhat, double *z_out)
+{
+    const or_cfg *c = s->c;
+    int nb = or_hyper_blocks(c), h = c->H, w = c->W, Ci = c->d;
+    double *x = zalloc((long)h * w * c->d);
+    for (int p = 0; p < s->HW; p++) or_rmsnorm(s->x1 + (long)p * c->d, WP(s->lay.g_za), c->d, x + (long)p * c->d);
+    for (int b = 0; b < nb; b++) {
+        double *y = or_rb_down(s, &s->lay.rbd[b], x, h, w, Ci, c->Ch);
+        free(x);
+        x = y; h = (h + 1) / 2; w = (w + 1) / 2; Ci = c->Ch;
+    }
+    for (long e = 0; e < (long)h * w * c->Ch; e++) {
+        double r = nearbyint(x[e]);
+        if (r < -32768.0) r = -32768.0;
+        if (r > 32767.0) r = 32767.0;
+        zhat[e] = (int16_t)r;
+        if (z_out) z_out[e] = x[e];
+    }
+    free(x);
 }
 
 /* Temporal cross-attention of one query over the co-located T x k x k
@@ -1018,19 +1210,115 @@ double or_rate_bits(long n, const int16_t *y, const double *mu, const double *si
 
 typedef struct { uint32_t *cum, *freq; int *T, *n; } or_tables;
 
+static void tables_alloc(or_tables *tb, int nt)
+{
+    tb->cum = (uint32_t *)malloc(sizeof(uint32_t) * nt * 4096);
+    tb->freq = (uint32_t *)malloc(sizeof(uint32_t) * nt * 4096);
+    tb->T = (int *)malloc(sizeof(int) * nt);
+    tb->n = (int *)malloc(sizeof(int) * nt);
+}
+
+static void tables_cum(or_tables *tb, int l)
+{
+    uint32_t *f = tb->freq + (long)l * 4096, *cm = tb->cum + (long)l * 4096, acc = 0;
+    for (int s = 0; s < tb->n[l]; s++) { cm[s] = acc; acc += f[s]; }
+}
+
 static void tables_build(or_tables *tb)
 {
-    tb->cum = (uint32_t *)malloc(sizeof(uint32_t) * OR_NSCALES * 4096);
-    tb->freq = (uint32_t *)malloc(sizeof(uint32_t) * OR_NSCALES * 4096);
-    tb->T = (int *)malloc(sizeof(int) * OR_NSCALES);
-    tb->n = (int *)malloc(sizeof(int) * OR_NSCALES);
+    tables_alloc(tb, OR_NSCALES);
     for (int l = 0; l < OR_NSCALES; l++) {
-        uint32_t *f = tb->freq + (long)l * 4096, *cm = tb->cum + (long)l * 4096;
-        tb->n[l] = or_cdf_freq(l, f);
+        tb->n[l] = or_cdf_freq(l, tb->freq + (long)l * 4096);
         tb->T[l] = or_cdf_T(l);
-        uint32_t acc = 0;
-        for (int s = 0; s < tb->n[l]; s++) { cm[s] = acc; acc += f[s]; }
+        tables_cum(tb, l);
     }
+}
+
+/* Factorized prior of z-hat (Fig. 1 right "Factorized Prior"; the
+ * univariate non-parametric density of Balle et al. 2018 that the
+ * hyperprior literature uses): per channel a cumulative
+ * c(x) = sigmoid(f4(f3(f2(f1(x))))) through widths 1 -> 3 -> 3 -> 3 -> 1, with
+ * f_k(v) = g_k(softplus(H_k) v + b_k), g_k(t) = t + tanh(a_k) tanh(t) for
+ * k < 4 (elementwise), f_4 affine; softplus keeps every matrix entry
+ * positive, so c is increasing.  P(z-hat = k) = c(k + 1/2) - c(k - 1/2).
+ * Sums run over ascending inputs after the bias. */
+static double fp_softplus(double x) { return x > 30.0 ? x : log1p(exp(x)); }
+
+static double prior_cdf(const double *w, const or_layout *L, int ch, double x)
+{
+    double v1[3], v2[3], v3[3];
+    for (int i = 0; i < 3; i++) {
+        double t = w[L->fp_b1 + ch * 3 + i] + fp_softplus(w[L->fp_H1 + ch * 3 + i]) * x;
+        v1[i] = t + tanh(w[L->fp_a1 + ch * 3 + i]) * tanh(t);
+    }
+    for (int i = 0; i < 3; i++) {
+        double t = w[L->fp_b2 + ch * 3 + i];
+        for (int k = 0; k < 3; k++) t += fp_softplus(w[L->fp_H2 + (ch * 3 + i) * 3 + k]) * v1[k];
+        v2[i] = t + tanh(w[L->fp_a2 + ch * 3 + i]) * tanh(t);
+    }
+    for (int i = 0; i < 3; i++) {
+        double t = w[L->fp_b3 + ch * 3 + i];
+        for (int k = 0; k < 3; k++) t += fp_softplus(w[L->fp_H3 + (ch * 3 + i) * 3 + k]) * v2[k];
+        v3[i] = t + tanh(w[L->fp_a3 + ch * 3 + i]) * tanh(t);
+    }
+    double t = w[L->fp_b4 + ch];
+    for (int k = 0; k < 3; k++) t += fp_softplus(w[L->fp_H4 + ch * 3 + k]) * v3[k];
+    return 1.0 / (1.0 + exp(-t));
+}
+
+#define OR_TZ 31   /* support half-width of every channel's z-hat table */
+
+/* Integer table of channel ch: slots -TZ..TZ then ESC (both tails), with
+ * the rule of the scale tables (freq = 1 + floor(pmf (2^16 - n)), the
+ * remainder to symbol 0).  Returns n. */
+static int prior_freq(const double *w, const or_layout *L, int ch, uint32_t *freq)
+{
+    int T = OR_TZ, n = 2 * T + 2;
+    long sum = 0;
+    for (int v = -T; v <= T; v++) {
+        double pmf = prior_cdf(w, L, ch, v + 0.5) - prior_cdf(w, L, ch, v - 0.5);
+        freq[v + T] = 1u + (uint32_t)floor(pmf * (double)(OR_M - (uint32_t)n));
+        sum += freq[v + T];
+    }
+    double pesc = prior_cdf(w, L, ch, -T - 0.5) + (1.0 - prior_cdf(w, L, ch, T + 0.5));
+    freq[2 * T + 1] = 1u + (uint32_t)floor(pesc * (double)(OR_M - (uint32_t)n));
+    sum += freq[2 * T + 1];
+    freq[T] = (uint32_t)((long)freq[T] + ((long)OR_M - sum));
+    return n;
+}
+
+static void tables_prior(or_tables *tb, const or_cfg *c, const double *w)
+{
+    or_layout L;
+    make_layout(c, &L);
+    tables_alloc(tb, c->Ch);
+    for (int ch = 0; ch < c->Ch; ch++) {
+        tb->n[ch] = prior_freq(w, &L, ch, tb->freq + (long)ch * 4096);
+        tb->T[ch] = OR_TZ;
+        tables_cum(tb, ch);
+    }
+}
+
+int or_prior_freq(const or_cfg *c, const double *w, int ch, uint32_t *freq)
+{
+    or_layout L;
+    if (!c->hp || ch < 0 || ch >= c->Ch) return 0;
+    make_layout(c, &L);
+    return prior_freq(w, &L, ch, freq);
+}
+
+/* -sum log2 P(z-hat) under the factorized prior (P floored at 1e-9). */
+double or_hyper_rate(const or_cfg *c, const double *w, const int16_t *zhat)
+{
+    or_layout L;
+    make_layout(c, &L);
+    double bits = 0.0;
+    for (long a = 0; a < (long)c->Hh * c->Wh * c->Ch; a++) {
+        int ch = (int)(a % c->Ch);
+        double p = prior_cdf(w, &L, ch, zhat[a] + 0.5) - prior_cdf(w, &L, ch, zhat[a] - 0.5);
+        bits -= log2(p < 1e-9 ? 1e-9 : p);
+    }
+    return bits;
 }
 
 static void tables_free(or_tables *tb) { free(tb->cum); free(tb->freq); free(tb->T); free(tb->n); }
@@ -1043,15 +1331,28 @@ static uint32_t get32(const uint8_t *b) { return (uint32_t)get16(b) | ((uint32_t
 /* Encode one frame.  y, idx, m: [HW][C] in raster layout; order: the
  * schedule's position order.  Returns the container size, or -1 if it does
  * not fit in cap bytes, or -2 on an unencodable symbol. */
+static long rans_encode_tb(const or_tables *tbp, int H, int W, int C, int schedule, const int *order,
+                           const int16_t *y, const uint8_t *idx, const int32_t *m, uint8_t *out, long cap);
+
 long or_rans_encode(int H, int W, int C, int schedule, const int *order, const int16_t *y,
                     const uint8_t *idx, const int32_t *m, uint8_t *out, long cap)
 {
     or_tables tb;
     tables_build(&tb);
+    long r = rans_encode_tb(&tb, H, W, C, schedule, order, y, idx, m, out, cap);
+    tables_free(&tb);
+    return r;
+}
+
+/* The encoder with a given table set (idx: table of each symbol). */
+static long rans_encode_tb(const or_tables *tbp, int H, int W, int C, int schedule, const int *order,
+                           const int16_t *y, const uint8_t *idx, const int32_t *m, uint8_t *out, long cap)
+{
+    const or_tables tb = *tbp;
     int HW = H * W;
     long hdr = 16 + 4L * (C + 1), pos = hdr;
     uint16_t *words = (uint16_t *)malloc(sizeof(uint16_t) * (3L * HW + 2));
-    if (hdr > cap) { free(words); tables_free(&tb); return -1; }
+    if (hdr > cap) { free(words); return -1; }
     put32(out, OR_MAGIC); put16(out + 4, 1); put16(out + 6, (uint16_t)schedule);
     put16(out + 8, (uint16_t)H); put16(out + 10, (uint16_t)W); put16(out + 12, (uint16_t)C); put16(out + 14, 0);
     for (int c = 0; c < C; c++) {
@@ -1068,9 +1369,9 @@ long or_rans_encode(int H, int W, int C, int schedule, const int *order, const i
                 slot = 2 * T + 1;
                 long e = (sv < 0 ? -sv : sv) - T - 1;
                 long v = 2 * e + (sv < 0 ? 1 : 0);
-                if (v < 0 || v >= (1L << 32)) { free(words); tables_free(&tb); return -2; }
+                if (v < 0 || v >= (1L << 32)) { free(words); return -2; }
                 uint32_t dig[2] = { (uint32_t)(v & 0xFFFF), (uint32_t)(v >> 16) };
-                if (dig[1] > 0xFFFF) { free(words); tables_free(&tb); return -2; }
+                if (dig[1] > 0xFFFF) { free(words); return -2; }
                 for (int q = 1; q >= 0; q--) {     /* d1 first: decoded last */
                     words[nw++] = (uint16_t)(x[lane] & 0xFFFF);
                     x[lane] >>= 16;
@@ -1082,7 +1383,7 @@ long or_rans_encode(int H, int W, int C, int schedule, const int *order, const i
             x[lane] = ((x[lane] / f) << 16) + (x[lane] % f) + cm;
         }
         long sz = 128 + 2 * nw + ((nw & 1) ? 2 : 0);
-        if (pos + sz > cap) { free(words); tables_free(&tb); return -1; }
+        if (pos + sz > cap) { free(words); return -1; }
         put32(out + 16 + 4L * c, (uint32_t)pos);
         for (int l = 0; l < 32; l++) put32(out + pos + 4L * l, x[l]);
         for (long q = 0; q < nw; q++) put16(out + pos + 128 + 2 * q, words[nw - 1 - q]);
@@ -1091,7 +1392,6 @@ long or_rans_encode(int H, int W, int C, int schedule, const int *order, const i
     }
     put32(out + 16 + 4L * C, (uint32_t)pos);
     free(words);
-    tables_free(&tb);
     return pos;
 }
 
@@ -1106,7 +1406,17 @@ typedef struct {
     or_tables tb;
 } or_dec;
 
+static int dec_open_hdr(or_dec *D, const uint8_t *buf, long len, int H, int W, int C, int schedule);
+
 static int dec_open(or_dec *D, const uint8_t *buf, long len, int H, int W, int C, int schedule)
+{
+    if (dec_open_hdr(D, buf, len, H, W, C, schedule)) return -1;
+    tables_build(&D->tb);
+    return 0;
+}
+
+/* Header and stream checks, lane states; no tables. */
+static int dec_open_hdr(or_dec *D, const uint8_t *buf, long len, int H, int W, int C, int schedule)
 {
     memset(D, 0, sizeof(*D));
     D->buf = buf; D->len = len; D->C = C;
@@ -1120,7 +1430,6 @@ static int dec_open(or_dec *D, const uint8_t *buf, long len, int H, int W, int C
         for (int l = 0; l < 32; l++) D->x[c][l] = get32(buf + a + 4L * l);
         D->ptr[c] = a + 128; D->end[c] = b;
     }
-    tables_build(&D->tb);
     return 0;
 }
 
@@ -1190,6 +1499,42 @@ static int dec_close(or_dec *D)
     return bad ? -1 : 0;
 }
 
+/* z-hat container (the coder's format: raster order over the hyperprior
+ * grid, one stream per channel, channel ch coded with its factorized-prior
+ * table, mean 0).  Returns the size, -1 if it does not fit, -2 on an
+ * unencodable symbol. */
+long or_hyper_encode(const or_cfg *c, const double *w, const int16_t *zhat, uint8_t *out, long cap)
+{
+    long HW = (long)c->Hh * c->Wh, n = HW * c->Ch;
+    int *order = (int *)malloc(sizeof(int) * HW);
+    uint8_t *idx = (uint8_t *)malloc((size_t)n);
+    int32_t *m = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    for (long p = 0; p < HW; p++) order[p] = (int)p;
+    for (long a = 0; a < n; a++) idx[a] = (uint8_t)(a % c->Ch);
+    or_tables tb;
+    tables_prior(&tb, c, w);
+    long r = rans_encode_tb(&tb, c->Hh, c->Wh, c->Ch, 1, order, zhat, idx, m, out, cap);
+    tables_free(&tb);
+    free(order); free(idx); free(m);
+    return r;
+}
+
+/* Decode a z-hat container: 0, or -1 if it fails validation. */
+int or_hyper_decode(const or_cfg *c, const double *w, const uint8_t *buf, long len, int16_t *zhat)
+{
+    long HW = (long)c->Hh * c->Wh, n = HW * c->Ch;
+    or_dec *D = (or_dec *)malloc(sizeof(or_dec));
+    if (c->Ch > 256 || dec_open_hdr(D, buf, len, c->Hh, c->Wh, c->Ch, 1)) { free(D); return -1; }
+    tables_prior(&D->tb, c, w);
+    uint8_t *idx = (uint8_t *)malloc((size_t)n);
+    int32_t *m = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    for (long a = 0; a < n; a++) idx[a] = (uint8_t)(a % c->Ch);
+    dec_symbols(D, (int)HW, idx, m, zhat);
+    int rc = dec_close(D);
+    free(D); free(idx); free(m);
+    return rc;
+}
+
 /* Coder-only decode with known per-symbol (idx, m) (they do not depend on
  * the decoded values in this entry point).  Returns 0 or -1 (corrupt). */
 int or_rans_decode(int H, int W, int C, int schedule, const int *order, const int *start, int T,
@@ -1241,6 +1586,7 @@ int or_run_lrp(const or_cfg *c, const double *w, int nf, int16_t *y, const int16
 {
     or_state st, *s = &st;
     if (c->L > OR_MAXL || c->Lc > OR_MAXL || c->Llrp > OR_MAXL || c->Lct > OR_MAXL) return -1;
+    if (c->hp && or_hyper_blocks(c) < 0) return -1;
     if (eps && c->Llrp <= 0) return -1;
     if (state_init(s, c, w)) { state_free(s); return -1; }
     int HW = s->HW, C = c->C;
@@ -1317,6 +1663,32 @@ int or_run_lrp(const or_cfg *c, const double *w, int nf, int16_t *y, const int16
     free(order); free(start); free(yvis);
     state_free(s);
     return rc;
+}
+
+/* The encoder's hyperprior analysis of nf frames (convolutional
+ * hyperprior models): per frame the Context Transformer (temporal model)
+ * and Spatial Module 1 over every position with the frame's latents, then
+ * the RB-down blocks and rounding.  zhat: [nf][Hh][Wh][Ch]; z (optional,
+ * may be NULL) receives the unrounded values.  Returns 0 or -1. */
+int or_hyper_analysis(const or_cfg *c, const double *w, int nf, const int16_t *y, int16_t *zhat, double *z)
+{
+    or_state st, *s = &st;
+    if (!c->hp || or_hyper_blocks(c) < 0 || c->L > OR_MAXL || c->Lc > OR_MAXL) return -1;
+    if (state_init(s, c, w)) { state_free(s); return -1; }
+    int HW = s->HW, C = c->C;
+    long nz = (long)c->Hh * c->Wh * c->Ch;
+    int *all = (int *)malloc(sizeof(int) * HW);
+    for (int p = 0; p < HW; p++) all[p] = p;
+    for (int f = 0; f < nf; f++) {
+        s->frame = f;
+        memset(s->x1, 0, sizeof(double) * HW * c->d);
+        if (c->temporal) run_context(s, f > 0 ? y + (long)(f - 1) * HW * C : NULL);
+        run_sm1(s, all, HW, y + (long)f * HW * C);
+        hyper_analysis(s, zhat + f * nz, z ? z + f * nz : NULL);
+    }
+    free(all);
+    state_free(s);
+    return 0;
 }
 
 int or_run(const or_cfg *c, const double *w, int nf, int16_t *y, const int16_t *z,

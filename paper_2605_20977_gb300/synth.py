@@ -38,6 +38,9 @@ class ModelConfig:
                prediction over a decoded frame
     Nc, dc     Channel Transformer: channel groups (0: none) and width
     Lct, Fc    its blocks and the SwiGLU hidden width of each group
+    hp         1: convolutional hyperprior (log2 r down / upsampling residual
+               blocks, z-hat coded under a factorized prior); 0: z-hat given,
+               embedded by a transposed convolution
     """
     H: int
     W: int
@@ -60,6 +63,7 @@ class ModelConfig:
     dc: int = 0
     Lct: int = 0
     Fc: int = 0
+    hp: int = 0
 
     def with_grid(self, H: int, W: int) -> "ModelConfig":
         d = asdict(self)
@@ -95,6 +99,8 @@ def config(name: str) -> ModelConfig:
     tiny_cyc_ct  tiny_ct with the cyclic s = 4 mask (16 steps per frame)
     tiny_p_ct tiny_p with the same Channel Transformer
     tiny_ct_lrp  tiny_ct with a 2-block LRP Transformer on its output
+    tiny_hp, tiny_p_hp, i1080_hp, p1080_hp  the model with the convolutional
+              hyperprior (z-hat produced by the analysis and coded)
     i1080_ct  i1080 with a Channel Transformer: 4 groups, width 1024, 2 blocks
     i1080_cyc_ct  i1080_ct with the cyclic s = 4 mask: s x N = 16 steps
     """
@@ -126,6 +132,10 @@ def config(name: str) -> ModelConfig:
         base = config({"tiny_ct": "tiny", "tiny_cyc_ct": "tiny_cyc", "tiny_p_ct": "tiny_p"}[name])
         d = asdict(base)
         d.update(Nc=4, dc=256, Lct=2, Fc=ffn_width(64))
+        return ModelConfig(**d)
+    if name in ("tiny_hp", "tiny_p_hp", "i1080_hp", "p1080_hp"):
+        d = asdict(config(name[:-3]))
+        d.update(hp=1)
         return ModelConfig(**d)
     if name == "tiny_ct_lrp":
         d = asdict(config("tiny_ct"))
@@ -193,9 +203,39 @@ def weight_spec(c: ModelConfig) -> list:
     s = [Tensor("gamma_in", (C,), "const", 0.25),
          Tensor("W_in", (C, d), "lin", fan_in=C, matrix=True),
          Tensor("b_in", (d,), "bias"),
-         Tensor("gamma_z", (Ch,), "const", 0.5),
-         Tensor("W_hp", (c.r * c.r, Ch, d), "lin", fan_in=Ch),
-         Tensor("b_hp", (d,), "bias")]
+         Tensor("gamma_z", (Ch,), "const", 0.5)]
+    if c.hp:
+        # convolutional hyperprior: analysis RB-down blocks (d -> Ch, then
+        # Ch -> Ch), synthesis RB-up blocks (Ch -> Ch, last Ch -> d), then the
+        # factorized prior's per-channel parameters
+        nb = int(round(math.log2(c.r)))
+        s.append(Tensor("hp.g_za", (d,), "gain"))
+        for b in range(nb):
+            ci, co = (d if b == 0 else Ch), Ch
+            s += [Tensor(f"hp.d{b}.Wa", (3, 3, ci, co), "lin", fan_in=9 * ci, matrix=True),
+                  Tensor(f"hp.d{b}.ba", (co,), "bias"),
+                  Tensor(f"hp.d{b}.Wb", (3, 3, co, co), "lin_res", value=0.5, fan_in=9 * co, matrix=True),
+                  Tensor(f"hp.d{b}.bb", (co,), "bias"),
+                  Tensor(f"hp.d{b}.Ws", (ci, co), "lin", fan_in=ci, matrix=True),
+                  Tensor(f"hp.d{b}.bs", (co,), "bias")]
+        for b in range(nb):
+            ci, co = Ch, (d if b == nb - 1 else Ch)
+            s += [Tensor(f"hp.u{b}.Wa", (3, 3, ci, 4 * co), "lin", fan_in=9 * ci, matrix=True),
+                  Tensor(f"hp.u{b}.ba", (4 * co,), "bias"),
+                  Tensor(f"hp.u{b}.Wb", (3, 3, co, co), "lin_res", value=0.5, fan_in=9 * co, matrix=True),
+                  Tensor(f"hp.u{b}.bb", (co,), "bias"),
+                  Tensor(f"hp.u{b}.Ws", (3, 3, ci, 4 * co), "lin", fan_in=9 * ci, matrix=True),
+                  Tensor(f"hp.u{b}.bs", (4 * co,), "bias")]
+        s += [Tensor("hp.fp_H1", (Ch, 3), "softplus_inv", 1.5), Tensor("hp.fp_b1", (Ch, 3), "bias"),
+              Tensor("hp.fp_a1", (Ch, 3), "bias"),
+              Tensor("hp.fp_H2", (Ch, 3, 3), "softplus_inv", 1.0 / 3.0), Tensor("hp.fp_b2", (Ch, 3), "bias"),
+              Tensor("hp.fp_a2", (Ch, 3), "bias"),
+              Tensor("hp.fp_H3", (Ch, 3, 3), "softplus_inv", 1.0 / 3.0), Tensor("hp.fp_b3", (Ch, 3), "bias"),
+              Tensor("hp.fp_a3", (Ch, 3), "bias"),
+              Tensor("hp.fp_H4", (Ch, 3), "softplus_inv", 0.2), Tensor("hp.fp_b4", (Ch,), "bias")]
+    else:
+        s += [Tensor("W_hp", (c.r * c.r, Ch, d), "lin", fan_in=Ch),
+              Tensor("b_hp", (d,), "bias")]
     if c.temporal:
         s += [Tensor("gamma_c", (C,), "const", 0.25),
               Tensor("W_c", (C, d), "lin", fan_in=C),
@@ -290,6 +330,9 @@ def weights(c: ModelConfig, seed: int = 42) -> np.ndarray:
             a = 0.5 * rng.standard_normal(n)
         elif t.init == "normal":
             a = rng.standard_normal(n)
+        elif t.init == "softplus_inv":
+            # raw parameter whose softplus is about `value` (positive entries)
+            a = math.log(math.expm1(t.value)) + 0.1 * rng.standard_normal(n)
         else:
             raise ValueError(t.init)
         parts.append(a.astype(np.float32))
@@ -314,7 +357,7 @@ def e4m3_tensor(t: Tensor) -> bool:
     the Channel Transformer and the LRP Transformer stay in the compute
     dtype."""
     if (not t.matrix or t.name in ("W_in", "W1m", "W2m", "W1s", "W2s") or t.name.startswith("lrp")
-            or t.name.startswith("ct")):
+            or t.name.startswith("ct") or t.name.startswith("hp.")):
         return False
     K = t.shape[0]
     return K % 128 == 0 and K <= (1024 if t.name.split(".")[-1] in ("Wo", "Wxo", "Wd") else 512)

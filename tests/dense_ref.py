@@ -82,10 +82,47 @@ def ffn(x, Wg, Wu, Wd):
     return (silu(x @ Wg) * (x @ Wu)) @ Wd
 
 
-def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray, with_eps: bool = False):
+def conv3(x, W, b, stride=1):
+    """3x3 correlation with zero padding 1: x [h][w][Ci], W [3][3][Ci][Co]
+    -> [ceil(h/stride)][ceil(w/stride)][Co], as nine shifted views."""
+    h, w_, _ = x.shape
+    ho, wo = -(-h // stride), -(-w_ // stride)
+    xp = np.pad(x, ((1, 1), (1, 1), (0, 0)))
+    out = np.broadcast_to(b, (ho, wo, W.shape[3])).copy()
+    for di in range(3):
+        for dj in range(3):
+            v = xp[di:di + stride * (ho - 1) + 1:stride, dj:dj + stride * (wo - 1) + 1:stride]
+            out += np.tensordot(v, W[di, dj], axes=([2], [0]))
+    return out
+
+
+def shuffle2(u):
+    """[h][w][4C] -> [2h][2w][C], channel (2a + b) C + c to sub-position (a, b)."""
+    h, w_, c4 = u.shape
+    return u.reshape(h, w_, 2, 2, c4 // 4).transpose(0, 2, 1, 3, 4).reshape(2 * h, 2 * w_, c4 // 4)
+
+
+def lrelu(x):
+    return np.where(x >= 0, x, 0.01 * x)
+
+
+def rb_down(P, pre, x):
+    a = lrelu(conv3(x, P[pre + "Wa"], P[pre + "ba"], 2))
+    return conv3(a, P[pre + "Wb"], P[pre + "bb"]) + (x[::2, ::2] @ P[pre + "Ws"] + P[pre + "bs"])
+
+
+def rb_up(P, pre, x):
+    a = lrelu(shuffle2(conv3(x, P[pre + "Wa"], P[pre + "ba"])))
+    return conv3(a, P[pre + "Wb"], P[pre + "bb"]) + shuffle2(conv3(x, P[pre + "Ws"], P[pre + "bs"]))
+
+
+def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray, with_eps: bool = False,
+        with_z: bool = False):
     """(mu, sigma) [nf, H, W, C] for a sequence, by the masked parallel pass;
     with with_eps also the LRP Transformer's residual eps of every frame
-    (full [HW x HW] attention under the unmasked window mask)."""
+    (full [HW x HW] attention under the unmasked window mask); with with_z
+    (a convolutional hyperprior model) also the unrounded analysis output z
+    of every frame, from that frame's Spatial Module 1 output."""
     P = split_weights(c, w)
     H, W, C, d, nh = c.H, c.W, c.C, c.d, c.nh
     HW = H * W
@@ -138,17 +175,29 @@ def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray, with_
             x = x + attention(qx, Kc, Vc, Mc, Bc, nh) @ P[pre + "Wxo"]
         return x + ffn(rms(x, P[pre + "g_ffn"]), P[pre + "Wg"], P[pre + "Wu"], P[pre + "Wd"])
 
-    mus, sigs, epss = [], [], []
+    mus, sigs, epss, zs = [], [], [], []
+    nb = int(round(np.log2(c.r)))
     LK = [[] for _ in range(c.Llrp)]       # LRP keys / values of every coded frame, per block
     LV = [[] for _ in range(c.Llrp)]
     for f in range(nf):
         ii, jj = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
-        zz = z[f][ii // c.r, jj // c.r].reshape(HW, c.Ch) * P["gamma_z"]
-        sub = ((ii % c.r) * c.r + (jj % c.r)).ravel()
-        eh = np.einsum("pc,pcd->pd", zz, P["W_hp"][sub]) + P["b_hp"]
+        if c.hp:
+            xh = z[f].astype(np.float64) * P["gamma_z"]
+            for b in range(nb):
+                xh = rb_up(P, f"hp.u{b}.", xh)
+            eh = xh[:H, :W].reshape(HW, d)
+        else:
+            zz = z[f][ii // c.r, jj // c.r].reshape(HW, c.Ch) * P["gamma_z"]
+            sub = ((ii % c.r) * c.r + (jj % c.r)).ravel()
+            eh = np.einsum("pc,pcd->pd", zz, P["W_hp"][sub]) + P["b_hp"]
         x1 = (y[f].reshape(HW, C) * P["gamma_in"]) @ P["W_in"] + P["b_in"]
         for l in range(c.L):
             x1 = block(f"sm1.{l}.", x1, S, f)
+        if with_z:
+            xa = rms(x1, P["hp.g_za"]).reshape(H, W, d)
+            for b in range(nb):
+                xa = rb_down(P, f"hp.d{b}.", xa)
+            zs.append(xa)
         m = rms(x1, P["acc.g_kv"])
         qa = rms(eh, P["acc.g_q"]) @ P["acc.Wq"]
         x2 = eh + attention(qa, m @ P["acc.Wk"], m @ P["acc.Wv"], A, bias_of(P["acc.bias"]), nh) @ P["acc.Wo"]
@@ -205,6 +254,9 @@ def run(c: synth.ModelConfig, w: np.ndarray, y: np.ndarray, z: np.ndarray, with_
                 u = u + attention(n @ P[pre + "Wq"], Kc, Vc, M, B, nh) @ P[pre + "Wo"]
                 u = u + ffn(rms(u, P[pre + "g_ffn"]), P[pre + "Wg"], P[pre + "Wu"], P[pre + "Wd"])
             epss.append((rms(u, P["lrp.g_out"]) @ P["lrp.W_eps"] + P["lrp.b_eps"]).reshape(H, W, C))
+    out = (np.stack(mus), np.stack(sigs))
     if with_eps:
-        return np.stack(mus), np.stack(sigs), np.stack(epss)
-    return np.stack(mus), np.stack(sigs)
+        out = out + (np.stack(epss),)
+    if with_z:
+        out = out + (np.stack(zs),)
+    return out

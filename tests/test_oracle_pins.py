@@ -264,7 +264,7 @@ def test_lrp_window_is_spatially_unmasked_and_local():
 
 def test_weight_layout_count_matches_generator():
     for nm in ("tiny", "tiny_p", "i1080", "p1080", "tiny_lrp", "i1080_lrp", "tiny_p_lrp", "p1080_lrp",
-               "tiny_ct", "tiny_p_ct", "tiny_ct_lrp", "i1080_ct", "i1080_cyc_ct"):
+               "tiny_ct", "tiny_p_ct", "tiny_ct_lrp", "i1080_ct", "i1080_cyc_ct", "tiny_hp", "i1080_hp", "p1080_hp"):
         c = synth.config(nm)
         assert O.weights_count(c) == synth.weights_count(c)
 
@@ -352,6 +352,107 @@ def test_channel_transformer_lrp_on_its_output():
     assert np.max(np.abs(e0 - e1)) < 1e-11
     _, _, e2 = O.run(c, w, fr.y, fr.z, driver=1, with_eps=True)
     assert np.array_equal(e0, e2)
+
+
+# ----------------------------------------------------------- hyperprior
+
+@pytest.mark.parametrize("name,grid", [("tiny_hp", None), ("tiny_p_hp", None), ("i1080_hp", (9, 14))])
+def test_hyperprior_matches_dense_formulation(name, grid):
+    """Convolutional hyperprior (Fig. 1 right): the oracle's analysis (z
+    from the Spatial Module 1 output through the RB-down blocks) and its
+    synthesis (the hyperprior tokens from z-hat through the RB-up blocks,
+    cropped) against a NumPy formulation by shifted views and a reshape
+    pixel shuffle; 9 x 14 is ragged (hyperprior grid 3 x 4, synthesis grid
+    12 x 16 cropped).  z-hat is z rounded half to even."""
+    c = synth.config(name)
+    if grid:
+        c = c.with_grid(*grid)
+    w = synth.weights(c)
+    fr = synth.frames(c, 2 if c.temporal else 1, seed=21)
+    zh, z = O.hyper_analysis(c, w, fr.y)
+    assert np.array_equal(zh, np.rint(z).astype(np.int16))
+    mu0, s0 = O.run(c, w, fr.y, zh, driver=0)
+    mu1, s1, z1 = dense_ref.run(c, w, fr.y, zh, with_z=True)
+    assert np.max(np.abs(z - z1)) < 1e-11
+    assert np.max(np.abs(mu0 - mu1)) < 1e-11 and np.max(np.abs(np.log(s0) - np.log(s1))) < 1e-11
+
+
+def test_hyperprior_model_schedules_and_round_trip():
+    """With the convolutional hyperprior the wavefront decode reproduces the
+    masked pass bit for bit and the container round trip is lossless."""
+    c = synth.config("tiny_hp")
+    w = synth.weights(c)
+    fr = synth.frames(c, 1, seed=22)
+    zh, _ = O.hyper_analysis(c, w, fr.y)
+    mu0, s0 = O.run(c, w, fr.y, zh, driver=0)
+    mu1, s1 = O.run(c, w, fr.y, zh, driver=1)
+    assert np.array_equal(mu0, mu1) and np.array_equal(s0, s1)
+    bs, mu, sg = O.encode_frames(c, w, fr.y, zh)
+    yd, mud, sgd = O.decode_frames(c, w, bs, zh)
+    assert np.array_equal(yd, fr.y) and np.array_equal(mu, mud)
+
+
+def _softplus(x):
+    return np.log1p(np.exp(x))
+
+
+def test_factorized_prior_closed_form_without_gating():
+    """With every gate a_k = 0 the cumulative is the logistic
+    sigmoid(alpha x + beta) of the composed affine maps (alpha the product of
+    the softplus matrices, beta the propagated biases): the oracle's rate of
+    a z-hat equals the closed form; and the tables sum to 2^16 with every
+    slot at least 1, close to the prior's probabilities."""
+    c = synth.config("tiny_hp")
+    w = synth.weights(c).astype(np.float64)
+    P = dense_ref.split_weights(c, w)
+    off, offs = 0, {}
+    for t in synth.weight_spec(c):
+        offs[t.name] = off
+        off += int(np.prod(t.shape))
+    for k in (1, 2, 3):
+        n = int(np.prod(P[f"hp.fp_a{k}"].shape))
+        w[offs[f"hp.fp_a{k}"]:offs[f"hp.fp_a{k}"] + n] = 0.0
+    P = dense_ref.split_weights(c, w)
+    rng = np.random.default_rng(5)
+    zh = rng.integers(-6, 7, size=(c.Hh, c.Wh, c.Ch)).astype(np.int16)
+    bits = 0.0
+    for ch in range(c.Ch):
+        H1 = _softplus(P["hp.fp_H1"][ch]).reshape(3, 1); b1 = P["hp.fp_b1"][ch]
+        H2 = _softplus(P["hp.fp_H2"][ch]); b2 = P["hp.fp_b2"][ch]
+        H3 = _softplus(P["hp.fp_H3"][ch]); b3 = P["hp.fp_b3"][ch]
+        H4 = _softplus(P["hp.fp_H4"][ch]).reshape(1, 3); b4 = P["hp.fp_b4"][ch]
+        alpha = float((H4 @ H3 @ H2 @ H1)[0, 0])
+        beta = float((H4 @ (H3 @ (H2 @ b1 + b2) + b3))[0] + b4)
+        sig = lambda x: 1.0 / (1.0 + np.exp(-(alpha * x + beta)))
+        v = zh[..., ch].astype(np.float64)
+        p = np.maximum(sig(v + 0.5) - sig(v - 0.5), 1e-9)
+        bits -= np.log2(p).sum()
+        f = O.prior_freq(c, w, ch)
+        assert f.sum() == 1 << 16 and f.min() >= 1 and len(f) == 64
+        T = 31
+        pm = np.array([sig(k + 0.5) - sig(k - 0.5) for k in range(-T, T + 1)])
+        assert np.max(np.abs(f[:-1] / 65536.0 - pm)) < 2e-3
+    assert abs(O.hyper_rate(c, w, zh) - bits) <= 1e-9 * bits
+
+
+def test_zhat_coder_round_trip_escapes_and_corruption():
+    """The z-hat container: lossless for values inside and far outside the
+    table support (escapes, int16 extremes), and a flipped byte or a
+    truncation is reported."""
+    c = synth.config("tiny_hp")
+    w = synth.weights(c)
+    rng = np.random.default_rng(6)
+    zh = rng.integers(-4, 5, size=(c.Hh, c.Wh, c.Ch)).astype(np.int16)
+    zh[0, 0, :4] = [-32768, 32767, 40, -33]
+    bs = O.hyper_encode(c, w, zh)
+    ok, zd = O.hyper_decode(c, w, bs)
+    assert ok and np.array_equal(zd, zh)
+    bad = bytearray(bs)
+    bad[len(bad) // 2] ^= 0x5A
+    ok2, zd2 = O.hyper_decode(c, w, bytes(bad))
+    ok3, _ = O.hyper_decode(c, w, bs[:-8])
+    assert not ok2 or not np.array_equal(zd2, zh)
+    assert not ok3
 
 
 # ----------------------------------------------------------- rate, tables

@@ -83,7 +83,14 @@ typedef enum {
  *          C and dc divisible by Nc, dg = dc / Nc a multiple of 64 and at
  *          most 512;
  *   dc     its width; Lct its blocks (1..16); Fc the SwiGLU hidden width of
- *          each group (a multiple of 64).  All four are 0 without it. */
+ *          each group (a multiple of 64).  All four are 0 without it.
+ *   hp     1 = convolutional hyperprior (Fig. 1 right): psw_hyper_encode
+ *          computes z-hat from the frame (log2 r downsampling residual
+ *          blocks on Spatial Module 1's output) and codes it under a
+ *          factorized prior, psw_hyper_decode decodes it, and the
+ *          hyperprior tokens come from log2 r upsampling residual blocks
+ *          (r a power of two, Ch <= 256); 0 = z-hat is an input embedded by a
+ *          transposed convolution. */
 typedef struct {
     int C, Ch, r;
     int d, nh, F, L, k;
@@ -91,6 +98,7 @@ typedef struct {
     int mask;
     int Llrp;
     int Nc, dc, Lct, Fc;
+    int hp;
 } psw_model_desc;
 
 /* One frame: latent grid H x W (hyperprior grid ceil(H/r) x ceil(W/r)) and
@@ -102,7 +110,19 @@ typedef struct {
 
 /* Number of float32 values in the flat weight vector of a model.
  * Packing order (every projection stored [in][out], used as x . W):
- *   gamma_in[C] W_in[C][d] b_in[d] gamma_z[Ch] W_hp[r*r][Ch][d] b_hp[d]
+ *   gamma_in[C] W_in[C][d] b_in[d] gamma_z[Ch]
+ *   if hp (nb = log2 r residual blocks per direction):
+ *          g_za[d]
+ *          nb x RB-down { Wa[3][3][Ci][Ch] ba[Ch] Wb[3][3][Ch][Ch] bb[Ch] Ws[Ci][Ch] bs[Ch] }
+ *             (Ci = d for the first block, else Ch)
+ *          nb x RB-up { Wa[3][3][Ch][4Co] ba[4Co] Wb[3][3][Co][Co] bb[Co]
+ *             Ws[3][3][Ch][4Co] bs[4Co] } (Co = d for the last block, else Ch;
+ *             the 4Co outputs of a sub-pixel convolution are the 2 x 2
+ *             sub-positions a, b at channel (2a + b) Co + c)
+ *          factorized prior per channel: H1[Ch][3] b1[Ch][3] a1[Ch][3]
+ *             H2[Ch][3][3] b2[Ch][3] a2[Ch][3] H3[Ch][3][3] b3[Ch][3] a3[Ch][3]
+ *             H4[Ch][3] b4[Ch]
+ *   else   W_hp[r*r][Ch][d] b_hp[d]
  *   if temporal: gamma_c[C] W_c[C][d] b_c[d] pad[d]
  *                Lc x { g_attn[d] Wq Wk Wv Wo [d][d] bias[nh][Tf][k][k]
  *                       g_ffn[d] Wg[d][F] Wu[d][F] Wd[F][d] }  g_ctx[d]
@@ -222,6 +242,43 @@ psw_status psw_decode_batch(psw_ctx *ctx, int n, psw_seq *const *seqs, const psw
                             const int16_t *const *zhat_dev, int16_t *const *yhat_out_dev,
                             float *const *mu_dev, float *const *sigma_dev,
                             int *status_out, void *stream);
+
+/* Convolutional hyperprior, encoder side (Fig. 1 right; hp = 1): for the
+ * next frame of seq (the one psw_encode_params codes next; the sequence
+ * does not advance), Spatial Module 1 over every position with the frame's
+ * latents (after the Context Transformer for the temporal model), then
+ * RMSNorm and nb downsampling residual blocks (a 3 x 3 convolution of
+ * stride 2 and LeakyReLU 0.01, a 3 x 3 convolution, plus a 1 x 1
+ * convolution of stride 2) give z; z-hat = round-half-even(z) (int16).
+ * z-hat is coded by interleaved rANS under the factorized prior: per
+ * channel the cumulative c(x) = sigmoid(f4(f3(f2(f1(x))))), f_k(v) =
+ * g_k(softplus(H_k) v + b_k), g_k(t) = t + tanh(a_k) tanh(t) (k < 4), f4
+ * affine, widths 1-3-3-3-1; the table of channel c holds slots -31..31 and
+ * an escape, freq = 1 + floor(P (2^16 - 64)) with the remainder on 0; the
+ * container has the latent containers' format (raster order over the
+ * ceil(H/r) x ceil(W/r) grid, one stream per hyperprior channel).
+ *   yhat_dev   [H][W][C] int16 latents of the frame
+ *   zhat_dev   [ceil(H/r)][ceil(W/r)][Ch] int16 output
+ *   z_dev      optional float32 output of the unrounded z (NULL to skip)
+ *   bitstream_dev  optional device buffer of cap bytes for the z-hat
+ *              container (NULL: analysis only, *len_out 0)
+ * Errors: PSW_ERR_INVALID (no convolutional hyperprior, shape),
+ * PSW_ERR_CAPACITY, PSW_ERR_CUDA.  Synchronises `stream`. */
+psw_status psw_hyper_encode(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd, const int16_t *yhat_dev,
+                            int16_t *zhat_dev, float *z_dev, uint8_t *bitstream_dev, size_t cap, size_t *len_out,
+                            void *stream);
+
+/* Decoder side: z-hat of a frame with grid fd from its container (len
+ * bytes, 4-byte aligned device memory) into zhat_dev; PSW_ERR_CORRUPT if the
+ * container fails validation (as for the latent containers).  z-hat then
+ * goes to psw_decode_frame / psw_decode_batch, whose hyperprior tokens come
+ * from the upsampling residual blocks.  Synchronises `stream`. */
+psw_status psw_hyper_decode(psw_ctx *ctx, const psw_frame_desc *fd, const uint8_t *bitstream_dev, size_t len,
+                            int16_t *zhat_dev, void *stream);
+
+/* Frequency table of hyperprior channel ch of the factorized prior (64
+ * slots: -31..31, escape; sum 2^16).  Host output. */
+psw_status psw_prior_table(const psw_ctx *ctx, int ch, uint32_t *freq_host, int cap, int *n_out);
 
 /* LRP Transformer (Sec. 3.1 latent residual prediction; Sec. 4.3): the
  * residual eps of the sequence's last coded frame, from the quantised

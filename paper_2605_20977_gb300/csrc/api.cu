@@ -31,8 +31,16 @@ struct BlockOff {
     long g_x, Wxq, Wxk, Wxv, Wxo, xbias;
     long g_ffn, Wg, Wu, Wd;
 };
+// A down- or upsampling residual block of the convolutional hyperprior.
+struct RbOff {
+    long Wa, ba, Wb, bb, Ws, bs;
+};
 struct Layout {
     long gamma_in, W_in, b_in, gamma_z, W_hp, b_hp;
+    long g_za = -1;                                   // convolutional hyperprior (-1: none)
+    std::vector<RbOff> rbd, rbu;
+    long fp_H1 = -1, fp_b1 = -1, fp_a1 = -1, fp_H2 = -1, fp_b2 = -1, fp_a2 = -1, fp_H3 = -1, fp_b3 = -1,
+         fp_a3 = -1, fp_H4 = -1, fp_b4 = -1;
     long gamma_c, W_c, b_c, pad, g_ctx;
     std::vector<BlockOff> ctx, sm1, sm2;
     long acc_g_q, acc_g_kv, acc_Wq, acc_Wk, acc_Wv, acc_Wo, acc_bias, acc_g_ffn, acc_Wg, acc_Wu, acc_Wd;
@@ -69,13 +77,48 @@ BlockOff layout_block(Cursor &cu, const psw_model_desc &m, bool cross, bool tf_b
     return b;
 }
 
+// Residual blocks per hyperprior transform: log2 r (0 if r is not a power
+// of two in [2, 16]).
+int hyper_blocks(const psw_model_desc &m)
+{
+    for (int b = 1; b <= 4; b++)
+        if (m.r == (1 << b)) return b;
+    return 0;
+}
+
 Layout make_layout(const psw_model_desc &m)
 {
     Layout y;
     Cursor cu;
     long dd = (long)m.d * m.d, kk = (long)m.k * m.k;
     y.gamma_in = cu.take(m.C); y.W_in = cu.take((long)m.C * m.d); y.b_in = cu.take(m.d);
-    y.gamma_z = cu.take(m.Ch); y.W_hp = cu.take((long)m.r * m.r * m.Ch * m.d); y.b_hp = cu.take(m.d);
+    y.gamma_z = cu.take(m.Ch);
+    if (m.hp) {
+        const int nb = hyper_blocks(m);
+        const long Ch = m.Ch;
+        y.W_hp = y.b_hp = -1;
+        y.g_za = cu.take(m.d);
+        for (int b = 0; b < nb; b++) {           // analysis: d -> Ch, then Ch -> Ch
+            long Ci = b == 0 ? m.d : Ch, Co = Ch;
+            RbOff r;
+            r.Wa = cu.take(9 * Ci * Co); r.ba = cu.take(Co); r.Wb = cu.take(9 * Co * Co); r.bb = cu.take(Co);
+            r.Ws = cu.take(Ci * Co); r.bs = cu.take(Co);
+            y.rbd.push_back(r);
+        }
+        for (int b = 0; b < nb; b++) {           // synthesis: Ch -> Ch, last Ch -> d
+            long Ci = Ch, Co = b == nb - 1 ? m.d : Ch;
+            RbOff r;
+            r.Wa = cu.take(9 * Ci * 4 * Co); r.ba = cu.take(4 * Co); r.Wb = cu.take(9 * Co * Co); r.bb = cu.take(Co);
+            r.Ws = cu.take(9 * Ci * 4 * Co); r.bs = cu.take(4 * Co);
+            y.rbu.push_back(r);
+        }
+        y.fp_H1 = cu.take(Ch * 3); y.fp_b1 = cu.take(Ch * 3); y.fp_a1 = cu.take(Ch * 3);
+        y.fp_H2 = cu.take(Ch * 9); y.fp_b2 = cu.take(Ch * 3); y.fp_a2 = cu.take(Ch * 3);
+        y.fp_H3 = cu.take(Ch * 9); y.fp_b3 = cu.take(Ch * 3); y.fp_a3 = cu.take(Ch * 3);
+        y.fp_H4 = cu.take(Ch * 3); y.fp_b4 = cu.take(Ch);
+    } else {
+        y.W_hp = cu.take((long)m.r * m.r * m.Ch * m.d); y.b_hp = cu.take(m.d);
+    }
     y.gamma_c = y.W_c = y.b_c = y.pad = y.g_ctx = -1;
     if (m.temporal) {
         y.gamma_c = cu.take(m.C); y.W_c = cu.take((long)m.C * m.d); y.b_c = cu.take(m.d); y.pad = cu.take(m.d);
@@ -133,6 +176,11 @@ bool desc_valid(const psw_model_desc *m, std::string &why)
     if (m->k < 1 || m->k % 2 == 0 || m->k * m->k > MAX_KK) { why = "k must be odd with k*k <= 81"; return false; }
     if (m->mask != 0 && m->mask != 1) { why = "mask must be 0 or 1"; return false; }
     if (m->Llrp < 0 || m->Llrp > 64) { why = "Llrp must be in [0, 64]"; return false; }
+    if (m->hp != 0 && m->hp != 1) { why = "hp must be 0 or 1"; return false; }
+    if (m->hp && (!hyper_blocks(*m) || m->Ch > 256 || m->Ch % 4 || m->d % 4)) {
+        why = "convolutional hyperprior: r a power of two in [2, 16], Ch <= 256 and Ch, d multiples of 4";
+        return false;
+    }
     if (m->Nc == 0) {
         if (m->dc || m->Lct || m->Fc) { why = "dc, Lct and Fc must be 0 without channel groups"; return false; }
     } else {
@@ -211,6 +259,25 @@ struct psw_ctx {
     // heads [2 dg][dg], interleaved [2 Cg][2 dg] and their first-layer bias
     std::vector<void *> ct_win, ct_mix, ct_wg, ct_wu, ct_wd, ct_wh1, ct_wh2;
     std::vector<float *> ct_bh1;
+    // convolutional hyperprior: convolution operands [out][K] (K = taps x
+    // input channels, tap-major) per block; an RB-up block's first
+    // convolution and skip stacked [8 Co][9 Ch]; merged biases (RB-down:
+    // bs + bb [Co]; RB-up: ba then bs + bb per sub-position [8 Co])
+    std::vector<void *> hd_wa, hd_wb, hd_ws, hu_w, hu_wb;
+    std::vector<float *> hd_bias, hu_bias;
+    float *hg[3] = {nullptr, nullptr, nullptr};   // FP32 grids
+    void *hcol = nullptr;                         // im2col operand rows (compute type)
+    size_t hg_elems = 0, hcol_elems = 0, hz_cap = 0, h_bytes = 0;
+    // z-hat coder: factorized-prior tables (host copy and device) and scratch
+    std::vector<uint32_t> ptab;
+    uint32_t *d_pcdf = nullptr;
+    int *d_pmeta = nullptr;
+    uint8_t *hz_idx = nullptr;
+    int32_t *hz_m = nullptr;
+    int *hz_order = nullptr, *hz_status = nullptr;
+    uint32_t *hz_rstate = nullptr, *hz_rptr = nullptr, *hz_rend = nullptr, *hz_nw = nullptr;
+    uint16_t *hz_scratch = nullptr;
+    uint64_t *hz_total = nullptr;
     void *Win = nullptr;               // latent embedding [d][C]
     void *Wh1 = nullptr;               // heads, first layers [W1m; W1s]: [2d][d]
     void *Wh2 = nullptr;               // heads, second layers interleaved: row 2c = mu_c, 2c+1 = sigma_c: [2C][2d]
@@ -473,6 +540,24 @@ bool prepare_projections(psw_ctx *c, bool dry)
             ct_bh1.push_back((float *)carve(2 * dg, es == 2 ? 2 : 1));   // 2 dg floats
         }
     }
+    std::vector<void *> hd_wa, hd_wb, hd_ws, hu_w, hu_wb;
+    std::vector<float *> hd_bias, hu_bias;
+    if (m.hp) {
+        const int nb = hyper_blocks(m), Ch = m.Ch;
+        for (int b = 0; b < nb; b++) {
+            const int Ci = b == 0 ? d : Ch, Co = Ch;
+            hd_wa.push_back(operand(Co, 9 * Ci, A_DIRECT, {lay.rbd[b].Wa}));
+            hd_wb.push_back(operand(Co, 9 * Co, A_DIRECT, {lay.rbd[b].Wb}));
+            hd_ws.push_back(operand(Co, Ci, A_DIRECT, {lay.rbd[b].Ws}));
+            hd_bias.push_back((float *)carve_b((size_t)Co * 4));
+        }
+        for (int b = 0; b < nb; b++) {
+            const int Ci = Ch, Co = b == nb - 1 ? d : Ch;
+            hu_w.push_back(operand(8 * Co, 9 * Ci, A_DIRECT, {lay.rbu[b].Wa, lay.rbu[b].Ws}));
+            hu_wb.push_back(operand(Co, 9 * Co, A_DIRECT, {lay.rbu[b].Wb}));
+            hu_bias.push_back((float *)carve_b((size_t)8 * Co * 4));
+        }
+    }
     cudaFree(stage);
     if (!ok) return false;
     void *win = carve(d, m.C); tr(lay.W_in, m.C, d, win, 0);
@@ -547,10 +632,99 @@ bool prepare_projections(psw_ctx *c, bool dry)
     }
     c->ctxb = ctxb; c->sm1 = sm1; c->sm2 = sm2; c->acc = ab;
     c->lrpb = lrpb; c->Wrep = wrep; c->Wy = wy; c->Weps = weps;
+    if (m.hp) {
+        // merged biases of the residual sums (host FP32 additions)
+        const int nb = hyper_blocks(m), Ch = m.Ch;
+        std::vector<float> a, b2, b3, buf;
+        for (int b = 0; b < nb; b++) {
+            a.resize(Ch); b2.resize(Ch);
+            cudaMemcpy(a.data(), c->w + lay.rbd[b].bs, Ch * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(b2.data(), c->w + lay.rbd[b].bb, Ch * 4, cudaMemcpyDeviceToHost);
+            for (int o = 0; o < Ch; o++) a[o] += b2[o];
+            cudaMemcpy(hd_bias[b], a.data(), Ch * 4, cudaMemcpyHostToDevice);
+        }
+        for (int b = 0; b < nb; b++) {
+            const int Co = b == nb - 1 ? d : Ch;
+            a.resize(4 * Co); b2.resize(4 * Co); b3.resize(Co); buf.assign(8 * Co, 0.0f);
+            cudaMemcpy(a.data(), c->w + lay.rbu[b].ba, 4 * Co * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(b2.data(), c->w + lay.rbu[b].bs, 4 * Co * 4, cudaMemcpyDeviceToHost);
+            cudaMemcpy(b3.data(), c->w + lay.rbu[b].bb, Co * 4, cudaMemcpyDeviceToHost);
+            for (int e = 0; e < 4 * Co; e++) buf[e] = a[e];
+            for (int sub = 0; sub < 4; sub++)
+                for (int o = 0; o < Co; o++) buf[4 * Co + sub * Co + o] = b2[sub * Co + o] + b3[o];
+            cudaMemcpy(hu_bias[b], buf.data(), 8 * Co * 4, cudaMemcpyHostToDevice);
+        }
+    }
     c->ct_win = ct_win; c->ct_mix = ct_mix; c->ct_wg = ct_wg; c->ct_wu = ct_wu; c->ct_wd = ct_wd;
     c->ct_wh1 = ct_wh1; c->ct_wh2 = ct_wh2; c->ct_bh1 = ct_bh1;
+    c->hd_wa = hd_wa; c->hd_wb = hd_wb; c->hd_ws = hd_ws; c->hu_w = hu_w; c->hu_wb = hu_wb;
+    c->hd_bias = hd_bias; c->hu_bias = hu_bias;
     c->Win = win; c->Wh1 = wh1; c->Wh2 = wh2; c->bh1 = bh1;
     return true;
+}
+
+// ---------------------------------------------------------------- factorized prior
+
+// The factorized prior of z-hat (Fig. 1 right; the univariate density of
+// Balle et al. 2018): per channel the cumulative
+// c(x) = sigmoid(f4(f3(f2(f1(x))))) through widths 1 -> 3 -> 3 -> 3 -> 1,
+// f_k(v) = g_k(softplus(H_k) v + b_k), g_k(t) = t + tanh(a_k) tanh(t) for
+// k < 4, f_4 affine; double precision, sums over ascending inputs after the
+// bias.  Host code: the tables are built once per context.
+double prior_softplus(double x) { return x > 30.0 ? x : log1p(exp(x)); }
+
+double prior_cdf(const Layout &L, const float *w, int ch, double x)
+{
+    auto W_ = [&](long off) { return (double)w[off]; };
+    double v1[3], v2[3], v3[3];
+    for (int i = 0; i < 3; i++) {
+        double t = W_(L.fp_b1 + ch * 3 + i) + prior_softplus(W_(L.fp_H1 + ch * 3 + i)) * x;
+        v1[i] = t + tanh(W_(L.fp_a1 + ch * 3 + i)) * tanh(t);
+    }
+    for (int i = 0; i < 3; i++) {
+        double t = W_(L.fp_b2 + ch * 3 + i);
+        for (int k = 0; k < 3; k++) t += prior_softplus(W_(L.fp_H2 + (ch * 3 + i) * 3 + k)) * v1[k];
+        v2[i] = t + tanh(W_(L.fp_a2 + ch * 3 + i)) * tanh(t);
+    }
+    for (int i = 0; i < 3; i++) {
+        double t = W_(L.fp_b3 + ch * 3 + i);
+        for (int k = 0; k < 3; k++) t += prior_softplus(W_(L.fp_H3 + (ch * 3 + i) * 3 + k)) * v2[k];
+        v3[i] = t + tanh(W_(L.fp_a3 + ch * 3 + i)) * tanh(t);
+    }
+    double t = W_(L.fp_b4 + ch);
+    for (int k = 0; k < 3; k++) t += prior_softplus(W_(L.fp_H4 + ch * 3 + k)) * v3[k];
+    return 1.0 / (1.0 + exp(-t));
+}
+
+constexpr int PRIOR_T = 31;                 // support half-width of every channel's table
+constexpr int PRIOR_N = 2 * PRIOR_T + 2;    // slots: -T..T, escape
+
+// Packed tables (cum | freq << 16, PRIOR_N slots per channel) with the
+// scale tables' rule: freq = 1 + floor(pmf (2^16 - n)), escape = both tails,
+// the remainder to symbol 0.
+void build_prior_tables(const psw_model_desc &m, const Layout &L, const float *w, std::vector<uint32_t> &packed)
+{
+    packed.assign((size_t)m.Ch * PRIOR_N, 0);
+    const int T = PRIOR_T, n = PRIOR_N;
+    const double room = (double)((1u << CDF_PREC) - (uint32_t)n);
+    uint32_t fr[PRIOR_N];
+    for (int ch = 0; ch < m.Ch; ch++) {
+        long sum = 0;
+        for (int v = -T; v <= T; v++) {
+            double pmf = prior_cdf(L, w, ch, v + 0.5) - prior_cdf(L, w, ch, v - 0.5);
+            fr[v + T] = 1u + (uint32_t)floor(pmf * room);
+            sum += fr[v + T];
+        }
+        double pesc = prior_cdf(L, w, ch, -T - 0.5) + (1.0 - prior_cdf(L, w, ch, T + 0.5));
+        fr[2 * T + 1] = 1u + (uint32_t)floor(pesc * room);
+        sum += fr[2 * T + 1];
+        fr[T] = (uint32_t)((long)fr[T] + ((long)(1u << CDF_PREC) - sum));
+        uint32_t cum = 0;
+        for (int sl = 0; sl < n; sl++) {
+            packed[(size_t)ch * n + sl] = cum | (fr[sl] << 16);
+            cum += fr[sl];
+        }
+    }
 }
 
 // ---------------------------------------------------------------- schedules
@@ -669,6 +843,81 @@ psw_status ensure_workspace(psw_ctx *c, size_t rows)
     c->ws_rows = rows;
     c->ws_bytes = 3 * bd + bf + 2 * bx + bg + bc + bn;
     c->bytes += c->ws_bytes;
+    c->ws_gen++;
+    for (auto &kv : c->graphs) graph_free(kv.second);
+    c->graphs.clear();
+    return PSW_OK;
+}
+
+// Hyperprior workspace for frames up to H x W: the largest FP32 grid and
+// im2col operand over the analysis and synthesis blocks, and the z-hat
+// coder's scratch for the ceil(H/r) x ceil(W/r) grid.
+void hyper_sizes(const psw_model_desc &m, int H, int W_, size_t &grid, size_t &col, size_t &hz)
+{
+    const int nb = hyper_blocks(m), r = m.r, Ch = m.Ch, d = m.d;
+    grid = (size_t)H * W_ * d;
+    col = 0;
+    int h = H, w = W_, Ci = d;
+    for (int b = 0; b < nb; b++) {
+        int ho = (h + 1) / 2, wo = (w + 1) / 2;
+        size_t P = (size_t)ho * wo;
+        grid = std::max(grid, P * Ch);
+        col = std::max(col, std::max(P * 9 * Ci, P * 9 * Ch));
+        h = ho; w = wo; Ci = Ch;
+    }
+    h = (H + r - 1) / r; w = (W_ + r - 1) / r;
+    hz = (size_t)h * w;
+    grid = std::max(grid, hz * Ch);
+    for (int b = 0; b < nb; b++) {
+        const int Co = b == nb - 1 ? d : Ch;
+        size_t P = (size_t)h * w;
+        grid = std::max(grid, std::max(P * 8 * Co, 4 * P * Co));
+        col = std::max(col, std::max(P * 9 * Ch, 4 * P * 9 * Co));
+        h *= 2; w *= 2;
+    }
+}
+
+psw_status ensure_hyper(psw_ctx *c, int H, int W_)
+{
+    if (!c->md.hp) return PSW_OK;
+    size_t grid, col, hz;
+    hyper_sizes(c->md, H, W_, grid, col, hz);
+    if (grid <= c->hg_elems && col <= c->hcol_elems && hz <= c->hz_cap) return PSW_OK;
+    grid = std::max(grid, c->hg_elems); col = std::max(col, c->hcol_elems); hz = std::max(hz, c->hz_cap);
+    CK_CUDA(c, cudaDeviceSynchronize());
+    for (float *&g : c->hg) { cudaFree(g); g = nullptr; }
+    cudaFree(c->hcol); cudaFree(c->hz_idx); cudaFree(c->hz_m); cudaFree(c->hz_order); cudaFree(c->hz_status);
+    cudaFree(c->hz_rstate); cudaFree(c->hz_rptr); cudaFree(c->hz_rend); cudaFree(c->hz_nw); cudaFree(c->hz_scratch);
+    cudaFree(c->hz_total);
+    c->hcol = nullptr; c->hz_idx = nullptr; c->hz_m = nullptr; c->hz_order = c->hz_status = nullptr;
+    c->hz_rstate = c->hz_rptr = c->hz_rend = c->hz_nw = nullptr; c->hz_scratch = nullptr; c->hz_total = nullptr;
+    c->bytes -= c->h_bytes;
+    c->h_bytes = 0; c->hg_elems = c->hcol_elems = c->hz_cap = 0;
+    const size_t Ch = c->md.Ch, es = esize(c->prec);
+    bool ok = true;
+    size_t bytes = 0;
+    auto al = [&](void **p, size_t b) {
+        if (ok && cudaMalloc(p, b ? b : 16) != cudaSuccess) ok = false;
+        bytes += b;
+    };
+    for (float *&g : c->hg) al((void **)&g, grid * 4);
+    al(&c->hcol, col * es);
+    al((void **)&c->hz_idx, hz * Ch);
+    al((void **)&c->hz_m, hz * Ch * 4);
+    al((void **)&c->hz_order, hz * 4);
+    al((void **)&c->hz_status, 4);
+    al((void **)&c->hz_rstate, Ch * 32 * 4);
+    al((void **)&c->hz_rptr, Ch * 4);
+    al((void **)&c->hz_rend, Ch * 4);
+    al((void **)&c->hz_nw, (2 * Ch + 1) * 4);
+    al((void **)&c->hz_scratch, Ch * (3 * hz + 64) * 2);
+    al((void **)&c->hz_total, 8);
+    if (!ok) return fail(c, PSW_ERR_OOM, "hyperprior workspace for %dx%d", H, W_);
+    c->hg_elems = grid; c->hcol_elems = col; c->hz_cap = hz; c->h_bytes = bytes;
+    c->bytes += bytes;
+    launch_hyper_coder_tables((int)hz, (int)Ch, c->hz_idx, c->hz_m, c->hz_order, 0);
+    CK_CUDA(c, cudaDeviceSynchronize());
+    // recorded graphs name the old buffers
     c->ws_gen++;
     for (auto &kv : c->graphs) graph_free(kv.second);
     c->graphs.clear();
@@ -857,6 +1106,69 @@ void spatial_block(const Pass &P, const BlockOff &bo, const BlockDev &bd, int bi
     ffn(P, bd, bo.g_ffn, X, tok, n);
 }
 
+// Hyperprior synthesis (Fig. 1 right, RB-up blocks): gamma_z * z-hat of
+// the slot of tok[0] through the sub-pixel residual blocks; the last grid
+// cropped into the slot's hyperprior tokens.  Per block, one projection
+// computes the first convolution and the skip convolution of the same
+// taps (stacked, biases ba and bs + bb); the skip half is shuffled into the
+// output grid, the first half is the LeakyReLU'd, shuffled input of the
+// second convolution, whose result is added.
+void hyper_synthesis(const Pass &P, const int *tok, int H, int W_)
+{
+    psw_ctx *c = P.c;
+    const psw_model_desc &m = c->md;
+    const int nb = hyper_blocks(m), Ch = m.Ch, d = m.d;
+    int h = (H + m.r - 1) / m.r, w = (W_ + m.r - 1) / m.r;
+    float *x = c->hg[0], *U = c->hg[1], *o = c->hg[2];
+    P.xn_rows = nullptr;
+    LAUNCH(P, K_EMBED, 0.0, (double)h * w * Ch * 6.0,
+           launch_zhat_grid(P.S, tok, h * w, W(c, c->lay.gamma_z), Ch, x, P.s));
+    for (int b = 0; b < nb; b++) {
+        const int Co = b == nb - 1 ? d : Ch, Pn = h * w;
+        LAUNCH(P, K_EMBED, 0.0, (double)Pn * 9 * Ch * 6.0,
+               launch_im2col(c->prec, x, h, w, Ch, 0, 0, 0, 3, 1, c->hcol, P.s));
+        gemm_call(P, c->hcol, 9 * Ch, c->hu_w[b], nullptr, Pn, 8 * Co, 9 * Ch, epi_set_bias(nullptr, U, c->hu_bias[b]));
+        LAUNCH(P, K_EMBED, 0.0, (double)Pn * 4 * Co * 8.0, launch_shuffle(U + 4 * Co, h, w, Co, 8 * Co, o, P.s));
+        LAUNCH(P, K_EMBED, 0.0, (double)Pn * 4 * 9 * Co * 6.0,
+               launch_im2col(c->prec, U, 2 * h, 2 * w, Co, 1, 8 * Co, 1, 3, 1, c->hcol, P.s));
+        gemm_call(P, c->hcol, 9 * Co, c->hu_wb[b], nullptr, 4 * Pn, Co, 9 * Co, epi_resid(nullptr, o));
+        h *= 2; w *= 2;
+        float *t = x; x = o; o = U; U = t;               // the output is the next block's input
+    }
+    LAUNCH(P, K_EMBED, 0.0, (double)H * W_ * d * 8.0, launch_crop_eh(P.S, tok, x, w, H, W_, d, P.s));
+}
+
+// Hyperprior analysis (RB-down blocks) of the H x W frame whose Spatial
+// Module 1 rows are in Xa (raster order): RMSNorm(x1) * g_za, per block the
+// strided 3 x 3 convolution and LeakyReLU, the 3 x 3 convolution added to
+// the strided 1 x 1 skip (biases bs + bb merged); z rounded into zhat.
+void hyper_analysis(const Pass &P, int H, int W_, int16_t *zhat, float *z_out)
+{
+    psw_ctx *c = P.c;
+    const psw_model_desc &m = c->md;
+    const int nb = hyper_blocks(m), Ch = m.Ch, d = m.d;
+    float *x = c->hg[0], *A = c->hg[1], *o = c->hg[2];
+    LAUNCH(P, K_NORM, 0.0, (double)H * W_ * d * 8.0, launch_rmsnorm(P_F32, c->Xa, H * W_, W(c, c->lay.g_za), d, x, P.s));
+    int h = H, w = W_, Ci = d;
+    for (int b = 0; b < nb; b++) {
+        const int ho = (h + 1) / 2, wo = (w + 1) / 2, Pn = ho * wo;
+        LAUNCH(P, K_EMBED, 0.0, (double)Pn * 9 * Ci * 6.0,
+               launch_im2col(c->prec, x, h, w, Ci, 0, 0, 0, 3, 2, c->hcol, P.s));
+        gemm_call(P, c->hcol, 9 * Ci, c->hd_wa[b], nullptr, Pn, Ch, 9 * Ci,
+                  epi_set_bias(nullptr, A, W(c, c->lay.rbd[b].ba)));
+        LAUNCH(P, K_EMBED, 0.0, (double)Pn * Ci * 6.0, launch_im2col(c->prec, x, h, w, Ci, 0, 0, 0, 1, 2, c->hcol, P.s));
+        gemm_call(P, c->hcol, Ci, c->hd_ws[b], nullptr, Pn, Ch, Ci, epi_set_bias(nullptr, o, c->hd_bias[b]));
+        LAUNCH(P, K_EMBED, 0.0, (double)Pn * 9 * Ch * 6.0,
+               launch_im2col(c->prec, A, ho, wo, Ch, 0, 0, 1, 3, 1, c->hcol, P.s));
+        gemm_call(P, c->hcol, 9 * Ch, c->hd_wb[b], nullptr, Pn, Ch, 9 * Ch, epi_resid(nullptr, o));
+        h = ho; w = wo; Ci = Ch;
+        float *t = x; x = o; o = A; A = t;
+    }
+    LAUNCH(P, K_OTHER, 0.0, (double)h * w * Ch * 6.0, launch_round_z(x, (long)h * w * Ch, zhat, z_out, P.s));
+}
+
+void frame_context(const Pass &P, const int *tok, int n);
+
 // Per-frame preparation for the tokens tok[0..n) (all positions of one
 // slot, in raster order; eh: that slot's hyperprior rows): hyperprior
 // tokens and accumulator queries (they depend only on the hyperlatents,
@@ -869,11 +1181,25 @@ void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *e
     const psw_model_desc &m = c->md;
     int d = m.d, kk = m.k * m.k;
     P.xn_rows = nullptr;                               // rows written outside gemm_any follow
-    LAUNCH(P, K_EMBED, 2.0 * n * m.Ch * d, n * (m.Ch * 2.0 + d * 4.0),
-           launch_embed_hyper(P.S, tok, n, H, W_, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp),
-                              W(c, c->lay.b_hp), d, P.s));
+    if (m.hp) {
+        hyper_synthesis(P, tok, H, W_);
+    } else {
+        LAUNCH(P, K_EMBED, 2.0 * n * m.Ch * d, n * (m.Ch * 2.0 + d * 4.0),
+               launch_embed_hyper(P.S, tok, n, H, W_, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp),
+                                  W(c, c->lay.b_hp), d, P.s));
+    }
     gemm_norm(P, eh, c->lay.acc_g_q, c->acc.Wqkv, nullptr, n, d, d, epi_store(tok, nullptr, d, CS_QA, 0, d));
     if (!m.temporal) return;
+    frame_context(P, tok, n);
+}
+
+// The temporal model's per-frame context: the Context Transformer pass and
+// every spatial block's cross-attention keys and values (Sec. 3.1).
+void frame_context(const Pass &P, const int *tok, int n)
+{
+    psw_ctx *c = P.c;
+    const psw_model_desc &m = c->md;
+    int d = m.d, kk = m.k * m.k;
     // Context Transformer (Sec. 3.1): temporally shifted latents (learned
     // padding vector for frame 0), time-causal window attention over the
     // frames of the ring at each layer, final RMSNorm.
@@ -1511,6 +1837,18 @@ psw_status psw_create(const psw_model_desc *desc, const float *weights_host, siz
     if (e == cudaSuccess) e = cudaMemcpy(c->d_meta, meta, sizeof(meta), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_scale, c->tabs.scale, 64 * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !prepare_projections(c, /*dry=*/false)) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess && desc->hp) {
+        build_prior_tables(*desc, lay, weights_host, c->ptab);
+        std::vector<int> pm(3 * (size_t)desc->Ch);
+        for (int ch = 0; ch < desc->Ch; ch++) {
+            pm[ch] = PRIOR_T; pm[desc->Ch + ch] = PRIOR_N; pm[2 * desc->Ch + ch] = ch * PRIOR_N;
+        }
+        e = cudaMalloc(&c->d_pcdf, c->ptab.size() * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_pmeta, pm.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_pcdf, c->ptab.data(), c->ptab.size() * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_pmeta, pm.data(), pm.size() * sizeof(int), cudaMemcpyHostToDevice);
+        c->bytes += c->ptab.size() * 4 + pm.size() * sizeof(int);
+    }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         psw_destroy(c);
@@ -1532,6 +1870,10 @@ void psw_destroy(psw_ctx *c)
     cudaFree(c->rate_buf); cudaFree(c->d_slots); cudaFree(c->d_status); cudaFree(c->d_tok); cudaFree(c->d_kn);
     cudaFree(c->Xn); cudaFree(c->Q); cudaFree(c->O); cudaFree(c->Hid);
     cudaFree(c->Xa); cudaFree(c->Xb); cudaFree(c->Xg); cudaFree(c->Xc); cudaFree(c->NM);
+    for (float *g : c->hg) cudaFree(g);
+    cudaFree(c->hcol); cudaFree(c->hz_idx); cudaFree(c->hz_m); cudaFree(c->hz_order); cudaFree(c->hz_status);
+    cudaFree(c->hz_rstate); cudaFree(c->hz_rptr); cudaFree(c->hz_rend); cudaFree(c->hz_nw); cudaFree(c->hz_scratch);
+    cudaFree(c->hz_total); cudaFree(c->d_pcdf); cudaFree(c->d_pmeta);
     if (c->h_rate) cudaFreeHost(c->h_rate);
     if (c->h_slots) cudaFreeHost(c->h_slots);
     if (c->h_status) cudaFreeHost(c->h_status);
@@ -1560,6 +1902,7 @@ psw_status psw_seq_create(psw_ctx *c, int max_H, int max_W, psw_seq **out)
         return fail(c, PSW_ERR_OOM, "sequence needs %zu bytes; %zu of %zu in use", need + ws_more, used, c->budget);
     psw_status st = ensure_workspace(c, HW);
     if (st) return st;
+    if ((st = ensure_hyper(c, max_H, max_W))) return st;
     psw_seq *q = new psw_seq();
     q->ctx = c; q->maxH = max_H; q->maxW = max_W; q->maxHW = (int)HW; q->bytes = need;
     const psw_model_desc &m = c->md;
@@ -1751,6 +2094,117 @@ psw_status psw_lrp_residual(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, fl
     if (failed) return fail(c, PSW_ERR_CUDA, "a GEMM launch could not be prepared");
     q->lrp_done = q->frame;
     return status_code(c, sts[0]);
+}
+
+psw_status psw_hyper_encode(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, const int16_t *yhat_dev,
+                            int16_t *zhat_dev, float *z_dev, uint8_t *bitstream_dev, size_t cap, size_t *len_out,
+                            void *stream)
+{
+    psw_status st = check_frame(c, q, fd);
+    if (st) return st;
+    const psw_model_desc &m = c->md;
+    if (!m.hp) return fail(c, PSW_ERR_INVALID, "the model has no convolutional hyperprior");
+    if (!yhat_dev || !zhat_dev) return fail(c, PSW_ERR_INVALID, "null latent / hyperlatent pointer");
+    if (bitstream_dev && !len_out) return fail(c, PSW_ERR_INVALID, "len_out required with a bitstream");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = seq_schedule(q, fd->H, fd->W, fd->schedule))) return st;
+    const int HW = fd->H * fd->W, Hh = (fd->H + m.r - 1) / m.r, Wh = (fd->W + m.r - 1) / m.r, HWz = Hh * Wh;
+    if ((st = ensure_workspace(c, HW))) return st;
+    if ((st = grow_tokens(c, HW, 1))) return st;
+    if ((st = ensure_hyper(c, fd->H, fd->W))) return st;
+    // slot 0: the frame (Spatial Module 1 and, for the temporal model, its
+    // context); slot 1: the z-hat coder
+    Slot sl = make_slot(q, fd->H, fd->W, fd->schedule);
+    sl.zhat = zhat_dev;
+    c->h_slots[0] = sl;
+    Slot zs;
+    memset(&zs, 0, sizeof(zs));
+    zs.H = Hh; zs.W = Wh; zs.stride = HWz; zs.sched = PSW_SCHED_RASTER; zs.nfr = 1;
+    zs.y = zhat_dev; zs.idx = c->hz_idx; zs.m = c->hz_m; zs.order = c->hz_order;
+    zs.rstate = c->hz_rstate; zs.rptr = c->hz_rptr; zs.rend = c->hz_rend; zs.status = c->hz_status;
+    c->h_slots[1] = zs;
+    std::vector<psw_seq *> qs{q};
+    if ((st = upload_slots(c, qs, 2, s))) return st;
+    CK_CUDA(c, cudaMemsetAsync(c->hz_status, 0, sizeof(int), s));
+    std::vector<int> tok(HW);
+    for (int p = 0; p < HW; p++) tok[p] = tok_make(0, p);
+    CK_CUDA(c, cudaMemcpyAsync(c->d_tok, tok.data(), HW * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK_CUDA(c, cudaMemcpyAsync(q->y, yhat_dev, (size_t)HW * m.C * 2, cudaMemcpyDeviceToDevice, s));
+    bool failed = false;
+    Pass P{c, s, c->d_slots, &failed};
+    if (m.temporal) frame_context(P, c->d_tok, HW);
+    run_sm1(P, c->d_tok, HW);
+    hyper_analysis(P, fd->H, fd->W, zhat_dev, z_dev);
+    if (len_out) *len_out = 0;
+    if (bitstream_dev) {
+        const int cap_words = 3 * HWz + 64;
+        CoderDev cd{c->d_pcdf, c->d_pmeta, m.Ch};
+        {
+            Scope sc(c, s, K_RANS, 0.0, (double)HWz * m.Ch * 7.0);
+            launch_rans_encode(cd, c->d_slots, 1, HWz, m.Ch, c->hz_scratch, cap_words, c->hz_nw, c->hz_rstate, s);
+        }
+        Scope sc(c, s, K_RANS, 0.0, (double)HWz * m.Ch * 2.0);
+        launch_rans_assemble(Hh, Wh, m.Ch, PSW_SCHED_RASTER, c->hz_scratch, cap_words, c->hz_nw, c->hz_rstate,
+                             bitstream_dev, cap, c->hz_total, c->hz_status, s);
+    }
+    CK_CUDA(c, cudaGetLastError());
+    uint64_t total = 0;
+    int zst = 0;
+    if (bitstream_dev) CK_CUDA(c, cudaMemcpyAsync(&total, c->hz_total, 8, cudaMemcpyDeviceToHost, s));
+    CK_CUDA(c, cudaMemcpyAsync(&zst, c->hz_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    std::vector<int> sts;
+    if ((st = read_status(c, qs, s, sts))) return st;   // synchronises
+    if (failed) return fail(c, PSW_ERR_CUDA, "a GEMM launch could not be prepared");
+    if (bitstream_dev) *len_out = (size_t)total;
+    if (zst & ST_CAPACITY) return fail(c, PSW_ERR_CAPACITY, "z-hat container needs %zu bytes, capacity %zu",
+                                       (size_t)total, cap);
+    return status_code(c, sts[0] | zst);
+}
+
+psw_status psw_hyper_decode(psw_ctx *c, const psw_frame_desc *fd, const uint8_t *bitstream_dev, size_t len,
+                            int16_t *zhat_dev, void *stream)
+{
+    if (!c) return PSW_ERR_INVALID;
+    const psw_model_desc &m = c->md;
+    if (!m.hp) return fail(c, PSW_ERR_INVALID, "the model has no convolutional hyperprior");
+    if (!fd || fd->H < 1 || fd->W < 1 || !bitstream_dev || !zhat_dev) return fail(c, PSW_ERR_INVALID, "bad argument");
+    if ((uintptr_t)bitstream_dev & 3) return fail(c, PSW_ERR_INVALID, "bitstream must be 4-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Hh = (fd->H + m.r - 1) / m.r, Wh = (fd->W + m.r - 1) / m.r, HWz = Hh * Wh;
+    psw_status st;
+    if ((st = ensure_hyper(c, fd->H, fd->W))) return st;
+    if ((st = grow_tokens(c, 1, 1))) return st;
+    Slot zs;
+    memset(&zs, 0, sizeof(zs));
+    zs.H = Hh; zs.W = Wh; zs.stride = HWz; zs.sched = PSW_SCHED_RASTER; zs.nfr = 1;
+    zs.y = zhat_dev; zs.idx = c->hz_idx; zs.m = c->hz_m; zs.order = c->hz_order;
+    zs.rstate = c->hz_rstate; zs.rptr = c->hz_rptr; zs.rend = c->hz_rend; zs.status = c->hz_status;
+    zs.bs = bitstream_dev; zs.len = len;
+    c->h_slots[0] = zs;
+    CK_CUDA(c, cudaMemcpyAsync(c->d_slots, c->h_slots, sizeof(Slot), cudaMemcpyHostToDevice, s));
+    CK_CUDA(c, cudaMemsetAsync(c->hz_status, 0, sizeof(int), s));
+    int2 kn = make_int2(0, HWz);
+    CK_CUDA(c, cudaMemcpyAsync(c->d_kn, &kn, sizeof(int2), cudaMemcpyHostToDevice, s));
+    CoderDev cd{c->d_pcdf, c->d_pmeta, m.Ch};
+    launch_rans_dec_init(c->d_slots, 1, m.Ch, s);
+    launch_rans_dec_step(cd, c->d_slots, 1, c->d_kn, m.Ch, s);
+    launch_rans_dec_finish(c->d_slots, 1, m.Ch, s);
+    c->launches += 3;
+    CK_CUDA(c, cudaGetLastError());
+    int zst = 0;
+    CK_CUDA(c, cudaMemcpyAsync(&zst, c->hz_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK_CUDA(c, cudaStreamSynchronize(s));
+    return status_code(c, zst);
+}
+
+psw_status psw_prior_table(const psw_ctx *c, int ch, uint32_t *freq_host, int cap, int *n_out)
+{
+    if (!c || !c->md.hp || ch < 0 || ch >= c->md.Ch) return PSW_ERR_INVALID;
+    if (n_out) *n_out = PRIOR_N;
+    if (!freq_host) return PSW_OK;
+    if (cap < PRIOR_N) return PSW_ERR_CAPACITY;
+    for (int a = 0; a < PRIOR_N; a++) freq_host[a] = c->ptab[(size_t)ch * PRIOR_N + a] >> 16;
+    return PSW_OK;
 }
 
 psw_status psw_rate(psw_ctx *c, size_t n, const int16_t *yhat_dev, const float *mu_dev, const float *sigma_dev,

@@ -256,7 +256,8 @@ void free_cdf_tables(CdfTables &t);
 
 struct CoderDev {
     const uint32_t *cdf;                     // packed slots
-    const int *meta;                         // [3][64]: T, n, off
+    const int *meta;                         // [3][nt]: T, n, off of each table
+    int nt = NSCALES;                        // tables (the scale tables; the factorized prior: one per channel)
 };
 size_t container_capacity(int H, int W, int C);
 // Encoder of one slot: symbols y / idx / m and the schedule order from the slot.
@@ -273,6 +274,26 @@ void launch_rans_dec_step(const CoderDev &cd, const Slot *S, int nslots, const i
                           int c0 = 0, int nc = -1);
 void launch_rans_dec_finish(const Slot *S, int nslots, int C, cudaStream_t s);
 
+
+// ---------------------------------------------------------------- hyperprior (hyper.cu)
+// Token operand of a convolution over the FP32 grid src (logical [h][w][C];
+// view 1: the pixel-shuffle source of [h/2][w/2] positions ls floats apart,
+// ls 0 meaning 4C): ks = 3: every 3 x 3 tap at stride st, zero padded
+// (K = 9C, tap-major); ks = 1: the tap (st i, st j) (K = C); LeakyReLU
+// (0.01) first when act; rows of ceil(h/st) x ceil(w/st) positions in
+// raster order, compute type.
+void launch_im2col(int prec, const float *src, int h, int w, int C, int view, int ls, int act, int ks, int st,
+                   void *dst, cudaStream_t s);
+// dst [2h][2w][C] = pixel shuffle of src ([h][w] positions ls floats apart).
+void launch_shuffle(const float *src, int h, int w, int C, int ls, float *dst, cudaStream_t s);
+// gamma * z-hat of the slot of tok[0] (n hyperprior positions x Ch) as FP32.
+void launch_zhat_grid(const Slot *S, const int *tok, int n, const float *gamma, int Ch, float *dst, cudaStream_t s);
+// The slot's hyperprior tokens: the top-left H x W of a grid of row width ws.
+void launch_crop_eh(const Slot *S, const int *tok, const float *src, int ws, int H, int W, int d, cudaStream_t s);
+// z-hat = round-half-even(z), clamped to int16; zout (may be null) = z.
+void launch_round_z(const float *z, long n, int16_t *zhat, float *zout, cudaStream_t s);
+// z-hat coder inputs: table index = channel, mean 0, raster order.
+void launch_hyper_coder_tables(int HW, int Ch, uint8_t *idx, int32_t *m, int *order, cudaStream_t s);
 
 // ---------------------------------------------------------------- persistent decoder
 // One phase of a wavefront step, as the persistent decoder runs it: a

@@ -118,7 +118,7 @@ __global__ void k_rans_encode(CoderDev cd, const Slot *__restrict__ S, int slot,
         uint32_t cnt = 0, w[3] = {0, 0, 0};
         if (k < HW) {
             long a = (long)order[k] * C + c;
-            int l = idx[a], T = cd.meta[l], off = cd.meta[2 * NSCALES + l];
+            int l = idx[a], T = cd.meta[l], off = cd.meta[2 * cd.nt + l];
             long sv = (long)y[a] - (long)m[a];
             int slot_ = 0;
             bool esc = false;

@@ -63,7 +63,7 @@ __device__ __forceinline__ void rans_step_item(const CoderDev &cd, const Slot *_
             int l = sl.idx[a];
             mm = sl.m[a];
             T = cd.meta[l];
-            int nsl = cd.meta[NSCALES + l], off = cd.meta[2 * NSCALES + l];
+            int nsl = cd.meta[cd.nt + l], off = cd.meta[2 * cd.nt + l];
             uint32_t v = x & 0xFFFFu;
             int lo = 0, hi = nsl - 1;                  // last slot with cum <= v
             while (lo < hi) {

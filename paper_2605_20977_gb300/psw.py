@@ -26,14 +26,15 @@ EXPORTS = ["psw_weights_count", "psw_create", "psw_destroy", "psw_last_error", "
            "psw_decode_frame", "psw_decode_batch", "psw_rate", "psw_quantize", "psw_scale_table", "psw_cdf_table",
            "psw_rans_encode", "psw_rans_decode", "psw_launch_count", "psw_profile_begin", "psw_profile_end",
            "psw_rans_encode_noalloc", "psw_set_engine", "psw_last_engine", "psw_quantize_e4m3",
-           "psw_check_wait_timeout", "psw_lrp_residual"]
+           "psw_check_wait_timeout", "psw_lrp_residual", "psw_hyper_encode", "psw_hyper_decode",
+           "psw_prior_table"]
 
 ENGINE_AUTO, ENGINE_GRAPH, ENGINE_PERSISTENT = 0, 1, 2
 
 
 class ModelDesc(ct.Structure):
     _fields_ = [(n, ct.c_int) for n in ("C", "Ch", "r", "d", "nh", "F", "L", "k", "temporal", "Lc", "Tf", "mask",
-                                         "Llrp", "Nc", "dc", "Lct", "Fc")]
+                                         "Llrp", "Nc", "dc", "Lct", "Fc", "hp")]
 
 
 class FrameDesc(ct.Structure):
@@ -83,6 +84,9 @@ def load(path: str = LIB_PATH):
             "psw_decode_batch": (I, [P, I, P, FD, P, P, P, P, P, P, P, P]),
             "psw_rate": (I, [P, S, P, P, P, ct.POINTER(ct.c_double), P]),
             "psw_lrp_residual": (I, [P, P, FD, P, P]),
+            "psw_hyper_encode": (I, [P, P, FD, P, P, P, P, S, ct.POINTER(S), P]),
+            "psw_hyper_decode": (I, [P, FD, P, S, P, P]),
+            "psw_prior_table": (I, [P, I, P, I, ct.POINTER(I)]),
             "psw_quantize": (I, [P, S, P, P, P, P, P]),
             "psw_scale_table": (I, [P, P]),
             "psw_cdf_table": (I, [P, I, P, I, ct.POINTER(I), ct.POINTER(I)]),
@@ -214,6 +218,18 @@ class Context:
         self._check(self.lib.psw_cdf_table(self.h, l, f.ctypes.data, 4096, ct.byref(n), ct.byref(T)))
         return f[:n.value].copy(), T.value
 
+    def hyper_decode(self, fd: FrameDesc, bitstream, length: int, zhat, stream=None, check: bool = True) -> int:
+        st = self.lib.psw_hyper_decode(self.h, ct.byref(fd), _ptr(bitstream), length, _ptr(zhat), _stream(stream))
+        if check:
+            self._check(st)
+        return st
+
+    def prior_table(self, ch: int) -> np.ndarray:
+        f = (ct.c_uint32 * 64)()
+        n = ct.c_int(0)
+        self._check(self.lib.psw_prior_table(self.h, ch, f, 64, ct.byref(n)))
+        return np.array(f[:n.value], np.uint32)
+
     def rans_encode_noalloc(self, fd: FrameDesc, y, idx, m, bitstream, stream=None, check: bool = True):
         """Coder-only encode without device allocation; returns (status, length)."""
         n = ct.c_size_t(0)
@@ -299,6 +315,15 @@ class Sequence:
         if check:
             self.ctx._check(st)
         return st
+
+    def hyper_encode(self, fd: FrameDesc, y, zhat, z=None, bitstream=None, stream=None) -> int:
+        """Convolutional hyperprior: z-hat of the next frame (and z), and
+        its container if a bitstream buffer is given; returns its length."""
+        n = ct.c_size_t(0)
+        cap = bitstream.numel() if bitstream is not None else 0
+        self.ctx._check(self.ctx.lib.psw_hyper_encode(self.ctx.h, self.h, ct.byref(fd), _ptr(y), _ptr(zhat), _ptr(z),
+                                                      _ptr(bitstream), cap, ct.byref(n), _stream(stream)))
+        return int(n.value)
 
     def lrp_residual(self, fd: FrameDesc, eps=None, stream=None):
         """The LRP Transformer's residual eps [H][W][C] float32 of the last

@@ -36,7 +36,7 @@ def test_exports_every_declared_symbol(lib):
 
 @pytest.mark.parametrize("name", ["tiny", "tiny_p", "tiny_cyc", "i1080", "p1080", "tiny_lrp", "tiny_p_lrp",
                                   "i1080_lrp", "p1080_lrp", "tiny_ct", "tiny_cyc_ct", "tiny_p_ct", "tiny_ct_lrp",
-                                  "i1080_ct", "i1080_cyc_ct"])
+                                  "i1080_ct", "i1080_cyc_ct", "tiny_hp", "tiny_p_hp", "i1080_hp", "p1080_hp"])
 def test_weights_count_matches_layouts(lib, name):
     c = synth.config(name)
     assert psw.psw_weights_count(c) == synth.weights_count(c) == O.weights_count(c)
@@ -48,7 +48,7 @@ def test_invalid_descriptors_rejected(lib):
                 dict(temporal=1, Lc=0), dict(temporal=1, Lc=1, Tf=5), dict(Llrp=-1), dict(Llrp=65),
                 dict(dc=256), dict(Nc=4, dc=256, Lct=0, Fc=192), dict(Nc=3, dc=192, Lct=2, Fc=192),
                 dict(Nc=4, dc=128, Lct=2, Fc=192), dict(Nc=4, dc=256, Lct=2, Fc=100),
-                dict(Nc=2, dc=2048, Lct=2, Fc=192)):
+                dict(Nc=2, dc=2048, Lct=2, Fc=192), dict(hp=2), dict(hp=1, r=3), dict(hp=1, Ch=30)):
         d = dict(c); d.update(bad)
         assert psw.psw_weights_count(d) == 0, bad
 

@@ -68,6 +68,8 @@ def parse(argv=None):
                     help="timed steps of the cyclic s = 4 schedule leg (0: skip)")
     ap.add_argument("--lrp-steps", type=int, default=3,
                     help="timed LRP Transformer passes over one decoded 1080p frame (0: skip)")
+    ap.add_argument("--hyper-steps", type=int, default=3,
+                    help="timed passes of the convolutional hyperprior leg (0: skip)")
     ap.add_argument("--engine", choices=["auto", "graph", "persistent"], default="auto",
                     help="decode engine: one cooperative kernel over all steps, or per-phase kernels in CUDA graphs")
     return ap.parse_args(argv)
@@ -390,6 +392,71 @@ def lrp_run(args, dev, timed, ys, zs):
     return out
 
 
+def hyper_run(args, dev, timed, ys, B):
+    """The convolutional hyperprior (Fig. 1 right) at 1080p: per frame the
+    encoder's analysis and z-hat coding (psw_hyper_encode: Spatial Module 1,
+    two RB-down blocks, rANS under the factorized prior), the decoder's
+    z-hat decode (psw_hyper_decode), and a B-frame batched decode whose
+    prologues synthesise the hyperprior tokens (two RB-up blocks per frame).
+    Inputs resident in HBM; the z-hat of each frame comes from its own
+    analysis."""
+    import torch
+    from paper_2605_20977_gb300 import psw, synth
+    cfg = synth.config("i1080_hp")
+    ctx = psw.Context(cfg, synth.weights(cfg), precision=psw.PSW_BF16)
+    fd = psw.frame_desc(cfg.H, cfg.W, psw.PSW_SCHED_WAVEFRONT)
+    cap_z = ctx.bitstream_capacity(cfg.Hh, cfg.Wh) + 16 * cfg.Ch
+    cap_y = ctx.bitstream_capacity(cfg.H, cfg.W)
+    enc = ctx.seq_create(cfg.H, cfg.W)
+    zhs, bzs, nzs, bys, nys = [], [], [], [], []
+    for b in range(B):
+        enc.reset()
+        zh = torch.zeros((cfg.Hh, cfg.Wh, cfg.Ch), dtype=torch.int16, device=dev)
+        bz = torch.zeros(cap_z, dtype=torch.uint8, device=dev)
+        nzs.append(enc.hyper_encode(fd, ys[b], zh, None, bz))
+        by = torch.zeros(cap_y, dtype=torch.uint8, device=dev)
+        nys.append(enc.encode_params(fd, ys[b], zh, None, None, by))
+        zhs.append(zh); bzs.append(bz); bys.append(by)
+    zt = torch.zeros_like(zhs[0])
+    ms_enc = timed(lambda: (enc.reset(), enc.hyper_encode(fd, ys[0], zt, None, bzs[0])), args.hyper_steps)
+    ms_dec = timed(lambda: ctx.hyper_decode(fd, bzs[0], nzs[0], zt), args.hyper_steps)
+    if not torch.equal(zt, zhs[0]):
+        raise RuntimeError("z-hat decode differs")
+    ctx.profile_begin()
+    enc.reset()
+    enc.hyper_encode(fd, ys[0], zt, None, bzs[0])
+    st_enc = ctx.profile_end()
+    enc.close()
+    decs = [ctx.seq_create(cfg.H, cfg.W) for _ in range(B)]
+    outs = [torch.zeros_like(y) for y in ys[:B]]
+
+    def step():
+        for q in decs:
+            q.reset()
+        ctx.decode_batch(decs, [fd] * B, bys, nys, zhs, outs)
+
+    step()
+    ms = timed(step, max(2, args.hyper_steps - 1))
+    for b in range(B):
+        if not torch.equal(outs[b], ys[b]):
+            raise RuntimeError("hyperprior-model decode differs")
+    for q in decs:
+        q.close()
+    ctx.close()
+    g = next((s_ for s_ in st_enc if s_["name"] == "gemm_tc"), None)
+    out = {"analysis_and_zhat_coding_ms_per_frame": float(np.mean(ms_enc)),
+           "zhat_decode_ms_per_frame": float(np.mean(ms_dec)),
+           "decode": {"value": B * 1e3 / float(np.mean(ms)), "unit": "frames/s", "frames_per_step": B},
+           "zhat_bytes_per_frame": float(np.mean(nzs)),
+           "workload": "1080p I-frames 68x120x192 with the convolutional hyperprior (2 RB-down / 2 RB-up "
+                       "blocks, Ch = 128, factorized prior), BF16",
+           "encode_classes": {s_["name"]: {"ms": round(s_["ms"], 3), "launches": s_["launches"],
+                                           "gflop": round(s_["flops"] / 1e9, 2)} for s_ in st_enc}}
+    if g:
+        out["encode_projections_tflops"] = g["flops"] / (g["ms"] / 1e3) / 1e12
+    return out
+
+
 def cyclic_run(args, dev, timed, w, ys, zs, B, name="i1080_cyc"):
     """The paper's own schedule (cyclic s = 4 mask, Fig. 2a): the same model
     sizes and frames, 4 steps per frame of 2040 positions each.  Frames/s at
@@ -699,6 +766,11 @@ def run_ours(args, rank: int, world: int, local: int):
     if rank == 0 and args.cyclic_steps > 0 and args.precision == "bf16":
         cyclic_ct = cyclic_run(args, dev, timed, w, ys, zs, B, name="i1080_cyc_ct")
 
+    # the convolutional hyperprior
+    hyper = None
+    if rank == 0 and args.hyper_steps > 0 and args.precision == "bf16":
+        hyper = hyper_run(args, dev, timed, ys, min(B, 16))
+
     # the LRP Transformer over one coded frame
     lrp = None
     if rank == 0 and args.lrp_steps > 0 and args.precision == "bf16":
@@ -747,7 +819,7 @@ def run_ours(args, rank: int, world: int, local: int):
             "latency_one_frame": lat,
             "roofline": roof, "raster": raster, "speedup_vs_raster": speedup,
             "rate": rate, "clocks": clk, "cpu_baseline": cpu, "pframe": pframe, "fp8": fp8, "cyclic": cyclic,
-            "cyclic_channel_groups": cyclic_ct, "lrp": lrp}
+            "cyclic_channel_groups": cyclic_ct, "lrp": lrp, "hyperprior": hyper}
     print(json.dumps(line), flush=True)
     return 0
 

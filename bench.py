@@ -70,6 +70,11 @@ def parse(argv=None):
                     help="timed LRP Transformer passes over one decoded 1080p frame (0: skip)")
     ap.add_argument("--hyper-steps", type=int, default=3,
                     help="timed passes of the convolutional hyperprior leg (0: skip)")
+    ap.add_argument("--mixed-frames", type=int, default=4,
+                    help="batched-uneven leg: frames per sequence of 32 P-frame sequences over four grids (0: skip)")
+    ap.add_argument("--serve-rates", default="2,4,8",
+                    help="serving sweep: Poisson request rates per second, comma separated (empty: skip)")
+    ap.add_argument("--serve-window", type=float, default=10.0, help="serving sweep: arrival window in seconds")
     ap.add_argument("--engine", choices=["auto", "graph", "persistent"], default="auto",
                     help="decode engine: one cooperative kernel over all steps, or per-phase kernels in CUDA graphs")
     return ap.parse_args(argv)
@@ -771,6 +776,30 @@ def run_ours(args, rank: int, world: int, local: int):
     if rank == 0 and args.hyper_steps > 0 and args.precision == "bf16":
         hyper = hyper_run(args, dev, timed, ys, min(B, 16))
 
+    # batched uneven: four grids of P-frame sequences per call, autotuned plan
+    mixed = None
+    if rank == 0 and args.mixed_frames > 0 and args.precision == "bf16":
+        from paper_2605_20977_gb300 import workloads
+        mixed = workloads.run_mixed(32, args.mixed_frames, dev=dev, precision="bf16")
+
+    # serving: continuous batching under Poisson arrivals, a sweep of rates
+    serving = None
+    if rank == 0 and args.serve_rates.strip() and args.precision == "bf16":
+        from paper_2605_20977_gb300 import workloads
+        sweep = []
+        for lam in [float(x) for x in args.serve_rates.split(",") if x.strip()]:
+            st = workloads.run_serve(rate=lam, window=args.serve_window, dev=dev, unbatched=False, precision="bf16")
+            b = st["batched"]
+            offered = b["frames"] / args.serve_window
+            sweep.append({"rate_per_s": lam, "offered_frames_per_s": offered, "served_frames_per_s": b["frames_per_s"],
+                          "latency_p50_s": b["latency_p50_s"], "latency_p99_s": b["latency_p99_s"],
+                          "requests": b["requests"], "frames": b["frames"], "mean_batch": b["mean_batch"]})
+        # the knee: the highest rate served at 90 % or more of its offered load
+        ok = [x["rate_per_s"] for x in sweep if x["served_frames_per_s"] >= 0.9 * x["offered_frames_per_s"]]
+        serving = {"workload": f"P-frame requests of 1..16 frames at the grids 15x26, 30x52, 68x120, 135x240, "
+                               f"Poisson arrivals over {args.serve_window:g} s, continuous batching, BF16, graph engine",
+                   "sweep": sweep, "knee_rate_per_s": max(ok) if ok else None}
+
     # the LRP Transformer over one coded frame
     lrp = None
     if rank == 0 and args.lrp_steps > 0 and args.precision == "bf16":
@@ -819,7 +848,8 @@ def run_ours(args, rank: int, world: int, local: int):
             "latency_one_frame": lat,
             "roofline": roof, "raster": raster, "speedup_vs_raster": speedup,
             "rate": rate, "clocks": clk, "cpu_baseline": cpu, "pframe": pframe, "fp8": fp8, "cyclic": cyclic,
-            "cyclic_channel_groups": cyclic_ct, "lrp": lrp, "hyperprior": hyper}
+            "cyclic_channel_groups": cyclic_ct, "lrp": lrp, "hyperprior": hyper,
+            "batched_uneven": mixed, "serving": serving}
     print(json.dumps(line), flush=True)
     return 0
 

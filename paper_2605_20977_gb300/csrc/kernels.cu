@@ -9,6 +9,7 @@
 #include "internal.h"
 #include "device_common.cuh"
 #include "attn_dev.cuh"
+#include "attn_tok.cuh"
 
 #include <math.h>
 
@@ -253,6 +254,18 @@ __global__ void __launch_bounds__(32 * attn_wpb<T, DH>()) k_attention(AttnArgs a
     attn_item<T, DH, true, CK, MAXC>(a, gw, sm[wib]);
 }
 
+// 64-wide BF16 heads: one warp per token and head group, on the tensor
+// cores (attn_tok.cuh); TK_WPB warps per block, each with its own staging.
+constexpr int TK_WPB = 4;
+
+__global__ void __launch_bounds__(32 * TK_WPB, 4) k_attn_tok(AttnArgs a)
+{
+    extern __shared__ __align__(16) unsigned char tk_smem[];
+    const int wib = threadIdx.x >> 5, gw = blockIdx.x * TK_WPB + wib;
+    if (gw >= a.n * (a.nh / TK_HG)) return;                    // warps are independent: no block barrier
+    attn_token<true>(a, gw, tk_smem + (size_t)wib * attn_tok_bytes());
+}
+
 // Spatial windows (k * k <= 81 candidates) take the compact staging.
 template <typename T, int DH>
 static void attention_dh(const AttnArgs &a, cudaStream_t s)
@@ -281,6 +294,11 @@ static bool attention_carveout()
 
 bool attention_prepare()
 {
+    if (cudaFuncSetAttribute(k_attn_tok, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(TK_WPB * attn_tok_bytes())) != cudaSuccess ||
+        cudaFuncSetAttribute(k_attn_tok, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return false;
     if (cudaFuncSetAttribute(k_embed_hyper, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 4096 * 4) != cudaSuccess)
         return false;                                 // 4 staged hyperlatents of 4096 channels
     return attention_carveout<__nv_bfloat16, 32>() && attention_carveout<__nv_bfloat16, 64>() &&
@@ -302,6 +320,11 @@ static void attention_t(const AttnArgs &a, cudaStream_t s)
 void launch_attention(int prec, const AttnArgs &a, cudaStream_t s)
 {
     if (a.n <= 0) return;
+    if (attn_tok_ok(prec, a.d, a.nh, a.mask, a.kind)) {
+        launch_pdl(k_attn_tok, dim3(cdiv((long)a.n * (a.nh / TK_HG), TK_WPB)), dim3(32 * TK_WPB),
+                   TK_WPB * attn_tok_bytes(), s, a);
+        return;
+    }
     if (prec == P_BF16) attention_t<__nv_bfloat16>(a, s);
     else attention_t<float>(a, s);
 }

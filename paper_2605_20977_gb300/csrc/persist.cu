@@ -28,6 +28,7 @@
 // guaranteed by the cooperative launch.
 #include "gemm_dev.cuh"
 #include "attn_dev.cuh"
+#include "attn_tok.cuh"
 #include "rans_dev.cuh"
 
 #include <map>
@@ -212,6 +213,15 @@ __device__ __noinline__ void run_gemm(GemmShared &S, uint8_t *ring, uint32_t tme
     }
 }
 
+// 64-wide heads: one warp per token and head group (attn_tok.cuh), the
+// same function as the attention kernel's.
+__device__ __noinline__ void attn_tok_phase(const AttnArgs &a, uint8_t *dyn, int rank)
+{
+    const int warp = threadIdx.x >> 5, items = a.n * (a.nh / TK_HG);
+    unsigned char *sm = dyn + (size_t)warp * attn_tok_bytes();
+    for (int gw = rank * PWARPS + warp; gw < items; gw += gridDim.x * PWARPS) attn_token<false>(a, gw, sm);
+}
+
 template <int DH>
 __device__ __noinline__ void attn_phase(const AttnArgs &a, uint8_t *dyn, int rank)
 {
@@ -235,7 +245,8 @@ __device__ __forceinline__ int phase_units(const PersistArgs &P, const Op &op)
         int nf;
         return gemm_tiles(op.g, nf);
     }
-    int items = op.type == OP_ATTN ? op.a.n * op.a.nh : P.nslots * P.C;
+    int items = op.type == OP_ATTN ? (attn_tok_ok(P_BF16, op.a.d, op.a.nh, op.a.mask, op.a.kind) ? op.a.n * (op.a.nh / TK_HG) : op.a.n * op.a.nh)
+                                   : P.nslots * P.C;
     return (items + PWARPS - 1) / PWARPS;
 }
 
@@ -293,7 +304,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_persist(const __grid_constant__
             if (op.type == OP_GEMM) run_gemm<F8>(S, dyn, tmem, maps, op, rank, prepared, first, pp);
             else if (op.type == OP_ATTN) {
                 const int dh = op.a.d / op.a.nh;
-                if (dh == 64) attn_phase<64>(op.a, dyn, rank);
+                if (attn_tok_ok(P_BF16, op.a.d, op.a.nh, op.a.mask, op.a.kind)) attn_tok_phase(op.a, dyn, rank);
+                else if (dh == 64) attn_phase<64>(op.a, dyn, rank);
                 else if (dh == 32) attn_phase<32>(op.a, dyn, rank);
                 else attn_phase<128>(op.a, dyn, rank);
             } else {
@@ -403,8 +415,9 @@ void program_attn(ProgramBuilder *b, const AttnArgs &a, int tokset)
     op.a = a;
     b->ops.push_back(op);
     int dh = a.d / a.nh;
-    size_t per = dh == 32 ? sizeof(AttnWarp<__nv_bfloat16, 32>)
-                          : dh == 64 ? sizeof(AttnWarp<__nv_bfloat16, 64>) : sizeof(AttnWarp<__nv_bfloat16, 128>);
+    size_t per = attn_tok_ok(P_BF16, a.d, a.nh, a.mask, a.kind) ? attn_tok_bytes()
+                 : dh == 32 ? sizeof(AttnWarp<__nv_bfloat16, 32>)
+                 : dh == 64 ? sizeof(AttnWarp<__nv_bfloat16, 64>) : sizeof(AttnWarp<__nv_bfloat16, 128>);
     b->smem = std::max(b->smem, per * PWARPS);
 }
 

@@ -5,7 +5,7 @@ Workload: the 1080p I-frame configuration -- latents 68x120x192 (a
 1088x1920 frame after the /16 feature transform), hyperlatents 17x30x128,
 context model d=384, 6 heads, 7x7 windows, 8 blocks in each spatial module
 plus the accumulator, BF16 projections with FP32 accumulation.  A step
-decodes one batch of frames (default 1) from their rANS containers along the
+decodes one batch of frames (default 256) from their rANS containers along the
 254 wavefronts 2i+j = t: every position of a wavefront is predicted
 together, its symbols decoded, and the next wavefront follows.  Inputs are
 synthetic (seeded AR(1) latents, random weights); the containers are made by
@@ -50,7 +50,7 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--batch", type=int, default=128, help="frames decoded per step")
+    ap.add_argument("--batch", type=int, default=256, help="frames decoded per step")
     ap.add_argument("--raster-frames", type=int, default=1, help="timed raster steps (0: skip raster)")
     ap.add_argument("--no-raster-batch", dest="raster_batch", action="store_false")
     ap.add_argument("--raster-batch-size", type=int, default=16,
@@ -466,8 +466,7 @@ def cyclic_run(args, dev, timed, w, ys, zs, B, name="i1080_cyc"):
     """The paper's own schedule (cyclic s = 4 mask, Fig. 2a): the same model
     sizes and frames, 4 steps per frame of 2040 positions each.  Frames/s at
     B frames per call, single-frame latency, and the projections' tensor
-    rate from one instrumented step (about 261 k tokens per launch at 128
-    frames).  name = "i1080_cyc_ct" adds the Channel Transformer (4 channel
+    rate from one instrumented step (2040 tokens per frame in every launch).  name = "i1080_cyc_ct" adds the Channel Transformer (4 channel
     groups after each spatial step: s x N = 16 steps per frame, the paper's
     configuration), with its own weights."""
     import torch

@@ -228,7 +228,7 @@ psw_status psw_decode_frame(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd
                             int16_t *yhat_out_dev, float *mu_dev, float *sigma_dev, void *stream);
 
 /* Batched decode: n frames of n different sequences (any mix of grids and
- * schedules up to each sequence's maximum, 1 <= n <= 128) decoded together:
+ * schedules up to each sequence's maximum, 1 <= n <= 256) decoded together:
  * step t of every frame runs in global step t, so each launch carries the
  * positions of all frames (Sec. 3.2 parallelism across frames as well as
  * along a wavefront).  Arrays have n entries; mu_dev / sigma_dev may be NULL

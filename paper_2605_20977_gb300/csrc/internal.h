@@ -20,7 +20,7 @@ constexpr int NSCALES = 64;
 constexpr int CDF_PREC = 16;
 constexpr int MAX_KK = 81;        // largest window (9 x 9)
 constexpr int MAX_TF = 4;         // frames in a temporal window
-constexpr int MAX_SLOTS = 128;    // frames in one batch (token word: slot << 24 | position)
+constexpr int MAX_SLOTS = 256;    // frames in one batch (token word: slot << 24 | position)
 constexpr int WIDE_M = 1024;      // tokens from which a projection takes the persistent tensor-core kernel
 
 // One frame in flight.  A device-resident table of these lets one launch
@@ -53,7 +53,7 @@ struct Slot {
 
 __host__ __device__ inline int tok_slot(int t) { return (int)((unsigned)t >> 24); }
 __host__ __device__ inline int tok_pos(int t) { return t & 0xFFFFFF; }
-__host__ __device__ inline int tok_make(int slot, int pos) { return (slot << 24) | pos; }
+__host__ __device__ inline int tok_make(int slot, int pos) { return (int)(((unsigned)slot << 24) | (unsigned)pos); }
 
 // Caches a kernel can name.
 enum CacheSel { CS_NONE = -1, CS_K1 = 0, CS_V1, CS_K2, CS_V2, CS_KA, CS_VA, CS_QA, CS_CK, CS_CV, CS_XK, CS_XV,

@@ -75,6 +75,8 @@ def parse(argv=None):
     ap.add_argument("--serve-rates", default="2,8,24",
                     help="serving sweep: Poisson request rates per second, comma separated (empty: skip)")
     ap.add_argument("--serve-window", type=float, default=5.0, help="serving sweep: arrival window in seconds")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="skip the tile-width autotuner (keep the library's cost model)")
     ap.add_argument("--engine", choices=["auto", "graph", "persistent"], default="auto",
                     help="decode engine: one cooperative kernel over all steps, or per-phase kernels in CUDA graphs")
     return ap.parse_args(argv)
@@ -604,6 +606,13 @@ def run_ours(args, rank: int, world: int, local: int):
     for _ in range(args.warmup):
         batch_step(decs, fdw, bss, lens, B)
     torch.cuda.synchronize()
+    # the autotuner picks the projection tile widths on this very step
+    tuned = None
+    if args.tune:
+        from paper_2605_20977_gb300 import workloads
+        tuned = workloads.tune_tiles(ctx, lambda: batch_step(decs, fdw, bss, lens, B))
+        batch_step(decs, fdw, bss, lens, B)
+        torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clocks = Clocks(local)
@@ -851,7 +860,7 @@ def run_ours(args, rank: int, world: int, local: int):
             "roofline": roof, "raster": raster, "speedup_vs_raster": speedup,
             "rate": rate, "clocks": clk, "cpu_baseline": cpu, "pframe": pframe, "fp8": fp8, "cyclic": cyclic,
             "cyclic_channel_groups": cyclic_ct, "lrp": lrp, "hyperprior": hyper,
-            "batched_uneven": mixed, "serving": serving}
+            "batched_uneven": mixed, "serving": serving, "tile_autotune": tuned}
     print(json.dumps(line), flush=True)
     return 0
 

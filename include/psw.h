@@ -402,6 +402,21 @@ typedef enum { PSW_ENGINE_AUTO = 0, PSW_ENGINE_GRAPH = 1, PSW_ENGINE_PERSISTENT 
 psw_status psw_set_engine(psw_ctx *ctx, int engine);
 int psw_last_engine(const psw_ctx *ctx);
 
+/* Tile policy of the persistent warp-specialised projection kernel (not in
+ * the paper; an implementation choice the autotuner makes): tokens per tile
+ * (64, 128 or 256; 0 = the library's cost model) for each launch class --
+ * QKV projections, residual projections (attention output, FFN down,
+ * accumulator output), the SwiGLU gate/up pair, and the rest.  A width the
+ * class's epilogue cannot take is capped.  Every width gives bit-identical
+ * results (one accumulator per output, K in ascending order), so the policy
+ * changes only speed.  Setting it synchronises the device and drops the
+ * recorded decode graphs.  PSW_ERR_INVALID for an unknown class or width;
+ * psw_tile_policy returns the current value (-1 for a bad argument). */
+typedef enum { PSW_TILE_QKV = 0, PSW_TILE_RESIDUAL = 1, PSW_TILE_SWIGLU = 2, PSW_TILE_OTHER = 3,
+               PSW_TILE_CLASSES = 4 } psw_tile_class;
+psw_status psw_set_tile_policy(psw_ctx *ctx, int cls, int tokens);
+int psw_tile_policy(const psw_ctx *ctx, int cls);
+
 /* Instrumentation (not in the paper; measurement support).
  * psw_launch_count: kernels this context has launched so far.
  * psw_profile_begin: from now on every kernel launch of this context is

@@ -308,6 +308,7 @@ struct psw_ctx {
     // persistent decoder: the program of one step (rebuilt when the
     // workspace moves), its kernel's shared memory and grid, barrier words
     int engine = PSW_ENGINE_AUTO;
+    int tile_policy[PSW_TILE_CLASSES] = {0, 0, 0, 0};   // wide kernel tokens per tile per launch class (0: automatic)
     int last_engine = 0;               // engine of the last decode (0: direct launches)
     ProgramBuilder *prog = nullptr;
     int prog_gen = -1;
@@ -952,6 +953,9 @@ void gemm_any(const Pass &P, int asrc, const float *xrows, const float *a_gain, 
     g.Wt = Wt; g.Wt2 = Wt2; g.M = M; g.N = N; g.K = K; g.epi = e;
     g.epi.slots = P.S;
     g.status = P.c->d_status;
+    g.tnb = P.c->tile_policy[e.mode == EPI_QKV ? PSW_TILE_QKV
+                             : (e.mode == EPI_RESID || e.mode == EPI_RESID_BASE) ? PSW_TILE_RESIDUAL
+                             : e.mode == EPI_SWIGLU ? PSW_TILE_SWIGLU : PSW_TILE_OTHER];
     auto f8 = P.c->f8sc.find(Wt);
     if (f8 != P.c->f8sc.end()) {
         auto f82 = Wt2 ? P.c->f8sc.find(Wt2) : P.c->f8sc.end();
@@ -2355,6 +2359,27 @@ psw_status psw_set_engine(psw_ctx *c, int engine)
 }
 
 int psw_last_engine(const psw_ctx *c) { return c ? c->last_engine : 0; }
+
+psw_status psw_set_tile_policy(psw_ctx *c, int cls, int tokens)
+{
+    if (!c) return fail(nullptr, PSW_ERR_INVALID, "null context");
+    if (cls < 0 || cls >= PSW_TILE_CLASSES) return fail(c, PSW_ERR_INVALID, "unknown launch class %d", cls);
+    if (tokens != 0 && tokens != 64 && tokens != 128 && tokens != 256)
+        return fail(c, PSW_ERR_INVALID, "tokens per tile must be 0, 64, 128 or 256");
+    if (c->tile_policy[cls] == tokens) return PSW_OK;
+    CK_CUDA(c, cudaDeviceSynchronize());
+    c->tile_policy[cls] = tokens;
+    // recorded graphs hold the old launches
+    c->ws_gen++;
+    for (auto &kv : c->graphs) graph_free(kv.second);
+    c->graphs.clear();
+    return PSW_OK;
+}
+
+int psw_tile_policy(const psw_ctx *c, int cls)
+{
+    return c && cls >= 0 && cls < PSW_TILE_CLASSES ? c->tile_policy[cls] : -1;
+}
 
 psw_status psw_profile_begin(psw_ctx *c)
 {

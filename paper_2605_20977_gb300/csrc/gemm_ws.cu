@@ -513,7 +513,8 @@ bool gemm_ws(const GemmArgs &g, cudaStream_t s)
 {
     if (!gemm_ws_supported(g)) return false;
     const bool dual = g.epi.mode == EPI_SWIGLU;
-    const int tnb = gemm_ws_tile_tokens(g.N, g.M, g.K, dual, g.epi.mode == EPI_RESID || g.epi.mode == EPI_RESID_BASE);
+    int tnb = gemm_ws_tile_tokens(g.N, g.M, g.K, dual, g.epi.mode == EPI_RESID || g.epi.mode == EPI_RESID_BASE);
+    if (g.tnb == 64 || g.tnb == 128 || g.tnb == 256) tnb = std::min(g.tnb, ws_max_tn(dual, g.epi.mode));
     CUtensorMap tw, tw2, tx;
     if (!gemm_tensor_map(g.Wt, g.N, g.K, g.K, TM, &tw)) return false;
     if (dual && !gemm_tensor_map(g.Wt2, g.N, g.K, g.K, TM, &tw2)) return false;

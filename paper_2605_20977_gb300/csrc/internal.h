@@ -138,6 +138,8 @@ struct GemmArgs {
     int M, N, K;
     Epi epi;
     int *status;                  // device status word (ST_TIMEOUT from bounded waits)
+    int tnb;                      // wide kernel's tokens per tile (0: its cost model; else 64, 128 or 256,
+                                  //    capped at the largest its epilogue takes)
 };
 
 // Enqueue one GEMM.  BF16 projections whose N and K tile evenly run on the

@@ -27,7 +27,8 @@ EXPORTS = ["psw_weights_count", "psw_create", "psw_destroy", "psw_last_error", "
            "psw_rans_encode", "psw_rans_decode", "psw_launch_count", "psw_profile_begin", "psw_profile_end",
            "psw_rans_encode_noalloc", "psw_set_engine", "psw_last_engine", "psw_quantize_e4m3",
            "psw_check_wait_timeout", "psw_lrp_residual", "psw_hyper_encode", "psw_hyper_decode",
-           "psw_prior_table"]
+           "psw_prior_table", "psw_set_tile_policy", "psw_tile_policy"]
+TILE_QKV, TILE_RESIDUAL, TILE_SWIGLU, TILE_OTHER = 0, 1, 2, 3
 
 ENGINE_AUTO, ENGINE_GRAPH, ENGINE_PERSISTENT = 0, 1, 2
 
@@ -87,6 +88,8 @@ def load(path: str = LIB_PATH):
             "psw_hyper_encode": (I, [P, P, FD, P, P, P, P, S, ct.POINTER(S), P]),
             "psw_hyper_decode": (I, [P, FD, P, S, P, P]),
             "psw_prior_table": (I, [P, I, P, I, ct.POINTER(I)]),
+            "psw_set_tile_policy": (I, [P, I, I]),
+            "psw_tile_policy": (I, [P, I]),
             "psw_quantize": (I, [P, S, P, P, P, P, P]),
             "psw_scale_table": (I, [P, P]),
             "psw_cdf_table": (I, [P, I, P, I, ct.POINTER(I), ct.POINTER(I)]),
@@ -249,6 +252,12 @@ class Context:
     def set_engine(self, engine: int):
         """Decode engine: ENGINE_AUTO, ENGINE_GRAPH or ENGINE_PERSISTENT."""
         self._check(self.lib.psw_set_engine(self.h, int(engine)))
+
+    def set_tile_policy(self, cls: int, tokens: int):
+        self._check(self.lib.psw_set_tile_policy(self.h, cls, tokens))
+
+    def tile_policy(self) -> list:
+        return [int(self.lib.psw_tile_policy(self.h, k)) for k in range(4)]
 
     def last_engine(self) -> int:
         """Engine of the last decode (0: individual launches)."""

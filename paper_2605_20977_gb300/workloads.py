@@ -128,6 +128,46 @@ def run_mixed(nseq=32, nframes=4, tune_frames=1, seed=7, dev=None, precision="bf
             "tflops": work / dt / 1e3, "seconds": dt}
 
 
+def tune_tiles(ctx, step, reps: int = 1, classes=(0, 1, 2, 3), widths=(0, 64, 128, 256)):
+    """Autotuner of the wide projection kernel's tile widths (tokens per
+    tile per launch class, psw_set_tile_policy): coordinate descent from the
+    library's cost model, each candidate timed over `reps` calls of `step`
+    after one untimed call (which records the new graphs).  Every width
+    gives bit-identical results, so only time decides.  Leaves the best
+    policy set; returns it with the timings."""
+    import torch
+
+    def timed():
+        step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            step()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / reps
+
+    names = {0: "qkv", 1: "residual", 2: "swiglu", 3: "other"}
+    policy = [0, 0, 0, 0]
+    for k in range(4):
+        ctx.set_tile_policy(k, 0)
+    best = timed()
+    trials = {"auto": best}
+    for k in classes:
+        choice = policy[k]
+        for wdt in widths:
+            if wdt == policy[k]:
+                continue
+            ctx.set_tile_policy(k, wdt)
+            t = timed()
+            trials[f"{names[k]}={wdt}"] = t
+            if t < best * 0.99:
+                best, choice = t, wdt
+        policy[k] = choice
+        ctx.set_tile_policy(k, choice)
+    return {"policy": {names[k]: policy[k] for k in range(4)}, "seconds_per_step": best,
+            "trials_seconds_per_step": trials}
+
+
 def run_serve(rate=200.0, window=0.1, per_grid=2, gop=16, budget_gb=120.0, max_batch=128, seed=1005, dev=None,
               unbatched=True, precision="fp8", engines=("graph",)):
     """Batched service in `precision` (once per decode engine in `engines`)

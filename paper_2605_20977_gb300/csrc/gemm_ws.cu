@@ -8,12 +8,10 @@
 // the MMA's A operand (M = 128, one feature per tensor-memory lane), the
 // tokens its B operand (N = TNB).  One CTA per SM walks the tiles
 // blockIdx.x, + grid, ... (feature tile fastest, so CTAs running together
-// share token tiles in L2); where each CTA has three or more tiles and a
-// feature tile's weights fit (<= 96 KB: the single projections of width up
-// to 384), the tiles, feature tile major, are split into equal contiguous
-// ranges instead and a CTA keeps its feature tile's weights resident in
-// shared memory (copied again only where its range crosses into the next
-// feature tile), so only token chunks stream through the ring.
+// share token tiles in L2).  A resident-weight schedule (contiguous
+// feature-major ranges per CTA, the feature tile's weights kept in shared
+// memory) is built in but off (WS_RESIDENT): it measured slower at decode
+// sizes, its first tile starting later.
 // Roles:
 //   warp 0, lane 0     copies (the first resident weights before waiting for
 //                      the previous kernel, then the 64-wide K chunks of

@@ -292,6 +292,8 @@ struct psw_ctx {
     void *Xn = nullptr, *Q = nullptr, *O = nullptr, *Hid = nullptr;
     float *Xa = nullptr, *Xb = nullptr, *Xg = nullptr;   // FP32 residual rows: SM1 / accumulator+SM2 / context
     float *Xc = nullptr;               // Channel Transformer rows, group-major: group g at Xc + g * ws_rows * dg
+    uint8_t *Xn8 = nullptr;            // FP8 contexts: E4M3 token rows streamed to the wide kernel [ws_rows][<= 1024]
+    float *xs8 = nullptr;              // and their dequantisation scales [ws_rows]
     void *NM = nullptr;                // its normalised mixing inputs [Lct][ws_rows][dc] (compute type)
     size_t ws_rows = 0, ws_bytes = 0;
     int ws_gen = 0;
@@ -829,8 +831,10 @@ psw_status ensure_workspace(psw_ctx *c, size_t rows)
     CK_CUDA(c, cudaDeviceSynchronize());
     cudaFree(c->Xn); cudaFree(c->Q); cudaFree(c->O); cudaFree(c->Hid);
     cudaFree(c->Xa); cudaFree(c->Xb); cudaFree(c->Xg); cudaFree(c->Xc); cudaFree(c->NM);
+    cudaFree(c->Xn8); cudaFree(c->xs8);
     c->Xn = c->Q = c->O = c->Hid = c->NM = nullptr;
     c->Xa = c->Xb = c->Xg = c->Xc = nullptr;
+    c->Xn8 = nullptr; c->xs8 = nullptr;
     c->bytes -= c->ws_bytes;
     c->ws_rows = 0; c->ws_bytes = 0;
     size_t bd, bf, bx, bg, bc, bn;
@@ -841,8 +845,11 @@ psw_status ensure_workspace(psw_ctx *c, size_t rows)
         cudaMalloc(&c->Xg, bg) != cudaSuccess || cudaMalloc(&c->Xc, bc) != cudaSuccess ||
         cudaMalloc(&c->NM, bn) != cudaSuccess)
         return fail(c, PSW_ERR_OOM, "workspace of %zu rows", rows);
+    const size_t b8 = c->fp8 ? rows * 1024 : 16, bs8 = c->fp8 ? rows * 4 : 16;
+    if (cudaMalloc(&c->Xn8, b8) != cudaSuccess || cudaMalloc(&c->xs8, bs8) != cudaSuccess)
+        return fail(c, PSW_ERR_OOM, "workspace of %zu rows", rows);
     c->ws_rows = rows;
-    c->ws_bytes = 3 * bd + bf + 2 * bx + bg + bc + bn;
+    c->ws_bytes = 3 * bd + bf + 2 * bx + bg + bc + bn + b8 + bs8;
     c->bytes += c->ws_bytes;
     c->ws_gen++;
     for (auto &kv : c->graphs) graph_free(kv.second);
@@ -938,6 +945,9 @@ struct Pass {
     // (written by the last launch that produced or updated those rows)
     mutable const float *xn_rows = nullptr, *xn_gain = nullptr;
     mutable int xn_m = 0;
+    // FP8: Xn8 / xs8 hold the E4M3 rows of RMSNorm(x8_rows[m]) * x8_gain for m < x8_m
+    mutable const float *x8_rows = nullptr, *x8_gain = nullptr;
+    mutable int x8_m = 0;
 };
 
 // One projection; asrc / a_stream / a_gain say where its token operand
@@ -980,7 +990,30 @@ void gemm_any(const Pass &P, int asrc, const float *xrows, const float *a_gain, 
         }
         g.asrc = asrc = A_DIRECT; g.A = P.c->Xn; g.lda = K;
     }
-    if (writes_rows) P.xn_rows = nullptr;              // the rows change: Xn no longer holds their norm
+    if (g.f8 && M >= WIDE_M && K % 128 == 0 && (asrc == A_NORM ? K <= 512 : asrc == A_DIRECT ? K <= 1024 : false)) {
+        // a wide E4M3 launch: its token rows are quantised once (the bytes
+        // and scales an E4M3 tile would build) and streamed to the tiles
+        GemmArgs t = g;
+        t.asrc = A_DIRECT; t.A = P.c->Xn8; t.lda = K; t.xs = P.c->xs8;
+        if (gemm_takes_ws(P.c->prec, t)) {
+            if (asrc == A_NORM) {
+                if (!(P.x8_rows == xrows && P.x8_gain == a_gain && P.x8_m == M)) {
+                    LAUNCH(P, K_NORM, 0.0, (double)M * K * 5.0,
+                           if (!launch_rows8(A_NORM, xrows, a_gain, nullptr, 0, M, K, P.c->Xn8, P.c->xs8, P.s))
+                               *P.failed = true);
+                    P.x8_rows = xrows; P.x8_gain = a_gain; P.x8_m = M;
+                }
+            } else {
+                LAUNCH(P, K_NORM, 0.0, (double)M * K * 3.0,
+                       if (!launch_rows8(A_DIRECT, nullptr, nullptr, A, lda, M, K, P.c->Xn8, P.c->xs8, P.s))
+                           *P.failed = true);
+                P.x8_rows = nullptr;
+            }
+            g = t;
+            asrc = A_DIRECT;
+        }
+    }
+    if (writes_rows) P.xn_rows = P.x8_rows = nullptr;  // the rows change: Xn / Xn8 no longer hold their norm
     if (!tc && asrc != A_DIRECT) P.c->launches++;      // the operand-preparation kernel
     double es = P.c->prec == P_BF16 ? 2.0 : 4.0, nw = Wt2 ? 2.0 : 1.0, wes = g.f8 ? 1.0 : es;
     double out_b = (e.mode == EPI_RESID || e.mode == EPI_RESID_BASE) ? 8.0 : es;
@@ -1124,7 +1157,7 @@ void hyper_synthesis(const Pass &P, const int *tok, int H, int W_)
     const int nb = hyper_blocks(m), Ch = m.Ch, d = m.d;
     int h = (H + m.r - 1) / m.r, w = (W_ + m.r - 1) / m.r;
     float *x = c->hg[0], *U = c->hg[1], *o = c->hg[2];
-    P.xn_rows = nullptr;
+    P.xn_rows = P.x8_rows = nullptr;
     LAUNCH(P, K_EMBED, 0.0, (double)h * w * Ch * 6.0,
            launch_zhat_grid(P.S, tok, h * w, W(c, c->lay.gamma_z), Ch, x, P.s));
     for (int b = 0; b < nb; b++) {
@@ -1184,7 +1217,7 @@ void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *e
     psw_ctx *c = P.c;
     const psw_model_desc &m = c->md;
     int d = m.d, kk = m.k * m.k;
-    P.xn_rows = nullptr;                               // rows written outside gemm_any follow
+    P.xn_rows = P.x8_rows = nullptr;                   // rows written outside gemm_any follow
     if (m.hp) {
         hyper_synthesis(P, tok, H, W_);
     } else {
@@ -1210,7 +1243,7 @@ void frame_context(const Pass &P, const int *tok, int n)
     LAUNCH(P, K_EMBED, 2.0 * n * m.C * d, n * (m.C * 2.0 + d * 4.0),
            launch_embed_context(P.S, tok, n, m.C, W(c, c->lay.gamma_c), W(c, c->lay.W_c), W(c, c->lay.b_c),
                                 W(c, c->lay.pad), d, c->Xg, P.s));
-    P.xn_rows = nullptr;
+    P.xn_rows = P.x8_rows = nullptr;
     for (int l = 0; l < m.Lc; l++) {
         const BlockOff &bo = c->lay.ctx[l];
         const BlockDev &bd = c->ctxb[l];
@@ -1294,7 +1327,7 @@ void run_ct_group(const Pass &P, const int *tok, int n, int g)
     float *Xg = c->Xc + (size_t)g * c->ws_rows * dg;
     gemm_norm(P, c->Xb, y.ct_g_in, c->ct_win[g], nullptr, n, dg, d, epi_set_bias(tok, Xg, W(c, y.ct_b_in) + g * dg));
     if (g > 0) {
-        P.xn_rows = nullptr;                           // rows written outside gemm_any
+        P.xn_rows = P.x8_rows = nullptr;               // rows written outside gemm_any
         LAUNCH(P, K_EMBED, 2.0 * n * Cg * dg, n * (Cg * 2.0 + dg * 8.0),
                launch_ct_embed(P.S, tok, n, m.C, (g - 1) * Cg, Cg, W(c, y.ct_gamma_y) + (g - 1) * Cg,
                                W(c, y.ct_E) + (long)(g - 1) * Cg * dg, dg, Xg, P.s));
@@ -1340,7 +1373,7 @@ void run_lrp(const Pass &P, const int *tok, int n, const float *rep, float *eps)
     const psw_model_desc &m = c->md;
     const Layout &y = c->lay;
     int d = m.d, kk = m.k * m.k, tmp = m.temporal != 0;
-    P.xn_rows = nullptr;
+    P.xn_rows = P.x8_rows = nullptr;
     gemm_any(P, A_EMBED, nullptr, W(c, y.lrp_gamma_y), nullptr, 0, c->Wy, nullptr, n, d, m.C,
              epi_set_bias(tok, c->Xa, W(c, y.lrp_b_in)));
     gemm_norm(P, rep, y.lrp_g_rep, c->Wrep, nullptr, n, d, m.Nc ? m.dc : d, epi_resid(tok, c->Xa));
@@ -1874,6 +1907,7 @@ void psw_destroy(psw_ctx *c)
     cudaFree(c->rate_buf); cudaFree(c->d_slots); cudaFree(c->d_status); cudaFree(c->d_tok); cudaFree(c->d_kn);
     cudaFree(c->Xn); cudaFree(c->Q); cudaFree(c->O); cudaFree(c->Hid);
     cudaFree(c->Xa); cudaFree(c->Xb); cudaFree(c->Xg); cudaFree(c->Xc); cudaFree(c->NM);
+    cudaFree(c->Xn8); cudaFree(c->xs8);
     for (float *g : c->hg) cudaFree(g);
     cudaFree(c->hcol); cudaFree(c->hz_idx); cudaFree(c->hz_m); cudaFree(c->hz_order); cudaFree(c->hz_status);
     cudaFree(c->hz_rstate); cudaFree(c->hz_rptr); cudaFree(c->hz_rend); cudaFree(c->hz_nw); cudaFree(c->hz_scratch);

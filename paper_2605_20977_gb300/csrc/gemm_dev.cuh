@@ -488,6 +488,84 @@ __device__ __forceinline__ void norm_row_global(const float *__restrict__ x, con
     }
 }
 
+// The E4M3 operand rows of norm_rows8 and quant_rows8 for one row in global
+// memory: the same lane layout and operations (sum of squares, reciprocal
+// square root, gain, absolute maximum, power-of-two scale, conversion), so a
+// row streamed by the wide projection kernel equals, byte for byte, the row
+// a tile builds in shared memory; *xs receives its dequantisation scale.
+template <int CH>
+__device__ __forceinline__ void norm_row8_global(const float *__restrict__ x, const float4 *gh, float invK, int K,
+                                                 uint8_t *__restrict__ dst, float *xs)
+{
+    const int lane = threadIdx.x & 31;
+    float4 v[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        int e = lane * 4 + c * 128;
+        v[c] = e < K ? *(const float4 *)(x + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float ss = 0.0f;
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        ss = fmaf(v[c].x, v[c].x, ss); ss = fmaf(v[c].y, v[c].y, ss);
+        ss = fmaf(v[c].z, v[c].z, ss); ss = fmaf(v[c].w, v[c].w, ss);
+    }
+    ss = warp_sum(ss);
+    const float inv = inv_rms(ss, invK);
+    float amax = 0.0f;
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        int e = lane * 4 + c * 128;
+        if (e >= K) continue;
+        v[c] = make_float4(v[c].x * inv * gh[c].x, v[c].y * inv * gh[c].y, v[c].z * inv * gh[c].z,
+                           v[c].w * inv * gh[c].w);
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[c].x), fabsf(v[c].y)), fmaxf(fabsf(v[c].z), fabsf(v[c].w))));
+    }
+    float qm, sc = row_scale_e4m3(warp_max(amax), &qm);
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        int e = lane * 4 + c * 128;
+        if (e >= K) continue;
+        *(uint32_t *)(dst + e) = e4m3x4(v[c].x * qm, v[c].y * qm, v[c].z * qm, v[c].w * qm);
+    }
+    if (lane == 0) *xs = sc;
+}
+
+template <int CH>
+__device__ __forceinline__ void quant_row8_global(const __nv_bfloat16 *__restrict__ row, int K,
+                                                  uint8_t *__restrict__ dst, float *xs)
+{
+    const int lane = threadIdx.x & 31;
+    uint4 q[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        int e = lane * 8 + c * 256;
+        q[c] = e < K ? *(const uint4 *)(row + e) : make_uint4(0, 0, 0, 0);
+    }
+    float amax = 0.0f;
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&q[c]);
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            float2 f = __bfloat1622float2(h[i]);
+            amax = fmaxf(amax, fmaxf(fabsf(f.x), fabsf(f.y)));
+        }
+    }
+    float qm, sc = row_scale_e4m3(warp_max(amax), &qm);
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        int e = lane * 8 + c * 256;
+        if (e >= K) continue;
+        const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&q[c]);
+        float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
+        float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
+        *(uint2 *)(dst + e) = make_uint2(e4m3x4(f0.x * qm, f0.y * qm, f1.x * qm, f1.y * qm),
+                                         e4m3x4(f2.x * qm, f2.y * qm, f3.x * qm, f3.y * qm));
+    }
+    if (lane == 0) *xs = sc;
+}
+
 // Build the token operand of rows m0 .. m0+63 in shared memory; rows past M
 // are zero.  Warp w builds rows 8w .. 8w+7.  A_NORM: RMSNorm of the FP32 rows
 // xrows[m] times the gain; A_EMBED: the channel-scaled latents of the token

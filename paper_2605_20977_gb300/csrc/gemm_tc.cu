@@ -69,6 +69,30 @@ __global__ void __launch_bounds__(256) k_norm_rows(const float *__restrict__ X, 
     if (m < M) norm_row_global<CH>(X + (long)m * K, gh, invK, K, dst + (long)m * ldd);
 }
 
+// E4M3 streamed rows: one warp per row, 8 rows per block.
+template <int CH>
+__global__ void __launch_bounds__(256) k_rows8_norm(const float *__restrict__ X, const float *__restrict__ gain, int M,
+                                                    int K, uint8_t *__restrict__ dst, float *__restrict__ xs)
+{
+    pdl_trigger();
+    float4 gh[CH];
+    load_gain<CH>(gain, K, gh);
+    const float invK = 1.0f / (float)K;
+    const int m = blockIdx.x * 8 + (threadIdx.x >> 5);
+    pdl_wait();
+    if (m < M) norm_row8_global<CH>(X + (long)m * K, gh, invK, K, dst + (long)m * K, xs + m);
+}
+
+template <int CH>
+__global__ void __launch_bounds__(256) k_rows8_quant(const __nv_bfloat16 *__restrict__ A, int lda, int M, int K,
+                                                     uint8_t *__restrict__ dst, float *__restrict__ xs)
+{
+    pdl_trigger();
+    const int m = blockIdx.x * 8 + (threadIdx.x >> 5);
+    pdl_wait();
+    if (m < M) quant_row8_global<CH>(A + (long)m * lda, K, dst + (long)m * K, xs + m);
+}
+
 // ---------------------------------------------------------------- host side
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -180,6 +204,26 @@ bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst
     dim3 grid((M + 7) / 8), block(256);
     cudaError_t e = K <= 384 ? launch_pdl(k_norm_rows<3>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst, ldd)
                              : launch_pdl(k_norm_rows<4>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst, ldd);
+    return e == cudaSuccess;
+}
+
+bool launch_rows8(int asrc, const float *X, const float *gain, const void *A, int lda, int M, int K, uint8_t *dst,
+                  float *xs, cudaStream_t s)
+{
+    if (M <= 0) return true;
+    if (K % KC8 || ((uintptr_t)dst & 15)) return false;
+    dim3 grid((M + 7) / 8), block(256);
+    cudaError_t e;
+    if (asrc == A_NORM) {
+        if (K > KRES_MAX) return false;
+        e = K <= 384 ? launch_pdl(k_rows8_norm<3>, grid, block, 0, s, X, gain, M, K, dst, xs)
+                     : launch_pdl(k_rows8_norm<4>, grid, block, 0, s, X, gain, M, K, dst, xs);
+    } else {
+        if (K > 1024 || lda % 8) return false;
+        const __nv_bfloat16 *Ab = (const __nv_bfloat16 *)A;
+        e = K <= 512 ? launch_pdl(k_rows8_quant<2>, grid, block, 0, s, Ab, lda, M, K, dst, xs)
+                     : launch_pdl(k_rows8_quant<4>, grid, block, 0, s, Ab, lda, M, K, dst, xs);
+    }
     return e == cudaSuccess;
 }
 

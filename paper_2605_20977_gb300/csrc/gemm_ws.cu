@@ -135,7 +135,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t *r)
 // at parity par; false if that wait expired).  Residual modes read the rows
 // they update while the MMAs still run (all of a thread's values in flight
 // at once); the other modes read the accumulator 32 columns per wait.
-template <bool DUAL, int MODE, int TNB>
+template <bool DUAL, int MODE, int TNB, bool F8>
 __device__ __forceinline__ bool ws_epilogue(const GemmArgs &g, WsShared &S, const uintptr_t *tab, uint64_t *full,
                                             uint32_t par, uint32_t tacc, int f0, int m0, int quarter, int cb,
                                             uint16_t *stg)
@@ -148,6 +148,12 @@ __device__ __forceinline__ bool ws_epilogue(const GemmArgs &g, WsShared &S, cons
     const int f = f0 + quarter * 32 + lane;
     const bool fok = f < N;
     const uint32_t trow = tacc + (uint32_t)cb;
+    // E4M3: the feature row's and each token's dequantisation scales (their
+    // products are powers of two, exact), applied as the one-tile kernel does
+    float wf = 1.0f, wf2 = 1.0f;
+    if constexpr (F8) {
+        if (fok) { wf = g.wsc[f]; if (DUAL) wf2 = g.wsc2[f]; }
+    }
     if constexpr (RESID) {
         static_assert(NC <= 64, "residual tiles keep their old values in registers");
         float old[NC];
@@ -166,8 +172,14 @@ __device__ __forceinline__ bool ws_epilogue(const GemmArgs &g, WsShared &S, cons
             tmem_ld32(trow + 32 * h, v);
             tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 32; j++)
-                if (32 * h + j < nv) rowf[(32 * h + j) * N] = old[32 * h + j] + __uint_as_float(v[j]);
+            for (int j = 0; j < 32; j++) {
+                float y = __uint_as_float(v[j]);
+                if constexpr (F8) {
+                    const int m = m0 + cb + 32 * h + j;
+                    y *= wf * (m < M ? g.xs[m] : 0.0f);
+                }
+                if (32 * h + j < nv) rowf[(32 * h + j) * N] = old[32 * h + j] + y;
+            }
         }
         return true;
     } else {
@@ -192,10 +204,17 @@ __device__ __forceinline__ bool ws_epilogue(const GemmArgs &g, WsShared &S, cons
                 float o[8];
                 int oi[8];
 #pragma unroll
-                for (int j = 0; j < 8; j++)
-                    o[j] = epi_value<MODE, DUAL>(__uint_as_float(v[8 * q + j]),
-                                                 DUAL ? __uint_as_float(v2[(8 * q + j) % (DUAL ? 32 : 1)]) : 0.0f,
-                                                 f, bf, ga, gb, S.stab, &oi[j]);
+                for (int j = 0; j < 8; j++) {
+                    float y = __uint_as_float(v[8 * q + j]);
+                    float y2 = DUAL ? __uint_as_float(v2[(8 * q + j) % (DUAL ? 32 : 1)]) : 0.0f;
+                    if constexpr (F8) {
+                        const int m = m0 + c0 + j;
+                        const float t = m < M ? g.xs[m] : 0.0f;
+                        y *= wf * t;
+                        if (DUAL) y2 *= wf2 * t;
+                    }
+                    o[j] = epi_value<MODE, DUAL>(y, y2, f, bf, ga, gb, S.stab, &oi[j]);
+                }
                 if constexpr (MODE == EPI_HEADS || MODE == EPI_SET_BIAS) {
 #pragma unroll
                     for (int j = 0; j < 8; j++) {
@@ -223,16 +242,18 @@ __device__ __forceinline__ bool ws_epilogue(const GemmArgs &g, WsShared &S, cons
     }
 }
 
-template <bool DUAL, int MODE, int TNB>
+template <bool DUAL, int MODE, int TNB, bool F8>
 __global__ void __launch_bounds__(WS_THREADS, 1)
 k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmW2,
           const __grid_constant__ CUtensorMap tmX, const __grid_constant__ GemmArgs g, int sms, int *status)
 {
     constexpr int NACC = DUAL ? 2 : 1;
+    // a K chunk is one 128-byte swizzle row of both operands: 64 bf16 or 128 E4M3
+    constexpr int KCH = F8 ? KC8 : KC;
     extern __shared__ uint8_t smem_raw[];
     __shared__ WsShared S;
-    const WsGeom q = ws_geom(TNB, DUAL, g.M, g.N, g.K, sms);
-    const int nk = g.K / KC;
+    const WsGeom q = ws_geom(TNB, DUAL, g.M, g.N, F8 ? g.K / 2 : g.K, sms);   // the ring's geometry in bytes
+    const int nk = g.K / KCH;
     uint8_t *wbuf = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *ring = wbuf + (q.wres ? q.wchunk * nk : 0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -273,8 +294,8 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
             auto load_weights = [&](int fi) {
                 mbar_expect_tx(&S.wbar, (uint32_t)(q.wchunk * nk));
                 for (int j = 0; j < nk; j++) {
-                    tma_load(wbuf + j * q.wchunk, &tmW, &S.wbar, j * KC, fi * TM);
-                    if (DUAL) tma_load(wbuf + j * q.wchunk + A_BYTES, &tmW2, &S.wbar, j * KC, fi * TM);
+                    tma_load(wbuf + j * q.wchunk, &tmW, &S.wbar, j * KCH, fi * TM);
+                    if (DUAL) tma_load(wbuf + j * q.wchunk + A_BYTES, &tmW2, &S.wbar, j * KCH, fi * TM);
                 }
             };
             int cur_f = -1, nload = 0;
@@ -291,8 +312,8 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
             for (int j = 0; j < pre; j++) {
                 uint8_t *st = ring + j * q.stage;
                 mbar_expect_tx(&S.full[j], (uint32_t)q.stage);
-                tma_load(st + q.xchunk, &tmW, &S.full[j], j * KC, tile_f(tb) * TM);
-                if (DUAL) tma_load(st + q.xchunk + A_BYTES, &tmW2, &S.full[j], j * KC, tile_f(tb) * TM);
+                tma_load(st + q.xchunk, &tmW, &S.full[j], j * KCH, tile_f(tb) * TM);
+                if (DUAL) tma_load(st + q.xchunk + A_BYTES, &tmW2, &S.full[j], j * KCH, tile_f(tb) * TM);
             }
             pdl_wait();                                    // the token rows are the previous kernel's output
             fence_proxy_global();
@@ -312,15 +333,15 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
                     const int s = it % q.nst, u = it / q.nst;
                     uint8_t *st = ring + s * q.stage;
                     if (it < pre) {                          // its weights already on the way
-                        tma_load(st, &tmX, &S.full[s], j * KC, m0);
+                        tma_load(st, &tmX, &S.full[s], j * KCH, m0);
                         continue;
                     }
                     if (u > 0 && !mbar_wait(&S.empty[s], (u - 1) & 1)) { S.abort = 1; break; }
                     mbar_expect_tx(&S.full[s], (uint32_t)q.stage);
-                    tma_load(st, &tmX, &S.full[s], j * KC, m0);
+                    tma_load(st, &tmX, &S.full[s], j * KCH, m0);
                     if (!q.wres) {
-                        tma_load(st + q.xchunk, &tmW, &S.full[s], j * KC, f0);
-                        if (DUAL) tma_load(st + q.xchunk + A_BYTES, &tmW2, &S.full[s], j * KC, f0);
+                        tma_load(st + q.xchunk, &tmW, &S.full[s], j * KCH, f0);
+                        if (DUAL) tma_load(st + q.xchunk + A_BYTES, &tmW2, &S.full[s], j * KCH, f0);
                     }
                 }
             }
@@ -331,7 +352,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
         }
     } else if (warp == 1 || (DUAL && warp == 2)) {
         if (lane == 0) {
-            const uint32_t id = idesc_bf16(TM, TNB);
+            const uint32_t id = F8 ? idesc_e4m3(TM, TNB) : idesc_bf16(TM, TNB);
             const uint32_t woff = warp == 2 ? (uint32_t)A_BYTES : 0u;
             int it = 0, i = 0, cur_f = -1, nuse = 0;
             for (int t = tb; t < te && !S.abort; t += ts, i++) {
@@ -353,9 +374,12 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
                     fence_after();
                     const uint32_t xb = su32(ring + s * q.stage);
                     const uint32_t wa = (q.wres ? su32(wbuf + j * q.wchunk) : xb + q.xchunk) + woff;
+                    // four K steps of 32 bytes along the 128-byte rows (16 bf16 or 32 E4M3 each)
 #pragma unroll
-                    for (int k = 0; k < 4; k++)
-                        mma(acc, sdesc(wa + k * 32), sdesc(xb + k * 32), id, (j | k) != 0);
+                    for (int k = 0; k < 4; k++) {
+                        if constexpr (F8) mma8(acc, sdesc(wa + k * 32), sdesc(xb + k * 32), id, (j | k) != 0);
+                        else mma(acc, sdesc(wa + k * 32), sdesc(xb + k * 32), id, (j | k) != 0);
+                    }
                     mma_commit(&S.empty[s]);
                 }
                 mma_commit(&S.tfull[b]);
@@ -386,7 +410,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
         for (int t = tb; t < te && !S.abort; t += ts, i++) {
             const int b = i & 1, ub = i >> 1;
             bool ok = !ws_needs_table(MODE) || mbar_wait(&S.tabfull[b], ub & 1);
-            ok = ok && ws_epilogue<DUAL, MODE, TNB>(g, S, S.tab[b], &S.tfull[b], ub & 1,
+            ok = ok && ws_epilogue<DUAL, MODE, TNB, F8>(g, S, S.tab[b], &S.tfull[b], ub & 1,
                                                     tmem + lanes + (uint32_t)(b * NACC * TNB), tile_f(t) * TM,
                                                     tile_m(t) * TNB, quarter, cb, stg);
             if (!ok) S.abort = 1;
@@ -413,17 +437,25 @@ __host__ __device__ constexpr int ws_max_tn(bool dual, int mode)
     return (dual || mode == EPI_RESID || mode == EPI_RESID_BASE) ? 128 : 256;
 }
 
-template <bool DUAL, int MODE, int TNB>
+template <bool DUAL, int MODE, int TNB, bool F8>
 bool ws_attr()
 {
-    return cudaFuncSetAttribute(k_gemm_ws<DUAL, MODE, TNB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_gemm_ws<DUAL, MODE, TNB, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 WS_DYN + WS_EPI_WARPS * WS_STG + 1024) == cudaSuccess;
 }
 
-template <bool DUAL, int MODE>
+template <bool DUAL, int MODE, bool F8 = false>
 bool ws_attr_all()
 {
-    return ws_attr<DUAL, MODE, 64>() && ws_attr<DUAL, MODE, 128>() && ws_attr<DUAL, MODE, ws_max_tn(DUAL, MODE)>();
+    return ws_attr<DUAL, MODE, 64, F8>() && ws_attr<DUAL, MODE, 128, F8>() &&
+           ws_attr<DUAL, MODE, ws_max_tn(DUAL, MODE), F8>();
+}
+
+// Modes whose E4M3 projections take the wide kernel (the transformer
+// blocks' projections; the embedding and heads stay BF16).
+__host__ __device__ constexpr bool ws_f8_mode(int mode)
+{
+    return mode == EPI_STORE || mode == EPI_QKV || mode == EPI_RESID || mode == EPI_RESID_BASE || mode == EPI_SWIGLU;
 }
 
 int ws_sms()
@@ -438,24 +470,25 @@ int ws_sms()
     return n;
 }
 
-template <bool DUAL, int MODE, int TNB>
+template <bool DUAL, int MODE, int TNB, bool F8>
 cudaError_t ws_launch(const CUtensorMap &tw, const CUtensorMap &tw2, const CUtensorMap &tx, const GemmArgs &g,
                       cudaStream_t s)
 {
     const int sms = ws_sms();
-    const WsGeom q = ws_geom(TNB, DUAL, g.M, g.N, g.K, sms);
+    const int kb = F8 ? g.K / 2 : g.K;                 // the bf16 width of the same bytes (ring geometry)
+    const WsGeom q = ws_geom(TNB, DUAL, g.M, g.N, kb, sms);
     dim3 grid(q.grid), block(WS_THREADS);
-    return launch_pdl(k_gemm_ws<DUAL, MODE, TNB>, grid, block, (size_t)ws_smem_bytes(q, g.K), s, tw, tw2, tx, g, sms,
-                      g.status);
+    return launch_pdl(k_gemm_ws<DUAL, MODE, TNB, F8>, grid, block, (size_t)ws_smem_bytes(q, kb), s, tw, tw2, tx, g,
+                      sms, g.status);
 }
 
-template <bool DUAL, int MODE>
+template <bool DUAL, int MODE, bool F8 = false>
 cudaError_t ws_launch_tn(int tnb, const CUtensorMap &tw, const CUtensorMap &tw2, const CUtensorMap &tx,
                          const GemmArgs &g, cudaStream_t s)
 {
-    if (tnb == 64) return ws_launch<DUAL, MODE, 64>(tw, tw2, tx, g, s);
-    if (tnb == 128) return ws_launch<DUAL, MODE, 128>(tw, tw2, tx, g, s);
-    return ws_launch<DUAL, MODE, ws_max_tn(DUAL, MODE)>(tw, tw2, tx, g, s);
+    if (tnb == 64) return ws_launch<DUAL, MODE, 64, F8>(tw, tw2, tx, g, s);
+    if (tnb == 128) return ws_launch<DUAL, MODE, 128, F8>(tw, tw2, tx, g, s);
+    return ws_launch<DUAL, MODE, ws_max_tn(DUAL, MODE), F8>(tw, tw2, tx, g, s);
 }
 
 }  // namespace
@@ -464,7 +497,10 @@ bool gemm_ws_prepare()
 {
     return ws_attr_all<false, EPI_STORE>() && ws_attr_all<false, EPI_QKV>() && ws_attr_all<false, EPI_RESID>() &&
            ws_attr_all<false, EPI_RESID_BASE>() && ws_attr_all<false, EPI_BIAS_SILU>() &&
-           ws_attr_all<false, EPI_HEADS>() && ws_attr_all<true, EPI_SWIGLU>();
+           ws_attr_all<false, EPI_HEADS>() && ws_attr_all<true, EPI_SWIGLU>() &&
+           ws_attr_all<false, EPI_STORE, true>() && ws_attr_all<false, EPI_QKV, true>() &&
+           ws_attr_all<false, EPI_RESID, true>() && ws_attr_all<false, EPI_RESID_BASE, true>() &&
+           ws_attr_all<true, EPI_SWIGLU, true>();
 }
 
 bool gemm_takes_ws(int prec, const GemmArgs &g)
@@ -480,7 +516,8 @@ bool gemm_ws_supported(const GemmArgs &g)
     if (m == EPI_STORE && g.epi.st_sel == CS_NONE && g.epi.ld_out % 8) return false;
     if ((m == EPI_STORE || m == EPI_QKV) && g.epi.d % 8) return false;
     if ((m == EPI_SWIGLU || m == EPI_BIAS_SILU) && g.epi.ld_out % 8) return false;
-    return !g.f8 && g.asrc == A_DIRECT && g.K % KC == 0 && g.K >= KC && g.N >= 32 && g.N % 32 == 0 &&
+    if (g.f8 && (!ws_f8_mode(m) || !g.xs || !g.wsc || (m == EPI_SWIGLU && !g.wsc2) || g.K % KC8)) return false;
+    return g.asrc == A_DIRECT && g.K % KC == 0 && g.K >= KC && g.N >= 32 && g.N % 32 == 0 &&
            g.lda % 8 == 0 &&
            (m == EPI_STORE || m == EPI_QKV || m == EPI_RESID || m == EPI_RESID_BASE || m == EPI_BIAS_SILU ||
             m == EPI_HEADS || m == EPI_SWIGLU);
@@ -510,15 +547,28 @@ int gemm_ws_tile_tokens(int N, int M, int K, bool dual, bool resid)
 bool gemm_ws(const GemmArgs &g, cudaStream_t s)
 {
     if (!gemm_ws_supported(g)) return false;
-    const bool dual = g.epi.mode == EPI_SWIGLU;
-    int tnb = gemm_ws_tile_tokens(g.N, g.M, g.K, dual, g.epi.mode == EPI_RESID || g.epi.mode == EPI_RESID_BASE);
+    const bool dual = g.epi.mode == EPI_SWIGLU, f8 = g.f8 != 0;
+    // an E4M3 projection has half the MMAs of a BF16 one of the same K
+    int tnb = gemm_ws_tile_tokens(g.N, g.M, f8 ? g.K / 2 : g.K, dual,
+                                  g.epi.mode == EPI_RESID || g.epi.mode == EPI_RESID_BASE);
     if (g.tnb == 64 || g.tnb == 128 || g.tnb == 256) tnb = std::min(g.tnb, ws_max_tn(dual, g.epi.mode));
     CUtensorMap tw, tw2, tx;
-    if (!gemm_tensor_map(g.Wt, g.N, g.K, g.K, TM, &tw)) return false;
-    if (dual && !gemm_tensor_map(g.Wt2, g.N, g.K, g.K, TM, &tw2)) return false;
+    if (!gemm_tensor_map(g.Wt, g.N, g.K, g.K, TM, &tw, f8)) return false;
+    if (dual && !gemm_tensor_map(g.Wt2, g.N, g.K, g.K, TM, &tw2, f8)) return false;
     if (!dual) tw2 = tw;
-    if (!gemm_tensor_map(g.A, g.M, g.K, g.lda, tnb, &tx)) return false;
+    if (!gemm_tensor_map(g.A, g.M, g.K, g.lda, tnb, &tx, f8)) return false;
     cudaError_t e;
+    if (f8) {
+        switch (g.epi.mode) {
+        case EPI_SWIGLU: e = ws_launch_tn<true, EPI_SWIGLU, true>(tnb, tw, tw2, tx, g, s); break;
+        case EPI_STORE: e = ws_launch_tn<false, EPI_STORE, true>(tnb, tw, tw2, tx, g, s); break;
+        case EPI_QKV: e = ws_launch_tn<false, EPI_QKV, true>(tnb, tw, tw2, tx, g, s); break;
+        case EPI_RESID: e = ws_launch_tn<false, EPI_RESID, true>(tnb, tw, tw2, tx, g, s); break;
+        case EPI_RESID_BASE: e = ws_launch_tn<false, EPI_RESID_BASE, true>(tnb, tw, tw2, tx, g, s); break;
+        default: return false;
+        }
+        return e == cudaSuccess;
+    }
     switch (g.epi.mode) {
     case EPI_SWIGLU: e = ws_launch_tn<true, EPI_SWIGLU>(tnb, tw, tw2, tx, g, s); break;
     case EPI_STORE: e = ws_launch_tn<false, EPI_STORE>(tnb, tw, tw2, tx, g, s); break;

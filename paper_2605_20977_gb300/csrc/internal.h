@@ -140,6 +140,8 @@ struct GemmArgs {
     int *status;                  // device status word (ST_TIMEOUT from bounded waits)
     int tnb;                      // wide kernel's tokens per tile (0: its cost model; else 64, 128 or 256,
                                   //    capped at the largest its epilogue takes)
+    const float *xs;              // f8 with streamed E4M3 rows (A_DIRECT, wide kernel): each row's
+                                  //    dequantisation scale
 };
 
 // Enqueue one GEMM.  BF16 projections whose N and K tile evenly run on the
@@ -155,6 +157,12 @@ bool gemm(int prec, const GemmArgs &g, cudaStream_t s);
 // normalised token operand of a projection whose tiles then stream it
 // (A_DIRECT), bit-identical to the operand an A_NORM tile builds.
 bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst, cudaStream_t s, int ldd = 0);
+// E4M3 token rows dst[m][k] (bytes) and their dequantisation scales xs[m]
+// for m < M: of RMSNorm(X[m]) * gain (asrc A_NORM, K <= 512) or of the bf16
+// rows A[m][lda] (A_DIRECT, K <= 1024), K a multiple of 128; byte-identical
+// to the operand an E4M3 tile builds in shared memory.
+bool launch_rows8(int asrc, const float *X, const float *gain, const void *A, int lda, int M, int K, uint8_t *dst,
+                  float *xs, cudaStream_t s);
 // The persistent warp-specialised kernel for launches with many token tiles
 // (gemm_ws.cu): BF16, a streamed token operand (A_DIRECT), the epilogues of
 // block projections and heads; bit-identical to the one-tile-per-CTA kernel.

@@ -183,7 +183,8 @@ size_t psw_seq_bytes(const psw_ctx *ctx, int max_H, int max_W);
  * frames).  Frames must be coded in order; psw_encode_params and
  * psw_decode_frame advance it identically.  psw_seq_reset starts a new
  * sequence (the next frame is frame 0, whose temporal context is the learned
- * padding vector). */
+ * padding vector).  max_H and max_W are 1..4096 with max_H * max_W < 2^23
+ * (PSW_ERR_INVALID otherwise). */
 psw_status psw_seq_create(psw_ctx *ctx, int max_H, int max_W, psw_seq **out);
 psw_status psw_seq_reset(psw_seq *seq);
 void psw_seq_destroy(psw_seq *seq);
@@ -228,7 +229,7 @@ psw_status psw_decode_frame(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd
                             int16_t *yhat_out_dev, float *mu_dev, float *sigma_dev, void *stream);
 
 /* Batched decode: n frames of n different sequences (any mix of grids and
- * schedules up to each sequence's maximum, 1 <= n <= 256) decoded together:
+ * schedules up to each sequence's maximum, 1 <= n <= 512) decoded together:
  * step t of every frame runs in global step t, so each launch carries the
  * positions of all frames (Sec. 3.2 parallelism across frames as well as
  * along a wavefront).  Arrays have n entries; mu_dev / sigma_dev may be NULL

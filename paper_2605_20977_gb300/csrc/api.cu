@@ -1925,7 +1925,7 @@ psw_status psw_seq_create(psw_ctx *c, int max_H, int max_W, psw_seq **out)
 {
     if (!c || !out) return fail(c, PSW_ERR_INVALID, "null argument");
     *out = nullptr;
-    if (max_H < 1 || max_W < 1 || max_H > 4096 || max_W > 4096 || (long)max_H * max_W > (1L << 24))
+    if (max_H < 1 || max_W < 1 || max_H > 4096 || max_W > 4096 || (long)max_H * max_W >= (1L << POS_BITS))
         return fail(c, PSW_ERR_INVALID, "bad maximum grid %dx%d", max_H, max_W);
     size_t need = seq_bytes_for(c->md, c->prec, max_H, max_W);
     size_t ws_more = 0, HW = (size_t)max_H * max_W;

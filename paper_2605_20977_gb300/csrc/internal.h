@@ -20,12 +20,13 @@ constexpr int NSCALES = 64;
 constexpr int CDF_PREC = 16;
 constexpr int MAX_KK = 81;        // largest window (9 x 9)
 constexpr int MAX_TF = 4;         // frames in a temporal window
-constexpr int MAX_SLOTS = 256;    // frames in one batch (token word: slot << 24 | position)
+constexpr int MAX_SLOTS = 512;    // frames in one batch (token word: slot << 23 | position)
+constexpr int POS_BITS = 23;      // raster positions per frame: below 2^23
 constexpr int WIDE_M = 1024;      // tokens from which a projection takes the persistent tensor-core kernel
 
 // One frame in flight.  A device-resident table of these lets one launch
 // serve tokens of several frames (of different sequences and grids): a token
-// is the word (slot << 24) | raster position.  Caches are [layer][stride][d]
+// is the word (slot << 23) | raster position.  Caches are [layer][stride][d]
 // in the compute type; the hyperprior tokens eh are FP32 [stride][d]; stride
 // is the sequence's maximum H*W.  (Residual streams are not per-position
 // state: a position's stream lives only while its step runs, in compact
@@ -51,9 +52,9 @@ struct Slot {
     int *status;
 };
 
-__host__ __device__ inline int tok_slot(int t) { return (int)((unsigned)t >> 24); }
-__host__ __device__ inline int tok_pos(int t) { return t & 0xFFFFFF; }
-__host__ __device__ inline int tok_make(int slot, int pos) { return (int)(((unsigned)slot << 24) | (unsigned)pos); }
+__host__ __device__ inline int tok_slot(int t) { return (int)((unsigned)t >> POS_BITS); }
+__host__ __device__ inline int tok_pos(int t) { return t & ((1 << POS_BITS) - 1); }
+__host__ __device__ inline int tok_make(int slot, int pos) { return (int)(((unsigned)slot << POS_BITS) | (unsigned)pos); }
 
 // Caches a kernel can name.
 enum CacheSel { CS_NONE = -1, CS_K1 = 0, CS_V1, CS_K2, CS_V2, CS_KA, CS_VA, CS_QA, CS_CK, CS_CV, CS_XK, CS_XV,

@@ -307,6 +307,33 @@ def test_wide_batch_1080p_lean_tiles(precision):
     _check_same(alone, [batched[k] for k in pick], [items[k] for k in pick])
 
 
+def test_largest_batch_512_frames():
+    """512 frames in one call (the largest batch; slots 256-511 set the top
+    bit of the token word): 8 x 120 crops of the 1080p model, BF16.  Every
+    frame decodes losslessly, frames in both halves of the slot range equal
+    the same frames decoded alone, and a 513-frame batch is refused."""
+    cfg = synth.config("i1080").with_grid(8, 120)
+    ctx = psw.Context(synth.config("i1080"), synth.weights(synth.config("i1080")), precision=psw.PSW_BF16)
+    B = 512
+    four = _encode(ctx, cfg, synth.frames(cfg, 4, seed=2110), 0)
+    items = [four[b % 4] for b in range(B)]
+    fds = [psw.frame_desc(cfg.H, cfg.W, 0)] * B
+    batched, seqs = _batched(ctx, cfg, items, fds)
+    for (yb, _, _), it in zip(batched, items):
+        assert np.array_equal(yb, it[3])
+    pick = [0, 255, 256, 511]
+    alone = _alone(ctx, cfg, [items[k] for k in pick], [fds[k] for k in pick])
+    _check_same(alone, [batched[k] for k in pick], [items[k] for k in pick])
+    extra = ctx.seq_create(cfg.H, cfg.W)
+    outs = [_alloc(cfg.H, cfg.W, cfg.C) for _ in range(B + 1)]
+    with pytest.raises(psw.PswError):
+        ctx.decode_batch(seqs + [extra], fds + [fds[0]], [it[0] for it in items] + [items[0][0]],
+                         [it[1] for it in items] + [items[0][1]], [it[2] for it in items] + [items[0][2]],
+                         [o[0] for o in outs])
+    for s in seqs + [extra]:
+        s.close()
+
+
 def test_bounded_wait_expires_and_the_context_stays_usable():
     """The persistent decoder's grid-barrier wait, on a barrier no block
     arrives at, expires after its limit and reports PSW_ERR_TIMEOUT through

@@ -64,6 +64,21 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// (c0, c1) = (a0 b0 + c0, a1 b1 + c1): two independent fused multiply-adds,
+// each rounded to nearest even as fmaf, in one packed instruction.
+__device__ __forceinline__ void fma2(float &c0, float &c1, float a0, float a1, float b0, float b1)
+{
+    asm("{\n\t.reg .b64 pa, pb, pc;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%0, %1};\n\t"
+        "fma.rn.f32x2 pc, pa, pb, pc;\n\tmov.b64 {%0, %1}, pc;\n\t}"
+        : "+f"(c0), "+f"(c1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
+// The two bf16 of a packed word as floats (exact: the bits move into place).
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
 // Shared staging of one attention warp: CK key rows (the 16-byte pieces of
 // row r stored in the order piece ^ (r & SWM), so that 16-byte reads of the
 // same piece by consecutive lanes hit distinct banks without padding) and CK
@@ -106,6 +121,12 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
     constexpr int RB = AttnWarp<T, DH, CK, MAXC>::RB, SWM = AttnWarp<T, DH, CK, MAXC>::SWM;
     constexpr int PR = RB / 16;                                // 16-byte pieces per row slice
     constexpr int EPU = 16 / (int)sizeof(T);                   // elements per piece
+    // 64-wide BF16 heads: each lane copies piece lane % 8 of rows lane / 8,
+    // + 4, ...; a key's score sums its even and its odd dimensions in two
+    // FP32 chains (packed pair FMAs) added at the end; values accumulate two
+    // dimensions per lane with packed pair FMAs (the same roundings as two
+    // fmaf)
+    constexpr bool PAIR = sizeof(T) == 2 && DH == 64;
     using VRaw = typename RawT<PER * (int)sizeof(T)>::type;
     const int lane = threadIdx.x & 31;
     const int tokn = gw / a.nh, h = gw % a.nh;
@@ -157,12 +178,28 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
     for (int i = 0; i < PER; i++) o[i] = 0.0f;
     for (int base = 0; base < cnt; base += CK) {
         const int nc = min(CK, cnt - base);
-        for (int x = lane; x < nc * PR; x += 32) {
-            int r = x / PR, u = x - r * PR;
-            long off = (long)sm.rows[base + r] * rsb + u * 16;
-            cp_async16(kb + r * RB + ((u ^ (r & SWM)) << 4), Kb + off);
-            cp_async16(vb + r * RB + u * 16, Vb + off);
+        if constexpr (PAIR) {
+            static_assert(PR == 8 && CK % 4 == 0, "64-wide bf16 rows: 8 pieces, 4 rows per pass");
+            const int u = lane & 7;
+#pragma unroll
+            for (int i = 0; i < CK / 4; i++) {
+                const int r = (lane >> 3) + 4 * i;
+                if (r < nc) {
+                    const long off = (long)sm.rows[base + r] * rsb + u * 16;
+                    cp_async16(kb + r * RB + ((u ^ (r & SWM)) << 4), Kb + off);
+                    cp_async16(vb + r * RB + u * 16, Vb + off);
+                }
+            }
+        } else {
+            for (int x = lane; x < nc * PR; x += 32) {
+                int r = x / PR, u = x - r * PR;
+                long off = (long)sm.rows[base + r] * rsb + u * 16;
+                cp_async16(kb + r * RB + ((u ^ (r & SWM)) << 4), Kb + off);
+                cp_async16(vb + r * RB + u * 16, Vb + off);
+            }
         }
+        // key lane's relative bias, loaded while the copies are in flight
+        const float bz = lane < nc ? bias[sm.bix[base + lane]] : 0.0f;
         cp_async_wait_all();
         __syncwarp();
         if (!qready) {
@@ -175,14 +212,29 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
             const uint4 *kr = reinterpret_cast<const uint4 *>(kb + lane * RB);
             const int sw = lane & SWM;
             float acc = 0.0f;
+            if constexpr (PAIR) {
+                const float4 *q4 = reinterpret_cast<const float4 *>(sm.qs);
+                float ae = 0.0f, ao = 0.0f;                    // even and odd dimensions
 #pragma unroll
-            for (int u = 0; u < PR; u++) {
-                float kv[EPU];
-                unpack<T, EPU>(kr[u ^ sw], kv);
+                for (int u = 0; u < PR; u++) {
+                    const uint4 w = kr[u ^ sw];
+                    const float4 qa = q4[2 * u], qb = q4[2 * u + 1];
+                    fma2(ae, ao, qa.x, qa.y, bf_lo(w.x), bf_hi(w.x));
+                    fma2(ae, ao, qa.z, qa.w, bf_lo(w.y), bf_hi(w.y));
+                    fma2(ae, ao, qb.x, qb.y, bf_lo(w.z), bf_hi(w.z));
+                    fma2(ae, ao, qb.z, qb.w, bf_lo(w.w), bf_hi(w.w));
+                }
+                acc = ae + ao;
+            } else {
 #pragma unroll
-                for (int i = 0; i < EPU; i++) acc = fmaf(sm.qs[u * EPU + i], kv[i], acc);
+                for (int u = 0; u < PR; u++) {
+                    float kv[EPU];
+                    unpack<T, EPU>(kr[u ^ sw], kv);
+#pragma unroll
+                    for (int i = 0; i < EPU; i++) acc = fmaf(sm.qs[u * EPU + i], kv[i], acc);
+                }
             }
-            sc = acc * scale + bias[sm.bix[base + lane]];
+            sc = acc * scale + bz;
         }
         const float mnew = fmaxf(mx, warp_max(sc));
         const float corr = expf(mx - mnew);
@@ -191,12 +243,22 @@ __device__ __forceinline__ void attn_item(const AttnArgs &a, int gw, AttnWarp<T,
 #pragma unroll
         for (int i = 0; i < PER; i++) o[i] *= corr;
         const VRaw *vr = reinterpret_cast<const VRaw *>(vb) + lane;
-        for (int u = 0; u < nc; u++) {
-            float pu = __shfl_sync(0xffffffffu, e, u);
-            float vv[PER];
-            unpack<T, PER>(vr[u * 32], vv);
+        if constexpr (PAIR) {
 #pragma unroll
-            for (int i = 0; i < PER; i++) o[i] = fmaf(pu, vv[i], o[i]);
+            for (int u = 0; u < CK; u++) {
+                if (u >= nc) break;                            // the same for the whole warp
+                const float pu = __shfl_sync(0xffffffffu, e, u);
+                const uint32_t wv = vr[u * 32];
+                fma2(o[0], o[1], pu, pu, bf_lo(wv), bf_hi(wv));
+            }
+        } else {
+            for (int u = 0; u < nc; u++) {
+                float pu = __shfl_sync(0xffffffffu, e, u);
+                float vv[PER];
+                unpack<T, PER>(vr[u * 32], vv);
+#pragma unroll
+                for (int i = 0; i < PER; i++) o[i] = fmaf(pu, vv[i], o[i]);
+            }
         }
         mx = mnew;
         __syncwarp();                                  // the next chunk reuses the buffers

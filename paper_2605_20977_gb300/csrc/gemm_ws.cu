@@ -23,12 +23,14 @@
 //   warp 3             resolves each tile's token table (the cache, hyperprior
 //                      or head rows its outputs go to) into one of two
 //                      shared tables, ahead of the epilogue;
-//   warps 4..11        the epilogue: warp w reads the 32 feature rows
+//   warps 4..19        the epilogue: warp w reads the 32 feature rows
 //                      32 (w % 4) .. + 31 of the buffer (lane = feature) and
-//                      half of its token columns and writes the mode's
-//                      outputs (residual rows coalesced along the features,
-//                      bf16 rows through a 512-byte staging buffer per warp
-//                      as 16-byte stores).
+//                      a quarter of its token columns, 16 at a time, and
+//                      writes the mode's outputs (residual rows coalesced
+//                      along the features, bf16 rows through a 512-byte
+//                      staging buffer per warp as 16-byte stores); four
+//                      epilogue warps per scheduler hide each other's
+//                      tensor-memory and store latencies.
 // The token operand is always compact bf16 rows (A_DIRECT; normalised
 // inputs come from launch_norm_rows).  The accumulation order (one
 // accumulator, K ascending) and the per-element epilogue (epi_value,
@@ -50,9 +52,10 @@ using namespace tc;
 
 namespace {
 
-constexpr int WS_THREADS = 384;                       // 12 warps
 constexpr int WS_EPI0 = 4;                            // first epilogue warp
-constexpr int WS_EPI_WARPS = 8;
+constexpr int WS_EPI_WARPS = 16;                      // four per scheduler: one per lane quarter and column group
+constexpr int WS_CGROUPS = WS_EPI_WARPS / 4;          // column groups of a tile (a quarter of its tokens each)
+constexpr int WS_THREADS = 32 * (WS_EPI0 + WS_EPI_WARPS);
 constexpr int WS_TAB = 256;                           // token-table rows (tokens of a tile at most)
 constexpr int WS_MAXST = 8;                           // ring stages at most
 constexpr int WS_STG = 512;                           // epilogue staging of one warp: 32 features x 8 tokens
@@ -116,32 +119,33 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
 
-// 32 consecutive accumulator columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t *r)
+// 16 consecutive accumulator columns at addr (and at addr2 for the dual
+// form) under one wait.
+template <bool DUAL>
+__device__ __forceinline__ void tmem_ld16x(uint32_t addr, uint32_t addr2, uint32_t *v, uint32_t *v2)
 {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(addr));
+    tmem_ld8_async(addr, v);
+    tmem_ld8_async(addr + 8, v + 8);
+    if (DUAL) {
+        tmem_ld8_async(addr2, v2);
+        tmem_ld8_async(addr2 + 8, v2 + 8);
+    }
+    tmem_wait_ld();
 }
 
 // Epilogue of one tile for this warp: feature rows f0 + 32 quarter + lane,
-// token columns cb .. cb + TNB / 2 of the accumulator at tacc (m0: the
-// tile's first token), once the tile's MMAs are complete (the full barrier
-// at parity par; false if that wait expired).  Residual modes read the rows
-// they update while the MMAs still run (all of a thread's values in flight
-// at once); the other modes read the accumulator 32 columns per wait.
+// token columns cb .. cb + TNB / WS_CGROUPS of the accumulator at tacc (m0:
+// the tile's first token), once the tile's MMAs are complete (the full
+// barrier at parity par; false if that wait expired).  Residual modes read
+// the rows they update while the MMAs still run (all of a thread's values in
+// flight at once); every mode reads the accumulator 16 columns per wait.
 template <bool DUAL, int MODE, int TNB, bool F8>
 __device__ __forceinline__ bool ws_epilogue(const GemmArgs &g, WsShared &S, const uintptr_t *tab, uint64_t *full,
                                             uint32_t par, uint32_t tacc, int f0, int m0, int quarter, int cb,
                                             uint16_t *stg)
 {
     constexpr bool RESID = MODE == EPI_RESID || MODE == EPI_RESID_BASE;
-    constexpr int NC = TNB / 2;                               // token columns of this warp
+    constexpr int NC = TNB / WS_CGROUPS;                      // token columns of this warp
     const int lane = threadIdx.x & 31;
     const int M = g.M, N = g.N;
     const Epi &e = g.epi;
@@ -167,18 +171,17 @@ __device__ __forceinline__ bool ws_epilogue(const GemmArgs &g, WsShared &S, cons
         if (S.abort || !mbar_wait(full, par)) return false;
         fence_after();
 #pragma unroll
-        for (int h = 0; h < NC / 32; h++) {
-            uint32_t v[32];
-            tmem_ld32(trow + 32 * h, v);
-            tmem_wait_ld();
+        for (int h = 0; h < NC / 16; h++) {
+            uint32_t v[16], v2[1];
+            tmem_ld16x<false>(trow + 16 * h, 0, v, v2);
 #pragma unroll
-            for (int j = 0; j < 32; j++) {
+            for (int j = 0; j < 16; j++) {
                 float y = __uint_as_float(v[j]);
                 if constexpr (F8) {
-                    const int m = m0 + cb + 32 * h + j;
+                    const int m = m0 + cb + 16 * h + j;
                     y *= wf * (m < M ? g.xs[m] : 0.0f);
                 }
-                if (32 * h + j < nv) rowf[(32 * h + j) * N] = old[32 * h + j] + y;
+                if (16 * h + j < nv) rowf[(16 * h + j) * N] = old[16 * h + j] + y;
             }
         }
         return true;
@@ -192,21 +195,19 @@ __device__ __forceinline__ bool ws_epilogue(const GemmArgs &g, WsShared &S, cons
             gb = (f & 1) ? e.bsg[f >> 1] : e.bmu[f >> 1];
         }
 #pragma unroll 1
-        for (int c32 = 0; c32 < NC; c32 += 32) {
-            uint32_t v[32], v2[DUAL ? 32 : 1];
-            tmem_ld32(trow + c32, v);
-            if constexpr (DUAL) tmem_ld32(trow + TNB + c32, v2);
-            tmem_wait_ld();
-            if (m0 + cb + c32 >= M) continue;                   // the same for the whole warp
+        for (int c16 = 0; c16 < NC; c16 += 16) {
+            uint32_t v[16], v2[DUAL ? 16 : 1];
+            tmem_ld16x<DUAL>(trow + c16, trow + TNB + c16, v, v2);
+            if (m0 + cb + c16 >= M) continue;                   // the same for the whole warp
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int c0 = cb + c32 + 8 * q;                 // tile column of the group's first token
+            for (int q = 0; q < 2; q++) {
+                const int c0 = cb + c16 + 8 * q;                 // tile column of the group's first token
                 float o[8];
                 int oi[8];
 #pragma unroll
                 for (int j = 0; j < 8; j++) {
                     float y = __uint_as_float(v[8 * q + j]);
-                    float y2 = DUAL ? __uint_as_float(v2[(8 * q + j) % (DUAL ? 32 : 1)]) : 0.0f;
+                    float y2 = DUAL ? __uint_as_float(v2[(8 * q + j) % (DUAL ? 16 : 1)]) : 0.0f;
                     if constexpr (F8) {
                         const int m = m0 + c0 + j;
                         const float t = m < M ? g.xs[m] : 0.0f;
@@ -403,7 +404,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
         }
     } else if (warp >= WS_EPI0) {
         pdl_wait();                                        // rows and caches of the previous kernel
-        const int quarter = warp & 3, cb = ((warp - WS_EPI0) >> 2) * (TNB / 2);
+        const int quarter = warp & 3, cb = ((warp - WS_EPI0) >> 2) * (TNB / WS_CGROUPS);
         const uint32_t lanes = (uint32_t)(quarter * 32) << 16;
         uint16_t *stg = (uint16_t *)(ring + q.nst * q.stage + (warp - WS_EPI0) * WS_STG);
         int i = 0;

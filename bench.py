@@ -244,7 +244,8 @@ def run_reference(args, rank: int):
 
 def traffic_for(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if
-    the kernel source is unchanged since it was taken."""
+    the kernel source is unchanged since it was taken (the summary names the
+    launch size it was measured at)."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")     # JSON: per-kernel DRAM bytes from the ncu summaries
     if not os.path.exists(p):
         return None

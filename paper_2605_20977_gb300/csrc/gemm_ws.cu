@@ -114,6 +114,66 @@ __host__ __device__ constexpr bool ws_needs_table(int mode)
     return mode == EPI_QKV || mode == EPI_STORE || mode == EPI_RESID_BASE || mode == EPI_HEADS;
 }
 
+// Byte offset of cache `sel`'s base pointer in a slot record.
+__device__ __forceinline__ int slot_cache_off(int sel)
+{
+    switch (sel) {
+    case CS_K1: return (int)offsetof(Slot, K1);
+    case CS_V1: return (int)offsetof(Slot, V1);
+    case CS_K2: return (int)offsetof(Slot, K2);
+    case CS_V2: return (int)offsetof(Slot, V2);
+    case CS_KA: return (int)offsetof(Slot, Ka);
+    case CS_VA: return (int)offsetof(Slot, Va);
+    case CS_QA: return (int)offsetof(Slot, qa);
+    case CS_CK: return (int)offsetof(Slot, CK);
+    case CS_CV: return (int)offsetof(Slot, CV);
+    case CS_XK: return (int)offsetof(Slot, XK);
+    case CS_LK: return (int)offsetof(Slot, LK);
+    case CS_LV: return (int)offsetof(Slot, LV);
+    default: return (int)offsetof(Slot, XV);
+    }
+}
+
+// The QKV token table rows lane + 32 j (j < PER) of the tile at m0: the
+// key and value cache rows of each token (table_row's values), with the
+// loads of all PER rows in flight together -- the token words, then the
+// slots' stride, cache bases and ring position -- and no branch between
+// them (rows past M read row M - 1 and are written as zero).
+template <int PER>
+__device__ __forceinline__ void qkv_table_rows(const GemmArgs &g, int m0, uintptr_t *tab, int ts)
+{
+    const Epi &e = g.epi;
+    const int lane = threadIdx.x & 31;
+    const int koff = slot_cache_off(e.kc_sel), voff = slot_cache_off(e.vc_sel);
+    int tk[PER];
+#pragma unroll
+    for (int j = 0; j < PER; j++) tk[j] = e.tok[min(m0 + lane + 32 * j, g.M - 1)];
+    const char *sl[PER];
+    int stride[PER], nfr[PER];
+    uintptr_t kb[PER], vb[PER];
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        sl[j] = (const char *)&e.slots[tok_slot(tk[j])];
+        stride[j] = ((const Slot *)sl[j])->stride;
+        nfr[j] = ((const Slot *)sl[j])->nfr;
+        kb[j] = *(const uintptr_t *)(sl[j] + koff);
+        vb[j] = *(const uintptr_t *)(sl[j] + voff);
+    }
+    int layer[PER];
+#pragma unroll
+    for (int j = 0; j < PER; j++)
+        layer[j] = e.ring ? e.kv_layer * e.Tf + ((const Slot *)sl[j])->ring[nfr[j] - 1] : e.kv_layer;
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        const int r = lane + 32 * j;
+        const bool ok = m0 + r < g.M;
+        const long row = ((long)layer[j] * stride[j] + tok_pos(tk[j])) * e.d * (long)sizeof(__nv_bfloat16);
+        tab[r] = ok ? kb[j] + (uintptr_t)row : 0;
+        tab[ts + r] = ok ? vb[j] + (uintptr_t)row : 0;
+        tab[2 * ts + r] = tab[3 * ts + r] = 0;
+    }
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *b)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
@@ -398,7 +458,11 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
             for (int t = tb; t < te && !S.abort; t += ts, i++) {
                 const int b = i & 1, ub = i >> 1;
                 if (ub > 0 && !mbar_wait(&S.tabempty[b], (ub - 1) & 1)) { S.abort = 1; break; }
-                for (int r = lane; r < TNB; r += 32) table_row<MODE>(g, tile_m(t) * TNB, r, S.tab[b], WS_TAB, nullptr);
+                if (MODE == EPI_QKV && g.epi.tok)
+                    qkv_table_rows<TNB / 32>(g, tile_m(t) * TNB, S.tab[b], WS_TAB);
+                else
+                    for (int r = lane; r < TNB; r += 32)
+                        table_row<MODE>(g, tile_m(t) * TNB, r, S.tab[b], WS_TAB, nullptr);
                 mbar_arrive(&S.tabfull[b]);
             }
         }

@@ -6,7 +6,8 @@
 // per launch; at most 128 for the dual SwiGLU form, whose gate and up
 // accumulators are both kept, and for the residual modes): the projection is
 // the MMA's A operand (M = 128, one feature per tensor-memory lane), the
-// tokens its B operand (N = TNB).  One CTA per SM walks the tiles
+// tokens its B operand (N = TNB; a 256-token tile is issued as two N = 128
+// halves by two threads).  One CTA per SM walks the tiles
 // blockIdx.x, + grid, ... (feature tile fastest, so CTAs running together
 // share token tiles in L2).  A resident-weight schedule (contiguous
 // feature-major ranges per CTA, the feature tile's weights kept in shared
@@ -17,7 +18,8 @@
 //                      the previous kernel, then the 64-wide K chunks of
 //                      every tile through a 4..8-stage ring of ~192 KB);
 //   warp 1 (2), lane 0 issues the MMAs, every K step in ascending order into
-//                      one accumulator (the up projection's on warp 2), into
+//                      one accumulator (the up projection's, or the second
+//                      128 tokens' of a 256-token tile, on warp 2), into
 //                      one of two tensor-memory buffers, so a tile's MMAs run
 //                      while the epilogue drains the previous tile;
 //   warp 3             resolves each tile's token table (the cache, hyperprior
@@ -308,7 +310,12 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
 k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmW2,
           const __grid_constant__ CUtensorMap tmX, const __grid_constant__ GemmArgs g, int sms, int *status)
 {
-    constexpr int NACC = DUAL ? 2 : 1;
+    // issuers: the dual form's two (one accumulator each); a 256-token tile
+    // of the single form is also issued by two threads, each into its own
+    // 128 accumulator columns for its 128 tokens (the same weights chunk)
+    constexpr bool SPLIT = !DUAL && TNB == 256;
+    constexpr int NACC = (DUAL || SPLIT) ? 2 : 1;
+    constexpr int BCOLS = DUAL ? 2 * TNB : TNB;             // tensor-memory columns of one buffer
     // a K chunk is one 128-byte swizzle row of both operands: 64 bf16 or 128 E4M3
     constexpr int KCH = F8 ? KC8 : KC;
     extern __shared__ uint8_t smem_raw[];
@@ -411,10 +418,13 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
             for (int k = it > q.nst ? it - q.nst : 0; k < it; k++) mbar_wait(&S.full[k % q.nst], (k / q.nst) & 1);
             if (nload) mbar_wait(&S.wbar, (nload - 1) & 1);
         }
-    } else if (warp == 1 || (DUAL && warp == 2)) {
+    } else if (warp == 1 || (NACC == 2 && warp == 2)) {
         if (lane == 0) {
-            const uint32_t id = F8 ? idesc_e4m3(TM, TNB) : idesc_bf16(TM, TNB);
-            const uint32_t woff = warp == 2 ? (uint32_t)A_BYTES : 0u;
+            constexpr int NI = SPLIT ? TNB / 2 : TNB;             // the MMA's N
+            const uint32_t id = F8 ? idesc_e4m3(TM, NI) : idesc_bf16(TM, NI);
+            const uint32_t woff = DUAL && warp == 2 ? (uint32_t)A_BYTES : 0u;
+            // the second issuer of a split tile: tokens NI.. (rows NI.. of the chunk)
+            const uint32_t xoff = SPLIT && warp == 2 ? (uint32_t)(NI * 128) : 0u;
             int it = 0, i = 0, cur_f = -1, nuse = 0;
             for (int t = tb; t < te && !S.abort; t += ts, i++) {
                 const int b = i & 1, ub = i >> 1, fi = tile_f(t);
@@ -427,14 +437,14 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
                 }
                 if (ub > 0 && !mbar_wait(&S.tempty[b], (ub - 1) & 1)) { S.abort = 1; break; }
                 fence_after();
-                const uint32_t acc = tmem + (uint32_t)(b * NACC * TNB) + (warp == 2 ? (uint32_t)TNB : 0u);
+                const uint32_t acc = tmem + (uint32_t)(b * BCOLS) + (warp == 2 ? (uint32_t)(DUAL ? TNB : NI) : 0u);
                 for (int j = 0; j < nk; j++, it++) {
                     const int s = it % q.nst, u = it / q.nst;
                     if (S.abort) break;
                     if (!mbar_wait(&S.full[s], u & 1)) { S.abort = 1; break; }
                     fence_after();
-                    const uint32_t xb = su32(ring + s * q.stage);
-                    const uint32_t wa = (q.wres ? su32(wbuf + j * q.wchunk) : xb + q.xchunk) + woff;
+                    const uint32_t xs0 = su32(ring + s * q.stage), xb = xs0 + xoff;
+                    const uint32_t wa = (q.wres ? su32(wbuf + j * q.wchunk) : xs0 + q.xchunk) + woff;
                     // four K steps of 32 bytes along the 128-byte rows (16 bf16 or 32 E4M3 each)
 #pragma unroll
                     for (int k = 0; k < 4; k++) {
@@ -476,7 +486,7 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
             const int b = i & 1, ub = i >> 1;
             bool ok = !ws_needs_table(MODE) || mbar_wait(&S.tabfull[b], ub & 1);
             ok = ok && ws_epilogue<DUAL, MODE, TNB, F8>(g, S, S.tab[b], &S.tfull[b], ub & 1,
-                                                    tmem + lanes + (uint32_t)(b * NACC * TNB), tile_f(t) * TM,
+                                                    tmem + lanes + (uint32_t)(b * BCOLS), tile_f(t) * TM,
                                                     tile_m(t) * TNB, quarter, cb, stg);
             if (!ok) S.abort = 1;
             fence_before();
@@ -591,8 +601,11 @@ bool gemm_ws_supported(const GemmArgs &g)
 // Tokens per tile: the width with the least estimated time of the busiest
 // CTA -- its tiles x the slower of a tile's MMAs and epilogue (they overlap
 // across tiles), plus the faster of the two once.  One thread issues an MMA
-// in about the same time for any N up to 128 and in ~1.5x that at N = 256
-// (the tensor pipe's rate); the epilogue grows with the tile's tokens.
+// in about the same time for any N up to 128 (~185 cycles, above the tensor
+// pipe's time for N = 128), so a tile's MMA time is its K chunks whatever
+// its width up to 128; a 256-token tile has two issuers (~1.1x); the
+// epilogue, ~0.86x a 128-token tile's MMA time at K = 384, grows with the
+// tile's tokens (measured with cycle counters on the 1080p projections).
 // Ties go to the wider tile (fewer weight re-reads).
 int gemm_ws_tile_tokens(int N, int M, int K, bool dual, bool resid)
 {
@@ -602,7 +615,7 @@ int gemm_ws_tile_tokens(int N, int M, int K, bool dual, bool resid)
     for (int tnb = ws_max_tn(dual, resid ? EPI_RESID : EPI_STORE); tnb >= 64; tnb /= 2) {
         const WsGeom q = ws_geom(tnb, dual, M, N, K, sms);
         const int tiles = (q.ntiles + q.grid - 1) / q.grid;
-        const double mma = (K / 384.0) * (tnb == 256 ? 1.5 : 1.0), epi = tnb / 128.0;
+        const double mma = (K / 384.0) * (tnb == 256 && !dual ? 1.1 : 1.0), epi = 0.86 * tnb / 128.0;
         const double cost = tiles * (mma > epi ? mma : epi) + (mma < epi ? mma : epi);
         if (cost < best_cost - 1e-9) { best_cost = cost; best = tnb; }
     }

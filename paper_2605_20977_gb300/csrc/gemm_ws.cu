@@ -4,7 +4,7 @@
 //
 // A tile is 128 output features x TNB tokens (TNB = 64, 128 or 256, chosen
 // per launch; at most 128 for the dual SwiGLU form, whose gate and up
-// accumulators are both kept, and for the residual modes): the projection is
+// accumulators are both kept): the projection is
 // the MMA's A operand (M = 128, one feature per tensor-memory lane), the
 // tokens its B operand (N = TNB; a 256-token tile is issued as two N = 128
 // halves by two threads).  One CTA per SM walks the tiles
@@ -222,18 +222,28 @@ __device__ __forceinline__ bool ws_epilogue(const GemmArgs &g, WsShared &S, cons
     }
     if constexpr (RESID) {
         static_assert(NC <= 64, "residual tiles keep their old values in registers");
+        // the rows' old values: the first 32 columns' read while the MMAs
+        // run (16 for a 256-token tile, whose warps hold 64 columns), each
+        // later 16-column chunk's ahead of its use
+        constexpr int PRE = NC <= 32 ? NC : 16;
+        constexpr int AHEAD = NC <= 32 ? 2 : 1;
         float old[NC];
         const int nv = fok ? min(NC, M - (m0 + cb)) : 0;         // this warp's rows m0 + cb + j, j < nv
         float *rowf = e.rows + (long)(m0 + cb) * N + f;          // row j at rowf[j * N]
-#pragma unroll
-        for (int j = 0; j < NC; j++) {
+        auto load_old = [&](int j) {
             const float *src = MODE == EPI_RESID ? rowf + j * N : (const float *)tab[WS_TAB + cb + j] + f;
             old[j] = j < nv ? *src : 0.0f;
-        }
+        };
+#pragma unroll
+        for (int j = 0; j < PRE; j++) load_old(j);
         if (S.abort || !mbar_wait(full, par)) return false;
         fence_after();
 #pragma unroll
         for (int h = 0; h < NC / 16; h++) {
+            if (16 * (h + AHEAD) >= PRE && 16 * (h + AHEAD) < NC) {
+#pragma unroll
+                for (int j = 0; j < 16; j++) load_old(16 * (h + AHEAD) + j);
+            }
             uint32_t v[16], v2[1];
             tmem_ld16x<false>(trow + 16 * h, 0, v, v2);
 #pragma unroll
@@ -506,10 +516,10 @@ k_gemm_ws(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
 }
 
 // Widest tile of a form: 128 tokens for the dual form (two accumulators
-// per buffer) and the residual modes (old values in registers), else 256.
+// per buffer), else 256.
 __host__ __device__ constexpr int ws_max_tn(bool dual, int mode)
 {
-    return (dual || mode == EPI_RESID || mode == EPI_RESID_BASE) ? 128 : 256;
+    return dual ? 128 : 256;
 }
 
 template <bool DUAL, int MODE, int TNB, bool F8>

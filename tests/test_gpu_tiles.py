@@ -1,5 +1,6 @@
 """The wide projection kernel's tile policy (tokens per tile per launch
-class, chosen by the autotuner) changes no value: the encoder's masked pass
+class, chosen by the autotuner; 256-token tiles are issued by two threads)
+changes no value, in BF16 and with E4M3 block projections: the encoder's masked pass
 over a 34 x 120 crop of the 1080p frame (4080 tokens per launch, every
 projection on the wide kernel) gives bit-identical parameters and
 containers under every policy, and a decoder under one policy reproduces an
@@ -27,9 +28,10 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
 
 
-def test_tile_policies_are_bit_identical():
+@pytest.mark.parametrize("precision", [psw.PSW_BF16, psw.PSW_FP8])
+def test_tile_policies_are_bit_identical(precision):
     base = synth.config("i1080")
-    ctx = psw.Context(base, synth.weights(base), precision=psw.PSW_BF16)
+    ctx = psw.Context(base, synth.weights(base), precision=precision)
     cfg = base.with_grid(34, base.W)
     fr = synth.frames(cfg, 1, seed=2401)
     fd = psw.frame_desc(cfg.H, cfg.W, 0)

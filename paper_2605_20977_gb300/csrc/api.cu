@@ -1211,7 +1211,7 @@ void frame_context(const Pass &P, const int *tok, int n);
 // tokens and accumulator queries (they depend only on the hyperlatents,
 // Sec. 3.1), and for the temporal model this frame's Context Transformer
 // pass and every spatial block's cross-attention K/V.
-void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *eh)
+void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *eh, bool embed = true)
 {
     const int n = H * W_;
     psw_ctx *c = P.c;
@@ -1220,7 +1220,7 @@ void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *e
     P.xn_rows = P.x8_rows = nullptr;                   // rows written outside gemm_any follow
     if (m.hp) {
         hyper_synthesis(P, tok, H, W_);
-    } else {
+    } else if (embed) {
         LAUNCH(P, K_EMBED, 2.0 * n * m.Ch * d, n * (m.Ch * 2.0 + d * 4.0),
                launch_embed_hyper(P.S, tok, n, H, W_, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp),
                                   W(c, c->lay.b_hp), d, P.s));
@@ -1548,7 +1548,20 @@ void enqueue_decode(psw_ctx *c, const DecodePlan &D, const int *d_tok, const int
 {
     Pass P{c, s, c->d_slots, failed};
     if (t0 == 0) {
-        for (int b = 0; b < D.n; b++) frame_prologue(P, d_tok + D.pro_off[b], D.pro_h[b], D.pro_w[b], D.eh[b]);
+        // the hyperprior tokens of every frame in one launch (the
+        // convolutional hyperprior's synthesis stays per frame)
+        const bool batch_embed = !c->md.hp && D.n > 1;
+        if (batch_embed) {
+            const int Hm = *std::max_element(D.pro_h.begin(), D.pro_h.end());
+            const int Wm = *std::max_element(D.pro_w.begin(), D.pro_w.end());
+            double npos = 0.0;
+            for (int b = 0; b < D.n; b++) npos += D.pro_n[b];
+            LAUNCH(P, K_EMBED, 2.0 * npos * c->md.Ch * c->md.d, npos * (c->md.Ch * 2.0 + c->md.d * 4.0),
+                   launch_embed_hyper_batch(P.S, D.n, Hm, Wm, c->md.Ch, c->md.r, W(c, c->lay.gamma_z),
+                                            W(c, c->lay.W_hp), W(c, c->lay.b_hp), c->md.d, P.s));
+        }
+        for (int b = 0; b < D.n; b++)
+            frame_prologue(P, d_tok + D.pro_off[b], D.pro_h[b], D.pro_w[b], D.eh[b], !batch_embed);
         Scope sc(c, s, K_RANS, 0.0, (double)D.n * c->md.C * 128.0);
         launch_rans_dec_init(c->d_slots, D.n, c->md.C, s);
     }

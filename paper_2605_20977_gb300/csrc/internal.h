@@ -217,6 +217,11 @@ void launch_embed_context(const Slot *S, const int *tok, int n, int C, const flo
                           const float *b, const float *pad, int d, float *out, cudaStream_t s);
 void launch_embed_hyper(const Slot *S, const int *tok, int n, int H, int W, int Ch, int r, const float *gamma,
                         const float *Whp, const float *b, int d, cudaStream_t s);
+// The same for slots 0 .. nslots - 1 of the table in one launch (each slot's
+// own grid, at most Hmax x Wmax): every element as launch_embed_hyper
+// computes it.
+void launch_embed_hyper_batch(const Slot *S, int nslots, int Hmax, int Wmax, int Ch, int r, const float *gamma,
+                              const float *Whp, const float *b, int d, cudaStream_t s);
 // dst[w * ldd + e] = RMSNorm(X[w]) * g in the compute type (ldd 0: d); the
 // SIMT path's operand.
 void launch_rmsnorm(int prec, const float *X, int n, const float *g, int d, void *dst, cudaStream_t s, int ldd = 0);

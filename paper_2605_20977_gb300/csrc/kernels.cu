@@ -98,17 +98,19 @@ void launch_embed_context(const Slot *S, const int *tok, int n, int C, const flo
 // adds the bias.
 constexpr int EH_NB = 32;
 
-__global__ void __launch_bounds__(384) k_embed_hyper(const Slot *__restrict__ S, const int *__restrict__ tok, int Ch,
-                                                     int r, int nbmax, const float *__restrict__ gamma,
+__global__ void __launch_bounds__(384) k_embed_hyper(const Slot *__restrict__ S, const int *__restrict__ tok, int nz,
+                                                     int Ch, int r, int nbmax, const float *__restrict__ gamma,
                                                      const float *__restrict__ Whp, const float *__restrict__ b, int d)
 {
     extern __shared__ float4 t4[];                    // [Ch][nbmax] floats: gamma * zhat, channel-major
     float *t = reinterpret_cast<float *>(t4);
-    const Slot &s = S[tok_slot(tok[0])];
+    // one frame (tok[0]'s slot), or (nz > 0) slot blockIdx.z / nz of a batch
+    const Slot &s = S[nz > 0 ? (int)(blockIdx.z / nz) : tok_slot(tok[0])];
+    const int zb = nz > 0 ? (int)(blockIdx.z % nz) : (int)blockIdx.z;
     const int H = s.H, W = s.W, Wh = (W + r - 1) / r;
-    const int ti = blockIdx.x / r, tj = blockIdx.x % r, a = blockIdx.y, b0 = blockIdx.z * nbmax;
+    const int ti = blockIdx.x / r, tj = blockIdx.x % r, a = blockIdx.y, b0 = zb * nbmax;
     const int i = a * r + ti;
-    if (i >= H) return;                               // uniform over the block
+    if (i >= H || b0 >= Wh) return;                   // uniform over the block
     const int nb = min(nbmax, Wh - b0);
     for (int x = threadIdx.x; x < nb * Ch; x += blockDim.x) {
         const int k = x / Ch, c = x - k * Ch;
@@ -153,7 +155,21 @@ void launch_embed_hyper(const Slot *S, const int *tok, int n, int H, int W, int 
     const int nbmax = std::max(4, std::min(EH_NB, (12288 / Ch) & ~3));   // staged hyperlatents: <= 64 KB
     const dim3 grid(r * r, Hh, (Wh + nbmax - 1) / nbmax);
     const int threads = d < 384 ? ((d + 31) / 32) * 32 : 384;
-    k_embed_hyper<<<grid, threads, (size_t)nbmax * Ch * sizeof(float), s>>>(S, tok, Ch, r, nbmax, gamma, Whp, b, d);
+    k_embed_hyper<<<grid, threads, (size_t)nbmax * Ch * sizeof(float), s>>>(S, tok, 0, Ch, r, nbmax, gamma, Whp, b,
+                                                                            d);
+}
+
+void launch_embed_hyper_batch(const Slot *S, int nslots, int Hmax, int Wmax, int Ch, int r, const float *gamma,
+                              const float *Whp, const float *b, int d, cudaStream_t s)
+{
+    if (nslots <= 0) return;
+    const int Hh = (Hmax + r - 1) / r, Wh = (Wmax + r - 1) / r;
+    const int nbmax = std::max(4, std::min(EH_NB, (12288 / Ch) & ~3));
+    const int nz = (Wh + nbmax - 1) / nbmax;
+    const dim3 grid(r * r, Hh, nslots * nz);
+    const int threads = d < 384 ? ((d + 31) / 32) * 32 : 384;
+    k_embed_hyper<<<grid, threads, (size_t)nbmax * Ch * sizeof(float), s>>>(S, nullptr, nz, Ch, r, nbmax, gamma, Whp,
+                                                                            b, d);
 }
 
 // ---------------------------------------------------------------- RMSNorm

@@ -279,6 +279,7 @@ struct psw_ctx {
     uint16_t *hz_scratch = nullptr;
     uint64_t *hz_total = nullptr;
     void *Win = nullptr;               // latent embedding [d][C]
+    std::vector<void *> Whp_t;         // tensor-core hyperprior embedding: tap t's [d][Ch] (empty: CUDA-core kernel)
     void *Wh1 = nullptr;               // heads, first layers [W1m; W1s]: [2d][d]
     void *Wh2 = nullptr;               // heads, second layers interleaved: row 2c = mu_c, 2c+1 = sigma_c: [2C][2d]
     float *bh1 = nullptr;              // [b1m; b1s]
@@ -564,6 +565,15 @@ bool prepare_projections(psw_ctx *c, bool dry)
     cudaFree(stage);
     if (!ok) return false;
     void *win = carve(d, m.C); tr(lay.W_in, m.C, d, win, 0);
+    // the hyperprior token embedding as r * r projections (one per sub-pixel
+    // tap) on the tensor cores, where their shape takes them
+    std::vector<void *> whp_t;
+    if (!m.hp && prec == P_BF16 && gemm_tc_supported(P_BF16, d, m.Ch, A_ZHAT))
+        for (int t = 0; t < m.r * m.r; t++) {
+            void *wt = carve(d, m.Ch);
+            tr(lay.W_hp + (long)t * m.Ch * d, m.Ch, d, wt, 0);
+            whp_t.push_back(wt);
+        }
     if (m.Llrp) { wy = carve(d, m.C); tr(lay.lrp_W_y, m.C, d, wy, 0); }
     // the plain heads (the grouped heads of a Channel Transformer replace them)
     void *wh1 = nullptr, *wh2 = nullptr;
@@ -663,6 +673,7 @@ bool prepare_projections(psw_ctx *c, bool dry)
     c->hd_wa = hd_wa; c->hd_wb = hd_wb; c->hd_ws = hd_ws; c->hu_w = hu_w; c->hu_wb = hu_wb;
     c->hd_bias = hd_bias; c->hu_bias = hu_bias;
     c->Win = win; c->Wh1 = wh1; c->Wh2 = wh2; c->bh1 = bh1;
+    c->Whp_t = whp_t;
     return true;
 }
 
@@ -1206,6 +1217,32 @@ void hyper_analysis(const Pass &P, int H, int W_, int16_t *zhat, float *z_out)
 
 void frame_context(const Pass &P, const int *tok, int n);
 
+// Positions of the frame of slot `slot` (H x W, hyperprior r times coarser)
+// grouped by sub-pixel tap t = (i mod r) r + (j mod r), raster order within
+// a tap, appended to the segment of each tap.
+void tap_tokens(int slot, int H, int W_, int r, std::vector<std::vector<int>> &seg)
+{
+    seg.resize((size_t)r * r);
+    for (int i = 0; i < H; i++)
+        for (int j = 0; j < W_; j++) seg[(size_t)(i % r) * r + j % r].push_back(tok_make(slot, i * W_ + j));
+}
+
+// The hyperprior tokens on the tensor cores (Sec. 3.1: the embedded
+// hyperprior; Fig. 1 right): for each tap t, the positions tok[off[t] ..
+// + n[t]) of every frame, eh[p] = W_hp[t]^T (gamma_z * z-hat of p's
+// hyperlatent) + b_hp -- the sub-pixel embedding launch_embed_hyper
+// computes on the CUDA cores, as one projection per tap.
+void hyper_embed_tc(const Pass &P, const int *tok, const std::vector<int> &off, const std::vector<int> &n)
+{
+    psw_ctx *c = P.c;
+    const psw_model_desc &m = c->md;
+    for (size_t t = 0; t < c->Whp_t.size(); t++) {
+        Epi e = epi_set_bias(tok + off[t], nullptr, W(c, c->lay.b_hp));
+        e.eh_out = 1; e.hr = m.r;
+        gemm_any(P, A_ZHAT, nullptr, W(c, c->lay.gamma_z), nullptr, 0, c->Whp_t[t], nullptr, n[t], m.d, m.Ch, e);
+    }
+}
+
 // Per-frame preparation for the tokens tok[0..n) (all positions of one
 // slot, in raster order; eh: that slot's hyperprior rows): hyperprior
 // tokens and accumulator queries (they depend only on the hyperlatents,
@@ -1220,7 +1257,7 @@ void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *e
     P.xn_rows = P.x8_rows = nullptr;                   // rows written outside gemm_any follow
     if (m.hp) {
         hyper_synthesis(P, tok, H, W_);
-    } else if (embed) {
+    } else if (embed && c->Whp_t.empty()) {
         LAUNCH(P, K_EMBED, 2.0 * n * m.Ch * d, n * (m.Ch * 2.0 + d * 4.0),
                launch_embed_hyper(P.S, tok, n, H, W_, m.Ch, m.r, W(c, c->lay.gamma_z), W(c, c->lay.W_hp),
                                   W(c, c->lay.b_hp), d, P.s));
@@ -1507,11 +1544,12 @@ struct DecodePlan {
     int n = 0, Tmax = 0;
     std::vector<const float *> eh;      // each slot's hyperprior rows
     std::vector<int> tok, pro_off, pro_n, pro_h, pro_w, step_off, step_n;
+    std::vector<int> tap_off, tap_n;    // tensor-core hyperprior embedding: each tap's positions of every frame
     std::vector<int2> kn;
     size_t max_step = 0;
 };
 
-DecodePlan plan_decode(const std::vector<psw_seq *> &qs, const psw_frame_desc *fds)
+DecodePlan plan_decode(const std::vector<psw_seq *> &qs, const psw_frame_desc *fds, int r_taps)
 {
     DecodePlan D;
     D.n = (int)qs.size();
@@ -1524,6 +1562,15 @@ DecodePlan plan_decode(const std::vector<psw_seq *> &qs, const psw_frame_desc *f
         D.pro_w.push_back(fds[b].W);
         for (int p = 0; p < HW; p++) D.tok.push_back(tok_make(b, p));
         D.Tmax = std::max(D.Tmax, qs[b]->T);
+    }
+    if (r_taps > 0) {
+        std::vector<std::vector<int>> seg;
+        for (int b = 0; b < D.n; b++) tap_tokens(b, fds[b].H, fds[b].W, r_taps, seg);
+        for (auto &v : seg) {
+            D.tap_off.push_back((int)D.tok.size());
+            D.tap_n.push_back((int)v.size());
+            D.tok.insert(D.tok.end(), v.begin(), v.end());
+        }
     }
     D.kn.assign((size_t)D.Tmax * D.n, make_int2(0, 0));
     for (int t = 0; t < D.Tmax; t++) {
@@ -1548,9 +1595,11 @@ void enqueue_decode(psw_ctx *c, const DecodePlan &D, const int *d_tok, const int
 {
     Pass P{c, s, c->d_slots, failed};
     if (t0 == 0) {
-        // the hyperprior tokens of every frame in one launch (the
-        // convolutional hyperprior's synthesis stays per frame)
-        const bool batch_embed = !c->md.hp && D.n > 1;
+        // the hyperprior tokens of every frame: per tap on the tensor cores,
+        // else in one CUDA-core launch (the convolutional hyperprior's
+        // synthesis stays per frame)
+        const bool batch_embed = !c->md.hp && D.n > 1 && c->Whp_t.empty();
+        if (!c->Whp_t.empty() && !c->md.hp) hyper_embed_tc(P, d_tok, D.tap_off, D.tap_n);
         if (batch_embed) {
             const int Hm = *std::max_element(D.pro_h.begin(), D.pro_h.end());
             const int Wm = *std::max_element(D.pro_w.begin(), D.pro_w.end());
@@ -1656,7 +1705,7 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
     DecodePlan D;
     psw_status st;
     if (!gr) {
-        D = plan_decode(qs, fds);
+        D = plan_decode(qs, fds, c->Whp_t.empty() ? 0 : c->md.r);
         size_t rows = D.max_step;
         for (int b = 0; b < n; b++) rows = std::max(rows, (size_t)D.pro_n[b]);
         if ((st = ensure_workspace(c, rows))) return st;
@@ -2055,7 +2104,8 @@ psw_status psw_encode_params(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, c
     int HW = fd->H * fd->W;
     size_t nsym = (size_t)HW * c->md.C;
     if ((st = ensure_workspace(c, HW))) return st;
-    if ((st = grow_tokens(c, HW, 1))) return st;
+    const bool tc_embed = !c->Whp_t.empty() && !c->md.hp;
+    if ((st = grow_tokens(c, tc_embed ? 2 * (size_t)HW : HW, 1))) return st;
     Slot sl = make_slot(q, fd->H, fd->W, fd->schedule);
     sl.zhat = zhat_dev;
     c->h_slots[0] = sl;
@@ -2063,11 +2113,23 @@ psw_status psw_encode_params(psw_ctx *c, psw_seq *q, const psw_frame_desc *fd, c
     if ((st = upload_slots(c, qs, 1, s))) return st;
     std::vector<int> tok(HW);
     for (int p = 0; p < HW; p++) tok[p] = tok_make(0, p);
-    CK_CUDA(c, cudaMemcpyAsync(c->d_tok, tok.data(), HW * sizeof(int), cudaMemcpyHostToDevice, s));
+    // the tensor-core hyperprior embedding's positions, tap by tap
+    std::vector<int> tap_off, tap_n;
+    if (tc_embed) {
+        std::vector<std::vector<int>> seg;
+        tap_tokens(0, fd->H, fd->W, c->md.r, seg);
+        for (auto &v : seg) {
+            tap_off.push_back((int)tok.size());
+            tap_n.push_back((int)v.size());
+            tok.insert(tok.end(), v.begin(), v.end());
+        }
+    }
+    CK_CUDA(c, cudaMemcpyAsync(c->d_tok, tok.data(), tok.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     CK_CUDA(c, cudaMemcpyAsync(q->y, yhat_dev, nsym * 2, cudaMemcpyDeviceToDevice, s));
     bool failed = false;
     Pass P{c, s, c->d_slots, &failed};
     // masked parallel pass over every position (Sec. 3.1, Sec. 3.2)
+    if (tc_embed) hyper_embed_tc(P, c->d_tok, tap_off, tap_n);
     frame_prologue(P, c->d_tok, fd->H, fd->W, q->eh);
     run_sm1(P, c->d_tok, HW);
     run_acc_sm2_heads(P, c->d_tok, HW);

@@ -568,8 +568,9 @@ __device__ __forceinline__ void quant_row8_global(const __nv_bfloat16 *__restric
 
 // Build the token operand of rows m0 .. m0+63 in shared memory; rows past M
 // are zero.  Warp w builds rows 8w .. 8w+7.  A_NORM: RMSNorm of the FP32 rows
-// xrows[m] times the gain; A_EMBED: the channel-scaled latents of the token
-// (row pointers resolved beforehand into yrow).  All of a warp's loads are in
+// xrows[m] times the gain; A_EMBED / A_ZHAT: the channel-scaled latents of
+// the token, or the z-hat of its hyperlatent (row pointers resolved
+// beforehand into yrow).  All of a warp's loads are in
 // flight together (K <= 384: the eight rows at once; lean tiles, with half
 // the registers, four at a time).  One out-of-line copy serves every
 // projection mode (keeps the instruction footprint small).
@@ -786,9 +787,10 @@ static __device__ __noinline__ void build_tokens8(const GemmArgs &g, int m0, uin
 
 // Per-token addresses a mode needs, resolved once per tile by threads 0..63:
 // cache rows (EPI_STORE into a cache, EPI_QKV), the hyperprior row
-// (EPI_RESID_BASE), the head outputs (EPI_HEADS), the latents (A_EMBED).
-// Entry r of a tile's token table (row m0 + r): tab[k][r * ts] for k < 4
-// (ts: the table's row stride) and, for A_EMBED, the latent row.
+// (EPI_RESID_BASE, EPI_SET_BIAS with eh_out), the head outputs (EPI_HEADS),
+// the latents (A_EMBED) or z-hat (A_ZHAT).  Entry r of a tile's token table
+// (row m0 + r): tab[k][r * ts] for k < 4 (ts: the table's row stride) and,
+// for A_EMBED / A_ZHAT, the operand's source row.
 template <int MODE>
 __device__ __forceinline__ void table_row(const GemmArgs &g, int m0, int r, uintptr_t *tab, int ts,
                                           const int16_t **yrow)
@@ -802,13 +804,17 @@ __device__ __forceinline__ void table_row(const GemmArgs &g, int m0, int r, uint
     const Slot &s = e.slots[tok_slot(tk)];
     int p = tok_pos(tk);
     if (yrow && g.asrc == A_EMBED) yrow[r] = s.y + (long)p * g.K;
+    if (yrow && g.asrc == A_ZHAT) {
+        const int i = p / s.W, j = p - i * s.W, Wh = (s.W + e.hr - 1) / e.hr;
+        yrow[r] = s.zhat + ((long)(i / e.hr) * Wh + j / e.hr) * g.K;
+    }
     if (MODE == EPI_STORE && e.st_sel != CS_NONE) {
         tab[r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.st_sel, e.st_layer, p, e.d);
     } else if (MODE == EPI_QKV) {
         int layer = e.ring ? e.kv_layer * e.Tf + s.ring[s.nfr - 1] : e.kv_layer;
         tab[r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.kc_sel, layer, p, e.d);
         tab[ts + r] = (uintptr_t)cache_row<__nv_bfloat16>(s, e.vc_sel, layer, p, e.d);
-    } else if (MODE == EPI_RESID_BASE) {
+    } else if (MODE == EPI_RESID_BASE || (MODE == EPI_SET_BIAS && e.eh_out)) {
         tab[ts + r] = (uintptr_t)(s.eh + (long)p * g.N);
     } else if (MODE == EPI_HEADS) {
         const long o = (long)p * e.C + e.c0;
@@ -998,6 +1004,8 @@ static __device__ __noinline__ void gemm_epilogue(GemmShared &S, uint8_t *ring, 
                             ((float *)S.tab[0][r])[c] = y;
                             ((int32_t *)S.tab[3][r])[c] = oi[j];
                         }
+                    } else if (e.eh_out) {
+                        ((float *)S.tab[1][r])[f] = y;
                     } else {
                         e.rows[(long)m * N + f] = y;
                     }

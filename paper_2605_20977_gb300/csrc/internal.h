@@ -115,13 +115,17 @@ struct Epi {
     const float *scale;           // EPI_HEADS scale table [64]
     int C;                        // EPI_HEADS channels of a position's mu / sigma row
     int c0;                       // EPI_HEADS first channel this projection writes (its N / 2 channels follow)
+    int eh_out;                   // EPI_SET_BIAS into the token's hyperprior-token row of its slot instead of rows
+    int hr;                       // A_ZHAT: the hyperprior's upsampling factor
 };
 
 // Source of the token operand of a GEMM.
 enum ASrc {
     A_DIRECT = 0,       // compact rows A[m][lda] in the compute type
     A_NORM = 1,         // RMSNorm(FP32 rows xrows[m]) * a_gain
-    A_EMBED = 2         // a_gain[c] * latent y[c] of the token (the latent embedding input)
+    A_EMBED = 2,        // a_gain[c] * latent y[c] of the token (the latent embedding input)
+    A_ZHAT = 3          // a_gain[c] * z-hat[c] of the token's hyperlatent (position (i, j) of a frame
+                        //    whose hyperprior is r times coarser: hyperlatent (i / r, j / r); r = epi.hr)
 };
 
 struct GemmArgs {

@@ -234,7 +234,9 @@ def weight_spec(c: ModelConfig) -> list:
               Tensor("hp.fp_a3", (Ch, 3), "bias"),
               Tensor("hp.fp_H4", (Ch, 3), "softplus_inv", 0.2), Tensor("hp.fp_b4", (Ch,), "bias")]
     else:
-        s += [Tensor("W_hp", (c.r * c.r, Ch, d), "lin", fan_in=Ch),
+        # one (Ch x d) projection per sub-pixel tap, stored in the compute
+        # dtype where the tensor cores take it (Ch a multiple of 64)
+        s += [Tensor("W_hp", (c.r * c.r, Ch, d), "lin", fan_in=Ch, matrix=Ch % 64 == 0),
               Tensor("b_hp", (d,), "bias")]
     if c.temporal:
         s += [Tensor("gamma_c", (C,), "const", 0.25),

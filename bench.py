@@ -638,22 +638,33 @@ def run_ours(args, rank: int, world: int, local: int):
     # end to end through the C ABI with pinned host buffers: every step copies
     # its containers and hyperlatents in and its latents out; the copies run
     # on a second stream, double-buffered, so step k+1's inputs go in and step
-    # k's latents come out while a decode runs (the host waits for each decode)
-    h_bs = [bss[b][:lens[b]].cpu().pin_memory() for b in range(B)]
-    h_z = [zs[b].cpu().pin_memory() for b in range(B)]
-    h_y = [torch.empty(ys[b].shape, dtype=torch.int16).pin_memory() for b in range(B)]
-    d_bs = [[torch.zeros(cap, dtype=torch.uint8, device=dev) for _ in range(B)] for _ in range(2)]
-    d_z = [[torch.zeros_like(zs[b]) for b in range(B)] for _ in range(2)]
-    d_y = [outs, [torch.zeros_like(y) for y in ys]]
+    # k's latents come out while a decode runs (the host waits for each
+    # decode).  The frames' containers, hyperlatents and latents each sit in
+    # one contiguous buffer per side, so a step's copies are three transfers
+    # (the library takes a pointer per frame into them)
+    boff = [0]
+    for b in range(B):
+        boff.append(boff[-1] + (int(lens[b]) + 255) // 256 * 256)
+    h_bs_all = torch.zeros(boff[-1], dtype=torch.uint8).pin_memory()
+    for b in range(B):
+        h_bs_all[boff[b]:boff[b] + lens[b]].copy_(bss[b][:lens[b]].cpu())
+    h_z_all = torch.stack([z.cpu() for z in zs]).pin_memory()
+    h_y_all = torch.empty((B,) + tuple(ys[0].shape), dtype=torch.int16).pin_memory()
+    h_y = [h_y_all[b] for b in range(B)]
+    d_bs_all = [torch.zeros(boff[-1], dtype=torch.uint8, device=dev) for _ in range(2)]
+    d_z_all = [torch.zeros_like(h_z_all, device=dev) for _ in range(2)]
+    d_y_all = [torch.zeros((B,) + tuple(ys[0].shape), dtype=torch.int16, device=dev) for _ in range(2)]
+    d_bs = [[d_bs_all[k][boff[b]:boff[b] + lens[b]] for b in range(B)] for k in range(2)]
+    d_z = [[d_z_all[k][b] for b in range(B)] for k in range(2)]
+    d_y = [[d_y_all[k][b] for b in range(B)] for k in range(2)]
     cstream = torch.cuda.Stream(device=dev)
     in_ready = [torch.cuda.Event(), torch.cuda.Event()]
     dec_done = [torch.cuda.Event(), torch.cuda.Event()]
 
     def copy_in(k):
         with torch.cuda.stream(cstream):
-            for b in range(B):
-                d_bs[k][b][:lens[b]].copy_(h_bs[b], non_blocking=True)
-                d_z[k][b].copy_(h_z[b], non_blocking=True)
+            d_bs_all[k].copy_(h_bs_all, non_blocking=True)
+            d_z_all[k].copy_(h_z_all, non_blocking=True)
             in_ready[k].record(cstream)
 
     def e2e_run(n):
@@ -669,8 +680,7 @@ def run_ours(args, rank: int, world: int, local: int):
             dec_done[cur].record(stream)
             with torch.cuda.stream(cstream):
                 cstream.wait_event(dec_done[cur])
-                for b in range(B):
-                    h_y[b].copy_(d_y[cur][b], non_blocking=True)
+                h_y_all.copy_(d_y_all[cur], non_blocking=True)
         stream.wait_stream(cstream)
 
     e2e_run(2)
@@ -685,8 +695,8 @@ def run_ours(args, rank: int, world: int, local: int):
         if not torch.equal(h_y[b], ys[b].cpu()):
             raise RuntimeError("end-to-end decode differs")
     e2e_value, _ = job_rate(B * args.steps, e0.elapsed_time(e1) / 1e3, world, dev)
-    h2d = sum(int(lens[b]) + h_z[b].numel() * 2 for b in range(B))
-    d2h = sum(h_y[b].numel() * 2 for b in range(B))
+    h2d = h_bs_all.numel() + h_z_all.numel() * 2
+    d2h = h_y_all.numel() * 2
 
     # roofline of the dominant kernel class from CUDA events (one
     # instrumented step with direct launches, after the timed region)

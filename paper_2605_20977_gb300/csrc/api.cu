@@ -1248,7 +1248,8 @@ void hyper_embed_tc(const Pass &P, const int *tok, const std::vector<int> &off, 
 // tokens and accumulator queries (they depend only on the hyperlatents,
 // Sec. 3.1), and for the temporal model this frame's Context Transformer
 // pass and every spatial block's cross-attention K/V.
-void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *eh, bool embed = true)
+void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *eh, bool embed = true,
+                    bool context = true)
 {
     const int n = H * W_;
     psw_ctx *c = P.c;
@@ -1263,8 +1264,29 @@ void frame_prologue(const Pass &P, const int *tok, int H, int W_, const float *e
                                   W(c, c->lay.b_hp), d, P.s));
     }
     gemm_norm(P, eh, c->lay.acc_g_q, c->acc.Wqkv, nullptr, n, d, d, epi_store(tok, nullptr, d, CS_QA, 0, d));
-    if (!m.temporal) return;
+    if (!m.temporal || !context) return;
     frame_context(P, tok, n);
+}
+
+// Rows of one batched Context Transformer pass at most (the workspace grows
+// to the pass's rows: ~9 KB per row at d = 384).
+constexpr int CTX_ROWS_MAX = 262144;
+
+// Frames b0 .. b1 - 1 of a decode plan whose prologue tokens are
+// consecutive; groups of whole frames of at most CTX_ROWS_MAX rows (one
+// frame alone if larger).
+template <typename F>
+void ctx_groups(const std::vector<int> &pro_n, F fn)
+{
+    int b0 = 0, rows = 0;
+    for (int b = 0; b < (int)pro_n.size(); b++) {
+        if (b > b0 && rows + pro_n[b] > CTX_ROWS_MAX) {
+            fn(b0, b, rows);
+            b0 = b; rows = 0;
+        }
+        rows += pro_n[b];
+    }
+    if (b0 < (int)pro_n.size()) fn(b0, (int)pro_n.size(), rows);
 }
 
 // The temporal model's per-frame context: the Context Transformer pass and
@@ -1610,7 +1632,11 @@ void enqueue_decode(psw_ctx *c, const DecodePlan &D, const int *d_tok, const int
                                             W(c, c->lay.W_hp), W(c, c->lay.b_hp), c->md.d, P.s));
         }
         for (int b = 0; b < D.n; b++)
-            frame_prologue(P, d_tok + D.pro_off[b], D.pro_h[b], D.pro_w[b], D.eh[b], !batch_embed);
+            frame_prologue(P, d_tok + D.pro_off[b], D.pro_h[b], D.pro_w[b], D.eh[b], !batch_embed, false);
+        // the temporal model's Context Transformer over the positions of
+        // groups of frames together (every launch is per token)
+        if (c->md.temporal)
+            ctx_groups(D.pro_n, [&](int b0, int, int rows) { frame_context(P, d_tok + D.pro_off[b0], rows); });
         Scope sc(c, s, K_RANS, 0.0, (double)D.n * c->md.C * 128.0);
         launch_rans_dec_init(c->d_slots, D.n, c->md.C, s);
     }
@@ -1708,6 +1734,7 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
         D = plan_decode(qs, fds, c->Whp_t.empty() ? 0 : c->md.r);
         size_t rows = D.max_step;
         for (int b = 0; b < n; b++) rows = std::max(rows, (size_t)D.pro_n[b]);
+        if (c->md.temporal) ctx_groups(D.pro_n, [&](int, int, int r) { rows = std::max(rows, (size_t)r); });
         if ((st = ensure_workspace(c, rows))) return st;
         key[0] = c->ws_gen;
     }

@@ -1001,6 +1001,19 @@ void gemm_any(const Pass &P, int asrc, const float *xrows, const float *a_gain, 
         }
         g.asrc = asrc = A_DIRECT; g.A = P.c->Xn; g.lda = K;
     }
+    if (tc && !g.f8 && asrc == A_EMBED && M >= WIDE_M && K <= 512 && e.tok) {
+        // a wide latent embedding: its operand rows (the bf16 values a tile
+        // would build) written once and streamed to the tiles
+        GemmArgs t = g;
+        t.asrc = A_DIRECT; t.A = P.c->Xn; t.lda = K;
+        if (gemm_takes_ws(P.c->prec, t)) {
+            LAUNCH(P, K_EMBED, 0.0, (double)M * K * 4.0,
+                   if (!launch_embed_rows(P.S, e.tok, M, a_gain, K, P.c->Xn, P.s)) *P.failed = true);
+            P.xn_rows = nullptr;                       // Xn holds these rows now
+            g = t;
+            asrc = A_DIRECT;
+        }
+    }
     if (g.f8 && M >= WIDE_M && K % 128 == 0 && (asrc == A_NORM ? K <= 512 : asrc == A_DIRECT ? K <= 1024 : false)) {
         // a wide E4M3 launch: its token rows are quantised once (the bytes
         // and scales an E4M3 tile would build) and streamed to the tiles

@@ -69,6 +69,27 @@ __global__ void __launch_bounds__(256) k_norm_rows(const float *__restrict__ X, 
     if (m < M) norm_row_global<CH>(X + (long)m * K, gh, invK, K, dst + (long)m * ldd);
 }
 
+// The latent embedding's operand rows for a projection whose tiles stream
+// them: dst[m][k] = bf16(gain[k] * y[k]) of token m's latents, one warp per
+// row, eight rows per block (the values embed_rows builds in a tile: lane l
+// holds elements 4l + 128c .. +3).
+__global__ void __launch_bounds__(256) k_embed_rows(const Slot *__restrict__ S, const int *__restrict__ tok, int M,
+                                                    const float *__restrict__ gain, int K,
+                                                    __nv_bfloat16 *__restrict__ dst)
+{
+    pdl_trigger();
+    const int m = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    pdl_wait();
+    if (m >= M) return;
+    const int tk = tok[m];
+    const int16_t *y = S[tok_slot(tk)].y + (long)tok_pos(tk) * K;
+    for (int e = lane * 4; e < K; e += 128) {
+        const short4 q = *(const short4 *)(y + e);
+        *(uint2 *)(dst + (long)m * K + e) = pack4(gain[e] * (float)q.x, gain[e + 1] * (float)q.y,
+                                                  gain[e + 2] * (float)q.z, gain[e + 3] * (float)q.w);
+    }
+}
+
 // E4M3 streamed rows: one warp per row, 8 rows per block.
 template <int CH>
 __global__ void __launch_bounds__(256) k_rows8_norm(const float *__restrict__ X, const float *__restrict__ gain, int M,
@@ -205,6 +226,14 @@ bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst
     cudaError_t e = K <= 384 ? launch_pdl(k_norm_rows<3>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst, ldd)
                              : launch_pdl(k_norm_rows<4>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst, ldd);
     return e == cudaSuccess;
+}
+
+bool launch_embed_rows(const Slot *S, const int *tok, int M, const float *gain, int K, void *dst, cudaStream_t s)
+{
+    if (M <= 0) return true;
+    if (K % 4 || ((uintptr_t)dst & 15)) return false;
+    return launch_pdl(k_embed_rows, dim3((M + 7) / 8), dim3(256), 0, s, S, tok, M, gain, K, (__nv_bfloat16 *)dst) ==
+           cudaSuccess;
 }
 
 bool launch_rows8(int asrc, const float *X, const float *gain, const void *A, int lda, int M, int K, uint8_t *dst,

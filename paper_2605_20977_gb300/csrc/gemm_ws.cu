@@ -582,7 +582,7 @@ bool gemm_ws_prepare()
 {
     return ws_attr_all<false, EPI_STORE>() && ws_attr_all<false, EPI_QKV>() && ws_attr_all<false, EPI_RESID>() &&
            ws_attr_all<false, EPI_RESID_BASE>() && ws_attr_all<false, EPI_BIAS_SILU>() &&
-           ws_attr_all<false, EPI_HEADS>() && ws_attr_all<true, EPI_SWIGLU>() &&
+           ws_attr_all<false, EPI_HEADS>() && ws_attr_all<true, EPI_SWIGLU>() && ws_attr_all<false, EPI_SET_BIAS>() &&
            ws_attr_all<false, EPI_STORE, true>() && ws_attr_all<false, EPI_QKV, true>() &&
            ws_attr_all<false, EPI_RESID, true>() && ws_attr_all<false, EPI_RESID_BASE, true>() &&
            ws_attr_all<true, EPI_SWIGLU, true>();
@@ -602,10 +602,11 @@ bool gemm_ws_supported(const GemmArgs &g)
     if ((m == EPI_STORE || m == EPI_QKV) && g.epi.d % 8) return false;
     if ((m == EPI_SWIGLU || m == EPI_BIAS_SILU) && g.epi.ld_out % 8) return false;
     if (g.f8 && (!ws_f8_mode(m) || !g.xs || !g.wsc || (m == EPI_SWIGLU && !g.wsc2) || g.K % KC8)) return false;
+    if (m == EPI_SET_BIAS && (g.f8 || g.epi.eh_out)) return false;
     return g.asrc == A_DIRECT && g.K % KC == 0 && g.K >= KC && g.N >= 32 && g.N % 32 == 0 &&
            g.lda % 8 == 0 &&
            (m == EPI_STORE || m == EPI_QKV || m == EPI_RESID || m == EPI_RESID_BASE || m == EPI_BIAS_SILU ||
-            m == EPI_HEADS || m == EPI_SWIGLU);
+            m == EPI_HEADS || m == EPI_SWIGLU || m == EPI_SET_BIAS);
 }
 
 // Tokens per tile: the width with the least estimated time of the busiest
@@ -665,6 +666,7 @@ bool gemm_ws(const GemmArgs &g, cudaStream_t s)
     case EPI_RESID_BASE: e = ws_launch_tn<false, EPI_RESID_BASE>(tnb, tw, tw2, tx, g, s); break;
     case EPI_BIAS_SILU: e = ws_launch_tn<false, EPI_BIAS_SILU>(tnb, tw, tw2, tx, g, s); break;
     case EPI_HEADS: e = ws_launch_tn<false, EPI_HEADS>(tnb, tw, tw2, tx, g, s); break;
+    case EPI_SET_BIAS: e = ws_launch_tn<false, EPI_SET_BIAS>(tnb, tw, tw2, tx, g, s); break;
     default: return false;
     }
     return e == cudaSuccess;

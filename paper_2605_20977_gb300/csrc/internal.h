@@ -162,6 +162,10 @@ bool gemm(int prec, const GemmArgs &g, cudaStream_t s);
 // normalised token operand of a projection whose tiles then stream it
 // (A_DIRECT), bit-identical to the operand an A_NORM tile builds.
 bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst, cudaStream_t s, int ldd = 0);
+// dst[m][k] = bf16(gain[k] * y[k]) of the latents of token tok[m] (m < M, K a
+// multiple of 4): the latent embedding's operand as an A_EMBED tile builds
+// it, for a projection whose tiles stream it.
+bool launch_embed_rows(const Slot *S, const int *tok, int M, const float *gain, int K, void *dst, cudaStream_t s);
 // E4M3 token rows dst[m][k] (bytes) and their dequantisation scales xs[m]
 // for m < M: of RMSNorm(X[m]) * gain (asrc A_NORM, K <= 512) or of the bf16
 // rows A[m][lda] (A_DIRECT, K <= 1024), K a multiple of 128; byte-identical

@@ -301,6 +301,8 @@ struct psw_ctx {
     Slot *d_slots = nullptr, *h_slots = nullptr;
     int *d_status = nullptr;           // timeouts of bounded device waits
     int *h_status = nullptr;           // pinned: [MAX_SLOTS + 1]
+    int *d_bstatus = nullptr;          // a batched decode's per-frame status words [MAX_SLOTS]
+    CopyJob *d_jobs = nullptr, *h_jobs = nullptr;   // a batched decode's output copies [4 MAX_SLOTS]
     int *d_tok = nullptr;              // direct-launch token lists
     int2 *d_kn = nullptr;
     size_t tok_cap = 0, kn_cap = 0;
@@ -1717,6 +1719,7 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
     for (int b = 0; b < n; b++) {
         Slot sl = make_slot(qs[b], fds[b].H, fds[b].W, fds[b].schedule);
         sl.bs = bs[b]; sl.len = lens[b]; sl.zhat = zhat[b];
+        sl.status = c->d_bstatus + b;                  // the call's status words sit together
         c->h_slots[b] = sl;
     }
     // graph key: the workspace generation, the engine and the batch shape
@@ -1766,7 +1769,10 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
             if (t + 1 < D.Tmax) ntok_prev += D.step_n[t];
         }
     }
-    if ((st = upload_slots(c, qs, n, s))) return st;
+    // slot table and status words: three transfers for the whole batch
+    CK_CUDA(c, cudaMemcpyAsync(c->d_slots, c->h_slots, sizeof(Slot) * n, cudaMemcpyHostToDevice, s));
+    CK_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+    CK_CUDA(c, cudaMemsetAsync(c->d_bstatus, 0, n * sizeof(int), s));
     if (graph) {
         if (!gr) {
             GraphRec g;
@@ -1853,16 +1859,30 @@ psw_status decode_run(psw_ctx *c, int n, psw_seq *const *seqs, const psw_frame_d
         c->last_engine = persist ? PSW_ENGINE_PERSISTENT : 0;
     }
     CK_CUDA(c, cudaGetLastError());
+    // every frame's outputs and its sequence's previous latents in one copy
+    // launch, then the status words back in two transfers
+    int nj = 0;
+    unsigned long long maxb = 0;
+    auto job = [&](const void *src, void *dst, size_t bytes) {
+        c->h_jobs[nj++] = CopyJob{src, dst, (unsigned long long)bytes};
+        maxb = std::max<unsigned long long>(maxb, bytes);
+    };
     for (int b = 0; b < n; b++) {
         psw_seq *q = qs[b];
         size_t nsym = (size_t)fds[b].H * fds[b].W * c->md.C;
-        CK_CUDA(c, cudaMemcpyAsync(yout[b], q->y, nsym * 2, cudaMemcpyDeviceToDevice, s));
-        if (mu_out && mu_out[b]) CK_CUDA(c, cudaMemcpyAsync(mu_out[b], q->mu, nsym * 4, cudaMemcpyDeviceToDevice, s));
-        if (sg_out && sg_out[b]) CK_CUDA(c, cudaMemcpyAsync(sg_out[b], q->sigma, nsym * 4, cudaMemcpyDeviceToDevice, s));
-        CK_CUDA(c, cudaMemcpyAsync(q->yprev, q->y, nsym * 2, cudaMemcpyDeviceToDevice, s));
+        job(q->y, yout[b], nsym * 2);
+        if (mu_out && mu_out[b]) job(q->mu, mu_out[b], nsym * 4);
+        if (sg_out && sg_out[b]) job(q->sigma, sg_out[b], nsym * 4);
+        job(q->y, q->yprev, nsym * 2);
     }
-    std::vector<int> sts;
-    if ((st = read_status(c, qs, s, sts))) return st;
+    CK_CUDA(c, cudaMemcpyAsync(c->d_jobs, c->h_jobs, nj * sizeof(CopyJob), cudaMemcpyHostToDevice, s));
+    launch_copy_jobs(c->d_jobs, nj, maxb, s);
+    CK_CUDA(c, cudaGetLastError());
+    CK_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK_CUDA(c, cudaMemcpyAsync(c->h_status + 1, c->d_bstatus, n * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK_CUDA(c, cudaStreamSynchronize(s));
+    std::vector<int> sts(n);
+    for (int b = 0; b < n; b++) sts[b] = c->h_status[1 + b] | c->h_status[0];
     psw_status first = PSW_OK;
     for (int b = 0; b < n; b++) {
         qs[b]->frame++;
@@ -1961,6 +1981,9 @@ psw_status psw_create(const psw_model_desc *desc, const float *weights_host, siz
     if (e == cudaSuccess) e = cudaMalloc(&c->d_scale, 64 * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_slots, MAX_SLOTS * sizeof(Slot));
     if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_bstatus, MAX_SLOTS * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_jobs, 4 * MAX_SLOTS * sizeof(CopyJob));
+    if (e == cudaSuccess) e = cudaMallocHost(&c->h_jobs, 4 * MAX_SLOTS * sizeof(CopyJob));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_slots, MAX_SLOTS * sizeof(Slot));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_status, (MAX_SLOTS + 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_rate, sizeof(double));
@@ -2006,6 +2029,8 @@ void psw_destroy(psw_ctx *c)
     cudaFree(c->d_pbar);
     cudaFree(c->d_step);
     cudaFree(c->w); cudaFree(c->wmat); cudaFree(c->d_cdf); cudaFree(c->d_meta); cudaFree(c->d_scale);
+    cudaFree(c->d_bstatus); cudaFree(c->d_jobs);
+    if (c->h_jobs) cudaFreeHost(c->h_jobs);
     cudaFree(c->rate_buf); cudaFree(c->d_slots); cudaFree(c->d_status); cudaFree(c->d_tok); cudaFree(c->d_kn);
     cudaFree(c->Xn); cudaFree(c->Q); cudaFree(c->O); cudaFree(c->Hid);
     cudaFree(c->Xa); cudaFree(c->Xb); cudaFree(c->Xg); cudaFree(c->Xc); cudaFree(c->NM);

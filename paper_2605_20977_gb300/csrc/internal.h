@@ -217,6 +217,15 @@ __device__ __forceinline__ T *cache_row(const Slot &s, int sel, int layer, int p
 
 
 // ---------------------------------------------------------------- kernels
+// One device-to-device copy of a batch's copy kernel.
+struct CopyJob {
+    const void *src;
+    void *dst;
+    unsigned long long bytes;
+};
+// jobs[0 .. n) (a device array) in one launch: 16-byte words where both
+// addresses are 16-byte aligned, bytes otherwise.
+void launch_copy_jobs(const CopyJob *jobs, int n, unsigned long long max_bytes, cudaStream_t s);
 void launch_transpose_convert(int prec, const float *src, int K, int N, void *dst, int row_off,
                               cudaStream_t s);
 // Context Transformer input rows out[m] of each token from the previous

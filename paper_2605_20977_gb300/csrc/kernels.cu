@@ -172,6 +172,31 @@ void launch_embed_hyper_batch(const Slot *S, int nslots, int Hmax, int Wmax, int
                                                                             b, d);
 }
 
+// ---------------------------------------------------------------- batched copies
+
+__global__ void k_copy_jobs(const CopyJob *__restrict__ jobs)
+{
+    const CopyJob j = jobs[blockIdx.y];
+    const size_t stride = (size_t)gridDim.x * blockDim.x, t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((((uintptr_t)j.src | (uintptr_t)j.dst) & 15) == 0) {
+        const size_t nw = j.bytes / 16;
+        const uint4 *src = (const uint4 *)j.src;
+        uint4 *dst = (uint4 *)j.dst;
+        for (size_t w = t0; w < nw; w += stride) dst[w] = src[w];
+        for (size_t b = nw * 16 + t0; b < j.bytes; b += stride) ((char *)j.dst)[b] = ((const char *)j.src)[b];
+    } else {
+        for (size_t b = t0; b < j.bytes; b += stride) ((char *)j.dst)[b] = ((const char *)j.src)[b];
+    }
+}
+
+void launch_copy_jobs(const CopyJob *jobs, int n, unsigned long long max_bytes, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const unsigned long long words = (max_bytes + 15) / 16;
+    const int gx = (int)std::max<unsigned long long>(1, std::min<unsigned long long>((words + 255) / 256, 64));
+    k_copy_jobs<<<dim3(gx, n), 256, 0, s>>>(jobs);
+}
+
 // ---------------------------------------------------------------- RMSNorm
 
 // One warp per row: y = x / sqrt(mean(x^2) + 1e-6) * g, FP32 statistics,

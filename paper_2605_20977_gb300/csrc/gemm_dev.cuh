@@ -453,24 +453,19 @@ __device__ __forceinline__ void norm_rows(const float *__restrict__ xrows, const
     }
 }
 
-// RMSNorm of one FP32 row x[0..K) times the gain (gh: this lane's gains,
-// load_gain) into a compact bf16 row dst[0..K) in global memory: the
-// arithmetic of norm_rows for one row (lane l holds elements 4l + 128c ..
-// +3, the same fused multiply-add chain and butterfly sum), so the row
-// equals, bit for bit, the operand a tile builds in shared memory.  Used
-// where a projection's tiles stream the normalised rows with TMA instead of
-// each feature tile normalising them again.
+// RMSNorm of one FP32 row times the gain into a compact bf16 row dst[0..K)
+// in global memory, the row's elements already in registers (v: lane l's
+// elements 4l + 128c .. +3, zero past K; gh: the same lanes' gains,
+// load_gain): the arithmetic of norm_rows for one row (the same fused
+// multiply-add chain and butterfly sum), so the row equals, bit for bit,
+// the operand a tile builds in shared memory.  Used where a projection's
+// tiles stream the normalised rows with TMA instead of each feature tile
+// normalising them again.
 template <int CH>
-__device__ __forceinline__ void norm_row_global(const float *__restrict__ x, const float4 *gh, float invK, int K,
-                                                __nv_bfloat16 *__restrict__ dst)
+__device__ __forceinline__ void norm_row_store(const float4 *v, const float4 *gh, float invK, int K,
+                                               __nv_bfloat16 *__restrict__ dst)
 {
     const int lane = threadIdx.x & 31;
-    float4 v[CH];
-#pragma unroll
-    for (int c = 0; c < CH; c++) {
-        int e = lane * 4 + c * 128;
-        v[c] = e < K ? *(const float4 *)(x + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
     float ss = 0.0f;
 #pragma unroll
     for (int c = 0; c < CH; c++) {
@@ -486,6 +481,21 @@ __device__ __forceinline__ void norm_row_global(const float *__restrict__ x, con
         *(uint2 *)(dst + e) = pack4(v[c].x * inv * gh[c].x, v[c].y * inv * gh[c].y, v[c].z * inv * gh[c].z,
                                     v[c].w * inv * gh[c].w);
     }
+}
+
+// norm_row_store of the FP32 row x[0..K), loaded here.
+template <int CH>
+__device__ __forceinline__ void norm_row_global(const float *__restrict__ x, const float4 *gh, float invK, int K,
+                                                __nv_bfloat16 *__restrict__ dst)
+{
+    const int lane = threadIdx.x & 31;
+    float4 v[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        int e = lane * 4 + c * 128;
+        v[c] = e < K ? *(const float4 *)(x + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    norm_row_store<CH>(v, gh, invK, K, dst);
 }
 
 // The E4M3 operand rows of norm_rows8 and quant_rows8 for one row in global

@@ -54,19 +54,47 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUten
 }
 
 // RMSNorm rows for a projection whose tiles stream their token operand:
-// dst[m] = bf16(RMSNorm(X[m]) * gain), one warp per row, eight rows per
-// block (norm_row_global: the same values a tile would build).
-template <int CH>
-__global__ void __launch_bounds__(256) k_norm_rows(const float *__restrict__ X, const float *__restrict__ gain, int M,
-                                                   int K, __nv_bfloat16 *__restrict__ dst, int ldd)
+// dst[m] = bf16(RMSNorm(X[m]) * gain), R consecutive rows per warp with all
+// their loads issued before the first reduction, eight warps per block, the
+// gains staged in shared memory before the wait for the previous kernel
+// (norm_row_store: the same values a tile would build, whatever R).
+// Blocks per SM the registers are bounded for: the R x CH float4 of a
+// warp's rows stay in registers without spilling.
+template <int CH, int R>
+constexpr int norm_rows_min_blocks() { return R == 1 ? 1 : CH * R <= 6 ? 4 : CH * R <= 12 ? 3 : 2; }
+
+template <int CH, int R>
+__global__ void __launch_bounds__(256, norm_rows_min_blocks<CH, R>())
+k_norm_rows(const float *__restrict__ X, const float *__restrict__ gain, int M, int K, __nv_bfloat16 *__restrict__ dst,
+            int ldd)
 {
+    __shared__ float4 sg[CH * 32];
     pdl_trigger();
-    float4 gh[CH];
-    load_gain<CH>(gain, K, gh);                        // weights: ready before the previous kernel ends
+    for (int i = threadIdx.x; i < CH * 32; i += blockDim.x) {
+        const int e = 4 * i;
+        sg[i] = e < K ? make_float4(gain[e], gain[e + 1], gain[e + 2], gain[e + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
     const float invK = 1.0f / (float)K;
-    const int m = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const long m0 = ((long)blockIdx.x * 8 + (threadIdx.x >> 5)) * R;
     pdl_wait();
-    if (m < M) norm_row_global<CH>(X + (long)m * K, gh, invK, K, dst + (long)m * ldd);
+    float4 v[R][CH];
+#pragma unroll
+    for (int b = 0; b < R; b++) {
+        const float *x = m0 + b < M ? X + (m0 + b) * K : nullptr;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            const int e = lane * 4 + c * 128;
+            v[b][c] = (x && e < K) ? *(const float4 *)(x + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    float4 gh[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) gh[c] = sg[lane + 32 * c];
+#pragma unroll
+    for (int b = 0; b < R; b++)
+        if (m0 + b < M) norm_row_store<CH>(v[b], gh, invK, K, dst + (m0 + b) * ldd);
 }
 
 // The latent embedding's operand rows for a projection whose tiles stream
@@ -222,9 +250,19 @@ bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst
     if (M <= 0) return true;
     if (ldd <= 0) ldd = K;
     if (K > KRES_MAX || K % 4 || ldd < K || ldd % 8 || ((uintptr_t)dst & 15)) return false;
-    dim3 grid((M + 7) / 8), block(256);
-    cudaError_t e = K <= 384 ? launch_pdl(k_norm_rows<3>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst, ldd)
-                             : launch_pdl(k_norm_rows<4>, grid, block, 0, s, X, gain, M, K, (__nv_bfloat16 *)dst, ldd);
+    // rows per warp: the most that still leaves two blocks per SM
+    const int R = (M + 31) / 32 >= 2 * sm_count() ? 4 : (M + 15) / 16 >= 2 * sm_count() ? 2 : 1;
+    dim3 grid((M + 8 * R - 1) / (8 * R)), block(256);
+    __nv_bfloat16 *d = (__nv_bfloat16 *)dst;
+    cudaError_t e;
+    if (K <= 384)
+        e = R == 4 ? launch_pdl(k_norm_rows<3, 4>, grid, block, 0, s, X, gain, M, K, d, ldd)
+          : R == 2 ? launch_pdl(k_norm_rows<3, 2>, grid, block, 0, s, X, gain, M, K, d, ldd)
+                   : launch_pdl(k_norm_rows<3, 1>, grid, block, 0, s, X, gain, M, K, d, ldd);
+    else
+        e = R == 4 ? launch_pdl(k_norm_rows<4, 4>, grid, block, 0, s, X, gain, M, K, d, ldd)
+          : R == 2 ? launch_pdl(k_norm_rows<4, 2>, grid, block, 0, s, X, gain, M, K, d, ldd)
+                   : launch_pdl(k_norm_rows<4, 1>, grid, block, 0, s, X, gain, M, K, d, ldd);
     return e == cudaSuccess;
 }
 

@@ -503,17 +503,14 @@ __device__ __forceinline__ void norm_row_global(const float *__restrict__ x, con
 // square root, gain, absolute maximum, power-of-two scale, conversion), so a
 // row streamed by the wide projection kernel equals, byte for byte, the row
 // a tile builds in shared memory; *xs receives its dequantisation scale.
+// The _store forms take the row already in registers (v: lane l's elements
+// 4l + 128c .. +3, zero past K, overwritten; q: lane l's elements
+// 8l + 256c .. +7 as bf16, zero past K), the _global forms load it first.
 template <int CH>
-__device__ __forceinline__ void norm_row8_global(const float *__restrict__ x, const float4 *gh, float invK, int K,
-                                                 uint8_t *__restrict__ dst, float *xs)
+__device__ __forceinline__ void norm_row8_store(float4 *v, const float4 *gh, float invK, int K,
+                                                uint8_t *__restrict__ dst, float *xs)
 {
     const int lane = threadIdx.x & 31;
-    float4 v[CH];
-#pragma unroll
-    for (int c = 0; c < CH; c++) {
-        int e = lane * 4 + c * 128;
-        v[c] = e < K ? *(const float4 *)(x + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
     float ss = 0.0f;
 #pragma unroll
     for (int c = 0; c < CH; c++) {
@@ -542,16 +539,23 @@ __device__ __forceinline__ void norm_row8_global(const float *__restrict__ x, co
 }
 
 template <int CH>
-__device__ __forceinline__ void quant_row8_global(const __nv_bfloat16 *__restrict__ row, int K,
-                                                  uint8_t *__restrict__ dst, float *xs)
+__device__ __forceinline__ void norm_row8_global(const float *__restrict__ x, const float4 *gh, float invK, int K,
+                                                 uint8_t *__restrict__ dst, float *xs)
 {
     const int lane = threadIdx.x & 31;
-    uint4 q[CH];
+    float4 v[CH];
 #pragma unroll
     for (int c = 0; c < CH; c++) {
-        int e = lane * 8 + c * 256;
-        q[c] = e < K ? *(const uint4 *)(row + e) : make_uint4(0, 0, 0, 0);
+        int e = lane * 4 + c * 128;
+        v[c] = e < K ? *(const float4 *)(x + e) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    norm_row8_store<CH>(v, gh, invK, K, dst, xs);
+}
+
+template <int CH>
+__device__ __forceinline__ void quant_row8_store(const uint4 *q, int K, uint8_t *__restrict__ dst, float *xs)
+{
+    const int lane = threadIdx.x & 31;
     float amax = 0.0f;
 #pragma unroll
     for (int c = 0; c < CH; c++) {
@@ -574,6 +578,20 @@ __device__ __forceinline__ void quant_row8_global(const __nv_bfloat16 *__restric
                                          e4m3x4(f2.x * qm, f2.y * qm, f3.x * qm, f3.y * qm));
     }
     if (lane == 0) *xs = sc;
+}
+
+template <int CH>
+__device__ __forceinline__ void quant_row8_global(const __nv_bfloat16 *__restrict__ row, int K,
+                                                  uint8_t *__restrict__ dst, float *xs)
+{
+    const int lane = threadIdx.x & 31;
+    uint4 q[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) {
+        int e = lane * 8 + c * 256;
+        q[c] = e < K ? *(const uint4 *)(row + e) : make_uint4(0, 0, 0, 0);
+    }
+    quant_row8_store<CH>(q, K, dst, xs);
 }
 
 // Build the token operand of rows m0 .. m0+63 in shared memory; rows past M

@@ -118,28 +118,65 @@ __global__ void __launch_bounds__(256) k_embed_rows(const Slot *__restrict__ S, 
     }
 }
 
-// E4M3 streamed rows: one warp per row, 8 rows per block.
-template <int CH>
-__global__ void __launch_bounds__(256) k_rows8_norm(const float *__restrict__ X, const float *__restrict__ gain, int M,
-                                                    int K, uint8_t *__restrict__ dst, float *__restrict__ xs)
+// E4M3 streamed rows: R consecutive rows per warp with all their loads
+// issued before the first reduction, eight warps per block; each row's
+// arithmetic is norm_row8_store's or quant_row8_store's, whatever R.
+template <int CH, int R>
+__global__ void __launch_bounds__(256, norm_rows_min_blocks<CH, R>())
+k_rows8_norm(const float *__restrict__ X, const float *__restrict__ gain, int M, int K, uint8_t *__restrict__ dst,
+             float *__restrict__ xs)
 {
+    __shared__ float4 sg[CH * 32];
     pdl_trigger();
-    float4 gh[CH];
-    load_gain<CH>(gain, K, gh);
+    for (int i = threadIdx.x; i < CH * 32; i += blockDim.x) {
+        const int e = 4 * i;
+        sg[i] = e < K ? make_float4(gain[e], gain[e + 1], gain[e + 2], gain[e + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
     const float invK = 1.0f / (float)K;
-    const int m = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const long m0 = ((long)blockIdx.x * 8 + (threadIdx.x >> 5)) * R;
     pdl_wait();
-    if (m < M) norm_row8_global<CH>(X + (long)m * K, gh, invK, K, dst + (long)m * K, xs + m);
+    float4 v[R][CH];
+#pragma unroll
+    for (int b = 0; b < R; b++) {
+        const float *x = m0 + b < M ? X + (m0 + b) * K : nullptr;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            const int e = lane * 4 + c * 128;
+            v[b][c] = (x && e < K) ? *(const float4 *)(x + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    float4 gh[CH];
+#pragma unroll
+    for (int c = 0; c < CH; c++) gh[c] = sg[lane + 32 * c];
+#pragma unroll
+    for (int b = 0; b < R; b++)
+        if (m0 + b < M) norm_row8_store<CH>(v[b], gh, invK, K, dst + (m0 + b) * K, xs + m0 + b);
 }
 
-template <int CH>
-__global__ void __launch_bounds__(256) k_rows8_quant(const __nv_bfloat16 *__restrict__ A, int lda, int M, int K,
-                                                     uint8_t *__restrict__ dst, float *__restrict__ xs)
+template <int CH, int R>
+__global__ void __launch_bounds__(256, norm_rows_min_blocks<CH, R>())
+k_rows8_quant(const __nv_bfloat16 *__restrict__ A, int lda, int M, int K, uint8_t *__restrict__ dst,
+              float *__restrict__ xs)
 {
     pdl_trigger();
-    const int m = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    const long m0 = ((long)blockIdx.x * 8 + (threadIdx.x >> 5)) * R;
     pdl_wait();
-    if (m < M) quant_row8_global<CH>(A + (long)m * lda, K, dst + (long)m * K, xs + m);
+    uint4 q[R][CH];
+#pragma unroll
+    for (int b = 0; b < R; b++) {
+        const __nv_bfloat16 *row = m0 + b < M ? A + (m0 + b) * lda : nullptr;
+#pragma unroll
+        for (int c = 0; c < CH; c++) {
+            const int e = lane * 8 + c * 256;
+            q[b][c] = (row && e < K) ? *(const uint4 *)(row + e) : make_uint4(0, 0, 0, 0);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < R; b++)
+        if (m0 + b < M) quant_row8_store<CH>(q[b], K, dst + (m0 + b) * K, xs + m0 + b);
 }
 
 // ---------------------------------------------------------------- host side
@@ -218,6 +255,13 @@ int tile_tokens(int nf, int M)
     return t64 < sm_count() && t32 <= sm_count() ? 32 : 64;
 }
 
+// Rows per warp of the row producers: the most (1, 2 or 4) that still
+// leaves two blocks of eight warps per SM.
+int rows_per_warp(int M)
+{
+    return (M + 31) / 32 >= 2 * sm_count() ? 4 : (M + 15) / 16 >= 2 * sm_count() ? 2 : 1;
+}
+
 // ---------------------------------------------------------------- E4M3 weights
 
 __global__ void k_absmax(const float *__restrict__ src, size_t n, unsigned *out)
@@ -250,8 +294,7 @@ bool launch_norm_rows(const float *X, const float *gain, int M, int K, void *dst
     if (M <= 0) return true;
     if (ldd <= 0) ldd = K;
     if (K > KRES_MAX || K % 4 || ldd < K || ldd % 8 || ((uintptr_t)dst & 15)) return false;
-    // rows per warp: the most that still leaves two blocks per SM
-    const int R = (M + 31) / 32 >= 2 * sm_count() ? 4 : (M + 15) / 16 >= 2 * sm_count() ? 2 : 1;
+    const int R = rows_per_warp(M);
     dim3 grid((M + 8 * R - 1) / (8 * R)), block(256);
     __nv_bfloat16 *d = (__nv_bfloat16 *)dst;
     cudaError_t e;
@@ -279,17 +322,30 @@ bool launch_rows8(int asrc, const float *X, const float *gain, const void *A, in
 {
     if (M <= 0) return true;
     if (K % KC8 || ((uintptr_t)dst & 15)) return false;
-    dim3 grid((M + 7) / 8), block(256);
+    const int R = rows_per_warp(M);
+    dim3 grid((M + 8 * R - 1) / (8 * R)), block(256);
     cudaError_t e;
     if (asrc == A_NORM) {
         if (K > KRES_MAX) return false;
-        e = K <= 384 ? launch_pdl(k_rows8_norm<3>, grid, block, 0, s, X, gain, M, K, dst, xs)
-                     : launch_pdl(k_rows8_norm<4>, grid, block, 0, s, X, gain, M, K, dst, xs);
+        if (K <= 384)
+            e = R == 4 ? launch_pdl(k_rows8_norm<3, 4>, grid, block, 0, s, X, gain, M, K, dst, xs)
+              : R == 2 ? launch_pdl(k_rows8_norm<3, 2>, grid, block, 0, s, X, gain, M, K, dst, xs)
+                       : launch_pdl(k_rows8_norm<3, 1>, grid, block, 0, s, X, gain, M, K, dst, xs);
+        else
+            e = R == 4 ? launch_pdl(k_rows8_norm<4, 4>, grid, block, 0, s, X, gain, M, K, dst, xs)
+              : R == 2 ? launch_pdl(k_rows8_norm<4, 2>, grid, block, 0, s, X, gain, M, K, dst, xs)
+                       : launch_pdl(k_rows8_norm<4, 1>, grid, block, 0, s, X, gain, M, K, dst, xs);
     } else {
         if (K > 1024 || lda % 8) return false;
         const __nv_bfloat16 *Ab = (const __nv_bfloat16 *)A;
-        e = K <= 512 ? launch_pdl(k_rows8_quant<2>, grid, block, 0, s, Ab, lda, M, K, dst, xs)
-                     : launch_pdl(k_rows8_quant<4>, grid, block, 0, s, Ab, lda, M, K, dst, xs);
+        if (K <= 512)
+            e = R == 4 ? launch_pdl(k_rows8_quant<2, 4>, grid, block, 0, s, Ab, lda, M, K, dst, xs)
+              : R == 2 ? launch_pdl(k_rows8_quant<2, 2>, grid, block, 0, s, Ab, lda, M, K, dst, xs)
+                       : launch_pdl(k_rows8_quant<2, 1>, grid, block, 0, s, Ab, lda, M, K, dst, xs);
+        else
+            e = R == 4 ? launch_pdl(k_rows8_quant<4, 4>, grid, block, 0, s, Ab, lda, M, K, dst, xs)
+              : R == 2 ? launch_pdl(k_rows8_quant<4, 2>, grid, block, 0, s, Ab, lda, M, K, dst, xs)
+                       : launch_pdl(k_rows8_quant<4, 1>, grid, block, 0, s, Ab, lda, M, K, dst, xs);
     }
     return e == cudaSuccess;
 }

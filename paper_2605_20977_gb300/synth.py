@@ -312,14 +312,23 @@ def weights_count(c: ModelConfig) -> int:
     return int(sum(int(np.prod(t.shape)) for t in weight_spec(c)))
 
 
-def weights(c: ModelConfig, seed: int = 42) -> np.ndarray:
-    """Flat FP32 weight vector in packing order (seeded PCG64)."""
+def weights(c: ModelConfig, seed: int = 42, vary_consts: bool = False) -> np.ndarray:
+    """Flat FP32 weight vector in packing order (seeded PCG64).
+
+    The channel-wise scales and offsets ("const" tensors) hold their value
+    in every channel; with vary_consts each channel draws its own around it
+    (value (1 + 0.2 n) + 0.05 n' from a second generator), so a wrong channel
+    index or a dropped offset changes results.  The other tensors are the
+    same either way."""
     rng = np.random.Generator(np.random.PCG64(seed))
+    rng_c = np.random.Generator(np.random.PCG64(seed + 1))
     parts = []
     for t in weight_spec(c):
         n = int(np.prod(t.shape))
         if t.init == "const":
             a = np.full(n, t.value, dtype=np.float64)
+            if vary_consts:
+                a = a * (1.0 + 0.2 * rng_c.standard_normal(n)) + 0.05 * rng_c.standard_normal(n)
         elif t.init == "gain":
             a = 1.0 + 0.1 * rng.standard_normal(n)
         elif t.init == "lin":

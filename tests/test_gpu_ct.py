@@ -99,6 +99,19 @@ def test_ct_fp32_vs_oracle(name, sched):
     _check(res, fr, cfg, mu_o, sg_o, FP32_TOL, sched, pct=False)
 
 
+def test_ct_per_channel_constants_fp32():
+    """The cyclic Channel Transformer model with every channel-wise scale and
+    offset different per channel (the shifted latents' scales of each group,
+    the grouped heads' output scales and offsets)."""
+    cfg = synth.config("tiny_cyc_ct")
+    w = synth.weights(cfg, vary_consts=True)
+    fr = synth.frames(cfg, 1, seed=2203)
+    ctx = psw.Context(cfg, w, precision=psw.PSW_FP32)
+    res = _code(ctx, fr, 0)
+    mu_o, sg_o = O.run(cfg, np.asarray(w, np.float64), fr.y, fr.z, driver=0)
+    _check(res, fr, cfg, mu_o, sg_o, FP32_TOL, 0, pct=False)
+
+
 @pytest.mark.parametrize("name,rows,precision", [("i1080_ct", 8, psw.PSW_BF16), ("i1080_cyc_ct", 8, psw.PSW_BF16),
                                                  ("i1080_cyc_ct", 8, psw.PSW_FP8)])
 def test_ct_1080p_width_vs_oracle(name, rows, precision):

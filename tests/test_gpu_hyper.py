@@ -89,10 +89,12 @@ def test_prior_tables_byte_identical(name):
         assert np.array_equal(ctx.prior_table(ch), O.prior_freq(cfg, w, ch)), ch
 
 
-@pytest.mark.parametrize("name,nf", [("tiny_hp", 1), ("tiny_p_hp", 3)])
-def test_hyperprior_fp32_vs_oracle(name, nf):
+@pytest.mark.parametrize("name,nf,vary", [("tiny_hp", 1, False), ("tiny_p_hp", 3, False), ("tiny_p_hp", 2, True)])
+def test_hyperprior_fp32_vs_oracle(name, nf, vary):
+    """vary: every channel-wise scale and offset differs per channel (the
+    z-hat scale of the synthesis among them)."""
     cfg = synth.config(name)
-    w = synth.weights(cfg)
+    w = synth.weights(cfg, vary_consts=vary)
     fr = synth.frames(cfg, nf, seed=2301)
     ctx = psw.Context(cfg, w, precision=psw.PSW_FP32)
     res = _run(ctx, cfg, fr)

@@ -66,12 +66,14 @@ def _err(e, e_ref):
     return np.abs(e.astype(np.float64) - e_ref) / np.sqrt(np.mean(e_ref ** 2))
 
 
-@pytest.mark.parametrize("name", ["tiny_lrp", "tiny_p_lrp"])
-def test_lrp_fp32_vs_oracle_and_decoder(name):
+@pytest.mark.parametrize("name,vary", [("tiny_lrp", False), ("tiny_p_lrp", False), ("tiny_p_lrp", True)])
+def test_lrp_fp32_vs_oracle_and_decoder(name, vary):
     """FP32: eps of every frame against the oracle's; the decoder's eps
-    equals the encoder's bit for bit (four P-frames: the ring wraps)."""
+    equals the encoder's bit for bit (four P-frames: the ring wraps).  With
+    vary every channel-wise scale and offset differs per channel (the LRP's
+    latent scales among them)."""
     cfg = synth.config(name)
-    w = synth.weights(cfg)
+    w = synth.weights(cfg, vary_consts=vary)
     fr = synth.frames(cfg, 4 if cfg.temporal else 2, seed=2101)
     ctx = psw.Context(cfg, w, precision=psw.PSW_FP32)
     res = _code(ctx, fr)

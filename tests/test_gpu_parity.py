@@ -221,6 +221,34 @@ def test_edge_grids_fp32(grid):
     _check_frame(cfg, oracle_weights(cfg, w, psw.PSW_FP32), fr, res, psw.PSW_FP32, 0)
 
 
+@pytest.mark.parametrize("name,nf", [("tiny", 1), ("tiny_p", 3)])
+def test_per_channel_constants_fp32(name, nf):
+    """Every channel-wise scale and offset (latent and context embedding
+    scales, the z-hat scale, the heads' output scales and offsets) different
+    per channel: the default synthetic weights hold one value in every
+    channel, which would hide a wrong channel index or a dropped offset."""
+    cfg = synth.config(name)
+    w = synth.weights(cfg, vary_consts=True)
+    ctx = psw.Context(cfg, w, precision=psw.PSW_FP32)
+    fr = synth.frames(cfg, nf, seed=1007)
+    res = _encode_decode(ctx, cfg, fr, psw.PSW_SCHED_WAVEFRONT)
+    _check_frame(cfg, oracle_weights(cfg, w, psw.PSW_FP32), fr, res, psw.PSW_FP32, 0)
+
+
+def test_per_channel_constants_bf16_1080p_rows():
+    """The same at the 1080p model sizes in BF16 on a 12 x 120 grid coded as
+    its own frame: the heads' epilogues of the persistent kernel (the
+    encoder's masked pass, 1440 tokens) and of the one-tile kernel (the
+    decoder's steps) read the per-channel scales and offsets."""
+    base = synth.config("i1080")
+    w = synth.weights(base, vary_consts=True)
+    cfg = base.with_grid(12, base.W)
+    fr = synth.frames(cfg, 1, seed=1008)
+    ctx = psw.Context(base, w, precision=psw.PSW_BF16)
+    res = _encode_decode(ctx, cfg, fr, psw.PSW_SCHED_WAVEFRONT)
+    _check_frame(cfg, oracle_weights(base, w, psw.PSW_BF16), fr, res, psw.PSW_BF16, 0)
+
+
 # ----------------------------------------------------------- 1080p, BF16
 
 CROP = 12

@@ -163,10 +163,17 @@ def test_schedule_step_counts():
 
 # ----------------------------------------------------------- model
 
-@pytest.mark.parametrize("name", ["tiny", "tiny_cyc", "tiny_p", "tiny_ct", "tiny_cyc_ct", "tiny_p_ct"])
-def test_oracle_matches_dense_mask_formulation(name):
+@pytest.mark.parametrize("name,vary", [(n, False) for n in ("tiny", "tiny_cyc", "tiny_p", "tiny_ct", "tiny_cyc_ct",
+                                                              "tiny_p_ct")] +
+                         [("tiny", True), ("tiny_p", True), ("tiny_cyc_ct", True)])
+def test_oracle_matches_dense_mask_formulation(name, vary):
+    """The whole model against full [HW x HW] attention under the masks.
+    With vary, every channel-wise scale and offset (input and context
+    embedding scales, the Channel Transformer's latent scales, the heads'
+    output scales and offsets) differs per channel, so a wrong channel index
+    or a dropped offset shows."""
     c = synth.config(name)
-    w = synth.weights(c)
+    w = synth.weights(c, vary_consts=vary)
     fr = synth.frames(c, 3 if c.temporal else 1, seed=7)
     mu0, s0 = O.run(c, w, fr.y, fr.z, driver=0)
     mu1, s1 = dense_ref.run(c, w, fr.y, fr.z)
@@ -202,7 +209,7 @@ def test_lrp_temporal_oracle_matches_dense_mask_formulation():
     so that the three-frame ring wraps: the oracle's ring of per-block keys
     and values against dense attention over the concatenated frames."""
     c = synth.config("tiny_p_lrp")
-    w = synth.weights(c)
+    w = synth.weights(c, vary_consts=True)       # the LRP's latent scales per channel
     fr = synth.frames(c, 4, seed=16)
     mu0, s0, e0 = O.run(c, w, fr.y, fr.z, driver=0, with_eps=True)
     mu1, s1, e1 = dense_ref.run(c, w, fr.y, fr.z, with_eps=True)
@@ -356,8 +363,9 @@ def test_channel_transformer_lrp_on_its_output():
 
 # ----------------------------------------------------------- hyperprior
 
-@pytest.mark.parametrize("name,grid", [("tiny_hp", None), ("tiny_p_hp", None), ("i1080_hp", (9, 14))])
-def test_hyperprior_matches_dense_formulation(name, grid):
+@pytest.mark.parametrize("name,grid,vary", [("tiny_hp", None, False), ("tiny_p_hp", None, True),
+                                           ("i1080_hp", (9, 14), False)])
+def test_hyperprior_matches_dense_formulation(name, grid, vary):
     """Convolutional hyperprior (Fig. 1 right): the oracle's analysis (z
     from the Spatial Module 1 output through the RB-down blocks) and its
     synthesis (the hyperprior tokens from z-hat through the RB-up blocks,
@@ -367,7 +375,7 @@ def test_hyperprior_matches_dense_formulation(name, grid):
     c = synth.config(name)
     if grid:
         c = c.with_grid(*grid)
-    w = synth.weights(c)
+    w = synth.weights(c, vary_consts=vary)      # vary: the z-hat scales per channel as well
     fr = synth.frames(c, 2 if c.temporal else 1, seed=21)
     zh, z = O.hyper_analysis(c, w, fr.y)
     assert np.array_equal(zh, np.rint(z).astype(np.int16))
@@ -433,6 +441,51 @@ def test_factorized_prior_closed_form_without_gating():
         pm = np.array([sig(k + 0.5) - sig(k - 0.5) for k in range(-T, T + 1)])
         assert np.max(np.abs(f[:-1] / 65536.0 - pm)) < 2e-3
     assert abs(O.hyper_rate(c, w, zh) - bits) <= 1e-9 * bits
+
+
+def test_factorized_prior_table_rule_on_a_wide_prior():
+    """The z-hat tables' rule, slot by slot, on a prior wide and off-centre
+    enough that both tails beyond +-31.5 carry many counts: with the gates
+    at 0 and every softplus matrix entry at 0.25 the cumulative is
+    sigmoid(alpha x + beta) (alpha ~ 0.1), and slot v gets
+    1 + floor(P(v) (2^16 - 64)), the escape slot the same of both tails,
+    slot 0 the remainder (within one where P (2^16 - 64) lies within 1e-6
+    of an integer)."""
+    c = synth.config("tiny_hp")
+    w = synth.weights(c).astype(np.float64)
+    P = dense_ref.split_weights(c, w)
+    off, offs = 0, {}
+    for t in synth.weight_spec(c):
+        offs[t.name] = off
+        off += int(np.prod(t.shape))
+
+    def put(name, value):
+        n = int(np.prod(P[name].shape))
+        w[offs[name]:offs[name] + n] = value
+
+    raw = math.log(math.expm1(0.25))                 # softplus(raw) = 0.25
+    for k in (1, 2, 3):
+        put(f"hp.fp_a{k}", 0.0)
+    for k in (1, 2, 3, 4):
+        put(f"hp.fp_H{k}", raw)
+        put(f"hp.fp_b{k}", 0.0)
+    put("hp.fp_b4", 1.5)
+    alpha, beta = 27 * 0.25 ** 4, 1.5
+    sig = lambda x: 1.0 / (1.0 + np.exp(-(alpha * x + beta)))
+    T, n = 31, 64
+    v = np.arange(-T, T + 1, dtype=np.float64)
+    p = np.append(sig(v + 0.5) - sig(v - 0.5), sig(-T - 0.5) + (1.0 - sig(T + 0.5)))
+    x = p * (65536 - n)
+    want = 1 + np.floor(x).astype(np.int64)
+    near = np.abs(x - np.rint(x)) < 1e-6
+    rest = np.ones(n, bool)
+    rest[T] = False
+    assert sig(-T - 0.5) * 65536 > 100 and (1.0 - sig(T + 0.5)) * 65536 > 100
+    for ch in (0, c.Ch - 1):
+        f = O.prior_freq(c, w, ch).astype(np.int64)
+        assert np.array_equal(f[rest & ~near], want[rest & ~near])
+        assert np.all(np.abs(f[rest & near] - want[rest & near]) <= 1)
+        assert f[T] == 65536 - f[rest].sum()
 
 
 def test_zhat_coder_round_trip_escapes_and_corruption():
@@ -569,6 +622,31 @@ def test_cdf_table_invariants(l):
     assert np.all(q >= pmf * (1 - (2 * T + 2) / 65536.0) - 1e-15)
     kl = float(np.sum(pmf * np.log2(np.maximum(pmf, 1e-300) / q)))
     assert kl <= -math.log2(1 - (2 * T + 2) / 65536.0)
+
+
+@pytest.mark.parametrize("l", [0, 1, 10, 30, 45, 63])
+def test_cdf_table_closed_form(l):
+    """Every slot's frequency from its definition, evaluated through the
+    normal distribution function rather than erfc: slot s in -T..T gets
+    1 + floor(P(s) (2^16 - n)) with P(s) the mass of [s - 1/2, s + 1/2]
+    under N(0, sigma^2), the escape slot the same of P(|s| > T) (both tails),
+    and slot 0 the remainder to 2^16.  Where P (2^16 - n) lies within 1e-6 of
+    an integer the two evaluations may round apart by one."""
+    from scipy.special import ndtr
+    t = O.scale_table()
+    sg, T = float(t[l]), O.cdf_T(l)
+    n = 2 * T + 2
+    f = O.cdf_freq(l).astype(np.int64)
+    s = np.arange(-T, T + 1, dtype=np.float64)
+    p = np.append(ndtr((s + 0.5) / sg) - ndtr((s - 0.5) / sg), 2.0 * ndtr(-(T + 0.5) / sg))
+    x = p * (65536 - n)
+    want = 1 + np.floor(x).astype(np.int64)
+    near = np.abs(x - np.rint(x)) < 1e-6
+    rest = np.ones(n, bool)
+    rest[T] = False                                  # slot 0 takes the remainder
+    assert np.array_equal(f[rest & ~near], want[rest & ~near])
+    assert np.all(np.abs(f[rest & near] - want[rest & near]) <= 1)
+    assert f[T] == 65536 - f[rest].sum()
 
 
 # ----------------------------------------------------------- rANS

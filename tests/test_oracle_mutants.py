@@ -69,6 +69,30 @@ MUTANTS = [
      "for (int ff = f0; ff <= f; ff++) {\n                int sl = ff % c->Tf, age = f - ff;",
      "for (int ff = f; ff <= f; ff++) {\n                int sl = ff % c->Tf, age = f - ff;",
      "dense_mask_formulation"),
+    ("ct_mask_reads_next_group", "(i / dg <= o / dg) ? M", "(i / dg <= o / dg + 1) ? M",
+     "channel_groups_causal or dense_mask_formulation"),
+    ("ct_mask_drops_own_group", "(i / dg <= o / dg) ? M", "(i / dg < o / dg) ? M", "dense_mask_formulation"),
+    ("ct_group_norm_over_all_groups",
+     "for (int j = 0; j < G; j++) or_rmsnorm(x + (long)j * w, g + (long)j * w, w, y + (long)j * w);",
+     "or_rmsnorm(x, g, n, y);", "channel_groups_causal or dense_mask_formulation"),
+    ("context_padding_zero", "if (f == 0) memcpy(g + (long)p * d, WP(s->lay.pad), sizeof(double) * d);",
+     "if (f == 0) memset(g + (long)p * d, 0, sizeof(double) * d);", "dense_mask_formulation"),
+    ("context_final_norm_gain", "or_rmsnorm(g + (long)p * d, WP(s->lay.g_ctx), d, cn);",
+     "or_rmsnorm(g + (long)p * d, WP(s->lay.ctx[0].g_attn), d, cn);", "dense_mask_formulation"),
+    ("cross_keys_from_value_weights", "or_matvec(cn, WP(bw->Wxk), d, d, s->XK + base);",
+     "or_matvec(cn, WP(bw->Wxv), d, d, s->XK + base);", "dense_mask_formulation"),
+    ("hyper_tap_index_transposed", "int sub = (i % c->r) * c->r + (j % c->r);",
+     "int sub = (j % c->r) * c->r + (i % c->r);", "dense_mask_formulation"),
+    ("latent_embedding_bias_dropped", "for (int e = 0; e < c->d; e++) out[e] += WP(b_off)[e];", "",
+     "dense_mask_formulation"),
+    ("accumulator_residual_dropped", "xp[e] = ep[e] + t[e];", "xp[e] = t[e];", "dense_mask_formulation"),
+    ("sigma_lower_clamp_dropped",
+     "if (v < lo) v = lo;\n        if (v > hi) v = hi;\n        s->sigma[(long)p * C + ch]",
+     "if (v > hi) v = hi;\n        s->sigma[(long)p * C + ch]", "sigma_clamped"),
+    ("sigma_upper_clamp_grouped_heads_dropped",
+     "if (v > hi) v = hi;\n            s->sigma[(long)p * C + cc]", "s->sigma[(long)p * C + cc]", "sigma_clamped"),
+    ("lrp_reads_module1_stream", "or_rmsnorm(s->x2 + (long)p * d, WP(s->lay.lrp_g_rep), d, nr);",
+     "or_rmsnorm(s->x1 + (long)p * d, WP(s->lay.lrp_g_rep), d, nr);", "lrp"),
     ("pixel_shuffle_transposed", "(2 * a + b) * C + c]", "(2 * b + a) * C + c]", "hyperprior_matches_dense"),
     ("conv_tap_wrong_column", "int ii = st * i + di - 1, jj = st * j + dj - 1;",
      "int ii = st * i + di - 1, jj = st * j + di - 1;", "hyperprior_matches_dense"),

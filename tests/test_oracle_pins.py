@@ -181,6 +181,32 @@ def test_oracle_matches_dense_mask_formulation(name, vary):
     assert np.max(np.abs(np.log(s0) - np.log(s1))) < 1e-11
 
 
+@pytest.mark.parametrize("name", ["tiny", "tiny_ct"])
+def test_heads_sigma_clamped_at_both_ends(name):
+    """sigma = exp of the scaled head output clamped to [ln 0.11, ln 256]
+    (Sec. 3.1 heads; the scale table's range): with the offsets of some
+    channels far below and of others far above the range, those channels
+    come out at exactly the clamp values and the rest as the dense
+    formulation gives them (the plain heads and the grouped heads)."""
+    c = synth.config(name)
+    w = synth.weights(c).astype(np.float64)
+    off = 0
+    for t in synth.weight_spec(c):
+        if t.name == "beta_sig":
+            break
+        off += int(np.prod(t.shape))
+    lo_ch, hi_ch = np.arange(0, c.C, 4), np.arange(1, c.C, 4)
+    w[off + lo_ch] = -12.0
+    w[off + hi_ch] = 14.0
+    fr = synth.frames(c, 1, seed=9)
+    mu0, s0 = O.run(c, w, fr.y, fr.z, driver=0)
+    mu1, s1 = dense_ref.run(c, w, fr.y, fr.z)
+    assert np.all(s0[..., lo_ch] == math.exp(math.log(0.11)))
+    assert np.all(s0[..., hi_ch] == math.exp(math.log(256.0)))
+    assert np.max(np.abs(mu0 - mu1)) < 1e-11
+    assert np.max(np.abs(np.log(s0) - np.log(s1))) < 1e-11
+
+
 @pytest.mark.parametrize("grid", [None, (5, 7), (1, 9)])
 def test_lrp_oracle_matches_dense_mask_formulation(grid):
     """The LRP Transformer's residual (Sec. 3.1): the oracle's per-position

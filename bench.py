@@ -121,9 +121,18 @@ class Clocks:
         self.proc.terminate()
         self.proc.wait()
         self.f.flush(); self.f.seek(0)
+        text = self.f.read()
+        os.unlink(self.f.name)
+        return self.summarise(text)
+
+    @staticmethod
+    def summarise(text: str) -> dict:
+        """Median SM clock, the maximum clock and the throttle reasons seen
+        active in nvidia-smi's CSV rows (the query Q, no header, no units);
+        rows that do not parse are skipped."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f.read().splitlines():
+        for line in text.splitlines():
             parts = [x.strip() for x in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -134,7 +143,6 @@ class Clocks:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
-        os.unlink(self.f.name)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 

@@ -59,3 +59,40 @@ def test_replicas_decode_distinct_frames():
 def test_reference_arm_runs_on_rank_zero_only():
     args = bench.parse(["--impl", "reference", "--steps", "1", "--warmup", "3"])
     assert bench.run_reference(args, rank=1) == 0          # no work, no output
+
+
+def test_clock_samples_summary():
+    """nvidia-smi rows (index, SM MHz, max MHz, power, active mask, then the
+    four reasons): the median SM clock, the maximum, every reason seen
+    active once, unparsable rows skipped."""
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 1200.5, 0x0, Not Active, Active, Not Active, Not Active",
+        "garbage",
+    ]
+    s = bench.Clocks.summarise("\n".join(rows))
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+    s = bench.Clocks.summarise("0, 1500, 2070, 1000, 0x8, Active, Not Active, Not Active, Not Active")
+    assert s["reasons"] == ["hw_slowdown"] and s["sm_mhz"] == 1500.0
+    assert bench.Clocks.summarise("")["sm_mhz"] is None
+
+
+def test_traffic_figure_is_dropped_once_its_kernel_source_changes(tmp_path, monkeypatch):
+    """The committed DRAM-traffic figure is reported only while the hash of
+    the kernel source it was taken on still matches."""
+    import hashlib
+    import json
+    src = tmp_path / "k.cu"
+    src.write_text("// kernel\n")
+    (tmp_path / "profiles").mkdir()
+    entry = {"source": "k.cu", "sha256": hashlib.sha256(src.read_bytes()).hexdigest(),
+             "dram_bytes_per_launch": 123.0}
+    (tmp_path / "profiles" / "traffic.txt").write_text(json.dumps({"k": entry}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_for("k") == 123.0
+    assert bench.traffic_for("other") is None
+    src.write_text("// kernel, changed\n")
+    assert bench.traffic_for("k") is None

@@ -115,6 +115,15 @@ MUTANTS = [
      "cdf_table_closed_form"),
     ("cdf_support_narrower", "int T = (int)ceil(7.0 * (double)tab[l]);", "int T = (int)ceil(6.0 * (double)tab[l]);",
      "cdf"),
+    ("rans_escape_digit_order", "for (int q = 1; q >= 0; q--) {     /* d1 first: decoded last */",
+     "for (int q = 0; q < 2; q++) {", "rans"),
+    ("rans_escape_sign", "sv = (vv & 1) ? -mag : mag;", "sv = (vv & 1) ? mag : -mag;", "rans"),
+    ("rans_decoder_lane", "int lane = (int)(k % 32), l = idx[(long)a * D->C + c], T = D->tb.T[l];",
+     "int lane = (int)((k + 1) % 32), l = idx[(long)a * D->C + c], T = D->tb.T[l];", "rans"),
+    ("rans_final_state_unchecked", "for (int l = 0; l < 32; l++) if (D->x[c][l] != OR_LOW) bad = 1;", "",
+     "rans"),
+    ("rans_latent_range_unchecked", "if (yv < -32768 || yv > 32767) { D->err = 1; yv = 0; }", "",
+     "outside_int16"),
     ("e4m3_ties_away", "double v = nearbyint(a / q) * q;", "double v = round(a / q) * q;", "e4m3"),
     ("e4m3_subnormal_step", "if (e < -6) e = -6;", "if (e < -7) e = -7;", "e4m3"),
     ("scale_index_strict", "if (tab[t] >= sigma[a]) { l = t; break; }", "if (tab[t] > sigma[a]) { l = t; break; }",

@@ -753,6 +753,26 @@ def test_rans_detects_corruption():
     assert flips == 20
 
 
+def test_rans_decoded_latent_outside_int16_is_an_error():
+    """A container decoded against means other than the encoder's can give a
+    latent m + s outside int16: that is reported as corrupt, not wrapped.
+    y = +-32767 coded at mean 0; decoding with the means moved 10 outward
+    leaves the int16 range at exactly those positions, while moving them 10
+    inward gives y -+ 10 and no error."""
+    c = synth.config("tiny").with_grid(2, 3)
+    y = np.zeros((c.H, c.W, c.C), np.int16)
+    y[0, 0, 0], y[1, 2, c.C - 1] = 32767, -32767
+    idx = np.full(y.shape, 10, np.uint8)
+    m = np.zeros(y.shape, np.int32)
+    bs = O.rans_encode(c, 0, y, idx, m)
+    assert O.rans_decode(c, 0, idx, m, bs)[0]
+    out = m.copy()
+    out[0, 0, 0], out[1, 2, c.C - 1] = 10, -10
+    assert not O.rans_decode(c, 0, idx, out, bs)[0]
+    ok, yd = O.rans_decode(c, 0, idx, -out, bs)
+    assert ok and yd[0, 0, 0] == 32757 and yd[1, 2, c.C - 1] == -32757
+
+
 def test_encode_decode_round_trip_through_the_model():
     for nm, nf in (("tiny", 1), ("tiny_p", 3), ("tiny_ct", 1), ("tiny_cyc_ct", 1), ("tiny_p_ct", 2)):
         c = synth.config(nm)

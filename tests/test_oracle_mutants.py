@@ -124,6 +124,12 @@ MUTANTS = [
      "rans"),
     ("rans_latent_range_unchecked", "if (yv < -32768 || yv > 32767) { D->err = 1; yv = 0; }", "",
      "outside_int16"),
+    ("window_radius_short", "for (int di = -w; di <= w; di++) {", "for (int di = -w; di < w; di++) {",
+     "dense_mask_formulation or lrp"),
+    ("mean_truncated_not_rounded", "m[a] = (int32_t)rintf(mc);", "m[a] = (int32_t)mc;", "quantize"),
+    ("likelihood_floor_lower", "return p < 1e-9 ? 1e-9 : p;", "return p < 1e-12 ? 1e-12 : p;", "likelihood or rate"),
+    ("e4m3_tensor_scale_exponent", "s = ldexp(1.0, e - 7);", "s = ldexp(1.0, e - 8);", "e4m3"),
+    ("e4m3_saturation", "if (v > 448.0) v = 448.0;", "if (v > 480.0) v = 480.0;", "e4m3"),
     ("e4m3_ties_away", "double v = nearbyint(a / q) * q;", "double v = round(a / q) * q;", "e4m3"),
     ("e4m3_subnormal_step", "if (e < -6) e = -6;", "if (e < -7) e = -7;", "e4m3"),
     ("scale_index_strict", "if (tab[t] >= sigma[a]) { l = t; break; }", "if (tab[t] > sigma[a]) { l = t; break; }",

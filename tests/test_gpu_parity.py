@@ -160,6 +160,33 @@ def test_rans_corruption_reported_not_faulted():
     assert np.array_equal(yo.cpu().numpy(), y)
 
 
+def test_rans_decoded_latent_outside_int16_reported():
+    """A container decoded against means other than the encoder's can give a
+    latent m + s outside int16: the decoder reports it as corrupt rather
+    than wrapping it (the oracle's rule); means moved inward decode to the
+    shifted latents, as the oracle's decoder gives them."""
+    base = synth.config("tiny")
+    c = base.with_grid(2, 3)
+    ctx, _ = _ctx(base, psw.PSW_FP32)
+    seq = ctx.seq_create(2, 3)
+    y = np.zeros((2, 3, c.C), np.int16)
+    y[0, 0, 0], y[1, 2, c.C - 1] = 32767, -32767
+    idx = np.full(y.shape, 10, np.uint8)
+    m = np.zeros(y.shape, np.int32)
+    fd = psw.frame_desc(2, 3, 0)
+    bs = torch.zeros(ctx.bitstream_capacity(2, 3), dtype=torch.uint8, device=dev())
+    n = seq.rans_encode(fd, _t(y), _t(idx), _t(m), bs)
+    out = m.copy()
+    out[0, 0, 0], out[1, 2, c.C - 1] = 10, -10
+    yo = torch.zeros(y.shape, dtype=torch.int16, device=dev())
+    assert seq.rans_decode(fd, bs, n, _t(idx), _t(out), yo, check=False) == psw.PSW_ERR_CORRUPT
+    seq.rans_decode(fd, bs, n, _t(idx), _t(-out), yo)
+    yd = yo.cpu().numpy()
+    assert yd[0, 0, 0] == 32757 and yd[1, 2, c.C - 1] == -32757
+    ok, y_o = O.rans_decode(c, 0, idx, -out, bs[:n].cpu().numpy().tobytes())
+    assert ok and np.array_equal(yd, y_o)
+
+
 # ----------------------------------------------------------- model parity
 
 def _check_frame(cfg, w64, fr, res, precision, sched, oracle_mu=None, oracle_sg=None):
@@ -232,6 +259,29 @@ def test_per_channel_constants_fp32(name, nf):
     ctx = psw.Context(cfg, w, precision=psw.PSW_FP32)
     fr = synth.frames(cfg, nf, seed=1007)
     res = _encode_decode(ctx, cfg, fr, psw.PSW_SCHED_WAVEFRONT)
+    _check_frame(cfg, oracle_weights(cfg, w, psw.PSW_FP32), fr, res, psw.PSW_FP32, 0)
+
+
+def test_sigma_clamped_at_both_ends_fp32():
+    """Heads whose scaled output leaves [ln 0.11, ln 256]: the offsets of
+    every fourth channel far below the range and of the next far above it;
+    sigma is clamped on the GPU as in the oracle, and the rest of the frame
+    keeps its tolerance, decoding and container checks."""
+    cfg = synth.config("tiny")
+    w = synth.weights(cfg)
+    off = 0
+    for t in synth.weight_spec(cfg):
+        if t.name == "beta_sig":
+            break
+        off += int(np.prod(t.shape))
+    w = w.copy()
+    w[off + np.arange(0, cfg.C, 4)] = -12.0
+    w[off + np.arange(1, cfg.C, 4)] = 14.0
+    ctx = psw.Context(cfg, w, precision=psw.PSW_FP32)
+    fr = synth.frames(cfg, 1, seed=1009)
+    res = _encode_decode(ctx, cfg, fr, psw.PSW_SCHED_WAVEFRONT)
+    sg = res[0]["sg"]
+    assert np.allclose(sg[..., 0::4], 0.11, rtol=1e-6) and np.allclose(sg[..., 1::4], 256.0, rtol=1e-6)
     _check_frame(cfg, oracle_weights(cfg, w, psw.PSW_FP32), fr, res, psw.PSW_FP32, 0)
 
 

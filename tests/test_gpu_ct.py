@@ -112,15 +112,18 @@ def test_ct_per_channel_constants_fp32():
     _check(res, fr, cfg, mu_o, sg_o, FP32_TOL, 0, pct=False)
 
 
-@pytest.mark.parametrize("name,rows,precision", [("i1080_ct", 8, psw.PSW_BF16), ("i1080_cyc_ct", 8, psw.PSW_BF16),
-                                                 ("i1080_cyc_ct", 8, psw.PSW_FP8)])
-def test_ct_1080p_width_vs_oracle(name, rows, precision):
+@pytest.mark.parametrize("name,rows,precision,vary", [("i1080_ct", 8, psw.PSW_BF16, False),
+                                                      ("i1080_cyc_ct", 8, psw.PSW_BF16, False),
+                                                      ("i1080_cyc_ct", 8, psw.PSW_FP8, False),
+                                                      ("i1080_cyc_ct", 8, psw.PSW_BF16, True)])
+def test_ct_1080p_width_vs_oracle(name, rows, precision, vary):
     """The 1080p model sizes with the Channel Transformer (4 groups, width
     1024, 2 blocks) on a rows x 120 grid coded as its own frame by both
     sides: BF16, and an FP8 context (E4M3 entropy-model blocks; the Channel
-    Transformer stays BF16)."""
+    Transformer stays BF16); vary: every channel-wise scale and offset
+    differs per channel (the grouped heads' epilogues on the tensor cores)."""
     base = synth.config(name)
-    w = synth.weights(base)
+    w = synth.weights(base, vary_consts=vary)
     cfg = base.with_grid(rows, base.W)
     fr = synth.frames(cfg, 1, seed=2202)
     ctx = psw.Context(base, w, precision=precision)

@@ -130,6 +130,21 @@ MUTANTS = [
     ("likelihood_floor_lower", "return p < 1e-9 ? 1e-9 : p;", "return p < 1e-12 ? 1e-12 : p;", "likelihood or rate"),
     ("e4m3_tensor_scale_exponent", "s = ldexp(1.0, e - 7);", "s = ldexp(1.0, e - 8);", "e4m3"),
     ("e4m3_saturation", "if (v > 448.0) v = 448.0;", "if (v > 480.0) v = 480.0;", "e4m3"),
+    # self-consistent coder changes (round trips still pass): only a reader
+    # of the format written apart from the oracle catches them
+    ("container_escape_digits_swapped",
+     ("for (int q = 1; q >= 0; q--) {     /* d1 first: decoded last */", "uint32_t vv = dig[0] | (dig[1] << 16);"),
+     ("for (int q = 0; q < 2; q++) {", "uint32_t vv = dig[1] | (dig[0] << 16);"), "independent_reader"),
+    ("container_lanes_reversed",
+     ("int lane = (int)(k % 32), l = idx[a], T = tb.T[l];",
+      "int lane = (int)(k % 32), l = idx[(long)a * D->C + c], T = D->tb.T[l];"),
+     ("int lane = 31 - (int)(k % 32), l = idx[a], T = tb.T[l];",
+      "int lane = 31 - (int)(k % 32), l = idx[(long)a * D->C + c], T = D->tb.T[l];"), "independent_reader"),
+    ("container_header_H_W_swapped",
+     ("put16(out + 8, (uint16_t)H); put16(out + 10, (uint16_t)W);",
+      "get16(buf + 8) != H || get16(buf + 10) != W"),
+     ("put16(out + 8, (uint16_t)W); put16(out + 10, (uint16_t)H);",
+      "get16(buf + 8) != W || get16(buf + 10) != H"), "independent_reader"),
     ("e4m3_ties_away", "double v = nearbyint(a / q) * q;", "double v = round(a / q) * q;", "e4m3"),
     ("e4m3_subnormal_step", "if (e < -6) e = -6;", "if (e < -7) e = -7;", "e4m3"),
     ("scale_index_strict", "if (tab[t] >= sigma[a]) { l = t; break; }", "if (tab[t] > sigma[a]) { l = t; break; }",
@@ -159,9 +174,14 @@ def _run_pins(tmp_path, name, source, kexpr):
 def _case(tmp_path, mutant):
     name, old, new, kexpr = mutant
     src = open(SRC).read()
-    if src.count(old) != 1:
-        return name, "the mutated text does not occur exactly once in the oracle"
-    rc, built, last = _run_pins(tmp_path, name, src.replace(old, new), kexpr)
+    # a tuple: one mistake made at several places that agree with each other
+    # (the encoder and the decoder changed together)
+    pairs = list(zip(old, new)) if isinstance(old, tuple) else [(old, new)]
+    for o, n in pairs:
+        if src.count(o) != 1:
+            return name, "the mutated text does not occur exactly once in the oracle"
+        src = src.replace(o, n)
+    rc, built, last = _run_pins(tmp_path, name, src, kexpr)
     if not built:
         return name, "the mutated oracle did not build: " + last
     # 1: some pin failed; a signal: the oracle crashed under the pins (e.g. a

@@ -733,6 +733,30 @@ def test_rans_size_bound():
     assert (len(bs) - hdr) * 8 <= bits + slack
 
 
+@pytest.mark.parametrize("name,sched,grid", [("tiny", 0, None), ("tiny", 1, None), ("tiny_cyc", 0, None),
+                                            ("tiny", 0, (3, 37)), ("tiny", 0, (1, 1))])
+def test_rans_container_read_by_an_independent_reader(name, sched, grid):
+    """The oracle's containers read back by a plain reader written from the
+    format alone (tests/rans_ref.py: header, offsets, lane states, word
+    order, slots, escape digits, schedule order, final states): random
+    symbols with escapes and int16 extremes, 2i+j, raster and cyclic orders,
+    a ragged and a 1 x 1 grid."""
+    import rans_ref
+    c = synth.config(name)
+    if grid:
+        c = c.with_grid(*grid)
+    rng = np.random.default_rng(31 + sched)
+    y, idx, m = _coder_case(c, rng, scale=1.5)
+    y[..., 0] = rng.choice([-32767, 32767], size=y.shape[:2])
+    idx[..., 0] = 0
+    m[..., 0] = 0
+    bs = O.rans_encode(c, sched, y, idx, m)
+    freqs = {l: O.cdf_freq(l).astype(np.int64) for l in range(64)}
+    HW = c.H * c.W
+    yd = rans_ref.decode(bs, c.H, c.W, c.C, sched, c.mask, idx.reshape(HW, c.C), m.reshape(HW, c.C), freqs)
+    assert np.array_equal(yd.reshape(y.shape), y.astype(np.int64))
+
+
 def test_rans_detects_corruption():
     c = synth.config("tiny")
     rng = np.random.default_rng(9)

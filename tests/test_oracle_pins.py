@@ -757,6 +757,24 @@ def test_rans_container_read_by_an_independent_reader(name, sched, grid):
     assert np.array_equal(yd.reshape(y.shape), y.astype(np.int64))
 
 
+def test_zhat_container_read_by_an_independent_reader():
+    """The z-hat container (raster order over the hyperprior grid, channel
+    ch coded with its factorized-prior table about mean 0) read back by the
+    same plain reader, with escapes past the tables' +-31 support."""
+    import rans_ref
+    c = synth.config("tiny_hp")
+    w = synth.weights(c).astype(np.float64)
+    rng = np.random.default_rng(41)
+    zh = rng.integers(-6, 7, size=(c.Hh, c.Wh, c.Ch)).astype(np.int16)
+    zh[0, 0, :4] = [40, -40, 32767, -32768]
+    bs = O.hyper_encode(c, w, zh)
+    HW = c.Hh * c.Wh
+    freqs = {ch: O.prior_freq(c, w, ch).astype(np.int64) for ch in range(c.Ch)}
+    idx = np.tile(np.arange(c.Ch), (HW, 1))
+    zd = rans_ref.decode(bs, c.Hh, c.Wh, c.Ch, 1, 0, idx, np.zeros((HW, c.Ch), np.int64), freqs)
+    assert np.array_equal(zd.reshape(zh.shape), zh.astype(np.int64))
+
+
 def test_rans_detects_corruption():
     c = synth.config("tiny")
     rng = np.random.default_rng(9)

@@ -61,6 +61,24 @@ def test_reference_arm_runs_on_rank_zero_only():
     assert bench.run_reference(args, rank=1) == 0          # no work, no output
 
 
+def test_reference_arm_line_on_rank_zero(capsys):
+    """Rank 0 times the FP64 oracle on a one-row crop and prints one JSON
+    line with the reference arm's keys: the same metric and unit as ours,
+    its own cpu_baseline (the oracle, the threads used, the sample) and an
+    e2e object with no host-device bytes."""
+    import json
+    args = bench.parse(["--impl", "reference", "--steps", "1", "--warmup", "0", "--cpu-rows", "1"])
+    assert bench.run_reference(args, rank=0) == 0
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "frames/s"
+    assert d["higher_is_better"] is True and d["value"] > 0 and d["dtype"] == "f64"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "1 rows" in cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
 def test_clock_samples_summary():
     """nvidia-smi rows (index, SM MHz, max MHz, power, active mask, then the
     four reasons): the median SM clock, the maximum, every reason seen

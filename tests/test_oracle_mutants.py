@@ -43,6 +43,8 @@ MUTANTS = [
      "if (mask == 0) ok = ok;", "fig2b or interior or same_step"),
     ("relative_bias_index_transposed", "off[n] = (di + w) * c->k + (dj + w);",
      "off[n] = (dj + w) * c->k + (di + w);", "dense_mask_formulation"),
+    ("relative_bias_by_absolute_column", "off[n] = (di + w) * c->k + (dj + w);",
+     "off[n] = (di + w) * c->k + (qj % c->k);", "translation"),
     ("attention_residual_dropped",
      "or_matvec(o, WP(bw->Wo), d, d, t);\n    for (int e = 0; e < d; e++) xp[e] += t[e];\n    if (c->temporal)",
      "or_matvec(o, WP(bw->Wo), d, d, t);\n    for (int e = 0; e < d; e++) xp[e] = t[e];\n    if (c->temporal)",

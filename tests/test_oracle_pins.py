@@ -181,6 +181,31 @@ def test_oracle_matches_dense_mask_formulation(name, vary):
     assert np.max(np.abs(np.log(s0) - np.log(s1))) < 1e-11
 
 
+@pytest.mark.parametrize("name", ["tiny", "tiny_cyc", "tiny_ct", "tiny_hp"])
+def test_translation_equivariance_away_from_borders(name):
+    """Window attention with relative biases under masks that depend only on
+    relative offsets (2i+j: label differences and, within a label, the
+    raster order; cyclic: labels of period 4): shifting the latents right by
+    4 columns and the hyperlatents by 4 / r shifts every parameter by 4
+    columns, bit for bit, wherever neither frame's border lies within the
+    model's reach (L w + w + L w = 10 columns here; 12 kept clear)."""
+    c = synth.config(name).with_grid(8, 44)
+    w = synth.weights(c)
+    fr = synth.frames(c, 1, seed=51)
+    s, sz = 4, 4 // c.r
+    y2 = np.zeros_like(fr.y)
+    y2[:, :, s:] = fr.y[:, :, :-s]
+    z2 = np.zeros_like(fr.z)
+    z2[:, :, sz:] = fr.z[:, :, :-sz]
+    mu0, s0 = O.run(c, w, fr.y, fr.z, driver=0)
+    mu1, s1 = O.run(c, w, y2, z2, driver=0)
+    cols = np.arange(12, c.W - s - 12)
+    assert np.array_equal(mu1[0][:, cols + s], mu0[0][:, cols])
+    assert np.array_equal(s1[0][:, cols + s], s0[0][:, cols])
+    # the comparison is not vacuous: the parameters differ between columns
+    assert not np.array_equal(mu0[0][:, cols + s], mu0[0][:, cols])
+
+
 @pytest.mark.parametrize("name", ["tiny", "tiny_ct"])
 def test_heads_sigma_clamped_at_both_ends(name):
     """sigma = exp of the scaled head output clamped to [ln 0.11, ln 256]

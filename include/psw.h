@@ -367,7 +367,7 @@ psw_status psw_rans_decode(psw_ctx *ctx, psw_seq *seq, const psw_frame_desc *fd,
  *   Limits: H*W <= 32768, C <= 256, H*W*C <= 1572864 (one 68 x 120 x 192
  *   latent frame); larger frames return PSW_ERR_INVALID.
  *   The first call on a device looks up the array's device address for that
- *   device; make that first call before any stream capture on the device.
+ *   device.
  *   Every call shares the array (the previous call's contents remain; the
  *   call clears what it needs), so calls whose GPU work overlaps -- on two
  *   streams, or from two host threads -- race; serialise them.

@@ -4,12 +4,13 @@ Some callers cannot allocate device memory where they encode (their device
 memory is handed out by another allocator or capped by a quota, or their
 loops forbid allocation after warm-up).  This entry point keeps its
 scratch in a static device array instead; its containers must be the same
-bytes the allocating coder produces, call after call.  Collected last so
+bytes the allocating coder and the oracle's coder produce, call after call.  Collected last so
 that a failure here comes after every other test has run.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 from gpu_util import dev, need_gpu, torch
 from paper_2605_20977_gb300 import psw, synth
 
@@ -43,6 +44,9 @@ def test_noalloc_encoder_matches_allocating_encoder_two_calls():
         st, n = ctx.rans_encode_noalloc(fd, y, idx, m, out)
         assert st == psw.PSW_OK and n == n_ref
         assert torch.equal(out[:n].cpu(), ref[:n_ref].cpu()), call
+        # and the oracle coder's bytes for the same symbols
+        assert out[:n].cpu().numpy().tobytes() == O.rans_encode(c, sched, y.cpu().numpy(), idx.cpu().numpy(),
+                                                                m.cpu().numpy()), call
         # the container decodes back to the symbols
         yd = torch.zeros_like(y)
         seq.rans_decode(fd, out, n, idx, m, yd)

@@ -222,6 +222,20 @@ def oracle_single_thread(rows: int = 1):
 
 # ------------------------------------------------------------------ reference arm
 
+def arm_config(args, world: int, engine: int) -> dict:
+    """The workload's config object, the same on both arms (the reference
+    arm's sample of it is described in its cpu_baseline).  engine: 2 for the
+    persistent decoder, else the graph engine."""
+    return {"workload": WORKLOAD if args.precision == "bf16" else WORKLOAD.replace(
+                "BF16 projections", "E4M3 block projections (BF16 embedding and heads)"),
+            "frames_per_step": args.batch,
+            "l2": "flushed between steps (256 MiB write)",
+            "launch": ("persistent: per-frame prologue in a CUDA graph, then one cooperative kernel "
+                       "(one CTA per SM, grid barrier between phases) over all wavefront steps"
+                       if engine == 2 else "CUDA graph per batch shape (segments of 512 wavefront steps)"),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def run_reference(args, rank: int):
     if rank != 0:
         return 0
@@ -241,7 +255,7 @@ def run_reference(args, rank: int):
             "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample_rows": rows},
+            "config": arm_config(args, args.gpus, 2 if args.engine == "persistent" else 1),
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -873,13 +887,7 @@ def run_ours(args, rank: int, world: int, local: int):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "e4m3+bf16",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.precision == "bf16" else WORKLOAD.replace(
-                           "BF16 projections", "E4M3 block projections (BF16 embedding and heads)"), "frames_per_step": B,
-                       "l2": "flushed between steps (256 MiB write)",
-                       "launch": ("persistent: per-frame prologue in a CUDA graph, then one cooperative kernel "
-                                  "(one CTA per SM, grid barrier between phases) over all wavefront steps"
-                                  if engine == 2 else "CUDA graph per batch shape (segments of 512 wavefront steps)"),
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": arm_config(args, world, engine),
             "e2e": {"value": e2e_value, "unit": "frames/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(round(launches)),
             "latency_one_frame": lat,

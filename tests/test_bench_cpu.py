@@ -77,6 +77,8 @@ def test_reference_arm_line_on_rank_zero(capsys):
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "1 rows" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    # the same config object as our arm's for the same flags
+    assert d["config"] == bench.arm_config(args, 1, 1)
 
 
 def test_clock_samples_summary():

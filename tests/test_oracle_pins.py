@@ -182,6 +182,29 @@ def test_oracle_matches_dense_mask_formulation(name, vary):
 
 
 @pytest.mark.parametrize("name", ["tiny", "tiny_cyc", "tiny_ct", "tiny_hp"])
+def test_translation_equivariance_downwards(name):
+    """The same for a shift of 4 rows down (hyperlatents 4 / r rows): every
+    row whose dependencies stay clear of the top and bottom borders in both
+    frames (the model's reach, 10 rows, each way: the cyclic mask sees lower
+    labels below a position, and the convolutional hyperprior's synthesis
+    reaches below it) shifts with the latents, bit for bit, across the whole
+    width."""
+    c = synth.config(name).with_grid(32, 16)
+    w = synth.weights(c)
+    fr = synth.frames(c, 1, seed=52)
+    s, sz = 4, 4 // c.r
+    y2 = np.zeros_like(fr.y)
+    y2[:, s:] = fr.y[:, :-s]
+    z2 = np.zeros_like(fr.z)
+    z2[:, sz:] = fr.z[:, :-sz]
+    mu0, s0 = O.run(c, w, fr.y, fr.z, driver=0)
+    mu1, s1 = O.run(c, w, y2, z2, driver=0)
+    rows = np.arange(10, c.H - s - 10)
+    assert np.array_equal(mu1[0][rows + s], mu0[0][rows]) and np.array_equal(s1[0][rows + s], s0[0][rows])
+    assert not np.array_equal(mu0[0][rows + s], mu0[0][rows])
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiny_cyc", "tiny_ct", "tiny_hp"])
 def test_translation_equivariance_away_from_borders(name):
     """Window attention with relative biases under masks that depend only on
     relative offsets (2i+j: label differences and, within a label, the
